@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the iterative polarizability solve on one GB300 (or N, each
+solving its own share of the frequencies).
+
+One step = one group of frequencies x 3 field directions solved to the
+workload's tolerance through the whole hot path (RHS formation chi0 . d,
+then GMRES with A z = z - chi0 (K z) until every right-hand side meets
+||b - A x|| / ||b|| <= tol, then P = d . X).  The metric is omega-points/s
+(an omega-point counts once all three directions converged).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload medium64]
+    python bench.py --impl reference     # the CPU oracle on the host cores
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1005_5340_gb300 import synth  # noqa: E402
+
+METRIC = "omega-points/s at 1e-6 rel. residual"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (DFMA) nominal rate; no tensor path for FP64
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="medium64")
+    p.add_argument("--omega-per-step", type=int, default=64)
+    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--cpu-sample", type=int, default=0,
+                   help="omega-points in the CPU-oracle sample (0: one per 3 host cores)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work
+# ---------------------------------------------------------------------------
+def chi0_flops_per_rhs(s) -> float:
+    """Algorithmic flops of one chi0 . v for one complex vector (same count for
+    every form): the two transforms, the block-sparse beta and G contractions
+    over the nonzero orbital blocks (mirrors included), the vertex sums and
+    the D(omega) scaling."""
+    n_orb, n_occ = s.n_orb, s.n_occ
+    n_virt = n_orb - n_occ
+    pairs = {(int(a), int(b)) for a, b in s.prod_atoms}
+    nb = sum(1 if a == b else 2 for a, b in pairs)
+    blk = 13 * 13
+    return (8.0 * n_orb * n_virt * n_occ + 8.0 * blk * n_occ * nb + 8.0 * blk * s.n_prod
+            + 6.0 * n_occ * n_virt)
+
+
+def omega_schedule(n_omega: int, rank: int, world: int, per_step: int):
+    """Round-robin share of the frequency grid for this rank (the paper's
+    distribution of frequencies over processes), cut into step groups."""
+    mine = np.arange(rank, n_omega, world)
+    groups = [mine[i:i + per_step] for i in range(0, mine.size, per_step)]
+    return [g for g in groups if g.size]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def cpu_oracle_run(workload: str, n_points: int, cores: int, pool_state: dict | None = None):
+    import oracle.tddft_oracle as O
+    w = synth.WORKLOADS[workload]
+    om = synth.omega_grid(w["n_omega"], w["w_hi"])
+    pick = om[np.linspace(0, om.size - 1, n_points).round().astype(int)]
+    t0 = time.perf_counter()
+    P, infos = O.polarizability_gmres_parallel((synth.workload_system, (workload,)), pick,
+                                               w["eps"], w["restart"], w["tol"], workers=cores)
+    dt = time.perf_counter() - t0
+    conv = all(i["converged"] for i in infos)
+    return n_points / dt, dt, conv, pick
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = host_cores()
+    w = synth.WORKLOADS[args.workload]
+    per_step = max(1, math.ceil(cores / 3))
+    for _ in range(args.warmup):
+        cpu_oracle_run(args.workload, per_step, cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt, conv, pick = cpu_oracle_run(args.workload, per_step, cores)
+        times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    sample = (f"{per_step} omega-points x 3 directions per step (evenly spread over the "
+              f"{w['n_omega']}-point grid), oracle GMRES(m={w['restart']}) to tol {w['tol']}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "omega-points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args.workload, "oracle on host cores"),
+        "cpu_baseline": {"value": value, "unit": "omega-points/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "omega-points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def config_of(workload: str, extra: str):
+    w = synth.WORKLOADS[workload]
+    return {"workload": f"{workload}: {w['n_atoms']} atoms, 13 orbitals/atom, "
+                        f"{w['n_omega']} omegas in [0,{w['w_hi']}] Ha x 3 directions, "
+                        f"eps {w['eps']} Ha, GMRES({w['restart']}) tol {w['tol']}",
+            "precision": "fp64", "l2": "operator inputs (K alone) larger than L2",
+            "note": extra}
+
+
+# ---------------------------------------------------------------------------
+# the GPU path
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_1005_5340_gb300 import tddft
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+
+    s, w = synth.workload(args.workload)
+    omega = w["omega"]
+    groups = omega_schedule(omega.size, rank, world, args.omega_per_step)
+    per_step = len(groups[0])
+    ctx = tddft.Context(s, batch=3 * per_step, restart=w["restart"], tol=w["tol"],
+                        max_restarts=200, stream=stream.cuda_stream)
+    dev_groups = [torch.tensor(omega[g], dtype=torch.float64, device=dev) for g in groups]
+
+    def step(i):
+        g = dev_groups[i % len(dev_groups)]
+        P, info = ctx.polarizability(g, w["eps"])
+        return int(np.sum(info["matvecs"])), int(g.numel())
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i)
+    torch.cuda.synchronize()
+
+    # timed region: device-resident inputs, device events on the library stream
+    clk = ClockSampler(local)
+    ctx.timing_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    points = 0
+    matvecs = 0
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for i in range(args.steps):
+            mv, n = step(args.warmup + i)
+            points += n
+            matvecs += mv
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    timing = ctx.timing()
+    ctx.timing_enable(False)
+    t = torch.tensor([ms, float(points)], dtype=torch.float64, device=dev)
+    if dist:
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tp = t[1:].clone()
+        dist.all_reduce(tp, op=dist.ReduceOp.SUM)
+        ms_max, total_points = float(tm.item()), float(tp.item())
+    else:
+        ms_max, total_points = ms, float(points)
+    value = total_points / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e_steps = max(1, args.e2e_steps)
+    host_groups = [omega[g] for g in groups]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_points = 0
+    for i in range(e2e_steps):
+        g = host_groups[i % len(host_groups)]
+        P, info = ctx.polarizability(g, w["eps"])
+        e2e_points += g.size
+    dt = time.perf_counter() - t0
+    e2e = {"value": world * e2e_points / dt, "unit": "omega-points/s",
+           "h2d_bytes_per_step": int(8 * per_step),
+           "d2h_bytes_per_step": int(16 * 9 * per_step + 24 * 3 * per_step)}
+
+    if rank != 0:
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel class
+    dom = max(timing.items(), key=lambda kv: kv[1]["ms"])
+    name, d = dom
+    launches = max(1, d["launches"])
+    chi_cls = ["vertex_contract", "beta", "gemm_T1", "dscale", "gemm_T2", "sddmm_dot"]
+    chi_ms = sum(timing[c]["ms"] for c in chi_cls)
+    n_virt = s.n_orb - s.n_occ
+    chi_applies = timing["gemm_T1"]["flops"] / (4.0 * n_virt * s.n_orb * s.n_occ)
+    chi0_tflops = chi_applies * chi0_flops_per_rhs(s) / (chi_ms / 1e3) / 1e12 if chi_ms else None
+    achieved = (d["flops"] / launches) / (d["ms"] / launches / 1e3) / 1e12 if d["flops"] else None
+    roofline = {"kernel": name, "bound": "alu", "achieved": achieved,
+                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / FP64_NOMINAL_TFLOPS) if achieved else None,
+                "traffic": None,
+                "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in the measured peaks)",
+                "share_of_step": d["ms"] / ms}
+    gpu_launches = int(sum(v["launches"] for v in timing.values()))
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        npts = args.cpu_sample or max(1, math.ceil(cores / 3))
+        v, dt_cpu, conv, pick = cpu_oracle_run(args.workload, npts, cores)
+        cpu = {"value": v, "unit": "omega-points/s", "cores": cores, "kind": "oracle",
+               "sample": f"{npts} omega-points x 3 directions spread over the grid "
+                         f"({dt_cpu:.1f} s wall, converged={conv})"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "omega-points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": dict(config_of(args.workload, "plain float64 GMRES, device resident"),
+                       omega_per_step=per_step, parallelism=f"frequency shards x{world}"),
+        "chi0_tflops": chi0_tflops,
+        "matvecs_per_rhs": matvecs / max(1, 3 * points),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": gpu_launches,
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},
+    }
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

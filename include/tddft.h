@@ -1,0 +1,191 @@
+/*
+ * tddft.h -- C boundary of the GB300 library for the iterative
+ * polarizability solve of Koval, Foerster and Coulaud (arXiv:1005.5340).
+ *
+ * At every frequency omega the library solves eq. sle,
+ *     (1 - chi0(omega) K) X_k = chi0(omega) d_k ,
+ * by restarted GMRES (Sec. 4.1) and returns P_ik(omega) = d_i . X_k
+ * (eq. eqpolarizability).  chi0(omega) is never formed: chi0 . z is applied
+ * in the five steps of Sec. 4.2 (Fig. f:flops, Table t:flops) with the
+ * vertex contraction re-associated (W(z) = sum_nu z^nu V_nu, then W X_occ),
+ * and K . z is a dense product (Sec. 4.1).  Everything runs on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Complex vectors cross the boundary interleaved (re, im) in float64;
+ *    a block of n_rhs vectors of length n_prod is n_rhs x n_prod complex,
+ *    vector-major (vector r occupies entries [r*n_prod, (r+1)*n_prod)).
+ *  - flags bit 0 (TDDFT_DEVICE_PTRS): the z/out/omega pointers of that call
+ *    are device pointers; otherwise they are host pointers and the call copies
+ *    through a device staging buffer on the context's stream and returns after
+ *    the result is on the host.  Device-pointer calls are asynchronous on the
+ *    context's stream.
+ *  - Every call returns a status and never aborts or traps.  On failure,
+ *    tddft_last_error() describes the cause.  A context is not thread-safe.
+ *  - Inputs are deep-copied by tddft_create; the caller keeps ownership of
+ *    its buffers and may free them on return.  Outputs are caller-allocated.
+ */
+#ifndef TDDFT_H_
+#define TDDFT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tddft_ctx tddft_ctx;
+
+typedef enum {
+  TDDFT_OK = 0,
+  TDDFT_ERR_INVALID_ARG = 1,   /* null pointer, eps <= 0, NaN/Inf input, bad option */
+  TDDFT_ERR_SHAPE = 2,         /* inconsistent sizes or offsets */
+  TDDFT_ERR_NOMEM = 3,         /* device or pinned host allocation failed */
+  TDDFT_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
+  TDDFT_ERR_NOT_CONVERGED = 5, /* some (omega, direction) did not reach tol */
+  TDDFT_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+  TDDFT_ERR_UNSUPPORTED = 7    /* input outside what the GPU path implements */
+} tddft_status;
+
+#define TDDFT_DEVICE_PTRS 1
+
+typedef enum {
+  TDDFT_PREC_FP64 = 0       /* every step in float64 */
+} tddft_precision;
+
+/*
+ * One molecule (inputs of Sec. 2-3: eqs. lcao, vertex-ansatz,
+ * matrix_self_energy; dipoles of eq. eqpolarizability).  Host pointers.
+ *
+ *  atom_orb_offset [n_atoms+1]: orbitals of atom A are
+ *      [atom_orb_offset[A], atom_orb_offset[A+1]), at most 16 per atom.
+ *  eigenvalues [n_orb]: Kohn-Sham energies (Hartree), non-decreasing.
+ *  occupations [n_orb]: a step profile: the first n_occ entries equal and
+ *      > 0, the rest 0 (closed-shell filling).  Other profiles are
+ *      TDDFT_ERR_UNSUPPORTED.
+ *  X [n_orb*n_orb]: LCAO coefficients, column-major: X[a + E*n_orb] = X_a^E
+ *      (column E = state E).
+ *  prod_atoms [2*n_prod]: (A, B) per product, A <= B; A == B is a local
+ *      product, A < B a bilocal one.
+ *  vertex_offset [n_prod+1], vertex[vertex_offset[n_prod]]: product mu owns
+ *      the n_A x n_B row-major block V_mu^{ab} (a in A, b in B) at
+ *      vertex[vertex_offset[mu]].  Local blocks must be symmetric; for a
+ *      bilocal product the B x A entries are the transpose (implied).
+ *  K [n_prod*n_prod]: f_Hxc^{mu nu}, row-major, symmetric
+ *      (|K - K^T| <= 1e-12 |K| elementwise in max norm).
+ *  dipole [3*n_prod]: d_i^mu, direction-major.
+ */
+typedef struct {
+  int32_t n_atoms;
+  const int32_t *atom_orb_offset;
+  int32_t n_orb;
+  const double *eigenvalues;
+  const double *occupations;
+  const double *X;
+  int32_t n_prod;
+  const int32_t *prod_atoms;
+  const int64_t *vertex_offset;
+  const double *vertex;
+  const double *K;
+  const double *dipole;
+} tddft_system;
+
+/*
+ * Solver and resource options.
+ *  prec: TDDFT_PREC_FP64.
+ *  restart: GMRES restart length m (1..256).
+ *  max_restarts: cycles before an (omega, direction) is declared not
+ *      converged (>= 1).
+ *  tol: stop when ||b - A x||_2 / ||b||_2 <= tol, the residual recomputed in
+ *      float64 at the end of each cycle (> 0).
+ *  batch: maximum number of right-hand sides solved together (>= 1); sizes
+ *      every device workspace allocated by tddft_create.
+ *  stream: cudaStream_t for all work (NULL = legacy default stream).
+ */
+typedef struct {
+  int32_t prec;
+  int32_t restart;
+  int32_t max_restarts;
+  double tol;
+  int32_t batch;
+  void *stream;
+} tddft_options;
+
+/* Per-(omega, direction) solver report. */
+typedef struct {
+  int32_t matvecs;   /* applications of A, residual checks included */
+  int32_t cycles;    /* GMRES cycles started */
+  double resid;      /* final ||b - A x|| / ||b|| (float64) */
+  int32_t converged; /* 1 if resid <= tol */
+  int32_t pad;
+} tddft_solve_stats;
+
+/*
+ * Validate and upload one molecule; allocate every device workspace for up
+ * to opts->batch right-hand sides.  *out receives the context.
+ * Errors: INVALID_ARG (null, NaN/Inf, bad option), SHAPE, UNSUPPORTED
+ * (occupations not a step profile, > 16 orbitals on an atom, K not
+ * symmetric), NOMEM, CUDA.
+ */
+tddft_status tddft_create(const tddft_system *sys, const tddft_options *opts, tddft_ctx **out);
+
+/*
+ * out_r = chi0(omega_r) . z_r for r < n_rhs (eq. response-mat applied by the
+ * steps of Table t:flops; Sec. 4.2).  omega [n_rhs] real frequencies
+ * (Hartree), eps > 0 the broadening of eq. response-eig.  z, out:
+ * n_rhs x n_prod complex interleaved.  1 <= n_rhs <= batch.
+ */
+tddft_status tddft_chi0_apply(tddft_ctx *ctx, int32_t n_rhs, const double *omega, double eps,
+                              const double *z, double *out, int32_t flags);
+
+/* out_r = K . z_r (the precomputed kernel of Sec. 4.1); same layout rules. */
+tddft_status tddft_kernel_apply(tddft_ctx *ctx, int32_t n_rhs, const double *z, double *out,
+                                int32_t flags);
+
+/* out_r = A(omega_r) z_r = z_r - chi0(omega_r) (K z_r)  (Sec. 4.1). */
+tddft_status tddft_apply_A(tddft_ctx *ctx, int32_t n_rhs, const double *omega, double eps,
+                           const double *z, double *out, int32_t flags);
+
+/*
+ * The polarizability spectrum (eq. eqpolarizability via eq. sle).
+ * For each omega[w] (w < n_omega) and field direction k < 3, GMRES solves
+ * A(omega) X_k = chi0(omega) d_k from a zero initial guess; then
+ * P[w][i][k] = d_i . X_k.  P: n_omega x 3 x 3 complex interleaved
+ * (row i, column k).  stats (may be NULL): n_omega x 3 entries, index w*3+k.
+ * Right-hand sides are solved in groups of at most opts->batch.  Returns
+ * NOT_CONVERGED (with P filled from the last iterate) if any entry missed tol.
+ */
+tddft_status tddft_polarizability(tddft_ctx *ctx, int32_t n_omega, const double *omega,
+                                  double eps, double *P, tddft_solve_stats *stats,
+                                  int32_t flags);
+
+/* Sizes of a context (any pointer may be NULL). */
+tddft_status tddft_sizes(const tddft_ctx *ctx, int32_t *n_orb, int32_t *n_occ, int32_t *n_prod,
+                         int32_t *n_blocks);
+
+/*
+ * Per-kernel timing.  While enabled, every kernel launch of the context is
+ * bracketed by CUDA events on the context's stream; the totals are per kernel
+ * class (the K product, vertex contraction, beta, the two transform GEMMs, the
+ * D(omega) scaling, the block dot, the GMRES kernels).  Enabling resets the
+ * totals.  tddft_timing_get synchronises the stream and returns, for class
+ * i < tddft_timing_count(), its name (static string), the number of timed
+ * launches, their summed device time in ms and the algorithmic float64
+ * flops those launches performed (2 M N K for a GEMM; 0 where not counted).
+ */
+tddft_status tddft_timing_enable(tddft_ctx *ctx, int32_t on);
+int32_t tddft_timing_count(const tddft_ctx *ctx);
+tddft_status tddft_timing_get(tddft_ctx *ctx, int32_t i, const char **name, int32_t *launches,
+                              double *total_ms, double *flops);
+
+/* Text of the last error on this context (never NULL; "" if none).  With
+ * ctx == NULL: the last error of a failed tddft_create on this thread. */
+const char *tddft_last_error(const tddft_ctx *ctx);
+
+/* Release the context and every device buffer it owns.  NULL is a no-op. */
+void tddft_destroy(tddft_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDDFT_H_ */

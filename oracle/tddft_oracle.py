@@ -353,7 +353,8 @@ def polarizability_gmres(sysm, omegas, eps: float, restart: int, tol: float,
 _W = {}
 
 
-def _worker_init(sysm, eps, restart, tol, max_restarts):
+def _worker_init(source, eps, restart, tol, max_restarts):
+    sysm = source[0](*source[1]) if isinstance(source, tuple) else source
     _W.update(sysm=sysm, eps=eps, restart=restart, tol=tol, max_restarts=max_restarts,
               op=StepOperator(sysm))
 
@@ -365,11 +366,12 @@ def _worker_task(task):
     return P[0, :, 0], infos[0]
 
 
-def polarizability_gmres_parallel(sysm, omegas, eps, restart, tol, workers: int,
+def polarizability_gmres_parallel(source, omegas, eps, restart, tol, workers: int,
                                   max_restarts: int = 200, dirs=(0, 1, 2)):
     """One (omega, direction) task per process with a dynamic schedule, the
     paper's scheme for this phase.  Workers are spawned with one BLAS thread
-    each.  Returns (P [n_omega, 3, len(dirs)], infos)."""
+    each.  ``source`` is a System or a picklable (factory, args) pair that each
+    worker calls to rebuild it.  Returns (P [n_omega, 3, len(dirs)], infos)."""
     import multiprocessing as mp
     omegas = np.atleast_1d(np.asarray(omegas, dtype=float))
     tasks = [(float(w), int(k)) for w in omegas for k in dirs]
@@ -380,7 +382,7 @@ def polarizability_gmres_parallel(sysm, omegas, eps, restart, tol, workers: int,
     try:
         ctx = mp.get_context("spawn")
         with ctx.Pool(workers, initializer=_worker_init,
-                      initargs=(sysm, eps, restart, tol, max_restarts)) as pool:
+                      initargs=(source, eps, restart, tol, max_restarts)) as pool:
             out = pool.map(_worker_task, tasks, chunksize=1)
     finally:
         for v, val in env.items():

@@ -1,0 +1,425 @@
+// Device-resident restarted GMRES for a group of right-hand sides, one per
+// (omega, field direction): eq. sle solved by the Krylov method of Sec. 4.1
+// (basis of eq. orthogonal-krylov-basis, minimal residual in the subspace),
+// float64 throughout.  Each right-hand side runs its own state machine:
+//   Arnoldi step j : w = A v_j, two passes of classical Gram-Schmidt
+//                    (CGS2) against v_0..v_j, Givens QR of the Hessenberg
+//                    column, residual estimate |g_{j+1}|;
+//   end of a cycle : x += V y, then the next operator application computes
+//                    A x so that the true residual b - A x decides between
+//                    done, not converged (cycle limit) and a restart.
+// Right-hand sides that are done drop out of the active list, so the batched
+// operator only works on live ones.
+#include "internal.h"
+
+namespace tddft {
+namespace {
+
+constexpr int NT = 256;
+constexpr int kStateArnoldi = 0, kStateResid = 1, kStateDone = 2;
+
+__device__ inline double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ inline double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ inline double cabs2(double2 a) { return hypot(a.x, a.y); }
+__device__ inline double2 cdiv(double2 a, double2 b) {
+  // a / b with scaling by the larger component of b
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, d = b.x + r * b.y;
+    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  } else {
+    double r = b.x / b.y, d = b.y + r * b.x;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+  }
+}
+
+// Sum of NV values over the CTA; every thread receives the totals.
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *red /* [NV][NT/32] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double t = v[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    v[q] = t;
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[q * (NT / 32) + warp] = v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) t += red[q * (NT / 32) + w];
+    v[q] = t;
+  }
+}
+
+struct Gs {
+  int m, max_restarts, n_prod;
+  double tol;
+  int *state, *jcur, *cycles, *matvecs, *conv;
+  double *bnorm, *resid, *omega;
+  double2 *H, *sn, *g;
+  double *cs, *V, *x, *b;
+  const int *act;
+};
+
+Gs view(const GmresState &s, int n_prod) {
+  Gs v;
+  v.m = s.m; v.max_restarts = s.max_restarts; v.n_prod = n_prod; v.tol = s.tol;
+  v.state = s.state; v.jcur = s.jcur; v.cycles = s.cycles; v.matvecs = s.matvecs; v.conv = s.conv;
+  v.bnorm = s.bnorm; v.resid = s.resid; v.omega = s.omega;
+  v.H = s.H; v.sn = s.sn; v.g = s.g; v.cs = s.cs; v.V = s.V; v.x = s.x; v.b = s.b; v.act = s.act;
+  return v;
+}
+
+// Start: store b, x = 0, v_0 = b / ||b||.
+__global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__restrict__ Bp) {
+  __shared__ double red[NT / 32];
+  const int r = blockIdx.x;
+  const int N = G.n_prod;
+  const double *bin = Bp + (int64_t)2 * r * N;
+  double *b = G.b + (int64_t)2 * r * N;
+  double *x = G.x + (int64_t)2 * r * N;
+  double *v0 = G.V + (int64_t)r * (G.m + 1) * 2 * N;
+  double s[1] = {0.0};
+  for (int e = threadIdx.x; e < 2 * N; e += NT) {
+    double t = bin[e];
+    b[e] = t;
+    x[e] = 0.0;
+    s[0] += t * t;
+  }
+  block_sum<1>(s, red);
+  const double nrm = sqrt(s[0]);
+  if (nrm > 0.0) {
+    const double inv = 1.0 / nrm;
+    for (int e = threadIdx.x; e < 2 * N; e += NT) v0[e] = bin[e] * inv;
+  }
+  if (threadIdx.x == 0) {
+    G.bnorm[r] = nrm;
+    G.matvecs[r] = 0;
+    G.jcur[r] = 0;
+    if (nrm > 0.0) {
+      G.state[r] = kStateArnoldi;
+      G.cycles[r] = 1;
+      G.conv[r] = 0;
+      G.resid[r] = 1.0;
+      G.g[(int64_t)r * (G.m + 1)] = make_double2(nrm, 0.0);
+    } else {
+      G.state[r] = kStateDone;
+      G.cycles[r] = 0;
+      G.conv[r] = 1;
+      G.resid[r] = 0.0;
+    }
+  }
+}
+
+// Ordered list of right-hand sides that are not done (one CTA).
+__global__ void __launch_bounds__(1024) gmres_select_kernel(const int *__restrict__ state, int n,
+                                                            int *__restrict__ act,
+                                                            int *__restrict__ count) {
+  __shared__ int sums[1024];
+  const int t = threadIdx.x;
+  const int chunk = (n + 1023) / 1024;
+  const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
+  int c = 0;
+  for (int i = lo; i < hi; ++i) c += state[i] != kStateDone;
+  sums[t] = c;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {   // inclusive Hillis-Steele scan
+    int v = (t >= off) ? sums[t - off] : 0;
+    __syncthreads();
+    sums[t] += v;
+    __syncthreads();
+  }
+  int pos = sums[t] - c;
+  for (int i = lo; i < hi; ++i)
+    if (state[i] != kStateDone) act[pos++] = i;
+  if (t == 1023) *count = sums[1023];
+}
+
+// Operator input of each active right-hand side: v_j (Arnoldi) or x (residual).
+__global__ void __launch_bounds__(NT) gmres_gather_kernel(Gs G, double *__restrict__ Zc,
+                                                          double *__restrict__ slot_omega) {
+  const int s = blockIdx.x;
+  const int r = G.act[s];
+  const int N = G.n_prod;
+  const double *src = (G.state[r] == kStateArnoldi)
+                          ? G.V + ((int64_t)r * (G.m + 1) + G.jcur[r]) * 2 * N
+                          : G.x + (int64_t)2 * r * N;
+  double *dst = Zc + (int64_t)2 * s * N;
+  for (int e = threadIdx.x; e < 2 * N; e += NT) dst[e] = src[e];
+  if (threadIdx.x == 0) slot_omega[s] = G.omega[r];
+}
+
+__global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const double *__restrict__ Wout) {
+  __shared__ double red[16 * (NT / 32)];
+  __shared__ double2 hs[257], hp[257], ys[257];
+  __shared__ int finish_flag;
+  const int s = blockIdx.x;
+  const int r = G.act[s];
+  const int N = G.n_prod;
+  const int m = G.m;
+  const int tid = threadIdx.x;
+  const double *win = Wout + (int64_t)2 * s * N;
+  double *Vr = G.V + (int64_t)r * (m + 1) * 2 * N;
+  const int state = G.state[r];
+
+  if (state == kStateResid) {
+    // r = b - A x ; decide done / not converged / restart
+    const double *b = G.b + (int64_t)2 * r * N;
+    double s2[1] = {0.0};
+    for (int e = tid; e < 2 * N; e += NT) {
+      double t = b[e] - win[e];
+      Vr[e] = t;
+      s2[0] += t * t;
+    }
+    block_sum<1>(s2, red);
+    const double rho = sqrt(s2[0]);
+    const double rel = rho / G.bnorm[r];
+    int next;
+    if (rel <= G.tol) next = 0;
+    else if (G.cycles[r] >= G.max_restarts) next = 1;
+    else next = 2;
+    if (next == 2) {
+      const double inv = 1.0 / rho;
+      for (int e = tid; e < 2 * N; e += NT) Vr[e] *= inv;
+    }
+    if (tid == 0) {
+      G.matvecs[r] += 1;
+      G.resid[r] = rel;
+      if (next == 0) { G.state[r] = kStateDone; G.conv[r] = 1; }
+      else if (next == 1) { G.state[r] = kStateDone; G.conv[r] = 0; }
+      else {
+        G.state[r] = kStateArnoldi;
+        G.jcur[r] = 0;
+        G.cycles[r] += 1;
+        G.g[(int64_t)r * (m + 1)] = make_double2(rho, 0.0);
+      }
+    }
+    return;
+  }
+  if (state != kStateArnoldi) return;
+
+  const int j = G.jcur[r];
+  double *w = Vr + (int64_t)(j + 1) * 2 * N;
+  for (int e = tid; e < 2 * N; e += NT) w[e] = win[e];
+  for (int i = tid; i <= j; i += NT) hs[i] = make_double2(0.0, 0.0);
+  __syncthreads();
+
+  for (int pass = 0; pass < 2; ++pass) {
+    // h_i = <v_i, w> for i <= j, eight at a time
+    for (int i0 = 0; i0 <= j; i0 += 8) {
+      double part[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) part[q] = 0.0;
+      for (int e = tid; e < N; e += NT) {
+        const double wr = w[e], wi = w[N + e];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (i0 + q <= j) {
+            const double *vi_ = Vr + (int64_t)(i0 + q) * 2 * N;
+            const double vr = vi_[e], vi = vi_[N + e];
+            part[2 * q] = fma(vr, wr, fma(vi, wi, part[2 * q]));
+            part[2 * q + 1] = fma(vr, wi, fma(-vi, wr, part[2 * q + 1]));
+          }
+        }
+      }
+      block_sum<16>(part, red);
+      if (tid < 8 && i0 + tid <= j) hp[i0 + tid] = make_double2(part[2 * tid], part[2 * tid + 1]);
+    }
+    __syncthreads();
+    // w -= sum_i h_i v_i
+    for (int e = tid; e < N; e += NT) {
+      double ar = 0.0, ai = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        const double *vi_ = Vr + (int64_t)i * 2 * N;
+        const double2 h = hp[i];
+        const double vr = vi_[e], vi = vi_[N + e];
+        ar += h.x * vr - h.y * vi;
+        ai += h.x * vi + h.y * vr;
+      }
+      w[e] -= ar;
+      w[N + e] -= ai;
+    }
+    for (int i = tid; i <= j; i += NT) hs[i] = make_double2(hs[i].x + hp[i].x, hs[i].y + hp[i].y);
+    __syncthreads();
+  }
+  double n2[1] = {0.0};
+  for (int e = tid; e < 2 * N; e += NT) n2[0] += w[e] * w[e];
+  block_sum<1>(n2, red);
+  const double hn = sqrt(n2[0]);
+
+  if (tid == 0) {
+    double2 *Hc = G.H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);
+    double *cs = G.cs + (int64_t)r * m;
+    double2 *sn = G.sn + (int64_t)r * m;
+    double2 *g = G.g + (int64_t)r * (m + 1);
+    // apply the earlier rotations to the new column
+    for (int i = 0; i < j; ++i) {
+      const double2 a = hs[i], bb = hs[i + 1];
+      const double2 t = make_double2(cs[i] * a.x + (sn[i].x * bb.x - sn[i].y * bb.y),
+                                     cs[i] * a.y + (sn[i].x * bb.y + sn[i].y * bb.x));
+      const double2 cb = cmul(cconj(sn[i]), a);
+      hs[i + 1] = make_double2(-cb.x + cs[i] * bb.x, -cb.y + cs[i] * bb.y);
+      hs[i] = t;
+    }
+    // new rotation mapping (hs[j], hn) to (rho, 0)
+    const double2 a = hs[j];
+    const double aa = cabs2(a);
+    double c;
+    double2 sv;
+    if (hn == 0.0) { c = 1.0; sv = make_double2(0.0, 0.0); }
+    else if (aa == 0.0) { c = 0.0; sv = make_double2(1.0, 0.0); }
+    else {
+      const double rr = hypot(aa, hn);
+      c = aa / rr;
+      sv = make_double2(a.x / aa * hn / rr, a.y / aa * hn / rr);
+    }
+    hs[j] = make_double2(c * a.x + sv.x * hn, c * a.y + sv.y * hn);
+    cs[j] = c;
+    sn[j] = sv;
+    const double2 gj = g[j];
+    const double2 t = cmul(cconj(sv), gj);
+    g[j + 1] = make_double2(-t.x, -t.y);
+    g[j] = make_double2(c * gj.x, c * gj.y);
+    for (int i = 0; i <= j; ++i) Hc[i] = hs[i];
+    const double est = cabs2(g[j + 1]);
+    const bool fin = (est <= G.tol * G.bnorm[r]) || (j + 1 == m) || !(hn > 0.0);
+    finish_flag = fin ? 1 : 0;
+    G.matvecs[r] += 1;
+    if (fin) {
+      // back substitution with the rotated (upper triangular) Hessenberg matrix
+      const int k = j + 1;
+      const double2 *Hr = G.H + (int64_t)r * (m + 1) * m;
+      for (int i = k - 1; i >= 0; --i) {
+        double2 acc = g[i];
+        for (int l = i + 1; l < k; ++l) {
+          const double2 p = cmul(Hr[(int64_t)l * (m + 1) + i], ys[l]);
+          acc.x -= p.x;
+          acc.y -= p.y;
+        }
+        ys[i] = cdiv(acc, Hr[(int64_t)i * (m + 1) + i]);
+      }
+      G.state[r] = kStateResid;
+    } else {
+      G.jcur[r] = j + 1;
+    }
+  }
+  __syncthreads();
+  if (!finish_flag) {
+    const double inv = 1.0 / hn;
+    for (int e = tid; e < 2 * N; e += NT) w[e] *= inv;
+  } else {
+    const int k = j + 1;
+    double *x = G.x + (int64_t)2 * r * N;
+    for (int e = tid; e < N; e += NT) {
+      double ar = 0.0, ai = 0.0;
+      for (int i = 0; i < k; ++i) {
+        const double *vi_ = Vr + (int64_t)i * 2 * N;
+        const double2 y = ys[i];
+        const double vr = vi_[e], vi = vi_[N + e];
+        ar += y.x * vr - y.y * vi;
+        ai += y.x * vi + y.y * vr;
+      }
+      x[e] += ar;
+      x[N + e] += ai;
+    }
+  }
+}
+
+// Right-hand sides g0 .. g0+n-1 of a spectrum: index g -> (omega g/3, direction g%3).
+__global__ void rhs_init_kernel(int n, int g0, int n_prod, const double *__restrict__ omega_all,
+                                const double *__restrict__ dip, double *__restrict__ Zc,
+                                double *__restrict__ slot_omega, double *__restrict__ gs_omega) {
+  const int r = blockIdx.x;
+  const int g = g0 + r;
+  const int k = g % 3;
+  const double *d = dip + (int64_t)k * n_prod;
+  double *z = Zc + (int64_t)2 * r * n_prod;
+  for (int e = threadIdx.x; e < n_prod; e += blockDim.x) {
+    z[e] = d[e];
+    z[n_prod + e] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    slot_omega[r] = omega_all[g / 3];
+    gs_omega[r] = omega_all[g / 3];
+  }
+}
+
+// P[w][i][k] = d_i . x_{(w,k)} for the right-hand sides g0 .. g0+n-1.
+__global__ void __launch_bounds__(NT) polarization_kernel(int g0, int n_prod,
+                                                          const double *__restrict__ dip,
+                                                          const double *__restrict__ X,
+                                                          double2 *__restrict__ P) {
+  __shared__ double red[6 * (NT / 32)];
+  const int r = blockIdx.x;
+  const int g = g0 + r;
+  const double *x = X + (int64_t)2 * r * n_prod;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int e = threadIdx.x; e < n_prod; e += NT) {
+    const double xr = x[e], xi = x[n_prod + e];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double d = dip[(int64_t)i * n_prod + e];
+      acc[2 * i] = fma(d, xr, acc[2 * i]);
+      acc[2 * i + 1] = fma(d, xi, acc[2 * i + 1]);
+    }
+  }
+  block_sum<6>(acc, red);
+  if (threadIdx.x == 0) {
+    const int w = g / 3, k = g % 3;
+    for (int i = 0; i < 3; ++i) P[((int64_t)w * 3 + i) * 3 + k] = make_double2(acc[2 * i], acc[2 * i + 1]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
+                               const double *Bplanar) {
+  if (n <= 0) return cudaSuccess;
+  gmres_start_kernel<<<n, NT, 0, st>>>(view(gs, sys.n_prod), Bplanar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n) {
+  gmres_select_kernel<<<1, 1024, 0, st>>>(gs.state, n, gs.act, gs.count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs, int S,
+                                double *Zc, double *slot_omega) {
+  if (S <= 0) return cudaSuccess;
+  gmres_gather_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), Zc, slot_omega);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs, int S,
+                              const double *Wout) {
+  if (S <= 0) return cudaSuccess;
+  gmres_step_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), Wout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0,
+                            const double *omega_all, double *Zc, double *slot_omega,
+                            double *gs_omega) {
+  if (n <= 0) return cudaSuccess;
+  rhs_init_kernel<<<n, 256, 0, st>>>(n, g0, sys.n_prod, omega_all, sys.dip, Zc, slot_omega, gs_omega);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_polarization(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
+                                int g0, double2 *P) {
+  if (n <= 0) return cudaSuccess;
+  polarization_kernel<<<n, NT, 0, st>>>(g0, sys.n_prod, sys.dip, gs.x, P);
+  return cudaGetLastError();
+}
+
+}  // namespace tddft

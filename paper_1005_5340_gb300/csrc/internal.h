@@ -1,0 +1,130 @@
+// Internal declarations shared by the CUDA translation units of libtddft.
+// Nothing here crosses the C boundary (include/tddft.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tddft.h"
+
+namespace tddft {
+
+// Orbitals of one atom are padded to this many rows/columns in every
+// per-block layout (vertex blocks, contracted blocks W).
+constexpr int kMaxOrb = 16;
+constexpr int kBlk = kMaxOrb * kMaxOrb;
+
+// Device copy of one molecule in the layouts the kernels read.
+struct DevSystem {
+  int n_atoms = 0, n_orb = 0, n_occ = 0, n_virt = 0, n_prod = 0, n_blocks = 0;
+  int n_adj = 0;
+  double occ_value = 0.0;      // n_o of every occupied state (n_u = 0)
+  int *aoff = nullptr;         // [n_atoms+1]
+  double *energy = nullptr;    // [n_orb]
+  double *Xo = nullptr;        // [n_orb][n_occ]   Xo[a][E]  = X_a^E, E occupied
+  double *XvT = nullptr;       // [n_virt][n_orb]  XvT[F][a] = X_a^{n_occ+F}
+  double *Xv = nullptr;        // [n_orb][n_virt]  Xv[a][F]  = X_a^{n_occ+F}
+  double *K = nullptr;         // [n_prod][n_prod] symmetric
+  double *dip = nullptr;       // [3][n_prod]
+  int2 *blk_atoms = nullptr;   // [n_blocks] (A, B), A <= B
+  int *blk_ptr = nullptr;      // [n_blocks+1] into blk_prod
+  int *blk_prod = nullptr;     // [n_prod] product index, grouped by block
+  double *Vpad = nullptr;      // [n_prod][kBlk] vertex blocks in blk_prod order, zero padded
+  int *adj_ptr = nullptr;      // [n_atoms+1]
+  int4 *adj = nullptr;         // [n_adj] (block, other atom, transposed, 0)
+};
+
+// Optional per-kernel timing: CUDA events recorded on the launching stream
+// around every launch of a kernel class; resolved when the host next waits.
+enum KernelClass {
+  kcGemmK = 0, kcVertex, kcBeta, kcGemmT1, kcDscale, kcGemmT2, kcSddmm, kcGmresStep,
+  kcGmresGather, kcGmresSelect, kcMisc, kcCount
+};
+const char *kernel_class_name(int k);
+
+struct Timer {
+  bool on = false;
+  struct Rec { int cls; cudaEvent_t a, b; double flops; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  int launches[kcCount] = {};
+  double ms[kcCount] = {};
+  double flops[kcCount] = {};
+  cudaEvent_t get();
+  void begin(cudaStream_t st, int cls, cudaEvent_t *a);
+  void end(cudaStream_t st, int cls, cudaEvent_t a, double fl);
+  void resolve();   // host-side; call after the stream has been synchronised
+  void reset();
+  void destroy();
+};
+
+// Workspace of the chi0 / A operator for up to `slots` right-hand sides.
+// Real columns: c = 2*s + p, p = 0 real plane, 1 imaginary plane.
+struct OpWork {
+  int slots = 0;
+  double *Y = nullptr;        // [2S][n_prod]   K z
+  double *W = nullptr;        // [2S][n_blocks][kBlk]  sum_nu y^nu V_nu per block
+  double *beta = nullptr;     // [n_orb][2S][n_occ]
+  double *abuf = nullptr;     // [n_virt][2S][n_occ]
+  double *gamma = nullptr;    // [n_orb][2S][n_occ]
+  double *omega = nullptr;    // [S] frequency of each slot
+  Timer *timer = nullptr;
+};
+
+enum OpMode { kChi0 = 0, kKernel = 1, kA = 2 };
+
+// Launchers (stream-ordered, no synchronisation).  Return cudaGetLastError().
+cudaError_t launch_gemm_f64(cudaStream_t st, int M, int N, int K, const double *A, int64_t lda,
+                            const double *B, int64_t ldb, double *C, int64_t ldc);
+cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S,
+                                  OpMode mode, double eps, const double *Zin, double *Out);
+cudaError_t launch_interleaved_to_planar(cudaStream_t st, int n_rhs, int n, const double *in,
+                                         double *out);
+cudaError_t launch_planar_to_interleaved(cudaStream_t st, int n_rhs, int n, const double *in,
+                                         double *out);
+
+// GMRES state of a group of right-hand sides (one per (omega, direction)).
+struct GmresState {
+  int cap = 0;          // right-hand sides allocated
+  int m = 0;            // restart length
+  int max_restarts = 0;
+  double tol = 0.0;
+  int *state = nullptr;     // [cap] 0 Arnoldi, 1 awaiting A x, 2 done
+  int *jcur = nullptr;      // [cap]
+  int *cycles = nullptr;    // [cap]
+  int *matvecs = nullptr;   // [cap]
+  int *conv = nullptr;      // [cap]
+  double *bnorm = nullptr;  // [cap]
+  double *resid = nullptr;  // [cap]
+  double *omega = nullptr;  // [cap]
+  double2 *H = nullptr;     // [cap][(m+1)*m] column-major
+  double *cs = nullptr;     // [cap][m]
+  double2 *sn = nullptr;    // [cap][m]
+  double2 *g = nullptr;     // [cap][m+1]
+  double *V = nullptr;      // [cap][m+1][2][n_prod]
+  double *x = nullptr;      // [cap][2][n_prod]
+  double *b = nullptr;      // [cap][2][n_prod]
+  int *act = nullptr;       // [cap] active right-hand sides, in order
+  int *count = nullptr;     // [1]
+};
+
+cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
+                               const double *Bplanar /*[2n][n_prod]*/);
+cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n);
+cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs, int S,
+                                double *Zc, double *slot_omega);
+cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs, int S,
+                              const double *Wout);
+// Right-hand sides g0..g0+n-1 of a spectrum (g -> omega g/3, direction g%3):
+// Zc rows 2r, 2r+1 = (d_{g%3}, 0), slot and solver frequencies set.
+cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0,
+                            const double *omega_all, double *Zc, double *slot_omega,
+                            double *gs_omega);
+// P[w][i][k] (complex) = d_i . x_g for g = w*3 + k in g0..g0+n-1.
+cudaError_t launch_polarization(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
+                                int g0, double2 *P);
+
+}  // namespace tddft

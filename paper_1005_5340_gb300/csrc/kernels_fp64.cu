@@ -1,0 +1,448 @@
+// Float64 kernels of the matrix-free operator A(omega) z = z - chi0(omega) (K z)
+// (Sec. 4.1) with chi0 . y applied by the steps of Sec. 4.2 (Fig. f:flops,
+// Table t:flops), re-associated so that the vertex is read instead of the
+// stored alpha object:
+//   W_k(y)  = sum_{nu in block k} y^nu V_nu              (steps 1+2, per block)
+//   beta    = W(y) X_occ                                 (steps 1+2)
+//   a       = X_virt^T beta,  a^{FE} *= D_EF(omega)      (step 3 + denominator)
+//   gamma   = X_virt a                                   (step 4)
+//   n_mu    = sum_ab V_mu^{ab} (X_occ gamma^T)^{ab}      (step 5)
+// Complex vectors are kept as two real planes; X, V and K are real, so only
+// the D(omega) scaling mixes the planes.
+#include "internal.h"
+
+namespace tddft {
+
+// ---------------------------------------------------------------------------
+// C[M x N] = A[M x K] . B[K x N], all row-major float64 (DFMA).
+// 64 x 64 tile per CTA, 16-deep K slices staged in shared memory, 4 x 4
+// outputs per thread.  Every edge is bounds-checked (ragged M, N, K).
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_nn(int M, int N, int K, const double *__restrict__ A,
+                                                   int64_t lda, const double *__restrict__ B,
+                                                   int64_t ldb, double *__restrict__ C,
+                                                   int64_t ldc) {
+  __shared__ double As[2][GB_K][GB_M + 2];
+  __shared__ double Bs[2][GB_K][GB_N];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * GB_M;
+  const int64_t n0 = (int64_t)blockIdx.x * GB_N;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  double ra[4], rb[4];
+  auto load_regs = [&](int k0) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      int idx = tid + 256 * l;
+      int i = idx >> 4, kk = idx & 15;                       // A: 64 rows x 16 k
+      int64_t gm = m0 + i;
+      int gk = k0 + kk;
+      ra[l] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.0;
+      int kb = idx >> 6, j = idx & 63;                       // B: 16 k x 64 cols
+      int64_t gn = n0 + j;
+      int gkb = k0 + kb;
+      rb[l] = (gn < N && gkb < K) ? B[(int64_t)gkb * ldb + gn] : 0.0;
+    }
+  };
+  auto store_smem = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      int idx = tid + 256 * l;
+      As[buf][idx & 15][idx >> 4] = ra[l];
+      Bs[buf][idx >> 6][idx & 63] = rb[l];
+    }
+  };
+
+  const int nk = (K + GB_K - 1) / GB_K;
+  if (nk > 0) {
+    load_regs(0);
+    store_smem(0);
+  }
+  __syncthreads();
+  for (int t = 0; t < nk; ++t) {
+    const int buf = t & 1;
+    if (t + 1 < nk) load_regs((t + 1) * GB_K);
+#pragma unroll
+    for (int kk = 0; kk < GB_K; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (t + 1 < nk) store_smem(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t gn = n0 + tx + 16 * j;
+      if (gn < N) C[gm * ldc + gn] = acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// W[c][k][ab] = sum_{nu in block k} Y[c][nu] * V_nu[ab]  (per block k, column c)
+// One CTA per (block, group of 8 columns); thread t owns entry ab = t.
+// ---------------------------------------------------------------------------
+constexpr int VW_COLS = 8;
+
+__global__ void __launch_bounds__(256) vertex_contract(int nb, int ncols, int n_prod,
+                                                       const int *__restrict__ blk_ptr,
+                                                       const int *__restrict__ blk_prod,
+                                                       const double *__restrict__ Vpad,
+                                                       const double *__restrict__ Y,
+                                                       double *__restrict__ W) {
+  __shared__ double ys[32][VW_COLS];
+  const int k = blockIdx.x;
+  const int c0 = blockIdx.y * VW_COLS;
+  const int t = threadIdx.x;
+  const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
+  double acc[VW_COLS];
+#pragma unroll
+  for (int c = 0; c < VW_COLS; ++c) acc[c] = 0.0;
+  for (int q0 = p0; q0 < p1; q0 += 32) {
+    __syncthreads();
+    {
+      int pp = t / VW_COLS, c = t % VW_COLS;
+      int q = q0 + pp;
+      ys[pp][c] = (q < p1 && c0 + c < ncols) ? Y[(int64_t)(c0 + c) * n_prod + blk_prod[q]] : 0.0;
+    }
+    __syncthreads();
+    const int qn = min(32, p1 - q0);
+    for (int pp = 0; pp < qn; ++pp) {
+      double v = Vpad[(int64_t)(q0 + pp) * kBlk + t];
+#pragma unroll
+      for (int c = 0; c < VW_COLS; ++c) acc[c] = fma(ys[pp][c], v, acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < VW_COLS; ++c)
+    if (c0 + c < ncols) W[((int64_t)(c0 + c) * nb + k) * kBlk + t] = acc[c];
+}
+
+// ---------------------------------------------------------------------------
+// beta[aoff[A]+a][c][E] = sum over blocks touching atom A of
+//   (W_k or W_k^T)[a][b] * Xo[aoff[B]+b][E]
+// One CTA per (atom A, group of 4 columns); thread = occupied state E.
+// ---------------------------------------------------------------------------
+constexpr int BT_COLS = 4;
+constexpr int BT_THREADS = 128;
+
+__global__ void __launch_bounds__(BT_THREADS) beta_kernel(
+    int ncols, int nb, int n_occ, const int *__restrict__ aoff, const int *__restrict__ adj_ptr,
+    const int4 *__restrict__ adj, const double *__restrict__ W, const double *__restrict__ Xo,
+    double *__restrict__ beta) {
+  __shared__ double Ws[BT_COLS][kMaxOrb][kMaxOrb + 1];
+  const int A = blockIdx.x;
+  const int c0 = blockIdx.y * BT_COLS;
+  const int nA = aoff[A + 1] - aoff[A];
+  const int e0 = adj_ptr[A], e1 = adj_ptr[A + 1];
+  for (int E0 = 0; E0 < n_occ; E0 += BT_THREADS) {
+    const int E = E0 + threadIdx.x;
+    double acc[BT_COLS][kMaxOrb];
+#pragma unroll
+    for (int c = 0; c < BT_COLS; ++c)
+#pragma unroll
+      for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      const int4 ent = adj[e];
+      const int k = ent.x, B = ent.y, tr = ent.z;
+      const int bo = aoff[B], nB = aoff[B + 1] - bo;
+      __syncthreads();
+      for (int i = threadIdx.x; i < BT_COLS * kBlk; i += BT_THREADS) {
+        int c = i / kBlk, ab = i % kBlk, a = ab / kMaxOrb, b = ab % kMaxOrb;
+        double v = 0.0;
+        if (c0 + c < ncols)
+          v = tr ? W[((int64_t)(c0 + c) * nb + k) * kBlk + b * kMaxOrb + a]
+                 : W[((int64_t)(c0 + c) * nb + k) * kBlk + a * kMaxOrb + b];
+        Ws[c][a][b] = v;
+      }
+      __syncthreads();
+      if (E < n_occ) {
+        for (int b = 0; b < nB; ++b) {
+          const double xv = Xo[(int64_t)(bo + b) * n_occ + E];
+#pragma unroll
+          for (int c = 0; c < BT_COLS; ++c)
+#pragma unroll
+            for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = fma(Ws[c][a][b], xv, acc[c][a]);
+        }
+      }
+    }
+    if (E < n_occ) {
+#pragma unroll
+      for (int c = 0; c < BT_COLS; ++c) {
+        if (c0 + c >= ncols) continue;
+#pragma unroll
+        for (int a = 0; a < kMaxOrb; ++a)
+          if (a < nA) beta[((int64_t)(aoff[A] + a) * ncols + c0 + c) * n_occ + E] = acc[c][a];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a[F][(2s, 2s+1)][E] *= D_EF(omega_s),
+// D = n_E [1/(omega - Delta + i eps) - 1/(omega + Delta + i eps)],
+// Delta = e_F - e_E  (eq. response-mat, both orderings of the pair merged).
+// ---------------------------------------------------------------------------
+__global__ void dscale_kernel(int n_virt, int S, int n_occ, double occ_value,
+                              const double *__restrict__ energy, const double *__restrict__ omega,
+                              double eps, double *__restrict__ a) {
+  const int64_t total = (int64_t)n_virt * S * n_occ;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int E = (int)(idx % n_occ);
+    const int64_t rest = idx / n_occ;
+    const int s = (int)(rest % S);
+    const int F = (int)(rest / S);
+    const double delta = energy[n_occ + F] - energy[E];
+    const double w = omega[s];
+    // 1/(x + i eps) = (x - i eps) / (x^2 + eps^2)
+    const double xm = w - delta, xp = w + delta;
+    const double im2 = 1.0 / (xm * xm + eps * eps), ip2 = 1.0 / (xp * xp + eps * eps);
+    const double d_re = occ_value * (xm * im2 - xp * ip2);
+    const double d_im = occ_value * (-eps * im2 + eps * ip2);
+    const int64_t base = ((int64_t)F * 2 * S + 2 * s) * n_occ + E;
+    const double re = a[base], im = a[base + n_occ];
+    a[base] = d_re * re - d_im * im;
+    a[base + n_occ] = d_re * im + d_im * re;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Step 5: for block k = (A, B) and column c
+//   G[a][b] = sum_E Xo[A+a][E] gamma[B+b][c][E]  (+ gamma[A+a][c][E] Xo[B+b][E] if A != B)
+//   n[c][mu] = sum_ab V_mu[a][b] G[a][b]  for mu in block k
+//   Out[c][mu] = Zin[c][mu] - n  (A operator)  or  n  (chi0 only)
+// One CTA per (block, 4 columns); thread t owns (a, b) = (t/16, t%16).
+// ---------------------------------------------------------------------------
+constexpr int SD_COLS = 4;
+constexpr int SD_E = 16;
+
+__global__ void __launch_bounds__(256) sddmm_dot(int ncols, int n_occ, int n_prod,
+                                                 const int *__restrict__ aoff,
+                                                 const int2 *__restrict__ blk_atoms,
+                                                 const int *__restrict__ blk_ptr,
+                                                 const int *__restrict__ blk_prod,
+                                                 const double *__restrict__ Vpad,
+                                                 const double *__restrict__ Xo,
+                                                 const double *__restrict__ gamma,
+                                                 const double *__restrict__ Zin, int subtract,
+                                                 double *__restrict__ Out) {
+  __shared__ double XA[kMaxOrb][SD_E + 1], XB[kMaxOrb][SD_E + 1];
+  __shared__ double gA[SD_COLS][kMaxOrb][SD_E + 1], gB[SD_COLS][kMaxOrb][SD_E + 1];
+  __shared__ double Gs[SD_COLS][kBlk];
+  const int k = blockIdx.x;
+  const int c0 = blockIdx.y * SD_COLS;
+  const int t = threadIdx.x;
+  const int a = t >> 4, b = t & 15;
+  const int2 AB = blk_atoms[k];
+  const int aoA = aoff[AB.x], nA = aoff[AB.x + 1] - aoA;
+  const int aoB = aoff[AB.y], nB = aoff[AB.y + 1] - aoB;
+  const bool bilocal = AB.x != AB.y;
+  double G[SD_COLS];
+#pragma unroll
+  for (int c = 0; c < SD_COLS; ++c) G[c] = 0.0;
+  for (int E0 = 0; E0 < n_occ; E0 += SD_E) {
+    __syncthreads();
+    for (int i = t; i < kMaxOrb * SD_E; i += 256) {
+      int r = i / SD_E, e = i % SD_E;
+      int E = E0 + e;
+      XA[r][e] = (r < nA && E < n_occ) ? Xo[(int64_t)(aoA + r) * n_occ + E] : 0.0;
+      XB[r][e] = (r < nB && E < n_occ) ? Xo[(int64_t)(aoB + r) * n_occ + E] : 0.0;
+    }
+    for (int i = t; i < SD_COLS * kMaxOrb * SD_E; i += 256) {
+      int c = i / (kMaxOrb * SD_E), rem = i % (kMaxOrb * SD_E);
+      int r = rem / SD_E, e = rem % SD_E;
+      int E = E0 + e;
+      bool okc = (c0 + c < ncols) && E < n_occ;
+      gA[c][r][e] = (okc && r < nA) ? gamma[((int64_t)(aoA + r) * ncols + c0 + c) * n_occ + E] : 0.0;
+      gB[c][r][e] = (okc && r < nB) ? gamma[((int64_t)(aoB + r) * ncols + c0 + c) * n_occ + E] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int e = 0; e < SD_E; ++e) {
+      const double xa = XA[a][e], xb = XB[b][e];
+#pragma unroll
+      for (int c = 0; c < SD_COLS; ++c) {
+        G[c] = fma(xa, gB[c][b][e], G[c]);
+        if (bilocal) G[c] = fma(gA[c][a][e], xb, G[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < SD_COLS; ++c) Gs[c][t] = G[c];
+  __syncthreads();
+  const int warp = t >> 5, lane = t & 31;
+  const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
+  for (int q = p0 + warp; q < p1; q += 8) {
+    double part[SD_COLS];
+#pragma unroll
+    for (int c = 0; c < SD_COLS; ++c) part[c] = 0.0;
+    for (int i = lane; i < kBlk; i += 32) {
+      const double v = Vpad[(int64_t)q * kBlk + i];
+#pragma unroll
+      for (int c = 0; c < SD_COLS; ++c) part[c] = fma(v, Gs[c][i], part[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < SD_COLS; ++c) {
+      double v = part[c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      part[c] = v;
+    }
+    if (lane == 0) {
+      const int mu = blk_prod[q];
+#pragma unroll
+      for (int c = 0; c < SD_COLS; ++c) {
+        if (c0 + c >= ncols) continue;
+        const int64_t o = (int64_t)(c0 + c) * n_prod + mu;
+        Out[o] = subtract ? Zin[o] - part[c] : part[c];
+      }
+    }
+  }
+}
+
+__global__ void i2p_kernel(int n_rhs, int n, const double *__restrict__ in, double *__restrict__ out) {
+  const int64_t total = (int64_t)n_rhs * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n, mu = i % n;
+    out[(2 * r) * n + mu] = in[2 * i];
+    out[(2 * r + 1) * n + mu] = in[2 * i + 1];
+  }
+}
+
+__global__ void p2i_kernel(int n_rhs, int n, const double *__restrict__ in, double *__restrict__ out) {
+  const int64_t total = (int64_t)n_rhs * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n, mu = i % n;
+    out[2 * i] = in[(2 * r) * n + mu];
+    out[2 * i + 1] = in[(2 * r + 1) * n + mu];
+  }
+}
+
+int grid_for(int64_t total, int threads) {
+  int64_t g = (total + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+}  // namespace
+
+cudaError_t launch_gemm_f64(cudaStream_t st, int M, int N, int K, const double *A, int64_t lda,
+                            const double *B, int64_t ldb, double *C, int64_t ldc) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M);
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  gemm_f64_nn<<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interleaved_to_planar(cudaStream_t st, int n_rhs, int n, const double *in,
+                                         double *out) {
+  i2p_kernel<<<grid_for((int64_t)n_rhs * n, 256), 256, 0, st>>>(n_rhs, n, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_planar_to_interleaved(cudaStream_t st, int n_rhs, int n, const double *in,
+                                         double *out) {
+  p2i_kernel<<<grid_for((int64_t)n_rhs * n, 256), 256, 0, st>>>(n_rhs, n, in, out);
+  return cudaGetLastError();
+}
+
+namespace {
+struct Scope {
+  Timer *t;
+  cudaStream_t st;
+  int cls;
+  double flops;
+  cudaEvent_t a = nullptr;
+  Scope(Timer *t_, cudaStream_t st_, int cls_, double fl) : t(t_), st(st_), cls(cls_), flops(fl) {
+    if (t && t->on) t->begin(st, cls, &a);
+  }
+  ~Scope() {
+    if (t && t->on) t->end(st, cls, a, flops);
+  }
+};
+}  // namespace
+
+cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S,
+                                  OpMode mode, double eps, const double *Zin, double *Out) {
+  if (S <= 0) return cudaSuccess;
+  if (S > wk.slots) return cudaErrorInvalidValue;
+  const int ncols = 2 * S;
+  const int np = sys.n_prod;
+  cudaError_t err;
+  const double *Y = Zin;
+  if (mode == kKernel || mode == kA) {
+    // Y = Z K  (K symmetric, so row c of Y is K z_c)
+    Scope sc(wk.timer, st, kcGemmK, 2.0 * ncols * (double)np * np);
+    err = launch_gemm_f64(st, ncols, np, np, Zin, np, sys.K, np, (mode == kKernel) ? Out : wk.Y, np);
+    if (err != cudaSuccess || mode == kKernel) return err;
+    Y = wk.Y;
+  }
+  {
+    Scope sc(wk.timer, st, kcVertex, 2.0 * ncols * (double)kBlk * np);
+    dim3 grid(sys.n_blocks, (ncols + VW_COLS - 1) / VW_COLS);
+    vertex_contract<<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
+                                          sys.Vpad, Y, wk.W);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  {
+    Scope sc(wk.timer, st, kcBeta, 0.0);
+    dim3 grid(sys.n_atoms, (ncols + BT_COLS - 1) / BT_COLS);
+    beta_kernel<<<grid, BT_THREADS, 0, st>>>(ncols, sys.n_blocks, sys.n_occ, sys.aoff, sys.adj_ptr,
+                                             sys.adj, wk.W, sys.Xo, wk.beta);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  const int64_t ncolE = (int64_t)ncols * sys.n_occ;
+  if (ncolE > INT32_MAX) return cudaErrorInvalidValue;
+  const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)ncolE;
+  {
+    Scope sc(wk.timer, st, kcGemmT1, tflops);
+    err = launch_gemm_f64(st, sys.n_virt, (int)ncolE, sys.n_orb, sys.XvT, sys.n_orb, wk.beta,
+                          ncolE, wk.abuf, ncolE);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(wk.timer, st, kcDscale, 0.0);
+    dscale_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
+        sys.n_virt, S, sys.n_occ, sys.occ_value, sys.energy, wk.omega, eps, wk.abuf);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  {
+    Scope sc(wk.timer, st, kcGemmT2, tflops);
+    err = launch_gemm_f64(st, sys.n_orb, (int)ncolE, sys.n_virt, sys.Xv, sys.n_virt, wk.abuf,
+                          ncolE, wk.gamma, ncolE);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(wk.timer, st, kcSddmm, 0.0);
+    dim3 grid(sys.n_blocks, (ncols + SD_COLS - 1) / SD_COLS);
+    sddmm_dot<<<grid, 256, 0, st>>>(ncols, sys.n_occ, np, sys.aoff, sys.blk_atoms, sys.blk_ptr,
+                                    sys.blk_prod, sys.Vpad, sys.Xo, wk.gamma, Zin,
+                                    mode == kA ? 1 : 0, Out);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace tddft

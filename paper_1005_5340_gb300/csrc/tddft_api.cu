@@ -1,0 +1,537 @@
+// C boundary of libtddft (include/tddft.h): validation, device layouts,
+// workspace ownership and the host side of the batched GMRES driver.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+using namespace tddft;
+
+struct tddft_ctx {
+  DevSystem sys;
+  OpWork wk;
+  GmresState gs;
+  Timer timer;
+  tddft_options opts{};
+  cudaStream_t st = nullptr;
+  double *Zc = nullptr;     // [2S][n_prod] operator input (planar)
+  double *Wout = nullptr;   // [2S][n_prod] operator output (planar)
+  double *stage = nullptr;  // [2S][n_prod] interleaved staging for boundary calls
+  int *h_count = nullptr;   // pinned
+  std::vector<void *> dev_allocs;
+  std::string err;
+};
+
+namespace {
+thread_local std::string g_create_error;
+
+tddft_status fail(tddft_ctx *c, tddft_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+#define CUDA_TRY(ctx, expr)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, TDDFT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+cudaError_t dev_alloc(tddft_ctx *c, T **p, size_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+  if (e != cudaSuccess) return e;
+  c->dev_allocs.push_back(q);
+  *p = static_cast<T *>(q);
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t upload(tddft_ctx *c, T **p, const std::vector<T> &h) {
+  cudaError_t e = dev_alloc(c, p, h.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+bool all_finite(const double *p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+void release(tddft_ctx *c) {
+  c->timer.destroy();
+  for (void *p : c->dev_allocs) cudaFree(p);
+  c->dev_allocs.clear();
+  if (c->h_count) cudaFreeHost(c->h_count);
+  c->h_count = nullptr;
+}
+
+tddft_status check_omega(tddft_ctx *c, int n, const double *omega, bool device) {
+  if (!omega) return fail(c, TDDFT_ERR_INVALID_ARG, "omega is NULL");
+  if (!device && !all_finite(omega, (size_t)n))
+    return fail(c, TDDFT_ERR_INVALID_ARG, "omega holds NaN or Inf");
+  return TDDFT_OK;
+}
+}  // namespace
+
+namespace tddft {
+const char *kernel_class_name(int k) {
+  static const char *names[kcCount] = {"gemm_K",     "vertex_contract", "beta",
+                                       "gemm_T1",    "dscale",          "gemm_T2",
+                                       "sddmm_dot",  "gmres_step",      "gmres_gather",
+                                       "gmres_select", "misc"};
+  return (k >= 0 && k < kcCount) ? names[k] : "?";
+}
+
+cudaEvent_t Timer::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+void Timer::begin(cudaStream_t st, int, cudaEvent_t *a) {
+  *a = get();
+  cudaEventRecord(*a, st);
+}
+void Timer::end(cudaStream_t st, int cls, cudaEvent_t a, double fl) {
+  cudaEvent_t b = get();
+  cudaEventRecord(b, st);
+  pending.push_back({cls, a, b, fl});
+}
+void Timer::resolve() {
+  for (auto &r : pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      ms[r.cls] += t;
+      launches[r.cls] += 1;
+      flops[r.cls] += r.flops;
+    }
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  pending.clear();
+}
+void Timer::reset() {
+  resolve();
+  for (int i = 0; i < kcCount; ++i) { ms[i] = 0; launches[i] = 0; flops[i] = 0; }
+}
+void Timer::destroy() {
+  for (auto &r : pending) { pool.push_back(r.a); pool.push_back(r.b); }
+  pending.clear();
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+}
+}  // namespace tddft
+
+namespace {
+struct TimedLaunch {
+  Timer &t; cudaStream_t st; int cls; cudaEvent_t a = nullptr;
+  TimedLaunch(Timer &t_, cudaStream_t s, int c) : t(t_), st(s), cls(c) { if (t.on) t.begin(st, cls, &a); }
+  ~TimedLaunch() { if (t.on) t.end(st, cls, a, 0.0); }
+};
+
+tddft_status validate_system(const tddft_system *s, std::string &msg, tddft_status &code,
+                             int &n_occ, double &occ_value) {
+  code = TDDFT_ERR_INVALID_ARG;
+  if (!s) { msg = "system is NULL"; return code; }
+  if (s->n_atoms < 1 || s->n_orb < 2 || s->n_prod < 1) {
+    code = TDDFT_ERR_SHAPE; msg = "need n_atoms >= 1, n_orb >= 2, n_prod >= 1"; return code;
+  }
+  if (!s->atom_orb_offset || !s->eigenvalues || !s->occupations || !s->X || !s->prod_atoms ||
+      !s->vertex_offset || !s->vertex || !s->K || !s->dipole) {
+    msg = "a system pointer is NULL"; return code;
+  }
+  const int32_t *ao = s->atom_orb_offset;
+  if (ao[0] != 0 || ao[s->n_atoms] != s->n_orb) {
+    code = TDDFT_ERR_SHAPE; msg = "atom_orb_offset must start at 0 and end at n_orb"; return code;
+  }
+  for (int A = 0; A < s->n_atoms; ++A) {
+    int n = ao[A + 1] - ao[A];
+    if (n < 1) { code = TDDFT_ERR_SHAPE; msg = "every atom needs at least one orbital"; return code; }
+    if (n > kMaxOrb) {
+      code = TDDFT_ERR_UNSUPPORTED; msg = "more than 16 orbitals on one atom"; return code;
+    }
+  }
+  const size_t no = (size_t)s->n_orb, np = (size_t)s->n_prod;
+  if (!all_finite(s->eigenvalues, no) || !all_finite(s->occupations, no) ||
+      !all_finite(s->X, no * no) || !all_finite(s->dipole, 3 * np) || !all_finite(s->K, np * np)) {
+    msg = "NaN or Inf in the system"; return code;
+  }
+  for (size_t i = 1; i < no; ++i)
+    if (s->eigenvalues[i] < s->eigenvalues[i - 1]) { msg = "eigenvalues not ascending"; return code; }
+  // step profile: n_occ equal positive values, then zeros
+  n_occ = 0;
+  occ_value = s->occupations[0];
+  while (n_occ < s->n_orb && s->occupations[n_occ] > 0.0) ++n_occ;
+  bool step = n_occ >= 1 && n_occ < s->n_orb;
+  for (int i = 0; step && i < s->n_orb; ++i) {
+    if (i < n_occ && s->occupations[i] != occ_value) step = false;
+    if (i >= n_occ && s->occupations[i] != 0.0) step = false;
+  }
+  if (!step) {
+    code = TDDFT_ERR_UNSUPPORTED;
+    msg = "occupations must be equal positive values on the lowest states, then zeros";
+    return code;
+  }
+  if (s->vertex_offset[0] != 0) { code = TDDFT_ERR_SHAPE; msg = "vertex_offset[0] != 0"; return code; }
+  double vmax = 0.0;
+  for (int mu = 0; mu < s->n_prod; ++mu) {
+    int A = s->prod_atoms[2 * mu], B = s->prod_atoms[2 * mu + 1];
+    if (A < 0 || B < A || B >= s->n_atoms) {
+      code = TDDFT_ERR_SHAPE; msg = "prod_atoms must satisfy 0 <= A <= B < n_atoms"; return code;
+    }
+    int64_t sz = (int64_t)(ao[A + 1] - ao[A]) * (ao[B + 1] - ao[B]);
+    if (s->vertex_offset[mu + 1] - s->vertex_offset[mu] != sz) {
+      code = TDDFT_ERR_SHAPE; msg = "vertex_offset does not match the block sizes"; return code;
+    }
+  }
+  const size_t nv = (size_t)s->vertex_offset[s->n_prod];
+  if (!all_finite(s->vertex, nv)) { msg = "NaN or Inf in the vertex"; return code; }
+  for (size_t i = 0; i < nv; ++i) vmax = std::fmax(vmax, std::fabs(s->vertex[i]));
+  for (int mu = 0; mu < s->n_prod; ++mu) {
+    int A = s->prod_atoms[2 * mu], B = s->prod_atoms[2 * mu + 1];
+    if (A != B) continue;
+    int n = ao[A + 1] - ao[A];
+    const double *v = s->vertex + s->vertex_offset[mu];
+    for (int a = 0; a < n; ++a)
+      for (int b = a + 1; b < n; ++b)
+        if (std::fabs(v[a * n + b] - v[b * n + a]) > 1e-12 * vmax) {
+          msg = "a local vertex block is not symmetric"; return code;
+        }
+  }
+  double kmax = 0.0;
+  for (size_t i = 0; i < np * np; ++i) kmax = std::fmax(kmax, std::fabs(s->K[i]));
+  const size_t T = 64;
+  for (size_t i0 = 0; i0 < np; i0 += T)
+    for (size_t j0 = i0; j0 < np; j0 += T)
+      for (size_t i = i0; i < std::min(np, i0 + T); ++i)
+        for (size_t j = std::max(j0, i + 1); j < std::min(np, j0 + T); ++j)
+          if (std::fabs(s->K[i * np + j] - s->K[j * np + i]) > 1e-12 * kmax) {
+            code = TDDFT_ERR_UNSUPPORTED; msg = "K is not symmetric"; return code;
+          }
+  code = TDDFT_OK;
+  return TDDFT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_ctx **out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, TDDFT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!o) return fail(nullptr, TDDFT_ERR_INVALID_ARG, "options are NULL");
+  if (o->prec != TDDFT_PREC_FP64)
+    return fail(nullptr, TDDFT_ERR_UNSUPPORTED, "unknown precision");
+  if (o->restart < 1 || o->restart > 256 || o->max_restarts < 1 || !(o->tol > 0.0) ||
+      !std::isfinite(o->tol) || o->batch < 1)
+    return fail(nullptr, TDDFT_ERR_INVALID_ARG, "bad options (restart 1..256, max_restarts >= 1, tol > 0, batch >= 1)");
+  std::string msg;
+  tddft_status code;
+  int n_occ = 0;
+  double occ_value = 0.0;
+  if (validate_system(s, msg, code, n_occ, occ_value) != TDDFT_OK) return fail(nullptr, code, msg);
+
+  tddft_ctx *c = new tddft_ctx();
+  c->opts = *o;
+  c->st = static_cast<cudaStream_t>(o->stream);
+  DevSystem &d = c->sys;
+  d.n_atoms = s->n_atoms;
+  d.n_orb = s->n_orb;
+  d.n_occ = n_occ;
+  d.n_virt = s->n_orb - n_occ;
+  d.n_prod = s->n_prod;
+  d.occ_value = occ_value;
+  const int no = d.n_orb, nocc = d.n_occ, nv = d.n_virt, np = d.n_prod;
+
+  // blocks: distinct (A, B) pairs in (A, B) order; products grouped per block
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  for (int mu = 0; mu < np; ++mu)
+    groups[{s->prod_atoms[2 * mu], s->prod_atoms[2 * mu + 1]}].push_back(mu);
+  std::vector<int2> blk_atoms;
+  std::vector<int> blk_ptr{0}, blk_prod;
+  std::vector<double> Vpad;
+  Vpad.reserve((size_t)np * kBlk);
+  std::vector<std::vector<int4>> adj_of(d.n_atoms);
+  const int32_t *ao = s->atom_orb_offset;
+  for (auto &kv : groups) {
+    const int A = kv.first.first, B = kv.first.second;
+    const int k = (int)blk_atoms.size();
+    blk_atoms.push_back(make_int2(A, B));
+    const int nA = ao[A + 1] - ao[A], nB = ao[B + 1] - ao[B];
+    for (int mu : kv.second) {
+      blk_prod.push_back(mu);
+      const double *v = s->vertex + s->vertex_offset[mu];
+      for (int a = 0; a < kMaxOrb; ++a)
+        for (int b = 0; b < kMaxOrb; ++b)
+          Vpad.push_back((a < nA && b < nB) ? v[a * nB + b] : 0.0);
+    }
+    blk_ptr.push_back((int)blk_prod.size());
+    adj_of[A].push_back(make_int4(k, B, 0, 0));
+    if (A != B) adj_of[B].push_back(make_int4(k, A, 1, 0));
+  }
+  d.n_blocks = (int)blk_atoms.size();
+  std::vector<int> adj_ptr{0};
+  std::vector<int4> adj;
+  for (int A = 0; A < d.n_atoms; ++A) {
+    for (auto &e : adj_of[A]) adj.push_back(e);
+    adj_ptr.push_back((int)adj.size());
+  }
+  d.n_adj = (int)adj.size();
+
+  std::vector<double> Xo((size_t)no * nocc), XvT((size_t)nv * no), Xv((size_t)no * nv);
+  for (int a = 0; a < no; ++a) {
+    for (int E = 0; E < nocc; ++E) Xo[(size_t)a * nocc + E] = s->X[a + (size_t)E * no];
+    for (int F = 0; F < nv; ++F) {
+      const double x = s->X[a + (size_t)(nocc + F) * no];
+      XvT[(size_t)F * no + a] = x;
+      Xv[(size_t)a * nv + F] = x;
+    }
+  }
+  std::vector<int> aoffv(ao, ao + d.n_atoms + 1);
+  std::vector<double> energy(s->eigenvalues, s->eigenvalues + no);
+  std::vector<double> dip(s->dipole, s->dipole + 3 * (size_t)np);
+
+  cudaError_t e = cudaSuccess;
+#define UP(ptr, vec) if (e == cudaSuccess) e = upload(c, &(ptr), vec)
+  UP(d.aoff, aoffv);
+  UP(d.energy, energy);
+  UP(d.Xo, Xo);
+  UP(d.XvT, XvT);
+  UP(d.Xv, Xv);
+  UP(d.dip, dip);
+  UP(d.blk_atoms, blk_atoms);
+  UP(d.blk_ptr, blk_ptr);
+  UP(d.blk_prod, blk_prod);
+  UP(d.Vpad, Vpad);
+  UP(d.adj_ptr, adj_ptr);
+  UP(d.adj, adj);
+#undef UP
+  if (e == cudaSuccess) e = dev_alloc(c, &d.K, (size_t)np * np);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(d.K, s->K, (size_t)np * np * sizeof(double), cudaMemcpyHostToDevice);
+
+  const size_t S = (size_t)o->batch, m = (size_t)o->restart;
+  OpWork &w = c->wk;
+  w.slots = (int)S;
+  w.timer = &c->timer;
+#define AL(ptr, n) if (e == cudaSuccess) e = dev_alloc(c, &(ptr), (n))
+  AL(w.Y, 2 * S * np);
+  AL(w.W, 2 * S * (size_t)d.n_blocks * kBlk);
+  AL(w.beta, (size_t)no * 2 * S * nocc);
+  AL(w.abuf, (size_t)nv * 2 * S * nocc);
+  AL(w.gamma, (size_t)no * 2 * S * nocc);
+  AL(w.omega, S);
+  AL(c->Zc, 2 * S * np);
+  AL(c->Wout, 2 * S * np);
+  AL(c->stage, 2 * S * np);
+  GmresState &g = c->gs;
+  g.cap = (int)S;
+  g.m = o->restart;
+  g.max_restarts = o->max_restarts;
+  g.tol = o->tol;
+  AL(g.state, S); AL(g.jcur, S); AL(g.cycles, S); AL(g.matvecs, S); AL(g.conv, S);
+  AL(g.bnorm, S); AL(g.resid, S); AL(g.omega, S);
+  AL(g.H, S * (m + 1) * m); AL(g.cs, S * m); AL(g.sn, S * m); AL(g.g, S * (m + 1));
+  AL(g.V, S * (m + 1) * 2 * np); AL(g.x, S * 2 * np); AL(g.b, S * 2 * np);
+  AL(g.act, S); AL(g.count, 1);
+#undef AL
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_count, sizeof(int));
+  if (e != cudaSuccess) {
+    std::string m2 = std::string("device allocation/upload failed: ") + cudaGetErrorString(e);
+    release(c);
+    delete c;
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? TDDFT_ERR_NOMEM : TDDFT_ERR_CUDA, m2);
+  }
+  *out = c;
+  return TDDFT_OK;
+}
+
+void tddft_destroy(tddft_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  release(c);
+  delete c;
+}
+
+const char *tddft_last_error(const tddft_ctx *c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+tddft_status tddft_sizes(const tddft_ctx *c, int32_t *n_orb, int32_t *n_occ, int32_t *n_prod,
+                         int32_t *n_blocks) {
+  if (!c) return TDDFT_ERR_INVALID_ARG;
+  if (n_orb) *n_orb = c->sys.n_orb;
+  if (n_occ) *n_occ = c->sys.n_occ;
+  if (n_prod) *n_prod = c->sys.n_prod;
+  if (n_blocks) *n_blocks = c->sys.n_blocks;
+  return TDDFT_OK;
+}
+
+static tddft_status boundary_apply(tddft_ctx *c, OpMode mode, int32_t n_rhs, const double *omega,
+                                   double eps, const double *z, double *out, int32_t flags) {
+  if (!c) return TDDFT_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!z || !out) return fail(c, TDDFT_ERR_INVALID_ARG, "z or out is NULL");
+  if (n_rhs < 1 || n_rhs > c->wk.slots)
+    return fail(c, TDDFT_ERR_SHAPE, "n_rhs must be in 1..batch");
+  const bool dev = (flags & TDDFT_DEVICE_PTRS) != 0;
+  if (mode != kKernel) {
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, TDDFT_ERR_INVALID_ARG, "eps must be > 0");
+    tddft_status s = check_omega(c, n_rhs, omega, dev);
+    if (s != TDDFT_OK) return s;
+  }
+  const int np = c->sys.n_prod;
+  const size_t bytes = (size_t)n_rhs * np * 2 * sizeof(double);
+  cudaStream_t st = c->st;
+  if (mode != kKernel)
+    CUDA_TRY(c, cudaMemcpyAsync(c->wk.omega, omega, n_rhs * sizeof(double),
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  const double *zin = z;
+  if (!dev) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->stage, z, bytes, cudaMemcpyHostToDevice, st));
+    zin = c->stage;
+  }
+  CUDA_TRY(c, launch_interleaved_to_planar(st, n_rhs, np, zin, c->Zc));
+  CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, n_rhs, mode, eps, c->Zc, c->Wout));
+  CUDA_TRY(c, launch_planar_to_interleaved(st, n_rhs, np, c->Wout, dev ? out : c->stage));
+  if (!dev) {
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->stage, bytes, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    c->timer.resolve();
+  }
+  return TDDFT_OK;
+}
+
+tddft_status tddft_chi0_apply(tddft_ctx *c, int32_t n_rhs, const double *omega, double eps,
+                              const double *z, double *out, int32_t flags) {
+  return boundary_apply(c, kChi0, n_rhs, omega, eps, z, out, flags);
+}
+
+tddft_status tddft_kernel_apply(tddft_ctx *c, int32_t n_rhs, const double *z, double *out,
+                                int32_t flags) {
+  return boundary_apply(c, kKernel, n_rhs, nullptr, 1.0, z, out, flags);
+}
+
+tddft_status tddft_apply_A(tddft_ctx *c, int32_t n_rhs, const double *omega, double eps,
+                           const double *z, double *out, int32_t flags) {
+  return boundary_apply(c, kA, n_rhs, omega, eps, z, out, flags);
+}
+
+tddft_status tddft_polarizability(tddft_ctx *c, int32_t n_omega, const double *omega, double eps,
+                                  double *P, tddft_solve_stats *stats, int32_t flags) {
+  if (!c) return TDDFT_ERR_INVALID_ARG;
+  c->err.clear();
+  if (n_omega < 1) return fail(c, TDDFT_ERR_SHAPE, "n_omega must be >= 1");
+  if (!P) return fail(c, TDDFT_ERR_INVALID_ARG, "P is NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, TDDFT_ERR_INVALID_ARG, "eps must be > 0");
+  const bool dev = (flags & TDDFT_DEVICE_PTRS) != 0;
+  tddft_status s0 = check_omega(c, n_omega, omega, dev);
+  if (s0 != TDDFT_OK) return s0;
+  cudaStream_t st = c->st;
+  const int total = 3 * n_omega;
+  const int S = c->wk.slots;
+  const int np = c->sys.n_prod;
+  GmresState &g = c->gs;
+
+  double *d_omega = nullptr;
+  double2 *d_P = nullptr;
+  CUDA_TRY(c, cudaMalloc(&d_omega, n_omega * sizeof(double)));
+  cudaError_t e = cudaMalloc(&d_P, (size_t)n_omega * 9 * sizeof(double2));
+  if (e != cudaSuccess) { cudaFree(d_omega); return fail(c, TDDFT_ERR_NOMEM, "P buffer"); }
+  struct Free { void *a, *b; ~Free() { cudaFree(a); cudaFree(b); } } fr{d_omega, d_P};
+  CUDA_TRY(c, cudaMemcpyAsync(d_omega, omega, n_omega * sizeof(double),
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+
+  bool all_conv = true;
+  std::vector<int> h_mv(S), h_cy(S), h_cv(S);
+  std::vector<double> h_res(S);
+  const long max_iter = (long)(g.max_restarts + 1) * (g.m + 1) + 4;
+  for (int g0 = 0; g0 < total; g0 += S) {
+    const int n = std::min(S, total - g0);
+    CUDA_TRY(c, launch_rhs_init(st, c->sys, n, g0, d_omega, c->Zc, c->wk.omega, g.omega));
+    CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, n, kChi0, eps, c->Zc, c->Wout));
+    CUDA_TRY(c, launch_gmres_start(st, c->sys, g, n, c->Wout));
+    long it = 0;
+    for (;; ++it) {
+      if (it > max_iter)
+        return fail(c, TDDFT_ERR_TIMEOUT, "GMRES driver exceeded its iteration bound");
+      {
+        TimedLaunch tl(c->timer, st, kcGmresSelect);
+        CUDA_TRY(c, launch_gmres_select(st, g, n));
+      }
+      CUDA_TRY(c, cudaMemcpyAsync(c->h_count, g.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(c, cudaStreamSynchronize(st));
+      const int cnt = *c->h_count;
+      if (cnt <= 0) break;
+      {
+        TimedLaunch tl(c->timer, st, kcGmresGather);
+        CUDA_TRY(c, launch_gmres_gather(st, c->sys, g, cnt, c->Zc, c->wk.omega));
+      }
+      CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, cnt, kA, eps, c->Zc, c->Wout));
+      {
+        TimedLaunch tl(c->timer, st, kcGmresStep);
+        CUDA_TRY(c, launch_gmres_step(st, c->sys, g, cnt, c->Wout));
+      }
+    }
+    CUDA_TRY(c, launch_polarization(st, c->sys, g, n, g0, d_P));
+    CUDA_TRY(c, cudaMemcpyAsync(h_mv.data(), g.matvecs, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(h_cy.data(), g.cycles, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(h_cv.data(), g.conv, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(h_res.data(), g.resid, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    c->timer.resolve();
+    for (int r = 0; r < n; ++r) {
+      if (!h_cv[r]) all_conv = false;
+      if (stats) {
+        tddft_solve_stats &t = stats[g0 + r];
+        t.matvecs = h_mv[r];
+        t.cycles = h_cy[r];
+        t.resid = h_res[r];
+        t.converged = h_cv[r];
+        t.pad = 0;
+      }
+    }
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(P, d_P, (size_t)n_omega * 9 * sizeof(double2),
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (!all_conv) return fail(c, TDDFT_ERR_NOT_CONVERGED, "some (omega, direction) missed tol");
+  return TDDFT_OK;
+}
+
+tddft_status tddft_timing_enable(tddft_ctx *c, int32_t on) {
+  if (!c) return TDDFT_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->st);
+  c->timer.reset();
+  c->timer.on = on != 0;
+  return TDDFT_OK;
+}
+
+int32_t tddft_timing_count(const tddft_ctx *) { return kcCount; }
+
+tddft_status tddft_timing_get(tddft_ctx *c, int32_t i, const char **name, int32_t *launches,
+                              double *total_ms, double *flops) {
+  if (!c || i < 0 || i >= kcCount) return TDDFT_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->st);
+  c->timer.resolve();
+  if (name) *name = kernel_class_name(i);
+  if (launches) *launches = c->timer.launches[i];
+  if (total_ms) *total_ms = c->timer.ms[i];
+  if (flops) *flops = c->timer.flops[i];
+  return TDDFT_OK;
+}
+
+}  // extern "C"

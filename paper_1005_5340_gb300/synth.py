@@ -249,3 +249,8 @@ def random_complex_vectors(n_rhs: int, n: int, seed: int) -> np.ndarray:
     rng = CounterRNG(seed, 77)
     z = rng.normal(2 * n_rhs * n).reshape(n_rhs, n, 2)
     return z[..., 0] + 1j * z[..., 1]
+
+
+def workload_system(name: str) -> System:
+    """The molecule of a named workload (picklable factory for worker processes)."""
+    return workload(name)[0]

@@ -1,0 +1,249 @@
+"""Python binding of libtddft (include/tddft.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels.  Host numpy
+arrays or CUDA torch tensors are accepted; torch supplies device memory and
+the stream.  If the shared library is missing the import fails loudly: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtddft.so")
+
+OK, ERR_INVALID_ARG, ERR_SHAPE, ERR_NOMEM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, \
+    ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = ["OK", "INVALID_ARG", "SHAPE", "NOMEM", "CUDA", "NOT_CONVERGED", "TIMEOUT",
+                "UNSUPPORTED"]
+DEVICE_PTRS = 1
+PREC = {"fp64": 0}
+
+
+class TddftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class _System(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("atom_orb_offset", ctypes.c_void_p),
+                ("n_orb", ctypes.c_int32), ("eigenvalues", ctypes.c_void_p),
+                ("occupations", ctypes.c_void_p), ("X", ctypes.c_void_p),
+                ("n_prod", ctypes.c_int32), ("prod_atoms", ctypes.c_void_p),
+                ("vertex_offset", ctypes.c_void_p), ("vertex", ctypes.c_void_p),
+                ("K", ctypes.c_void_p), ("dipole", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("max_restarts", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("batch", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("matvecs", ctypes.c_int32), ("cycles", ctypes.c_int32),
+                ("resid", ctypes.c_double), ("converged", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+# Every exported symbol with its ctypes signature (checked by the tests
+# against include/tddft.h).
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "tddft_create": (ctypes.c_int, [ctypes.POINTER(_System), ctypes.POINTER(_Options),
+                                    ctypes.POINTER(ctypes.c_void_p)]),
+    "tddft_chi0_apply": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
+                                        ctypes.c_int32]),
+    "tddft_kernel_apply": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
+    "tddft_apply_A": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
+                                     ctypes.c_int32]),
+    "tddft_polarizability": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
+                                            ctypes.c_int32]),
+    "tddft_sizes": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "tddft_timing_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "tddft_timing_count": (ctypes.c_int32, [_P]),
+    "tddft_timing_get": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
+                                        _P, _P, _P]),
+    "tddft_last_error": (ctypes.c_char_p, [_P]),
+    "tddft_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtddft.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_1005_5340_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Context:
+    """One molecule resident on the GPU (tddft_create .. tddft_destroy)."""
+
+    def __init__(self, system, *, restart: int = 40, max_restarts: int = 200, tol: float = 1e-6,
+                 batch: int = 64, prec: str = "fp64", stream=None):
+        lib = load_library()
+        self._lib = lib
+        keep = dict(
+            aoff=_c(system.atom_orb_offset, np.int32), E=_c(system.eigenvalues, np.float64),
+            occ=_c(system.occupations, np.float64),
+            X=np.asfortranarray(system.X, dtype=np.float64),
+            pa=_c(system.prod_atoms, np.int32), voff=_c(system.vertex_offset, np.int64),
+            v=_c(system.vertex, np.float64), K=_c(system.K, np.float64),
+            d=_c(system.dipole, np.float64))
+        s = _System(int(system.n_atoms), keep["aoff"].ctypes.data, int(keep["E"].size),
+                    keep["E"].ctypes.data, keep["occ"].ctypes.data, keep["X"].ctypes.data,
+                    int(keep["pa"].shape[0]), keep["pa"].ctypes.data, keep["voff"].ctypes.data,
+                    keep["v"].ctypes.data, keep["K"].ctypes.data, keep["d"].ctypes.data)
+        if stream is None:
+            stream = _current_stream()
+        self.stream_handle = stream
+        o = _Options(PREC[prec], restart, max_restarts, tol, batch, stream or 0)
+        h = ctypes.c_void_p()
+        st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
+        if st != OK:
+            raise TddftError(st, lib.tddft_last_error(None).decode())
+        self.h = h
+        self.batch = batch
+        self.n_prod = int(system.n_prod)
+        n_orb, n_occ, n_prod, nb = (ctypes.c_int32() for _ in range(4))
+        lib.tddft_sizes(h, ctypes.byref(n_orb), ctypes.byref(n_occ), ctypes.byref(n_prod),
+                        ctypes.byref(nb))
+        self.n_orb, self.n_occ, self.n_blocks = n_orb.value, n_occ.value, nb.value
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.tddft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st):
+        if st != OK:
+            raise TddftError(st, self._lib.tddft_last_error(self.h).decode())
+
+    # -- operators -----------------------------------------------------------
+    def _apply(self, fn, z, omega, eps, with_omega: bool):
+        if _is_torch(z) and z.is_cuda:
+            import torch
+            z = z.to(torch.complex128).contiguous()
+            n = z.shape[0]
+            out = torch.empty_like(z)
+            args = [self.h, n]
+            if with_omega:
+                om = torch.as_tensor(omega, dtype=torch.float64, device=z.device).reshape(-1)
+                om = om.expand(n).contiguous() if om.numel() == 1 else om.contiguous()
+                args += [om.data_ptr(), float(eps)]
+            args += [torch.view_as_real(z).data_ptr(), torch.view_as_real(out).data_ptr(),
+                     DEVICE_PTRS]
+            self._check(fn(*args))
+            return out
+        z = np.ascontiguousarray(np.atleast_2d(z), dtype=np.complex128)
+        n = z.shape[0]
+        out = np.empty_like(z)
+        args = [self.h, n]
+        if with_omega:
+            om = np.broadcast_to(np.asarray(omega, dtype=np.float64), (n,)).copy()
+            args += [om.ctypes.data, float(eps)]
+        args += [z.ctypes.data, out.ctypes.data, 0]
+        self._check(fn(*args))
+        return out
+
+    def chi0_apply(self, z, omega, eps):
+        """chi0(omega_r) z_r for each row r of z (n_rhs x n_prod complex)."""
+        return self._apply(self._lib.tddft_chi0_apply, z, omega, eps, True)
+
+    def kernel_apply(self, z):
+        """K z_r for each row r of z."""
+        return self._apply(self._lib.tddft_kernel_apply, z, None, None, False)
+
+    def apply_A(self, z, omega, eps):
+        """z_r - chi0(omega_r) K z_r for each row r of z."""
+        return self._apply(self._lib.tddft_apply_A, z, omega, eps, True)
+
+    def polarizability(self, omega, eps, *, raise_on_nonconvergence: bool = True):
+        """P[w, i, k] (complex, n_omega x 3 x 3) and per-(w, k) stats."""
+        if _is_torch(omega) and omega.is_cuda:
+            import torch
+            om = omega.to(torch.float64).contiguous()
+            n = om.numel()
+            P = torch.empty((n, 3, 3), dtype=torch.complex128, device=om.device)
+            stats = (SolveStats * (3 * n))()
+            st = self._lib.tddft_polarizability(self.h, n, om.data_ptr(), float(eps),
+                                                torch.view_as_real(P).data_ptr(), stats,
+                                                DEVICE_PTRS)
+        else:
+            om = np.ascontiguousarray(np.atleast_1d(omega), dtype=np.float64)
+            n = om.size
+            P = np.empty((n, 3, 3), dtype=np.complex128)
+            stats = (SolveStats * (3 * n))()
+            st = self._lib.tddft_polarizability(self.h, n, om.ctypes.data, float(eps),
+                                                P.ctypes.data, stats, 0)
+        if st != OK and not (st == ERR_NOT_CONVERGED and not raise_on_nonconvergence):
+            self._check(st)
+        info = dict(
+            matvecs=np.array([s.matvecs for s in stats]).reshape(n, 3),
+            cycles=np.array([s.cycles for s in stats]).reshape(n, 3),
+            resid=np.array([s.resid for s in stats]).reshape(n, 3),
+            converged=np.array([s.converged for s in stats], dtype=bool).reshape(n, 3))
+        return P, info
+
+    # -- timing ---------------------------------------------------------------
+    def timing_enable(self, on: bool = True):
+        self._check(self._lib.tddft_timing_enable(self.h, 1 if on else 0))
+
+    def timing(self) -> dict:
+        res = {}
+        for i in range(self._lib.tddft_timing_count(self.h)):
+            name = ctypes.c_char_p()
+            n = ctypes.c_int32()
+            ms = ctypes.c_double()
+            fl = ctypes.c_double()
+            self._check(self._lib.tddft_timing_get(self.h, i, ctypes.byref(name), ctypes.byref(n),
+                                                   ctypes.byref(ms), ctypes.byref(fl)))
+            res[name.value.decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value)
+        return res
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None

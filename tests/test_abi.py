@@ -1,0 +1,116 @@
+"""The C boundary without a GPU: the library builds, loads, exports every
+function include/tddft.h declares, and rejects bad input on the host before
+any device work."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1005_5340_gb300 import synth, tddft
+from tests.libutil import ensure_library, header_functions
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ensure_library()
+
+
+def test_every_declared_function_is_exported_and_bound(lib):
+    names = header_functions()
+    assert "tddft_create" in names and "tddft_polarizability" in names
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in tddft.SIGNATURES, n
+    assert set(tddft.SIGNATURES) <= set(names)
+
+
+def _create(sysm, **opt):
+    lib = tddft.load_library()
+    keep = dict(
+        aoff=np.ascontiguousarray(sysm.atom_orb_offset, np.int32),
+        E=np.ascontiguousarray(sysm.eigenvalues, np.float64),
+        occ=np.ascontiguousarray(sysm.occupations, np.float64),
+        X=np.asfortranarray(sysm.X, np.float64),
+        pa=np.ascontiguousarray(sysm.prod_atoms, np.int32),
+        voff=np.ascontiguousarray(sysm.vertex_offset, np.int64),
+        v=np.ascontiguousarray(sysm.vertex, np.float64),
+        K=np.ascontiguousarray(sysm.K, np.float64),
+        d=np.ascontiguousarray(sysm.dipole, np.float64))
+    s = tddft._System(sysm.n_atoms, keep["aoff"].ctypes.data, keep["E"].size, keep["E"].ctypes.data,
+                      keep["occ"].ctypes.data, keep["X"].ctypes.data, keep["pa"].shape[0],
+                      keep["pa"].ctypes.data, keep["voff"].ctypes.data, keep["v"].ctypes.data,
+                      keep["K"].ctypes.data, keep["d"].ctypes.data)
+    o = tddft._Options(opt.get("prec", 0), opt.get("restart", 10), opt.get("max_restarts", 5),
+                       opt.get("tol", 1e-8), opt.get("batch", 4), None)
+    h = ctypes.c_void_p()
+    st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
+    return st, lib.tddft_last_error(None).decode(), h
+
+
+def _bad(mutate, **opt):
+    s = synth.tiny_system(3)
+    mutate(s)
+    return _create(s, **opt)
+
+
+def test_validation_rejects_bad_input_before_device_work(lib):
+    def nan_k(s):
+        s.K = s.K.copy(); s.K[0, 1] = np.nan
+    st, msg, h = _bad(nan_k)
+    assert st == tddft.ERR_INVALID_ARG and "NaN" in msg and not h.value
+
+    def asym_k(s):
+        s.K = s.K.copy(); s.K[0, 1] += 1e-3
+    st, msg, _ = _bad(asym_k)
+    assert st == tddft.ERR_UNSUPPORTED and "symmetric" in msg
+
+    def unsorted(s):
+        s.eigenvalues = s.eigenvalues[::-1].copy()
+    assert _bad(unsorted)[0] == tddft.ERR_INVALID_ARG
+
+    def fractional(s):
+        s.occupations = s.occupations.copy(); s.occupations[0] = 1.0
+    assert _bad(fractional)[0] == tddft.ERR_UNSUPPORTED
+
+    def no_empty(s):
+        s.occupations = np.full_like(s.occupations, 2.0)
+    assert _bad(no_empty)[0] == tddft.ERR_UNSUPPORTED
+
+    def bad_pair(s):
+        s.prod_atoms = s.prod_atoms.copy(); s.prod_atoms[-1] = (1, 0)
+    assert _bad(bad_pair)[0] == tddft.ERR_SHAPE
+
+    def bad_offset(s):
+        s.vertex_offset = s.vertex_offset.copy(); s.vertex_offset[1] += 1
+    assert _bad(bad_offset)[0] == tddft.ERR_SHAPE
+
+    def asym_local(s):
+        s.vertex = s.vertex.copy(); s.vertex[1] += 0.5
+    assert _bad(asym_local)[0] == tddft.ERR_INVALID_ARG
+
+    assert _bad(lambda s: None, restart=0)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, tol=-1.0)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, batch=0)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, prec=9)[0] == tddft.ERR_UNSUPPORTED
+
+
+def test_more_than_16_orbitals_per_atom_is_unsupported(lib):
+    s = synth.make_system(2, 4, orb_per_atom=17, occ_per_atom=1, n_local=2, n_bilocal=1,
+                          density=0.02)
+    st, msg, _ = _create(s)
+    assert st == tddft.ERR_UNSUPPORTED and "16" in msg
+
+
+def test_calls_on_a_null_context_fail_cleanly(lib):
+    assert lib.tddft_chi0_apply(None, 1, None, 0.1, None, None, 0) == tddft.ERR_INVALID_ARG
+    assert lib.tddft_polarizability(None, 1, None, 0.1, None, None, 0) == tddft.ERR_INVALID_ARG
+    lib.tddft_destroy(None)
+    assert isinstance(lib.tddft_last_error(None), bytes)
+
+
+def test_create_without_a_gpu_reports_a_cuda_error(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, msg, h = _create(synth.tiny_system(3))
+    assert st in (tddft.ERR_CUDA, tddft.ERR_NOMEM) and msg and not h.value
