@@ -49,7 +49,12 @@ typedef enum {
 #define TDDFT_DEVICE_PTRS 1
 
 typedef enum {
-  TDDFT_PREC_FP64 = 0       /* every step in float64 */
+  TDDFT_PREC_FP64 = 0,      /* every step in float64 */
+  TDDFT_PREC_BF16X3_IR = 2  /* inner GMRES products in split bf16 on the tensor cores
+                               (hi*hi + hi*lo + lo*hi, float32 accumulation) and float32
+                               vertex contractions; right-hand sides, residuals that end
+                               each cycle, Arnoldi, Givens and the basis in float64
+                               (iterative refinement) */
 } tddft_precision;
 
 /*
@@ -91,7 +96,9 @@ typedef struct {
 
 /*
  * Solver and resource options.
- *  prec: TDDFT_PREC_FP64.
+ *  prec: TDDFT_PREC_FP64 or TDDFT_PREC_BF16X3_IR.  With BF16X3_IR,
+ *      tddft_chi0_apply and tddft_apply_A use the reduced-precision operator
+ *      (relative error ~1e-5) and tddft_kernel_apply stays float64.
  *  restart: GMRES restart length m (1..256).
  *  max_restarts: cycles before an (omega, direction) is declared not
  *      converged (>= 1).
@@ -100,6 +107,10 @@ typedef struct {
  *  batch: maximum number of right-hand sides solved together (>= 1); sizes
  *      every device workspace allocated by tddft_create.
  *  stream: cudaStream_t for all work (NULL = legacy default stream).
+ *  inner_tol: refinement forms only: a GMRES cycle (whose products are in
+ *      reduced precision) also ends once its residual estimate has dropped
+ *      by this factor; the float64 residual then starts the next cycle.
+ *      In (0, 1); ignored for TDDFT_PREC_FP64.
  */
 typedef struct {
   int32_t prec;
@@ -108,6 +119,7 @@ typedef struct {
   double tol;
   int32_t batch;
   void *stream;
+  double inner_tol;
 } tddft_options;
 
 /* Per-(omega, direction) solver report. */
@@ -176,6 +188,17 @@ tddft_status tddft_timing_enable(tddft_ctx *ctx, int32_t on);
 int32_t tddft_timing_count(const tddft_ctx *ctx);
 tddft_status tddft_timing_get(tddft_ctx *ctx, int32_t i, const char **name, int32_t *launches,
                               double *total_ms, double *flops);
+
+/*
+ * Self-test of the split-bf16 tensor-core GEMM used by TDDFT_PREC_BF16X3_IR:
+ * C^T = A B^T for deterministic pseudo-random A [M x K], B [N x K] (entries
+ * uniform in [-1, 1) from a hash of (index, seed)), compared with a float64
+ * product of the same operands.  *max_rel_err = max |C - C_ref| / max |C_ref|.
+ * Allocates and frees its own device buffers; synchronises the device.
+ * Returns TIMEOUT if a bounded wait inside the GEMM gave up.
+ */
+tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uint64_t seed,
+                                 double *max_rel_err);
 
 /* Text of the last error on this context (never NULL; "" if none).  With
  * ctx == NULL: the last error of a failed tddft_create on this thread. */

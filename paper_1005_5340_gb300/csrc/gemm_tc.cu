@@ -1,0 +1,443 @@
+// Tensor-core GEMM for the reduced-precision operator (sm_103a, tcgen05 +
+// TMA + mbarrier, inline PTX).
+//
+//   C^T[n][m] = sum_k A[m][k] * B[n][k]          (both operands K-major bf16)
+//
+// Split-bf16 ("bf16x3"): every real operand x is stored as two bf16 planes
+// x = hi + lo (+ O(2^-17 |x|)), each row laid out [hi | lo] with Kp columns
+// per plane (Kp a multiple of 64, zero padded).  The product is accumulated
+// in float32 in tensor memory over three segments,
+//   A_hi B_hi + A_hi B_lo + A_lo B_hi ,
+// i.e. segment g reads A plane aseg[g] and B plane bseg[g].  One launch
+// computes a 128 x 128 tile of C^T per CTA:
+//   warp 0 lane 0 : TMA producer (3-stage ring of 64-deep K slices, SW128)
+//   warp 1 lane 0 : issues tcgen05.mma (M=128, N=128, K=16) into TMEM
+//   warps 0-3     : epilogue, TMEM -> registers -> global, fused per use:
+//     kStoreF32    plain float32 C^T
+//     kDscaleSplit the D(omega) scaling of eq. response-mat on (re, im)
+//                  column pairs, written back as split bf16 for the next GEMM
+// Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
+// records an error code, stops issuing work and still frees its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace tddft {
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;    // 16 KB
+constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK * 2;    // 16 KB
+constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr size_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;      // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false once kWaitLimitNs has passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
+                                            int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+// K-major operand tile, 128-byte swizzle: rows of 64 bf16 (128 B), 8-row
+// groups 1024 B apart; start address advanced by 32 B per K=16 step.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                 // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   int M, int N, int Kp, int nseg, int4 segs, TcEpilogue ep, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + TC_STAGES * TC_STAGE_BYTES);
+  uint64_t *empty = full + TC_STAGES;
+  uint64_t *tfull = empty + TC_STAGES;
+  uint32_t *tslot = (uint32_t *)(tfull + 1);
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  const int nkb = Kp / TC_BK;
+  const int total = nseg * nkb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(TC_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int it = 0; it < total; ++it) {
+      const int s = it % TC_STAGES;
+      const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {
+        atomicExch(err, 1);
+        abort_flag = 1;
+        break;
+      }
+      if (*(volatile int *)&abort_flag) break;
+      const int g = it / nkb, kb = it % nkb;
+      const int ka = ((g == 0) ? segs.x : (g == 1) ? segs.y : segs.z) & 0xFF;
+      const int kbp = (((g == 0) ? segs.x : (g == 1) ? segs.y : segs.z) >> 8) & 0xFF;
+      uint8_t *sa = smem + s * TC_STAGE_BYTES;
+      uint8_t *sb = sa + TC_A_BYTES;
+      mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+      tma_load_2d(sa, &mapA, &full[s], ka * Kp + kb * TC_BK, m0);
+      tma_load_2d(sb, &mapB, &full[s], kbp * Kp + kb * TC_BK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(TC_BM, TC_BN);
+    bool ok = true;
+    for (int it = 0; it < total; ++it) {
+      const int s = it % TC_STAGES;
+      const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        atomicExch(err, 2);
+        abort_flag = 1;
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES);
+      const uint32_t sb = sa + TC_A_BYTES;
+#pragma unroll
+      for (int k = 0; k < TC_BK / 16; ++k)
+        mma_bf16(tmem, desc_sw128(sa + 32 * k), desc_sw128(sb + 32 * k), idesc,
+                 (it > 0 || k > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    if (ok) mma_commit(tfull);
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
+  bool have = mbar_wait(tfull, 0);
+  if (!have) atomicExch(err, 3);
+  fence_after();
+  // tcgen05.ld is warp-collective: take the decision once per warp
+  have = __all_sync(0xffffffffu, have && !*(volatile int *)&abort_flag);
+  const int m = m0 + warp * 32 + lane;
+  if (have) {
+    for (int j0 = 0; j0 < TC_BN; j0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
+      if (EPI == kStoreF32) {
+        if (m < M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + j0 + j;
+            if (n < N) ep.outF[(int64_t)n * ep.ldo + m] = v[j];
+          }
+        }
+      } else {
+        // (re, im) pairs: columns n (even) and n+1 of the same (slot, E)
+        if (m < ep.rows_out) {
+          const bool live = m < M;
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const int n = n0 + j0 + j;
+            if (n >= N) continue;
+            float re = 0.f, im = 0.f;
+            if (live) {
+              const int pair = n >> 1;
+              const int E = pair % ep.n_occ;
+              const int sl = pair / ep.n_occ;
+              const double delta = ep.energy[ep.n_occ + m] - ep.energy[E];
+              const double w = ep.omega[sl];
+              const double xm = w - delta, xp = w + delta, e2 = ep.eps * ep.eps;
+              const double im2 = 1.0 / (xm * xm + e2), ip2 = 1.0 / (xp * xp + e2);
+              const double dre = ep.occ_value * (xm * im2 - xp * ip2);
+              const double dim = ep.occ_value * ep.eps * (ip2 - im2);
+              re = (float)(dre * v[j] - dim * v[j + 1]);
+              im = (float)(dre * v[j + 1] + dim * v[j]);
+            }
+            __nv_bfloat16 h, l;
+            split_bf16(re, h, l);
+            ep.outB[(int64_t)n * ep.ldo + m] = h;
+            ep.outB[(int64_t)n * ep.ldo + ep.lo_off + m] = l;
+            split_bf16(im, h, l);
+            ep.outB[(int64_t)(n + 1) * ep.ldo + m] = h;
+            ep.outB[(int64_t)(n + 1) * ep.ldo + ep.lo_off + m] = l;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+}  // namespace
+
+// A 2-D bf16 operand [rows][2*Kp] ([hi | lo] planes), boxes of 64 x box_rows.
+cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if (Kp % TC_BK != 0 || ((uintptr_t)base & 15) != 0) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)(2 * Kp), (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(2 * Kp) * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(&op.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  op.rows = rows;
+  op.Kp = Kp;
+  return cudaSuccess;
+}
+
+cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
+                           int epi, const TcEpilogue &ep, int *err) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (A.Kp != B.Kp) return cudaErrorInvalidValue;
+  static bool attr_set[2] = {false, false};
+  dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN);
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  // segments: A_hi B_hi, A_hi B_lo, A_lo B_hi  (low byte: A plane, next byte: B plane)
+  const int4 segs = make_int4(0 | (0 << 8), 0 | (1 << 8), 1 | (0 << 8), 0);
+  if (epi == kStoreF32) {
+    if (!attr_set[0]) {
+      cudaFuncSetAttribute(gemm_tc_kernel<kStoreF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TC_SMEM);
+      attr_set[0] = true;
+    }
+    gemm_tc_kernel<kStoreF32><<<grid, TC_THREADS, TC_SMEM, st>>>(A.map, B.map, M, N, A.Kp, 3, segs,
+                                                                  ep, err);
+  } else {
+    if (!attr_set[1]) {
+      cudaFuncSetAttribute(gemm_tc_kernel<kDscaleSplit>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+      attr_set[1] = true;
+    }
+    gemm_tc_kernel<kDscaleSplit><<<grid, TC_THREADS, TC_SMEM, st>>>(A.map, B.map, M, N, A.Kp, 3,
+                                                                     segs, ep, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tddft
+
+// ---------------------------------------------------------------------------
+// Self-test of the split-bf16 tensor-core GEMM against a float64 product on
+// the same deterministic operands (entries uniform in [-1, 1) from a hash of
+// the index and the seed).
+// ---------------------------------------------------------------------------
+namespace tddft {
+namespace {
+__device__ __forceinline__ double hash_uniform(uint64_t i, uint64_t seed) {
+  uint64_t z = i * 0x9E3779B97F4A7C15ull + seed * 0xD1B54A32D192ED03ull + 0x632BE59BD9B4E019ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+__global__ void st_fill_split(int rows, int K, int Kp, uint64_t seed, double *full,
+                              __nv_bfloat16 *split) {
+  const int64_t total = (int64_t)rows * Kp;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / Kp;
+    const int k = (int)(i % Kp);
+    const double x = (k < K) ? hash_uniform((uint64_t)(r * K + k), seed) : 0.0;
+    if (k < K) full[r * K + k] = x;
+    const __nv_bfloat16 hi = __double2bfloat16(x);
+    split[r * 2 * Kp + k] = hi;
+    split[r * 2 * Kp + Kp + k] = __double2bfloat16(x - (double)__bfloat162float(hi));
+  }
+}
+__global__ void st_ref(int M, int N, int K, const double *A, const double *B, const float *C,
+                       double *err2) {
+  // err2[0] = max |C - ref|, err2[1] = max |ref| (as ordered bit patterns of non-negative doubles)
+  const int64_t total = (int64_t)M * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(i / M), m = (int)(i % M);
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) acc = fma(A[(int64_t)m * K + k], B[(int64_t)n * K + k], acc);
+    const double d = fabs((double)C[(int64_t)n * M + m] - acc);
+    atomicMax((unsigned long long *)&err2[0], __double_as_longlong(d));
+    atomicMax((unsigned long long *)&err2[1], __double_as_longlong(fabs(acc)));
+  }
+}
+}  // namespace
+}  // namespace tddft
+
+extern "C" tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uint64_t seed,
+                                            double *max_rel_err) {
+  using namespace tddft;
+  if (M < 1 || N < 1 || K < 1 || !max_rel_err) return TDDFT_ERR_INVALID_ARG;
+  const int Kp = round_up(K, 64);
+  double *A = nullptr, *B = nullptr, *e2 = nullptr;
+  __nv_bfloat16 *As = nullptr, *Bs = nullptr;
+  float *C = nullptr;
+  int *err = nullptr;
+  tddft_status status = TDDFT_OK;
+  cudaError_t e = cudaMalloc(&A, (size_t)M * K * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&B, (size_t)N * K * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&As, (size_t)M * 2 * Kp * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&Bs, (size_t)N * 2 * Kp * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&C, (size_t)N * M * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&e2, 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  TcOperand *opA = new TcOperand(), *opB = new TcOperand();
+  if (e == cudaSuccess) {
+    cudaMemset(e2, 0, 2 * sizeof(double));
+    cudaMemset(err, 0, sizeof(int));
+    st_fill_split<<<304, 256>>>(M, K, Kp, seed, A, As);
+    st_fill_split<<<304, 256>>>(N, K, Kp, seed + 1, B, Bs);
+    e = make_operand_map(*opA, As, M, Kp, 128);
+    if (e == cudaSuccess) e = make_operand_map(*opB, Bs, N, Kp, 128);
+  }
+  if (e == cudaSuccess) {
+    TcEpilogue ep;
+    ep.outF = C;
+    ep.ldo = M;
+    e = launch_gemm_tc(0, *opA, *opB, M, N, kStoreF32, ep, err);
+  }
+  if (e == cudaSuccess) {
+    st_ref<<<304, 256>>>(M, N, K, A, B, C, e2);
+    e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess) {
+    double h[2];
+    int herr = 0;
+    cudaMemcpy(h, e2, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    *max_rel_err = h[1] > 0 ? h[0] / h[1] : h[0];
+    if (herr) status = TDDFT_ERR_TIMEOUT;
+  } else {
+    status = TDDFT_ERR_CUDA;
+  }
+  delete opA;
+  delete opB;
+  cudaFree(A); cudaFree(B); cudaFree(As); cudaFree(Bs); cudaFree(C); cudaFree(e2); cudaFree(err);
+  return status;
+}

@@ -62,7 +62,8 @@ __device__ void block_sum(double (&v)[NV], double *red /* [NV][NT/32] */) {
 
 struct Gs {
   int m, max_restarts, n_prod;
-  double tol;
+  double tol, inner_tol;
+  double *rho0;
   int *state, *jcur, *cycles, *matvecs, *conv;
   double *bnorm, *resid, *omega;
   double2 *H, *sn, *g;
@@ -73,6 +74,7 @@ struct Gs {
 Gs view(const GmresState &s, int n_prod) {
   Gs v;
   v.m = s.m; v.max_restarts = s.max_restarts; v.n_prod = n_prod; v.tol = s.tol;
+  v.inner_tol = s.inner_tol; v.rho0 = s.rho0;
   v.state = s.state; v.jcur = s.jcur; v.cycles = s.cycles; v.matvecs = s.matvecs; v.conv = s.conv;
   v.bnorm = s.bnorm; v.resid = s.resid; v.omega = s.omega;
   v.H = s.H; v.sn = s.sn; v.g = s.g; v.cs = s.cs; v.V = s.V; v.x = s.x; v.b = s.b; v.act = s.act;
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__r
       G.conv[r] = 0;
       G.resid[r] = 1.0;
       G.g[(int64_t)r * (G.m + 1)] = make_double2(nrm, 0.0);
+      G.rho0[r] = nrm;
     } else {
       G.state[r] = kStateDone;
       G.cycles[r] = 0;
@@ -121,34 +124,53 @@ __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__r
 }
 
 // Ordered list of right-hand sides that are not done (one CTA).
+// With split, right-hand sides in an Arnoldi step go to act and those whose
+// next product is the residual check go to act2.
 __global__ void __launch_bounds__(1024) gmres_select_kernel(const int *__restrict__ state, int n,
-                                                            int *__restrict__ act,
+                                                            int split, int *__restrict__ act,
+                                                            int *__restrict__ act2,
                                                             int *__restrict__ count) {
-  __shared__ int sums[1024];
+  __shared__ int sums[2][1024];
   const int t = threadIdx.x;
   const int chunk = (n + 1023) / 1024;
   const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
-  int c = 0;
-  for (int i = lo; i < hi; ++i) c += state[i] != kStateDone;
-  sums[t] = c;
+  int c1 = 0, c2 = 0;
+  for (int i = lo; i < hi; ++i) {
+    const int st = state[i];
+    if (st == kStateDone) continue;
+    if (split && st == kStateResid) ++c2;
+    else ++c1;
+  }
+  sums[0][t] = c1;
+  sums[1][t] = c2;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {   // inclusive Hillis-Steele scan
-    int v = (t >= off) ? sums[t - off] : 0;
+  for (int off = 1; off < 1024; off <<= 1) {   // inclusive Hillis-Steele scans
+    int v1 = (t >= off) ? sums[0][t - off] : 0;
+    int v2 = (t >= off) ? sums[1][t - off] : 0;
     __syncthreads();
-    sums[t] += v;
+    sums[0][t] += v1;
+    sums[1][t] += v2;
     __syncthreads();
   }
-  int pos = sums[t] - c;
-  for (int i = lo; i < hi; ++i)
-    if (state[i] != kStateDone) act[pos++] = i;
-  if (t == 1023) *count = sums[1023];
+  int p1 = sums[0][t] - c1, p2 = sums[1][t] - c2;
+  for (int i = lo; i < hi; ++i) {
+    const int st = state[i];
+    if (st == kStateDone) continue;
+    if (split && st == kStateResid) act2[p2++] = i;
+    else act[p1++] = i;
+  }
+  if (t == 1023) {
+    count[0] = sums[0][1023];
+    count[1] = sums[1][1023];
+  }
 }
 
 // Operator input of each active right-hand side: v_j (Arnoldi) or x (residual).
-__global__ void __launch_bounds__(NT) gmres_gather_kernel(Gs G, double *__restrict__ Zc,
+__global__ void __launch_bounds__(NT) gmres_gather_kernel(Gs G, const int *__restrict__ list,
+                                                          double *__restrict__ Zc,
                                                           double *__restrict__ slot_omega) {
   const int s = blockIdx.x;
-  const int r = G.act[s];
+  const int r = list[s];
   const int N = G.n_prod;
   const double *src = (G.state[r] == kStateArnoldi)
                           ? G.V + ((int64_t)r * (G.m + 1) + G.jcur[r]) * 2 * N
@@ -158,12 +180,13 @@ __global__ void __launch_bounds__(NT) gmres_gather_kernel(Gs G, double *__restri
   if (threadIdx.x == 0) slot_omega[s] = G.omega[r];
 }
 
-__global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const double *__restrict__ Wout) {
+__global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restrict__ list,
+                                                        const double *__restrict__ Wout) {
   __shared__ double red[16 * (NT / 32)];
   __shared__ double2 hs[257], hp[257], ys[257];
   __shared__ int finish_flag;
   const int s = blockIdx.x;
-  const int r = G.act[s];
+  const int r = list[s];
   const int N = G.n_prod;
   const int m = G.m;
   const int tid = threadIdx.x;
@@ -201,6 +224,7 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const double *__re
         G.jcur[r] = 0;
         G.cycles[r] += 1;
         G.g[(int64_t)r * (m + 1)] = make_double2(rho, 0.0);
+        G.rho0[r] = rho;
       }
     }
     return;
@@ -291,7 +315,10 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const double *__re
     g[j] = make_double2(c * gj.x, c * gj.y);
     for (int i = 0; i <= j; ++i) Hc[i] = hs[i];
     const double est = cabs2(g[j + 1]);
-    const bool fin = (est <= G.tol * G.bnorm[r]) || (j + 1 == m) || !(hn > 0.0);
+    // a cycle ends at the tolerance, at the restart length, on breakdown, or
+    // (refinement forms) once it has reduced its own residual by inner_tol
+    const bool fin = (est <= G.tol * G.bnorm[r]) || (j + 1 == m) || !(hn > 0.0) ||
+                     (est <= G.inner_tol * G.rho0[r]);
     finish_flag = fin ? 1 : 0;
     G.matvecs[r] += 1;
     if (fin) {
@@ -388,22 +415,22 @@ cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState
   return cudaGetLastError();
 }
 
-cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n) {
-  gmres_select_kernel<<<1, 1024, 0, st>>>(gs.state, n, gs.act, gs.count);
+cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split) {
+  gmres_select_kernel<<<1, 1024, 0, st>>>(gs.state, n, split, gs.act, gs.act2, gs.count);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs, int S,
-                                double *Zc, double *slot_omega) {
+cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs,
+                                const int *list, int S, double *Zc, double *slot_omega) {
   if (S <= 0) return cudaSuccess;
-  gmres_gather_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), Zc, slot_omega);
+  gmres_gather_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Zc, slot_omega);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs, int S,
-                              const double *Wout) {
+cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs,
+                              const int *list, int S, const double *Wout) {
   if (S <= 0) return cudaSuccess;
-  gmres_step_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), Wout);
+  gmres_step_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Wout);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,8 @@
 // Nothing here crosses the C boundary (include/tddft.h).
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -86,6 +88,62 @@ cudaError_t launch_interleaved_to_planar(cudaStream_t st, int n_rhs, int n, cons
 cudaError_t launch_planar_to_interleaved(cudaStream_t st, int n_rhs, int n, const double *in,
                                          double *out);
 
+// ---------------------------------------------------------------------------
+// Reduced-precision operator (split bf16 on tcgen05, float32 elsewhere)
+// ---------------------------------------------------------------------------
+enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1 };
+
+// A bf16 operand [rows][2*Kp] ([hi | lo] planes) with its TMA descriptor.
+struct TcOperand {
+  CUtensorMap map;
+  int64_t rows = 0;
+  int Kp = 0;
+};
+
+struct TcEpilogue {
+  float *outF = nullptr;           // kStoreF32: C^T[n][m] at n*ldo + m
+  __nv_bfloat16 *outB = nullptr;   // kDscaleSplit: hi at n*ldo + m, lo at n*ldo + lo_off + m
+  int64_t ldo = 0;
+  int64_t lo_off = 0;
+  int rows_out = 0;                // kDscaleSplit: rows m < rows_out written (zeros past M)
+  const double *energy = nullptr;  // [n_orb]
+  const double *omega = nullptr;   // [S]
+  double eps = 0.0;
+  double occ_value = 0.0;
+  int n_occ = 0;
+};
+
+cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows);
+cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
+                           int epi, const TcEpilogue &ep, int *err);
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct LpWork {
+  int slots = 0;
+  int KpK = 0, Kp1 = 0, Kp2 = 0;   // padded K of the K product, transform 1, transform 2
+  __nv_bfloat16 *Ks = nullptr;     // [n_prod][2 KpK]   K split
+  __nv_bfloat16 *XvTs = nullptr;   // [n_virt][2 Kp1]   X_virt^T split
+  __nv_bfloat16 *Xvs = nullptr;    // [n_orb][2 Kp2]    X_virt split
+  float *Xo32 = nullptr;           // [n_orb][n_occ]
+  float *Vpad32 = nullptr;         // [n_prod][kBlk]
+  __nv_bfloat16 *Zb = nullptr;     // [2S][2 KpK]       operator input, split
+  float *Yt = nullptr;             // [2S][n_prod]      K z
+  float *W = nullptr;              // [2S][n_blocks][kBlk]
+  __nv_bfloat16 *betaT = nullptr;  // [2 S n_occ][2 Kp1], row (s*n_occ+E)*2+p
+  __nv_bfloat16 *aT = nullptr;     // [2 S n_occ][2 Kp2]
+  float *gammaT = nullptr;         // [2 S n_occ][n_orb]
+  double *omega = nullptr;         // [S]
+  int *err = nullptr;              // [1] device-side error code of the GEMM waits
+  TcOperand opK, opXvT, opXv, opZ, opBeta, opA;
+  Timer *timer = nullptr;
+};
+
+cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &lp);
+// Out[c][mu] (float64) = Zin - chi0 K Zin (kA) or chi0 Zin (kChi0), reduced precision.
+cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWork &lp, int S,
+                                     OpMode mode, double eps, const double *Zin, double *Out);
+
 // GMRES state of a group of right-hand sides (one per (omega, direction)).
 struct GmresState {
   int cap = 0;          // right-hand sides allocated
@@ -100,6 +158,8 @@ struct GmresState {
   double *bnorm = nullptr;  // [cap]
   double *resid = nullptr;  // [cap]
   double *omega = nullptr;  // [cap]
+  double *rho0 = nullptr;   // [cap] residual norm at the start of the current cycle
+  double inner_tol = 0.0;   // cycle stops once |g| <= inner_tol * rho0 (refinement forms)
   double2 *H = nullptr;     // [cap][(m+1)*m] column-major
   double *cs = nullptr;     // [cap][m]
   double2 *sn = nullptr;    // [cap][m]
@@ -108,16 +168,19 @@ struct GmresState {
   double *x = nullptr;      // [cap][2][n_prod]
   double *b = nullptr;      // [cap][2][n_prod]
   int *act = nullptr;       // [cap] active right-hand sides, in order
-  int *count = nullptr;     // [1]
+  int *act2 = nullptr;      // [cap] second list (right-hand sides awaiting A x) when split
+  int *count = nullptr;     // [2]
 };
 
 cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
                                const double *Bplanar /*[2n][n_prod]*/);
-cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n);
-cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs, int S,
-                                double *Zc, double *slot_omega);
-cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs, int S,
-                              const double *Wout);
+// split = 0: every live right-hand side in act (count[0]); split = 1: those in
+// an Arnoldi step in act (count[0]), those awaiting A x in act2 (count[1]).
+cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split);
+cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs,
+                                const int *list, int S, double *Zc, double *slot_omega);
+cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs,
+                              const int *list, int S, const double *Wout);
 // Right-hand sides g0..g0+n-1 of a spectrum (g -> omega g/3, direction g%3):
 // Zc rows 2r, 2r+1 = (d_{g%3}, 0), slot and solver frequencies set.
 cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0,

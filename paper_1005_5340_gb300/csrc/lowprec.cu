@@ -1,0 +1,344 @@
+// Reduced-precision application of A(omega) z = z - chi0(omega) (K z)
+// (Sec. 4.1, with chi0 . y by the re-associated steps of Sec. 4.2) used for
+// the inner GMRES iterations of the refinement forms.  The three dense
+// products (K z, X_virt^T beta, X_virt a) run on the tensor cores in split
+// bf16 with float32 accumulation (gemm_tc.cu); the block-sparse vertex
+// contractions run in float32 on the CUDA cores.  Layouts (n = right-hand-side
+// column, complex planes interleaved per occupied state):
+//   Zb     [2S][2 KpK]          z split, row c = 2 s + p
+//   Yt     [2S][n_prod]         K z
+//   W      [2S][nb][16x16]      sum_nu y^nu V_nu per block
+//   betaT  [2 S n_occ][2 Kp1]   beta^T split, row (s n_occ + E) 2 + p
+//   aT     [2 S n_occ][2 Kp2]   (D . X_virt^T beta)^T split
+//   gammaT [2 S n_occ][n_orb]   (X_virt a)^T
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace tddft {
+namespace {
+
+int grid_for(int64_t total, int threads) {
+  int64_t g = (total + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+struct Scope {
+  Timer *t;
+  cudaStream_t st;
+  int cls;
+  double flops;
+  cudaEvent_t a = nullptr;
+  Scope(Timer *t_, cudaStream_t st_, int cls_, double fl) : t(t_), st(st_), cls(cls_), flops(fl) {
+    if (t && t->on) t->begin(st, cls, &a);
+  }
+  ~Scope() {
+    if (t && t->on) t->end(st, cls, a, flops);
+  }
+};
+
+// dst[r][k] = hi(src[r, k]), dst[r][Kp + k] = lo(src[r, k]); zero for k >= cols.
+__global__ void split_rows_kernel(const double *__restrict__ src, int64_t rs, int64_t cs, int rows,
+                                  int cols, int Kp, __nv_bfloat16 *__restrict__ dst) {
+  const int64_t total = (int64_t)rows * Kp;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / Kp;
+    const int k = (int)(i % Kp);
+    double x = (k < cols) ? src[r * rs + (int64_t)k * cs] : 0.0;
+    const __nv_bfloat16 hi = __double2bfloat16(x);
+    const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+    dst[r * 2 * Kp + k] = hi;
+    dst[r * 2 * Kp + Kp + k] = lo;
+  }
+}
+
+__global__ void to_f32_kernel(const double *__restrict__ src, int64_t n, float *__restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+template <class TIn>
+__global__ void __launch_bounds__(256) lp_vertex(int nb, int ncols, int n_prod,
+                                                 const int *__restrict__ blk_ptr,
+                                                 const int *__restrict__ blk_prod,
+                                                 const float *__restrict__ Vpad,
+                                                 const TIn *__restrict__ Y, float *__restrict__ W) {
+  constexpr int COLS = 8;
+  __shared__ float ys[32][COLS];
+  const int k = blockIdx.x;
+  const int c0 = blockIdx.y * COLS;
+  const int t = threadIdx.x;
+  const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
+  float acc[COLS];
+#pragma unroll
+  for (int c = 0; c < COLS; ++c) acc[c] = 0.f;
+  for (int q0 = p0; q0 < p1; q0 += 32) {
+    __syncthreads();
+    {
+      const int pp = t / COLS, c = t % COLS;
+      const int q = q0 + pp;
+      ys[pp][c] = (q < p1 && c0 + c < ncols) ? (float)Y[(int64_t)(c0 + c) * n_prod + blk_prod[q]] : 0.f;
+    }
+    __syncthreads();
+    const int qn = min(32, p1 - q0);
+    for (int pp = 0; pp < qn; ++pp) {
+      const float v = Vpad[(int64_t)(q0 + pp) * kBlk + t];
+#pragma unroll
+      for (int c = 0; c < COLS; ++c) acc[c] = fmaf(ys[pp][c], v, acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < COLS; ++c)
+    if (c0 + c < ncols) W[((int64_t)(c0 + c) * nb + k) * kBlk + t] = acc[c];
+}
+
+// beta^T (split bf16) for atom A and 4 columns (2 slots); thread = occupied state E.
+__global__ void __launch_bounds__(128) lp_beta(int ncols, int nb, int n_occ, int Kp1,
+                                               const int *__restrict__ aoff,
+                                               const int *__restrict__ adj_ptr,
+                                               const int4 *__restrict__ adj,
+                                               const float *__restrict__ W,
+                                               const float *__restrict__ Xo,
+                                               __nv_bfloat16 *__restrict__ betaT) {
+  constexpr int COLS = 4;
+  __shared__ float Ws[COLS][kMaxOrb][kMaxOrb + 1];
+  const int A = blockIdx.x;
+  const int c0 = blockIdx.y * COLS;
+  const int aoA = aoff[A], nA = aoff[A + 1] - aoA;
+  const int e0 = adj_ptr[A], e1 = adj_ptr[A + 1];
+  for (int E0 = 0; E0 < n_occ; E0 += 128) {
+    const int E = E0 + threadIdx.x;
+    float acc[COLS][kMaxOrb];
+#pragma unroll
+    for (int c = 0; c < COLS; ++c)
+#pragma unroll
+      for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = 0.f;
+    for (int e = e0; e < e1; ++e) {
+      const int4 ent = adj[e];
+      const int k = ent.x, B = ent.y, tr = ent.z;
+      const int bo = aoff[B], nB = aoff[B + 1] - bo;
+      __syncthreads();
+      for (int i = threadIdx.x; i < COLS * kBlk; i += 128) {
+        const int c = i / kBlk, ab = i % kBlk, a = ab / kMaxOrb, b = ab % kMaxOrb;
+        float v = 0.f;
+        if (c0 + c < ncols)
+          v = tr ? W[((int64_t)(c0 + c) * nb + k) * kBlk + b * kMaxOrb + a]
+                 : W[((int64_t)(c0 + c) * nb + k) * kBlk + a * kMaxOrb + b];
+        Ws[c][a][b] = v;
+      }
+      __syncthreads();
+      if (E < n_occ) {
+        for (int b = 0; b < nB; ++b) {
+          const float xv = Xo[(int64_t)(bo + b) * n_occ + E];
+#pragma unroll
+          for (int c = 0; c < COLS; ++c)
+#pragma unroll
+            for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = fmaf(Ws[c][a][b], xv, acc[c][a]);
+        }
+      }
+    }
+    if (E < n_occ) {
+#pragma unroll
+      for (int c = 0; c < COLS; ++c) {
+        const int cc = c0 + c;
+        if (cc >= ncols) continue;
+        const int64_t row = ((int64_t)(cc >> 1) * n_occ + E) * 2 + (cc & 1);
+        __nv_bfloat16 *dst = betaT + row * 2 * Kp1 + aoA;
+#pragma unroll
+        for (int a = 0; a < kMaxOrb; ++a) {
+          if (a < nA) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(acc[c][a]);
+            dst[a] = hi;
+            dst[Kp1 + a] = __float2bfloat16_rn(acc[c][a] - __bfloat162float(hi));
+          }
+        }
+      }
+    }
+  }
+}
+
+// Step 5 on gamma^T; Out (float64) = Zin - n or n.
+__global__ void __launch_bounds__(256) lp_sddmm(int ncols, int n_occ, int n_prod, int n_orb,
+                                                const int *__restrict__ aoff,
+                                                const int2 *__restrict__ blk_atoms,
+                                                const int *__restrict__ blk_ptr,
+                                                const int *__restrict__ blk_prod,
+                                                const float *__restrict__ Vpad,
+                                                const float *__restrict__ Xo,
+                                                const float *__restrict__ gammaT,
+                                                const double *__restrict__ Zin, int subtract,
+                                                double *__restrict__ Out) {
+  constexpr int COLS = 4, EC = 32;
+  __shared__ float XA[kMaxOrb][EC + 1], XB[kMaxOrb][EC + 1];
+  __shared__ float gA[COLS][kMaxOrb][EC + 1], gB[COLS][kMaxOrb][EC + 1];
+  __shared__ float Gs[COLS][kBlk];
+  const int k = blockIdx.x;
+  const int c0 = blockIdx.y * COLS;
+  const int t = threadIdx.x;
+  const int a = t >> 4, b = t & 15;
+  const int2 AB = blk_atoms[k];
+  const int aoA = aoff[AB.x], nA = aoff[AB.x + 1] - aoA;
+  const int aoB = aoff[AB.y], nB = aoff[AB.y + 1] - aoB;
+  const bool bilocal = AB.x != AB.y;
+  float G[COLS];
+#pragma unroll
+  for (int c = 0; c < COLS; ++c) G[c] = 0.f;
+  for (int E0 = 0; E0 < n_occ; E0 += EC) {
+    __syncthreads();
+    for (int i = t; i < kMaxOrb * EC; i += 256) {
+      const int r = i / EC, e = i % EC, E = E0 + e;
+      XA[r][e] = (r < nA && E < n_occ) ? Xo[(int64_t)(aoA + r) * n_occ + E] : 0.f;
+      XB[r][e] = (r < nB && E < n_occ) ? Xo[(int64_t)(aoB + r) * n_occ + E] : 0.f;
+    }
+    for (int i = t; i < COLS * EC * kMaxOrb; i += 256) {
+      const int c = i / (EC * kMaxOrb), rem = i % (EC * kMaxOrb);
+      const int e = rem / kMaxOrb, r = rem % kMaxOrb;
+      const int E = E0 + e, cc = c0 + c;
+      const bool ok = cc < ncols && E < n_occ;
+      const int64_t row = ((int64_t)(cc >> 1) * n_occ + E) * 2 + (cc & 1);
+      gA[c][r][e] = (ok && r < nA) ? gammaT[row * n_orb + aoA + r] : 0.f;
+      gB[c][r][e] = (ok && r < nB) ? gammaT[row * n_orb + aoB + r] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int e = 0; e < EC; ++e) {
+      const float xa = XA[a][e], xb = XB[b][e];
+#pragma unroll
+      for (int c = 0; c < COLS; ++c) {
+        G[c] = fmaf(xa, gB[c][b][e], G[c]);
+        if (bilocal) G[c] = fmaf(gA[c][a][e], xb, G[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < COLS; ++c) Gs[c][t] = G[c];
+  __syncthreads();
+  const int warp = t >> 5, lane = t & 31;
+  const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
+  for (int q = p0 + warp; q < p1; q += 8) {
+    float part[COLS];
+#pragma unroll
+    for (int c = 0; c < COLS; ++c) part[c] = 0.f;
+    for (int i = lane; i < kBlk; i += 32) {
+      const float v = Vpad[(int64_t)q * kBlk + i];
+#pragma unroll
+      for (int c = 0; c < COLS; ++c) part[c] = fmaf(v, Gs[c][i], part[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < COLS; ++c) {
+      float v = part[c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      part[c] = v;
+    }
+    if (lane == 0) {
+      const int mu = blk_prod[q];
+#pragma unroll
+      for (int c = 0; c < COLS; ++c) {
+        if (c0 + c >= ncols) continue;
+        const int64_t o = (int64_t)(c0 + c) * n_prod + mu;
+        Out[o] = subtract ? Zin[o] - (double)part[c] : (double)part[c];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
+  const int g = 152 * 8;
+  split_rows_kernel<<<g, 256, 0, st>>>(sys.K, sys.n_prod, 1, sys.n_prod, sys.n_prod, lp.KpK, lp.Ks);
+  split_rows_kernel<<<g, 256, 0, st>>>(sys.XvT, sys.n_orb, 1, sys.n_virt, sys.n_orb, lp.Kp1, lp.XvTs);
+  split_rows_kernel<<<g, 256, 0, st>>>(sys.Xv, sys.n_virt, 1, sys.n_orb, sys.n_virt, lp.Kp2, lp.Xvs);
+  to_f32_kernel<<<g, 256, 0, st>>>(sys.Xo, (int64_t)sys.n_orb * sys.n_occ, lp.Xo32);
+  to_f32_kernel<<<g, 256, 0, st>>>(sys.Vpad, (int64_t)sys.n_prod * kBlk, lp.Vpad32);
+  const size_t rows = (size_t)2 * lp.slots * sys.n_occ;
+  cudaMemsetAsync(lp.Zb, 0, (size_t)2 * lp.slots * 2 * lp.KpK * sizeof(__nv_bfloat16), st);
+  cudaMemsetAsync(lp.betaT, 0, rows * 2 * lp.Kp1 * sizeof(__nv_bfloat16), st);
+  cudaMemsetAsync(lp.aT, 0, rows * 2 * lp.Kp2 * sizeof(__nv_bfloat16), st);
+  cudaMemsetAsync(lp.err, 0, sizeof(int), st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWork &lp, int S,
+                                     OpMode mode, double eps, const double *Zin, double *Out) {
+  if (S <= 0) return cudaSuccess;
+  if (S > lp.slots || mode == kKernel) return cudaErrorInvalidValue;
+  const int ncols = 2 * S;
+  const int np = sys.n_prod;
+  cudaError_t err;
+  const int64_t N1 = (int64_t)ncols * sys.n_occ;
+  if (N1 > INT32_MAX) return cudaErrorInvalidValue;
+  TcEpilogue ep;
+  if (mode == kA) {
+    {
+      Scope sc(lp.timer, st, kcMisc, 0.0);
+      split_rows_kernel<<<grid_for((int64_t)ncols * lp.KpK, 256), 256, 0, st>>>(
+          Zin, np, 1, ncols, np, lp.KpK, lp.Zb);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    {
+      Scope sc(lp.timer, st, kcGemmK, 2.0 * ncols * (double)np * np);
+      ep.outF = lp.Yt;
+      ep.ldo = np;
+      err = launch_gemm_tc(st, lp.opK, lp.opZ, np, ncols, kStoreF32, ep, lp.err);
+      if (err != cudaSuccess) return err;
+    }
+  }
+  {
+    Scope sc(lp.timer, st, kcVertex, 2.0 * ncols * (double)kBlk * np);
+    dim3 grid(sys.n_blocks, (ncols + 7) / 8);
+    if (mode == kA)
+      lp_vertex<float><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
+                                             lp.Vpad32, lp.Yt, lp.W);
+    else
+      lp_vertex<double><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
+                                              lp.Vpad32, Zin, lp.W);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  {
+    Scope sc(lp.timer, st, kcBeta, 0.0);
+    dim3 grid(sys.n_atoms, (ncols + 3) / 4);
+    lp_beta<<<grid, 128, 0, st>>>(ncols, sys.n_blocks, sys.n_occ, lp.Kp1, sys.aoff, sys.adj_ptr,
+                                  sys.adj, lp.W, lp.Xo32, lp.betaT);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)N1;
+  {
+    Scope sc(lp.timer, st, kcGemmT1, tflops);
+    TcEpilogue e1;
+    e1.outB = lp.aT;
+    e1.ldo = 2 * (int64_t)lp.Kp2;
+    e1.lo_off = lp.Kp2;
+    e1.rows_out = lp.Kp2;
+    e1.energy = sys.energy;
+    e1.omega = lp.omega;
+    e1.eps = eps;
+    e1.occ_value = sys.occ_value;
+    e1.n_occ = sys.n_occ;
+    err = launch_gemm_tc(st, lp.opXvT, lp.opBeta, sys.n_virt, (int)N1, kDscaleSplit, e1, lp.err);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(lp.timer, st, kcGemmT2, tflops);
+    TcEpilogue e2;
+    e2.outF = lp.gammaT;
+    e2.ldo = sys.n_orb;
+    err = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kStoreF32, e2, lp.err);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(lp.timer, st, kcSddmm, 0.0);
+    dim3 grid(sys.n_blocks, (ncols + 3) / 4);
+    lp_sddmm<<<grid, 256, 0, st>>>(ncols, sys.n_occ, np, sys.n_orb, sys.aoff, sys.blk_atoms,
+                                   sys.blk_ptr, sys.blk_prod, lp.Vpad32, lp.Xo32, lp.gammaT, Zin,
+                                   mode == kA ? 1 : 0, Out);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace tddft

@@ -15,6 +15,8 @@ using namespace tddft;
 struct tddft_ctx {
   DevSystem sys;
   OpWork wk;
+  LpWork lp;
+  bool lowprec = false;
   GmresState gs;
   Timer timer;
   tddft_options opts{};
@@ -233,8 +235,10 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   if (!out) return fail(nullptr, TDDFT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!o) return fail(nullptr, TDDFT_ERR_INVALID_ARG, "options are NULL");
-  if (o->prec != TDDFT_PREC_FP64)
+  if (o->prec != TDDFT_PREC_FP64 && o->prec != TDDFT_PREC_BF16X3_IR)
     return fail(nullptr, TDDFT_ERR_UNSUPPORTED, "unknown precision");
+  if (o->prec != TDDFT_PREC_FP64 && !(o->inner_tol > 0.0 && o->inner_tol < 1.0))
+    return fail(nullptr, TDDFT_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
   if (o->restart < 1 || o->restart > 256 || o->max_restarts < 1 || !(o->tol > 0.0) ||
       !std::isfinite(o->tol) || o->batch < 1)
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "bad options (restart 1..256, max_restarts >= 1, tol > 0, batch >= 1)");
@@ -346,9 +350,42 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   AL(g.bnorm, S); AL(g.resid, S); AL(g.omega, S);
   AL(g.H, S * (m + 1) * m); AL(g.cs, S * m); AL(g.sn, S * m); AL(g.g, S * (m + 1));
   AL(g.V, S * (m + 1) * 2 * np); AL(g.x, S * 2 * np); AL(g.b, S * 2 * np);
-  AL(g.act, S); AL(g.count, 1);
+  AL(g.act, S); AL(g.act2, S); AL(g.count, 2); AL(g.rho0, S);
+  g.inner_tol = 0.0;
+  c->lowprec = o->prec == TDDFT_PREC_BF16X3_IR;
+  if (c->lowprec) {
+    g.inner_tol = o->inner_tol;
+    LpWork &L = c->lp;
+    L.slots = (int)S;
+    L.KpK = round_up(np, 64);
+    L.Kp1 = round_up(no, 64);
+    L.Kp2 = round_up(nv, 64);
+    L.timer = &c->timer;
+    const size_t rows1 = 2 * S * (size_t)nocc;
+    AL(L.Ks, (size_t)np * 2 * L.KpK);
+    AL(L.XvTs, (size_t)nv * 2 * L.Kp1);
+    AL(L.Xvs, (size_t)no * 2 * L.Kp2);
+    AL(L.Xo32, (size_t)no * nocc);
+    AL(L.Vpad32, (size_t)np * kBlk);
+    AL(L.Zb, 2 * S * 2 * (size_t)L.KpK);
+    AL(L.Yt, 2 * S * (size_t)np);
+    AL(L.W, 2 * S * (size_t)d.n_blocks * kBlk);
+    AL(L.betaT, rows1 * 2 * L.Kp1);
+    AL(L.aT, rows1 * 2 * L.Kp2);
+    AL(L.gammaT, rows1 * no);
+    AL(L.omega, S);
+    AL(L.err, 1);
+    if (e == cudaSuccess) e = make_operand_map(L.opK, L.Ks, np, L.KpK, 128);
+    if (e == cudaSuccess) e = make_operand_map(L.opXvT, L.XvTs, nv, L.Kp1, 128);
+    if (e == cudaSuccess) e = make_operand_map(L.opXv, L.Xvs, no, L.Kp2, 128);
+    if (e == cudaSuccess) e = make_operand_map(L.opZ, L.Zb, 2 * (int64_t)S, L.KpK, 128);
+    if (e == cudaSuccess) e = make_operand_map(L.opBeta, L.betaT, (int64_t)rows1, L.Kp1, 128);
+    if (e == cudaSuccess) e = make_operand_map(L.opA, L.aT, (int64_t)rows1, L.Kp2, 128);
+    if (e == cudaSuccess) e = lp_prepare_constants(c->st, d, L);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  }
 #undef AL
-  if (e == cudaSuccess) e = cudaMallocHost(&c->h_count, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_count, 2 * sizeof(int));
   if (e != cudaSuccess) {
     std::string m2 = std::string("device allocation/upload failed: ") + cudaGetErrorString(e);
     release(c);
@@ -380,6 +417,8 @@ tddft_status tddft_sizes(const tddft_ctx *c, int32_t *n_orb, int32_t *n_occ, int
   return TDDFT_OK;
 }
 
+static tddft_status check_device_error(tddft_ctx *c);
+
 static tddft_status boundary_apply(tddft_ctx *c, OpMode mode, int32_t n_rhs, const double *omega,
                                    double eps, const double *z, double *out, int32_t flags) {
   if (!c) return TDDFT_ERR_INVALID_ARG;
@@ -405,12 +444,31 @@ static tddft_status boundary_apply(tddft_ctx *c, OpMode mode, int32_t n_rhs, con
     zin = c->stage;
   }
   CUDA_TRY(c, launch_interleaved_to_planar(st, n_rhs, np, zin, c->Zc));
-  CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, n_rhs, mode, eps, c->Zc, c->Wout));
+  if (c->lowprec && mode != kKernel) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->lp.omega, c->wk.omega, n_rhs * sizeof(double),
+                                cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(c, launch_apply_operator_lp(st, c->sys, c->lp, n_rhs, mode, eps, c->Zc, c->Wout));
+  } else {
+    CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, n_rhs, mode, eps, c->Zc, c->Wout));
+  }
   CUDA_TRY(c, launch_planar_to_interleaved(st, n_rhs, np, c->Wout, dev ? out : c->stage));
   if (!dev) {
     CUDA_TRY(c, cudaMemcpyAsync(out, c->stage, bytes, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
     c->timer.resolve();
+    return check_device_error(c);
+  }
+  return TDDFT_OK;
+}
+
+static tddft_status check_device_error(tddft_ctx *c) {
+  if (!c->lowprec) return TDDFT_OK;
+  int h = 0;
+  CUDA_TRY(c, cudaMemcpy(&h, c->lp.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    cudaMemset(c->lp.err, 0, sizeof(int));
+    return fail(c, TDDFT_ERR_TIMEOUT,
+                "a tensor-core GEMM wait gave up (code " + std::to_string(h) + ")");
   }
   return TDDFT_OK;
 }
@@ -465,26 +523,50 @@ tddft_status tddft_polarizability(tddft_ctx *c, int32_t n_omega, const double *o
     CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, n, kChi0, eps, c->Zc, c->Wout));
     CUDA_TRY(c, launch_gmres_start(st, c->sys, g, n, c->Wout));
     long it = 0;
+    const int split = c->lowprec ? 1 : 0;
     for (;; ++it) {
       if (it > max_iter)
         return fail(c, TDDFT_ERR_TIMEOUT, "GMRES driver exceeded its iteration bound");
       {
         TimedLaunch tl(c->timer, st, kcGmresSelect);
-        CUDA_TRY(c, launch_gmres_select(st, g, n));
+        CUDA_TRY(c, launch_gmres_select(st, g, n, split));
       }
-      CUDA_TRY(c, cudaMemcpyAsync(c->h_count, g.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(c, cudaMemcpyAsync(c->h_count, g.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
       CUDA_TRY(c, cudaStreamSynchronize(st));
-      const int cnt = *c->h_count;
-      if (cnt <= 0) break;
-      {
-        TimedLaunch tl(c->timer, st, kcGmresGather);
-        CUDA_TRY(c, launch_gmres_gather(st, c->sys, g, cnt, c->Zc, c->wk.omega));
+      const int cntA = c->h_count[0], cntB = c->h_count[1];
+      if (cntA <= 0 && cntB <= 0) break;
+      if (cntA > 0) {
+        // Arnoldi steps (reduced precision in the refinement forms)
+        {
+          TimedLaunch tl(c->timer, st, kcGmresGather);
+          CUDA_TRY(c, launch_gmres_gather(st, c->sys, g, g.act, cntA, c->Zc,
+                                          split ? c->lp.omega : c->wk.omega));
+        }
+        if (split)
+          CUDA_TRY(c, launch_apply_operator_lp(st, c->sys, c->lp, cntA, kA, eps, c->Zc, c->Wout));
+        else
+          CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, cntA, kA, eps, c->Zc, c->Wout));
+        {
+          TimedLaunch tl(c->timer, st, kcGmresStep);
+          CUDA_TRY(c, launch_gmres_step(st, c->sys, g, g.act, cntA, c->Wout));
+        }
       }
-      CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, cnt, kA, eps, c->Zc, c->Wout));
-      {
-        TimedLaunch tl(c->timer, st, kcGmresStep);
-        CUDA_TRY(c, launch_gmres_step(st, c->sys, g, cnt, c->Wout));
+      if (cntB > 0) {
+        // float64 residuals that end a refinement cycle
+        {
+          TimedLaunch tl(c->timer, st, kcGmresGather);
+          CUDA_TRY(c, launch_gmres_gather(st, c->sys, g, g.act2, cntB, c->Zc, c->wk.omega));
+        }
+        CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, cntB, kA, eps, c->Zc, c->Wout));
+        {
+          TimedLaunch tl(c->timer, st, kcGmresStep);
+          CUDA_TRY(c, launch_gmres_step(st, c->sys, g, g.act2, cntB, c->Wout));
+        }
       }
+    }
+    {
+      tddft_status se = check_device_error(c);
+      if (se != TDDFT_OK) return se;
     }
     CUDA_TRY(c, launch_polarization(st, c->sys, g, n, g0, d_P));
     CUDA_TRY(c, cudaMemcpyAsync(h_mv.data(), g.matvecs, n * sizeof(int), cudaMemcpyDeviceToHost, st));

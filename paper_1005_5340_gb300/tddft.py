@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_SHAPE, ERR_NOMEM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIME
 STATUS_NAMES = ["OK", "INVALID_ARG", "SHAPE", "NOMEM", "CUDA", "NOT_CONVERGED", "TIMEOUT",
                 "UNSUPPORTED"]
 DEVICE_PTRS = 1
-PREC = {"fp64": 0}
+PREC = {"fp64": 0, "bf16x3": 2}
 
 
 class TddftError(RuntimeError):
@@ -41,7 +41,8 @@ class _System(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("batch", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("batch", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("inner_tol", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -68,6 +69,8 @@ SIGNATURES = {
     "tddft_timing_count": (ctypes.c_int32, [_P]),
     "tddft_timing_get": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
                                         _P, _P, _P]),
+    "tddft_selftest_gemm": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "tddft_last_error": (ctypes.c_char_p, [_P]),
     "tddft_destroy": (None, [_P]),
 }
@@ -104,7 +107,7 @@ class Context:
     """One molecule resident on the GPU (tddft_create .. tddft_destroy)."""
 
     def __init__(self, system, *, restart: int = 40, max_restarts: int = 200, tol: float = 1e-6,
-                 batch: int = 64, prec: str = "fp64", stream=None):
+                 batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4, stream=None):
         lib = load_library()
         self._lib = lib
         keep = dict(
@@ -121,7 +124,8 @@ class Context:
         if stream is None:
             stream = _current_stream()
         self.stream_handle = stream
-        o = _Options(PREC[prec], restart, max_restarts, tol, batch, stream or 0)
+        o = _Options(PREC[prec], restart, max_restarts, tol, batch, stream or 0, inner_tol)
+        self.prec = prec
         h = ctypes.c_void_p()
         st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
         if st != OK:
@@ -237,6 +241,16 @@ class Context:
                                                    ctypes.byref(ms), ctypes.byref(fl)))
             res[name.value.decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value)
         return res
+
+
+def selftest_gemm(M: int, N: int, K: int, seed: int = 1) -> float:
+    """Max relative error of the split-bf16 tensor-core GEMM against float64."""
+    lib = load_library()
+    err = ctypes.c_double()
+    st = lib.tddft_selftest_gemm(M, N, K, seed, ctypes.byref(err))
+    if st != OK:
+        raise TddftError(st, "tensor-core GEMM self-test failed")
+    return err.value
 
 
 def _current_stream():

@@ -41,7 +41,7 @@ def _create(sysm, **opt):
                       keep["pa"].ctypes.data, keep["voff"].ctypes.data, keep["v"].ctypes.data,
                       keep["K"].ctypes.data, keep["d"].ctypes.data)
     o = tddft._Options(opt.get("prec", 0), opt.get("restart", 10), opt.get("max_restarts", 5),
-                       opt.get("tol", 1e-8), opt.get("batch", 4), None)
+                       opt.get("tol", 1e-8), opt.get("batch", 4), None, opt.get("inner_tol", 1e-4))
     h = ctypes.c_void_p()
     st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
     return st, lib.tddft_last_error(None).decode(), h
@@ -92,6 +92,8 @@ def test_validation_rejects_bad_input_before_device_work(lib):
     assert _bad(lambda s: None, tol=-1.0)[0] == tddft.ERR_INVALID_ARG
     assert _bad(lambda s: None, batch=0)[0] == tddft.ERR_INVALID_ARG
     assert _bad(lambda s: None, prec=9)[0] == tddft.ERR_UNSUPPORTED
+    assert _bad(lambda s: None, prec=2, inner_tol=0.0)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, prec=2, inner_tol=1.5)[0] == tddft.ERR_INVALID_ARG
 
 
 def test_more_than_16_orbitals_per_atom_is_unsupported(lib):

@@ -99,7 +99,8 @@ def test_single_rhs_and_device_pointers(tiny4):
     op = O.StepOperator(s)
     with T().Context(s, batch=3) as ctx:
         host = ctx.chi0_apply(z, [0.4], w["eps"])
-        dev = ctx.chi0_apply(torch.from_numpy(z).cuda(), torch.tensor([0.4]).cuda(), w["eps"])
+        dev = ctx.chi0_apply(torch.from_numpy(z).cuda(),
+                             torch.tensor([0.4], dtype=torch.float64).cuda(), w["eps"])
         torch.cuda.synchronize()
     ref = op.apply(z[0], 0.4, w["eps"])
     assert rel(host[0], ref) < 1e-12
