@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=0,
                    help="omega-points in the CPU-oracle sample (0: one per 3 host cores)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--prec", choices=["fp64", "bf16x3"], default="fp64")
+    p.add_argument("--inner-tol", type=float, default=1e-4)
     return p.parse_args()
 
 
@@ -218,7 +220,8 @@ def run_ours(args):
     groups = omega_schedule(omega.size, rank, world, args.omega_per_step)
     per_step = len(groups[0])
     ctx = tddft.Context(s, batch=3 * per_step, restart=w["restart"], tol=w["tol"],
-                        max_restarts=200, stream=stream.cuda_stream)
+                        max_restarts=200, stream=stream.cuda_stream, prec=args.prec,
+                        inner_tol=args.inner_tol)
     dev_groups = [torch.tensor(omega[g], dtype=torch.float64, device=dev) for g in groups]
 
     def step(i):
