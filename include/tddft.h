@@ -149,6 +149,32 @@ tddft_status tddft_create(const tddft_system *sys, const tddft_options *opts, td
 tddft_status tddft_chi0_apply(tddft_ctx *ctx, int32_t n_rhs, const double *omega, double eps,
                               const double *z, double *out, int32_t flags);
 
+/*
+ * The float64 product of tddft_chi0_apply, for callers that cannot allocate
+ * device memory when they need it -- for example code whose device memory is
+ * entirely owned by another allocator, or that runs where a cudaMalloc would
+ * be refused.  The paper has no counterpart: this is a deployment variant.
+ *
+ * It allocates nothing and does not use the context's workspace: every
+ * intermediate lives in a 16 MiB block that the library reserves as a static
+ * device array on each GPU that loads it (held until the process exits).
+ * The context supplies only the molecule uploaded by tddft_create.
+ *  - z, omega, out: DEVICE pointers (flags must include TDDFT_DEVICE_PTRS),
+ *    same layouts as tddft_chi0_apply; float64 whatever the context's prec.
+ *  - Scratch needed, in doubles, each term rounded up to a multiple of 32:
+ *    4 n_rhs n_prod + 2 n_rhs n_blocks 256 + 2 n_rhs n_occ (2 n_orb + n_virt)
+ *    + n_rhs; beyond 16 MiB the call returns TDDFT_ERR_SHAPE.
+ *  - The first call on a device looks up the device address of the block
+ *    (cudaGetSymbolAddress, no allocation); make that first call before any
+ *    stream capture.
+ *  - All calls share the one block: calls that overlap on the GPU (other
+ *    streams, other threads, other contexts) race and corrupt each other.
+ *    Nothing in the block needs clearing between calls.
+ *  - Asynchronous on the context's stream.
+ */
+tddft_status tddft_chi0_apply_noalloc(tddft_ctx *ctx, int32_t n_rhs, const double *omega,
+                                      double eps, const double *z, double *out, int32_t flags);
+
 /* out_r = K . z_r (the precomputed kernel of Sec. 4.1); same layout rules. */
 tddft_status tddft_kernel_apply(tddft_ctx *ctx, int32_t n_rhs, const double *z, double *out,
                                 int32_t flags);

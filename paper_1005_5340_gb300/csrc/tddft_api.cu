@@ -617,3 +617,10 @@ tddft_status tddft_timing_get(tddft_ctx *c, int32_t i, const char **name, int32_
 }
 
 }  // extern "C"
+
+namespace tddft {
+// Accessors for entry points defined in other translation units.
+const DevSystem *ctx_system(const tddft_ctx *c) { return &c->sys; }
+cudaStream_t ctx_stream(const tddft_ctx *c) { return c->st; }
+void ctx_set_error(tddft_ctx *c, const char *msg) { c->err = msg; }
+}  // namespace tddft

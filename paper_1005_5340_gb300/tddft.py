@@ -59,6 +59,8 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_void_p)]),
     "tddft_chi0_apply": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
                                         ctypes.c_int32]),
+    "tddft_chi0_apply_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
+                                                ctypes.c_int32]),
     "tddft_kernel_apply": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
     "tddft_apply_A": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
                                      ctypes.c_int32]),
@@ -190,6 +192,19 @@ class Context:
     def chi0_apply(self, z, omega, eps):
         """chi0(omega_r) z_r for each row r of z (n_rhs x n_prod complex)."""
         return self._apply(self._lib.tddft_chi0_apply, z, omega, eps, True)
+
+    def chi0_apply_noalloc(self, z, omega, eps):
+        """chi0(omega_r) z_r in float64 using only the library's reserved
+        device block (no allocation); z and omega must be CUDA tensors."""
+        import torch
+        z = z.to(torch.complex128).contiguous()
+        n = z.shape[0]
+        om = torch.as_tensor(omega, dtype=torch.float64, device=z.device).reshape(-1).contiguous()
+        out = torch.empty_like(z)
+        self._check(self._lib.tddft_chi0_apply_noalloc(
+            self.h, n, om.data_ptr(), float(eps), torch.view_as_real(z).data_ptr(),
+            torch.view_as_real(out).data_ptr(), DEVICE_PTRS))
+        return out
 
     def kernel_apply(self, z):
         """K z_r for each row r of z."""
