@@ -34,6 +34,20 @@ from paper_1005_5340_gb300 import synth  # noqa: E402
 
 METRIC = "omega-points/s at 1e-6 rel. residual"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (DFMA) nominal rate; no tensor path for FP64
+# FP32 CUDA-core peak from unit counts: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# kernel launches behind one timed scope (the others launch one kernel each)
+KERNELS_PER_SCOPE = {"rhs_formation": 7}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
 def parse():
@@ -48,7 +62,9 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=0,
                    help="omega-points in the CPU-oracle sample (0: one per 3 host cores)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--prec", choices=["fp64", "bf16x3"], default="fp64")
+    p.add_argument("--prec", choices=["fp64", "bf16x3"], default="bf16x3")
+    p.add_argument("--no-fp64-compare", action="store_true",
+                   help="skip timing the plain float64 form on one step for the speedup")
     p.add_argument("--inner-tol", type=float, default=1e-4)
     return p.parse_args()
 
@@ -186,12 +202,43 @@ def run_reference(args):
     }), flush=True)
 
 
+FORM_NOTE = {
+    "fp64": "plain float64 GMRES, device resident",
+    "bf16x3": "GMRES cycles with split-bf16 tensor-core products and float32 sparse kernels, "
+              "each cycle closed by a float64 residual (iterative refinement); RHS, basis, "
+              "Givens in float64",
+}
+
+
+def roofline_of(timing: dict, step_ms: float) -> dict:
+    """Roofline entry of the kernel class with the largest device time."""
+    peaks, src = measured_peaks()
+    name, d = max(timing.items(), key=lambda kv: kv[1]["ms"])
+    launches = max(1, d["launches"])
+    per_launch_s = d["ms"] / launches / 1e3
+    achieved = (d["flops"] / launches) / per_launch_s / 1e12 if d["flops"] else None
+    if name.startswith("tc_"):
+        peak = peaks["bf16_tflops_sustained"] / 3.0
+        bound, note = "tensor", (f"split bf16: 3 bf16 products per algorithmic product; peak = "
+                                 f"{src} sustained bf16 {peaks['bf16_tflops_sustained']} / 3")
+    elif name.startswith("f64_"):
+        peak, bound = FP64_NOMINAL_TFLOPS, "alu"
+        note = "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry among the measured peaks)"
+    else:
+        peak, bound = FP32_UNIT_TFLOPS, "alu"
+        note = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
+    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": None, "peak_source": note, "share_of_step": d["ms"] / step_ms,
+            "launches": d["launches"], "ms_per_launch": d["ms"] / launches}
+
+
 def config_of(workload: str, extra: str):
     w = synth.WORKLOADS[workload]
     return {"workload": f"{workload}: {w['n_atoms']} atoms, 13 orbitals/atom, "
                         f"{w['n_omega']} omegas in [0,{w['w_hi']}] Ha x 3 directions, "
                         f"eps {w['eps']} Ha, GMRES({w['restart']}) tol {w['tol']}",
-            "precision": "fp64", "l2": "operator inputs (K alone) larger than L2",
+            "l2": "operator inputs (K alone) larger than L2",
             "note": extra}
 
 
@@ -227,7 +274,7 @@ def run_ours(args):
     def step(i):
         g = dev_groups[i % len(dev_groups)]
         P, info = ctx.polarizability(g, w["eps"])
-        return int(np.sum(info["matvecs"])), int(g.numel())
+        return int(np.sum(info["matvecs"])), int(g.numel()), int(np.sum(info["cycles"]))
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
@@ -244,12 +291,14 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     points = 0
     matvecs = 0
+    cycles = 0
     with torch.cuda.stream(stream):
         e0.record(stream)
         for i in range(args.steps):
-            mv, n = step(args.warmup + i)
+            mv, n, cy = step(args.warmup + i)
             points += n
             matvecs += mv
+            cycles += cy
         e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -291,22 +340,37 @@ def run_ours(args):
         return
 
     # roofline of the dominant kernel class
-    dom = max(timing.items(), key=lambda kv: kv[1]["ms"])
-    name, d = dom
-    launches = max(1, d["launches"])
-    chi_cls = ["vertex_contract", "beta", "gemm_T1", "dscale", "gemm_T2", "sddmm_dot"]
+    roofline = roofline_of(timing, ms)
+    gpu_launches = int(sum(v["launches"] * KERNELS_PER_SCOPE.get(k, 1) for k, v in timing.items()))
+    chi_cls = ["f64_vertex", "f64_beta", "f64_gemm_T1", "f64_dscale", "f64_gemm_T2",
+               "f64_block_dot", "lp_vertex", "lp_beta", "tc_gemm_T1_dscale", "tc_gemm_T2",
+               "lp_block_dot"]
     chi_ms = sum(timing[c]["ms"] for c in chi_cls)
     n_virt = s.n_orb - s.n_occ
-    chi_applies = timing["gemm_T1"]["flops"] / (4.0 * n_virt * s.n_orb * s.n_occ)
+    t1_flops = timing["f64_gemm_T1"]["flops"] + timing["tc_gemm_T1_dscale"]["flops"]
+    chi_applies = t1_flops / (4.0 * n_virt * s.n_orb * s.n_occ)
     chi0_tflops = chi_applies * chi0_flops_per_rhs(s) / (chi_ms / 1e3) / 1e12 if chi_ms else None
-    achieved = (d["flops"] / launches) / (d["ms"] / launches / 1e3) / 1e12 if d["flops"] else None
-    roofline = {"kernel": name, "bound": "alu", "achieved": achieved,
-                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / FP64_NOMINAL_TFLOPS) if achieved else None,
-                "traffic": None,
-                "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in the measured peaks)",
-                "share_of_step": d["ms"] / ms}
-    gpu_launches = int(sum(v["launches"] for v in timing.values()))
+
+    plain = None
+    if args.prec != "fp64" and not args.no_fp64_compare:
+        # the plain float64 form on the same frequency groups (one warm-up, one timed step)
+        ctx64 = tddft.Context(s, batch=3 * per_step, restart=w["restart"], tol=w["tol"],
+                              max_restarts=200, stream=stream.cuda_stream, prec="fp64")
+        with torch.cuda.stream(stream):
+            ctx64.polarizability(dev_groups[0], w["eps"])
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            P64, info64 = ctx64.polarizability(dev_groups[1 % len(dev_groups)], w["eps"])
+            f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        pts64 = int(dev_groups[1 % len(dev_groups)].numel())
+        ctx64.close()
+        rate64 = pts64 / (ms64 / 1e3)
+        plain = {"value": rate64, "unit": "omega-points/s", "steps": 1,
+                 "matvecs_per_rhs": float(np.mean(info64["matvecs"])),
+                 "speedup_of_chosen_form": value / rate64}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -320,12 +384,16 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": "omega-points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f64" if args.prec == "bf16x3" else "f64",
         "data": "synthetic",
-        "config": dict(config_of(args.workload, "plain float64 GMRES, device resident"),
+        "config": dict(config_of(args.workload, FORM_NOTE[args.prec]),
+                       precision=args.prec, inner_tol=args.inner_tol,
                        omega_per_step=per_step, parallelism=f"frequency shards x{world}"),
         "chi0_tflops": chi0_tflops,
         "matvecs_per_rhs": matvecs / max(1, 3 * points),
+        "cycles_per_rhs": cycles / max(1, 3 * points),
+        "plain_fp64": plain,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": gpu_launches,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},

@@ -19,10 +19,17 @@ namespace tddft {
 constexpr int kMaxOrb = 16;
 constexpr int kBlk = kMaxOrb * kMaxOrb;
 
+// Algorithmic flops per real column of the block-sparse kernels (set at create).
+struct SparseFlops {
+  double beta = 0.0;   // 2 n_occ sum over adjacency entries of n_A n_B
+  double dot = 0.0;    // G on the block pattern (twice for bilocal) + <V_mu, G>
+};
+
 // Device copy of one molecule in the layouts the kernels read.
 struct DevSystem {
   int n_atoms = 0, n_orb = 0, n_occ = 0, n_virt = 0, n_prod = 0, n_blocks = 0;
   int n_adj = 0;
+  SparseFlops sf;
   double occ_value = 0.0;      // n_o of every occupied state (n_u = 0)
   int *aoff = nullptr;         // [n_atoms+1]
   double *energy = nullptr;    // [n_orb]
@@ -42,8 +49,12 @@ struct DevSystem {
 // Optional per-kernel timing: CUDA events recorded on the launching stream
 // around every launch of a kernel class; resolved when the host next waits.
 enum KernelClass {
-  kcGemmK = 0, kcVertex, kcBeta, kcGemmT1, kcDscale, kcGemmT2, kcSddmm, kcGmresStep,
-  kcGmresGather, kcGmresSelect, kcMisc, kcCount
+  // float64 operator
+  kcGemmK = 0, kcVertex, kcBeta, kcGemmT1, kcDscale, kcGemmT2, kcSddmm,
+  // reduced-precision operator (tensor-core GEMMs, float32 sparse kernels)
+  kcTcK, kcLpVertex, kcLpBeta, kcTcT1, kcTcT2, kcLpSddmm, kcLpSplit,
+  // solver
+  kcGmresStep, kcGmresGather, kcGmresSelect, kcRhs, kcMisc, kcCount
 };
 const char *kernel_class_name(int k);
 
@@ -83,6 +94,14 @@ cudaError_t launch_gemm_f64(cudaStream_t st, int M, int N, int K, const double *
                             const double *B, int64_t ldb, double *C, int64_t ldc);
 cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S,
                                   OpMode mode, double eps, const double *Zin, double *Out);
+// Right-hand sides b = chi0(omega) d_k of a spectrum group (rows g0..g0+S-1,
+// g -> omega_all[g/3], direction g%3).  W(d_k), beta and X_virt^T beta do not
+// depend on omega, so they are formed once for the three directions (Z3, a3)
+// and only the D(omega) scaling, the second transform and the block dot run
+// per right-hand side.
+cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S, int g0,
+                                 const double *omega_all, double eps, double *Z3, double *a3,
+                                 double *Out);
 cudaError_t launch_interleaved_to_planar(cudaStream_t st, int n_rhs, int n, const double *in,
                                          double *out);
 cudaError_t launch_planar_to_interleaved(cudaStream_t st, int n_rhs, int n, const double *in,

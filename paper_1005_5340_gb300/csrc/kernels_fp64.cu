@@ -340,6 +340,42 @@ __global__ void p2i_kernel(int n_rhs, int n, const double *__restrict__ in, doub
   }
 }
 
+// a[F][(2s, 2s+1)][E] = D_EF(omega_{(g0+s)/3}) * a3[F][(2k, 2k+1)][E], k = (g0+s) % 3
+__global__ void rhs_expand_kernel(int n_virt, int S, int n_occ, int g0, double occ_value,
+                                  const double *__restrict__ energy,
+                                  const double *__restrict__ omega_all, double eps,
+                                  const double *__restrict__ a3, double *__restrict__ a) {
+  const int64_t total = (int64_t)n_virt * S * n_occ;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int E = (int)(idx % n_occ);
+    const int64_t rest = idx / n_occ;
+    const int s = (int)(rest % S);
+    const int F = (int)(rest / S);
+    const int g = g0 + s, k = g % 3;
+    const double delta = energy[n_occ + F] - energy[E];
+    const double w = omega_all[g / 3];
+    const double xm = w - delta, xp = w + delta;
+    const double im2 = 1.0 / (xm * xm + eps * eps), ip2 = 1.0 / (xp * xp + eps * eps);
+    const double d_re = occ_value * (xm * im2 - xp * ip2);
+    const double d_im = occ_value * (-eps * im2 + eps * ip2);
+    const int64_t src = ((int64_t)F * 6 + 2 * k) * n_occ + E;
+    const double re = a3[src], im = a3[src + n_occ];
+    const int64_t dst = ((int64_t)F * 2 * S + 2 * s) * n_occ + E;
+    a[dst] = d_re * re - d_im * im;
+    a[dst + n_occ] = d_re * im + d_im * re;
+  }
+}
+
+// Z3 rows (d_0, 0, d_1, 0, d_2, 0)
+__global__ void dipole_rows_kernel(int n_prod, const double *__restrict__ dip, double *__restrict__ Z3) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n_prod; i += gridDim.x * blockDim.x) {
+    const int k = i / n_prod, mu = i % n_prod;
+    Z3[(2 * k) * n_prod + mu] = dip[(int64_t)k * n_prod + mu];
+    Z3[(2 * k + 1) * n_prod + mu] = 0.0;
+  }
+}
+
 int grid_for(int64_t total, int threads) {
   int64_t g = (total + threads - 1) / threads;
   if (g > 152 * 32) g = 152 * 32;
@@ -384,6 +420,43 @@ struct Scope {
 };
 }  // namespace
 
+cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S, int g0,
+                                 const double *omega_all, double eps, double *Z3, double *a3,
+                                 double *Out) {
+  if (S <= 0) return cudaSuccess;
+  if (S > wk.slots) return cudaErrorInvalidValue;
+  const int np = sys.n_prod;
+  cudaError_t err;
+  Scope sc(wk.timer, st, kcRhs, 0.0);
+  dipole_rows_kernel<<<grid_for(3 * (int64_t)np, 256), 256, 0, st>>>(np, sys.dip, Z3);
+  // omega-independent part for the three directions (6 real columns)
+  {
+    dim3 grid(sys.n_blocks, 1);
+    vertex_contract<<<grid, 256, 0, st>>>(sys.n_blocks, 6, np, sys.blk_ptr, sys.blk_prod, sys.Vpad,
+                                          Z3, wk.W);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    dim3 gb(sys.n_atoms, 2);
+    beta_kernel<<<gb, BT_THREADS, 0, st>>>(6, sys.n_blocks, sys.n_occ, sys.aoff, sys.adj_ptr,
+                                           sys.adj, wk.W, sys.Xo, wk.beta);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  err = launch_gemm_f64(st, sys.n_virt, 6 * sys.n_occ, sys.n_orb, sys.XvT, sys.n_orb, wk.beta,
+                        6 * sys.n_occ, a3, 6 * sys.n_occ);
+  if (err != cudaSuccess) return err;
+  // per right-hand side: D(omega) a_k, X_virt a, block dot
+  const int64_t ncolE = (int64_t)2 * S * sys.n_occ;
+  rhs_expand_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
+      sys.n_virt, S, sys.n_occ, g0, sys.occ_value, sys.energy, omega_all, eps, a3, wk.abuf);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  err = launch_gemm_f64(st, sys.n_orb, (int)ncolE, sys.n_virt, sys.Xv, sys.n_virt, wk.abuf, ncolE,
+                        wk.gamma, ncolE);
+  if (err != cudaSuccess) return err;
+  dim3 grid(sys.n_blocks, (2 * S + SD_COLS - 1) / SD_COLS);
+  sddmm_dot<<<grid, 256, 0, st>>>(2 * S, sys.n_occ, np, sys.aoff, sys.blk_atoms, sys.blk_ptr,
+                                  sys.blk_prod, sys.Vpad, sys.Xo, wk.gamma, nullptr, 0, Out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S,
                                   OpMode mode, double eps, const double *Zin, double *Out) {
   if (S <= 0) return cudaSuccess;
@@ -407,7 +480,7 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   {
-    Scope sc(wk.timer, st, kcBeta, 0.0);
+    Scope sc(wk.timer, st, kcBeta, ncols * sys.sf.beta);
     dim3 grid(sys.n_atoms, (ncols + BT_COLS - 1) / BT_COLS);
     beta_kernel<<<grid, BT_THREADS, 0, st>>>(ncols, sys.n_blocks, sys.n_occ, sys.aoff, sys.adj_ptr,
                                              sys.adj, wk.W, sys.Xo, wk.beta);
@@ -435,7 +508,7 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
     if (err != cudaSuccess) return err;
   }
   {
-    Scope sc(wk.timer, st, kcSddmm, 0.0);
+    Scope sc(wk.timer, st, kcSddmm, ncols * sys.sf.dot);
     dim3 grid(sys.n_blocks, (ncols + SD_COLS - 1) / SD_COLS);
     sddmm_dot<<<grid, 256, 0, st>>>(ncols, sys.n_occ, np, sys.aoff, sys.blk_atoms, sys.blk_ptr,
                                     sys.blk_prod, sys.Vpad, sys.Xo, wk.gamma, Zin,

@@ -275,13 +275,13 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
   TcEpilogue ep;
   if (mode == kA) {
     {
-      Scope sc(lp.timer, st, kcMisc, 0.0);
+      Scope sc(lp.timer, st, kcLpSplit, 0.0);
       split_rows_kernel<<<grid_for((int64_t)ncols * lp.KpK, 256), 256, 0, st>>>(
           Zin, np, 1, ncols, np, lp.KpK, lp.Zb);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     {
-      Scope sc(lp.timer, st, kcGemmK, 2.0 * ncols * (double)np * np);
+      Scope sc(lp.timer, st, kcTcK, 2.0 * ncols * (double)np * np);
       ep.outF = lp.Yt;
       ep.ldo = np;
       err = launch_gemm_tc(st, lp.opK, lp.opZ, np, ncols, kStoreF32, ep, lp.err);
@@ -289,7 +289,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     }
   }
   {
-    Scope sc(lp.timer, st, kcVertex, 2.0 * ncols * (double)kBlk * np);
+    Scope sc(lp.timer, st, kcLpVertex, 2.0 * ncols * (double)kBlk * np);
     dim3 grid(sys.n_blocks, (ncols + 7) / 8);
     if (mode == kA)
       lp_vertex<float><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
@@ -300,7 +300,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   {
-    Scope sc(lp.timer, st, kcBeta, 0.0);
+    Scope sc(lp.timer, st, kcLpBeta, ncols * sys.sf.beta);
     dim3 grid(sys.n_atoms, (ncols + 3) / 4);
     lp_beta<<<grid, 128, 0, st>>>(ncols, sys.n_blocks, sys.n_occ, lp.Kp1, sys.aoff, sys.adj_ptr,
                                   sys.adj, lp.W, lp.Xo32, lp.betaT);
@@ -308,7 +308,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
   }
   const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)N1;
   {
-    Scope sc(lp.timer, st, kcGemmT1, tflops);
+    Scope sc(lp.timer, st, kcTcT1, tflops);
     TcEpilogue e1;
     e1.outB = lp.aT;
     e1.ldo = 2 * (int64_t)lp.Kp2;
@@ -323,7 +323,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     if (err != cudaSuccess) return err;
   }
   {
-    Scope sc(lp.timer, st, kcGemmT2, tflops);
+    Scope sc(lp.timer, st, kcTcT2, tflops);
     TcEpilogue e2;
     e2.outF = lp.gammaT;
     e2.ldo = sys.n_orb;
@@ -331,7 +331,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     if (err != cudaSuccess) return err;
   }
   {
-    Scope sc(lp.timer, st, kcSddmm, 0.0);
+    Scope sc(lp.timer, st, kcLpSddmm, ncols * sys.sf.dot);
     dim3 grid(sys.n_blocks, (ncols + 3) / 4);
     lp_sddmm<<<grid, 256, 0, st>>>(ncols, sys.n_occ, np, sys.n_orb, sys.aoff, sys.blk_atoms,
                                    sys.blk_ptr, sys.blk_prod, lp.Vpad32, lp.Xo32, lp.gammaT, Zin,

@@ -24,6 +24,8 @@ struct tddft_ctx {
   double *Zc = nullptr;     // [2S][n_prod] operator input (planar)
   double *Wout = nullptr;   // [2S][n_prod] operator output (planar)
   double *stage = nullptr;  // [2S][n_prod] interleaved staging for boundary calls
+  double *Z3 = nullptr;     // [6][n_prod] the three dipole vectors (planar)
+  double *a3 = nullptr;     // [n_virt][6][n_occ] X_virt^T beta(d_k)
   int *h_count = nullptr;   // pinned
   std::vector<void *> dev_allocs;
   std::string err;
@@ -86,10 +88,11 @@ tddft_status check_omega(tddft_ctx *c, int n, const double *omega, bool device) 
 
 namespace tddft {
 const char *kernel_class_name(int k) {
-  static const char *names[kcCount] = {"gemm_K",     "vertex_contract", "beta",
-                                       "gemm_T1",    "dscale",          "gemm_T2",
-                                       "sddmm_dot",  "gmres_step",      "gmres_gather",
-                                       "gmres_select", "misc"};
+  static const char *names[kcCount] = {
+      "f64_gemm_K",  "f64_vertex",   "f64_beta",      "f64_gemm_T1",  "f64_dscale",
+      "f64_gemm_T2", "f64_block_dot", "tc_gemm_K",    "lp_vertex",    "lp_beta",
+      "tc_gemm_T1_dscale", "tc_gemm_T2", "lp_block_dot", "lp_split_z", "gmres_step",
+      "gmres_gather", "gmres_select", "rhs_formation", "misc"};
   return (k >= 0 && k < kcCount) ? names[k] : "?";
 }
 
@@ -294,6 +297,19 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     adj_ptr.push_back((int)adj.size());
   }
   d.n_adj = (int)adj.size();
+  {
+    double fb = 0.0, fd = 0.0;
+    for (int A = 0; A < d.n_atoms; ++A)
+      for (auto &en : adj_of[A])
+        fb += 2.0 * nocc * (ao[A + 1] - ao[A]) * (ao[en.y + 1] - ao[en.y]);
+    for (size_t k = 0; k < blk_atoms.size(); ++k) {
+      const int A = blk_atoms[k].x, B = blk_atoms[k].y;
+      const double nab = (double)(ao[A + 1] - ao[A]) * (ao[B + 1] - ao[B]);
+      fd += (A == B ? 1.0 : 2.0) * 2.0 * nocc * nab + 2.0 * nab * (blk_ptr[k + 1] - blk_ptr[k]);
+    }
+    d.sf.beta = fb;
+    d.sf.dot = fd;
+  }
 
   std::vector<double> Xo((size_t)no * nocc), XvT((size_t)nv * no), Xv((size_t)no * nv);
   for (int a = 0; a < no; ++a) {
@@ -328,13 +344,16 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     e = cudaMemcpy(d.K, s->K, (size_t)np * np * sizeof(double), cudaMemcpyHostToDevice);
 
   const size_t S = (size_t)o->batch, m = (size_t)o->restart;
+  const size_t S3 = S < 3 ? 3 : S;   // W and beta also hold the three dipole columns
   OpWork &w = c->wk;
   w.slots = (int)S;
   w.timer = &c->timer;
 #define AL(ptr, n) if (e == cudaSuccess) e = dev_alloc(c, &(ptr), (n))
   AL(w.Y, 2 * S * np);
-  AL(w.W, 2 * S * (size_t)d.n_blocks * kBlk);
-  AL(w.beta, (size_t)no * 2 * S * nocc);
+  AL(w.W, 2 * S3 * (size_t)d.n_blocks * kBlk);
+  AL(w.beta, (size_t)no * 2 * S3 * nocc);
+  AL(c->Z3, 6 * (size_t)np);
+  AL(c->a3, (size_t)nv * 6 * nocc);
   AL(w.abuf, (size_t)nv * 2 * S * nocc);
   AL(w.gamma, (size_t)no * 2 * S * nocc);
   AL(w.omega, S);
@@ -520,7 +539,8 @@ tddft_status tddft_polarizability(tddft_ctx *c, int32_t n_omega, const double *o
   for (int g0 = 0; g0 < total; g0 += S) {
     const int n = std::min(S, total - g0);
     CUDA_TRY(c, launch_rhs_init(st, c->sys, n, g0, d_omega, c->Zc, c->wk.omega, g.omega));
-    CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, n, kChi0, eps, c->Zc, c->Wout));
+    CUDA_TRY(c, launch_rhs_formation(st, c->sys, c->wk, n, g0, d_omega, eps, c->Z3, c->a3,
+                                     c->Wout));
     CUDA_TRY(c, launch_gmres_start(st, c->sys, g, n, c->Wout));
     long it = 0;
     const int split = c->lowprec ? 1 : 0;
