@@ -111,6 +111,12 @@ typedef struct {
  *      reduced precision) also ends once its residual estimate has dropped
  *      by this factor; the float64 residual then starts the next cycle.
  *      In (0, 1); ignored for TDDFT_PREC_FP64.
+ *  graph: 1 = tddft_polarizability captures one GMRES iteration of a group
+ *      (selection, gathers, operators, Arnoldi/Givens/residual updates) in a
+ *      CUDA graph and replays it, every kernel reading the live count on the
+ *      device; the host checks for completion every few replays.  0 = one
+ *      launch sequence per iteration sized on the host.  Per-kernel timing
+ *      (tddft_timing_*) forces 0.
  */
 typedef struct {
   int32_t prec;
@@ -120,6 +126,7 @@ typedef struct {
   int32_t batch;
   void *stream;
   double inner_tol;
+  int32_t graph;
 } tddft_options;
 
 /* Per-(omega, direction) solver report. */
@@ -128,7 +135,7 @@ typedef struct {
   int32_t cycles;    /* GMRES cycles started */
   double resid;      /* final ||b - A x|| / ||b|| (float64) */
   int32_t converged; /* 1 if resid <= tol */
-  int32_t pad;
+  int32_t flags;     /* bit 0: a supplied initial guess was worse than zero and dropped */
 } tddft_solve_stats;
 
 /*
@@ -196,6 +203,21 @@ tddft_status tddft_polarizability(tddft_ctx *ctx, int32_t n_omega, const double 
                                   double eps, double *P, tddft_solve_stats *stats,
                                   int32_t flags);
 
+/*
+ * tddft_polarizability with warm starts and the solutions returned.
+ *  x0 (may be NULL): n_omega x 3 x n_prod complex interleaved, row w*3+k the
+ *      initial guess of (omega[w], direction k).  Each guess first costs one
+ *      float64 product A x0; if ||b - A x0|| > ||b||, zero is used instead
+ *      (stats flags bit 0), so plain zero-guess GMRES is both the fallback
+ *      and the judge of a guess.
+ *  X (may be NULL): receives the solutions X_k(omega) in the same layout.
+ *  x0 and X are device pointers: flags must include TDDFT_DEVICE_PTRS when
+ *  either is given.  Everything else as tddft_polarizability.
+ */
+tddft_status tddft_polarizability_guess(tddft_ctx *ctx, int32_t n_omega, const double *omega,
+                                        double eps, const double *x0, double *X, double *P,
+                                        tddft_solve_stats *stats, int32_t flags);
+
 /* Sizes of a context (any pointer may be NULL). */
 tddft_status tddft_sizes(const tddft_ctx *ctx, int32_t *n_orb, int32_t *n_occ, int32_t *n_prod,
                          int32_t *n_blocks);
@@ -225,6 +247,88 @@ tddft_status tddft_timing_get(tddft_ctx *ctx, int32_t i, const char **name, int3
  */
 tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uint64_t seed,
                                  double *max_rel_err);
+
+/*
+ * Learned initial guess (the frequency sweep solves a coarse grid from zero,
+ * then each remaining frequency from its two solved neighbours omega- and
+ * omega+).  A small network, the same for every product mu, maps per-product
+ * features to a complex correction y_mu of the linear interpolation:
+ *     x0_mu = (1 - t) X_mu(omega-) + t X_mu(omega+) + s y_mu ,
+ * with t = (omega - omega-) / (omega+ - omega-) and s the rms of the two
+ * neighbours.  Features (10 per product): Re/Im X(omega-)/s, Re/Im
+ * X(omega+)/s, t, omega, (omega+ - omega-)/eps, bilocal flag, d_k^mu / rms(d_k),
+ * ||V_mu|| / mean ||V||.  The guess enters tddft_polarizability_guess, where
+ * zero-guess GMRES remains the fallback and the judge.
+ *
+ * Network: n_in -> width -> width -> n_out, tanh on the hidden layers,
+ * float32 parameters packed [W1 (width x n_in, row-major), b1, W2, b2,
+ * W3 (n_out x width), b3]; W3 and b3 start at zero, W1 and W2 uniform in
+ * +-1/sqrt(fan_in) from a hash of (index, seed).  Training (float32) and
+ * inference (bf16 weights, float32 activations) run in the library's kernels.
+ * All row arrays are device pointers; a network is not thread-safe.
+ */
+typedef struct tddft_mlp tddft_mlp;
+
+/* Allocate a network and scratch for up to max_rows rows on `stream`. */
+tddft_status tddft_mlp_create(int32_t n_in, int32_t width, int32_t n_out, int64_t max_rows,
+                              uint64_t seed, void *stream, tddft_mlp **out);
+void tddft_mlp_destroy(tddft_mlp *mlp);
+const char *tddft_mlp_last_error(const tddft_mlp *mlp);
+int64_t tddft_mlp_num_params(const tddft_mlp *mlp);
+/* Copy the packed parameters to (set = 0) or from (set = 1) a host buffer of
+ * n = tddft_mlp_num_params floats; setting also resets the Adam state. */
+tddft_status tddft_mlp_params(tddft_mlp *mlp, float *host, int64_t n, int32_t set);
+/* Y [rows][n_out] = network(F [rows][n_in]); bf16 != 0 uses bf16 weights. */
+tddft_status tddft_mlp_forward(tddft_mlp *mlp, int64_t rows, const float *F, float *Y,
+                               int32_t bf16);
+/* Gradient of sum_rows dY . Y with respect to the parameters (float32
+ * forward then backward); copied to grad_host (n floats) when not NULL. */
+tddft_status tddft_mlp_backward(tddft_mlp *mlp, int64_t rows, const float *F, const float *dY,
+                                float *grad_host);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the mean
+ * over n_target targets of |x0 - x*|^2 / |x*|^2, where x0 = lin + s y and
+ * the rows are n_target blocks of n_prod products.  lin, xstar: complex
+ * interleaved [n_target][n_prod]; scale [n_target]; loss[n_target] receives
+ * each target's relative squared error before the step. */
+tddft_status tddft_mlp_train_step(tddft_mlp *mlp, int32_t n_target, int32_t n_prod, const float *F,
+                                  const double *lin, const double *xstar, const double *scale,
+                                  double *loss, float lr);
+/* Features, interpolation and scale of n_target right-hand sides from the
+ * solved rows X (complex interleaved, n_prod per row): target r takes rows
+ * nb[2r] (omega-) and nb[2r+1] (omega+), weight t[r], frequency omega[r],
+ * direction dir[r].  F [n_target*n_prod][10] float, lin [n_target][n_prod]
+ * complex, scale [n_target].  On the context's stream. */
+tddft_status tddft_guess_features(tddft_ctx *ctx, int32_t n_target, const int32_t *nb,
+                                  const double *t, const double *omega, const int32_t *dir,
+                                  double h_over_eps, const double *X, float *F, double *lin,
+                                  double *scale);
+/* x0 [n_target][n_prod] complex = lin + scale * Y (Y [rows][2]). */
+tddft_status tddft_guess_combine(int64_t n_target, int32_t n_prod, const float *Y,
+                                 const double *lin, const double *scale, double *x0,
+                                 void *stream);
+
+/*
+ * Several molecules of uneven size solved together (every (molecule, omega,
+ * direction) is an independent right-hand side).  tddft_batch_create makes
+ * one context per molecule, each on a private stream, with the same options
+ * (options.stream and options.graph are ignored).  tddft_batch_polarizability
+ * solves the same omega grid (host pointer) for every molecule: in each
+ * round, every molecule forms its next group of at most options.batch
+ * right-hand sides, then one CUDA graph whose parallel branches hold one
+ * device-driven GMRES iteration of every molecule is replayed until all
+ * groups are done.  P (host): n_mol x n_omega x 3 x 3 complex interleaved;
+ * stats (host, may be NULL): n_mol x n_omega x 3.  Returns NOT_CONVERGED if
+ * any entry missed tol (P still filled).
+ */
+typedef struct tddft_batch tddft_batch;
+tddft_status tddft_batch_create(int32_t n_mol, const tddft_system *systems,
+                                const tddft_options *opts, tddft_batch **out);
+tddft_status tddft_batch_polarizability(tddft_batch *batch, int32_t n_omega, const double *omega,
+                                        double eps, double *P, tddft_solve_stats *stats);
+/* The context of molecule i (owned by the batch; NULL if out of range). */
+tddft_ctx *tddft_batch_context(tddft_batch *batch, int32_t i);
+const char *tddft_batch_last_error(const tddft_batch *batch);
+void tddft_batch_destroy(tddft_batch *batch);
 
 /* Text of the last error on this context (never NULL; "" if none).  With
  * ctx == NULL: the last error of a failed tddft_create on this thread. */

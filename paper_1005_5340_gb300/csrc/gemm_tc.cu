@@ -135,7 +135,11 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
 template <int EPI>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   int M, int N, int Kp, int nseg, int4 segs, TcEpilogue ep, int *err) {
+                   int M, int N, int Kp, int nseg, int4 segs, TcEpilogue ep, int *err,
+                   const int *dcnt, int mul_n) {
+  // graph replays: columns beyond the live count are skipped (whole CTAs)
+  if (dcnt) N = (int)min((int64_t)N, (int64_t)mul_n * (*dcnt));
+  if ((int)blockIdx.y * TC_BN >= N) return;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -245,17 +249,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             if (n >= N) continue;
             float re = 0.f, im = 0.f;
             if (live) {
+              // omega -+ Delta in float64 (they cancel near a resonance), the rest of
+              // D in float32: its rounding (~1e-7) is far below the split-bf16 error
               const int pair = n >> 1;
               const int E = pair % ep.n_occ;
               const int sl = pair / ep.n_occ;
               const double delta = ep.energy[ep.n_occ + m] - ep.energy[E];
               const double w = ep.omega[sl];
-              const double xm = w - delta, xp = w + delta, e2 = ep.eps * ep.eps;
-              const double im2 = 1.0 / (xm * xm + e2), ip2 = 1.0 / (xp * xp + e2);
-              const double dre = ep.occ_value * (xm * im2 - xp * ip2);
-              const double dim = ep.occ_value * ep.eps * (ip2 - im2);
-              re = (float)(dre * v[j] - dim * v[j + 1]);
-              im = (float)(dre * v[j + 1] + dim * v[j]);
+              const float xm = (float)(w - delta), xp = (float)(w + delta);
+              const float ef = (float)ep.eps, e2 = ef * ef, occ = (float)ep.occ_value;
+              const float im2 = __frcp_rn(fmaf(xm, xm, e2)), ip2 = __frcp_rn(fmaf(xp, xp, e2));
+              const float dre = occ * (xm * im2 - xp * ip2);
+              const float dim = occ * ef * (ip2 - im2);
+              re = dre * v[j] - dim * v[j + 1];
+              im = dre * v[j + 1] + dim * v[j];
             }
             __nv_bfloat16 h, l;
             split_bf16(re, h, l);
@@ -314,8 +321,18 @@ cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int 
   return cudaSuccess;
 }
 
+void tc_init_attributes() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(gemm_tc_kernel<kStoreF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TC_SMEM);
+  cudaFuncSetAttribute(gemm_tc_kernel<kDscaleSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TC_SMEM);
+  done = true;
+}
+
 cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
-                           int epi, const TcEpilogue &ep, int *err) {
+                           int epi, const TcEpilogue &ep, int *err, const int *dcnt, int mul_n) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (A.Kp != B.Kp) return cudaErrorInvalidValue;
   static bool attr_set[2] = {false, false};
@@ -330,7 +347,7 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
       attr_set[0] = true;
     }
     gemm_tc_kernel<kStoreF32><<<grid, TC_THREADS, TC_SMEM, st>>>(A.map, B.map, M, N, A.Kp, 3, segs,
-                                                                  ep, err);
+                                                                  ep, err, dcnt, mul_n);
   } else {
     if (!attr_set[1]) {
       cudaFuncSetAttribute(gemm_tc_kernel<kDscaleSplit>,
@@ -338,7 +355,7 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
       attr_set[1] = true;
     }
     gemm_tc_kernel<kDscaleSplit><<<grid, TC_THREADS, TC_SMEM, st>>>(A.map, B.map, M, N, A.Kp, 3,
-                                                                     segs, ep, err);
+                                                                     segs, ep, err, dcnt, mul_n);
   }
   return cudaGetLastError();
 }

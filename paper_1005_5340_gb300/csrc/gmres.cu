@@ -64,7 +64,7 @@ struct Gs {
   int m, max_restarts, n_prod;
   double tol, inner_tol;
   double *rho0;
-  int *state, *jcur, *cycles, *matvecs, *conv;
+  int *state, *jcur, *cycles, *matvecs, *conv, *flags;
   double *bnorm, *resid, *omega;
   double2 *H, *sn, *g;
   double *cs, *V, *x, *b;
@@ -76,6 +76,7 @@ Gs view(const GmresState &s, int n_prod) {
   v.m = s.m; v.max_restarts = s.max_restarts; v.n_prod = n_prod; v.tol = s.tol;
   v.inner_tol = s.inner_tol; v.rho0 = s.rho0;
   v.state = s.state; v.jcur = s.jcur; v.cycles = s.cycles; v.matvecs = s.matvecs; v.conv = s.conv;
+  v.flags = s.flags;
   v.bnorm = s.bnorm; v.resid = s.resid; v.omega = s.omega;
   v.H = s.H; v.sn = s.sn; v.g = s.g; v.cs = s.cs; v.V = s.V; v.x = s.x; v.b = s.b; v.act = s.act;
   return v;
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__r
     G.bnorm[r] = nrm;
     G.matvecs[r] = 0;
     G.jcur[r] = 0;
+    G.flags[r] = 0;
     if (nrm > 0.0) {
       G.state[r] = kStateArnoldi;
       G.cycles[r] = 1;
@@ -127,7 +129,8 @@ __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__r
 // With split, right-hand sides in an Arnoldi step go to act and those whose
 // next product is the residual check go to act2.
 __global__ void __launch_bounds__(1024) gmres_select_kernel(const int *__restrict__ state, int n,
-                                                            int split, int *__restrict__ act,
+                                                            int split, int min_b,
+                                                            int *__restrict__ act,
                                                             int *__restrict__ act2,
                                                             int *__restrict__ count) {
   __shared__ int sums[2][1024];
@@ -160,16 +163,20 @@ __global__ void __launch_bounds__(1024) gmres_select_kernel(const int *__restric
     else act[p1++] = i;
   }
   if (t == 1023) {
-    count[0] = sums[0][1023];
-    count[1] = sums[1][1023];
+    const int c0 = sums[0][1023], c1v = sums[1][1023];
+    count[0] = c0;
+    // the float64 group waits until it is worth a launch, unless nothing else is left
+    count[1] = (c0 > 0 && c1v < min_b) ? 0 : c1v;
   }
 }
 
 // Operator input of each active right-hand side: v_j (Arnoldi) or x (residual).
 __global__ void __launch_bounds__(NT) gmres_gather_kernel(Gs G, const int *__restrict__ list,
                                                           double *__restrict__ Zc,
-                                                          double *__restrict__ slot_omega) {
+                                                          double *__restrict__ slot_omega,
+                                                          const int *__restrict__ dcnt) {
   const int s = blockIdx.x;
+  if (dcnt && s >= *dcnt) return;
   const int r = list[s];
   const int N = G.n_prod;
   const double *src = (G.state[r] == kStateArnoldi)
@@ -181,11 +188,13 @@ __global__ void __launch_bounds__(NT) gmres_gather_kernel(Gs G, const int *__res
 }
 
 __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restrict__ list,
-                                                        const double *__restrict__ Wout) {
+                                                        const double *__restrict__ Wout,
+                                                        const int *__restrict__ dcnt) {
   __shared__ double red[16 * (NT / 32)];
   __shared__ double2 hs[257], hp[257], ys[257];
   __shared__ int finish_flag;
   const int s = blockIdx.x;
+  if (dcnt && s >= *dcnt) return;
   const int r = list[s];
   const int N = G.n_prod;
   const int m = G.m;
@@ -204,7 +213,19 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
       s2[0] += t * t;
     }
     block_sum<1>(s2, red);
-    const double rho = sqrt(s2[0]);
+    double rho = sqrt(s2[0]);
+    bool rejected = false;
+    if (G.cycles[r] == 0 && rho > G.bnorm[r]) {
+      // the residual of a supplied initial guess: zero is the fallback and the
+      // judge, so a guess worse than zero is dropped
+      double *x = G.x + (int64_t)2 * r * N;
+      for (int e = tid; e < 2 * N; e += NT) {
+        Vr[e] = b[e];
+        x[e] = 0.0;
+      }
+      rho = G.bnorm[r];
+      rejected = true;
+    }
     const double rel = rho / G.bnorm[r];
     int next;
     if (rel <= G.tol) next = 0;
@@ -217,6 +238,7 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
     if (tid == 0) {
       G.matvecs[r] += 1;
       G.resid[r] = rel;
+      if (rejected) G.flags[r] |= 1;
       if (next == 0) { G.state[r] = kStateDone; G.conv[r] = 1; }
       else if (next == 1) { G.state[r] = kStateDone; G.conv[r] = 0; }
       else {
@@ -361,6 +383,37 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
   }
 }
 
+// Initial guesses: x = x0 (interleaved complex rows g0..g0+n-1), and the first
+// operator product is A x0 (state "awaiting A x", no cycle started yet).
+__global__ void __launch_bounds__(NT) gmres_guess_kernel(Gs G, int g0,
+                                                         const double *__restrict__ x0) {
+  const int r = blockIdx.x;
+  const int N = G.n_prod;
+  if (G.state[r] == kStateDone) return;   // b = 0: x stays 0
+  const double *src = x0 + (int64_t)(g0 + r) * 2 * N;
+  double *x = G.x + (int64_t)2 * r * N;
+  for (int e = threadIdx.x; e < N; e += NT) {
+    x[e] = src[2 * e];
+    x[N + e] = src[2 * e + 1];
+  }
+  if (threadIdx.x == 0) {
+    G.state[r] = kStateResid;
+    G.cycles[r] = 0;
+  }
+}
+
+// X rows g0..g0+n-1 (interleaved complex) = x of each right-hand side.
+__global__ void __launch_bounds__(NT) gmres_export_kernel(Gs G, int g0, double *__restrict__ X) {
+  const int r = blockIdx.x;
+  const int N = G.n_prod;
+  const double *x = G.x + (int64_t)2 * r * N;
+  double *dst = X + (int64_t)(g0 + r) * 2 * N;
+  for (int e = threadIdx.x; e < N; e += NT) {
+    dst[2 * e] = x[e];
+    dst[2 * e + 1] = x[N + e];
+  }
+}
+
 // Right-hand sides g0 .. g0+n-1 of a spectrum: index g -> (omega g/3, direction g%3).
 __global__ void rhs_init_kernel(int n, int g0, int n_prod, const double *__restrict__ omega_all,
                                 const double *__restrict__ dip, double *__restrict__ Zc,
@@ -415,22 +468,23 @@ cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState
   return cudaGetLastError();
 }
 
-cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split) {
-  gmres_select_kernel<<<1, 1024, 0, st>>>(gs.state, n, split, gs.act, gs.act2, gs.count);
+cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split, int min_b) {
+  gmres_select_kernel<<<1, 1024, 0, st>>>(gs.state, n, split, min_b, gs.act, gs.act2, gs.count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs,
-                                const int *list, int S, double *Zc, double *slot_omega) {
+                                const int *list, int S, double *Zc, double *slot_omega,
+                                const int *dcnt) {
   if (S <= 0) return cudaSuccess;
-  gmres_gather_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Zc, slot_omega);
+  gmres_gather_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Zc, slot_omega, dcnt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs,
-                              const int *list, int S, const double *Wout) {
+                              const int *list, int S, const double *Wout, const int *dcnt) {
   if (S <= 0) return cudaSuccess;
-  gmres_step_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Wout);
+  gmres_step_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Wout, dcnt);
   return cudaGetLastError();
 }
 
@@ -439,6 +493,20 @@ cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0
                             double *gs_omega) {
   if (n <= 0) return cudaSuccess;
   rhs_init_kernel<<<n, 256, 0, st>>>(n, g0, sys.n_prod, omega_all, sys.dip, Zc, slot_omega, gs_omega);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_guess(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n, int g0,
+                               const double *x0) {
+  if (n <= 0) return cudaSuccess;
+  gmres_guess_kernel<<<n, NT, 0, st>>>(view(gs, sys.n_prod), g0, x0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_export(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n, int g0,
+                                double *X) {
+  if (n <= 0) return cudaSuccess;
+  gmres_export_kernel<<<n, NT, 0, st>>>(view(gs, sys.n_prod), g0, X);
   return cudaGetLastError();
 }
 

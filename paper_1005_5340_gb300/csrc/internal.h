@@ -44,6 +44,7 @@ struct DevSystem {
   double *Vpad = nullptr;      // [n_prod][kBlk] vertex blocks in blk_prod order, zero padded
   int *adj_ptr = nullptr;      // [n_atoms+1]
   int4 *adj = nullptr;         // [n_adj] (block, other atom, transposed, 0)
+  float *pfeat = nullptr;      // [n_prod][2] (bilocal flag, ||V_mu|| / mean ||V||)
 };
 
 // Optional per-kernel timing: CUDA events recorded on the launching stream
@@ -85,13 +86,17 @@ struct OpWork {
   double *gamma = nullptr;    // [n_orb][2S][n_occ]
   double *omega = nullptr;    // [S] frequency of each slot
   Timer *timer = nullptr;
+  const int *dcnt = nullptr;  // graph replays: device count of live slots (NULL: all S)
 };
 
 enum OpMode { kChi0 = 0, kKernel = 1, kA = 2 };
 
 // Launchers (stream-ordered, no synchronisation).  Return cudaGetLastError().
+// dcnt (may be NULL): device count of live right-hand sides; rows beyond
+// mul_m * count and columns beyond mul_n * count are skipped (0 = no limit).
 cudaError_t launch_gemm_f64(cudaStream_t st, int M, int N, int K, const double *A, int64_t lda,
-                            const double *B, int64_t ldb, double *C, int64_t ldc);
+                            const double *B, int64_t ldb, double *C, int64_t ldc,
+                            const int *dcnt = nullptr, int mul_m = 0, int mul_n = 0);
 cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S,
                                   OpMode mode, double eps, const double *Zin, double *Out);
 // Right-hand sides b = chi0(omega) d_k of a spectrum group (rows g0..g0+S-1,
@@ -133,8 +138,11 @@ struct TcEpilogue {
 };
 
 cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows);
+// dcnt (may be NULL): columns beyond mul_n * (*dcnt) are skipped.
 cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
-                           int epi, const TcEpilogue &ep, int *err);
+                           int epi, const TcEpilogue &ep, int *err, const int *dcnt = nullptr,
+                           int mul_n = 0);
+void tc_init_attributes();
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -156,6 +164,7 @@ struct LpWork {
   int *err = nullptr;              // [1] device-side error code of the GEMM waits
   TcOperand opK, opXvT, opXv, opZ, opBeta, opA;
   Timer *timer = nullptr;
+  const int *dcnt = nullptr;  // graph replays: device count of live slots (NULL: all S)
 };
 
 cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &lp);
@@ -174,6 +183,7 @@ struct GmresState {
   int *cycles = nullptr;    // [cap]
   int *matvecs = nullptr;   // [cap]
   int *conv = nullptr;      // [cap]
+  int *flags = nullptr;     // [cap] bit 0: the supplied initial guess was rejected
   double *bnorm = nullptr;  // [cap]
   double *resid = nullptr;  // [cap]
   double *omega = nullptr;  // [cap]
@@ -195,16 +205,27 @@ cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState
                                const double *Bplanar /*[2n][n_prod]*/);
 // split = 0: every live right-hand side in act (count[0]); split = 1: those in
 // an Arnoldi step in act (count[0]), those awaiting A x in act2 (count[1]).
-cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split);
+// min_b: with split, the float64 group runs only once min_b right-hand sides
+// await it or no Arnoldi work is left (otherwise count[1] is reported as 0).
+cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split, int min_b = 1);
 cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs,
-                                const int *list, int S, double *Zc, double *slot_omega);
+                                const int *list, int S, double *Zc, double *slot_omega,
+                                const int *dcnt = nullptr);
 cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs,
-                              const int *list, int S, const double *Wout);
+                              const int *list, int S, const double *Wout,
+                              const int *dcnt = nullptr);
 // Right-hand sides g0..g0+n-1 of a spectrum (g -> omega g/3, direction g%3):
 // Zc rows 2r, 2r+1 = (d_{g%3}, 0), slot and solver frequencies set.
 cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0,
                             const double *omega_all, double *Zc, double *slot_omega,
                             double *gs_omega);
+// x of right-hand sides g0..g0+n-1 = rows of x0 (interleaved); their first
+// product is then the residual of the guess.
+cudaError_t launch_gmres_guess(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n, int g0,
+                               const double *x0);
+// rows g0..g0+n-1 of X (interleaved) = x of each right-hand side
+cudaError_t launch_gmres_export(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n, int g0,
+                                double *X);
 // P[w][i][k] (complex) = d_i . x_g for g = w*3 + k in g0..g0+n-1.
 cudaError_t launch_polarization(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
                                 int g0, double2 *P);

@@ -24,13 +24,21 @@ constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
 __global__ void __launch_bounds__(256) gemm_f64_nn(int M, int N, int K, const double *__restrict__ A,
                                                    int64_t lda, const double *__restrict__ B,
                                                    int64_t ldb, double *__restrict__ C,
-                                                   int64_t ldc) {
+                                                   int64_t ldc, const int *__restrict__ dcnt,
+                                                   int mul_m, int mul_n) {
   __shared__ double As[2][GB_K][GB_M + 2];
   __shared__ double Bs[2][GB_K][GB_N];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = (int64_t)blockIdx.y * GB_M;
   const int64_t n0 = (int64_t)blockIdx.x * GB_N;
+  if (dcnt) {
+    // graph replays: the live extent is read on the device
+    const int c = *dcnt;
+    if (mul_m) M = min(M, mul_m * c);
+    if (mul_n) N = (int)min((int64_t)N, (int64_t)mul_n * c);
+  }
+  if (m0 >= M || n0 >= N) return;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -108,10 +116,13 @@ __global__ void __launch_bounds__(256) vertex_contract(int nb, int ncols, int n_
                                                        const int *__restrict__ blk_prod,
                                                        const double *__restrict__ Vpad,
                                                        const double *__restrict__ Y,
-                                                       double *__restrict__ W) {
+                                                       double *__restrict__ W,
+                                                       const int *__restrict__ dcnt) {
   __shared__ double ys[32][VW_COLS];
   const int k = blockIdx.x;
   const int c0 = blockIdx.y * VW_COLS;
+  if (dcnt) ncols = min(ncols, 2 * *dcnt);
+  if (c0 >= ncols) return;
   const int t = threadIdx.x;
   const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
   double acc[VW_COLS];
@@ -148,10 +159,13 @@ constexpr int BT_THREADS = 128;
 __global__ void __launch_bounds__(BT_THREADS) beta_kernel(
     int ncols, int nb, int n_occ, const int *__restrict__ aoff, const int *__restrict__ adj_ptr,
     const int4 *__restrict__ adj, const double *__restrict__ W, const double *__restrict__ Xo,
-    double *__restrict__ beta) {
+    double *__restrict__ beta, const int *__restrict__ dcnt) {
   __shared__ double Ws[BT_COLS][kMaxOrb][kMaxOrb + 1];
   const int A = blockIdx.x;
   const int c0 = blockIdx.y * BT_COLS;
+  // ncols is the column stride of beta; nact the live columns
+  const int nact = dcnt ? min(ncols, 2 * *dcnt) : ncols;
+  if (c0 >= nact) return;
   const int nA = aoff[A + 1] - aoff[A];
   const int e0 = adj_ptr[A], e1 = adj_ptr[A + 1];
   for (int E0 = 0; E0 < n_occ; E0 += BT_THREADS) {
@@ -169,7 +183,7 @@ __global__ void __launch_bounds__(BT_THREADS) beta_kernel(
       for (int i = threadIdx.x; i < BT_COLS * kBlk; i += BT_THREADS) {
         int c = i / kBlk, ab = i % kBlk, a = ab / kMaxOrb, b = ab % kMaxOrb;
         double v = 0.0;
-        if (c0 + c < ncols)
+        if (c0 + c < nact)
           v = tr ? W[((int64_t)(c0 + c) * nb + k) * kBlk + b * kMaxOrb + a]
                  : W[((int64_t)(c0 + c) * nb + k) * kBlk + a * kMaxOrb + b];
         Ws[c][a][b] = v;
@@ -188,7 +202,7 @@ __global__ void __launch_bounds__(BT_THREADS) beta_kernel(
     if (E < n_occ) {
 #pragma unroll
       for (int c = 0; c < BT_COLS; ++c) {
-        if (c0 + c >= ncols) continue;
+        if (c0 + c >= nact) continue;
 #pragma unroll
         for (int a = 0; a < kMaxOrb; ++a)
           if (a < nA) beta[((int64_t)(aoff[A] + a) * ncols + c0 + c) * n_occ + E] = acc[c][a];
@@ -204,14 +218,16 @@ __global__ void __launch_bounds__(BT_THREADS) beta_kernel(
 // ---------------------------------------------------------------------------
 __global__ void dscale_kernel(int n_virt, int S, int n_occ, double occ_value,
                               const double *__restrict__ energy, const double *__restrict__ omega,
-                              double eps, double *__restrict__ a) {
+                              double eps, double *__restrict__ a, const int *__restrict__ dcnt) {
   const int64_t total = (int64_t)n_virt * S * n_occ;
+  const int S_act = dcnt ? min(S, *dcnt) : S;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int E = (int)(idx % n_occ);
     const int64_t rest = idx / n_occ;
     const int s = (int)(rest % S);
     const int F = (int)(rest / S);
+    if (s >= S_act) continue;
     const double delta = energy[n_occ + F] - energy[E];
     const double w = omega[s];
     // 1/(x + i eps) = (x - i eps) / (x^2 + eps^2)
@@ -245,12 +261,16 @@ __global__ void __launch_bounds__(256) sddmm_dot(int ncols, int n_occ, int n_pro
                                                  const double *__restrict__ Xo,
                                                  const double *__restrict__ gamma,
                                                  const double *__restrict__ Zin, int subtract,
-                                                 double *__restrict__ Out) {
+                                                 double *__restrict__ Out,
+                                                 const int *__restrict__ dcnt) {
   __shared__ double XA[kMaxOrb][SD_E + 1], XB[kMaxOrb][SD_E + 1];
   __shared__ double gA[SD_COLS][kMaxOrb][SD_E + 1], gB[SD_COLS][kMaxOrb][SD_E + 1];
   __shared__ double Gs[SD_COLS][kBlk];
   const int k = blockIdx.x;
   const int c0 = blockIdx.y * SD_COLS;
+  // ncols is the column stride of gamma; nact the live columns
+  const int nact = dcnt ? min(ncols, 2 * *dcnt) : ncols;
+  if (c0 >= nact) return;
   const int t = threadIdx.x;
   const int a = t >> 4, b = t & 15;
   const int2 AB = blk_atoms[k];
@@ -272,7 +292,7 @@ __global__ void __launch_bounds__(256) sddmm_dot(int ncols, int n_occ, int n_pro
       int c = i / (kMaxOrb * SD_E), rem = i % (kMaxOrb * SD_E);
       int r = rem / SD_E, e = rem % SD_E;
       int E = E0 + e;
-      bool okc = (c0 + c < ncols) && E < n_occ;
+      bool okc = (c0 + c < nact) && E < n_occ;
       gA[c][r][e] = (okc && r < nA) ? gamma[((int64_t)(aoA + r) * ncols + c0 + c) * n_occ + E] : 0.0;
       gB[c][r][e] = (okc && r < nB) ? gamma[((int64_t)(aoB + r) * ncols + c0 + c) * n_occ + E] : 0.0;
     }
@@ -312,7 +332,7 @@ __global__ void __launch_bounds__(256) sddmm_dot(int ncols, int n_occ, int n_pro
       const int mu = blk_prod[q];
 #pragma unroll
       for (int c = 0; c < SD_COLS; ++c) {
-        if (c0 + c >= ncols) continue;
+        if (c0 + c >= nact) continue;
         const int64_t o = (int64_t)(c0 + c) * n_prod + mu;
         Out[o] = subtract ? Zin[o] - part[c] : part[c];
       }
@@ -384,11 +404,12 @@ int grid_for(int64_t total, int threads) {
 }  // namespace
 
 cudaError_t launch_gemm_f64(cudaStream_t st, int M, int N, int K, const double *A, int64_t lda,
-                            const double *B, int64_t ldb, double *C, int64_t ldc) {
+                            const double *B, int64_t ldb, double *C, int64_t ldc,
+                            const int *dcnt, int mul_m, int mul_n) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  gemm_f64_nn<<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc);
+  gemm_f64_nn<<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, dcnt, mul_m, mul_n);
   return cudaGetLastError();
 }
 
@@ -433,11 +454,11 @@ cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &
   {
     dim3 grid(sys.n_blocks, 1);
     vertex_contract<<<grid, 256, 0, st>>>(sys.n_blocks, 6, np, sys.blk_ptr, sys.blk_prod, sys.Vpad,
-                                          Z3, wk.W);
+                                          Z3, wk.W, nullptr);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     dim3 gb(sys.n_atoms, 2);
     beta_kernel<<<gb, BT_THREADS, 0, st>>>(6, sys.n_blocks, sys.n_occ, sys.aoff, sys.adj_ptr,
-                                           sys.adj, wk.W, sys.Xo, wk.beta);
+                                           sys.adj, wk.W, sys.Xo, wk.beta, nullptr);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   err = launch_gemm_f64(st, sys.n_virt, 6 * sys.n_occ, sys.n_orb, sys.XvT, sys.n_orb, wk.beta,
@@ -453,7 +474,7 @@ cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &
   if (err != cudaSuccess) return err;
   dim3 grid(sys.n_blocks, (2 * S + SD_COLS - 1) / SD_COLS);
   sddmm_dot<<<grid, 256, 0, st>>>(2 * S, sys.n_occ, np, sys.aoff, sys.blk_atoms, sys.blk_ptr,
-                                  sys.blk_prod, sys.Vpad, sys.Xo, wk.gamma, nullptr, 0, Out);
+                                  sys.blk_prod, sys.Vpad, sys.Xo, wk.gamma, nullptr, 0, Out, nullptr);
   return cudaGetLastError();
 }
 
@@ -468,7 +489,8 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
   if (mode == kKernel || mode == kA) {
     // Y = Z K  (K symmetric, so row c of Y is K z_c)
     Scope sc(wk.timer, st, kcGemmK, 2.0 * ncols * (double)np * np);
-    err = launch_gemm_f64(st, ncols, np, np, Zin, np, sys.K, np, (mode == kKernel) ? Out : wk.Y, np);
+    err = launch_gemm_f64(st, ncols, np, np, Zin, np, sys.K, np, (mode == kKernel) ? Out : wk.Y, np,
+                          wk.dcnt, 2, 0);
     if (err != cudaSuccess || mode == kKernel) return err;
     Y = wk.Y;
   }
@@ -476,14 +498,14 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
     Scope sc(wk.timer, st, kcVertex, 2.0 * ncols * (double)kBlk * np);
     dim3 grid(sys.n_blocks, (ncols + VW_COLS - 1) / VW_COLS);
     vertex_contract<<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
-                                          sys.Vpad, Y, wk.W);
+                                          sys.Vpad, Y, wk.W, wk.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   {
     Scope sc(wk.timer, st, kcBeta, ncols * sys.sf.beta);
     dim3 grid(sys.n_atoms, (ncols + BT_COLS - 1) / BT_COLS);
     beta_kernel<<<grid, BT_THREADS, 0, st>>>(ncols, sys.n_blocks, sys.n_occ, sys.aoff, sys.adj_ptr,
-                                             sys.adj, wk.W, sys.Xo, wk.beta);
+                                             sys.adj, wk.W, sys.Xo, wk.beta, wk.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   const int64_t ncolE = (int64_t)ncols * sys.n_occ;
@@ -492,19 +514,19 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
   {
     Scope sc(wk.timer, st, kcGemmT1, tflops);
     err = launch_gemm_f64(st, sys.n_virt, (int)ncolE, sys.n_orb, sys.XvT, sys.n_orb, wk.beta,
-                          ncolE, wk.abuf, ncolE);
+                          ncolE, wk.abuf, ncolE, wk.dcnt, 0, 2 * sys.n_occ);
     if (err != cudaSuccess) return err;
   }
   {
     Scope sc(wk.timer, st, kcDscale, 0.0);
     dscale_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
-        sys.n_virt, S, sys.n_occ, sys.occ_value, sys.energy, wk.omega, eps, wk.abuf);
+        sys.n_virt, S, sys.n_occ, sys.occ_value, sys.energy, wk.omega, eps, wk.abuf, wk.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   {
     Scope sc(wk.timer, st, kcGemmT2, tflops);
     err = launch_gemm_f64(st, sys.n_orb, (int)ncolE, sys.n_virt, sys.Xv, sys.n_virt, wk.abuf,
-                          ncolE, wk.gamma, ncolE);
+                          ncolE, wk.gamma, ncolE, wk.dcnt, 0, 2 * sys.n_occ);
     if (err != cudaSuccess) return err;
   }
   {
@@ -512,7 +534,7 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
     dim3 grid(sys.n_blocks, (ncols + SD_COLS - 1) / SD_COLS);
     sddmm_dot<<<grid, 256, 0, st>>>(ncols, sys.n_occ, np, sys.aoff, sys.blk_atoms, sys.blk_ptr,
                                     sys.blk_prod, sys.Vpad, sys.Xo, wk.gamma, Zin,
-                                    mode == kA ? 1 : 0, Out);
+                                    mode == kA ? 1 : 0, Out, wk.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   return cudaSuccess;

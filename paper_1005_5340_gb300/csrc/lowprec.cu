@@ -40,7 +40,9 @@ struct Scope {
 
 // dst[r][k] = hi(src[r, k]), dst[r][Kp + k] = lo(src[r, k]); zero for k >= cols.
 __global__ void split_rows_kernel(const double *__restrict__ src, int64_t rs, int64_t cs, int rows,
-                                  int cols, int Kp, __nv_bfloat16 *__restrict__ dst) {
+                                  int cols, int Kp, __nv_bfloat16 *__restrict__ dst,
+                                  const int *__restrict__ dcnt = nullptr, int mul_r = 0) {
+  if (dcnt) rows = min(rows, mul_r * *dcnt);
   const int64_t total = (int64_t)rows * Kp;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -65,11 +67,14 @@ __global__ void __launch_bounds__(256) lp_vertex(int nb, int ncols, int n_prod,
                                                  const int *__restrict__ blk_ptr,
                                                  const int *__restrict__ blk_prod,
                                                  const float *__restrict__ Vpad,
-                                                 const TIn *__restrict__ Y, float *__restrict__ W) {
+                                                 const TIn *__restrict__ Y, float *__restrict__ W,
+                                                 const int *__restrict__ dcnt) {
   constexpr int COLS = 8;
   __shared__ float ys[32][COLS];
   const int k = blockIdx.x;
   const int c0 = blockIdx.y * COLS;
+  if (dcnt) ncols = min(ncols, 2 * *dcnt);
+  if (c0 >= ncols) return;
   const int t = threadIdx.x;
   const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
   float acc[COLS];
@@ -102,11 +107,14 @@ __global__ void __launch_bounds__(128) lp_beta(int ncols, int nb, int n_occ, int
                                                const int4 *__restrict__ adj,
                                                const float *__restrict__ W,
                                                const float *__restrict__ Xo,
-                                               __nv_bfloat16 *__restrict__ betaT) {
+                                               __nv_bfloat16 *__restrict__ betaT,
+                                               const int *__restrict__ dcnt) {
   constexpr int COLS = 4;
   __shared__ float Ws[COLS][kMaxOrb][kMaxOrb + 1];
   const int A = blockIdx.x;
   const int c0 = blockIdx.y * COLS;
+  if (dcnt) ncols = min(ncols, 2 * *dcnt);
+  if (c0 >= ncols) return;
   const int aoA = aoff[A], nA = aoff[A + 1] - aoA;
   const int e0 = adj_ptr[A], e1 = adj_ptr[A + 1];
   for (int E0 = 0; E0 < n_occ; E0 += 128) {
@@ -170,8 +178,11 @@ __global__ void __launch_bounds__(256) lp_sddmm(int ncols, int n_occ, int n_prod
                                                 const float *__restrict__ Xo,
                                                 const float *__restrict__ gammaT,
                                                 const double *__restrict__ Zin, int subtract,
-                                                double *__restrict__ Out) {
+                                                double *__restrict__ Out,
+                                                const int *__restrict__ dcnt) {
   constexpr int COLS = 4, EC = 32;
+  if (dcnt) ncols = min(ncols, 2 * *dcnt);
+  if ((int)blockIdx.y * COLS >= ncols) return;
   __shared__ float XA[kMaxOrb][EC + 1], XB[kMaxOrb][EC + 1];
   __shared__ float gA[COLS][kMaxOrb][EC + 1], gB[COLS][kMaxOrb][EC + 1];
   __shared__ float Gs[COLS][kBlk];
@@ -277,14 +288,14 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     {
       Scope sc(lp.timer, st, kcLpSplit, 0.0);
       split_rows_kernel<<<grid_for((int64_t)ncols * lp.KpK, 256), 256, 0, st>>>(
-          Zin, np, 1, ncols, np, lp.KpK, lp.Zb);
+          Zin, np, 1, ncols, np, lp.KpK, lp.Zb, lp.dcnt, 2);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     {
       Scope sc(lp.timer, st, kcTcK, 2.0 * ncols * (double)np * np);
       ep.outF = lp.Yt;
       ep.ldo = np;
-      err = launch_gemm_tc(st, lp.opK, lp.opZ, np, ncols, kStoreF32, ep, lp.err);
+      err = launch_gemm_tc(st, lp.opK, lp.opZ, np, ncols, kStoreF32, ep, lp.err, lp.dcnt, 2);
       if (err != cudaSuccess) return err;
     }
   }
@@ -293,17 +304,17 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     dim3 grid(sys.n_blocks, (ncols + 7) / 8);
     if (mode == kA)
       lp_vertex<float><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
-                                             lp.Vpad32, lp.Yt, lp.W);
+                                             lp.Vpad32, lp.Yt, lp.W, lp.dcnt);
     else
       lp_vertex<double><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
-                                              lp.Vpad32, Zin, lp.W);
+                                              lp.Vpad32, Zin, lp.W, lp.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   {
     Scope sc(lp.timer, st, kcLpBeta, ncols * sys.sf.beta);
     dim3 grid(sys.n_atoms, (ncols + 3) / 4);
     lp_beta<<<grid, 128, 0, st>>>(ncols, sys.n_blocks, sys.n_occ, lp.Kp1, sys.aoff, sys.adj_ptr,
-                                  sys.adj, lp.W, lp.Xo32, lp.betaT);
+                                  sys.adj, lp.W, lp.Xo32, lp.betaT, lp.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)N1;
@@ -319,7 +330,8 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     e1.eps = eps;
     e1.occ_value = sys.occ_value;
     e1.n_occ = sys.n_occ;
-    err = launch_gemm_tc(st, lp.opXvT, lp.opBeta, sys.n_virt, (int)N1, kDscaleSplit, e1, lp.err);
+    err = launch_gemm_tc(st, lp.opXvT, lp.opBeta, sys.n_virt, (int)N1, kDscaleSplit, e1, lp.err,
+                         lp.dcnt, 2 * sys.n_occ);
     if (err != cudaSuccess) return err;
   }
   {
@@ -327,7 +339,8 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     TcEpilogue e2;
     e2.outF = lp.gammaT;
     e2.ldo = sys.n_orb;
-    err = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kStoreF32, e2, lp.err);
+    err = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kStoreF32, e2, lp.err, lp.dcnt,
+                         2 * sys.n_occ);
     if (err != cudaSuccess) return err;
   }
   {
@@ -335,7 +348,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     dim3 grid(sys.n_blocks, (ncols + 3) / 4);
     lp_sddmm<<<grid, 256, 0, st>>>(ncols, sys.n_occ, np, sys.n_orb, sys.aoff, sys.blk_atoms,
                                    sys.blk_ptr, sys.blk_prod, lp.Vpad32, lp.Xo32, lp.gammaT, Zin,
-                                   mode == kA ? 1 : 0, Out);
+                                   mode == kA ? 1 : 0, Out, lp.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   return cudaSuccess;

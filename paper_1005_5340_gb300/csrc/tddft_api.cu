@@ -21,6 +21,7 @@ struct tddft_ctx {
   Timer timer;
   tddft_options opts{};
   cudaStream_t st = nullptr;
+  cudaStream_t gst = nullptr;  // private stream for graph capture and replay
   double *Zc = nullptr;     // [2S][n_prod] operator input (planar)
   double *Wout = nullptr;   // [2S][n_prod] operator output (planar)
   double *stage = nullptr;  // [2S][n_prod] interleaved staging for boundary calls
@@ -72,6 +73,8 @@ bool all_finite(const double *p, size_t n) {
 
 void release(tddft_ctx *c) {
   c->timer.destroy();
+  if (c->gst) cudaStreamDestroy(c->gst);
+  c->gst = nullptr;
   for (void *p : c->dev_allocs) cudaFree(p);
   c->dev_allocs.clear();
   if (c->h_count) cudaFreeHost(c->h_count);
@@ -320,6 +323,22 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
       Xv[(size_t)a * nv + F] = x;
     }
   }
+  std::vector<float> pfeat(2 * (size_t)np);
+  {
+    double mean = 0.0;
+    std::vector<double> nrm(np);
+    for (int mu = 0; mu < np; ++mu) {
+      const int64_t a0 = s->vertex_offset[mu], a1 = s->vertex_offset[mu + 1];
+      double q = 0.0;
+      for (int64_t i = a0; i < a1; ++i) q += s->vertex[i] * s->vertex[i];
+      nrm[mu] = std::sqrt(q);
+      mean += nrm[mu] / np;
+    }
+    for (int mu = 0; mu < np; ++mu) {
+      pfeat[2 * mu] = s->prod_atoms[2 * mu] != s->prod_atoms[2 * mu + 1] ? 1.f : 0.f;
+      pfeat[2 * mu + 1] = mean > 0.0 ? (float)(nrm[mu] / mean) : 0.f;
+    }
+  }
   std::vector<int> aoffv(ao, ao + d.n_atoms + 1);
   std::vector<double> energy(s->eigenvalues, s->eigenvalues + no);
   std::vector<double> dip(s->dipole, s->dipole + 3 * (size_t)np);
@@ -338,6 +357,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   UP(d.Vpad, Vpad);
   UP(d.adj_ptr, adj_ptr);
   UP(d.adj, adj);
+  UP(d.pfeat, pfeat);
 #undef UP
   if (e == cudaSuccess) e = dev_alloc(c, &d.K, (size_t)np * np);
   if (e == cudaSuccess)
@@ -366,6 +386,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   g.max_restarts = o->max_restarts;
   g.tol = o->tol;
   AL(g.state, S); AL(g.jcur, S); AL(g.cycles, S); AL(g.matvecs, S); AL(g.conv, S);
+  AL(g.flags, S);
   AL(g.bnorm, S); AL(g.resid, S); AL(g.omega, S);
   AL(g.H, S * (m + 1) * m); AL(g.cs, S * m); AL(g.sn, S * m); AL(g.g, S * (m + 1));
   AL(g.V, S * (m + 1) * 2 * np); AL(g.x, S * 2 * np); AL(g.b, S * 2 * np);
@@ -405,6 +426,8 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   }
 #undef AL
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_count, 2 * sizeof(int));
+  if (e == cudaSuccess && o->graph) e = cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking);
+  if (e == cudaSuccess) tc_init_attributes();
   if (e != cudaSuccess) {
     std::string m2 = std::string("device allocation/upload failed: ") + cudaGetErrorString(e);
     release(c);
@@ -507,8 +530,95 @@ tddft_status tddft_apply_A(tddft_ctx *c, int32_t n_rhs, const double *omega, dou
   return boundary_apply(c, kA, n_rhs, omega, eps, z, out, flags);
 }
 
+static tddft_status polarizability_impl(tddft_ctx *c, int32_t n_omega, const double *omega,
+                                        double eps, const double *x0, double *Xout, double *P,
+                                        tddft_solve_stats *stats, int32_t flags);
+
 tddft_status tddft_polarizability(tddft_ctx *c, int32_t n_omega, const double *omega, double eps,
                                   double *P, tddft_solve_stats *stats, int32_t flags) {
+  return polarizability_impl(c, n_omega, omega, eps, nullptr, nullptr, P, stats, flags);
+}
+
+tddft_status tddft_polarizability_guess(tddft_ctx *c, int32_t n_omega, const double *omega,
+                                        double eps, const double *x0, double *X, double *P,
+                                        tddft_solve_stats *stats, int32_t flags) {
+  if (c && !(flags & TDDFT_DEVICE_PTRS) && (x0 || X))
+    return fail(c, TDDFT_ERR_INVALID_ARG, "x0 and X must be device pointers (flags bit 0)");
+  return polarizability_impl(c, n_omega, omega, eps, x0, X, P, stats, flags);
+}
+
+// One GMRES iteration of a group of n right-hand sides, captured once in a
+// CUDA graph on the private stream and replayed: launch shapes are those of
+// n live right-hand sides and every kernel reads the live counts on the
+// device, so no host decision is needed between iterations.  The host reads
+// the counts back every kReplays launches.
+// Enqueue one device-driven GMRES iteration of context c's current group of
+// n right-hand sides on stream gs (no host decision, no synchronisation).
+static cudaError_t enqueue_iteration(tddft_ctx *c, cudaStream_t gs, int n, double eps, int split,
+                                     int min_b) {
+  GmresState &g = c->gs;
+  OpWork wk = c->wk;
+  LpWork lp = c->lp;
+  wk.timer = nullptr;
+  lp.timer = nullptr;
+  wk.dcnt = g.count + (split ? 1 : 0);
+  lp.dcnt = g.count;
+  cudaError_t e = launch_gmres_select(gs, g, n, split, min_b);
+  if (split) {
+    if (e == cudaSuccess) e = launch_gmres_gather(gs, c->sys, g, g.act, n, c->Zc, lp.omega, g.count);
+    if (e == cudaSuccess) e = launch_apply_operator_lp(gs, c->sys, lp, n, kA, eps, c->Zc, c->Wout);
+    if (e == cudaSuccess) e = launch_gmres_step(gs, c->sys, g, g.act, n, c->Wout, g.count);
+    if (e == cudaSuccess)
+      e = launch_gmres_gather(gs, c->sys, g, g.act2, n, c->Zc, wk.omega, g.count + 1);
+    if (e == cudaSuccess) e = launch_apply_operator(gs, c->sys, wk, n, kA, eps, c->Zc, c->Wout);
+    if (e == cudaSuccess) e = launch_gmres_step(gs, c->sys, g, g.act2, n, c->Wout, g.count + 1);
+  } else {
+    if (e == cudaSuccess) e = launch_gmres_gather(gs, c->sys, g, g.act, n, c->Zc, wk.omega, g.count);
+    if (e == cudaSuccess) e = launch_apply_operator(gs, c->sys, wk, n, kA, eps, c->Zc, c->Wout);
+    if (e == cudaSuccess) e = launch_gmres_step(gs, c->sys, g, g.act, n, c->Wout, g.count);
+  }
+  return e;
+}
+
+static tddft_status run_group_graph(tddft_ctx *c, int n, double eps, int split, int min_b,
+                                    long max_iter) {
+  constexpr int kReplays = 4;
+  GmresState &g = c->gs;
+  cudaStream_t gs = c->gst;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct Cleanup {
+    cudaGraph_t &g; cudaGraphExec_t &e;
+    ~Cleanup() { if (e) cudaGraphExecDestroy(e); if (g) cudaGraphDestroy(g); }
+  } cleanup{graph, exec};
+  CUDA_TRY(c, cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_iteration(c, gs, n, eps, split, min_b);
+  cudaError_t e2 = cudaStreamEndCapture(gs, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(c, TDDFT_ERR_CUDA, std::string("graph capture failed: ") +
+                                       cudaGetErrorString(e != cudaSuccess ? e : e2));
+  CUDA_TRY(c, cudaGraphInstantiate(&exec, graph, 0));
+  for (long it = 0;; it += kReplays) {
+    if (it > max_iter + kReplays)
+      return fail(c, TDDFT_ERR_TIMEOUT, "GMRES driver exceeded its iteration bound");
+    for (int r = 0; r < kReplays; ++r) CUDA_TRY(c, cudaGraphLaunch(exec, gs));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_count, g.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, gs));
+    CUDA_TRY(c, cudaStreamSynchronize(gs));
+    if (c->h_count[0] <= 0 && c->h_count[1] <= 0) {
+      // the counts of the last replay's selection; one more selection confirms
+      CUDA_TRY(c, launch_gmres_select(gs, g, n, split, min_b));
+      CUDA_TRY(c, cudaMemcpyAsync(c->h_count, g.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, gs));
+      CUDA_TRY(c, cudaStreamSynchronize(gs));
+      if (c->h_count[0] <= 0 && c->h_count[1] <= 0) break;
+    }
+  }
+  return TDDFT_OK;
+}
+
+static tddft_status polarizability_impl(tddft_ctx *c, int32_t n_omega, const double *omega,
+                                        double eps, const double *x0, double *Xout, double *P,
+                                        tddft_solve_stats *stats, int32_t flags) {
   if (!c) return TDDFT_ERR_INVALID_ARG;
   c->err.clear();
   if (n_omega < 1) return fail(c, TDDFT_ERR_SHAPE, "n_omega must be >= 1");
@@ -533,7 +643,7 @@ tddft_status tddft_polarizability(tddft_ctx *c, int32_t n_omega, const double *o
                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
 
   bool all_conv = true;
-  std::vector<int> h_mv(S), h_cy(S), h_cv(S);
+  std::vector<int> h_mv(S), h_cy(S), h_cv(S), h_fl(S);
   std::vector<double> h_res(S);
   const long max_iter = (long)(g.max_restarts + 1) * (g.m + 1) + 4;
   for (int g0 = 0; g0 < total; g0 += S) {
@@ -542,45 +652,55 @@ tddft_status tddft_polarizability(tddft_ctx *c, int32_t n_omega, const double *o
     CUDA_TRY(c, launch_rhs_formation(st, c->sys, c->wk, n, g0, d_omega, eps, c->Z3, c->a3,
                                      c->Wout));
     CUDA_TRY(c, launch_gmres_start(st, c->sys, g, n, c->Wout));
+    if (x0) CUDA_TRY(c, launch_gmres_guess(st, c->sys, g, n, g0, x0));
     long it = 0;
     const int split = c->lowprec ? 1 : 0;
-    for (;; ++it) {
-      if (it > max_iter)
-        return fail(c, TDDFT_ERR_TIMEOUT, "GMRES driver exceeded its iteration bound");
-      {
-        TimedLaunch tl(c->timer, st, kcGmresSelect);
-        CUDA_TRY(c, launch_gmres_select(st, g, n, split));
-      }
-      CUDA_TRY(c, cudaMemcpyAsync(c->h_count, g.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CUDA_TRY(c, cudaStreamSynchronize(st));
-      const int cntA = c->h_count[0], cntB = c->h_count[1];
-      if (cntA <= 0 && cntB <= 0) break;
-      if (cntA > 0) {
-        // Arnoldi steps (reduced precision in the refinement forms)
+    // Float64 residuals that end a refinement cycle are batched: while reduced-
+    // precision Arnoldi work remains, right-hand sides awaiting their residual
+    // wait until enough of them have gathered to fill the float64 GEMM tiles.
+    const int min_b = split ? std::max(1, std::min(32, n / 4)) : 1;
+    if (c->opts.graph && !c->timer.on) {
+      tddft_status gs_ = run_group_graph(c, n, eps, split, min_b, max_iter);
+      if (gs_ != TDDFT_OK) return gs_;
+    } else {
+      for (;; ++it) {
+        if (it > max_iter)
+          return fail(c, TDDFT_ERR_TIMEOUT, "GMRES driver exceeded its iteration bound");
         {
-          TimedLaunch tl(c->timer, st, kcGmresGather);
-          CUDA_TRY(c, launch_gmres_gather(st, c->sys, g, g.act, cntA, c->Zc,
-                                          split ? c->lp.omega : c->wk.omega));
+          TimedLaunch tl(c->timer, st, kcGmresSelect);
+          CUDA_TRY(c, launch_gmres_select(st, g, n, split, min_b));
         }
-        if (split)
-          CUDA_TRY(c, launch_apply_operator_lp(st, c->sys, c->lp, cntA, kA, eps, c->Zc, c->Wout));
-        else
-          CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, cntA, kA, eps, c->Zc, c->Wout));
-        {
-          TimedLaunch tl(c->timer, st, kcGmresStep);
-          CUDA_TRY(c, launch_gmres_step(st, c->sys, g, g.act, cntA, c->Wout));
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_count, g.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaStreamSynchronize(st));
+        const int cntA = c->h_count[0], cntB = c->h_count[1];
+        if (cntA <= 0 && cntB <= 0) break;
+        if (cntA > 0) {
+          // Arnoldi steps (reduced precision in the refinement forms)
+          {
+            TimedLaunch tl(c->timer, st, kcGmresGather);
+            CUDA_TRY(c, launch_gmres_gather(st, c->sys, g, g.act, cntA, c->Zc,
+                                            split ? c->lp.omega : c->wk.omega));
+          }
+          if (split)
+            CUDA_TRY(c, launch_apply_operator_lp(st, c->sys, c->lp, cntA, kA, eps, c->Zc, c->Wout));
+          else
+            CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, cntA, kA, eps, c->Zc, c->Wout));
+          {
+            TimedLaunch tl(c->timer, st, kcGmresStep);
+            CUDA_TRY(c, launch_gmres_step(st, c->sys, g, g.act, cntA, c->Wout));
+          }
         }
-      }
-      if (cntB > 0) {
-        // float64 residuals that end a refinement cycle
-        {
-          TimedLaunch tl(c->timer, st, kcGmresGather);
-          CUDA_TRY(c, launch_gmres_gather(st, c->sys, g, g.act2, cntB, c->Zc, c->wk.omega));
-        }
-        CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, cntB, kA, eps, c->Zc, c->Wout));
-        {
-          TimedLaunch tl(c->timer, st, kcGmresStep);
-          CUDA_TRY(c, launch_gmres_step(st, c->sys, g, g.act2, cntB, c->Wout));
+        if (cntB > 0) {
+          // float64 residuals that end a refinement cycle
+          {
+            TimedLaunch tl(c->timer, st, kcGmresGather);
+            CUDA_TRY(c, launch_gmres_gather(st, c->sys, g, g.act2, cntB, c->Zc, c->wk.omega));
+          }
+          CUDA_TRY(c, launch_apply_operator(st, c->sys, c->wk, cntB, kA, eps, c->Zc, c->Wout));
+          {
+            TimedLaunch tl(c->timer, st, kcGmresStep);
+            CUDA_TRY(c, launch_gmres_step(st, c->sys, g, g.act2, cntB, c->Wout));
+          }
         }
       }
     }
@@ -589,10 +709,12 @@ tddft_status tddft_polarizability(tddft_ctx *c, int32_t n_omega, const double *o
       if (se != TDDFT_OK) return se;
     }
     CUDA_TRY(c, launch_polarization(st, c->sys, g, n, g0, d_P));
+    if (Xout) CUDA_TRY(c, launch_gmres_export(st, c->sys, g, n, g0, Xout));
     CUDA_TRY(c, cudaMemcpyAsync(h_mv.data(), g.matvecs, n * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaMemcpyAsync(h_cy.data(), g.cycles, n * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaMemcpyAsync(h_cv.data(), g.conv, n * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaMemcpyAsync(h_res.data(), g.resid, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(h_fl.data(), g.flags, n * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
     c->timer.resolve();
     for (int r = 0; r < n; ++r) {
@@ -603,7 +725,7 @@ tddft_status tddft_polarizability(tddft_ctx *c, int32_t n_omega, const double *o
         t.cycles = h_cy[r];
         t.resid = h_res[r];
         t.converged = h_cv[r];
-        t.pad = 0;
+        t.flags = h_fl[r];
       }
     }
   }
@@ -643,4 +765,232 @@ namespace tddft {
 const DevSystem *ctx_system(const tddft_ctx *c) { return &c->sys; }
 cudaStream_t ctx_stream(const tddft_ctx *c) { return c->st; }
 void ctx_set_error(tddft_ctx *c, const char *msg) { c->err = msg; }
+const float *ctx_product_features(const tddft_ctx *c) { return c->sys.pfeat; }
 }  // namespace tddft
+
+// ---------------------------------------------------------------------------
+// Several molecules solved together
+// ---------------------------------------------------------------------------
+struct tddft_batch {
+  std::vector<tddft_ctx *> ctx;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t main = nullptr;
+  int *h_counts = nullptr;   // pinned [2 n_mol]
+  std::string err;
+};
+
+namespace {
+thread_local std::string g_batch_error;
+
+tddft_status bfail(tddft_batch *b, tddft_status s, const std::string &msg) {
+  if (b) b->err = msg;
+  else g_batch_error = msg;
+  return s;
+}
+
+void batch_release(tddft_batch *b) {
+  for (auto *c : b->ctx) tddft_destroy(c);
+  b->ctx.clear();
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  b->streams.clear();
+  if (b->main) cudaStreamDestroy(b->main);
+  b->main = nullptr;
+  if (b->h_counts) cudaFreeHost(b->h_counts);
+  b->h_counts = nullptr;
+}
+
+#define BCUDA(b, expr)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return bfail(b, TDDFT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+}  // namespace
+
+extern "C" {
+
+tddft_status tddft_batch_create(int32_t n_mol, const tddft_system *systems,
+                                const tddft_options *opts, tddft_batch **out) {
+  g_batch_error.clear();
+  if (!out || !systems || !opts || n_mol < 1)
+    return bfail(nullptr, TDDFT_ERR_INVALID_ARG, "need n_mol >= 1, systems, options and out");
+  *out = nullptr;
+  tddft_batch *b = new tddft_batch();
+  cudaError_t e = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_counts, 2 * sizeof(int) * n_mol);
+  if (e != cudaSuccess) {
+    batch_release(b);
+    delete b;
+    return bfail(nullptr, TDDFT_ERR_CUDA, cudaGetErrorString(e));
+  }
+  for (int i = 0; i < n_mol; ++i) {
+    cudaStream_t s = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      batch_release(b);
+      delete b;
+      return bfail(nullptr, TDDFT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    b->streams.push_back(s);
+    tddft_options o = *opts;
+    o.stream = s;
+    o.graph = 0;
+    tddft_ctx *c = nullptr;
+    tddft_status st = tddft_create(&systems[i], &o, &c);
+    if (st != TDDFT_OK) {
+      std::string m = "molecule " + std::to_string(i) + ": " + tddft_last_error(nullptr);
+      batch_release(b);
+      delete b;
+      return bfail(nullptr, st, m);
+    }
+    b->ctx.push_back(c);
+  }
+  *out = b;
+  return TDDFT_OK;
+}
+
+void tddft_batch_destroy(tddft_batch *b) {
+  if (!b) return;
+  batch_release(b);
+  delete b;
+}
+
+const char *tddft_batch_last_error(const tddft_batch *b) {
+  return b ? b->err.c_str() : g_batch_error.c_str();
+}
+
+tddft_ctx *tddft_batch_context(tddft_batch *b, int32_t i) {
+  if (!b || i < 0 || i >= (int)b->ctx.size()) return nullptr;
+  return b->ctx[i];
+}
+
+tddft_status tddft_batch_polarizability(tddft_batch *b, int32_t n_omega, const double *omega,
+                                        double eps, double *P, tddft_solve_stats *stats) {
+  if (!b) return TDDFT_ERR_INVALID_ARG;
+  b->err.clear();
+  if (n_omega < 1 || !omega || !P) return bfail(b, TDDFT_ERR_INVALID_ARG, "bad omega or P");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return bfail(b, TDDFT_ERR_INVALID_ARG, "eps must be > 0");
+  if (!all_finite(omega, (size_t)n_omega))
+    return bfail(b, TDDFT_ERR_INVALID_ARG, "omega holds NaN or Inf");
+  const int nm = (int)b->ctx.size();
+  const int total = 3 * n_omega;
+  constexpr int kReplays = 4;
+  std::vector<double *> d_omega(nm, nullptr);
+  std::vector<double2 *> d_P(nm, nullptr);
+  struct Free {
+    std::vector<double *> &a; std::vector<double2 *> &p;
+    ~Free() { for (auto x : a) cudaFree(x); for (auto x : p) cudaFree(x); }
+  } fr{d_omega, d_P};
+  int rounds = 0;
+  for (int i = 0; i < nm; ++i) {
+    tddft_ctx *c = b->ctx[i];
+    BCUDA(b, cudaMalloc(&d_omega[i], n_omega * sizeof(double)));
+    BCUDA(b, cudaMalloc(&d_P[i], (size_t)n_omega * 9 * sizeof(double2)));
+    BCUDA(b, cudaMemcpyAsync(d_omega[i], omega, n_omega * sizeof(double), cudaMemcpyHostToDevice,
+                             c->st));
+    rounds = std::max(rounds, (total + c->wk.slots - 1) / c->wk.slots);
+  }
+  std::vector<cudaEvent_t> ev(nm + 1, nullptr);
+  struct EvFree {
+    std::vector<cudaEvent_t> &e;
+    ~EvFree() { for (auto x : e) if (x) cudaEventDestroy(x); }
+  } efr{ev};
+  for (auto &x : ev) BCUDA(b, cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+  bool all_conv = true;
+  const long max_iter = 1000000;
+  for (int r = 0; r < rounds; ++r) {
+    std::vector<int> act, g0v, nv, splitv, minbv;
+    for (int i = 0; i < nm; ++i) {
+      tddft_ctx *c = b->ctx[i];
+      const int S = c->wk.slots, g0 = r * S;
+      if (g0 >= total) continue;
+      const int n = std::min(S, total - g0);
+      GmresState &g = c->gs;
+      const int split = c->lowprec ? 1 : 0;
+      act.push_back(i);
+      g0v.push_back(g0);
+      nv.push_back(n);
+      splitv.push_back(split);
+      minbv.push_back(split ? std::max(1, std::min(32, n / 4)) : 1);
+      // right-hand sides of this round, on the molecule's stream
+      BCUDA(b, launch_rhs_init(c->st, c->sys, n, g0, d_omega[i], c->Zc, c->wk.omega, g.omega));
+      BCUDA(b, launch_rhs_formation(c->st, c->sys, c->wk, n, g0, d_omega[i], eps, c->Z3, c->a3,
+                                    c->Wout));
+      BCUDA(b, launch_gmres_start(c->st, c->sys, g, n, c->Wout));
+      BCUDA(b, cudaEventRecord(ev[i], c->st));
+      BCUDA(b, cudaStreamWaitEvent(b->main, ev[i], 0));
+    }
+    // one graph per round: a branch per molecule, each one GMRES iteration
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    struct GFree {
+      cudaGraph_t &g; cudaGraphExec_t &e;
+      ~GFree() { if (e) cudaGraphExecDestroy(e); if (g) cudaGraphDestroy(g); }
+    } gfr{graph, exec};
+    BCUDA(b, cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaEventRecord(ev[nm], b->main);
+    for (size_t a = 0; a < act.size() && ce == cudaSuccess; ++a) {
+      tddft_ctx *c = b->ctx[act[a]];
+      ce = cudaStreamWaitEvent(c->st, ev[nm], 0);
+      if (ce == cudaSuccess) ce = enqueue_iteration(c, c->st, nv[a], eps, splitv[a], minbv[a]);
+      if (ce == cudaSuccess) ce = cudaEventRecord(ev[act[a]], c->st);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->main, ev[act[a]], 0);
+    }
+    cudaError_t ce2 = cudaStreamEndCapture(b->main, &graph);
+    if (ce != cudaSuccess || ce2 != cudaSuccess)
+      return bfail(b, TDDFT_ERR_CUDA, std::string("graph capture failed: ") +
+                                          cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+    BCUDA(b, cudaGraphInstantiate(&exec, graph, 0));
+    for (long it = 0;; it += kReplays) {
+      if (it > max_iter) return bfail(b, TDDFT_ERR_TIMEOUT, "batch driver exceeded its bound");
+      for (int k = 0; k < kReplays; ++k) BCUDA(b, cudaGraphLaunch(exec, b->main));
+      for (size_t a = 0; a < act.size(); ++a)
+        BCUDA(b, cudaMemcpyAsync(b->h_counts + 2 * a, b->ctx[act[a]]->gs.count, 2 * sizeof(int),
+                                 cudaMemcpyDeviceToHost, b->main));
+      BCUDA(b, cudaStreamSynchronize(b->main));
+      bool live = false;
+      for (size_t a = 0; a < act.size(); ++a)
+        live = live || b->h_counts[2 * a] > 0 || b->h_counts[2 * a + 1] > 0;
+      if (!live) break;
+    }
+    // results of the round
+    for (size_t a = 0; a < act.size(); ++a) {
+      const int i = act[a];
+      tddft_ctx *c = b->ctx[i];
+      GmresState &g = c->gs;
+      const int n = nv[a], g0 = g0v[a];
+      BCUDA(b, launch_polarization(c->st, c->sys, g, n, g0, d_P[i]));
+      std::vector<int> mv(n), cy(n), cv(n), fl(n);
+      std::vector<double> rs(n);
+      BCUDA(b, cudaMemcpyAsync(mv.data(), g.matvecs, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      BCUDA(b, cudaMemcpyAsync(cy.data(), g.cycles, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      BCUDA(b, cudaMemcpyAsync(cv.data(), g.conv, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      BCUDA(b, cudaMemcpyAsync(fl.data(), g.flags, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      BCUDA(b, cudaMemcpyAsync(rs.data(), g.resid, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      BCUDA(b, cudaStreamSynchronize(c->st));
+      if (check_device_error(c) != TDDFT_OK)
+        return bfail(b, TDDFT_ERR_TIMEOUT, "molecule " + std::to_string(i) + ": " + c->err);
+      for (int q = 0; q < n; ++q) {
+        if (!cv[q]) all_conv = false;
+        if (stats) {
+          tddft_solve_stats &t = stats[(size_t)i * total + g0 + q];
+          t.matvecs = mv[q];
+          t.cycles = cy[q];
+          t.resid = rs[q];
+          t.converged = cv[q];
+          t.flags = fl[q];
+        }
+      }
+    }
+  }
+  for (int i = 0; i < nm; ++i) {
+    tddft_ctx *c = b->ctx[i];
+    BCUDA(b, cudaMemcpyAsync(P + (size_t)i * n_omega * 18, d_P[i], (size_t)n_omega * 9 * sizeof(double2),
+                             cudaMemcpyDeviceToHost, c->st));
+    BCUDA(b, cudaStreamSynchronize(c->st));
+  }
+  if (!all_conv) return bfail(b, TDDFT_ERR_NOT_CONVERGED, "some (molecule, omega, direction) missed tol");
+  return TDDFT_OK;
+}
+
+}  // extern "C"

@@ -200,8 +200,14 @@ def make_system(n_atoms: int, seed: int, *, orb_per_atom: int = 13, occ_per_atom
     vertex = np.concatenate([b.ravel() for b in blocks])
 
     if with_K:
-        d2 = np.sum((centres[:, None, :] - centres[None, :, :]) ** 2, axis=-1)
-        K = 1.0 / np.sqrt(d2 + 1.0)
+        # row blocks keep the temporaries small for tens of thousands of products
+        K = np.empty((n_prod, n_prod))
+        for r0 in range(0, n_prod, 2048):
+            r1 = min(n_prod, r0 + 2048)
+            d2 = np.zeros((r1 - r0, n_prod))
+            for ax in range(3):
+                d2 += (centres[r0:r1, ax, None] - centres[None, :, ax]) ** 2
+            K[r0:r1] = 1.0 / np.sqrt(d2 + 1.0)
         K[np.diag_indices(n_prod)] += 0.05
     else:
         K = np.zeros((0, 0))

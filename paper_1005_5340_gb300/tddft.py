@@ -42,13 +42,13 @@ class _Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("batch", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("graph", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("matvecs", ctypes.c_int32), ("cycles", ctypes.c_int32),
                 ("resid", ctypes.c_double), ("converged", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
 
 
 # Every exported symbol with its ctypes signature (checked by the tests
@@ -66,7 +66,28 @@ SIGNATURES = {
                                      ctypes.c_int32]),
     "tddft_polarizability": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
                                             ctypes.c_int32]),
+    "tddft_polarizability_guess": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P,
+                                                  _P, _P, _P, ctypes.c_int32]),
     "tddft_sizes": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "tddft_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "tddft_batch_polarizability": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P]),
+    "tddft_batch_context": (ctypes.c_void_p, [_P, ctypes.c_int32]),
+    "tddft_batch_last_error": (ctypes.c_char_p, [_P]),
+    "tddft_batch_destroy": (None, [_P]),
+    "tddft_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int64, ctypes.c_uint64, _P,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "tddft_mlp_destroy": (None, [_P]),
+    "tddft_mlp_last_error": (ctypes.c_char_p, [_P]),
+    "tddft_mlp_num_params": (ctypes.c_int64, [_P]),
+    "tddft_mlp_params": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32]),
+    "tddft_mlp_forward": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int32]),
+    "tddft_mlp_backward": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
+    "tddft_mlp_train_step": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                                            _P, ctypes.c_float]),
+    "tddft_guess_features": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
+                                            _P, _P, _P, _P]),
+    "tddft_guess_combine": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P, _P]),
     "tddft_timing_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "tddft_timing_count": (ctypes.c_int32, [_P]),
     "tddft_timing_get": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
@@ -105,28 +126,36 @@ def _c(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+def _marshal(system):
+    """A _System pointing into contiguous copies (returned too, to keep them alive)."""
+    keep = dict(
+        aoff=_c(system.atom_orb_offset, np.int32), E=_c(system.eigenvalues, np.float64),
+        occ=_c(system.occupations, np.float64),
+        X=np.asfortranarray(system.X, dtype=np.float64),
+        pa=_c(system.prod_atoms, np.int32), voff=_c(system.vertex_offset, np.int64),
+        v=_c(system.vertex, np.float64), K=_c(system.K, np.float64),
+        d=_c(system.dipole, np.float64))
+    s = _System(int(system.n_atoms), keep["aoff"].ctypes.data, int(keep["E"].size),
+                keep["E"].ctypes.data, keep["occ"].ctypes.data, keep["X"].ctypes.data,
+                int(keep["pa"].shape[0]), keep["pa"].ctypes.data, keep["voff"].ctypes.data,
+                keep["v"].ctypes.data, keep["K"].ctypes.data, keep["d"].ctypes.data)
+    return s, keep
+
+
 class Context:
     """One molecule resident on the GPU (tddft_create .. tddft_destroy)."""
 
     def __init__(self, system, *, restart: int = 40, max_restarts: int = 200, tol: float = 1e-6,
-                 batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4, stream=None):
+                 batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4, stream=None,
+                 graph: bool = False):
         lib = load_library()
         self._lib = lib
-        keep = dict(
-            aoff=_c(system.atom_orb_offset, np.int32), E=_c(system.eigenvalues, np.float64),
-            occ=_c(system.occupations, np.float64),
-            X=np.asfortranarray(system.X, dtype=np.float64),
-            pa=_c(system.prod_atoms, np.int32), voff=_c(system.vertex_offset, np.int64),
-            v=_c(system.vertex, np.float64), K=_c(system.K, np.float64),
-            d=_c(system.dipole, np.float64))
-        s = _System(int(system.n_atoms), keep["aoff"].ctypes.data, int(keep["E"].size),
-                    keep["E"].ctypes.data, keep["occ"].ctypes.data, keep["X"].ctypes.data,
-                    int(keep["pa"].shape[0]), keep["pa"].ctypes.data, keep["voff"].ctypes.data,
-                    keep["v"].ctypes.data, keep["K"].ctypes.data, keep["d"].ctypes.data)
+        s, keep = _marshal(system)
         if stream is None:
             stream = _current_stream()
         self.stream_handle = stream
-        o = _Options(PREC[prec], restart, max_restarts, tol, batch, stream or 0, inner_tol)
+        o = _Options(PREC[prec], restart, max_restarts, tol, batch, stream or 0, inner_tol,
+                     1 if graph else 0)
         self.prec = prec
         h = ctypes.c_void_p()
         st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
@@ -214,6 +243,48 @@ class Context:
         """z_r - chi0(omega_r) K z_r for each row r of z."""
         return self._apply(self._lib.tddft_apply_A, z, omega, eps, True)
 
+    def polarizability_guess(self, omega, eps, x0=None, want_x: bool = True, *,
+                             raise_on_nonconvergence: bool = True):
+        """Like polarizability, on CUDA tensors, with optional initial guesses
+        x0 (n_omega*3 x n_prod complex, row w*3+k) and the solutions returned
+        (same layout) when want_x.  Returns (P, X or None, stats)."""
+        import torch
+        om = torch.as_tensor(omega, dtype=torch.float64).cuda().contiguous()
+        n = om.numel()
+        P = torch.empty((n, 3, 3), dtype=torch.complex128, device=om.device)
+        X = torch.empty((3 * n, self.n_prod), dtype=torch.complex128, device=om.device) \
+            if want_x else None
+        if x0 is not None:
+            x0 = x0.to(torch.complex128).contiguous()
+            assert x0.shape == (3 * n, self.n_prod)
+        stats = (SolveStats * (3 * n))()
+        st = self._lib.tddft_polarizability_guess(
+            self.h, n, om.data_ptr(), float(eps),
+            torch.view_as_real(x0).data_ptr() if x0 is not None else None,
+            torch.view_as_real(X).data_ptr() if X is not None else None,
+            torch.view_as_real(P).data_ptr(), stats, DEVICE_PTRS)
+        if st != OK and not (st == ERR_NOT_CONVERGED and not raise_on_nonconvergence):
+            self._check(st)
+        return P, X, _stats_dict(stats, n)
+
+    def guess_features(self, nb, t, omega, direction, h_over_eps, X):
+        """Features F, interpolation lin and scale of the targets (CUDA tensors)."""
+        import torch
+        dev = X.device
+        nb = torch.as_tensor(nb, dtype=torch.int32, device=dev).contiguous()
+        t = torch.as_tensor(t, dtype=torch.float64, device=dev).contiguous()
+        om = torch.as_tensor(omega, dtype=torch.float64, device=dev).contiguous()
+        dr = torch.as_tensor(direction, dtype=torch.int32, device=dev).contiguous()
+        nt = t.numel()
+        F = torch.empty((nt * self.n_prod, 10), dtype=torch.float32, device=dev)
+        lin = torch.empty((nt, self.n_prod), dtype=torch.complex128, device=dev)
+        scale = torch.empty(nt, dtype=torch.float64, device=dev)
+        self._check(self._lib.tddft_guess_features(
+            self.h, nt, nb.data_ptr(), t.data_ptr(), om.data_ptr(), dr.data_ptr(),
+            float(h_over_eps), torch.view_as_real(X.contiguous()).data_ptr(), F.data_ptr(),
+            torch.view_as_real(lin).data_ptr(), scale.data_ptr()))
+        return F, lin, scale
+
     def polarizability(self, omega, eps, *, raise_on_nonconvergence: bool = True):
         """P[w, i, k] (complex, n_omega x 3 x 3) and per-(w, k) stats."""
         if _is_torch(omega) and omega.is_cuda:
@@ -234,12 +305,7 @@ class Context:
                                                 P.ctypes.data, stats, 0)
         if st != OK and not (st == ERR_NOT_CONVERGED and not raise_on_nonconvergence):
             self._check(st)
-        info = dict(
-            matvecs=np.array([s.matvecs for s in stats]).reshape(n, 3),
-            cycles=np.array([s.cycles for s in stats]).reshape(n, 3),
-            resid=np.array([s.resid for s in stats]).reshape(n, 3),
-            converged=np.array([s.converged for s in stats], dtype=bool).reshape(n, 3))
-        return P, info
+        return P, _stats_dict(stats, n)
 
     # -- timing ---------------------------------------------------------------
     def timing_enable(self, on: bool = True):
@@ -256,6 +322,141 @@ class Context:
                                                    ctypes.byref(ms), ctypes.byref(fl)))
             res[name.value.decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value)
         return res
+
+
+class Batch:
+    """Several molecules solved together (tddft_batch_*)."""
+
+    def __init__(self, systems, *, restart: int = 40, max_restarts: int = 200, tol: float = 1e-6,
+                 batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4):
+        lib = load_library()
+        self._lib = lib
+        marsh = [_marshal(s) for s in systems]
+        arr = (_System * len(systems))(*[m[0] for m in marsh])
+        o = _Options(PREC[prec], restart, max_restarts, tol, batch, None, inner_tol, 0)
+        h = ctypes.c_void_p()
+        st = lib.tddft_batch_create(len(systems), arr, ctypes.byref(o), ctypes.byref(h))
+        if st != OK:
+            raise TddftError(st, lib.tddft_batch_last_error(None).decode())
+        self.h = h
+        self.n_mol = len(systems)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.tddft_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def polarizability(self, omega, eps, *, raise_on_nonconvergence: bool = True):
+        """P [n_mol, n_omega, 3, 3] complex and stats [n_mol, n_omega, 3]."""
+        om = np.ascontiguousarray(np.atleast_1d(omega), dtype=np.float64)
+        n = om.size
+        P = np.empty((self.n_mol, n, 3, 3), dtype=np.complex128)
+        stats = (SolveStats * (3 * n * self.n_mol))()
+        st = self._lib.tddft_batch_polarizability(self.h, n, om.ctypes.data, float(eps),
+                                                  P.ctypes.data, stats)
+        if st != OK and not (st == ERR_NOT_CONVERGED and not raise_on_nonconvergence):
+            raise TddftError(st, self._lib.tddft_batch_last_error(self.h).decode())
+        d = _stats_dict(stats, n * self.n_mol)
+        return P, {k: v.reshape(self.n_mol, n, 3) for k, v in d.items()}
+
+
+def _stats_dict(stats, n):
+    return dict(
+        matvecs=np.array([s.matvecs for s in stats]).reshape(n, 3),
+        cycles=np.array([s.cycles for s in stats]).reshape(n, 3),
+        resid=np.array([s.resid for s in stats]).reshape(n, 3),
+        converged=np.array([s.converged for s in stats], dtype=bool).reshape(n, 3),
+        guess_rejected=np.array([s.flags & 1 for s in stats], dtype=bool).reshape(n, 3))
+
+
+class Mlp:
+    """The guess network (tddft_mlp_*): parameters and training live on the GPU."""
+
+    def __init__(self, n_in=10, width=256, n_out=2, max_rows=1 << 20, seed=0, stream=None):
+        lib = load_library()
+        self._lib = lib
+        h = ctypes.c_void_p()
+        st = lib.tddft_mlp_create(n_in, width, n_out, max_rows, seed,
+                                  stream if stream is not None else _current_stream(),
+                                  ctypes.byref(h))
+        if st != OK:
+            raise TddftError(st, lib.tddft_mlp_last_error(None).decode())
+        self.h = h
+        self.n_in, self.width, self.n_out, self.max_rows = n_in, width, n_out, max_rows
+        self.n_params = lib.tddft_mlp_num_params(h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.tddft_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise TddftError(st, self._lib.tddft_mlp_last_error(self.h).decode())
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.n_params, dtype=np.float32)
+        self._check(self._lib.tddft_mlp_params(self.h, p.ctypes.data, self.n_params, 0))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self._lib.tddft_mlp_params(self.h, p.ctypes.data, self.n_params, 1))
+
+    def forward(self, F, bf16: bool = False):
+        import torch
+        F = F.contiguous()
+        Y = torch.empty((F.shape[0], self.n_out), dtype=torch.float32, device=F.device)
+        self._check(self._lib.tddft_mlp_forward(self.h, F.shape[0], F.data_ptr(), Y.data_ptr(),
+                                                1 if bf16 else 0))
+        return Y
+
+    def backward(self, F, dY) -> np.ndarray:
+        g = np.empty(self.n_params, dtype=np.float32)
+        self._check(self._lib.tddft_mlp_backward(self.h, F.shape[0], F.contiguous().data_ptr(),
+                                                 dY.contiguous().data_ptr(), g.ctypes.data))
+        return g
+
+    def train_step(self, F, lin, xstar, scale, lr: float):
+        import torch
+        nt, n_prod = lin.shape
+        loss = torch.empty(nt, dtype=torch.float64, device=lin.device)
+        self._check(self._lib.tddft_mlp_train_step(
+            self.h, nt, n_prod, F.contiguous().data_ptr(),
+            torch.view_as_real(lin.contiguous()).data_ptr(),
+            torch.view_as_real(xstar.contiguous()).data_ptr(), scale.contiguous().data_ptr(),
+            loss.data_ptr(), float(lr)))
+        return loss
+
+    def combine(self, Y, lin, scale):
+        import torch
+        nt, n_prod = lin.shape
+        x0 = torch.empty_like(lin)
+        st = self._lib.tddft_guess_combine(nt, n_prod, Y.contiguous().data_ptr(),
+                                           torch.view_as_real(lin.contiguous()).data_ptr(),
+                                           scale.contiguous().data_ptr(),
+                                           torch.view_as_real(x0).data_ptr(), _current_stream())
+        if st != OK:
+            raise TddftError(st, "tddft_guess_combine failed")
+        return x0
 
 
 def selftest_gemm(M: int, N: int, K: int, seed: int = 1) -> float:

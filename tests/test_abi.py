@@ -41,7 +41,8 @@ def _create(sysm, **opt):
                       keep["pa"].ctypes.data, keep["voff"].ctypes.data, keep["v"].ctypes.data,
                       keep["K"].ctypes.data, keep["d"].ctypes.data)
     o = tddft._Options(opt.get("prec", 0), opt.get("restart", 10), opt.get("max_restarts", 5),
-                       opt.get("tol", 1e-8), opt.get("batch", 4), None, opt.get("inner_tol", 1e-4))
+                       opt.get("tol", 1e-8), opt.get("batch", 4), None, opt.get("inner_tol", 1e-4),
+                       opt.get("graph", 0))
     h = ctypes.c_void_p()
     st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
     return st, lib.tddft_last_error(None).decode(), h

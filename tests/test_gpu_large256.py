@@ -1,0 +1,66 @@
+"""The precision form at full size: the 256-atom molecule (n_orb 3328,
+n_occ 512, about 35k products, K about 9.9 GB).  Sampled operator products
+against the oracle's five-step operator, and Im alpha(omega) of the
+refinement form against the float64 path on a fixed subset of the 512-point
+grid (every 64th frequency, 3 directions), with the error reported."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle.tddft_oracle as O
+from paper_1005_5340_gb300 import synth
+from tests.libutil import ensure_library
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def large():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_library()
+    return synth.workload("large256")
+
+
+def T():
+    from paper_1005_5340_gb300 import tddft
+    return tddft
+
+
+def test_large256_operator_samples(large):
+    s, w = large
+    op = O.StepOperator(s)
+    omegas = np.array([0.1, 0.9])
+    z = synth.random_complex_vectors(2, s.n_prod, 31)
+    with T().Context(s, batch=2) as ctx:
+        chi = ctx.chi0_apply(z, omegas, w["eps"])
+    with T().Context(s, batch=2, prec="bf16x3") as ctx:
+        chi_lp = ctx.chi0_apply(z, omegas, w["eps"])
+    for r, x in enumerate(omegas):
+        ref = op.apply(z[r], x, w["eps"])
+        e64 = np.max(np.abs(chi[r] - ref)) / np.max(np.abs(ref))
+        elp = np.max(np.abs(chi_lp[r] - ref)) / np.max(np.abs(ref))
+        assert e64 < 1e-12 and elp < 1e-4, (e64, elp)
+
+
+def test_large256_im_alpha_of_the_refinement_form(large):
+    s, w = large
+    om = w["omega"][::64]
+    out = {}
+    for prec in ("bf16x3", "fp64"):
+        with T().Context(s, batch=3 * om.size, restart=w["restart"], tol=w["tol"],
+                         prec=prec) as ctx:
+            t0 = time.perf_counter()
+            P, info = ctx.polarizability(om, w["eps"])
+            dt = time.perf_counter() - t0
+        assert info["converged"].all() and np.all(info["resid"] <= w["tol"])
+        out[prec] = (P, dt, info)
+    im_lp = np.einsum("wii->wi", -out["bf16x3"][0]).imag
+    im_64 = np.einsum("wii->wi", -out["fp64"][0]).imag
+    err = np.max(np.abs(im_lp - im_64)) / np.max(np.abs(im_64))
+    print(f"large256 subset ({om.size} omega x 3): Im alpha normwise error {err:.2e}; "
+          f"bf16x3 {out['bf16x3'][1]:.1f} s ({out['bf16x3'][2]['matvecs'].mean():.1f} products/RHS),"
+          f" fp64 {out['fp64'][1]:.1f} s ({out['fp64'][2]['matvecs'].mean():.1f} products/RHS)")
+    assert err < 1e-4
