@@ -218,6 +218,14 @@ tddft_status tddft_polarizability_guess(tddft_ctx *ctx, int32_t n_omega, const d
                                         double eps, const double *x0, double *X, double *P,
                                         tddft_solve_stats *stats, int32_t flags);
 
+/*
+ * Tile shapes chosen by the autotuner of a refinement-form context: at
+ * create, each tensor-core product (K z, X_virt^T beta, X_virt a) is timed
+ * with 128- and 64-wide N tiles on the context's full batch and the faster
+ * is kept.  n_tiles[0..2] receive the widths (0 for a float64 context).
+ */
+tddft_status tddft_tuning(const tddft_ctx *ctx, int32_t *n_tiles);
+
 /* Sizes of a context (any pointer may be NULL). */
 tddft_status tddft_sizes(const tddft_ctx *ctx, int32_t *n_orb, int32_t *n_occ, int32_t *n_prod,
                          int32_t *n_blocks);
@@ -241,7 +249,8 @@ tddft_status tddft_timing_get(tddft_ctx *ctx, int32_t i, const char **name, int3
  * Self-test of the split-bf16 tensor-core GEMM used by TDDFT_PREC_BF16X3_IR:
  * C^T = A B^T for deterministic pseudo-random A [M x K], B [N x K] (entries
  * uniform in [-1, 1) from a hash of (index, seed)), compared with a float64
- * product of the same operands.  *max_rel_err = max |C - C_ref| / max |C_ref|.
+ * product of the same operands, for both N-tile widths (128 and 64).
+ * *max_rel_err = max |C - C_ref| / max |C_ref| over both.
  * Allocates and frees its own device buffers; synchronises the device.
  * Returns TIMEOUT if a bounded wait inside the GEMM gave up.
  */

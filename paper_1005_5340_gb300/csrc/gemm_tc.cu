@@ -26,12 +26,17 @@
 namespace tddft {
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 3;
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;    // 16 KB
-constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK * 2;    // 16 KB
-constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr size_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
+// The N tile (TMEM columns, B box rows, MMA N) is a template parameter: 128
+// (2 CTAs per SM) or 64 (3 CTAs per SM), chosen per product by the autotuner.
+template <int BN> struct TcShape {
+  static constexpr uint32_t B_BYTES = BN * TC_BK * 2;
+  static constexpr uint32_t STAGE_BYTES = TC_A_BYTES + B_BYTES;
+  static constexpr size_t SMEM = TC_STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int MIN_CTAS = BN == 64 ? 3 : 2;
+};
 constexpr uint64_t kWaitLimitNs = 2000000000ull;      // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -132,14 +137,15 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(TC_THREADS, 2)
+template <int EPI, int TC_BN>
+__global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int M, int N, int Kp, int nseg, int4 segs, TcEpilogue ep, int *err,
                    const int *dcnt, int mul_n) {
   // graph replays: columns beyond the live count are skipped (whole CTAs)
   if (dcnt) N = (int)min((int64_t)N, (int64_t)mul_n * (*dcnt));
   if ((int)blockIdx.y * TC_BN >= N) return;
+  constexpr uint32_t TC_STAGE_BYTES = TcShape<TC_BN>::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -310,54 +316,65 @@ cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int 
   if (Kp % TC_BK != 0 || ((uintptr_t)base & 15) != 0) return cudaErrorInvalidValue;
   cuuint64_t dims[2] = {(cuuint64_t)(2 * Kp), (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(2 * Kp) * 2};
-  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(&op.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
-                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  for (int which = 0; which < 2; ++which) {
+    // box_rows for the A role (128) or the 128-wide B tile; 64 for the 64-wide B tile
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)(which == 0 ? box_rows : 64)};
+    CUresult r = fn(which == 0 ? &op.map : &op.map64, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  op.has64 = true;
   op.rows = rows;
   op.Kp = Kp;
   return cudaSuccess;
 }
 
+template <int EPI, int BN>
+void set_attr() {
+  cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TcShape<BN>::SMEM);
+}
+
 void tc_init_attributes() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(gemm_tc_kernel<kStoreF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TC_SMEM);
-  cudaFuncSetAttribute(gemm_tc_kernel<kDscaleSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TC_SMEM);
+  set_attr<kStoreF32, 128>();
+  set_attr<kDscaleSplit, 128>();
+  set_attr<kStoreF32, 64>();
+  set_attr<kDscaleSplit, 64>();
   done = true;
 }
 
-cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
-                           int epi, const TcEpilogue &ep, int *err, const int *dcnt, int mul_n) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  if (A.Kp != B.Kp) return cudaErrorInvalidValue;
-  static bool attr_set[2] = {false, false};
-  dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN);
+template <int EPI, int BN>
+cudaError_t launch_tc(cudaStream_t st, const CUtensorMap &mA, const CUtensorMap &mB, int M, int N,
+                      int Kp, const TcEpilogue &ep, int *err, const int *dcnt, int mul_n) {
+  dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   // segments: A_hi B_hi, A_hi B_lo, A_lo B_hi  (low byte: A plane, next byte: B plane)
   const int4 segs = make_int4(0 | (0 << 8), 0 | (1 << 8), 1 | (0 << 8), 0);
-  if (epi == kStoreF32) {
-    if (!attr_set[0]) {
-      cudaFuncSetAttribute(gemm_tc_kernel<kStoreF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)TC_SMEM);
-      attr_set[0] = true;
-    }
-    gemm_tc_kernel<kStoreF32><<<grid, TC_THREADS, TC_SMEM, st>>>(A.map, B.map, M, N, A.Kp, 3, segs,
-                                                                  ep, err, dcnt, mul_n);
-  } else {
-    if (!attr_set[1]) {
-      cudaFuncSetAttribute(gemm_tc_kernel<kDscaleSplit>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-      attr_set[1] = true;
-    }
-    gemm_tc_kernel<kDscaleSplit><<<grid, TC_THREADS, TC_SMEM, st>>>(A.map, B.map, M, N, A.Kp, 3,
-                                                                     segs, ep, err, dcnt, mul_n);
-  }
+  gemm_tc_kernel<EPI, BN><<<grid, TC_THREADS, TcShape<BN>::SMEM, st>>>(mA, mB, M, N, Kp, 3, segs,
+                                                                         ep, err, dcnt, mul_n);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
+                           int epi, const TcEpilogue &ep, int *err, const int *dcnt, int mul_n,
+                           int bn) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (A.Kp != B.Kp) return cudaErrorInvalidValue;
+  tc_init_attributes();
+  if (bn == 64) {
+    if (!B.has64) return cudaErrorInvalidValue;
+    return epi == kStoreF32
+               ? launch_tc<kStoreF32, 64>(st, A.map, B.map64, M, N, A.Kp, ep, err, dcnt, mul_n)
+               : launch_tc<kDscaleSplit, 64>(st, A.map, B.map64, M, N, A.Kp, ep, err, dcnt, mul_n);
+  }
+  return epi == kStoreF32
+             ? launch_tc<kStoreF32, 128>(st, A.map, B.map, M, N, A.Kp, ep, err, dcnt, mul_n)
+             : launch_tc<kDscaleSplit, 128>(st, A.map, B.map, M, N, A.Kp, ep, err, dcnt, mul_n);
 }
 
 }  // namespace tddft
@@ -399,7 +416,8 @@ __global__ void st_ref(int M, int N, int K, const double *A, const double *B, co
     const int n = (int)(i / M), m = (int)(i % M);
     double acc = 0.0;
     for (int k = 0; k < K; ++k) acc = fma(A[(int64_t)m * K + k], B[(int64_t)n * K + k], acc);
-    const double d = fabs((double)C[(int64_t)n * M + m] - acc);
+    double d = fabs((double)C[(int64_t)n * M + m] - acc);
+    if (!(d == d)) d = 1e300;   // an unwritten (NaN) entry is a failure
     atomicMax((unsigned long long *)&err2[0], __double_as_longlong(d));
     atomicMax((unsigned long long *)&err2[1], __double_as_longlong(fabs(acc)));
   }
@@ -433,15 +451,19 @@ extern "C" tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uin
     e = make_operand_map(*opA, As, M, Kp, 128);
     if (e == cudaSuccess) e = make_operand_map(*opB, Bs, N, Kp, 128);
   }
-  if (e == cudaSuccess) {
-    TcEpilogue ep;
-    ep.outF = C;
-    ep.ldo = M;
-    e = launch_gemm_tc(0, *opA, *opB, M, N, kStoreF32, ep, err);
-  }
-  if (e == cudaSuccess) {
-    st_ref<<<304, 256>>>(M, N, K, A, B, C, e2);
-    e = cudaDeviceSynchronize();
+  // both N-tile widths, each checked against the float64 product
+  for (int bn : {128, 64}) {
+    if (e == cudaSuccess) {
+      cudaMemset(C, 0xFF, (size_t)N * M * sizeof(float));   // NaN: unwritten entries fail
+      TcEpilogue ep;
+      ep.outF = C;
+      ep.ldo = M;
+      e = launch_gemm_tc(0, *opA, *opB, M, N, kStoreF32, ep, err, nullptr, 0, bn);
+    }
+    if (e == cudaSuccess) {
+      st_ref<<<304, 256>>>(M, N, K, A, B, C, e2);
+      e = cudaDeviceSynchronize();
+    }
   }
   if (e == cudaSuccess) {
     double h[2];

@@ -119,7 +119,9 @@ enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1 };
 
 // A bf16 operand [rows][2*Kp] ([hi | lo] planes) with its TMA descriptor.
 struct TcOperand {
-  CUtensorMap map;
+  CUtensorMap map;     // boxes of 64 x 128 rows
+  CUtensorMap map64;   // boxes of 64 x 64 rows (the B operand of the 64-wide tile)
+  bool has64 = false;
   int64_t rows = 0;
   int Kp = 0;
 };
@@ -139,9 +141,10 @@ struct TcEpilogue {
 
 cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows);
 // dcnt (may be NULL): columns beyond mul_n * (*dcnt) are skipped.
+// bn: N tile of the kernel, 128 or 64.
 cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
                            int epi, const TcEpilogue &ep, int *err, const int *dcnt = nullptr,
-                           int mul_n = 0);
+                           int mul_n = 0, int bn = 128);
 void tc_init_attributes();
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -163,11 +166,14 @@ struct LpWork {
   double *omega = nullptr;         // [S]
   int *err = nullptr;              // [1] device-side error code of the GEMM waits
   TcOperand opK, opXvT, opXv, opZ, opBeta, opA;
+  int bnK = 128, bn1 = 128, bn2 = 128;   // N tiles chosen by the autotuner
   Timer *timer = nullptr;
   const int *dcnt = nullptr;  // graph replays: device count of live slots (NULL: all S)
 };
 
 cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &lp);
+// Time both N tiles on this context's three products (full batch) and keep the faster.
+cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp);
 // Out[c][mu] (float64) = Zin - chi0 K Zin (kA) or chi0 Zin (kChi0), reduced precision.
 cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWork &lp, int S,
                                      OpMode mode, double eps, const double *Zin, double *Out);

@@ -274,6 +274,71 @@ cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &
   return cudaGetLastError();
 }
 
+cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
+  // The workspace holds zeros here; timing does not depend on the values.
+  const int S = lp.slots, ncols = 2 * S;
+  const int64_t N1 = (int64_t)ncols * sys.n_occ;
+  if (N1 > INT32_MAX) return cudaErrorInvalidValue;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  auto time_one = [&](int which, int bn, float &ms) -> cudaError_t {
+    TcEpilogue ep;
+    cudaError_t r = cudaSuccess;
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && r == cudaSuccess; ++rep) {
+      r = cudaEventRecord(a, st);
+      if (which == 0) {
+        ep.outF = lp.Yt;
+        ep.ldo = sys.n_prod;
+        if (r == cudaSuccess)
+          r = launch_gemm_tc(st, lp.opK, lp.opZ, sys.n_prod, ncols, kStoreF32, ep, lp.err, nullptr,
+                             0, bn);
+      } else if (which == 1) {
+        ep.outB = lp.aT;
+        ep.ldo = 2 * (int64_t)lp.Kp2;
+        ep.lo_off = lp.Kp2;
+        ep.rows_out = lp.Kp2;
+        ep.energy = sys.energy;
+        ep.omega = lp.omega;
+        ep.eps = 0.01;
+        ep.occ_value = sys.occ_value;
+        ep.n_occ = sys.n_occ;
+        if (r == cudaSuccess)
+          r = launch_gemm_tc(st, lp.opXvT, lp.opBeta, sys.n_virt, (int)N1, kDscaleSplit, ep, lp.err,
+                             nullptr, 0, bn);
+      } else {
+        ep.outF = lp.gammaT;
+        ep.ldo = sys.n_orb;
+        if (r == cudaSuccess)
+          r = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kStoreF32, ep, lp.err,
+                             nullptr, 0, bn);
+      }
+      if (r == cudaSuccess) r = cudaEventRecord(b, st);
+      if (r == cudaSuccess) r = cudaEventSynchronize(b);
+      float t = 0.f;
+      if (r == cudaSuccess) r = cudaEventElapsedTime(&t, a, b);
+      if (rep > 0) best = fminf(best, t);   // first launch is a warm-up
+    }
+    ms = best;
+    return r;
+  };
+  int *pick[3] = {&lp.bnK, &lp.bn1, &lp.bn2};
+  for (int which = 0; which < 3 && e == cudaSuccess; ++which) {
+    float t128 = 0.f, t64 = 0.f;
+    e = time_one(which, 128, t128);
+    if (e == cudaSuccess) e = time_one(which, 64, t64);
+    if (e == cudaSuccess) *pick[which] = (t64 < t128) ? 64 : 128;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  // the timing runs wrote the workspace; the pads of aT must be zero again
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(lp.aT, 0, (size_t)N1 * 2 * lp.Kp2 * sizeof(__nv_bfloat16), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(lp.err, 0, sizeof(int), st);
+  return e;
+}
+
 cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWork &lp, int S,
                                      OpMode mode, double eps, const double *Zin, double *Out) {
   if (S <= 0) return cudaSuccess;
@@ -295,7 +360,8 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
       Scope sc(lp.timer, st, kcTcK, 2.0 * ncols * (double)np * np);
       ep.outF = lp.Yt;
       ep.ldo = np;
-      err = launch_gemm_tc(st, lp.opK, lp.opZ, np, ncols, kStoreF32, ep, lp.err, lp.dcnt, 2);
+      err = launch_gemm_tc(st, lp.opK, lp.opZ, np, ncols, kStoreF32, ep, lp.err, lp.dcnt, 2,
+                           lp.bnK);
       if (err != cudaSuccess) return err;
     }
   }
@@ -331,7 +397,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     e1.occ_value = sys.occ_value;
     e1.n_occ = sys.n_occ;
     err = launch_gemm_tc(st, lp.opXvT, lp.opBeta, sys.n_virt, (int)N1, kDscaleSplit, e1, lp.err,
-                         lp.dcnt, 2 * sys.n_occ);
+                         lp.dcnt, 2 * sys.n_occ, lp.bn1);
     if (err != cudaSuccess) return err;
   }
   {
@@ -340,7 +406,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     e2.outF = lp.gammaT;
     e2.ldo = sys.n_orb;
     err = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kStoreF32, e2, lp.err, lp.dcnt,
-                         2 * sys.n_occ);
+                         2 * sys.n_occ, lp.bn2);
     if (err != cudaSuccess) return err;
   }
   {

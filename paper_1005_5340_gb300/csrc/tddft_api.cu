@@ -422,6 +422,8 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     if (e == cudaSuccess) e = make_operand_map(L.opBeta, L.betaT, (int64_t)rows1, L.Kp1, 128);
     if (e == cudaSuccess) e = make_operand_map(L.opA, L.aT, (int64_t)rows1, L.Kp2, 128);
     if (e == cudaSuccess) e = lp_prepare_constants(c->st, d, L);
+    if (e == cudaSuccess) tc_init_attributes();
+    if (e == cudaSuccess) e = lp_autotune(c->st, d, L);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   }
 #undef AL
@@ -447,6 +449,14 @@ void tddft_destroy(tddft_ctx *c) {
 
 const char *tddft_last_error(const tddft_ctx *c) {
   return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+tddft_status tddft_tuning(const tddft_ctx *c, int32_t *n_tiles) {
+  if (!c || !n_tiles) return TDDFT_ERR_INVALID_ARG;
+  n_tiles[0] = c->lowprec ? c->lp.bnK : 0;
+  n_tiles[1] = c->lowprec ? c->lp.bn1 : 0;
+  n_tiles[2] = c->lowprec ? c->lp.bn2 : 0;
+  return TDDFT_OK;
 }
 
 tddft_status tddft_sizes(const tddft_ctx *c, int32_t *n_orb, int32_t *n_occ, int32_t *n_prod,

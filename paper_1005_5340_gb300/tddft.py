@@ -69,6 +69,7 @@ SIGNATURES = {
     "tddft_polarizability_guess": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P,
                                                   _P, _P, _P, ctypes.c_int32]),
     "tddft_sizes": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "tddft_tuning": (ctypes.c_int, [_P, _P]),
     "tddft_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "tddft_batch_polarizability": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P]),
     "tddft_batch_context": (ctypes.c_void_p, [_P, ctypes.c_int32]),
@@ -306,6 +307,12 @@ class Context:
         if st != OK and not (st == ERR_NOT_CONVERGED and not raise_on_nonconvergence):
             self._check(st)
         return P, _stats_dict(stats, n)
+
+    def tuning(self):
+        """N-tile widths the autotuner chose for (K z, transform 1, transform 2)."""
+        t = (ctypes.c_int32 * 3)()
+        self._check(self._lib.tddft_tuning(self.h, t))
+        return tuple(t)
 
     # -- timing ---------------------------------------------------------------
     def timing_enable(self, on: bool = True):
