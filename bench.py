@@ -425,10 +425,69 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """The uneven batch: 32 molecules of 8-128 atoms solved together (one graph
+    per round with a branch per molecule); a step is omega_per_step frequencies
+    x 3 directions for every molecule.  Also times the molecules one after the
+    other through single contexts on one step for comparison."""
+    import torch
+    from paper_1005_5340_gb300 import tddft
+    torch.cuda.set_device(0)
+    mols = synth.batch_molecules()
+    eps, tol, restart = 0.005, 1e-6, 40
+    per = args.omega_per_step
+    omega = synth.omega_grid(per * max(1, args.steps), 1.5)
+    groups = [omega[i::max(1, args.steps)] for i in range(max(1, args.steps))]
+    b = tddft.Batch(mols, batch=3 * per, restart=restart, tol=tol, prec=args.prec,
+                    inner_tol=args.inner_tol)
+    for i in range(args.warmup):
+        b.polarizability(groups[i % len(groups)], eps)
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    t0 = time.perf_counter()
+    mv = 0
+    for i in range(args.steps):
+        P, st = b.polarizability(groups[i], eps)
+        mv += int(st["matvecs"].sum())
+    dt = time.perf_counter() - t0
+    clocks = clk.stop()
+    b.close()
+    points = len(mols) * per * args.steps
+    # the same molecules one at a time (single contexts, host-driven), one step
+    seq_time = 0.0
+    for s in mols:
+        with tddft.Context(s, batch=3 * per, restart=restart, tol=tol, prec=args.prec,
+                           inner_tol=args.inner_tol) as ctx:
+            ctx.polarizability(groups[0][:1], eps)       # warm the context
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            ctx.polarizability(groups[0], eps)
+            seq_time += time.perf_counter() - a
+    seq_rate = len(mols) * per / seq_time
+    print(json.dumps({
+        "metric": METRIC, "value": points / dt, "unit": "omega-points/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f64" if args.prec == "bf16x3" else "f64", "data": "synthetic",
+        "config": {"workload": f"batch32: 32 molecules of {min(x.n_atoms for x in mols)}-"
+                               f"{max(x.n_atoms for x in mols)} atoms (sizes log-uniform 8-128), "
+                               f"{per} omega x 3 directions each per step, eps {eps}, "
+                               f"GMRES({restart}) tol {tol}",
+                   "precision": args.prec, "parallelism": "one graph per round, a branch per molecule"},
+        "matvecs_per_rhs": mv / (3 * points), "clocks": clocks,
+        "one_molecule_at_a_time": {"value": seq_rate, "unit": "omega-points/s",
+                                   "speedup_of_batch": (points / dt) / seq_rate},
+        "roofline": None, "e2e": None, "cpu_baseline": None,
+    }), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch32":
+        run_batch(args)
     else:
         run_ours(args)
 

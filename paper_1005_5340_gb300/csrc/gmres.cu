@@ -255,10 +255,19 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
 
   const int j = G.jcur[r];
   double *w = Vr + (int64_t)(j + 1) * 2 * N;
-  for (int e = tid; e < 2 * N; e += NT) w[e] = win[e];
+  double n0[1] = {0.0};
+  for (int e = tid; e < 2 * N; e += NT) {
+    const double t = win[e];
+    w[e] = t;
+    n0[0] += t * t;
+  }
   for (int i = tid; i <= j; i += NT) hs[i] = make_double2(0.0, 0.0);
-  __syncthreads();
+  block_sum<1>(n0, red);   // ||A v_j||^2 (the block sum synchronises)
+  double hn = 0.0;
 
+  // Classical Gram-Schmidt with selective reorthogonalisation: the second
+  // pass runs only when the first one removed more than half of ||w||^2
+  // (the Daniel-Gragg-Kaufman-Stewart criterion with eta = 1/sqrt(2)).
   for (int pass = 0; pass < 2; ++pass) {
     // h_i = <v_i, w> for i <= j, eight at a time
     for (int i0 = 0; i0 <= j; i0 += 8) {
@@ -281,7 +290,8 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
       if (tid < 8 && i0 + tid <= j) hp[i0 + tid] = make_double2(part[2 * tid], part[2 * tid + 1]);
     }
     __syncthreads();
-    // w -= sum_i h_i v_i
+    // w -= sum_i h_i v_i, with the new ||w||^2
+    double n1[1] = {0.0};
     for (int e = tid; e < N; e += NT) {
       double ar = 0.0, ai = 0.0;
       for (int i = 0; i <= j; ++i) {
@@ -291,16 +301,17 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
         ar += h.x * vr - h.y * vi;
         ai += h.x * vi + h.y * vr;
       }
-      w[e] -= ar;
-      w[N + e] -= ai;
+      const double nr = w[e] - ar, ni = w[N + e] - ai;
+      w[e] = nr;
+      w[N + e] = ni;
+      n1[0] += nr * nr + ni * ni;
     }
     for (int i = tid; i <= j; i += NT) hs[i] = make_double2(hs[i].x + hp[i].x, hs[i].y + hp[i].y);
-    __syncthreads();
+    block_sum<1>(n1, red);   // synchronises: w and hs complete
+    hn = sqrt(n1[0]);
+    if (n1[0] > 0.5 * n0[0]) break;   // uniform across the CTA
+    n0[0] = n1[0];
   }
-  double n2[1] = {0.0};
-  for (int e = tid; e < 2 * N; e += NT) n2[0] += w[e] * w[e];
-  block_sum<1>(n2, red);
-  const double hn = sqrt(n2[0]);
 
   if (tid == 0) {
     double2 *Hc = G.H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);

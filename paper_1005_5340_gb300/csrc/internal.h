@@ -107,6 +107,11 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
 cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S, int g0,
                                  const double *omega_all, double eps, double *Z3, double *a3,
                                  double *Out);
+// Step 5 (block dots) for ncols real columns: float64 (gamma [n_orb][ncols][n_occ],
+// Vpad/Xo double) or float32 (gamma^T [(s n_occ+E) 2+p][n_orb], Vpad/Xo float).
+cudaError_t launch_block_dot(cudaStream_t st, bool f64, int ncols, const DevSystem &sys,
+                             const void *Vpad, const void *Xo, const void *gamma,
+                             const double *Zin, int subtract, double *Out, const int *dcnt);
 cudaError_t launch_interleaved_to_planar(cudaStream_t st, int n_rhs, int n, const double *in,
                                          double *out);
 cudaError_t launch_planar_to_interleaved(cudaStream_t st, int n_rhs, int n, const double *in,

@@ -6,7 +6,7 @@
 //   beta    = W(y) X_occ                                 (steps 1+2)
 //   a       = X_virt^T beta,  a^{FE} *= D_EF(omega)      (step 3 + denominator)
 //   gamma   = X_virt a                                   (step 4)
-//   n_mu    = sum_ab V_mu^{ab} (X_occ gamma^T)^{ab}      (step 5)
+//   n_mu    = sum_ab V_mu^{ab} (X_occ gamma^T)^{ab}      (step 5, blockdot.cu)
 // Complex vectors are kept as two real planes; X, V and K are real, so only
 // the D(omega) scaling mixes the planes.
 #include "internal.h"
@@ -15,23 +15,28 @@ namespace tddft {
 
 // ---------------------------------------------------------------------------
 // C[M x N] = A[M x K] . B[K x N], all row-major float64 (DFMA).
-// 64 x 64 tile per CTA, 16-deep K slices staged in shared memory, 4 x 4
-// outputs per thread.  Every edge is bounds-checked (ragged M, N, K).
+// BM x BN tile per CTA (64 x 64, or 32 x 128 when M is small so that few rows
+// of the tile are wasted), 16-deep K slices staged in shared memory through
+// registers (double buffered), (BM/16) x (BN/16) outputs per thread on a
+// 16 x 16 thread grid.  Every edge is bounds-checked (ragged M, N, K).
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+constexpr int GB_K = 16;
 
-__global__ void __launch_bounds__(256) gemm_f64_nn(int M, int N, int K, const double *__restrict__ A,
+template <int BM, int BN>
+__global__ void __launch_bounds__(256, (BM == 32 ? 2 : 3)) gemm_f64_nn(int M, int N, int K, const double *__restrict__ A,
                                                    int64_t lda, const double *__restrict__ B,
                                                    int64_t ldb, double *__restrict__ C,
                                                    int64_t ldc, const int *__restrict__ dcnt,
                                                    int mul_m, int mul_n) {
-  __shared__ double As[2][GB_K][GB_M + 2];
-  __shared__ double Bs[2][GB_K][GB_N];
+  constexpr int TM = BM / 16, TN = BN / 16;     // outputs per thread
+  constexpr int LA = BM * GB_K / 256, LB = BN * GB_K / 256;   // loads per thread
+  __shared__ double As[2][GB_K][BM + 2];
+  __shared__ double Bs[2][GB_K][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int64_t m0 = (int64_t)blockIdx.y * GB_M;
-  const int64_t n0 = (int64_t)blockIdx.x * GB_N;
+  const int64_t m0 = (int64_t)blockIdx.y * BM;
+  const int64_t n0 = (int64_t)blockIdx.x * BN;
   if (dcnt) {
     // graph replays: the live extent is read on the device
     const int c = *dcnt;
@@ -39,33 +44,41 @@ __global__ void __launch_bounds__(256) gemm_f64_nn(int M, int N, int K, const do
     if (mul_n) N = (int)min((int64_t)N, (int64_t)mul_n * c);
   }
   if (m0 >= M || n0 >= N) return;
-  double acc[4][4];
+  double acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
 
-  double ra[4], rb[4];
+  double ra[LA], rb[LB];
   auto load_regs = [&](int k0) {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      int idx = tid + 256 * l;
-      int i = idx >> 4, kk = idx & 15;                       // A: 64 rows x 16 k
-      int64_t gm = m0 + i;
-      int gk = k0 + kk;
+    for (int l = 0; l < LA; ++l) {
+      const int idx = tid + 256 * l;
+      const int i = idx >> 4, kk = idx & 15;                  // A: BM rows x 16 k
+      const int64_t gm = m0 + i;
+      const int gk = k0 + kk;
       ra[l] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.0;
-      int kb = idx >> 6, j = idx & 63;                       // B: 16 k x 64 cols
-      int64_t gn = n0 + j;
-      int gkb = k0 + kb;
+    }
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int idx = tid + 256 * l;
+      const int kb = idx / BN, j = idx % BN;                  // B: 16 k x BN cols
+      const int64_t gn = n0 + j;
+      const int gkb = k0 + kb;
       rb[l] = (gn < N && gkb < K) ? B[(int64_t)gkb * ldb + gn] : 0.0;
     }
   };
   auto store_smem = [&](int buf) {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      int idx = tid + 256 * l;
+    for (int l = 0; l < LA; ++l) {
+      const int idx = tid + 256 * l;
       As[buf][idx & 15][idx >> 4] = ra[l];
-      Bs[buf][idx >> 6][idx & 63] = rb[l];
+    }
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int idx = tid + 256 * l;
+      Bs[buf][idx / BN][idx % BN] = rb[l];
     }
   };
 
@@ -80,26 +93,26 @@ __global__ void __launch_bounds__(256) gemm_f64_nn(int M, int N, int K, const do
     if (t + 1 < nk) load_regs((t + 1) * GB_K);
 #pragma unroll
     for (int kk = 0; kk < GB_K; ++kk) {
-      double a[4], b[4];
+      double a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     if (t + 1 < nk) store_smem(buf ^ 1);
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int64_t gm = m0 + ty + 16 * i;
+  for (int i = 0; i < TM; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int64_t gn = n0 + tx + 16 * j;
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
       if (gn < N) C[gm * ldc + gn] = acc[i][j];
     }
   }
@@ -161,6 +174,7 @@ __global__ void __launch_bounds__(BT_THREADS) beta_kernel(
     const int4 *__restrict__ adj, const double *__restrict__ W, const double *__restrict__ Xo,
     double *__restrict__ beta, const int *__restrict__ dcnt) {
   __shared__ double Ws[BT_COLS][kMaxOrb][kMaxOrb + 1];
+  __shared__ double Xs[kMaxOrb][BT_THREADS];
   const int A = blockIdx.x;
   const int c0 = blockIdx.y * BT_COLS;
   // ncols is the column stride of beta; nact the live columns
@@ -179,7 +193,16 @@ __global__ void __launch_bounds__(BT_THREADS) beta_kernel(
       const int4 ent = adj[e];
       const int k = ent.x, B = ent.y, tr = ent.z;
       const int bo = aoff[B], nB = aoff[B + 1] - bo;
-      __syncthreads();
+      // this entry's X_occ column: all loads issued together, parked in shared memory
+      {
+        double xr[kMaxOrb];
+#pragma unroll
+        for (int b = 0; b < kMaxOrb; ++b)
+          xr[b] = (b < nB && E < n_occ) ? Xo[(int64_t)(bo + b) * n_occ + E] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < kMaxOrb; ++b) Xs[b][threadIdx.x] = xr[b];
+      }
       for (int i = threadIdx.x; i < BT_COLS * kBlk; i += BT_THREADS) {
         int c = i / kBlk, ab = i % kBlk, a = ab / kMaxOrb, b = ab % kMaxOrb;
         double v = 0.0;
@@ -189,14 +212,12 @@ __global__ void __launch_bounds__(BT_THREADS) beta_kernel(
         Ws[c][a][b] = v;
       }
       __syncthreads();
-      if (E < n_occ) {
-        for (int b = 0; b < nB; ++b) {
-          const double xv = Xo[(int64_t)(bo + b) * n_occ + E];
+      for (int b = 0; b < nB; ++b) {
+        const double xv = Xs[b][threadIdx.x];
 #pragma unroll
-          for (int c = 0; c < BT_COLS; ++c)
+        for (int c = 0; c < BT_COLS; ++c)
 #pragma unroll
-            for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = fma(Ws[c][a][b], xv, acc[c][a]);
-        }
+          for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = fma(Ws[c][a][b], xv, acc[c][a]);
       }
     }
     if (E < n_occ) {
@@ -239,104 +260,6 @@ __global__ void dscale_kernel(int n_virt, int S, int n_occ, double occ_value,
     const double re = a[base], im = a[base + n_occ];
     a[base] = d_re * re - d_im * im;
     a[base + n_occ] = d_re * im + d_im * re;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Step 5: for block k = (A, B) and column c
-//   G[a][b] = sum_E Xo[A+a][E] gamma[B+b][c][E]  (+ gamma[A+a][c][E] Xo[B+b][E] if A != B)
-//   n[c][mu] = sum_ab V_mu[a][b] G[a][b]  for mu in block k
-//   Out[c][mu] = Zin[c][mu] - n  (A operator)  or  n  (chi0 only)
-// One CTA per (block, 4 columns); thread t owns (a, b) = (t/16, t%16).
-// ---------------------------------------------------------------------------
-constexpr int SD_COLS = 4;
-constexpr int SD_E = 16;
-
-__global__ void __launch_bounds__(256) sddmm_dot(int ncols, int n_occ, int n_prod,
-                                                 const int *__restrict__ aoff,
-                                                 const int2 *__restrict__ blk_atoms,
-                                                 const int *__restrict__ blk_ptr,
-                                                 const int *__restrict__ blk_prod,
-                                                 const double *__restrict__ Vpad,
-                                                 const double *__restrict__ Xo,
-                                                 const double *__restrict__ gamma,
-                                                 const double *__restrict__ Zin, int subtract,
-                                                 double *__restrict__ Out,
-                                                 const int *__restrict__ dcnt) {
-  __shared__ double XA[kMaxOrb][SD_E + 1], XB[kMaxOrb][SD_E + 1];
-  __shared__ double gA[SD_COLS][kMaxOrb][SD_E + 1], gB[SD_COLS][kMaxOrb][SD_E + 1];
-  __shared__ double Gs[SD_COLS][kBlk];
-  const int k = blockIdx.x;
-  const int c0 = blockIdx.y * SD_COLS;
-  // ncols is the column stride of gamma; nact the live columns
-  const int nact = dcnt ? min(ncols, 2 * *dcnt) : ncols;
-  if (c0 >= nact) return;
-  const int t = threadIdx.x;
-  const int a = t >> 4, b = t & 15;
-  const int2 AB = blk_atoms[k];
-  const int aoA = aoff[AB.x], nA = aoff[AB.x + 1] - aoA;
-  const int aoB = aoff[AB.y], nB = aoff[AB.y + 1] - aoB;
-  const bool bilocal = AB.x != AB.y;
-  double G[SD_COLS];
-#pragma unroll
-  for (int c = 0; c < SD_COLS; ++c) G[c] = 0.0;
-  for (int E0 = 0; E0 < n_occ; E0 += SD_E) {
-    __syncthreads();
-    for (int i = t; i < kMaxOrb * SD_E; i += 256) {
-      int r = i / SD_E, e = i % SD_E;
-      int E = E0 + e;
-      XA[r][e] = (r < nA && E < n_occ) ? Xo[(int64_t)(aoA + r) * n_occ + E] : 0.0;
-      XB[r][e] = (r < nB && E < n_occ) ? Xo[(int64_t)(aoB + r) * n_occ + E] : 0.0;
-    }
-    for (int i = t; i < SD_COLS * kMaxOrb * SD_E; i += 256) {
-      int c = i / (kMaxOrb * SD_E), rem = i % (kMaxOrb * SD_E);
-      int r = rem / SD_E, e = rem % SD_E;
-      int E = E0 + e;
-      bool okc = (c0 + c < nact) && E < n_occ;
-      gA[c][r][e] = (okc && r < nA) ? gamma[((int64_t)(aoA + r) * ncols + c0 + c) * n_occ + E] : 0.0;
-      gB[c][r][e] = (okc && r < nB) ? gamma[((int64_t)(aoB + r) * ncols + c0 + c) * n_occ + E] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int e = 0; e < SD_E; ++e) {
-      const double xa = XA[a][e], xb = XB[b][e];
-#pragma unroll
-      for (int c = 0; c < SD_COLS; ++c) {
-        G[c] = fma(xa, gB[c][b][e], G[c]);
-        if (bilocal) G[c] = fma(gA[c][a][e], xb, G[c]);
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < SD_COLS; ++c) Gs[c][t] = G[c];
-  __syncthreads();
-  const int warp = t >> 5, lane = t & 31;
-  const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
-  for (int q = p0 + warp; q < p1; q += 8) {
-    double part[SD_COLS];
-#pragma unroll
-    for (int c = 0; c < SD_COLS; ++c) part[c] = 0.0;
-    for (int i = lane; i < kBlk; i += 32) {
-      const double v = Vpad[(int64_t)q * kBlk + i];
-#pragma unroll
-      for (int c = 0; c < SD_COLS; ++c) part[c] = fma(v, Gs[c][i], part[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < SD_COLS; ++c) {
-      double v = part[c];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      part[c] = v;
-    }
-    if (lane == 0) {
-      const int mu = blk_prod[q];
-#pragma unroll
-      for (int c = 0; c < SD_COLS; ++c) {
-        if (c0 + c >= nact) continue;
-        const int64_t o = (int64_t)(c0 + c) * n_prod + mu;
-        Out[o] = subtract ? Zin[o] - part[c] : part[c];
-      }
-    }
   }
 }
 
@@ -407,9 +330,16 @@ cudaError_t launch_gemm_f64(cudaStream_t st, int M, int N, int K, const double *
                             const double *B, int64_t ldb, double *C, int64_t ldc,
                             const int *dcnt, int mul_m, int mul_n) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M);
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  gemm_f64_nn<<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, dcnt, mul_m, mul_n);
+  if (M < 256) {
+    // few rows (the K product of a small batch): a 32-row tile wastes less
+    dim3 grid((N + 127) / 128, (M + 31) / 32);
+    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    gemm_f64_nn<32, 128><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, dcnt, mul_m, mul_n);
+  } else {
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    gemm_f64_nn<64, 64><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, dcnt, mul_m, mul_n);
+  }
   return cudaGetLastError();
 }
 
@@ -472,10 +402,8 @@ cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &
   err = launch_gemm_f64(st, sys.n_orb, (int)ncolE, sys.n_virt, sys.Xv, sys.n_virt, wk.abuf, ncolE,
                         wk.gamma, ncolE);
   if (err != cudaSuccess) return err;
-  dim3 grid(sys.n_blocks, (2 * S + SD_COLS - 1) / SD_COLS);
-  sddmm_dot<<<grid, 256, 0, st>>>(2 * S, sys.n_occ, np, sys.aoff, sys.blk_atoms, sys.blk_ptr,
-                                  sys.blk_prod, sys.Vpad, sys.Xo, wk.gamma, nullptr, 0, Out, nullptr);
-  return cudaGetLastError();
+  return launch_block_dot(st, true, 2 * S, sys, sys.Vpad, sys.Xo, wk.gamma, nullptr, 0, Out,
+                          nullptr);
 }
 
 cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S,
@@ -531,11 +459,9 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
   }
   {
     Scope sc(wk.timer, st, kcSddmm, ncols * sys.sf.dot);
-    dim3 grid(sys.n_blocks, (ncols + SD_COLS - 1) / SD_COLS);
-    sddmm_dot<<<grid, 256, 0, st>>>(ncols, sys.n_occ, np, sys.aoff, sys.blk_atoms, sys.blk_ptr,
-                                    sys.blk_prod, sys.Vpad, sys.Xo, wk.gamma, Zin,
-                                    mode == kA ? 1 : 0, Out, wk.dcnt);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    err = launch_block_dot(st, true, ncols, sys, sys.Vpad, sys.Xo, wk.gamma, Zin,
+                           mode == kA ? 1 : 0, Out, wk.dcnt);
+    if (err != cudaSuccess) return err;
   }
   return cudaSuccess;
 }

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(128) lp_beta(int ncols, int nb, int n_occ, int
                                                const int *__restrict__ dcnt) {
   constexpr int COLS = 4;
   __shared__ float Ws[COLS][kMaxOrb][kMaxOrb + 1];
+  __shared__ float Xs[kMaxOrb][128];
   const int A = blockIdx.x;
   const int c0 = blockIdx.y * COLS;
   if (dcnt) ncols = min(ncols, 2 * *dcnt);
@@ -128,7 +129,16 @@ __global__ void __launch_bounds__(128) lp_beta(int ncols, int nb, int n_occ, int
       const int4 ent = adj[e];
       const int k = ent.x, B = ent.y, tr = ent.z;
       const int bo = aoff[B], nB = aoff[B + 1] - bo;
-      __syncthreads();
+      // this entry's X_occ column: all loads issued together, parked in shared memory
+      {
+        float xr[kMaxOrb];
+#pragma unroll
+        for (int b = 0; b < kMaxOrb; ++b)
+          xr[b] = (b < nB && E < n_occ) ? Xo[(int64_t)(bo + b) * n_occ + E] : 0.f;
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < kMaxOrb; ++b) Xs[b][threadIdx.x] = xr[b];
+      }
       for (int i = threadIdx.x; i < COLS * kBlk; i += 128) {
         const int c = i / kBlk, ab = i % kBlk, a = ab / kMaxOrb, b = ab % kMaxOrb;
         float v = 0.f;
@@ -138,14 +148,12 @@ __global__ void __launch_bounds__(128) lp_beta(int ncols, int nb, int n_occ, int
         Ws[c][a][b] = v;
       }
       __syncthreads();
-      if (E < n_occ) {
-        for (int b = 0; b < nB; ++b) {
-          const float xv = Xo[(int64_t)(bo + b) * n_occ + E];
+      for (int b = 0; b < nB; ++b) {
+        const float xv = Xs[b][threadIdx.x];
 #pragma unroll
-          for (int c = 0; c < COLS; ++c)
+        for (int c = 0; c < COLS; ++c)
 #pragma unroll
-            for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = fmaf(Ws[c][a][b], xv, acc[c][a]);
-        }
+          for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = fmaf(Ws[c][a][b], xv, acc[c][a]);
       }
     }
     if (E < n_occ) {
@@ -163,95 +171,6 @@ __global__ void __launch_bounds__(128) lp_beta(int ncols, int nb, int n_occ, int
             dst[Kp1 + a] = __float2bfloat16_rn(acc[c][a] - __bfloat162float(hi));
           }
         }
-      }
-    }
-  }
-}
-
-// Step 5 on gamma^T; Out (float64) = Zin - n or n.
-__global__ void __launch_bounds__(256) lp_sddmm(int ncols, int n_occ, int n_prod, int n_orb,
-                                                const int *__restrict__ aoff,
-                                                const int2 *__restrict__ blk_atoms,
-                                                const int *__restrict__ blk_ptr,
-                                                const int *__restrict__ blk_prod,
-                                                const float *__restrict__ Vpad,
-                                                const float *__restrict__ Xo,
-                                                const float *__restrict__ gammaT,
-                                                const double *__restrict__ Zin, int subtract,
-                                                double *__restrict__ Out,
-                                                const int *__restrict__ dcnt) {
-  constexpr int COLS = 4, EC = 32;
-  if (dcnt) ncols = min(ncols, 2 * *dcnt);
-  if ((int)blockIdx.y * COLS >= ncols) return;
-  __shared__ float XA[kMaxOrb][EC + 1], XB[kMaxOrb][EC + 1];
-  __shared__ float gA[COLS][kMaxOrb][EC + 1], gB[COLS][kMaxOrb][EC + 1];
-  __shared__ float Gs[COLS][kBlk];
-  const int k = blockIdx.x;
-  const int c0 = blockIdx.y * COLS;
-  const int t = threadIdx.x;
-  const int a = t >> 4, b = t & 15;
-  const int2 AB = blk_atoms[k];
-  const int aoA = aoff[AB.x], nA = aoff[AB.x + 1] - aoA;
-  const int aoB = aoff[AB.y], nB = aoff[AB.y + 1] - aoB;
-  const bool bilocal = AB.x != AB.y;
-  float G[COLS];
-#pragma unroll
-  for (int c = 0; c < COLS; ++c) G[c] = 0.f;
-  for (int E0 = 0; E0 < n_occ; E0 += EC) {
-    __syncthreads();
-    for (int i = t; i < kMaxOrb * EC; i += 256) {
-      const int r = i / EC, e = i % EC, E = E0 + e;
-      XA[r][e] = (r < nA && E < n_occ) ? Xo[(int64_t)(aoA + r) * n_occ + E] : 0.f;
-      XB[r][e] = (r < nB && E < n_occ) ? Xo[(int64_t)(aoB + r) * n_occ + E] : 0.f;
-    }
-    for (int i = t; i < COLS * EC * kMaxOrb; i += 256) {
-      const int c = i / (EC * kMaxOrb), rem = i % (EC * kMaxOrb);
-      const int e = rem / kMaxOrb, r = rem % kMaxOrb;
-      const int E = E0 + e, cc = c0 + c;
-      const bool ok = cc < ncols && E < n_occ;
-      const int64_t row = ((int64_t)(cc >> 1) * n_occ + E) * 2 + (cc & 1);
-      gA[c][r][e] = (ok && r < nA) ? gammaT[row * n_orb + aoA + r] : 0.f;
-      gB[c][r][e] = (ok && r < nB) ? gammaT[row * n_orb + aoB + r] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int e = 0; e < EC; ++e) {
-      const float xa = XA[a][e], xb = XB[b][e];
-#pragma unroll
-      for (int c = 0; c < COLS; ++c) {
-        G[c] = fmaf(xa, gB[c][b][e], G[c]);
-        if (bilocal) G[c] = fmaf(gA[c][a][e], xb, G[c]);
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < COLS; ++c) Gs[c][t] = G[c];
-  __syncthreads();
-  const int warp = t >> 5, lane = t & 31;
-  const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
-  for (int q = p0 + warp; q < p1; q += 8) {
-    float part[COLS];
-#pragma unroll
-    for (int c = 0; c < COLS; ++c) part[c] = 0.f;
-    for (int i = lane; i < kBlk; i += 32) {
-      const float v = Vpad[(int64_t)q * kBlk + i];
-#pragma unroll
-      for (int c = 0; c < COLS; ++c) part[c] = fmaf(v, Gs[c][i], part[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < COLS; ++c) {
-      float v = part[c];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      part[c] = v;
-    }
-    if (lane == 0) {
-      const int mu = blk_prod[q];
-#pragma unroll
-      for (int c = 0; c < COLS; ++c) {
-        if (c0 + c >= ncols) continue;
-        const int64_t o = (int64_t)(c0 + c) * n_prod + mu;
-        Out[o] = subtract ? Zin[o] - (double)part[c] : (double)part[c];
       }
     }
   }
@@ -411,11 +330,9 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
   }
   {
     Scope sc(lp.timer, st, kcLpSddmm, ncols * sys.sf.dot);
-    dim3 grid(sys.n_blocks, (ncols + 3) / 4);
-    lp_sddmm<<<grid, 256, 0, st>>>(ncols, sys.n_occ, np, sys.n_orb, sys.aoff, sys.blk_atoms,
-                                   sys.blk_ptr, sys.blk_prod, lp.Vpad32, lp.Xo32, lp.gammaT, Zin,
-                                   mode == kA ? 1 : 0, Out, lp.dcnt);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    err = launch_block_dot(st, false, ncols, sys, lp.Vpad32, lp.Xo32, lp.gammaT, Zin,
+                           mode == kA ? 1 : 0, Out, lp.dcnt);
+    if (err != cudaSuccess) return err;
   }
   return cudaSuccess;
 }

@@ -257,6 +257,18 @@ def random_complex_vectors(n_rhs: int, n: int, seed: int) -> np.ndarray:
     return z[..., 0] + 1j * z[..., 1]
 
 
+def batch_sizes(n_mol: int = 32, lo: int = 8, hi: int = 128, seed: int = 4999) -> list[int]:
+    """Atom counts of the uneven batch: round(exp(U(ln lo, ln hi))) per molecule."""
+    u = CounterRNG(seed, _S_SIZES).uniform(n_mol)
+    return [int(round(math.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * x))) for x in u]
+
+
+def batch_molecules(n_mol: int = 32, lo: int = 8, hi: int = 128) -> list[System]:
+    """The uneven batch: molecule i has seed 4000 + i, atom count from batch_sizes."""
+    return [make_system(n, 4000 + i, density=0.0094)
+            for i, n in enumerate(batch_sizes(n_mol, lo, hi))]
+
+
 def workload_system(name: str) -> System:
     """The molecule of a named workload (picklable factory for worker processes)."""
     return workload(name)[0]
