@@ -28,7 +28,9 @@ __global__ void __launch_bounds__(256, 2) block_dot_kernel(
   __shared__ T XA[BD_E][kMaxOrb + 1], XB[BD_E][kMaxOrb + 1];
   // gamma slices of the A and B rows, [2][BD_COLS][BD_E][kMaxOrb + 1], reused for G
   __shared__ T gbuf[2 * BD_COLS * BD_E * (kMaxOrb + 1)];
-  static_assert(2 * BD_COLS * BD_E * (kMaxOrb + 1) >= BD_COLS * kBlk, "G must fit in gbuf");
+  // G is stored with rows of 17 (bank-conflict free): 16 columns x 16 x 17
+  constexpr int GS = kMaxOrb * (kMaxOrb + 1);
+  static_assert(2 * BD_COLS * BD_E * (kMaxOrb + 1) >= BD_COLS * GS, "G must fit in gbuf");
   auto gA = [&](int c, int e, int r) -> T & {
     return gbuf[(c * BD_E + e) * (kMaxOrb + 1) + r];
   };
@@ -110,11 +112,11 @@ __global__ void __launch_bounds__(256, 2) block_dot_kernel(
   }
   // G of all 16 columns to shared memory (reusing gbuf), then the block dots
   __syncthreads();
-  T *Gs = gbuf;   // [BD_COLS][kBlk]
+  T *Gs = gbuf;   // [BD_COLS][kMaxOrb][kMaxOrb + 1]
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) Gs[cl * kBlk + (a0 + i) * kMaxOrb + b0 + j] = G[i][j];
+    for (int j = 0; j < 4; ++j) Gs[cl * GS + (a0 + i) * (kMaxOrb + 1) + b0 + j] = G[i][j];
   __syncthreads();
   const int warp = t >> 5, lane = t & 31;
   const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
@@ -124,8 +126,9 @@ __global__ void __launch_bounds__(256, 2) block_dot_kernel(
     for (int c = 0; c < BD_COLS; ++c) part[c] = T(0);
     for (int i = lane; i < kBlk; i += 32) {
       const T v = Vpad[(int64_t)q * kBlk + i];
+      const int gi = (i >> 4) * (kMaxOrb + 1) + (i & 15);
 #pragma unroll
-      for (int c = 0; c < BD_COLS; ++c) part[c] = fma(v, Gs[c * kBlk + i], part[c]);
+      for (int c = 0; c < BD_COLS; ++c) part[c] = fma(v, Gs[c * GS + gi], part[c]);
     }
 #pragma unroll
     for (int c = 0; c < BD_COLS; ++c) {

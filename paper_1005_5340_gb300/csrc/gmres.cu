@@ -10,7 +10,11 @@
 //                    done, not converged (cycle limit) and a restart.
 // Right-hand sides that are done drop out of the active list, so the batched
 // operator only works on live ones.
+#include <cooperative_groups.h>
+
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace tddft {
 namespace {
@@ -187,41 +191,77 @@ __global__ void __launch_bounds__(NT) gmres_gather_kernel(Gs G, const int *__res
   if (threadIdx.x == 0) slot_omega[s] = G.omega[r];
 }
 
+// Sum of NV values over the P CTAs of the cluster (after the block sums), in
+// rank order, so every CTA gets bit-identical totals.
+template <int P, int NV>
+__device__ void cluster_sum(double (&v)[NV], double *red, double *clx) {
+  block_sum<NV>(v, red);
+  if (P == 1) return;
+  cg::cluster_group cl = cg::this_cluster();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) clx[q] = v[q];
+  }
+  cl.sync();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  for (int rk = 0; rk < P; ++rk) {
+    const double *rem = cl.map_shared_rank(clx, rk);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] += rem[q];
+  }
+  cl.sync();   // clx may be reused once every CTA has read it
+}
+
+// One GMRES step of the right-hand side in slot blockIdx.y, its vectors split
+// over the P CTAs of a cluster (element range per CTA); dot products and norms
+// are reduced across the cluster through distributed shared memory.  Every
+// CTA takes the same decisions from the same totals; rank 0 writes the
+// per-right-hand-side scalars.
+template <int P>
 __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restrict__ list,
                                                         const double *__restrict__ Wout,
                                                         const int *__restrict__ dcnt) {
   __shared__ double red[16 * (NT / 32)];
+  __shared__ double clx[16];
   __shared__ double2 hs[257], hp[257], ys[257];
   __shared__ int finish_flag;
-  const int s = blockIdx.x;
-  if (dcnt && s >= *dcnt) return;
+  const int s = blockIdx.y;
+  if (dcnt && s >= *dcnt) return;          // the same for the whole cluster
+  const int rank = (P > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const int r = list[s];
   const int N = G.n_prod;
   const int m = G.m;
   const int tid = threadIdx.x;
+  const int chunk = (N + P - 1) / P;
+  const int lo = rank * chunk, hi = min(N, lo + chunk);
   const double *win = Wout + (int64_t)2 * s * N;
   double *Vr = G.V + (int64_t)r * (m + 1) * 2 * N;
   const int state = G.state[r];
+  const int cyc = G.cycles[r];
 
   if (state == kStateResid) {
     // r = b - A x ; decide done / not converged / restart
     const double *b = G.b + (int64_t)2 * r * N;
     double s2[1] = {0.0};
-    for (int e = tid; e < 2 * N; e += NT) {
-      double t = b[e] - win[e];
-      Vr[e] = t;
-      s2[0] += t * t;
+    for (int e = lo + tid; e < hi; e += NT) {
+      const double tr = b[e] - win[e], ti = b[N + e] - win[N + e];
+      Vr[e] = tr;
+      Vr[N + e] = ti;
+      s2[0] += tr * tr + ti * ti;
     }
-    block_sum<1>(s2, red);
+    cluster_sum<P, 1>(s2, red, clx);
     double rho = sqrt(s2[0]);
     bool rejected = false;
-    if (G.cycles[r] == 0 && rho > G.bnorm[r]) {
+    if (cyc == 0 && rho > G.bnorm[r]) {
       // the residual of a supplied initial guess: zero is the fallback and the
       // judge, so a guess worse than zero is dropped
       double *x = G.x + (int64_t)2 * r * N;
-      for (int e = tid; e < 2 * N; e += NT) {
+      for (int e = lo + tid; e < hi; e += NT) {
         Vr[e] = b[e];
+        Vr[N + e] = b[N + e];
         x[e] = 0.0;
+        x[N + e] = 0.0;
       }
       rho = G.bnorm[r];
       rejected = true;
@@ -229,13 +269,16 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
     const double rel = rho / G.bnorm[r];
     int next;
     if (rel <= G.tol) next = 0;
-    else if (G.cycles[r] >= G.max_restarts) next = 1;
+    else if (cyc >= G.max_restarts) next = 1;
     else next = 2;
     if (next == 2) {
       const double inv = 1.0 / rho;
-      for (int e = tid; e < 2 * N; e += NT) Vr[e] *= inv;
+      for (int e = lo + tid; e < hi; e += NT) {
+        Vr[e] *= inv;
+        Vr[N + e] *= inv;
+      }
     }
-    if (tid == 0) {
+    if (tid == 0 && rank == 0) {
       G.matvecs[r] += 1;
       G.resid[r] = rel;
       if (rejected) G.flags[r] |= 1;
@@ -244,7 +287,7 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
       else {
         G.state[r] = kStateArnoldi;
         G.jcur[r] = 0;
-        G.cycles[r] += 1;
+        G.cycles[r] = cyc + 1;
         G.g[(int64_t)r * (m + 1)] = make_double2(rho, 0.0);
         G.rho0[r] = rho;
       }
@@ -254,15 +297,18 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
   if (state != kStateArnoldi) return;
 
   const int j = G.jcur[r];
+  const double2 gj0 = G.g[(int64_t)r * (m + 1) + j];
+  const double rho0 = G.rho0[r];
   double *w = Vr + (int64_t)(j + 1) * 2 * N;
   double n0[1] = {0.0};
-  for (int e = tid; e < 2 * N; e += NT) {
-    const double t = win[e];
-    w[e] = t;
-    n0[0] += t * t;
+  for (int e = lo + tid; e < hi; e += NT) {
+    const double tr = win[e], ti = win[N + e];
+    w[e] = tr;
+    w[N + e] = ti;
+    n0[0] += tr * tr + ti * ti;
   }
   for (int i = tid; i <= j; i += NT) hs[i] = make_double2(0.0, 0.0);
-  block_sum<1>(n0, red);   // ||A v_j||^2 (the block sum synchronises)
+  cluster_sum<P, 1>(n0, red, clx);   // ||A v_j||^2 (synchronises)
   double hn = 0.0;
 
   // Classical Gram-Schmidt with selective reorthogonalisation: the second
@@ -274,7 +320,7 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
       double part[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) part[q] = 0.0;
-      for (int e = tid; e < N; e += NT) {
+      for (int e = lo + tid; e < hi; e += NT) {
         const double wr = w[e], wi = w[N + e];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -286,13 +332,13 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
           }
         }
       }
-      block_sum<16>(part, red);
+      cluster_sum<P, 16>(part, red, clx);
       if (tid < 8 && i0 + tid <= j) hp[i0 + tid] = make_double2(part[2 * tid], part[2 * tid + 1]);
     }
     __syncthreads();
     // w -= sum_i h_i v_i, with the new ||w||^2
     double n1[1] = {0.0};
-    for (int e = tid; e < N; e += NT) {
+    for (int e = lo + tid; e < hi; e += NT) {
       double ar = 0.0, ai = 0.0;
       for (int i = 0; i <= j; ++i) {
         const double *vi_ = Vr + (int64_t)i * 2 * N;
@@ -307,18 +353,16 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
       n1[0] += nr * nr + ni * ni;
     }
     for (int i = tid; i <= j; i += NT) hs[i] = make_double2(hs[i].x + hp[i].x, hs[i].y + hp[i].y);
-    block_sum<1>(n1, red);   // synchronises: w and hs complete
+    cluster_sum<P, 1>(n1, red, clx);   // synchronises: w and hs complete
     hn = sqrt(n1[0]);
-    if (n1[0] > 0.5 * n0[0]) break;   // uniform across the CTA
+    if (n1[0] > 0.5 * n0[0]) break;   // uniform across the cluster
     n0[0] = n1[0];
   }
 
   if (tid == 0) {
-    double2 *Hc = G.H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);
-    double *cs = G.cs + (int64_t)r * m;
-    double2 *sn = G.sn + (int64_t)r * m;
-    double2 *g = G.g + (int64_t)r * (m + 1);
-    // apply the earlier rotations to the new column
+    // every CTA rotates its own copy of the new column (identical inputs)
+    const double *cs = G.cs + (int64_t)r * m;
+    const double2 *sn = G.sn + (int64_t)r * m;
     for (int i = 0; i < j; ++i) {
       const double2 a = hs[i], bb = hs[i + 1];
       const double2 t = make_double2(cs[i] * a.x + (sn[i].x * bb.x - sn[i].y * bb.y),
@@ -340,46 +384,56 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
       sv = make_double2(a.x / aa * hn / rr, a.y / aa * hn / rr);
     }
     hs[j] = make_double2(c * a.x + sv.x * hn, c * a.y + sv.y * hn);
-    cs[j] = c;
-    sn[j] = sv;
-    const double2 gj = g[j];
-    const double2 t = cmul(cconj(sv), gj);
-    g[j + 1] = make_double2(-t.x, -t.y);
-    g[j] = make_double2(c * gj.x, c * gj.y);
-    for (int i = 0; i <= j; ++i) Hc[i] = hs[i];
-    const double est = cabs2(g[j + 1]);
+    const double2 t = cmul(cconj(sv), gj0);
+    const double2 gnext = make_double2(-t.x, -t.y);
+    const double2 gj = make_double2(c * gj0.x, c * gj0.y);
+    const double est = cabs2(gnext);
     // a cycle ends at the tolerance, at the restart length, on breakdown, or
     // (refinement forms) once it has reduced its own residual by inner_tol
     const bool fin = (est <= G.tol * G.bnorm[r]) || (j + 1 == m) || !(hn > 0.0) ||
-                     (est <= G.inner_tol * G.rho0[r]);
+                     (est <= G.inner_tol * rho0);
     finish_flag = fin ? 1 : 0;
-    G.matvecs[r] += 1;
     if (fin) {
-      // back substitution with the rotated (upper triangular) Hessenberg matrix
+      // back substitution with the rotated (upper triangular) Hessenberg
+      // matrix: columns < j from memory, column j and g[j] from this step
       const int k = j + 1;
       const double2 *Hr = G.H + (int64_t)r * (m + 1) * m;
+      const double2 *gg = G.g + (int64_t)r * (m + 1);
       for (int i = k - 1; i >= 0; --i) {
-        double2 acc = g[i];
+        double2 acc = (i == j) ? gj : gg[i];
         for (int l = i + 1; l < k; ++l) {
-          const double2 p = cmul(Hr[(int64_t)l * (m + 1) + i], ys[l]);
+          const double2 hil = (l == j) ? hs[i] : Hr[(int64_t)l * (m + 1) + i];
+          const double2 p = cmul(hil, ys[l]);
           acc.x -= p.x;
           acc.y -= p.y;
         }
-        ys[i] = cdiv(acc, Hr[(int64_t)i * (m + 1) + i]);
+        const double2 hii = (i == j) ? hs[j] : Hr[(int64_t)i * (m + 1) + i];
+        ys[i] = cdiv(acc, hii);
       }
-      G.state[r] = kStateResid;
-    } else {
-      G.jcur[r] = j + 1;
+    }
+    if (rank == 0) {
+      double2 *Hc = G.H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);
+      for (int i = 0; i <= j; ++i) Hc[i] = hs[i];
+      G.cs[(int64_t)r * m + j] = c;
+      G.sn[(int64_t)r * m + j] = sv;
+      G.g[(int64_t)r * (m + 1) + j] = gj;
+      G.g[(int64_t)r * (m + 1) + j + 1] = gnext;
+      G.matvecs[r] += 1;
+      if (fin) G.state[r] = kStateResid;
+      else G.jcur[r] = j + 1;
     }
   }
   __syncthreads();
   if (!finish_flag) {
     const double inv = 1.0 / hn;
-    for (int e = tid; e < 2 * N; e += NT) w[e] *= inv;
+    for (int e = lo + tid; e < hi; e += NT) {
+      w[e] *= inv;
+      w[N + e] *= inv;
+    }
   } else {
     const int k = j + 1;
     double *x = G.x + (int64_t)2 * r * N;
-    for (int e = tid; e < N; e += NT) {
+    for (int e = lo + tid; e < hi; e += NT) {
       double ar = 0.0, ai = 0.0;
       for (int i = 0; i < k; ++i) {
         const double *vi_ = Vr + (int64_t)i * 2 * N;
@@ -495,8 +549,30 @@ cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresStat
 cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs,
                               const int *list, int S, const double *Wout, const int *dcnt) {
   if (S <= 0) return cudaSuccess;
-  gmres_step_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Wout, dcnt);
-  return cudaGetLastError();
+  if (S > 65535) return cudaErrorInvalidConfiguration;
+  const Gs G = view(gs, sys.n_prod);
+  // Long vectors: a cluster of CTAs per right-hand side, so that the FP64
+  // work of the orthogonalisation is spread over more SMs than there are
+  // live right-hand sides.
+  const int P = sys.n_prod >= 8192 ? 4 : (sys.n_prod >= 2048 ? 2 : 1);
+  if (P == 1) {
+    gmres_step_kernel<1><<<dim3(1, S), NT, 0, st>>>(G, list, Wout, dcnt);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P, S);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return P == 4 ? cudaLaunchKernelEx(&cfg, gmres_step_kernel<4>, G, list, Wout, dcnt)
+                : cudaLaunchKernelEx(&cfg, gmres_step_kernel<2>, G, list, Wout, dcnt);
 }
 
 cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0,

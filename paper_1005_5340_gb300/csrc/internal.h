@@ -87,6 +87,8 @@ struct OpWork {
   double *omega = nullptr;    // [S] frequency of each slot
   Timer *timer = nullptr;
   const int *dcnt = nullptr;  // graph replays: device count of live slots (NULL: all S)
+  double *splitws = nullptr;  // split-K slices of the K product
+  int64_t splitws_elems = 0;
 };
 
 enum OpMode { kChi0 = 0, kKernel = 1, kA = 2 };
@@ -94,9 +96,12 @@ enum OpMode { kChi0 = 0, kKernel = 1, kA = 2 };
 // Launchers (stream-ordered, no synchronisation).  Return cudaGetLastError().
 // dcnt (may be NULL): device count of live right-hand sides; rows beyond
 // mul_m * count and columns beyond mul_n * count are skipped (0 = no limit).
+// ws (may be NULL): workspace of ws_elems doubles for a deterministic split-K
+// when the tile grid is too small to fill the GPU.
 cudaError_t launch_gemm_f64(cudaStream_t st, int M, int N, int K, const double *A, int64_t lda,
                             const double *B, int64_t ldb, double *C, int64_t ldc,
-                            const int *dcnt = nullptr, int mul_m = 0, int mul_n = 0);
+                            const int *dcnt = nullptr, int mul_m = 0, int mul_n = 0,
+                            double *ws = nullptr, int64_t ws_elems = 0);
 cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S,
                                   OpMode mode, double eps, const double *Zin, double *Out);
 // Right-hand sides b = chi0(omega) d_k of a spectrum group (rows g0..g0+S-1,

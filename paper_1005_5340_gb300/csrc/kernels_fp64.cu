@@ -28,7 +28,8 @@ __global__ void __launch_bounds__(256, (BM == 32 ? 2 : 3)) gemm_f64_nn(int M, in
                                                    int64_t lda, const double *__restrict__ B,
                                                    int64_t ldb, double *__restrict__ C,
                                                    int64_t ldc, const int *__restrict__ dcnt,
-                                                   int mul_m, int mul_n) {
+                                                   int mul_m, int mul_n, int kchunk,
+                                                   int64_t zstride) {
   constexpr int TM = BM / 16, TN = BN / 16;     // outputs per thread
   constexpr int LA = BM * GB_K / 256, LB = BN * GB_K / 256;   // loads per thread
   __shared__ double As[2][GB_K][BM + 2];
@@ -44,6 +45,12 @@ __global__ void __launch_bounds__(256, (BM == 32 ? 2 : 3)) gemm_f64_nn(int M, in
     if (mul_n) N = (int)min((int64_t)N, (int64_t)mul_n * c);
   }
   if (m0 >= M || n0 >= N) return;
+  // split K: CTA z sums k in [z kchunk, (z+1) kchunk) into its own slice of C
+  const int kb = blockIdx.z * kchunk;
+  K = min(K, kb + kchunk) - kb;
+  A += kb;
+  B += (int64_t)kb * ldb;
+  C += (int64_t)blockIdx.z * zstride;
   double acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -326,20 +333,61 @@ int grid_for(int64_t total, int threads) {
 }
 }  // namespace
 
+// C[m][n] = sum over the split slices ws[z][m][n], in slice order (deterministic)
+// (slices of zstride elements, rows of ldw; only the live M x N part is summed)
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const double *__restrict__ ws,
+                                     int64_t zstride, int64_t ldw, double *__restrict__ C,
+                                     int64_t ldc, const int *__restrict__ dcnt, int mul_m,
+                                     int mul_n) {
+  if (dcnt) {
+    const int c = *dcnt;
+    if (mul_m) M = min(M, mul_m * c);
+    if (mul_n) N = (int)min((int64_t)N, (int64_t)mul_n * c);
+  }
+  const int64_t total = (int64_t)M * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = i / N, n = i % N;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += ws[z * zstride + m * ldw + n];
+    C[m * ldc + n] = s;
+  }
+}
+
 cudaError_t launch_gemm_f64(cudaStream_t st, int M, int N, int K, const double *A, int64_t lda,
                             const double *B, int64_t ldb, double *C, int64_t ldc,
-                            const int *dcnt, int mul_m, int mul_n) {
+                            const int *dcnt, int mul_m, int mul_n, double *ws, int64_t ws_elems) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (M < 256) {
-    // few rows (the K product of a small batch): a 32-row tile wastes less
-    dim3 grid((N + 127) / 128, (M + 31) / 32);
-    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-    gemm_f64_nn<32, 128><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, dcnt, mul_m, mul_n);
-  } else {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-    gemm_f64_nn<64, 64><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, dcnt, mul_m, mul_n);
+  const bool small = M < 256;
+  // Long reductions (the K product: K = n_prod) with few output tiles leave SMs
+  // idle, so K is cut into slices of 2048 summed afterwards in a fixed order.
+  // The slicing depends on K alone: every launch shape (host-driven or graph
+  // replay, any batch) sums each output in the same order.
+  constexpr int kSlice = 2048, kMaxSlices = 8;
+  int kchunk = K, splits = 1;
+  if (ws && K >= 2 * kSlice) {
+    kchunk = std::max(kSlice, ((K + kMaxSlices - 1) / kMaxSlices + 15) / 16 * 16);
+    splits = (K + kchunk - 1) / kchunk;
+    if ((int64_t)splits * M * N > ws_elems) return cudaErrorInvalidValue;
   }
+  double *out = splits > 1 ? ws : C;
+  const int64_t ldo = splits > 1 ? N : ldc;
+  const int64_t zstride = (int64_t)M * N;
+  if (small) {
+    dim3 grid((N + 127) / 128, (M + 31) / 32, splits);
+    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    gemm_f64_nn<32, 128><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, out, ldo, dcnt, mul_m,
+                                               mul_n, kchunk, zstride);
+  } else {
+    dim3 grid((N + 63) / 64, (M + 63) / 64, splits);
+    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    gemm_f64_nn<64, 64><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, out, ldo, dcnt, mul_m,
+                                              mul_n, kchunk, zstride);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  splitk_reduce_kernel<<<grid_for((int64_t)M * N, 256), 256, 0, st>>>(
+      M, N, splits, ws, zstride, N, C, ldc, dcnt, mul_m, mul_n);
   return cudaGetLastError();
 }
 
@@ -418,7 +466,7 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
     // Y = Z K  (K symmetric, so row c of Y is K z_c)
     Scope sc(wk.timer, st, kcGemmK, 2.0 * ncols * (double)np * np);
     err = launch_gemm_f64(st, ncols, np, np, Zin, np, sys.K, np, (mode == kKernel) ? Out : wk.Y, np,
-                          wk.dcnt, 2, 0);
+                          wk.dcnt, 2, 0, wk.splitws, wk.splitws_elems);
     if (err != cudaSuccess || mode == kKernel) return err;
     Y = wk.Y;
   }

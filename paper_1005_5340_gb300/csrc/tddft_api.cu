@@ -372,6 +372,8 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   AL(w.Y, 2 * S * np);
   AL(w.W, 2 * S3 * (size_t)d.n_blocks * kBlk);
   AL(w.beta, (size_t)no * 2 * S3 * nocc);
+  w.splitws_elems = (int64_t)8 * 2 * S * np;
+  AL(w.splitws, (size_t)w.splitws_elems);
   AL(c->Z3, 6 * (size_t)np);
   AL(c->a3, (size_t)nv * 6 * nocc);
   AL(w.abuf, (size_t)nv * 2 * S * nocc);
