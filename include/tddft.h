@@ -50,11 +50,20 @@ typedef enum {
 
 typedef enum {
   TDDFT_PREC_FP64 = 0,      /* every step in float64 */
-  TDDFT_PREC_BF16X3_IR = 2  /* inner GMRES products in split bf16 on the tensor cores
+  TDDFT_PREC_FP64_EMU = 1,  /* as TDDFT_PREC_FP64, but the three dense products of every
+                               operator application (K z, X_virt^T beta, X_virt a) are
+                               float64 products emulated on the bf16 tensor cores
+                               (tddft_gemm_f64_emulated with 6 slices: error about
+                               2^-42 |A|_row |B|_col K); vertex contractions, block dots,
+                               Arnoldi and Givens stay native float64 */
+  TDDFT_PREC_BF16X3_IR = 2, /* inner GMRES products in split bf16 on the tensor cores
                                (hi*hi + hi*lo + lo*hi, float32 accumulation) and float32
                                vertex contractions; right-hand sides, residuals that end
                                each cycle, Arnoldi, Givens and the basis in float64
                                (iterative refinement) */
+  TDDFT_PREC_BF16X3_IR_EMU = 3  /* TDDFT_PREC_BF16X3_IR whose float64 right-hand sides and
+                                   cycle-end residuals use the emulated float64 products of
+                                   TDDFT_PREC_FP64_EMU */
 } tddft_precision;
 
 /*
@@ -96,9 +105,9 @@ typedef struct {
 
 /*
  * Solver and resource options.
- *  prec: TDDFT_PREC_FP64 or TDDFT_PREC_BF16X3_IR.  With BF16X3_IR,
- *      tddft_chi0_apply and tddft_apply_A use the reduced-precision operator
- *      (relative error ~1e-5) and tddft_kernel_apply stays float64.
+ *  prec: a tddft_precision.  With BF16X3_IR(_EMU), tddft_chi0_apply and
+ *      tddft_apply_A use the reduced-precision operator (relative error
+ *      ~1e-5) and tddft_kernel_apply stays float64 (emulated with _EMU).
  *  restart: GMRES restart length m (1..256).
  *  max_restarts: cycles before an (omega, direction) is declared not
  *      converged (>= 1).
@@ -110,7 +119,7 @@ typedef struct {
  *  inner_tol: refinement forms only: a GMRES cycle (whose products are in
  *      reduced precision) also ends once its residual estimate has dropped
  *      by this factor; the float64 residual then starts the next cycle.
- *      In (0, 1); ignored for TDDFT_PREC_FP64.
+ *      In (0, 1); ignored for TDDFT_PREC_FP64 and TDDFT_PREC_FP64_EMU.
  *  graph: 1 = tddft_polarizability captures one GMRES iteration of a group
  *      (selection, gathers, operators, Arnoldi/Givens/residual updates) in a
  *      CUDA graph and replays it, every kernel reading the live count on the
@@ -256,6 +265,29 @@ tddft_status tddft_timing_get(tddft_ctx *ctx, int32_t i, const char **name, int3
  */
 tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uint64_t seed,
                                  double *max_rel_err);
+
+/*
+ * Float64 matrix product emulated on the bf16 tensor cores (the dense
+ * products of eqs. chi0-transform-1/-2 and of K z, Sec. 3, in float64
+ * accuracy; used by TDDFT_PREC_FP64_EMU and TDDFT_PREC_BF16X3_IR_EMU):
+ *     C[m*ldc + n] = sum_k A[m*lda + k] B[k*ldb + n],  m < M, n < N, k < K.
+ * Device pointers (row-major, unaligned strides allowed); the stream
+ * (cudaStream_t, NULL = legacy default) orders the work and is synchronised
+ * before returning.  Each row of A and each column of B is scaled by a power
+ * of two and cut into `slices` (3..8) integer slices of 7 bits; the slice
+ * products are summed exactly in float32 on the tensor cores over chunks of
+ * K and in 64-bit integers across chunks.  Error:
+ *     |C - AB|_mn <= about (1 + (slices+1)/4) 2^(-7 slices) max_k|A_mk| max_k|B_kn| K
+ * (2.3e-13 relative to that scale for 6 slices); an exact result whenever
+ * the operands' entries are integers of at most 7*slices - 1 bits scaled
+ * alike.  Allocates and frees its own slice buffers (about
+ * (M+N) * slices * 2 bytes per K entry).  Errors: INVALID_ARG (NULL, sizes
+ * < 1, slices outside 3..8), SHAPE (lda < K, ldb < N or ldc < N), NOMEM,
+ * CUDA, TIMEOUT (a bounded wait inside the kernel gave up).
+ */
+tddft_status tddft_gemm_f64_emulated(int32_t M, int32_t N, int32_t K, const double *A,
+                                     int64_t lda, const double *B, int64_t ldb, double *C,
+                                     int64_t ldc, int32_t slices, void *stream);
 
 /*
  * Learned initial guess (the frequency sweep solves a coarse grid from zero,

@@ -22,9 +22,11 @@
 #include <cuda_bf16.h>
 
 #include "internal.h"
+#include "tc_ptx.h"
 
 namespace tddft {
 namespace {
+using namespace ptx;
 
 constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 3;
 constexpr int TC_THREADS = 128;
@@ -37,100 +39,6 @@ template <int BN> struct TcShape {
   static constexpr size_t SMEM = TC_STAGES * STAGE_BYTES + 1024 + 256;
   static constexpr int MIN_CTAS = BN == 64 ? 3 : 2;
 };
-constexpr uint64_t kWaitLimitNs = 2000000000ull;      // 2 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false once kWaitLimitNs has passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > kWaitLimitNs) return false;
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
-                                            int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-      : "memory");
-}
-// K-major operand tile, 128-byte swizzle: rows of 64 bf16 (128 B), 8-row
-// groups 1024 B apart; start address advanced by 32 B per K=16 step.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                 // descriptor version (tcgen05)
-  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
-  return d;
-}
-// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
   hi = __float2bfloat16_rn(x);
@@ -309,23 +217,30 @@ EncodeTiledFn encode_fn() {
 }
 }  // namespace
 
-// A 2-D bf16 operand [rows][2*Kp] ([hi | lo] planes), boxes of 64 x box_rows.
-cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows) {
+// Row-major bf16 matrix [rows][cols] as a TMA map with 128-byte swizzled
+// boxes of 64 columns x box_rows rows.
+cudaError_t encode_bf16_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols,
+                            int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  if (Kp % TC_BK != 0 || ((uintptr_t)base & 15) != 0) return cudaErrorInvalidValue;
-  cuuint64_t dims[2] = {(cuuint64_t)(2 * Kp), (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(2 * Kp) * 2};
+  if (cols % TC_BK != 0 || ((uintptr_t)base & 15) != 0) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
   cuuint32_t estr[2] = {1, 1};
-  for (int which = 0; which < 2; ++which) {
-    // box_rows for the A role (128) or the 128-wide B tile; 64 for the 64-wide B tile
-    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)(which == 0 ? box_rows : 64)};
-    CUresult r = fn(which == 0 ? &op.map : &op.map64, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                    const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  }
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// A 2-D bf16 operand [rows][2*Kp] ([hi | lo] planes), boxes of 64 x box_rows.
+cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows) {
+  if (Kp % TC_BK != 0) return cudaErrorInvalidValue;
+  // box_rows for the A role (128) or the 128-wide B tile; 64 for the 64-wide B tile
+  cudaError_t e = encode_bf16_map(&op.map, base, rows, 2 * (int64_t)Kp, box_rows);
+  if (e == cudaSuccess) e = encode_bf16_map(&op.map64, base, rows, 2 * (int64_t)Kp, 64);
+  if (e != cudaSuccess) return e;
   op.has64 = true;
   op.rows = rows;
   op.Kp = Kp;

@@ -55,7 +55,9 @@ enum KernelClass {
   // reduced-precision operator (tensor-core GEMMs, float32 sparse kernels)
   kcTcK, kcLpVertex, kcLpBeta, kcTcT1, kcTcT2, kcLpSddmm, kcLpSplit,
   // solver
-  kcGmresStep, kcGmresGather, kcGmresSelect, kcRhs, kcMisc, kcCount
+  kcGmresStep, kcGmresGather, kcGmresSelect, kcRhs, kcMisc,
+  // float64 products emulated on the tensor cores (integer slices)
+  kcOzSlice, kcOzK, kcOzT1, kcOzT2, kcCount
 };
 const char *kernel_class_name(int k);
 
@@ -75,6 +77,8 @@ struct Timer {
   void destroy();
 };
 
+struct OzWork;
+
 // Workspace of the chi0 / A operator for up to `slots` right-hand sides.
 // Real columns: c = 2*s + p, p = 0 real plane, 1 imaginary plane.
 struct OpWork {
@@ -89,6 +93,7 @@ struct OpWork {
   const int *dcnt = nullptr;  // graph replays: device count of live slots (NULL: all S)
   double *splitws = nullptr;  // split-K slices of the K product
   int64_t splitws_elems = 0;
+  OzWork *oz = nullptr;       // non-NULL: the three GEMMs are emulated float64 products
 };
 
 enum OpMode { kChi0 = 0, kKernel = 1, kA = 2 };
@@ -150,6 +155,10 @@ struct TcEpilogue {
 };
 
 cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows);
+// Row-major bf16 [rows][cols] (cols a multiple of 64) with 128-byte swizzled
+// boxes of 64 columns x box_rows rows.
+cudaError_t encode_bf16_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols,
+                            int box_rows);
 // dcnt (may be NULL): columns beyond mul_n * (*dcnt) are skipped.
 // bn: N tile of the kernel, 128 or 64.
 cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
@@ -187,6 +196,51 @@ cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp);
 // Out[c][mu] (float64) = Zin - chi0 K Zin (kA) or chi0 Zin (kChi0), reduced precision.
 cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWork &lp, int S,
                                      OpMode mode, double eps, const double *Zin, double *Out);
+
+// ---------------------------------------------------------------------------
+// Float64 products emulated on the tensor cores (ozaki.cu)
+// ---------------------------------------------------------------------------
+// A float64 operand cut into s integer slices per row: row r is
+//   x[r][k] = 2^e[r] * sum_i q_i[r][k] 2^(-7 i),   |q_1| <= 128, |q_i| <= 64,
+// stored as exact bf16 integers [rows][s*Kp] (slice i at column i*Kp).
+struct OzOperand {
+  CUtensorMap map;
+  __nv_bfloat16 *q = nullptr;
+  int *e = nullptr;
+  int64_t rows = 0;
+  int Kp = 0;
+  int s = 0;
+};
+constexpr int kOzMinSlices = 3, kOzMaxSlices = 8;
+constexpr int kOzDefaultSlices = 6;
+
+// Allocation-free set-up of an operand over caller-owned storage
+// (q: rows * s * Kp bf16, 16-byte aligned; e: rows ints).  box_rows 128 for
+// the A role, 64 for the B role.
+cudaError_t oz_operand(OzOperand &op, __nv_bfloat16 *q, int *e, int64_t rows, int Kdim, int s,
+                       int box_rows);
+// Slices of rows r < rows (live rows mul*dcnt) of X [rows][ldx] (first Kdim entries).
+cudaError_t launch_oz_slice_rows(cudaStream_t st, const double *X, int64_t ldx, int rows, int Kdim,
+                                 OzOperand &op, const int *dcnt = nullptr, int mul = 0);
+// Slices of the columns n < N (live mul*dcnt) of X [Kdim][ldx]: operand row n
+// holds column n of X.
+cudaError_t launch_oz_slice_cols(cudaStream_t st, const double *X, int64_t ldx, int Kdim, int N,
+                                 OzOperand &op, const int *dcnt = nullptr, int mul = 0);
+// C = A B^T over the sliced operands (A rows m < M, B rows n < N, shared K):
+// C[m*ldc + n] (trans = 0) or C[n*ldc + m] (trans = 1), float64.
+cudaError_t launch_gemm_oz(cudaStream_t st, const OzOperand &A, const OzOperand &B, int M, int N,
+                           double *C, int64_t ldc, int trans, int *err, const int *dcnt = nullptr,
+                           int mul_n = 0);
+
+struct OzWork {
+  int s = kOzDefaultSlices;
+  OzOperand K, XvT, Xv;   // constants, A role
+  OzOperand Z;            // [2S][s KpK] operator input, B role
+  OzOperand Bt1, Bt2;     // [2S n_occ] rows: beta^T (K = n_orb), a^T (K = n_virt); one buffer
+  int *err = nullptr;
+};
+cudaError_t oz_setup(cudaStream_t st, const DevSystem &sys, OzWork &oz, int slots,
+                     std::vector<void *> &allocs);
 
 // GMRES state of a group of right-hand sides (one per (omega, direction)).
 struct GmresState {

@@ -439,16 +439,29 @@ cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &
                                            sys.adj, wk.W, sys.Xo, wk.beta, nullptr);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  err = launch_gemm_f64(st, sys.n_virt, 6 * sys.n_occ, sys.n_orb, sys.XvT, sys.n_orb, wk.beta,
-                        6 * sys.n_occ, a3, 6 * sys.n_occ);
+  const int n6 = 6 * sys.n_occ;
+  if (wk.oz) {
+    err = launch_oz_slice_cols(st, wk.beta, n6, sys.n_orb, n6, wk.oz->Bt1);
+    if (err == cudaSuccess)
+      err = launch_gemm_oz(st, wk.oz->XvT, wk.oz->Bt1, sys.n_virt, n6, a3, n6, 0, wk.oz->err);
+  } else {
+    err = launch_gemm_f64(st, sys.n_virt, n6, sys.n_orb, sys.XvT, sys.n_orb, wk.beta, n6, a3, n6);
+  }
   if (err != cudaSuccess) return err;
   // per right-hand side: D(omega) a_k, X_virt a, block dot
   const int64_t ncolE = (int64_t)2 * S * sys.n_occ;
   rhs_expand_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
       sys.n_virt, S, sys.n_occ, g0, sys.occ_value, sys.energy, omega_all, eps, a3, wk.abuf);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  err = launch_gemm_f64(st, sys.n_orb, (int)ncolE, sys.n_virt, sys.Xv, sys.n_virt, wk.abuf, ncolE,
-                        wk.gamma, ncolE);
+  if (wk.oz) {
+    err = launch_oz_slice_cols(st, wk.abuf, ncolE, sys.n_virt, (int)ncolE, wk.oz->Bt2);
+    if (err == cudaSuccess)
+      err = launch_gemm_oz(st, wk.oz->Xv, wk.oz->Bt2, sys.n_orb, (int)ncolE, wk.gamma, ncolE, 0,
+                           wk.oz->err);
+  } else {
+    err = launch_gemm_f64(st, sys.n_orb, (int)ncolE, sys.n_virt, sys.Xv, sys.n_virt, wk.abuf,
+                          ncolE, wk.gamma, ncolE);
+  }
   if (err != cudaSuccess) return err;
   return launch_block_dot(st, true, 2 * S, sys, sys.Vpad, sys.Xo, wk.gamma, nullptr, 0, Out,
                           nullptr);
@@ -464,9 +477,19 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
   const double *Y = Zin;
   if (mode == kKernel || mode == kA) {
     // Y = Z K  (K symmetric, so row c of Y is K z_c)
-    Scope sc(wk.timer, st, kcGemmK, 2.0 * ncols * (double)np * np);
-    err = launch_gemm_f64(st, ncols, np, np, Zin, np, sys.K, np, (mode == kKernel) ? Out : wk.Y, np,
-                          wk.dcnt, 2, 0, wk.splitws, wk.splitws_elems);
+    double *Yout = (mode == kKernel) ? Out : wk.Y;
+    if (wk.oz) {
+      // emulated: (K z_c)_mu = sum_nu K[mu][nu] z_c[nu], stored transposed
+      Scope sc(wk.timer, st, kcOzK, 2.0 * ncols * (double)np * np);
+      err = launch_oz_slice_rows(st, Zin, np, ncols, np, wk.oz->Z, wk.dcnt, 2);
+      if (err == cudaSuccess)
+        err = launch_gemm_oz(st, wk.oz->K, wk.oz->Z, np, ncols, Yout, np, 1, wk.oz->err, wk.dcnt,
+                             2);
+    } else {
+      Scope sc(wk.timer, st, kcGemmK, 2.0 * ncols * (double)np * np);
+      err = launch_gemm_f64(st, ncols, np, np, Zin, np, sys.K, np, Yout, np, wk.dcnt, 2, 0,
+                            wk.splitws, wk.splitws_elems);
+    }
     if (err != cudaSuccess || mode == kKernel) return err;
     Y = wk.Y;
   }
@@ -487,7 +510,16 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
   const int64_t ncolE = (int64_t)ncols * sys.n_occ;
   if (ncolE > INT32_MAX) return cudaErrorInvalidValue;
   const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)ncolE;
-  {
+  if (wk.oz) {
+    // emulated: slices of the columns of beta (rows of beta^T), then X_virt^T beta
+    Scope sc(wk.timer, st, kcOzT1, tflops);
+    err = launch_oz_slice_cols(st, wk.beta, ncolE, sys.n_orb, (int)ncolE, wk.oz->Bt1, wk.dcnt,
+                               2 * sys.n_occ);
+    if (err == cudaSuccess)
+      err = launch_gemm_oz(st, wk.oz->XvT, wk.oz->Bt1, sys.n_virt, (int)ncolE, wk.abuf, ncolE, 0,
+                           wk.oz->err, wk.dcnt, 2 * sys.n_occ);
+    if (err != cudaSuccess) return err;
+  } else {
     Scope sc(wk.timer, st, kcGemmT1, tflops);
     err = launch_gemm_f64(st, sys.n_virt, (int)ncolE, sys.n_orb, sys.XvT, sys.n_orb, wk.beta,
                           ncolE, wk.abuf, ncolE, wk.dcnt, 0, 2 * sys.n_occ);
@@ -499,7 +531,15 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
         sys.n_virt, S, sys.n_occ, sys.occ_value, sys.energy, wk.omega, eps, wk.abuf, wk.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  {
+  if (wk.oz) {
+    Scope sc(wk.timer, st, kcOzT2, tflops);
+    err = launch_oz_slice_cols(st, wk.abuf, ncolE, sys.n_virt, (int)ncolE, wk.oz->Bt2, wk.dcnt,
+                               2 * sys.n_occ);
+    if (err == cudaSuccess)
+      err = launch_gemm_oz(st, wk.oz->Xv, wk.oz->Bt2, sys.n_orb, (int)ncolE, wk.gamma, ncolE, 0,
+                           wk.oz->err, wk.dcnt, 2 * sys.n_occ);
+    if (err != cudaSuccess) return err;
+  } else {
     Scope sc(wk.timer, st, kcGemmT2, tflops);
     err = launch_gemm_f64(st, sys.n_orb, (int)ncolE, sys.n_virt, sys.Xv, sys.n_virt, wk.abuf,
                           ncolE, wk.gamma, ncolE, wk.dcnt, 0, 2 * sys.n_occ);

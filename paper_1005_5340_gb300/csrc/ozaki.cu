@@ -1,0 +1,586 @@
+// Float64 matrix products emulated on the bf16 tensor cores (sm_103a,
+// tcgen05 + TMA + mbarrier, inline PTX) by error-free splitting of both
+// operands into integer slices (the Ozaki scheme).
+//
+// Every row of an operand is scaled by a power of two 2^e (|x| < 2^e over the
+// row) and cut into s integer slices,
+//     x = 2^e sum_{i=1..s} q_i 2^(-7 i),   q_1 in [-128, 128], q_i in [-64, 64],
+// each q_i an exact bf16.  The product of two rows is then
+//     2^(eA+eB) sum_t 2^(-7 t) G_t,        G_t = sum_{i+j=t} sum_k qA_i qB_j ,
+// kept for t <= s+1 (pairs below the last slice's weight are dropped).  The
+// t-1 pairs of a group contribute at most 2^12 (s+2) per k, so over a K chunk
+// of L <= 2^12 / (s+2) entries every partial sum of G_t is an integer of at
+// most 2^24 and the float32 accumulation in tensor memory is exact.  The
+// epilogue warps read each G_t of a chunk, convert it to an integer and add
+// it, shifted to its weight, into one 64-bit integer accumulator per output;
+// u = max(0, 7s - 35) low bits are dropped so that the accumulator stays below
+// 2^63 over up to 1024 chunks.  The float64 result is 2^(eA+eB+u-7(s+1)) acc,
+// with an error of about (1 + (s+1)/4) 2^(-7s) 2^(eA+eB) K at most (2^-42
+// relative for s = 6).
+//
+// One CTA computes a 128 x 64 output tile:
+//   warp 0     TMA producer: per 64-deep K block, the s slices of the A tile
+//              (16 KB each) and of the B tile (8 KB each), one stage per
+//              slice index, into a 9-stage ring (128-byte swizzle)
+//   warp 1     tcgen05.mma issuer (M=128, N=64, K=16): once slice i of a K
+//              block has landed, every pair (i, j) and (j, i) with j <= i and
+//              i + j <= s+1 goes to the TMEM accumulator of group i+j (s
+//              groups x 64 columns); the block's stages are released together
+//              after its last MMA
+//   warps 2-9  epilogue (two warps per TMEM lane quadrant, 32 columns each):
+//              per chunk, TMEM -> registers -> int64 accumulators; at the end
+//              the float64 tile is stored (C or C^T)
+// Every mbarrier wait is bounded; on expiry the CTA records an error code,
+// stops issuing work, waits (bounded) for its TMA copies in flight and still
+// frees its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "tc_ptx.h"
+
+namespace tddft {
+namespace {
+using namespace ptx;
+
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64, OZ_STAGES = 9;
+constexpr int OZ_EPI_WARPS = 8;                        // 2 per TMEM lane quadrant
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;      // producer, MMA, epilogue
+constexpr int OZ_EPI_COLS = OZ_BN / 2;                  // columns per epilogue thread
+constexpr uint32_t OZ_A_BYTES = OZ_BM * OZ_BK * 2;   // 16 KB
+constexpr uint32_t OZ_B_BYTES = OZ_BN * OZ_BK * 2;   //  8 KB
+constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
+constexpr size_t OZ_SMEM = (size_t)OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+
+struct OzArgs {
+  int M, N, Kp;
+  int ns;       // slices (the kernel's template argument)
+  int cb;       // K blocks per exact chunk
+  const int *eA, *eB;
+  double *C;
+  int64_t ldc;
+  int trans;    // 0: C[m*ldc+n], 1: C[n*ldc+m]
+  int vec;      // trans == 0 and 16-byte aligned rows: double2 stores
+  int *err;
+  const int *dcnt;
+  int mul_n;
+};
+
+// Low bits dropped from the integer accumulator for S slices: with u(S) the
+// largest value, 2^(24 + 7(S-1) - u) summed over up to 1024 chunks (and the
+// lower groups, < 1% more) stays below 2^63.
+__host__ __device__ constexpr int oz_drop_bits(int S) { return 7 * S - 35 > 0 ? 7 * S - 35 : 0; }
+constexpr int kOzMaxChunks = 1024;
+
+// acc += G_t of every group (t = grp + 2) read from tensor memory (this
+// thread's 32 columns at tcol), at weight 2^(7 (S - 1 - grp) - u); a negative
+// weight is a rounded right shift of the (exact, < 2^25) group sum.  One
+// group's values are live at a time (the loop is not unrolled).
+// (ns == S, passed at run time so that the loop stays rolled)
+template <int S>
+__device__ __forceinline__ void read_groups(uint32_t tcol, long long (&acc)[OZ_EPI_COLS], int ns) {
+#pragma unroll 1
+  for (int grp = 0; grp < ns; ++grp) {
+    const int sh = 7 * (S - 1 - grp) - oz_drop_bits(S);
+    float v[32];
+    tmem_ld32(tcol + (uint32_t)(grp * OZ_BN), v);
+    if (sh >= 0) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] += (long long)__float2int_rn(v[j]) << sh;
+    } else {
+      const int r = -sh, half = 1 << (r - 1);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] += (long long)((__float2int_rn(v[j]) + half) >> r);
+    }
+  }
+}
+
+// 2^e for a normal-range exponent (clamped to [-1022, 1023])
+__device__ __forceinline__ double pow2(int e) {
+  e = max(-1022, min(1023, e));
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+template <int S>
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                      const __grid_constant__ CUtensorMap mapB, OzArgs a) {
+  int N = a.N;
+  if (a.dcnt) N = (int)min((int64_t)N, (int64_t)a.mul_n * (*a.dcnt));
+  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
+  if (n0 >= N) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
+  uint64_t *empty = full + OZ_STAGES;
+  uint64_t *tfull = empty + OZ_STAGES;
+  uint64_t *tempty = tfull + 1;
+  uint32_t *tslot = (uint32_t *)(tempty + 1);
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int s = S;
+  const int nkb = a.Kp / OZ_BK, cb = a.cb;
+  const int nchunks = (nkb + cb - 1) / cb;
+  constexpr uint32_t tcols = S <= 4 ? 256u : 512u;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < OZ_STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, OZ_EPI_WARPS);   // one arrival per epilogue warp
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: stage g = kb * s + i holds slice i of K block kb
+      int g = 0;
+      bool ok = true;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        for (int i = 0; i < s; ++i, ++g) {
+          const int slot = g % OZ_STAGES;
+          const uint32_t ph = (uint32_t)(g / OZ_STAGES) & 1u;
+          if (!mbar_wait(&empty[slot], ph ^ 1u)) {
+            atomicExch(a.err, 21);
+            abort_flag = 1;
+            ok = false;
+            break;
+          }
+          if (*(volatile int *)&abort_flag) {
+            ok = false;
+            break;
+          }
+          uint8_t *sa = smem + slot * OZ_STAGE_BYTES;
+          mbar_expect_tx(&full[slot], OZ_STAGE_BYTES);
+          tma_load_2d(sa, &mapA, &full[slot], i * a.Kp + kb * OZ_BK, m0);
+          tma_load_2d(sa + OZ_A_BYTES, &mapB, &full[slot], i * a.Kp + kb * OZ_BK, n0);
+        }
+      }
+      // copies in flight: the last OZ_STAGES stages issued (each the latest
+      // use of its slot) must have landed before the CTA may exit
+      for (int h = max(0, g - OZ_STAGES); h < g; ++h)
+        mbar_wait(&full[h % OZ_STAGES], (uint32_t)(h / OZ_STAGES) & 1u);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(OZ_BM, OZ_BN);
+      const uint32_t base = smem_u32(smem);
+      int g = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        if (c > 0) {
+          // the epilogue has read the previous chunk's groups
+          if (!mbar_wait(tempty, (uint32_t)(c - 1) & 1u)) {
+            atomicExch(a.err, 22);
+            abort_flag = 1;
+            ok = false;
+            break;
+          }
+          fence_after();
+        }
+        uint32_t written = 0;
+        const int kb1 = min(nkb, (c + 1) * cb);
+        for (int kb = c * cb; kb < kb1 && ok; ++kb) {
+          for (int i = 0; i < s; ++i) {
+            const int gi = g + i;
+            if (!mbar_wait(&full[gi % OZ_STAGES], (uint32_t)(gi / OZ_STAGES) & 1u)) {
+              atomicExch(a.err, 23);
+              abort_flag = 1;
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint32_t si = base + (uint32_t)(gi % OZ_STAGES) * OZ_STAGE_BYTES;
+            const int jmax = min(i, s - 1 - i);
+            for (int j = 0; j <= jmax; ++j) {
+              const uint32_t sj = base + (uint32_t)((g + j) % OZ_STAGES) * OZ_STAGE_BYTES;
+              const int grp = i + j;
+              const uint32_t d = tmem + (uint32_t)(grp * OZ_BN);
+              uint32_t acc = (written >> grp) & 1u;
+              // A slice i x B slice j
+#pragma unroll
+              for (int k = 0; k < OZ_BK / 16; ++k)
+                mma_bf16(d, desc_sw128(si + 32 * k), desc_sw128(sj + OZ_A_BYTES + 32 * k), idesc,
+                         (acc | (uint32_t)k) ? 1u : 0u);
+              if (j < i) {
+                // A slice j x B slice i
+#pragma unroll
+                for (int k = 0; k < OZ_BK / 16; ++k)
+                  mma_bf16(d, desc_sw128(sj + 32 * k), desc_sw128(si + OZ_A_BYTES + 32 * k),
+                           idesc, 1u);
+              }
+              written |= 1u << grp;
+            }
+          }
+          if (!ok) break;
+          for (int i = 0; i < s; ++i) mma_commit(&empty[(g + i) % OZ_STAGES]);
+          g += s;
+        }
+        if (ok) mma_commit(tfull);
+      }
+    }
+    __syncwarp();
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of the tile)
+    // and columns 32 h .. 32 h + 31 of every group, h = (w - 2) / 4
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int m = m0 + q * 32 + lane;
+    const int nc = n0 + h * OZ_EPI_COLS;
+    const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * OZ_EPI_COLS);
+    long long acc[OZ_EPI_COLS];
+#pragma unroll
+    for (int j = 0; j < OZ_EPI_COLS; ++j) acc[j] = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      bool have = mbar_wait(tfull, (uint32_t)c & 1u);
+      // tcgen05.ld is warp-collective: one decision per warp
+      have = __all_sync(0xffffffffu, have && !*(volatile int *)&abort_flag);
+      if (!have) {
+        if (lane == 0) atomicExch(a.err, 24);
+        abort_flag = 1;
+        ok = false;
+        break;
+      }
+      fence_after();
+      read_groups<S>(tcol, acc, a.ns);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+    }
+    if (ok && m < a.M && nc < N) {
+      // C = acc 2^(eA + eB + u - 7(S+1)), as two exact power-of-two factors
+      const double fa = pow2(a.eA[m] + oz_drop_bits(S) - 7 * (S + 1));
+      if (!a.trans) {
+        double *crow = a.C + (int64_t)m * a.ldc + nc;
+        if (a.vec && nc + OZ_EPI_COLS <= N) {
+#pragma unroll
+          for (int j = 0; j < OZ_EPI_COLS; j += 2) {
+            double2 w;
+            w.x = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+            w.y = (double)acc[j + 1] * fa * pow2(__ldg(a.eB + nc + j + 1));
+            *(double2 *)(crow + j) = w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < OZ_EPI_COLS; ++j)
+            if (nc + j < N) crow[j] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < OZ_EPI_COLS; ++j)
+          if (nc + j < N)
+            a.C[(int64_t)(nc + j) * a.ldc + m] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Slicing
+// ---------------------------------------------------------------------------
+// Exponent e with |x| < 2^e for every x of a row whose largest magnitude is mx.
+__device__ __forceinline__ int row_exponent(double mx) {
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  return e;
+}
+
+// s slices of y = x 2^(7-e) (|y| < 128): q_1 = rint(y), then the remainder
+// (exact in float64) scaled by 2^7 and rounded again, and so on.
+__device__ __forceinline__ void store_slices(double y0, double y1, int s, int Kp,
+                                             __nv_bfloat16 *dst) {
+  for (int i = 0; i < s; ++i) {
+    const double q0 = rint(y0), q1 = rint(y1);
+    *(__nv_bfloat162 *)(dst + (int64_t)i * Kp) = __floats2bfloat162_rn((float)q0, (float)q1);
+    y0 = (y0 - q0) * 128.0;
+    y1 = (y1 - q1) * 128.0;
+  }
+}
+
+__global__ void oz_slice_rows_kernel(int rows, int Kdim, const double *__restrict__ X, int64_t ldx,
+                                     int s, int Kp, __nv_bfloat16 *__restrict__ Q,
+                                     int *__restrict__ E, const int *dcnt, int mul) {
+  __shared__ double red[32];
+  int live = rows;
+  if (dcnt) live = min(rows, mul * (*dcnt));
+  for (int r = blockIdx.x; r < live; r += gridDim.x) {
+    const double *x = X + (int64_t)r * ldx;
+    double mx = 0.0;
+    for (int k = threadIdx.x; k < Kdim; k += blockDim.x) mx = fmax(mx, fabs(x[k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const int e = row_exponent(red[0]);
+    __syncthreads();
+    if (threadIdx.x == 0) E[r] = e;
+    const double sc = ldexp(1.0, 7 - e);
+    __nv_bfloat16 *qr = Q + (int64_t)r * s * Kp;
+    for (int k = 2 * threadIdx.x; k < Kp; k += 2 * blockDim.x) {
+      const double y0 = k < Kdim ? x[k] * sc : 0.0;
+      const double y1 = k + 1 < Kdim ? x[k + 1] * sc : 0.0;
+      store_slices(y0, y1, s, Kp, qr + k);
+    }
+  }
+}
+
+// 32 columns per CTA (256 threads): column maxima, then 64-row tiles staged
+// through shared memory and written as rows of the transposed operand.
+__global__ void __launch_bounds__(256) oz_slice_cols_kernel(int Kdim, int N,
+                                                            const double *__restrict__ X,
+                                                            int64_t ldx, int s, int Kp,
+                                                            __nv_bfloat16 *__restrict__ Q,
+                                                            int *__restrict__ E, const int *dcnt,
+                                                            int mul) {
+  __shared__ double tile[32][65];
+  __shared__ double red[8][32];
+  __shared__ double scl[32];
+  int live = N;
+  if (dcnt) live = (int)min((int64_t)N, (int64_t)mul * (*dcnt));
+  const int n0 = blockIdx.x * 32;
+  if (n0 >= live) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int n = n0 + tx;
+  double mx = 0.0;
+  if (n < live)
+    for (int k = ty; k < Kdim; k += 8) mx = fmax(mx, fabs(X[(int64_t)k * ldx + n]));
+  red[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0) {
+    double v = 0.0;
+    for (int i = 0; i < 8; ++i) v = fmax(v, red[i][tx]);
+    const int e = row_exponent(v);
+    if (n < live) E[n] = e;
+    scl[tx] = ldexp(1.0, 7 - e);
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < Kp; k0 += 64) {
+    for (int rr = ty; rr < 64; rr += 8) {
+      const int k = k0 + rr;
+      tile[tx][rr] = (k < Kdim && n < live) ? X[(int64_t)k * ldx + n] * scl[tx] : 0.0;
+    }
+    __syncthreads();
+    for (int cc = 0; cc < 4; ++cc) {
+      const int col = ty * 4 + cc;
+      if (n0 + col < live)
+        store_slices(tile[col][2 * tx], tile[col][2 * tx + 1], s, Kp,
+                     Q + (int64_t)(n0 + col) * s * Kp + k0 + 2 * tx);
+    }
+    __syncthreads();
+  }
+}
+
+int chunk_blocks(int s) { return std::max(1, 4096 / (s + 2) / OZ_BK); }
+
+template <int S>
+cudaError_t launch_oz_kernel(cudaStream_t st, dim3 grid, const CUtensorMap &mA,
+                             const CUtensorMap &mB, const OzArgs &a) {
+  ozaki_gemm_kernel<S><<<grid, OZ_THREADS, OZ_SMEM, st>>>(mA, mB, a);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(ozaki_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)OZ_SMEM);
+}
+}  // namespace
+
+// Dynamic shared memory limits of every slice count (once; outside any
+// stream capture).
+cudaError_t oz_init_attributes() {
+  static cudaError_t done = cudaErrorNotReady;
+  if (done == cudaSuccess) return done;
+  cudaError_t e = set_smem_attr<3>();
+  if (e == cudaSuccess) e = set_smem_attr<4>();
+  if (e == cudaSuccess) e = set_smem_attr<5>();
+  if (e == cudaSuccess) e = set_smem_attr<6>();
+  if (e == cudaSuccess) e = set_smem_attr<7>();
+  if (e == cudaSuccess) e = set_smem_attr<8>();
+  done = e;
+  return e;
+}
+
+cudaError_t oz_operand(OzOperand &op, __nv_bfloat16 *q, int *e, int64_t rows, int Kdim, int s,
+                       int box_rows) {
+  if (s < kOzMinSlices || s > kOzMaxSlices || rows < 1 || Kdim < 1) return cudaErrorInvalidValue;
+  op.q = q;
+  op.e = e;
+  op.rows = rows;
+  op.Kp = round_up(Kdim, OZ_BK);
+  op.s = s;
+  return encode_bf16_map(&op.map, q, rows, (int64_t)s * op.Kp, box_rows);
+}
+
+cudaError_t launch_oz_slice_rows(cudaStream_t st, const double *X, int64_t ldx, int rows, int Kdim,
+                                 OzOperand &op, const int *dcnt, int mul) {
+  if (rows <= 0) return cudaSuccess;
+  if (rows > op.rows || Kdim > op.Kp) return cudaErrorInvalidValue;
+  const int grid = std::min(rows, 152 * 8);
+  oz_slice_rows_kernel<<<grid, 256, 0, st>>>(rows, Kdim, X, ldx, op.s, op.Kp, op.q, op.e, dcnt,
+                                             mul);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_slice_cols(cudaStream_t st, const double *X, int64_t ldx, int Kdim, int N,
+                                 OzOperand &op, const int *dcnt, int mul) {
+  if (N <= 0) return cudaSuccess;
+  if (N > op.rows || Kdim > op.Kp) return cudaErrorInvalidValue;
+  oz_slice_cols_kernel<<<(N + 31) / 32, 256, 0, st>>>(Kdim, N, X, ldx, op.s, op.Kp, op.q, op.e,
+                                                      dcnt, mul);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_oz(cudaStream_t st, const OzOperand &A, const OzOperand &B, int M, int N,
+                           double *C, int64_t ldc, int trans, int *err, const int *dcnt,
+                           int mul_n) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (A.Kp != B.Kp || A.s != B.s || M > A.rows || N > B.rows) return cudaErrorInvalidValue;
+  cudaError_t e = oz_init_attributes();
+  if (e != cudaSuccess) return e;
+  OzArgs a;
+  a.M = M;
+  a.N = N;
+  a.Kp = A.Kp;
+  a.ns = A.s;
+  a.cb = chunk_blocks(A.s);
+  if ((A.Kp / OZ_BK + a.cb - 1) / a.cb > kOzMaxChunks) return cudaErrorInvalidValue;
+  a.eA = A.e;
+  a.eB = B.e;
+  a.C = C;
+  a.ldc = ldc;
+  a.trans = trans;
+  a.vec = (!trans && (ldc % 2) == 0 && ((uintptr_t)C & 15) == 0) ? 1 : 0;
+  a.err = err;
+  a.dcnt = dcnt;
+  a.mul_n = mul_n;
+  dim3 grid((M + OZ_BM - 1) / OZ_BM, (N + OZ_BN - 1) / OZ_BN);
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  switch (A.s) {
+    case 3: return launch_oz_kernel<3>(st, grid, A.map, B.map, a);
+    case 4: return launch_oz_kernel<4>(st, grid, A.map, B.map, a);
+    case 5: return launch_oz_kernel<5>(st, grid, A.map, B.map, a);
+    case 6: return launch_oz_kernel<6>(st, grid, A.map, B.map, a);
+    case 7: return launch_oz_kernel<7>(st, grid, A.map, B.map, a);
+    case 8: return launch_oz_kernel<8>(st, grid, A.map, B.map, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Constants sliced once; dynamic operands sized for `slots` right-hand sides.
+cudaError_t oz_setup(cudaStream_t st, const DevSystem &sys, OzWork &oz, int slots,
+                     std::vector<void *> &allocs) {
+  const int s = oz.s, np = sys.n_prod, no = sys.n_orb, nv = sys.n_virt;
+  const int64_t rowsB = 2 * (int64_t)slots * sys.n_occ;
+  const int64_t rows6 = 6 * (int64_t)sys.n_occ;   // the three dipole columns
+  const int64_t rowsT = std::max(rowsB, rows6);
+  const int KpK = round_up(np, OZ_BK), Kp1 = round_up(no, OZ_BK), Kp2 = round_up(nv, OZ_BK);
+  auto alloc = [&](size_t bytes, void **p) -> cudaError_t {
+    cudaError_t e = cudaMalloc(p, bytes + 16);
+    if (e == cudaSuccess) allocs.push_back(*p);
+    return e;
+  };
+  void *qK, *qXvT, *qXv, *qZ, *qT, *e;
+  const size_t bf = sizeof(__nv_bfloat16);
+  const int64_t rowsZ = 2 * (int64_t)slots;
+  cudaError_t r = alloc((size_t)np * s * KpK * bf, &qK);
+  if (r == cudaSuccess) r = alloc((size_t)nv * s * Kp1 * bf, &qXvT);
+  if (r == cudaSuccess) r = alloc((size_t)no * s * Kp2 * bf, &qXv);
+  if (r == cudaSuccess) r = alloc((size_t)rowsZ * s * KpK * bf, &qZ);
+  if (r == cudaSuccess) r = alloc((size_t)rowsT * s * std::max(Kp1, Kp2) * bf, &qT);
+  const int64_t ne = (int64_t)np + nv + no + rowsZ + 2 * rowsT;
+  if (r == cudaSuccess) r = alloc((size_t)ne * sizeof(int), &e);
+  if (r == cudaSuccess) r = alloc(sizeof(int), (void **)&oz.err);
+  if (r != cudaSuccess) return r;
+  int *ep = (int *)e;
+  auto bq = [](void *p) { return (__nv_bfloat16 *)p; };
+  r = oz_operand(oz.K, bq(qK), ep, np, np, s, OZ_BM);
+  ep += np;
+  if (r == cudaSuccess) r = oz_operand(oz.XvT, bq(qXvT), ep, nv, no, s, OZ_BM);
+  ep += nv;
+  if (r == cudaSuccess) r = oz_operand(oz.Xv, bq(qXv), ep, no, nv, s, OZ_BM);
+  ep += no;
+  if (r == cudaSuccess) r = oz_operand(oz.Z, bq(qZ), ep, rowsZ, np, s, OZ_BN);
+  ep += rowsZ;
+  if (r == cudaSuccess) r = oz_operand(oz.Bt1, bq(qT), ep, rowsT, no, s, OZ_BN);
+  ep += rowsT;
+  if (r == cudaSuccess) r = oz_operand(oz.Bt2, bq(qT), ep, rowsT, nv, s, OZ_BN);
+  if (r == cudaSuccess) r = oz_init_attributes();
+  if (r == cudaSuccess) r = cudaMemsetAsync(oz.err, 0, sizeof(int), st);
+  if (r == cudaSuccess) r = launch_oz_slice_rows(st, sys.K, np, np, np, oz.K);
+  if (r == cudaSuccess) r = launch_oz_slice_rows(st, sys.XvT, no, nv, no, oz.XvT);
+  if (r == cudaSuccess) r = launch_oz_slice_rows(st, sys.Xv, nv, no, nv, oz.Xv);
+  return r;
+}
+
+}  // namespace tddft
+
+// ---------------------------------------------------------------------------
+// C boundary: one emulated float64 product on device buffers
+// ---------------------------------------------------------------------------
+extern "C" tddft_status tddft_gemm_f64_emulated(int32_t M, int32_t N, int32_t K, const double *A,
+                                                int64_t lda, const double *B, int64_t ldb,
+                                                double *C, int64_t ldc, int32_t slices,
+                                                void *stream) {
+  using namespace tddft;
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return TDDFT_ERR_INVALID_ARG;
+  if (slices < kOzMinSlices || slices > kOzMaxSlices) return TDDFT_ERR_INVALID_ARG;
+  if (lda < K || ldb < N || ldc < N) return TDDFT_ERR_SHAPE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int Kp = round_up(K, OZ_BK);
+  std::vector<void *> allocs;
+  auto alloc = [&](size_t bytes, void **p) -> cudaError_t {
+    cudaError_t e = cudaMalloc(p, bytes + 16);
+    if (e == cudaSuccess) allocs.push_back(*p);
+    return e;
+  };
+  void *qa = nullptr, *qb = nullptr, *ea = nullptr, *eb = nullptr, *err = nullptr;
+  cudaError_t e = alloc((size_t)M * slices * Kp * sizeof(__nv_bfloat16), &qa);
+  if (e == cudaSuccess) e = alloc((size_t)N * slices * Kp * sizeof(__nv_bfloat16), &qb);
+  if (e == cudaSuccess) e = alloc((size_t)M * sizeof(int), &ea);
+  if (e == cudaSuccess) e = alloc((size_t)N * sizeof(int), &eb);
+  if (e == cudaSuccess) e = alloc(sizeof(int), &err);
+  OzOperand oa, ob;
+  if (e == cudaSuccess) e = oz_operand(oa, (__nv_bfloat16 *)qa, (int *)ea, M, K, slices, OZ_BM);
+  if (e == cudaSuccess) e = oz_operand(ob, (__nv_bfloat16 *)qb, (int *)eb, N, K, slices, OZ_BN);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_oz_slice_rows(st, A, lda, M, K, oa);
+  if (e == cudaSuccess) e = launch_oz_slice_cols(st, B, ldb, K, N, ob);
+  if (e == cudaSuccess) e = launch_gemm_oz(st, oa, ob, M, N, C, ldc, 0, (int *)err);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  for (void *p : allocs) cudaFree(p);
+  if (e == cudaErrorMemoryAllocation) return TDDFT_ERR_NOMEM;
+  if (e != cudaSuccess) return TDDFT_ERR_CUDA;
+  return herr ? TDDFT_ERR_TIMEOUT : TDDFT_OK;
+}

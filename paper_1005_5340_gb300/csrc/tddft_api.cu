@@ -17,6 +17,8 @@ struct tddft_ctx {
   OpWork wk;
   LpWork lp;
   bool lowprec = false;
+  OzWork oz;
+  bool emu = false;
   GmresState gs;
   Timer timer;
   tddft_options opts{};
@@ -95,7 +97,8 @@ const char *kernel_class_name(int k) {
       "f64_gemm_K",  "f64_vertex",   "f64_beta",      "f64_gemm_T1",  "f64_dscale",
       "f64_gemm_T2", "f64_block_dot", "tc_gemm_K",    "lp_vertex",    "lp_beta",
       "tc_gemm_T1_dscale", "tc_gemm_T2", "lp_block_dot", "lp_split_z", "gmres_step",
-      "gmres_gather", "gmres_select", "rhs_formation", "misc"};
+      "gmres_gather", "gmres_select", "rhs_formation", "misc", "emu_slice", "emu_gemm_K",
+      "emu_gemm_T1", "emu_gemm_T2"};
   return (k >= 0 && k < kcCount) ? names[k] : "?";
 }
 
@@ -241,9 +244,10 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   if (!out) return fail(nullptr, TDDFT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!o) return fail(nullptr, TDDFT_ERR_INVALID_ARG, "options are NULL");
-  if (o->prec != TDDFT_PREC_FP64 && o->prec != TDDFT_PREC_BF16X3_IR)
+  if (o->prec < TDDFT_PREC_FP64 || o->prec > TDDFT_PREC_BF16X3_IR_EMU)
     return fail(nullptr, TDDFT_ERR_UNSUPPORTED, "unknown precision");
-  if (o->prec != TDDFT_PREC_FP64 && !(o->inner_tol > 0.0 && o->inner_tol < 1.0))
+  const bool refine = o->prec == TDDFT_PREC_BF16X3_IR || o->prec == TDDFT_PREC_BF16X3_IR_EMU;
+  if (refine && !(o->inner_tol > 0.0 && o->inner_tol < 1.0))
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
   if (o->restart < 1 || o->restart > 256 || o->max_restarts < 1 || !(o->tol > 0.0) ||
       !std::isfinite(o->tol) || o->batch < 1)
@@ -394,7 +398,13 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   AL(g.V, S * (m + 1) * 2 * np); AL(g.x, S * 2 * np); AL(g.b, S * 2 * np);
   AL(g.act, S); AL(g.act2, S); AL(g.count, 2); AL(g.rho0, S);
   g.inner_tol = 0.0;
-  c->lowprec = o->prec == TDDFT_PREC_BF16X3_IR;
+  c->lowprec = refine;
+  c->emu = o->prec == TDDFT_PREC_FP64_EMU || o->prec == TDDFT_PREC_BF16X3_IR_EMU;
+  if (e == cudaSuccess && c->emu) {
+    e = oz_setup(c->st, d, c->oz, (int)S, c->dev_allocs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    w.oz = &c->oz;
+  }
   if (c->lowprec) {
     g.inner_tol = o->inner_tol;
     LpWork &L = c->lp;
@@ -516,13 +526,15 @@ static tddft_status boundary_apply(tddft_ctx *c, OpMode mode, int32_t n_rhs, con
 }
 
 static tddft_status check_device_error(tddft_ctx *c) {
-  if (!c->lowprec) return TDDFT_OK;
-  int h = 0;
-  CUDA_TRY(c, cudaMemcpy(&h, c->lp.err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (h != 0) {
-    cudaMemset(c->lp.err, 0, sizeof(int));
-    return fail(c, TDDFT_ERR_TIMEOUT,
-                "a tensor-core GEMM wait gave up (code " + std::to_string(h) + ")");
+  for (int *flag : {c->lowprec ? c->lp.err : nullptr, c->emu ? c->oz.err : nullptr}) {
+    if (!flag) continue;
+    int h = 0;
+    CUDA_TRY(c, cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) {
+      cudaMemset(flag, 0, sizeof(int));
+      return fail(c, TDDFT_ERR_TIMEOUT,
+                  "a tensor-core GEMM wait gave up (code " + std::to_string(h) + ")");
+    }
   }
   return TDDFT_OK;
 }

@@ -20,7 +20,7 @@ OK, ERR_INVALID_ARG, ERR_SHAPE, ERR_NOMEM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIME
 STATUS_NAMES = ["OK", "INVALID_ARG", "SHAPE", "NOMEM", "CUDA", "NOT_CONVERGED", "TIMEOUT",
                 "UNSUPPORTED"]
 DEVICE_PTRS = 1
-PREC = {"fp64": 0, "bf16x3": 2}
+PREC = {"fp64": 0, "fp64emu": 1, "bf16x3": 2, "bf16x3emu": 3}
 
 
 class TddftError(RuntimeError):
@@ -95,6 +95,9 @@ SIGNATURES = {
                                         _P, _P, _P]),
     "tddft_selftest_gemm": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "tddft_gemm_f64_emulated": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                               _P, ctypes.c_int64, _P, ctypes.c_int64, _P,
+                                               ctypes.c_int64, ctypes.c_int32, _P]),
     "tddft_last_error": (ctypes.c_char_p, [_P]),
     "tddft_destroy": (None, [_P]),
 }
@@ -474,6 +477,30 @@ def selftest_gemm(M: int, N: int, K: int, seed: int = 1) -> float:
     if st != OK:
         raise TddftError(st, "tensor-core GEMM self-test failed")
     return err.value
+
+
+def gemm_f64_emulated(A, B, slices: int = 6, out=None):
+    """C = A @ B for float64 CUDA matrices (row-major, unit column stride),
+    emulated on the tensor cores with `slices` integer slices per operand.
+    Runs on the current torch stream."""
+    import torch
+    if A.dtype != torch.float64 or B.dtype != torch.float64 or not (A.is_cuda and B.is_cuda):
+        raise ValueError("A and B must be float64 CUDA tensors")
+    if A.dim() != 2 or B.dim() != 2 or A.shape[1] != B.shape[0]:
+        raise ValueError("shapes do not match")
+    if A.stride(1) != 1 or B.stride(1) != 1:
+        raise ValueError("rows must be contiguous")
+    M, K = A.shape
+    N = B.shape[1]
+    C = out if out is not None else torch.empty((M, N), dtype=torch.float64, device=A.device)
+    if C.stride(1) != 1 or tuple(C.shape) != (M, N):
+        raise ValueError("bad output")
+    lib = load_library()
+    st = lib.tddft_gemm_f64_emulated(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                     C.data_ptr(), C.stride(0), slices, _current_stream())
+    if st != OK:
+        raise TddftError(st, "emulated float64 GEMM failed")
+    return C
 
 
 def _current_stream():

@@ -95,6 +95,20 @@ def test_validation_rejects_bad_input_before_device_work(lib):
     assert _bad(lambda s: None, prec=9)[0] == tddft.ERR_UNSUPPORTED
     assert _bad(lambda s: None, prec=2, inner_tol=0.0)[0] == tddft.ERR_INVALID_ARG
     assert _bad(lambda s: None, prec=2, inner_tol=1.5)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, prec=3, inner_tol=0.0)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, prec=-1)[0] == tddft.ERR_UNSUPPORTED
+
+
+def test_emulated_gemm_rejects_bad_arguments_on_the_host(lib):
+    f = lib.tddft_gemm_f64_emulated
+    buf = ctypes.c_void_p(16)   # never dereferenced: every call fails validation
+    assert f(4, 4, 4, None, 4, buf, 4, buf, 4, 6, None) == tddft.ERR_INVALID_ARG
+    assert f(0, 4, 4, buf, 4, buf, 4, buf, 4, 6, None) == tddft.ERR_INVALID_ARG
+    assert f(4, 4, 4, buf, 4, buf, 4, buf, 4, 2, None) == tddft.ERR_INVALID_ARG
+    assert f(4, 4, 4, buf, 4, buf, 4, buf, 4, 9, None) == tddft.ERR_INVALID_ARG
+    assert f(4, 4, 8, buf, 4, buf, 4, buf, 4, 6, None) == tddft.ERR_SHAPE
+    assert f(4, 8, 4, buf, 4, buf, 4, buf, 8, 6, None) == tddft.ERR_SHAPE
+    assert f(4, 8, 4, buf, 4, buf, 8, buf, 4, 6, None) == tddft.ERR_SHAPE
 
 
 def test_more_than_16_orbitals_per_atom_is_unsupported(lib):

@@ -18,7 +18,7 @@ def _gpu():
     ensure_library()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "bf16x3emu"])
 @pytest.mark.parametrize("batch", [192, 50])
 def test_graph_replays_match_host_driven_iterations(prec, batch):
     from paper_1005_5340_gb300 import tddft
