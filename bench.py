@@ -37,7 +37,10 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (DFMA) nominal rate; no tensor path fo
 # FP32 CUDA-core peak from unit counts: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
 FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # kernel launches behind one timed scope (the others launch one kernel each)
-KERNELS_PER_SCOPE = {"rhs_formation": 7}
+KERNELS_PER_SCOPE = {"rhs_formation": 7, "emu_gemm_K": 2, "emu_gemm_T1": 2, "emu_gemm_T2": 2}
+KERNELS_PER_SCOPE_EMU = dict(KERNELS_PER_SCOPE, rhs_formation=9)
+# slice pairs of one emulated float64 product (6 slices: pairs with i + j <= 7)
+EMU_PAIRS = 21
 
 
 def measured_peaks():
@@ -62,7 +65,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=0,
                    help="omega-points in the CPU-oracle sample (0: one per 3 host cores)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--prec", choices=["fp64", "bf16x3"], default="bf16x3")
+    p.add_argument("--prec", choices=["fp64", "fp64emu", "bf16x3", "bf16x3emu"],
+                   default="bf16x3emu")
     p.add_argument("--no-fp64-compare", action="store_true",
                    help="skip timing the plain float64 form on one step for the speedup")
     p.add_argument("--inner-tol", type=float, default=1e-4)
@@ -207,10 +211,18 @@ def run_reference(args):
 
 FORM_NOTE = {
     "fp64": "plain float64 GMRES, device resident",
+    "fp64emu": "float64 GMRES whose dense products are float64 emulated on the bf16 tensor "
+               "cores (6 integer slices per operand, exact sums)",
     "bf16x3": "GMRES cycles with split-bf16 tensor-core products and float32 sparse kernels, "
               "each cycle closed by a float64 residual (iterative refinement); RHS, basis, "
               "Givens in float64",
+    "bf16x3emu": "GMRES cycles with split-bf16 tensor-core products and float32 sparse "
+                 "kernels, each cycle closed by a float64 residual whose dense products are "
+                 "float64 emulated on the tensor cores (6 integer slices, exact sums); RHS "
+                 "formation likewise; basis and Givens in float64",
 }
+DTYPE = {"fp64": "f64", "fp64emu": "f64 (emulated on bf16 tensor cores)",
+         "bf16x3": "bf16x3+f64", "bf16x3emu": "bf16x3+f64 (emulated on bf16 tensor cores)"}
 
 
 def roofline_of(timing: dict, step_ms: float) -> dict:
@@ -224,6 +236,11 @@ def roofline_of(timing: dict, step_ms: float) -> dict:
         peak = peaks["bf16_tflops_sustained"] / 3.0
         bound, note = "tensor", (f"split bf16: 3 bf16 products per algorithmic product; peak = "
                                  f"{src} sustained bf16 {peaks['bf16_tflops_sustained']} / 3")
+    elif name.startswith("emu_gemm"):
+        peak = peaks["bf16_tflops_sustained"] / EMU_PAIRS
+        bound, note = "tensor", (f"float64 emulated with {EMU_PAIRS} bf16 slice products per "
+                                 f"algorithmic product; peak = {src} sustained bf16 "
+                                 f"{peaks['bf16_tflops_sustained']} / {EMU_PAIRS}")
     elif name.startswith("f64_"):
         peak, bound = FP64_NOMINAL_TFLOPS, "alu"
         note = "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry among the measured peaks)"
@@ -360,15 +377,17 @@ def run_ours(args):
     roofline = roofline_of(timing, timing_ms)
     if args.graph:
         roofline["timing"] = "kernel split from one instrumented (non-graph) step after the timed region"
-    gpu_launches = int(sum(v["launches"] * KERNELS_PER_SCOPE.get(k, 1) for k, v in timing.items()))
+    per_scope = KERNELS_PER_SCOPE_EMU if args.prec.endswith("emu") else KERNELS_PER_SCOPE
+    gpu_launches = int(sum(v["launches"] * per_scope.get(k, 1) for k, v in timing.items()))
     if args.graph:
         gpu_launches = int(round(gpu_launches * args.steps))
     chi_cls = ["f64_vertex", "f64_beta", "f64_gemm_T1", "f64_dscale", "f64_gemm_T2",
                "f64_block_dot", "lp_vertex", "lp_beta", "tc_gemm_T1_dscale", "tc_gemm_T2",
-               "lp_block_dot"]
+               "lp_block_dot", "emu_gemm_T1", "emu_gemm_T2"]
     chi_ms = sum(timing[c]["ms"] for c in chi_cls)
     n_virt = s.n_orb - s.n_occ
-    t1_flops = timing["f64_gemm_T1"]["flops"] + timing["tc_gemm_T1_dscale"]["flops"]
+    t1_flops = (timing["f64_gemm_T1"]["flops"] + timing["tc_gemm_T1_dscale"]["flops"]
+                + timing["emu_gemm_T1"]["flops"])
     chi_applies = t1_flops / (4.0 * n_virt * s.n_orb * s.n_occ)
     chi0_tflops = chi_applies * chi0_flops_per_rhs(s) / (chi_ms / 1e3) / 1e12 if chi_ms else None
 
@@ -406,7 +425,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "omega-points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x3+f64" if args.prec == "bf16x3" else "f64",
+        "dtype": DTYPE[args.prec],
         "data": "synthetic",
         "config": dict(config_of(args.workload, FORM_NOTE[args.prec]),
                        precision=args.prec, inner_tol=args.inner_tol,
@@ -469,7 +488,7 @@ def run_batch(args):
         "metric": METRIC, "value": points / dt, "unit": "omega-points/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x3+f64" if args.prec == "bf16x3" else "f64", "data": "synthetic",
+        "dtype": DTYPE[args.prec], "data": "synthetic",
         "config": {"workload": f"batch32: 32 molecules of {min(x.n_atoms for x in mols)}-"
                                f"{max(x.n_atoms for x in mols)} atoms (sizes log-uniform 8-128), "
                                f"{per} omega x 3 directions each per step, eps {eps}, "
