@@ -45,14 +45,37 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+__device__ __forceinline__ void store_split(__nv_bfloat16 *p, int64_t lo_off, float x) {
+  __nv_bfloat16 h, l;
+  split_bf16(x, h, l);
+  p[0] = h;
+  p[lo_off] = l;
+}
+
 template <int EPI, int TC_BN>
 __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   int M, int N, int Kp, int nseg, int4 segs, TcEpilogue ep, int *err,
-                   const int *dcnt, int mul_n) {
+                   int M, int N, int KpA, int KpB, int nseg, int4 segs, TcEpilogue ep, int *err,
+                   const int *dcnt, int mul_n, const GTile *tiles) {
   // graph replays: columns beyond the live count are skipped (whole CTAs)
   if (dcnt) N = (int)min((int64_t)N, (int64_t)mul_n * (*dcnt));
   if ((int)blockIdx.y * TC_BN >= N) return;
+  // this CTA's rows of A and K range of B (grouped products: from the tile table)
+  int m0, xoff, nkb, rows_valid, atom;
+  if (tiles) {
+    const GTile t = tiles[blockIdx.x];
+    m0 = t.row0;
+    xoff = t.xoff;
+    nkb = t.nkb;
+    rows_valid = t.rows;
+    atom = t.atom;
+  } else {
+    m0 = blockIdx.x * TC_BM;
+    xoff = 0;
+    nkb = KpA / TC_BK;
+    rows_valid = min(TC_BM, M - m0);
+    atom = -1;
+  }
   constexpr uint32_t TC_STAGE_BYTES = TcShape<TC_BN>::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
@@ -64,8 +87,7 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
-  const int nkb = Kp / TC_BK;
+  const int n0 = blockIdx.y * TC_BN;
   const int total = nseg * nkb;
 
   if (threadIdx.x == 0) {
@@ -105,8 +127,8 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
       uint8_t *sa = smem + s * TC_STAGE_BYTES;
       uint8_t *sb = sa + TC_A_BYTES;
       mbar_expect_tx(&full[s], TC_STAGE_BYTES);
-      tma_load_2d(sa, &mapA, &full[s], ka * Kp + kb * TC_BK, m0);
-      tma_load_2d(sb, &mapB, &full[s], kbp * Kp + kb * TC_BK, n0);
+      tma_load_2d(sa, &mapA, &full[s], ka * KpA + kb * TC_BK, m0);
+      tma_load_2d(sb, &mapB, &full[s], kbp * KpB + xoff + kb * TC_BK, n0);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -140,7 +162,8 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
   fence_after();
   // tcgen05.ld is warp-collective: take the decision once per warp
   have = __all_sync(0xffffffffu, have && !*(volatile int *)&abort_flag);
-  const int m = m0 + warp * 32 + lane;
+  const int lr = warp * 32 + lane;
+  const int m = m0 + lr;
   if (have) {
     for (int j0 = 0; j0 < TC_BN; j0 += 16) {
       float v[16];
@@ -151,6 +174,46 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + j0 + j;
             if (n < N) ep.outF[(int64_t)n * ep.ldo + m] = v[j];
+          }
+        }
+      } else if (EPI == kPartialF32) {
+        // C layout, rows of the grouped operand
+        if (lr < rows_valid) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + j0 + j;
+            if (n < N) ep.outF[(int64_t)m * ep.ldo + n] = v[j];
+          }
+        }
+      } else if (EPI == kBetaTSplit) {
+        // row m = (atom A, E, c) of the step-2 operand; column n = 2 s + p:
+        // beta^T row (s n_occ + E) 2 + p, column ao_A + c
+        if (lr < rows_valid) {
+          const int aoA = ep.aoff[atom], nA = ep.aoff[atom + 1] - aoA;
+          const int r = m - aoA * ep.n_occ, E = r / nA, c = r - E * nA;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + j0 + j;
+            if (n < N) {
+              const int64_t row = ((int64_t)(n >> 1) * ep.n_occ + E) * 2 + (n & 1);
+              store_split(ep.outB + row * ep.ldo + aoA + c, ep.lo_off, v[j]);
+            }
+          }
+        }
+      } else if (EPI == kGammaCatSplit) {
+        // row m = orbital (atom B, b); column n = (s n_occ + E) 2 + p, j = 2 s + p:
+        // Gcat[j][xoff5_B + b n_occ + E]
+        if (m < M) {
+          const int B = ep.orb_atom[m], b = m - ep.aoff[B];
+          const int64_t xo = ep.xoff5[B] + (int64_t)b * ep.n_occ;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + j0 + j;
+            if (n < N) {
+              const int pair = n >> 1, p = n & 1;
+              const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
+              store_split(ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E, ep.lo_off, v[j]);
+            }
           }
         }
       } else {
@@ -247,33 +310,68 @@ cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int 
   return cudaSuccess;
 }
 
+namespace {
 template <int EPI, int BN>
 void set_attr() {
   cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)TcShape<BN>::SMEM);
 }
 
+template <int BN>
+void set_attr_all() {
+  set_attr<kStoreF32, BN>();
+  set_attr<kDscaleSplit, BN>();
+  set_attr<kBetaTSplit, BN>();
+  set_attr<kGammaCatSplit, BN>();
+  set_attr<kPartialF32, BN>();
+}
+}  // namespace
+
 void tc_init_attributes() {
   static bool done = false;
   if (done) return;
-  set_attr<kStoreF32, 128>();
-  set_attr<kDscaleSplit, 128>();
-  set_attr<kStoreF32, 64>();
-  set_attr<kDscaleSplit, 64>();
+  set_attr_all<128>();
+  set_attr_all<64>();
   done = true;
 }
 
+namespace {
 template <int EPI, int BN>
-cudaError_t launch_tc(cudaStream_t st, const CUtensorMap &mA, const CUtensorMap &mB, int M, int N,
-                      int Kp, const TcEpilogue &ep, int *err, const int *dcnt, int mul_n) {
-  dim3 grid((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN);
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+cudaError_t launch_tc(cudaStream_t st, dim3 grid, const CUtensorMap &mA, const CUtensorMap &mB,
+                      int M, int N, int KpA, int KpB, const TcEpilogue &ep, int *err,
+                      const int *dcnt, int mul_n, const GTile *tiles) {
   // segments: A_hi B_hi, A_hi B_lo, A_lo B_hi  (low byte: A plane, next byte: B plane)
   const int4 segs = make_int4(0 | (0 << 8), 0 | (1 << 8), 1 | (0 << 8), 0);
-  gemm_tc_kernel<EPI, BN><<<grid, TC_THREADS, TcShape<BN>::SMEM, st>>>(mA, mB, M, N, Kp, 3, segs,
-                                                                         ep, err, dcnt, mul_n);
+  gemm_tc_kernel<EPI, BN><<<grid, TC_THREADS, TcShape<BN>::SMEM, st>>>(
+      mA, mB, M, N, KpA, KpB, 3, segs, ep, err, dcnt, mul_n, tiles);
   return cudaGetLastError();
 }
+
+template <int BN>
+cudaError_t launch_tc_epi(cudaStream_t st, int epi, dim3 grid, const CUtensorMap &mA,
+                          const CUtensorMap &mB, int M, int N, int KpA, int KpB,
+                          const TcEpilogue &ep, int *err, const int *dcnt, int mul_n,
+                          const GTile *tiles) {
+  switch (epi) {
+    case kStoreF32:
+      return launch_tc<kStoreF32, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n, tiles);
+    case kDscaleSplit:
+      return launch_tc<kDscaleSplit, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+                                         tiles);
+    case kBetaTSplit:
+      return launch_tc<kBetaTSplit, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+                                        tiles);
+    case kGammaCatSplit:
+      return launch_tc<kGammaCatSplit, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+                                           tiles);
+    case kPartialF32:
+      return launch_tc<kPartialF32, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+                                        tiles);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
 
 cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
                            int epi, const TcEpilogue &ep, int *err, const int *dcnt, int mul_n,
@@ -281,15 +379,30 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (A.Kp != B.Kp) return cudaErrorInvalidValue;
   tc_init_attributes();
-  if (bn == 64) {
-    if (!B.has64) return cudaErrorInvalidValue;
-    return epi == kStoreF32
-               ? launch_tc<kStoreF32, 64>(st, A.map, B.map64, M, N, A.Kp, ep, err, dcnt, mul_n)
-               : launch_tc<kDscaleSplit, 64>(st, A.map, B.map64, M, N, A.Kp, ep, err, dcnt, mul_n);
-  }
-  return epi == kStoreF32
-             ? launch_tc<kStoreF32, 128>(st, A.map, B.map, M, N, A.Kp, ep, err, dcnt, mul_n)
-             : launch_tc<kDscaleSplit, 128>(st, A.map, B.map, M, N, A.Kp, ep, err, dcnt, mul_n);
+  if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
+  dim3 grid((M + TC_BM - 1) / TC_BM, (N + bn - 1) / bn);
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  if (bn == 64)
+    return launch_tc_epi<64>(st, epi, grid, A.map, B.map64, M, N, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+                             nullptr);
+  return launch_tc_epi<128>(st, epi, grid, A.map, B.map, M, N, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+                            nullptr);
+}
+
+cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const TcOperand &B,
+                                   const GTile *tiles, int n_tiles, int N, int epi,
+                                   const TcEpilogue &ep, int *err, const int *dcnt, int mul_n,
+                                   int bn) {
+  if (n_tiles <= 0 || N <= 0) return cudaSuccess;
+  tc_init_attributes();
+  if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
+  dim3 grid(n_tiles, (N + bn - 1) / bn);
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  if (bn == 64)
+    return launch_tc_epi<64>(st, epi, grid, A.map, B.map64, 0, N, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+                             tiles);
+  return launch_tc_epi<128>(st, epi, grid, A.map, B.map, 0, N, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+                            tiles);
 }
 
 }  // namespace tddft

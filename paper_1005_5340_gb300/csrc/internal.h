@@ -57,7 +57,9 @@ enum KernelClass {
   // solver
   kcGmresStep, kcGmresGather, kcGmresSelect, kcRhs, kcMisc,
   // float64 products emulated on the tensor cores (integer slices)
-  kcOzSlice, kcOzK, kcOzT1, kcOzT2, kcCount
+  kcOzSlice, kcOzK, kcOzT1, kcOzT2,
+  // steps 2 and 5 on the stored transition vertex
+  kcAlphaGather, kcTcStep2, kcTcStep5, kcOzStep2, kcOzStep5, kcCount
 };
 const char *kernel_class_name(int k);
 
@@ -78,6 +80,7 @@ struct Timer {
 };
 
 struct OzWork;
+struct AlphaRoute;
 
 // Workspace of the chi0 / A operator for up to `slots` right-hand sides.
 // Real columns: c = 2*s + p, p = 0 real plane, 1 imaginary plane.
@@ -94,6 +97,7 @@ struct OpWork {
   double *splitws = nullptr;  // split-K slices of the K product
   int64_t splitws_elems = 0;
   OzWork *oz = nullptr;       // non-NULL: the three GEMMs are emulated float64 products
+  AlphaRoute *ar = nullptr;   // with oz: steps 2 and 5 on the stored transition vertex
 };
 
 enum OpMode { kChi0 = 0, kKernel = 1, kA = 2 };
@@ -130,7 +134,14 @@ cudaError_t launch_planar_to_interleaved(cudaStream_t st, int n_rhs, int n, cons
 // ---------------------------------------------------------------------------
 // Reduced-precision operator (split bf16 on tcgen05, float32 elsewhere)
 // ---------------------------------------------------------------------------
-enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1 };
+// One M tile of a grouped product (per-atom operands of steps 2 and 5 of
+// Table t:flops): A rows row0 .. row0 + rows - 1 (rows <= 128), B columns
+// from xoff (within each slice / split plane) over nkb 64-deep K blocks.
+struct GTile {
+  int row0, xoff, nkb, rows, atom, pad0, pad1, pad2;
+};
+
+enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1, kBetaTSplit = 2, kGammaCatSplit = 3, kPartialF32 = 4 };
 
 // A bf16 operand [rows][2*Kp] ([hi | lo] planes) with its TMA descriptor.
 struct TcOperand {
@@ -152,6 +163,9 @@ struct TcEpilogue {
   double eps = 0.0;
   double occ_value = 0.0;
   int n_occ = 0;
+  const int *aoff = nullptr;       // kBetaTSplit, kGammaCatSplit
+  const int *orb_atom = nullptr;   // kGammaCatSplit
+  const int *xoff5 = nullptr;      // kGammaCatSplit
 };
 
 cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows);
@@ -164,6 +178,18 @@ cudaError_t encode_bf16_map(CUtensorMap *map, const void *base, int64_t rows, in
 cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
                            int epi, const TcEpilogue &ep, int *err, const int *dcnt = nullptr,
                            int mul_n = 0, int bn = 128);
+// Grouped product over a tile table (one CTA row per tile, see GTile):
+//   kBetaTSplit     A row m = (atom A, E, c) of the step-2 operand, column n =
+//                   2 s + p: beta^T split at row (s n_occ + E) 2 + p, column
+//                   ao_A + c (hi at outB[row*ldo + col], lo at + lo_off)
+//   kPartialF32     outF[m*ldo + n] for the valid rows of each tile
+// (the plain launch_gemm_tc also takes kGammaCatSplit: row m = orbital (B, b),
+// column n = (s n_occ + E) 2 + p -> Gcat split at row 2 s + p, column
+// xoff5_B + b n_occ + E.)
+cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const TcOperand &B,
+                                   const GTile *tiles, int n_tiles, int N, int epi,
+                                   const TcEpilogue &ep, int *err, const int *dcnt = nullptr,
+                                   int mul_n = 0, int bn = 128);
 void tc_init_attributes();
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -185,6 +211,7 @@ struct LpWork {
   double *omega = nullptr;         // [S]
   int *err = nullptr;              // [1] device-side error code of the GEMM waits
   TcOperand opK, opXvT, opXv, opZ, opBeta, opA;
+  AlphaRoute *ar = nullptr;        // steps 2 and 5 on the stored transition vertex
   int bnK = 128, bn1 = 128, bn2 = 128;   // N tiles chosen by the autotuner
   Timer *timer = nullptr;
   const int *dcnt = nullptr;  // graph replays: device count of live slots (NULL: all S)
@@ -219,13 +246,36 @@ constexpr int kOzDefaultSlices = 6;
 // the A role, 64 for the B role.
 cudaError_t oz_operand(OzOperand &op, __nv_bfloat16 *q, int *e, int64_t rows, int Kdim, int s,
                        int box_rows);
-// Slices of rows r < rows (live rows mul*dcnt) of X [rows][ldx] (first Kdim entries).
+// Slices of rows r < rows (live rows mul*dcnt) of X [rows][ldx] (first Kdim
+// entries; with cols, entry k of row r is X[r][cols[k]], zero where cols[k] < 0).
 cudaError_t launch_oz_slice_rows(cudaStream_t st, const double *X, int64_t ldx, int rows, int Kdim,
-                                 OzOperand &op, const int *dcnt = nullptr, int mul = 0);
+                                 OzOperand &op, const int *dcnt = nullptr, int mul = 0,
+                                 const int *cols = nullptr);
 // Slices of the columns n < N (live mul*dcnt) of X [Kdim][ldx]: operand row n
 // holds column n of X.
 cudaError_t launch_oz_slice_cols(cudaStream_t st, const double *X, int64_t ldx, int Kdim, int N,
                                  OzOperand &op, const int *dcnt = nullptr, int mul = 0);
+enum OzEpiMode { kOzC = 0, kOzCT = 1, kOzBetaT = 2, kOzGammaCat = 3 };
+struct OzEpilogue {
+  int mode = kOzC;
+  double *C = nullptr;
+  int64_t ldc = 0;
+  const int *aoff = nullptr;      // kOzBetaT, kOzGammaCat: atom orbital offsets
+  const int *orb_atom = nullptr;  // kOzGammaCat: atom of each orbital
+  const int *xoff5 = nullptr;     // kOzGammaCat: Gcat segment of each atom
+  int n_occ = 0;
+};
+// Grouped or plain product with a chosen epilogue:
+//   kOzC      C[m*ldc + n]                 kOzCT  C[n*ldc + m]
+//   kOzBetaT  A row m = (atom A, E, c) of the step-2 operand:
+//             beta^T[(n n_occ + E) ldc + ao_A + c]
+//   kOzGammaCat  A row m = orbital (B, b), column n = j n_occ + E:
+//             Gcat[j ldc + xoff5_B + b n_occ + E]
+// tiles (device, n_tiles entries; max_nkb = largest nkb) or NULL for plain
+// 128-row tiles of M rows.
+cudaError_t launch_gemm_oz_ex(cudaStream_t st, const OzOperand &A, const OzOperand &B, int M,
+                              int N, const OzEpilogue &ep, const GTile *tiles, int n_tiles,
+                              int max_nkb, int *err, const int *dcnt = nullptr, int mul_n = 0);
 // C = A B^T over the sliced operands (A rows m < M, B rows n < N, shared K):
 // C[m*ldc + n] (trans = 0) or C[n*ldc + m] (trans = 1), float64.
 cudaError_t launch_gemm_oz(cudaStream_t st, const OzOperand &A, const OzOperand &B, int M, int N,
@@ -241,6 +291,59 @@ struct OzWork {
 };
 cudaError_t oz_setup(cudaStream_t st, const DevSystem &sys, OzWork &oz, int slots,
                      std::vector<void *> &allocs);
+
+// ---------------------------------------------------------------------------
+// The stored transition vertex (alpha.cu): step 1 of Table t:flops,
+//   alpha_nu^{cE} = sum_d V_nu^{cd} X_d^E ,
+// kept for steps 2 (beta^{cE} = sum_nu alpha_nu^{cE} v^nu) and 5
+// (n_mu = sum_{bE} alpha_mu^{bE} gamma_b^E) as per-atom dense operands:
+//   step 2, atom A: rows (E, c) (c in A, row ao_A n_occ + E n_A + c), one
+//           column per product of L_A (the products whose block holds A, in
+//           increasing order), row length K2max; the right-hand side rows are
+//           gathered into Ycat = [v^nu, nu in L_A] per atom (segments of
+//           round_up(|L_A|, 64))
+//   step 5, atom B: one row per product of L_B (rows rowoff5_B + index),
+//           columns b n_occ + E (b in B), row length K5max; gamma is written
+//           by the second transform into Gcat = [gamma_b^E] per atom (segments
+//           of round_up(n_B n_occ, 64)); the per-atom partial sums of n_mu
+//           (P2, one row per (atom, product)) are added per product.
+// ---------------------------------------------------------------------------
+struct AlphaRoute {
+  int K2max = 0, K5max = 0;
+  int64_t rows2 = 0;          // n_orb n_occ
+  int rows5 = 0;              // sum_B |L_B|
+  int kcat2 = 0, kcat5 = 0;   // Ycat, Gcat row lengths
+  int n_tiles2 = 0, n_tiles5 = 0, max_nkb2 = 0, max_nkb5 = 0;
+  double flops2 = 0.0, flops5 = 0.0;   // per real column
+  GTile *tiles2 = nullptr, *tiles5 = nullptr;
+  int *lcat = nullptr;        // [kcat2] product at each Ycat position (-1: padding)
+  int2 *pos5 = nullptr;       // [n_prod] P2 rows of each product (y = -1: local product)
+  int *xoff5 = nullptr;       // [n_atoms] Gcat segment of each atom
+  int *orb_atom = nullptr;    // [n_orb]
+  int ldp = 0;                // P2 row stride (2 S)
+  // split bf16 (reduced-precision operator)
+  bool lp = false;
+  TcOperand a2, a5, ycat, gcat;
+  __nv_bfloat16 *ycat_q = nullptr, *gcat_q = nullptr;   // [2S][2 kcat2], [2S][2 kcat5]
+  float *P2f = nullptr;
+  // emulated float64
+  bool emu = false;
+  OzOperand oa2, oa5, oycat, ogcat;
+  double *gcat64 = nullptr;   // [2S][kcat5]
+  double *P2d = nullptr;      // [rows5][2S]
+};
+// Lists, tiles and both operand forms (lp: split bf16; emu: s slices);
+// device buffers recorded in allocs.
+cudaError_t alpha_setup(cudaStream_t st, const tddft_system *host, const DevSystem &sys,
+                        AlphaRoute &ar, int slots, bool lp, bool emu, int slices,
+                        std::vector<void *> &allocs);
+// Ycat split bf16 from rows of Y (float32 or float64, row stride ld)
+cudaError_t launch_alpha_gather_lp(cudaStream_t st, const AlphaRoute &ar, int ncols, const void *Y,
+                                   bool y_f64, int64_t ld, const int *dcnt);
+// Out[c][mu] = Zin - n (subtract) or n, n_mu summed from the per-atom partials
+cudaError_t launch_alpha_combine(cudaStream_t st, const AlphaRoute &ar, int ncols, int n_prod,
+                                 bool p_f64, const double *Zin, int subtract, double *Out,
+                                 const int *dcnt);
 
 // GMRES state of a group of right-hand sides (one per (omega, direction)).
 struct GmresState {

@@ -419,6 +419,97 @@ struct Scope {
 };
 }  // namespace
 
+namespace {
+// Step 2 on the stored transition vertex, emulated float64: rows of Ysrc
+// (n_rows columns y, row stride n_prod) gathered per atom and sliced, then
+// beta^T[(c n_occ + E)][a] (into wk.beta) per atom on the tensor cores.
+cudaError_t alpha_beta_emulated(cudaStream_t st, const DevSystem &sys, OpWork &wk, int n_rows,
+                                const double *Ysrc, const int *dcnt) {
+  AlphaRoute &ar = *wk.ar;
+  Scope sc(wk.timer, st, kcOzStep2, n_rows * ar.flops2);
+  cudaError_t err = launch_oz_slice_rows(st, Ysrc, sys.n_prod, n_rows, ar.kcat2, ar.oycat, dcnt, 2,
+                                         ar.lcat);
+  if (err != cudaSuccess) return err;
+  OzEpilogue eb;
+  eb.mode = kOzBetaT;
+  eb.C = wk.beta;
+  eb.ldc = sys.n_orb;
+  eb.aoff = sys.aoff;
+  eb.n_occ = sys.n_occ;
+  return launch_gemm_oz_ex(st, ar.oa2, ar.oycat, 0, n_rows, eb, ar.tiles2, ar.n_tiles2,
+                           ar.max_nkb2, wk.oz->err, dcnt, 2);
+}
+
+// Transform 2 (X_virt a, a = wk.abuf [n_virt][ncols n_occ]) written per atom
+// into Gcat, step 5 per atom, and Out = Zin - n (subtract) or n.
+cudaError_t alpha_dot_emulated(cudaStream_t st, const DevSystem &sys, OpWork &wk, int ncols,
+                               const double *Zin, int subtract, double *Out, const int *dcnt,
+                               int timer_class) {
+  AlphaRoute &ar = *wk.ar;
+  OzWork &oz = *wk.oz;
+  const int64_t ncolE = (int64_t)ncols * sys.n_occ;
+  cudaError_t err;
+  {
+    Scope sc(wk.timer, st, timer_class,
+             timer_class == kcOzT2 ? 2.0 * sys.n_virt * (double)sys.n_orb * ncolE : 0.0);
+    err = launch_oz_slice_cols(st, wk.abuf, ncolE, sys.n_virt, (int)ncolE, oz.Bt2, dcnt,
+                               2 * sys.n_occ);
+    OzEpilogue eg;
+    eg.mode = kOzGammaCat;
+    eg.C = ar.gcat64;
+    eg.ldc = ar.kcat5;
+    eg.aoff = sys.aoff;
+    eg.orb_atom = ar.orb_atom;
+    eg.xoff5 = ar.xoff5;
+    eg.n_occ = sys.n_occ;
+    if (err == cudaSuccess)
+      err = launch_gemm_oz_ex(st, oz.Xv, oz.Bt2, sys.n_orb, (int)ncolE, eg, nullptr, 0, 0, oz.err,
+                              dcnt, 2 * sys.n_occ);
+    if (err != cudaSuccess) return err;
+  }
+  Scope sc(wk.timer, st, kcOzStep5, ncols * ar.flops5);
+  err = launch_oz_slice_rows(st, ar.gcat64, ar.kcat5, ncols, ar.kcat5, ar.ogcat, dcnt, 2);
+  OzEpilogue ep;
+  ep.mode = kOzC;
+  ep.C = ar.P2d;
+  ep.ldc = ar.ldp;
+  if (err == cudaSuccess)
+    err = launch_gemm_oz_ex(st, ar.oa5, ar.ogcat, 0, ncols, ep, ar.tiles5, ar.n_tiles5,
+                            ar.max_nkb5, oz.err, dcnt, 2);
+  if (err == cudaSuccess)
+    err = launch_alpha_combine(st, ar, ncols, sys.n_prod, true, Zin, subtract, Out, dcnt);
+  return err;
+}
+
+// chi0 (or A) with every dense product emulated in float64 and steps 2 and
+// 5 on the stored transition vertex; Y = K z (kA) or z (kChi0).
+cudaError_t apply_alpha_emulated(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S,
+                                 OpMode mode, double eps, const double *Y, const double *Zin,
+                                 double *Out) {
+  const int ncols = 2 * S;
+  const int64_t ncolE = (int64_t)ncols * sys.n_occ;
+  OzWork &oz = *wk.oz;
+  cudaError_t err = alpha_beta_emulated(st, sys, wk, ncols, Y, wk.dcnt);
+  if (err != cudaSuccess) return err;
+  {
+    Scope sc(wk.timer, st, kcOzT1, 2.0 * sys.n_virt * (double)sys.n_orb * ncolE);
+    err = launch_oz_slice_rows(st, wk.beta, sys.n_orb, (int)ncolE, sys.n_orb, oz.Bt1, wk.dcnt,
+                               2 * sys.n_occ);
+    if (err == cudaSuccess)
+      err = launch_gemm_oz(st, oz.XvT, oz.Bt1, sys.n_virt, (int)ncolE, wk.abuf, ncolE, 0, oz.err,
+                           wk.dcnt, 2 * sys.n_occ);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(wk.timer, st, kcDscale, 0.0);
+    dscale_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
+        sys.n_virt, S, sys.n_occ, sys.occ_value, sys.energy, wk.omega, eps, wk.abuf, wk.dcnt);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return alpha_dot_emulated(st, sys, wk, ncols, Zin, mode == kA ? 1 : 0, Out, wk.dcnt, kcOzT2);
+}
+}  // namespace
+
 cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S, int g0,
                                  const double *omega_all, double eps, double *Z3, double *a3,
                                  double *Out) {
@@ -428,6 +519,27 @@ cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &
   cudaError_t err;
   Scope sc(wk.timer, st, kcRhs, 0.0);
   dipole_rows_kernel<<<grid_for(3 * (int64_t)np, 256), 256, 0, st>>>(np, sys.dip, Z3);
+  if (wk.oz && wk.ar) {
+    // emulated float64 on the stored transition vertex: beta(d_k) and
+    // X_virt^T beta once, then per right-hand side D(omega), X_virt a, step 5
+    Timer *saved = wk.timer;
+    wk.timer = nullptr;
+    const int n6 = 6 * sys.n_occ;
+    err = alpha_beta_emulated(st, sys, wk, 6, Z3, nullptr);
+    if (err == cudaSuccess)
+      err = launch_oz_slice_rows(st, wk.beta, sys.n_orb, n6, sys.n_orb, wk.oz->Bt1);
+    if (err == cudaSuccess)
+      err = launch_gemm_oz(st, wk.oz->XvT, wk.oz->Bt1, sys.n_virt, n6, a3, n6, 0, wk.oz->err);
+    if (err == cudaSuccess) {
+      rhs_expand_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
+          sys.n_virt, S, sys.n_occ, g0, sys.occ_value, sys.energy, omega_all, eps, a3, wk.abuf);
+      err = cudaGetLastError();
+    }
+    if (err == cudaSuccess)
+      err = alpha_dot_emulated(st, sys, wk, 2 * S, nullptr, 0, Out, nullptr, kcRhs);
+    wk.timer = saved;
+    return err;
+  }
   // omega-independent part for the three directions (6 real columns)
   {
     dim3 grid(sys.n_blocks, 1);
@@ -493,6 +605,7 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
     if (err != cudaSuccess || mode == kKernel) return err;
     Y = wk.Y;
   }
+  if (wk.oz && wk.ar) return apply_alpha_emulated(st, sys, wk, S, mode, eps, Y, Zin, Out);
   {
     Scope sc(wk.timer, st, kcVertex, 2.0 * ncols * (double)kBlk * np);
     dim3 grid(sys.n_blocks, (ncols + VW_COLS - 1) / VW_COLS);

@@ -284,23 +284,47 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
       if (err != cudaSuccess) return err;
     }
   }
-  {
-    Scope sc(lp.timer, st, kcLpVertex, 2.0 * ncols * (double)kBlk * np);
-    dim3 grid(sys.n_blocks, (ncols + 7) / 8);
-    if (mode == kA)
-      lp_vertex<float><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
-                                             lp.Vpad32, lp.Yt, lp.W, lp.dcnt);
-    else
-      lp_vertex<double><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
-                                              lp.Vpad32, Zin, lp.W, lp.dcnt);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  }
-  {
-    Scope sc(lp.timer, st, kcLpBeta, ncols * sys.sf.beta);
-    dim3 grid(sys.n_atoms, (ncols + 3) / 4);
-    lp_beta<<<grid, 128, 0, st>>>(ncols, sys.n_blocks, sys.n_occ, lp.Kp1, sys.aoff, sys.adj_ptr,
-                                  sys.adj, lp.W, lp.Xo32, lp.betaT, lp.dcnt);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (lp.ar) {
+    // steps 1-2 on the stored transition vertex: gather v^nu per atom, then
+    // beta^T = (alpha_A Ycat_A)^T per atom on the tensor cores
+    const AlphaRoute &ar = *lp.ar;
+    {
+      Scope sc(lp.timer, st, kcAlphaGather, 0.0);
+      err = launch_alpha_gather_lp(st, ar, ncols, mode == kA ? (const void *)lp.Yt : Zin,
+                                   mode != kA, np, lp.dcnt);
+      if (err != cudaSuccess) return err;
+    }
+    {
+      Scope sc(lp.timer, st, kcTcStep2, ncols * ar.flops2);
+      TcEpilogue eb;
+      eb.outB = lp.betaT;
+      eb.ldo = 2 * (int64_t)lp.Kp1;
+      eb.lo_off = lp.Kp1;
+      eb.n_occ = sys.n_occ;
+      eb.aoff = sys.aoff;
+      err = launch_gemm_tc_grouped(st, ar.a2, ar.ycat, ar.tiles2, ar.n_tiles2, ncols, kBetaTSplit,
+                                   eb, lp.err, lp.dcnt, 2);
+      if (err != cudaSuccess) return err;
+    }
+  } else {
+    {
+      Scope sc(lp.timer, st, kcLpVertex, 2.0 * ncols * (double)kBlk * np);
+      dim3 grid(sys.n_blocks, (ncols + 7) / 8);
+      if (mode == kA)
+        lp_vertex<float><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
+                                               lp.Vpad32, lp.Yt, lp.W, lp.dcnt);
+      else
+        lp_vertex<double><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
+                                                lp.Vpad32, Zin, lp.W, lp.dcnt);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    {
+      Scope sc(lp.timer, st, kcLpBeta, ncols * sys.sf.beta);
+      dim3 grid(sys.n_atoms, (ncols + 3) / 4);
+      lp_beta<<<grid, 128, 0, st>>>(ncols, sys.n_blocks, sys.n_occ, lp.Kp1, sys.aoff, sys.adj_ptr,
+                                    sys.adj, lp.W, lp.Xo32, lp.betaT, lp.dcnt);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
   }
   const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)N1;
   {
@@ -318,6 +342,37 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     err = launch_gemm_tc(st, lp.opXvT, lp.opBeta, sys.n_virt, (int)N1, kDscaleSplit, e1, lp.err,
                          lp.dcnt, 2 * sys.n_occ, lp.bn1);
     if (err != cudaSuccess) return err;
+  }
+  if (lp.ar) {
+    // gamma into the per-atom Gcat rows, then step 5 per atom and the sum
+    // of each product's (one or two) partials
+    const AlphaRoute &ar = *lp.ar;
+    {
+      Scope sc(lp.timer, st, kcTcT2, tflops);
+      TcEpilogue e2;
+      e2.outB = ar.gcat_q;
+      e2.ldo = 2 * (int64_t)ar.kcat5;
+      e2.lo_off = ar.kcat5;
+      e2.n_occ = sys.n_occ;
+      e2.aoff = sys.aoff;
+      e2.orb_atom = ar.orb_atom;
+      e2.xoff5 = ar.xoff5;
+      err = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kGammaCatSplit, e2, lp.err,
+                           lp.dcnt, 2 * sys.n_occ, lp.bn2);
+      if (err != cudaSuccess) return err;
+    }
+    {
+      Scope sc(lp.timer, st, kcTcStep5, ncols * ar.flops5);
+      TcEpilogue e5;
+      e5.outF = ar.P2f;
+      e5.ldo = ar.ldp;
+      err = launch_gemm_tc_grouped(st, ar.a5, ar.gcat, ar.tiles5, ar.n_tiles5, ncols, kPartialF32,
+                                   e5, lp.err, lp.dcnt, 2);
+      if (err == cudaSuccess)
+        err = launch_alpha_combine(st, ar, ncols, np, false, Zin, mode == kA ? 1 : 0, Out, lp.dcnt);
+      if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
   }
   {
     Scope sc(lp.timer, st, kcTcT2, tflops);

@@ -56,14 +56,14 @@ constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr size_t OZ_SMEM = (size_t)OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
 
 struct OzArgs {
-  int M, N, Kp;
+  int M, N;
+  int KpA, KpB; // slice-plane widths of the two operands
   int ns;       // slices (the kernel's template argument)
   int cb;       // K blocks per exact chunk
   const int *eA, *eB;
-  double *C;
-  int64_t ldc;
-  int trans;    // 0: C[m*ldc+n], 1: C[n*ldc+m]
-  int vec;      // trans == 0 and 16-byte aligned rows: double2 stores
+  OzEpilogue ep;
+  int vec;      // kOzC with 16-byte aligned rows: double2 stores
+  const GTile *tiles;   // grouped product: one entry per M tile (NULL: plain row tiles)
   int *err;
   const int *dcnt;
   int mul_n;
@@ -110,8 +110,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                       const __grid_constant__ CUtensorMap mapB, OzArgs a) {
   int N = a.N;
   if (a.dcnt) N = (int)min((int64_t)N, (int64_t)a.mul_n * (*a.dcnt));
-  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
+  const int n0 = blockIdx.y * OZ_BN;
   if (n0 >= N) return;
+  // this CTA's rows of A and K range of B
+  int m0, xoff, nkb, rows_valid, atom;
+  if (a.tiles) {
+    const GTile t = a.tiles[blockIdx.x];
+    m0 = t.row0;
+    xoff = t.xoff;
+    nkb = t.nkb;
+    rows_valid = t.rows;
+    atom = t.atom;
+  } else {
+    m0 = blockIdx.x * OZ_BM;
+    xoff = 0;
+    nkb = a.KpA / OZ_BK;
+    rows_valid = min(OZ_BM, a.M - m0);
+    atom = -1;
+  }
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
@@ -123,7 +139,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int s = S;
-  const int nkb = a.Kp / OZ_BK, cb = a.cb;
+  const int cb = a.cb;
   const int nchunks = (nkb + cb - 1) / cb;
   constexpr uint32_t tcols = S <= 4 ? 256u : 512u;
 
@@ -169,8 +185,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           uint8_t *sa = smem + slot * OZ_STAGE_BYTES;
           mbar_expect_tx(&full[slot], OZ_STAGE_BYTES);
-          tma_load_2d(sa, &mapA, &full[slot], i * a.Kp + kb * OZ_BK, m0);
-          tma_load_2d(sa + OZ_A_BYTES, &mapB, &full[slot], i * a.Kp + kb * OZ_BK, n0);
+          tma_load_2d(sa, &mapA, &full[slot], i * a.KpA + kb * OZ_BK, m0);
+          tma_load_2d(sa + OZ_A_BYTES, &mapB, &full[slot], i * a.KpB + xoff + kb * OZ_BK, n0);
         }
       }
       // copies in flight: the last OZ_STAGES stages issued (each the latest
@@ -242,7 +258,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of the tile)
     // and columns 32 h .. 32 h + 31 of every group, h = (w - 2) / 4
     const int q = warp & 3, h = (warp - 2) >> 2;
-    const int m = m0 + q * 32 + lane;
+    const int lr = q * 32 + lane;
+    const int m = m0 + lr;
     const int nc = n0 + h * OZ_EPI_COLS;
     const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * OZ_EPI_COLS);
     long long acc[OZ_EPI_COLS];
@@ -265,11 +282,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty);
     }
-    if (ok && m < a.M && nc < N) {
+    if (ok && lr < rows_valid && nc < N) {
       // C = acc 2^(eA + eB + u - 7(S+1)), as two exact power-of-two factors
       const double fa = pow2(a.eA[m] + oz_drop_bits(S) - 7 * (S + 1));
-      if (!a.trans) {
-        double *crow = a.C + (int64_t)m * a.ldc + nc;
+      const OzEpilogue &ep = a.ep;
+      if (ep.mode == kOzC) {
+        double *crow = ep.C + (int64_t)m * ep.ldc + nc;
         if (a.vec && nc + OZ_EPI_COLS <= N) {
 #pragma unroll
           for (int j = 0; j < OZ_EPI_COLS; j += 2) {
@@ -283,11 +301,37 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           for (int j = 0; j < OZ_EPI_COLS; ++j)
             if (nc + j < N) crow[j] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
         }
-      } else {
+      } else if (ep.mode == kOzCT) {
 #pragma unroll
         for (int j = 0; j < OZ_EPI_COLS; ++j)
           if (nc + j < N)
-            a.C[(int64_t)(nc + j) * a.ldc + m] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+            ep.C[(int64_t)(nc + j) * ep.ldc + m] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+      } else if (ep.mode == kOzBetaT) {
+        // row m = (atom A, E, c): beta^T[(j n_occ + E)][ao_A + c] for column j
+        const int aoA = ep.aoff[atom], nA = ep.aoff[atom + 1] - aoA;
+        const int r = m - aoA * ep.n_occ, E = r / nA, c = r - E * nA;
+        double *dst = ep.C + (int64_t)E * ep.ldc + aoA + c;
+        const int64_t step = (int64_t)ep.n_occ * ep.ldc;
+#pragma unroll
+        for (int j = 0; j < OZ_EPI_COLS; ++j)
+          if (nc + j < N)
+            dst[(int64_t)(nc + j) * step] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+      } else {
+        // kOzGammaCat: row m = orbital (atom B, b), column n = j n_occ + E ->
+        // Gcat[j][xoff_B + b n_occ + E]
+        const int B = ep.orb_atom[m], b = m - ep.aoff[B];
+        const int64_t xo = ep.xoff5[B] + (int64_t)b * ep.n_occ;
+        int jj = nc / ep.n_occ, E = nc - jj * ep.n_occ;
+#pragma unroll
+        for (int j = 0; j < OZ_EPI_COLS; ++j) {
+          if (nc + j < N)
+            ep.C[(int64_t)jj * ep.ldc + xo + E] =
+                (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+          if (++E == ep.n_occ) {
+            E = 0;
+            ++jj;
+          }
+        }
       }
     }
   }
@@ -321,16 +365,25 @@ __device__ __forceinline__ void store_slices(double y0, double y1, int s, int Kp
   }
 }
 
+// Row r of the operand: X[r][k] for k < Kdim, or, with a column map,
+// X[r][cols[k]] (zero where cols[k] < 0).
 __global__ void oz_slice_rows_kernel(int rows, int Kdim, const double *__restrict__ X, int64_t ldx,
-                                     int s, int Kp, __nv_bfloat16 *__restrict__ Q,
-                                     int *__restrict__ E, const int *dcnt, int mul) {
+                                     const int *__restrict__ cols, int s, int Kp,
+                                     __nv_bfloat16 *__restrict__ Q, int *__restrict__ E,
+                                     const int *dcnt, int mul) {
   __shared__ double red[32];
   int live = rows;
   if (dcnt) live = min(rows, mul * (*dcnt));
+  auto val = [&](const double *x, int k) -> double {
+    if (k >= Kdim) return 0.0;
+    if (!cols) return x[k];
+    const int c = cols[k];
+    return c >= 0 ? x[c] : 0.0;
+  };
   for (int r = blockIdx.x; r < live; r += gridDim.x) {
     const double *x = X + (int64_t)r * ldx;
     double mx = 0.0;
-    for (int k = threadIdx.x; k < Kdim; k += blockDim.x) mx = fmax(mx, fabs(x[k]));
+    for (int k = threadIdx.x; k < Kdim; k += blockDim.x) mx = fmax(mx, fabs(val(x, k)));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
@@ -345,11 +398,8 @@ __global__ void oz_slice_rows_kernel(int rows, int Kdim, const double *__restric
     if (threadIdx.x == 0) E[r] = e;
     const double sc = ldexp(1.0, 7 - e);
     __nv_bfloat16 *qr = Q + (int64_t)r * s * Kp;
-    for (int k = 2 * threadIdx.x; k < Kp; k += 2 * blockDim.x) {
-      const double y0 = k < Kdim ? x[k] * sc : 0.0;
-      const double y1 = k + 1 < Kdim ? x[k + 1] * sc : 0.0;
-      store_slices(y0, y1, s, Kp, qr + k);
-    }
+    for (int k = 2 * threadIdx.x; k < Kp; k += 2 * blockDim.x)
+      store_slices(val(x, k) * sc, val(x, k + 1) * sc, s, Kp, qr + k);
   }
 }
 
@@ -442,12 +492,12 @@ cudaError_t oz_operand(OzOperand &op, __nv_bfloat16 *q, int *e, int64_t rows, in
 }
 
 cudaError_t launch_oz_slice_rows(cudaStream_t st, const double *X, int64_t ldx, int rows, int Kdim,
-                                 OzOperand &op, const int *dcnt, int mul) {
+                                 OzOperand &op, const int *dcnt, int mul, const int *cols) {
   if (rows <= 0) return cudaSuccess;
   if (rows > op.rows || Kdim > op.Kp) return cudaErrorInvalidValue;
   const int grid = std::min(rows, 152 * 8);
-  oz_slice_rows_kernel<<<grid, 256, 0, st>>>(rows, Kdim, X, ldx, op.s, op.Kp, op.q, op.e, dcnt,
-                                             mul);
+  oz_slice_rows_kernel<<<grid, 256, 0, st>>>(rows, Kdim, X, ldx, cols, op.s, op.Kp, op.q, op.e,
+                                             dcnt, mul);
   return cudaGetLastError();
 }
 
@@ -460,30 +510,32 @@ cudaError_t launch_oz_slice_cols(cudaStream_t st, const double *X, int64_t ldx, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_oz(cudaStream_t st, const OzOperand &A, const OzOperand &B, int M, int N,
-                           double *C, int64_t ldc, int trans, int *err, const int *dcnt,
-                           int mul_n) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  if (A.Kp != B.Kp || A.s != B.s || M > A.rows || N > B.rows) return cudaErrorInvalidValue;
+cudaError_t launch_gemm_oz_ex(cudaStream_t st, const OzOperand &A, const OzOperand &B, int M,
+                              int N, const OzEpilogue &ep, const GTile *tiles, int n_tiles,
+                              int max_nkb, int *err, const int *dcnt, int mul_n) {
+  if (N <= 0 || (tiles ? n_tiles <= 0 : M <= 0)) return cudaSuccess;
+  if (A.s != B.s || N > B.rows || (!tiles && (A.Kp != B.Kp || M > A.rows)))
+    return cudaErrorInvalidValue;
   cudaError_t e = oz_init_attributes();
   if (e != cudaSuccess) return e;
   OzArgs a;
   a.M = M;
   a.N = N;
-  a.Kp = A.Kp;
+  a.KpA = A.Kp;
+  a.KpB = B.Kp;
   a.ns = A.s;
   a.cb = chunk_blocks(A.s);
-  if ((A.Kp / OZ_BK + a.cb - 1) / a.cb > kOzMaxChunks) return cudaErrorInvalidValue;
+  const int nkb = tiles ? max_nkb : A.Kp / OZ_BK;
+  if ((nkb + a.cb - 1) / a.cb > kOzMaxChunks) return cudaErrorInvalidValue;
   a.eA = A.e;
   a.eB = B.e;
-  a.C = C;
-  a.ldc = ldc;
-  a.trans = trans;
-  a.vec = (!trans && (ldc % 2) == 0 && ((uintptr_t)C & 15) == 0) ? 1 : 0;
+  a.ep = ep;
+  a.vec = (ep.mode == kOzC && (ep.ldc % 2) == 0 && ((uintptr_t)ep.C & 15) == 0) ? 1 : 0;
+  a.tiles = tiles;
   a.err = err;
   a.dcnt = dcnt;
   a.mul_n = mul_n;
-  dim3 grid((M + OZ_BM - 1) / OZ_BM, (N + OZ_BN - 1) / OZ_BN);
+  dim3 grid(tiles ? n_tiles : (M + OZ_BM - 1) / OZ_BM, (N + OZ_BN - 1) / OZ_BN);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   switch (A.s) {
     case 3: return launch_oz_kernel<3>(st, grid, A.map, B.map, a);
@@ -494,6 +546,16 @@ cudaError_t launch_gemm_oz(cudaStream_t st, const OzOperand &A, const OzOperand 
     case 8: return launch_oz_kernel<8>(st, grid, A.map, B.map, a);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_gemm_oz(cudaStream_t st, const OzOperand &A, const OzOperand &B, int M, int N,
+                           double *C, int64_t ldc, int trans, int *err, const int *dcnt,
+                           int mul_n) {
+  OzEpilogue ep;
+  ep.mode = trans ? kOzCT : kOzC;
+  ep.C = C;
+  ep.ldc = ldc;
+  return launch_gemm_oz_ex(st, A, B, M, N, ep, nullptr, 0, 0, err, dcnt, mul_n);
 }
 
 // Constants sliced once; dynamic operands sized for `slots` right-hand sides.

@@ -19,6 +19,7 @@ struct tddft_ctx {
   bool lowprec = false;
   OzWork oz;
   bool emu = false;
+  AlphaRoute ar;
   GmresState gs;
   Timer timer;
   tddft_options opts{};
@@ -98,7 +99,8 @@ const char *kernel_class_name(int k) {
       "f64_gemm_T2", "f64_block_dot", "tc_gemm_K",    "lp_vertex",    "lp_beta",
       "tc_gemm_T1_dscale", "tc_gemm_T2", "lp_block_dot", "lp_split_z", "gmres_step",
       "gmres_gather", "gmres_select", "rhs_formation", "misc", "emu_slice", "emu_gemm_K",
-      "emu_gemm_T1", "emu_gemm_T2"};
+      "emu_gemm_T1", "emu_gemm_T2", "alpha_gather", "tc_alpha_beta", "tc_alpha_dot",
+      "emu_alpha_beta", "emu_alpha_dot"};
   return (k >= 0 && k < kcCount) ? names[k] : "?";
 }
 
@@ -404,7 +406,13 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     e = oz_setup(c->st, d, c->oz, (int)S, c->dev_allocs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     w.oz = &c->oz;
+    w.ar = &c->ar;
+    // beta^T columns of atoms without products are never written
+    if (e == cudaSuccess)
+      e = cudaMemset(w.beta, 0, (size_t)no * 2 * S3 * nocc * sizeof(double));
   }
+  if (e == cudaSuccess && (c->emu || refine))
+    e = alpha_setup(c->st, s, d, c->ar, (int)S, refine, c->emu, c->oz.s, c->dev_allocs);
   if (c->lowprec) {
     g.inner_tol = o->inner_tol;
     LpWork &L = c->lp;
@@ -413,6 +421,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     L.Kp1 = round_up(no, 64);
     L.Kp2 = round_up(nv, 64);
     L.timer = &c->timer;
+    L.ar = &c->ar;
     const size_t rows1 = 2 * S * (size_t)nocc;
     AL(L.Ks, (size_t)np * 2 * L.KpK);
     AL(L.XvTs, (size_t)nv * 2 * L.Kp1);
