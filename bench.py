@@ -37,8 +37,11 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (DFMA) nominal rate; no tensor path fo
 # FP32 CUDA-core peak from unit counts: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
 FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # kernel launches behind one timed scope (the others launch one kernel each)
-KERNELS_PER_SCOPE = {"rhs_formation": 7, "emu_gemm_K": 2, "emu_gemm_T1": 2, "emu_gemm_T2": 2}
-KERNELS_PER_SCOPE_EMU = dict(KERNELS_PER_SCOPE, rhs_formation=9)
+KERNELS_PER_SCOPE = {"rhs_formation": 7, "emu_gemm_K": 2, "emu_gemm_T1": 2, "emu_gemm_T2": 2,
+                     "emu_alpha_beta": 2, "emu_alpha_dot": 3, "tc_alpha_dot": 2}
+# emulated right-hand-side formation: dipole rows, slice + step 2, slice + T1,
+# expand, slice + T2, slice + step 5, combine
+KERNELS_PER_SCOPE_EMU = dict(KERNELS_PER_SCOPE, rhs_formation=11)
 # slice pairs of one emulated float64 product (6 slices: pairs with i + j <= 7)
 EMU_PAIRS = 21
 
@@ -236,7 +239,7 @@ def roofline_of(timing: dict, step_ms: float) -> dict:
         peak = peaks["bf16_tflops_sustained"] / 3.0
         bound, note = "tensor", (f"split bf16: 3 bf16 products per algorithmic product; peak = "
                                  f"{src} sustained bf16 {peaks['bf16_tflops_sustained']} / 3")
-    elif name.startswith("emu_gemm"):
+    elif name.startswith("emu_gemm") or name.startswith("emu_alpha"):
         peak = peaks["bf16_tflops_sustained"] / EMU_PAIRS
         bound, note = "tensor", (f"float64 emulated with {EMU_PAIRS} bf16 slice products per "
                                  f"algorithmic product; peak = {src} sustained bf16 "
@@ -383,7 +386,8 @@ def run_ours(args):
         gpu_launches = int(round(gpu_launches * args.steps))
     chi_cls = ["f64_vertex", "f64_beta", "f64_gemm_T1", "f64_dscale", "f64_gemm_T2",
                "f64_block_dot", "lp_vertex", "lp_beta", "tc_gemm_T1_dscale", "tc_gemm_T2",
-               "lp_block_dot", "emu_gemm_T1", "emu_gemm_T2"]
+               "lp_block_dot", "emu_gemm_T1", "emu_gemm_T2", "alpha_gather", "tc_alpha_beta",
+               "tc_alpha_dot", "emu_alpha_beta", "emu_alpha_dot"]
     chi_ms = sum(timing[c]["ms"] for c in chi_cls)
     n_virt = s.n_orb - s.n_occ
     t1_flops = (timing["f64_gemm_T1"]["flops"] + timing["tc_gemm_T1_dscale"]["flops"]

@@ -206,13 +206,29 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
         if (m < M) {
           const int B = ep.orb_atom[m], b = m - ep.aoff[B];
           const int64_t xo = ep.xoff5[B] + (int64_t)b * ep.n_occ;
+          const int pair0 = (n0 + j0) >> 1;
+          if (ep.n_occ % 8 == 0 && n0 + j0 + 16 <= N) {
+            // the 16 columns are E0 .. E0+7 of one slot, both planes: four
+            // 16-byte stores (hi and lo of p = 0 and p = 1)
+            const int sl = pair0 / ep.n_occ, E0 = pair0 - sl * ep.n_occ;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + j0 + j;
-            if (n < N) {
-              const int pair = n >> 1, p = n & 1;
-              const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
-              store_split(ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E, ep.lo_off, v[j]);
+            for (int p = 0; p < 2; ++p) {
+              __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) split_bf16(v[2 * e + p], h[e], l[e]);
+              __nv_bfloat16 *dst = ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E0;
+              *(uint4 *)dst = *(const uint4 *)h;
+              *(uint4 *)(dst + ep.lo_off) = *(const uint4 *)l;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = n0 + j0 + j;
+              if (n < N) {
+                const int pair = n >> 1, p = n & 1;
+                const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
+                store_split(ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E, ep.lo_off, v[j]);
+              }
             }
           }
         }

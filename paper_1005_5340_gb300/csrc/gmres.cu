@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
                                                         const int *__restrict__ dcnt) {
   __shared__ double red[16 * (NT / 32)];
   __shared__ double clx[16];
-  __shared__ double2 hs[257], hp[257], ys[257];
+  __shared__ double2 hs[257], hp[257], ys[257], hq[257];
   __shared__ int finish_flag;
   const int s = blockIdx.y;
   if (dcnt && s >= *dcnt) return;          // the same for the whole cluster
@@ -314,26 +314,44 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
   // Classical Gram-Schmidt with selective reorthogonalisation: the second
   // pass runs only when the first one removed more than half of ||w||^2
   // (the Daniel-Gragg-Kaufman-Stewart criterion with eta = 1/sqrt(2)).
+  const int warp = tid >> 5, lane = tid & 31;
   for (int pass = 0; pass < 2; ++pass) {
-    // h_i = <v_i, w> for i <= j, eight at a time
-    for (int i0 = 0; i0 <= j; i0 += 8) {
-      double part[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) part[q] = 0.0;
-      for (int e = lo + tid; e < hi; e += NT) {
+    // h_i = <v_i, w> for i <= j: warp q streams v_q, v_{q+8}, ... over this
+    // CTA's elements; the partial dots of all i are then reduced across the
+    // cluster at once (rank order)
+    for (int i = warp; i <= j; i += NT / 32) {
+      const double *vi_ = Vr + (int64_t)i * 2 * N;
+      double pr = 0.0, pim = 0.0;
+#pragma unroll 4
+      for (int e = lo + lane; e < hi; e += 32) {
         const double wr = w[e], wi = w[N + e];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (i0 + q <= j) {
-            const double *vi_ = Vr + (int64_t)(i0 + q) * 2 * N;
-            const double vr = vi_[e], vi = vi_[N + e];
-            part[2 * q] = fma(vr, wr, fma(vi, wi, part[2 * q]));
-            part[2 * q + 1] = fma(vr, wi, fma(-vi, wr, part[2 * q + 1]));
-          }
-        }
+        const double vr = vi_[e], vi = vi_[N + e];
+        pr = fma(vr, wr, fma(vi, wi, pr));
+        pim = fma(vr, wi, fma(-vi, wr, pim));
       }
-      cluster_sum<P, 16>(part, red, clx);
-      if (tid < 8 && i0 + tid <= j) hp[i0 + tid] = make_double2(part[2 * tid], part[2 * tid + 1]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        pr += __shfl_xor_sync(0xffffffffu, pr, off);
+        pim += __shfl_xor_sync(0xffffffffu, pim, off);
+      }
+      if (lane == 0) hq[i] = make_double2(pr, pim);
+    }
+    if (P == 1) {
+      __syncthreads();
+      for (int i = tid; i <= j; i += NT) hp[i] = hq[i];
+    } else {
+      cg::cluster_group cl = cg::this_cluster();
+      cl.sync();
+      for (int i = tid; i <= j; i += NT) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int rk = 0; rk < P; ++rk) {
+          const double2 q = cl.map_shared_rank(hq, rk)[i];
+          t.x += q.x;
+          t.y += q.y;
+        }
+        hp[i] = t;
+      }
+      cl.sync();   // hq may be rewritten once every CTA has read it
     }
     __syncthreads();
     // w -= sum_i h_i v_i, with the new ||w||^2
@@ -554,7 +572,7 @@ cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState 
   // Long vectors: a cluster of CTAs per right-hand side, so that the FP64
   // work of the orthogonalisation is spread over more SMs than there are
   // live right-hand sides.
-  const int P = sys.n_prod >= 8192 ? 4 : (sys.n_prod >= 2048 ? 2 : 1);
+  const int P = sys.n_prod >= 8192 ? 8 : (sys.n_prod >= 4096 ? 4 : (sys.n_prod >= 2048 ? 2 : 1));
   if (P == 1) {
     gmres_step_kernel<1><<<dim3(1, S), NT, 0, st>>>(G, list, Wout, dcnt);
     return cudaGetLastError();
@@ -571,6 +589,7 @@ cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (P == 8) return cudaLaunchKernelEx(&cfg, gmres_step_kernel<8>, G, list, Wout, dcnt);
   return P == 4 ? cudaLaunchKernelEx(&cfg, gmres_step_kernel<4>, G, list, Wout, dcnt)
                 : cudaLaunchKernelEx(&cfg, gmres_step_kernel<2>, G, list, Wout, dcnt);
 }

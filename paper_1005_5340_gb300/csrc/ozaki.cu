@@ -403,6 +403,64 @@ __global__ void oz_slice_rows_kernel(int rows, int Kdim, const double *__restric
   }
 }
 
+// Long rows: grid (chunks, rows).  Pass 1 raises E[r] (preset to a large
+// negative value) to the exponent of each chunk's largest magnitude; pass 2
+// slices every chunk with the row's exponent (a row of zeros keeps the preset
+// value and gives zero slices).
+constexpr int OZ_CHUNK = 4096;
+constexpr int kOzZeroRow = -1100;   // below every finite exponent
+
+__device__ __forceinline__ double gathered(const double *x, const int *cols, int k, int Kdim) {
+  if (k >= Kdim) return 0.0;
+  if (!cols) return x[k];
+  const int c = cols[k];
+  return c >= 0 ? x[c] : 0.0;
+}
+
+__global__ void __launch_bounds__(256) oz_rowmax_kernel(int rows, int Kdim,
+                                                        const double *__restrict__ X, int64_t ldx,
+                                                        const int *__restrict__ cols,
+                                                        int *__restrict__ E, const int *dcnt,
+                                                        int mul) {
+  __shared__ double red[8];
+  int live = rows;
+  if (dcnt) live = min(rows, mul * (*dcnt));
+  const int r = blockIdx.y;
+  if (r >= live) return;
+  const double *x = X + (int64_t)r * ldx;
+  const int k0 = blockIdx.x * OZ_CHUNK, k1 = min(Kdim, k0 + OZ_CHUNK);
+  double mx = 0.0;
+  for (int k = k0 + threadIdx.x; k < k1; k += 256) mx = fmax(mx, fabs(gathered(x, cols, k, Kdim)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < 8; ++i) mx = fmax(mx, red[i]);
+    if (mx > 0.0) atomicMax(E + r, row_exponent(mx));
+  }
+}
+
+__global__ void __launch_bounds__(256) oz_slice_chunks_kernel(int rows, int Kdim,
+                                                              const double *__restrict__ X,
+                                                              int64_t ldx,
+                                                              const int *__restrict__ cols, int s,
+                                                              int Kp, __nv_bfloat16 *__restrict__ Q,
+                                                              const int *__restrict__ E,
+                                                              const int *dcnt, int mul) {
+  int live = rows;
+  if (dcnt) live = min(rows, mul * (*dcnt));
+  const int r = blockIdx.y;
+  if (r >= live) return;
+  const double *x = X + (int64_t)r * ldx;
+  const int e = max(E[r], kOzZeroRow);   // zero row: any scale gives zero slices
+  const double sc = ldexp(1.0, 7 - (e == kOzZeroRow ? 0 : e));
+  __nv_bfloat16 *qr = Q + (int64_t)r * s * Kp;
+  const int k0 = blockIdx.x * OZ_CHUNK, k1 = min(Kp, k0 + OZ_CHUNK);
+  for (int k = k0 + 2 * threadIdx.x; k < k1; k += 512)
+    store_slices(gathered(x, cols, k, Kdim) * sc, gathered(x, cols, k + 1, Kdim) * sc, s, Kp,
+                 qr + k);
+}
+
 // 32 columns per CTA (256 threads): column maxima, then 64-row tiles staged
 // through shared memory and written as rows of the transposed operand.
 __global__ void __launch_bounds__(256) oz_slice_cols_kernel(int Kdim, int N,
@@ -495,6 +553,16 @@ cudaError_t launch_oz_slice_rows(cudaStream_t st, const double *X, int64_t ldx, 
                                  OzOperand &op, const int *dcnt, int mul, const int *cols) {
   if (rows <= 0) return cudaSuccess;
   if (rows > op.rows || Kdim > op.Kp) return cudaErrorInvalidValue;
+  if (op.Kp >= 2 * OZ_CHUNK && rows <= 65535) {
+    // long rows: chunks of a row on separate CTAs (exponent by atomic max)
+    cudaError_t e = cudaMemsetAsync(op.e, 0x80, (size_t)rows * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    dim3 g1((Kdim + OZ_CHUNK - 1) / OZ_CHUNK, rows), g2((op.Kp + OZ_CHUNK - 1) / OZ_CHUNK, rows);
+    oz_rowmax_kernel<<<g1, 256, 0, st>>>(rows, Kdim, X, ldx, cols, op.e, dcnt, mul);
+    oz_slice_chunks_kernel<<<g2, 256, 0, st>>>(rows, Kdim, X, ldx, cols, op.s, op.Kp, op.q, op.e,
+                                               dcnt, mul);
+    return cudaGetLastError();
+  }
   const int grid = std::min(rows, 152 * 8);
   oz_slice_rows_kernel<<<grid, 256, 0, st>>>(rows, Kdim, X, ldx, cols, op.s, op.Kp, op.q, op.e,
                                              dcnt, mul);
