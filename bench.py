@@ -235,6 +235,16 @@ def roofline_of(timing: dict, step_ms: float) -> dict:
     launches = max(1, d["launches"])
     per_launch_s = d["ms"] / launches / 1e3
     achieved = (d["flops"] / launches) / per_launch_s / 1e12 if d["flops"] else None
+    if not d["flops"] and d.get("bytes"):
+        # memory-bound class with device-counted algorithmic bytes
+        achieved = (d["bytes"] / launches) / per_launch_s / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{src} HBM copy bandwidth",
+                "algorithmic_bytes_per_launch": d["bytes"] / launches,
+                "share_of_step": d["ms"] / step_ms, "launches": d["launches"],
+                "ms_per_launch": d["ms"] / launches}
     if name.startswith("tc_"):
         peak = peaks["bf16_tflops_sustained"] / 3.0
         bound, note = "tensor", (f"split bf16: 3 bf16 products per algorithmic product; peak = "
@@ -441,6 +451,8 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": gpu_launches,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},
+        "kernel_launches": {k: v["launches"] for k, v in timing.items() if v["launches"]},
+        "tc_n_tiles": list(ctx.tuning()),
     }
     print(json.dumps(out), flush=True)
     ctx.close()

@@ -253,6 +253,16 @@ tddft_status tddft_timing_enable(tddft_ctx *ctx, int32_t on);
 int32_t tddft_timing_count(const tddft_ctx *ctx);
 tddft_status tddft_timing_get(tddft_ctx *ctx, int32_t i, const char **name, int32_t *launches,
                               double *total_ms, double *flops);
+/*
+ * Algorithmic bytes moved by the timed launches of class i, where counted
+ * (0 otherwise).  The GMRES step counts on the device, per right-hand side
+ * and step, the float64 vectors (16 n_prod bytes each) it must read or write
+ * at least: 2 (j + 1) + 3 for Arnoldi step j (the basis v_0..v_j read for the
+ * inner products and again for the update, A v_j read, v_{j+1} written and
+ * normalised in place), j + 3 more when the cycle ends (x += V y), and 3 for
+ * a residual check (b, A x read, v_0 written).  Synchronises the stream.
+ */
+tddft_status tddft_timing_bytes(tddft_ctx *ctx, int32_t i, double *bytes);
 
 /*
  * Self-test of the split-bf16 tensor-core GEMM used by TDDFT_PREC_BF16X3_IR:

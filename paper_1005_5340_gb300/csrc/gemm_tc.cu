@@ -233,24 +233,51 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
           }
         }
       } else {
-        // (re, im) pairs: columns n (even) and n+1 of the same (slot, E)
+        // (re, im) pairs: columns n (even) and n+1 of the same (slot, E).
+        // omega -+ Delta, Delta = e_F - e_E, cancel near a resonance: they are
+        // formed as (omega -+ e_F) +- e_E from float (hi, lo) pairs, the
+        // first once per slot in float64; the rest of D in float32 (its
+        // rounding, ~1e-7, is far below the split-bf16 error).
         if (m < ep.rows_out) {
           const bool live = m < M;
+          const float ef = (float)ep.eps, e2 = ef * ef, occ = (float)ep.occ_value;
+          const int pair0 = (n0 + j0) >> 1;
+          const int sl0 = pair0 / ep.n_occ, E0 = pair0 - sl0 * ep.n_occ;
+          // (omega -+ e_F) of the chunk's slot, once (the usual case: all 8
+          // pairs in one slot); otherwise per pair
+          float am_hi = 0.f, am_lo = 0.f, ap_hi = 0.f, ap_lo = 0.f;
+          const bool one_slot = E0 + 8 <= ep.n_occ;
+          double eF = 0.0;
+          if (live) {
+            eF = ep.energy[ep.n_occ + m];
+            if (one_slot) {
+              const double w = ep.omega[sl0];
+              const double am = w - eF, ap = w + eF;
+              am_hi = (float)am;
+              am_lo = (float)(am - (double)am_hi);
+              ap_hi = (float)ap;
+              ap_lo = (float)(ap - (double)ap_hi);
+            }
+          }
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
             const int n = n0 + j0 + j;
             if (n >= N) continue;
             float re = 0.f, im = 0.f;
             if (live) {
-              // omega -+ Delta in float64 (they cancel near a resonance), the rest of
-              // D in float32: its rounding (~1e-7) is far below the split-bf16 error
-              const int pair = n >> 1;
-              const int E = pair % ep.n_occ;
-              const int sl = pair / ep.n_occ;
-              const double delta = ep.energy[ep.n_occ + m] - ep.energy[E];
-              const double w = ep.omega[sl];
-              const float xm = (float)(w - delta), xp = (float)(w + delta);
-              const float ef = (float)ep.eps, e2 = ef * ef, occ = (float)ep.occ_value;
+              float xm, xp;
+              if (one_slot) {
+                const float2 eE = ep.eocc2[E0 + (j >> 1)];
+                xm = (am_hi + eE.x) + (am_lo + eE.y);
+                xp = (ap_hi - eE.x) + (ap_lo - eE.y);
+              } else {
+                const int pair = n >> 1;
+                const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
+                const double delta = eF - ep.energy[E];
+                const double w = ep.omega[sl];
+                xm = (float)(w - delta);
+                xp = (float)(w + delta);
+              }
               const float im2 = __frcp_rn(fmaf(xm, xm, e2)), ip2 = __frcp_rn(fmaf(xp, xp, e2));
               const float dre = occ * (xm * im2 - xp * ip2);
               const float dim = occ * ef * (ip2 - im2);

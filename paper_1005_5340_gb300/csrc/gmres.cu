@@ -2,9 +2,10 @@
 // (omega, field direction): eq. sle solved by the Krylov method of Sec. 4.1
 // (basis of eq. orthogonal-krylov-basis, minimal residual in the subspace),
 // float64 throughout.  Each right-hand side runs its own state machine:
-//   Arnoldi step j : w = A v_j, two passes of classical Gram-Schmidt
-//                    (CGS2) against v_0..v_j, Givens QR of the Hessenberg
-//                    column, residual estimate |g_{j+1}|;
+//   Arnoldi step j : w = A v_j, classical Gram-Schmidt against v_0..v_j
+//                    with the second (reorthogonalising) pass folded in
+//                    through the basis Gram matrix, Givens QR of the
+//                    Hessenberg column, residual estimate |g_{j+1}|;
 //   end of a cycle : x += V y, then the next operator application computes
 //                    A x so that the true residual b - A x decides between
 //                    done, not converged (cycle limit) and a restart.
@@ -73,6 +74,8 @@ struct Gs {
   double2 *H, *sn, *g;
   double *cs, *V, *x, *b;
   const int *act;
+  unsigned long long *bytes;
+  double2 *Gm;
 };
 
 Gs view(const GmresState &s, int n_prod) {
@@ -83,6 +86,8 @@ Gs view(const GmresState &s, int n_prod) {
   v.flags = s.flags;
   v.bnorm = s.bnorm; v.resid = s.resid; v.omega = s.omega;
   v.H = s.H; v.sn = s.sn; v.g = s.g; v.cs = s.cs; v.V = s.V; v.x = s.x; v.b = s.b; v.act = s.act;
+  v.bytes = s.bytes;
+  v.Gm = s.Gm;
   return v;
 }
 
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
                                                         const int *__restrict__ dcnt) {
   __shared__ double red[16 * (NT / 32)];
   __shared__ double clx[16];
-  __shared__ double2 hs[257], hp[257], ys[257], hq[257];
+  __shared__ double2 hs[257], hp[257], ys[257], hq[257], gq[257], gp[257];
   __shared__ int finish_flag;
   const int s = blockIdx.y;
   if (dcnt && s >= *dcnt) return;          // the same for the whole cluster
@@ -279,6 +284,7 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
       }
     }
     if (tid == 0 && rank == 0) {
+      atomicAdd(G.bytes, 3ull * 16ull * (unsigned long long)N);
       G.matvecs[r] += 1;
       G.resid[r] = rel;
       if (rejected) G.flags[r] |= 1;
@@ -300,82 +306,110 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
   const double2 gj0 = G.g[(int64_t)r * (m + 1) + j];
   const double rho0 = G.rho0[r];
   double *w = Vr + (int64_t)(j + 1) * 2 * N;
-  double n0[1] = {0.0};
-  for (int e = lo + tid; e < hi; e += NT) {
-    const double tr = win[e], ti = win[N + e];
-    w[e] = tr;
-    w[N + e] = ti;
-    n0[0] += tr * tr + ti * ti;
-  }
-  for (int i = tid; i <= j; i += NT) hs[i] = make_double2(0.0, 0.0);
-  cluster_sum<P, 1>(n0, red, clx);   // ||A v_j||^2 (synchronises)
-  double hn = 0.0;
-
-  // Classical Gram-Schmidt with selective reorthogonalisation: the second
-  // pass runs only when the first one removed more than half of ||w||^2
-  // (the Daniel-Gragg-Kaufman-Stewart criterion with eta = 1/sqrt(2)).
+  const double *vj = Vr + (int64_t)j * 2 * N;
   const int warp = tid >> 5, lane = tid & 31;
-  for (int pass = 0; pass < 2; ++pass) {
-    // h_i = <v_i, w> for i <= j: warp q streams v_q, v_{q+8}, ... over this
-    // CTA's elements; the partial dots of all i are then reduced across the
-    // cluster at once (rank order)
-    for (int i = warp; i <= j; i += NT / 32) {
-      const double *vi_ = Vr + (int64_t)i * 2 * N;
-      double pr = 0.0, pim = 0.0;
+
+  // Classical Gram-Schmidt with the reorthogonalisation folded in through the
+  // Gram matrix of the basis, G_ik = <v_i, v_k>: one pass over v_0..v_j gives
+  // h1_i = <v_i, A v_j> and the new column g_i = <v_i, v_j>; the second CGS
+  // pass would add h2 = V^H (w - V h1) = h1 - G h1, so the coefficients are
+  // h = 2 h1 - G h1 and w = A v_j - V h (one update pass).  Warp q streams
+  // v_q, v_{q+8}, ... over this CTA's elements; the partial dots of all i
+  // are reduced across the cluster at once, in rank order.
+  for (int i = warp; i <= j; i += NT / 32) {
+    const double *vi_ = Vr + (int64_t)i * 2 * N;
+    double pr = 0.0, pim = 0.0, gr = 0.0, gim = 0.0;
 #pragma unroll 4
-      for (int e = lo + lane; e < hi; e += 32) {
-        const double wr = w[e], wi = w[N + e];
-        const double vr = vi_[e], vi = vi_[N + e];
-        pr = fma(vr, wr, fma(vi, wi, pr));
-        pim = fma(vr, wi, fma(-vi, wr, pim));
-      }
+    for (int e = lo + lane; e < hi; e += 32) {
+      const double wr = win[e], wi = win[N + e];
+      const double ar = vj[e], ai = vj[N + e];
+      const double vr = vi_[e], vi = vi_[N + e];
+      pr = fma(vr, wr, fma(vi, wi, pr));
+      pim = fma(vr, wi, fma(-vi, wr, pim));
+      gr = fma(vr, ar, fma(vi, ai, gr));
+      gim = fma(vr, ai, fma(-vi, ar, gim));
+    }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        pr += __shfl_xor_sync(0xffffffffu, pr, off);
-        pim += __shfl_xor_sync(0xffffffffu, pim, off);
-      }
-      if (lane == 0) hq[i] = make_double2(pr, pim);
+    for (int off = 16; off > 0; off >>= 1) {
+      pr += __shfl_xor_sync(0xffffffffu, pr, off);
+      pim += __shfl_xor_sync(0xffffffffu, pim, off);
+      gr += __shfl_xor_sync(0xffffffffu, gr, off);
+      gim += __shfl_xor_sync(0xffffffffu, gim, off);
     }
-    if (P == 1) {
-      __syncthreads();
-      for (int i = tid; i <= j; i += NT) hp[i] = hq[i];
-    } else {
-      cg::cluster_group cl = cg::this_cluster();
-      cl.sync();
-      for (int i = tid; i <= j; i += NT) {
-        double2 t = make_double2(0.0, 0.0);
-        for (int rk = 0; rk < P; ++rk) {
-          const double2 q = cl.map_shared_rank(hq, rk)[i];
-          t.x += q.x;
-          t.y += q.y;
-        }
-        hp[i] = t;
-      }
-      cl.sync();   // hq may be rewritten once every CTA has read it
+    if (lane == 0) {
+      hq[i] = make_double2(pr, pim);
+      gq[i] = make_double2(gr, gim);
     }
-    __syncthreads();
-    // w -= sum_i h_i v_i, with the new ||w||^2
-    double n1[1] = {0.0};
-    for (int e = lo + tid; e < hi; e += NT) {
-      double ar = 0.0, ai = 0.0;
-      for (int i = 0; i <= j; ++i) {
-        const double *vi_ = Vr + (int64_t)i * 2 * N;
-        const double2 h = hp[i];
-        const double vr = vi_[e], vi = vi_[N + e];
-        ar += h.x * vr - h.y * vi;
-        ai += h.x * vi + h.y * vr;
-      }
-      const double nr = w[e] - ar, ni = w[N + e] - ai;
-      w[e] = nr;
-      w[N + e] = ni;
-      n1[0] += nr * nr + ni * ni;
-    }
-    for (int i = tid; i <= j; i += NT) hs[i] = make_double2(hs[i].x + hp[i].x, hs[i].y + hp[i].y);
-    cluster_sum<P, 1>(n1, red, clx);   // synchronises: w and hs complete
-    hn = sqrt(n1[0]);
-    if (n1[0] > 0.5 * n0[0]) break;   // uniform across the cluster
-    n0[0] = n1[0];
   }
+  if (P == 1) {
+    __syncthreads();
+    for (int i = tid; i <= j; i += NT) {
+      hp[i] = hq[i];
+      gp[i] = gq[i];
+    }
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    for (int i = tid; i <= j; i += NT) {
+      double2 t = make_double2(0.0, 0.0), u = make_double2(0.0, 0.0);
+      for (int rk = 0; rk < P; ++rk) {
+        const double2 a = cl.map_shared_rank(hq, rk)[i];
+        const double2 b = cl.map_shared_rank(gq, rk)[i];
+        t.x += a.x;
+        t.y += a.y;
+        u.x += b.x;
+        u.y += b.y;
+      }
+      hp[i] = t;
+      gp[i] = u;
+    }
+    cl.sync();   // hq, gq may be rewritten once every CTA has read them
+  }
+  __syncthreads();
+  // h_i = 2 h1_i - sum_k G_ik h1_k (warp per row i, lanes over k); column k
+  // of G (entries i <= k) is stored at Gr[k (m+1) + i], column j is gp
+  double2 *Gr = G.Gm + (int64_t)r * (m + 1) * (m + 1);
+  for (int i = warp; i <= j; i += NT / 32) {
+    double sr = 0.0, si = 0.0;
+    for (int k = lane; k <= j; k += 32) {
+      double2 gik;
+      if (k == j) gik = gp[i];
+      else if (i == j) gik = cconj(gp[k]);
+      else if (k >= i) gik = Gr[(int64_t)k * (m + 1) + i];
+      else gik = cconj(Gr[(int64_t)i * (m + 1) + k]);
+      const double2 t = cmul(gik, hp[k]);
+      sr += t.x;
+      si += t.y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, off);
+      si += __shfl_xor_sync(0xffffffffu, si, off);
+    }
+    if (lane == 0) hs[i] = make_double2(2.0 * hp[i].x - sr, 2.0 * hp[i].y - si);
+  }
+  __syncthreads();
+  if (rank == 0)
+    for (int i = tid; i <= j; i += NT) Gr[(int64_t)j * (m + 1) + i] = gp[i];
+  // w = A v_j - V h, with ||w||^2
+  double n1[1] = {0.0};
+  for (int e = lo + tid; e < hi; e += NT) {
+    double ar = 0.0, ai = 0.0;
+#pragma unroll 4
+    for (int i = 0; i <= j; ++i) {
+      const double *vi_ = Vr + (int64_t)i * 2 * N;
+      const double2 h = hs[i];
+      const double vr = vi_[e], vi = vi_[N + e];
+      ar += h.x * vr - h.y * vi;
+      ai += h.x * vi + h.y * vr;
+    }
+    const double nr = win[e] - ar, ni = win[N + e] - ai;
+    w[e] = nr;
+    w[N + e] = ni;
+    n1[0] += nr * nr + ni * ni;
+  }
+  cluster_sum<P, 1>(n1, red, clx);   // synchronises: w complete
+  const double hn = sqrt(n1[0]);
 
   if (tid == 0) {
     // every CTA rotates its own copy of the new column (identical inputs)
@@ -439,6 +473,9 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
       G.matvecs[r] += 1;
       if (fin) G.state[r] = kStateResid;
       else G.jcur[r] = j + 1;
+      // algorithmic traffic of this step (vectors of 16 N bytes)
+      const unsigned long long nv = 2ull * (j + 1) + 3ull + (fin ? (unsigned long long)j + 3ull : 0ull);
+      atomicAdd(G.bytes, nv * 16ull * (unsigned long long)N);
     }
   }
   __syncthreads();
@@ -453,6 +490,7 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
     double *x = G.x + (int64_t)2 * r * N;
     for (int e = lo + tid; e < hi; e += NT) {
       double ar = 0.0, ai = 0.0;
+#pragma unroll 4
       for (int i = 0; i < k; ++i) {
         const double *vi_ = Vr + (int64_t)i * 2 * N;
         const double2 y = ys[i];

@@ -71,6 +71,11 @@ struct Timer {
   int launches[kcCount] = {};
   double ms[kcCount] = {};
   double flops[kcCount] = {};
+  double bytes[kcCount] = {};
+  // a device counter of algorithmic bytes (kernels whose traffic depends on
+  // device state), added to class dev_bytes_cls at every resolve
+  unsigned long long *dev_bytes = nullptr;
+  int dev_bytes_cls = -1;
   cudaEvent_t get();
   void begin(cudaStream_t st, int cls, cudaEvent_t *a);
   void end(cudaStream_t st, int cls, cudaEvent_t a, double fl);
@@ -159,6 +164,7 @@ struct TcEpilogue {
   int64_t lo_off = 0;
   int rows_out = 0;                // kDscaleSplit: rows m < rows_out written (zeros past M)
   const double *energy = nullptr;  // [n_orb]
+  const float2 *eocc2 = nullptr;   // [n_occ] occupied energies as float (hi, lo)
   const double *omega = nullptr;   // [S]
   double eps = 0.0;
   double occ_value = 0.0;
@@ -210,6 +216,7 @@ struct LpWork {
   float *gammaT = nullptr;         // [2 S n_occ][n_orb]
   double *omega = nullptr;         // [S]
   int *err = nullptr;              // [1] device-side error code of the GEMM waits
+  float2 *eocc2 = nullptr;         // [n_occ] occupied energies as float (hi, lo)
   TcOperand opK, opXvT, opXv, opZ, opBeta, opA;
   AlphaRoute *ar = nullptr;        // steps 2 and 5 on the stored transition vertex
   int bnK = 128, bn1 = 128, bn2 = 128;   // N tiles chosen by the autotuner
@@ -363,6 +370,7 @@ struct GmresState {
   double *rho0 = nullptr;   // [cap] residual norm at the start of the current cycle
   double inner_tol = 0.0;   // cycle stops once |g| <= inner_tol * rho0 (refinement forms)
   double2 *H = nullptr;     // [cap][(m+1)*m] column-major
+  double2 *Gm = nullptr;    // [cap][(m+1)*(m+1)] basis Gram matrix, column k holds <v_i, v_k>, i <= k
   double *cs = nullptr;     // [cap][m]
   double2 *sn = nullptr;    // [cap][m]
   double2 *g = nullptr;     // [cap][m+1]
@@ -372,6 +380,7 @@ struct GmresState {
   int *act = nullptr;       // [cap] active right-hand sides, in order
   int *act2 = nullptr;      // [cap] second list (right-hand sides awaiting A x) when split
   int *count = nullptr;     // [2]
+  unsigned long long *bytes = nullptr;   // [1] algorithmic bytes of the GMRES steps
 };
 
 cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,

@@ -56,6 +56,14 @@ __global__ void split_rows_kernel(const double *__restrict__ src, int64_t rs, in
   }
 }
 
+__global__ void split_f32_pairs_kernel(const double *__restrict__ src, int n,
+                                       float2 *__restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float hi = (float)src[i];
+    dst[i] = make_float2(hi, (float)(src[i] - (double)hi));
+  }
+}
+
 __global__ void to_f32_kernel(const double *__restrict__ src, int64_t n, float *__restrict__ dst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -184,6 +192,7 @@ cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &
   split_rows_kernel<<<g, 256, 0, st>>>(sys.XvT, sys.n_orb, 1, sys.n_virt, sys.n_orb, lp.Kp1, lp.XvTs);
   split_rows_kernel<<<g, 256, 0, st>>>(sys.Xv, sys.n_virt, 1, sys.n_orb, sys.n_virt, lp.Kp2, lp.Xvs);
   to_f32_kernel<<<g, 256, 0, st>>>(sys.Xo, (int64_t)sys.n_orb * sys.n_occ, lp.Xo32);
+  split_f32_pairs_kernel<<<4, 256, 0, st>>>(sys.energy, sys.n_occ, lp.eocc2);
   to_f32_kernel<<<g, 256, 0, st>>>(sys.Vpad, (int64_t)sys.n_prod * kBlk, lp.Vpad32);
   const size_t rows = (size_t)2 * lp.slots * sys.n_occ;
   cudaMemsetAsync(lp.Zb, 0, (size_t)2 * lp.slots * 2 * lp.KpK * sizeof(__nv_bfloat16), st);
@@ -219,6 +228,7 @@ cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
         ep.lo_off = lp.Kp2;
         ep.rows_out = lp.Kp2;
         ep.energy = sys.energy;
+        ep.eocc2 = lp.eocc2;
         ep.omega = lp.omega;
         ep.eps = 0.01;
         ep.occ_value = sys.occ_value;
@@ -335,6 +345,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     e1.lo_off = lp.Kp2;
     e1.rows_out = lp.Kp2;
     e1.energy = sys.energy;
+    e1.eocc2 = lp.eocc2;
     e1.omega = lp.omega;
     e1.eps = eps;
     e1.occ_value = sys.occ_value;

@@ -135,10 +135,17 @@ void Timer::resolve() {
     pool.push_back(r.b);
   }
   pending.clear();
+  if (dev_bytes && dev_bytes_cls >= 0) {
+    unsigned long long h = 0;
+    if (cudaMemcpy(&h, dev_bytes, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      if (on) bytes[dev_bytes_cls] += (double)h;
+      cudaMemset(dev_bytes, 0, sizeof(h));
+    }
+  }
 }
 void Timer::reset() {
   resolve();
-  for (int i = 0; i < kcCount; ++i) { ms[i] = 0; launches[i] = 0; flops[i] = 0; }
+  for (int i = 0; i < kcCount; ++i) { ms[i] = 0; launches[i] = 0; flops[i] = 0; bytes[i] = 0; }
 }
 void Timer::destroy() {
   for (auto &r : pending) { pool.push_back(r.a); pool.push_back(r.b); }
@@ -396,9 +403,12 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   AL(g.state, S); AL(g.jcur, S); AL(g.cycles, S); AL(g.matvecs, S); AL(g.conv, S);
   AL(g.flags, S);
   AL(g.bnorm, S); AL(g.resid, S); AL(g.omega, S);
-  AL(g.H, S * (m + 1) * m); AL(g.cs, S * m); AL(g.sn, S * m); AL(g.g, S * (m + 1));
+  AL(g.H, S * (m + 1) * m); AL(g.Gm, S * (m + 1) * (m + 1)); AL(g.cs, S * m); AL(g.sn, S * m); AL(g.g, S * (m + 1));
   AL(g.V, S * (m + 1) * 2 * np); AL(g.x, S * 2 * np); AL(g.b, S * 2 * np);
-  AL(g.act, S); AL(g.act2, S); AL(g.count, 2); AL(g.rho0, S);
+  AL(g.act, S); AL(g.act2, S); AL(g.count, 2); AL(g.rho0, S); AL(g.bytes, 1);
+  if (e == cudaSuccess) e = cudaMemset(g.bytes, 0, sizeof(unsigned long long));
+  c->timer.dev_bytes = g.bytes;
+  c->timer.dev_bytes_cls = kcGmresStep;
   g.inner_tol = 0.0;
   c->lowprec = refine;
   c->emu = o->prec == TDDFT_PREC_FP64_EMU || o->prec == TDDFT_PREC_BF16X3_IR_EMU;
@@ -436,6 +446,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     AL(L.gammaT, rows1 * no);
     AL(L.omega, S);
     AL(L.err, 1);
+    AL(L.eocc2, (size_t)nocc);
     if (e == cudaSuccess) e = make_operand_map(L.opK, L.Ks, np, L.KpK, 128);
     if (e == cudaSuccess) e = make_operand_map(L.opXvT, L.XvTs, nv, L.Kp1, 128);
     if (e == cudaSuccess) e = make_operand_map(L.opXv, L.Xvs, no, L.Kp2, 128);
@@ -778,6 +789,14 @@ tddft_status tddft_timing_enable(tddft_ctx *c, int32_t on) {
 }
 
 int32_t tddft_timing_count(const tddft_ctx *) { return kcCount; }
+
+tddft_status tddft_timing_bytes(tddft_ctx *c, int32_t i, double *bytes) {
+  if (!c || !bytes || i < 0 || i >= kcCount) return TDDFT_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->st);
+  c->timer.resolve();
+  *bytes = c->timer.bytes[i];
+  return TDDFT_OK;
+}
 
 tddft_status tddft_timing_get(tddft_ctx *c, int32_t i, const char **name, int32_t *launches,
                               double *total_ms, double *flops) {

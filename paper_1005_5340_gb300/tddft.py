@@ -93,6 +93,7 @@ SIGNATURES = {
     "tddft_timing_count": (ctypes.c_int32, [_P]),
     "tddft_timing_get": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
                                         _P, _P, _P]),
+    "tddft_timing_bytes": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "tddft_selftest_gemm": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "tddft_gemm_f64_emulated": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -328,9 +329,12 @@ class Context:
             n = ctypes.c_int32()
             ms = ctypes.c_double()
             fl = ctypes.c_double()
+            by = ctypes.c_double()
             self._check(self._lib.tddft_timing_get(self.h, i, ctypes.byref(name), ctypes.byref(n),
                                                    ctypes.byref(ms), ctypes.byref(fl)))
-            res[name.value.decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value)
+            self._check(self._lib.tddft_timing_bytes(self.h, i, ctypes.byref(by)))
+            res[name.value.decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value,
+                                            bytes=by.value)
         return res
 
 
