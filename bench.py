@@ -42,8 +42,8 @@ KERNELS_PER_SCOPE = {"rhs_formation": 7, "emu_gemm_K": 2, "emu_gemm_T1": 2, "emu
 # emulated right-hand-side formation: dipole rows, slice + step 2, slice + T1,
 # expand, slice + T2, slice + step 5, combine
 KERNELS_PER_SCOPE_EMU = dict(KERNELS_PER_SCOPE, rhs_formation=11)
-# slice pairs of one emulated float64 product (6 slices: pairs with i + j <= 7)
-EMU_PAIRS = 21
+# slice pairs of one emulated float64 product (s slices: pairs with i + j <= s + 1)
+EMU_PAIRS = {"fp64emu": 21, "bf16x3emu": 15}
 
 
 def measured_peaks():
@@ -219,16 +219,16 @@ FORM_NOTE = {
     "bf16x3": "GMRES cycles with split-bf16 tensor-core products and float32 sparse kernels, "
               "each cycle closed by a float64 residual (iterative refinement); RHS, basis, "
               "Givens in float64",
-    "bf16x3emu": "GMRES cycles with split-bf16 tensor-core products and float32 sparse "
-                 "kernels, each cycle closed by a float64 residual whose dense products are "
-                 "float64 emulated on the tensor cores (6 integer slices, exact sums); RHS "
-                 "formation likewise; basis and Givens in float64",
+    "bf16x3emu": "GMRES cycles with split-bf16 tensor-core products (steps 2 and 5 on the "
+                 "stored transition vertex), each cycle closed by a float64 residual whose "
+                 "products are float64 emulated on the tensor cores (5 integer slices, exact "
+                 "sums); RHS formation likewise; basis, Arnoldi and Givens in float64",
 }
 DTYPE = {"fp64": "f64", "fp64emu": "f64 (emulated on bf16 tensor cores)",
          "bf16x3": "bf16x3+f64", "bf16x3emu": "bf16x3+f64 (emulated on bf16 tensor cores)"}
 
 
-def roofline_of(timing: dict, step_ms: float) -> dict:
+def roofline_of(timing: dict, step_ms: float, prec: str = "bf16x3emu") -> dict:
     """Roofline entry of the kernel class with the largest device time."""
     peaks, src = measured_peaks()
     name, d = max(timing.items(), key=lambda kv: kv[1]["ms"])
@@ -250,10 +250,11 @@ def roofline_of(timing: dict, step_ms: float) -> dict:
         bound, note = "tensor", (f"split bf16: 3 bf16 products per algorithmic product; peak = "
                                  f"{src} sustained bf16 {peaks['bf16_tflops_sustained']} / 3")
     elif name.startswith("emu_gemm") or name.startswith("emu_alpha"):
-        peak = peaks["bf16_tflops_sustained"] / EMU_PAIRS
-        bound, note = "tensor", (f"float64 emulated with {EMU_PAIRS} bf16 slice products per "
+        pairs = EMU_PAIRS.get(prec, 21)
+        peak = peaks["bf16_tflops_sustained"] / pairs
+        bound, note = "tensor", (f"float64 emulated with {pairs} bf16 slice products per "
                                  f"algorithmic product; peak = {src} sustained bf16 "
-                                 f"{peaks['bf16_tflops_sustained']} / {EMU_PAIRS}")
+                                 f"{peaks['bf16_tflops_sustained']} / {pairs}")
     elif name.startswith("f64_"):
         peak, bound = FP64_NOMINAL_TFLOPS, "alu"
         note = "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry among the measured peaks)"
@@ -387,7 +388,7 @@ def run_ours(args):
         return
 
     # roofline of the dominant kernel class
-    roofline = roofline_of(timing, timing_ms)
+    roofline = roofline_of(timing, timing_ms, args.prec)
     if args.graph:
         roofline["timing"] = "kernel split from one instrumented (non-graph) step after the timed region"
     per_scope = KERNELS_PER_SCOPE_EMU if args.prec.endswith("emu") else KERNELS_PER_SCOPE

@@ -62,8 +62,9 @@ typedef enum {
                                each cycle, Arnoldi, Givens and the basis in float64
                                (iterative refinement) */
   TDDFT_PREC_BF16X3_IR_EMU = 3  /* TDDFT_PREC_BF16X3_IR whose float64 right-hand sides and
-                                   cycle-end residuals use the emulated float64 products of
-                                   TDDFT_PREC_FP64_EMU */
+                                   cycle-end residuals use emulated float64 products as in
+                                   TDDFT_PREC_FP64_EMU, with 5 slices (error about 2^-35
+                                   |A|_row |B|_col K, far below the residual tolerance) */
 } tddft_precision;
 
 /*

@@ -21,6 +21,7 @@ namespace tddft {
 namespace {
 
 constexpr int NT = 256;
+constexpr int kHsmemMaxM = 48;   // restart lengths whose Hessenberg matrix is staged in shared memory
 constexpr int kStateArnoldi = 0, kStateResid = 1, kStateDone = 2;
 
 __device__ inline double2 cmul(double2 a, double2 b) {
@@ -224,13 +225,16 @@ __device__ void cluster_sum(double (&v)[NV], double *red, double *clx) {
 // CTA takes the same decisions from the same totals; rank 0 writes the
 // per-right-hand-side scalars.
 template <int P>
-__global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restrict__ list,
+__global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__restrict__ list,
                                                         const double *__restrict__ Wout,
-                                                        const int *__restrict__ dcnt) {
+                                                        const int *__restrict__ dcnt,
+                                                        int h_smem) {
   __shared__ double red[16 * (NT / 32)];
   __shared__ double clx[16];
   __shared__ double2 hs[257], hp[257], ys[257], hq[257], gq[257], gp[257];
   __shared__ int finish_flag;
+  __shared__ double2 s_gj;
+  extern __shared__ double2 hdyn[];   // the Hessenberg columns when h_smem
   const int s = blockIdx.y;
   if (dcnt && s >= *dcnt) return;          // the same for the whole cluster
   const int rank = (P > 1) ? (int)cg::this_cluster().block_rank() : 0;
@@ -411,16 +415,27 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
   cluster_sum<P, 1>(n1, red, clx);   // synchronises: w complete
   const double hn = sqrt(n1[0]);
 
+  // the earlier rotations to shared memory (all threads), then thread 0
+  // applies them to the new column in order
+  {
+    const double *csg = G.cs + (int64_t)r * m;
+    const double2 *sng = G.sn + (int64_t)r * m;
+    for (int i = tid; i < j; i += NT) {
+      gq[i] = make_double2(csg[i], 0.0);
+      hq[i] = sng[i];
+    }
+  }
+  __syncthreads();
   if (tid == 0) {
     // every CTA rotates its own copy of the new column (identical inputs)
-    const double *cs = G.cs + (int64_t)r * m;
-    const double2 *sn = G.sn + (int64_t)r * m;
     for (int i = 0; i < j; ++i) {
+      const double csi = gq[i].x;
+      const double2 sni = hq[i];
       const double2 a = hs[i], bb = hs[i + 1];
-      const double2 t = make_double2(cs[i] * a.x + (sn[i].x * bb.x - sn[i].y * bb.y),
-                                     cs[i] * a.y + (sn[i].x * bb.y + sn[i].y * bb.x));
-      const double2 cb = cmul(cconj(sn[i]), a);
-      hs[i + 1] = make_double2(-cb.x + cs[i] * bb.x, -cb.y + cs[i] * bb.y);
+      const double2 t = make_double2(csi * a.x + (sni.x * bb.x - sni.y * bb.y),
+                                     csi * a.y + (sni.x * bb.y + sni.y * bb.x));
+      const double2 cb = cmul(cconj(sni), a);
+      hs[i + 1] = make_double2(-cb.x + csi * bb.x, -cb.y + csi * bb.y);
       hs[i] = t;
     }
     // new rotation mapping (hs[j], hn) to (rho, 0)
@@ -445,24 +460,7 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
     const bool fin = (est <= G.tol * G.bnorm[r]) || (j + 1 == m) || !(hn > 0.0) ||
                      (est <= G.inner_tol * rho0);
     finish_flag = fin ? 1 : 0;
-    if (fin) {
-      // back substitution with the rotated (upper triangular) Hessenberg
-      // matrix: columns < j from memory, column j and g[j] from this step
-      const int k = j + 1;
-      const double2 *Hr = G.H + (int64_t)r * (m + 1) * m;
-      const double2 *gg = G.g + (int64_t)r * (m + 1);
-      for (int i = k - 1; i >= 0; --i) {
-        double2 acc = (i == j) ? gj : gg[i];
-        for (int l = i + 1; l < k; ++l) {
-          const double2 hil = (l == j) ? hs[i] : Hr[(int64_t)l * (m + 1) + i];
-          const double2 p = cmul(hil, ys[l]);
-          acc.x -= p.x;
-          acc.y -= p.y;
-        }
-        const double2 hii = (i == j) ? hs[j] : Hr[(int64_t)i * (m + 1) + i];
-        ys[i] = cdiv(acc, hii);
-      }
-    }
+    s_gj = gj;
     if (rank == 0) {
       double2 *Hc = G.H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);
       for (int i = 0; i <= j; ++i) Hc[i] = hs[i];
@@ -479,6 +477,47 @@ __global__ void __launch_bounds__(NT) gmres_step_kernel(Gs G, const int *__restr
     }
   }
   __syncthreads();
+  if (finish_flag) {
+    // back substitution R y = g with the rotated (upper triangular)
+    // Hessenberg matrix: its earlier columns (shared memory when they fit)
+    // and g_0..g_{j-1} staged by all threads, column j and g_j from this
+    // step; warp 0 solves, lanes over the columns l > i
+    const int k = j + 1;
+    const double2 *Hr = G.H + (int64_t)r * (m + 1) * m;
+    const double2 *gg = G.g + (int64_t)r * (m + 1);
+    if (h_smem) {
+      for (int idx = tid; idx < j * (m + 1); idx += NT) {
+        const int l = idx / (m + 1), i = idx - l * (m + 1);
+        if (i <= l) hdyn[idx] = Hr[idx];
+      }
+    }
+    for (int i = tid; i < j; i += NT) hp[i] = gg[i];
+    __syncthreads();
+    const double2 *Hs = h_smem ? hdyn : Hr;
+    if (warp == 0) {
+      for (int i = k - 1; i >= 0; --i) {
+        double sr = 0.0, si = 0.0;
+        for (int l = i + 1 + lane; l < k; l += 32) {
+          const double2 hil = (l == j) ? hs[i] : Hs[(int64_t)l * (m + 1) + i];
+          const double2 p = cmul(hil, ys[l]);
+          sr += p.x;
+          si += p.y;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, off);
+          si += __shfl_xor_sync(0xffffffffu, si, off);
+        }
+        if (lane == 0) {
+          const double2 gi = (i == j) ? s_gj : hp[i];
+          const double2 hii = (i == j) ? hs[j] : Hs[(int64_t)i * (m + 1) + i];
+          ys[i] = cdiv(make_double2(gi.x - sr, gi.y - si), hii);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
   if (!finish_flag) {
     const double inv = 1.0 / hn;
     for (int e = lo + tid; e < hi; e += NT) {
@@ -611,14 +650,27 @@ cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState 
   // work of the orthogonalisation is spread over more SMs than there are
   // live right-hand sides.
   const int P = sys.n_prod >= 8192 ? 8 : (sys.n_prod >= 4096 ? 4 : (sys.n_prod >= 2048 ? 2 : 1));
+  // the Hessenberg columns go to shared memory for the back substitution
+  // when the restart length allows (m (m+1) complex values)
+  const int h_smem = gs.m <= kHsmemMaxM ? 1 : 0;
+  const size_t dyn = h_smem ? (size_t)gs.m * (gs.m + 1) * sizeof(double2) : 0;
+  static bool attr_set = false;
+  if (!attr_set) {
+    const int mx = (int)((size_t)kHsmemMaxM * (kHsmemMaxM + 1) * sizeof(double2));
+    cudaFuncSetAttribute(gmres_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    attr_set = true;
+  }
   if (P == 1) {
-    gmres_step_kernel<1><<<dim3(1, S), NT, 0, st>>>(G, list, Wout, dcnt);
+    gmres_step_kernel<1><<<dim3(1, S), NT, dyn, st>>>(G, list, Wout, dcnt, h_smem);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(P, S);
   cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = dyn;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -627,9 +679,9 @@ cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (P == 8) return cudaLaunchKernelEx(&cfg, gmres_step_kernel<8>, G, list, Wout, dcnt);
-  return P == 4 ? cudaLaunchKernelEx(&cfg, gmres_step_kernel<4>, G, list, Wout, dcnt)
-                : cudaLaunchKernelEx(&cfg, gmres_step_kernel<2>, G, list, Wout, dcnt);
+  if (P == 8) return cudaLaunchKernelEx(&cfg, gmres_step_kernel<8>, G, list, Wout, dcnt, h_smem);
+  return P == 4 ? cudaLaunchKernelEx(&cfg, gmres_step_kernel<4>, G, list, Wout, dcnt, h_smem)
+                : cudaLaunchKernelEx(&cfg, gmres_step_kernel<2>, G, list, Wout, dcnt, h_smem);
 }
 
 cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0,

@@ -412,6 +412,9 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   g.inner_tol = 0.0;
   c->lowprec = refine;
   c->emu = o->prec == TDDFT_PREC_FP64_EMU || o->prec == TDDFT_PREC_BF16X3_IR_EMU;
+  // the refinement form's float64 products only resolve residuals far below
+  // its tolerance: 5 slices (2^-35 of the operand scales); 6 otherwise
+  c->oz.s = o->prec == TDDFT_PREC_BF16X3_IR_EMU ? 5 : kOzDefaultSlices;
   if (e == cudaSuccess && c->emu) {
     e = oz_setup(c->st, d, c->oz, (int)S, c->dev_allocs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
@@ -702,7 +705,7 @@ static tddft_status polarizability_impl(tddft_ctx *c, int32_t n_omega, const dou
     // Float64 residuals that end a refinement cycle are batched: while reduced-
     // precision Arnoldi work remains, right-hand sides awaiting their residual
     // wait until enough of them have gathered to fill the float64 GEMM tiles.
-    const int min_b = split ? std::max(1, std::min(32, n / 4)) : 1;
+    const int min_b = split ? std::max(1, std::min(64, n / 3)) : 1;
     if (c->opts.graph && !c->timer.on) {
       tddft_status gs_ = run_group_graph(c, n, eps, split, min_b, max_iter);
       if (gs_ != TDDFT_OK) return gs_;
