@@ -63,8 +63,10 @@ typedef enum {
                                (iterative refinement) */
   TDDFT_PREC_BF16X3_IR_EMU = 3  /* TDDFT_PREC_BF16X3_IR whose float64 right-hand sides and
                                    cycle-end residuals use emulated float64 products as in
-                                   TDDFT_PREC_FP64_EMU, with 5 slices (error about 2^-35
-                                   |A|_row |B|_col K, far below the residual tolerance) */
+                                   TDDFT_PREC_FP64_EMU, with the slice count chosen from tol
+                                   so that their error stays well below it: 5 slices (about
+                                   2^-35 |A|_row |B|_col K) for tol >= 1e-8, 6 for tol >=
+                                   1e-12, 7 below */
 } tddft_precision;
 
 /*
@@ -257,11 +259,13 @@ tddft_status tddft_timing_get(tddft_ctx *ctx, int32_t i, const char **name, int3
 /*
  * Algorithmic bytes moved by the timed launches of class i, where counted
  * (0 otherwise).  The GMRES step counts on the device, per right-hand side
- * and step, the float64 vectors (16 n_prod bytes each) it must read or write
- * at least: 2 (j + 1) + 3 for Arnoldi step j (the basis v_0..v_j read for the
- * inner products and again for the update, A v_j read, v_{j+1} written and
- * normalised in place), j + 3 more when the cycle ends (x += V y), and 3 for
- * a residual check (b, A x read, v_0 written).  Synchronises the stream.
+ * and step, the vectors it must read or write at least, a basis vector being
+ * 2 n_prod elements of the basis type (float64, or float32 in the refinement
+ * forms) and a float64 vector 16 n_prod bytes: for Arnoldi step j, 2 (j + 1)
+ * + 3 basis vectors (v_0..v_j read for the inner products and again for the
+ * update, v_{j+1} written and normalised) and A v_j; at a cycle end, j + 1
+ * more basis vectors and x read and written; for a residual check, b and A x
+ * read and v_0 written and normalised.  Synchronises the stream.
  */
 tddft_status tddft_timing_bytes(tddft_ctx *ctx, int32_t i, double *bytes);
 

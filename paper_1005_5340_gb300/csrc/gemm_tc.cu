@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
           const int pair0 = (n0 + j0) >> 1;
           const int sl0 = pair0 / ep.n_occ, E0 = pair0 - sl0 * ep.n_occ;
           // (omega -+ e_F) of the chunk's slot, once (the usual case: all 8
-          // pairs in one slot); otherwise per pair
+          // pairs in one slot); otherwise per pair, with identical arithmetic
+          // so that no result depends on a right-hand side's slot
           float am_hi = 0.f, am_lo = 0.f, ap_hi = 0.f, ap_lo = 0.f;
           const bool one_slot = E0 + 8 <= ep.n_occ;
           double eF = 0.0;
@@ -271,12 +272,16 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
                 xm = (am_hi + eE.x) + (am_lo + eE.y);
                 xp = (ap_hi - eE.x) + (ap_lo - eE.y);
               } else {
+                // the same arithmetic with this pair's slot (chunks that cross a slot)
                 const int pair = n >> 1;
                 const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
-                const double delta = eF - ep.energy[E];
                 const double w = ep.omega[sl];
-                xm = (float)(w - delta);
-                xp = (float)(w + delta);
+                const double am = w - eF, ap = w + eF;
+                const float bm_hi = (float)am, bm_lo = (float)(am - (double)bm_hi);
+                const float bp_hi = (float)ap, bp_lo = (float)(ap - (double)bp_hi);
+                const float2 eE = ep.eocc2[E];
+                xm = (bm_hi + eE.x) + (bm_lo + eE.y);
+                xp = (bp_hi - eE.x) + (bp_lo - eE.y);
               }
               const float im2 = __frcp_rn(fmaf(xm, xm, e2)), ip2 = __frcp_rn(fmaf(xp, xp, e2));
               const float dre = occ * (xm * im2 - xp * ip2);

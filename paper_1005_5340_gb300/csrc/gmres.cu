@@ -74,6 +74,7 @@ struct Gs {
   double *bnorm, *resid, *omega;
   double2 *H, *sn, *g;
   double *cs, *V, *x, *b;
+  float *Vf;   // the basis in float32 (refinement forms), else NULL
   const int *act;
   unsigned long long *bytes;
   double2 *Gm;
@@ -87,12 +88,18 @@ Gs view(const GmresState &s, int n_prod) {
   v.flags = s.flags;
   v.bnorm = s.bnorm; v.resid = s.resid; v.omega = s.omega;
   v.H = s.H; v.sn = s.sn; v.g = s.g; v.cs = s.cs; v.V = s.V; v.x = s.x; v.b = s.b; v.act = s.act;
+  v.Vf = s.Vf;
   v.bytes = s.bytes;
   v.Gm = s.Gm;
   return v;
 }
 
+template <class T> __device__ __forceinline__ T *basis(const Gs &G);
+template <> __device__ __forceinline__ double *basis<double>(const Gs &G) { return G.V; }
+template <> __device__ __forceinline__ float *basis<float>(const Gs &G) { return G.Vf; }
+
 // Start: store b, x = 0, v_0 = b / ||b||.
+template <class T>
 __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__restrict__ Bp) {
   __shared__ double red[NT / 32];
   const int r = blockIdx.x;
@@ -100,7 +107,7 @@ __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__r
   const double *bin = Bp + (int64_t)2 * r * N;
   double *b = G.b + (int64_t)2 * r * N;
   double *x = G.x + (int64_t)2 * r * N;
-  double *v0 = G.V + (int64_t)r * (G.m + 1) * 2 * N;
+  T *v0 = basis<T>(G) + (int64_t)r * (G.m + 1) * 2 * N;
   double s[1] = {0.0};
   for (int e = threadIdx.x; e < 2 * N; e += NT) {
     double t = bin[e];
@@ -112,7 +119,7 @@ __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__r
   const double nrm = sqrt(s[0]);
   if (nrm > 0.0) {
     const double inv = 1.0 / nrm;
-    for (int e = threadIdx.x; e < 2 * N; e += NT) v0[e] = bin[e] * inv;
+    for (int e = threadIdx.x; e < 2 * N; e += NT) v0[e] = (T)(bin[e] * inv);
   }
   if (threadIdx.x == 0) {
     G.bnorm[r] = nrm;
@@ -181,6 +188,7 @@ __global__ void __launch_bounds__(1024) gmres_select_kernel(const int *__restric
 }
 
 // Operator input of each active right-hand side: v_j (Arnoldi) or x (residual).
+template <class T>
 __global__ void __launch_bounds__(NT) gmres_gather_kernel(Gs G, const int *__restrict__ list,
                                                           double *__restrict__ Zc,
                                                           double *__restrict__ slot_omega,
@@ -189,11 +197,14 @@ __global__ void __launch_bounds__(NT) gmres_gather_kernel(Gs G, const int *__res
   if (dcnt && s >= *dcnt) return;
   const int r = list[s];
   const int N = G.n_prod;
-  const double *src = (G.state[r] == kStateArnoldi)
-                          ? G.V + ((int64_t)r * (G.m + 1) + G.jcur[r]) * 2 * N
-                          : G.x + (int64_t)2 * r * N;
   double *dst = Zc + (int64_t)2 * s * N;
-  for (int e = threadIdx.x; e < 2 * N; e += NT) dst[e] = src[e];
+  if (G.state[r] == kStateArnoldi) {
+    const T *src = basis<T>(G) + ((int64_t)r * (G.m + 1) + G.jcur[r]) * 2 * N;
+    for (int e = threadIdx.x; e < 2 * N; e += NT) dst[e] = (double)src[e];
+  } else {
+    const double *src = G.x + (int64_t)2 * r * N;
+    for (int e = threadIdx.x; e < 2 * N; e += NT) dst[e] = src[e];
+  }
   if (threadIdx.x == 0) slot_omega[s] = G.omega[r];
 }
 
@@ -224,7 +235,7 @@ __device__ void cluster_sum(double (&v)[NV], double *red, double *clx) {
 // are reduced across the cluster through distributed shared memory.  Every
 // CTA takes the same decisions from the same totals; rank 0 writes the
 // per-right-hand-side scalars.
-template <int P>
+template <int P, class T>
 __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__restrict__ list,
                                                         const double *__restrict__ Wout,
                                                         const int *__restrict__ dcnt,
@@ -232,6 +243,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   __shared__ double red[16 * (NT / 32)];
   __shared__ double clx[16];
   __shared__ double2 hs[257], hp[257], ys[257], hq[257], gq[257], gp[257];
+  __shared__ float2 hT[257];   // coefficients in float32 for the float32 basis
   __shared__ int finish_flag;
   __shared__ double2 s_gj;
   extern __shared__ double2 hdyn[];   // the Hessenberg columns when h_smem
@@ -245,7 +257,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   const int chunk = (N + P - 1) / P;
   const int lo = rank * chunk, hi = min(N, lo + chunk);
   const double *win = Wout + (int64_t)2 * s * N;
-  double *Vr = G.V + (int64_t)r * (m + 1) * 2 * N;
+  T *Vr = basis<T>(G) + (int64_t)r * (m + 1) * 2 * N;
   const int state = G.state[r];
   const int cyc = G.cycles[r];
 
@@ -255,8 +267,8 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     double s2[1] = {0.0};
     for (int e = lo + tid; e < hi; e += NT) {
       const double tr = b[e] - win[e], ti = b[N + e] - win[N + e];
-      Vr[e] = tr;
-      Vr[N + e] = ti;
+      Vr[e] = (T)tr;
+      Vr[N + e] = (T)ti;
       s2[0] += tr * tr + ti * ti;
     }
     cluster_sum<P, 1>(s2, red, clx);
@@ -267,8 +279,8 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
       // judge, so a guess worse than zero is dropped
       double *x = G.x + (int64_t)2 * r * N;
       for (int e = lo + tid; e < hi; e += NT) {
-        Vr[e] = b[e];
-        Vr[N + e] = b[N + e];
+        Vr[e] = (T)b[e];
+        Vr[N + e] = (T)b[N + e];
         x[e] = 0.0;
         x[N + e] = 0.0;
       }
@@ -283,12 +295,13 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     if (next == 2) {
       const double inv = 1.0 / rho;
       for (int e = lo + tid; e < hi; e += NT) {
-        Vr[e] *= inv;
-        Vr[N + e] *= inv;
+        Vr[e] *= (T)inv;
+        Vr[N + e] *= (T)inv;
       }
     }
     if (tid == 0 && rank == 0) {
-      atomicAdd(G.bytes, 3ull * 16ull * (unsigned long long)N);
+      // algorithmic traffic: b and A x read, v_0 written and normalised
+      atomicAdd(G.bytes, (2ull * 16ull + 3ull * 2ull * sizeof(T)) * (unsigned long long)N);
       G.matvecs[r] += 1;
       G.resid[r] = rel;
       if (rejected) G.flags[r] |= 1;
@@ -309,8 +322,8 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   const int j = G.jcur[r];
   const double2 gj0 = G.g[(int64_t)r * (m + 1) + j];
   const double rho0 = G.rho0[r];
-  double *w = Vr + (int64_t)(j + 1) * 2 * N;
-  const double *vj = Vr + (int64_t)j * 2 * N;
+  T *w = Vr + (int64_t)(j + 1) * 2 * N;
+  const T *vj = Vr + (int64_t)j * 2 * N;
   const int warp = tid >> 5, lane = tid & 31;
 
   // Classical Gram-Schmidt with the reorthogonalisation folded in through the
@@ -320,29 +333,45 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   // h = 2 h1 - G h1 and w = A v_j - V h (one update pass).  Warp q streams
   // v_q, v_{q+8}, ... over this CTA's elements; the partial dots of all i
   // are reduced across the cluster at once, in rank order.
+  // Arithmetic of the streaming passes in the basis type T: float32 in the
+  // refinement forms (float64 would make these passes FP64-pipe bound; the
+  // per-lane sums are short and every reduction across lanes, CTAs and the
+  // Gram and Hessenberg algebra stay float64), float64 otherwise.
+  const T *aw;   // A v_j in type T
+  if constexpr (sizeof(T) == 4) {
+    for (int e = lo + tid; e < hi; e += NT) {
+      w[e] = (T)win[e];
+      w[N + e] = (T)win[N + e];
+    }
+    __syncthreads();
+    aw = w;
+  } else {
+    aw = win;
+  }
   for (int i = warp; i <= j; i += NT / 32) {
-    const double *vi_ = Vr + (int64_t)i * 2 * N;
-    double pr = 0.0, pim = 0.0, gr = 0.0, gim = 0.0;
+    const T *vi_ = Vr + (int64_t)i * 2 * N;
+    T pr = 0, pim = 0, gr = 0, gim = 0;
 #pragma unroll 4
     for (int e = lo + lane; e < hi; e += 32) {
-      const double wr = win[e], wi = win[N + e];
-      const double ar = vj[e], ai = vj[N + e];
-      const double vr = vi_[e], vi = vi_[N + e];
+      const T wr = aw[e], wi = aw[N + e];
+      const T ar = vj[e], ai = vj[N + e];
+      const T vr = vi_[e], vi = vi_[N + e];
       pr = fma(vr, wr, fma(vi, wi, pr));
       pim = fma(vr, wi, fma(-vi, wr, pim));
       gr = fma(vr, ar, fma(vi, ai, gr));
       gim = fma(vr, ai, fma(-vi, ar, gim));
     }
+    double dpr = pr, dpim = pim, dgr = gr, dgim = gim;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      pr += __shfl_xor_sync(0xffffffffu, pr, off);
-      pim += __shfl_xor_sync(0xffffffffu, pim, off);
-      gr += __shfl_xor_sync(0xffffffffu, gr, off);
-      gim += __shfl_xor_sync(0xffffffffu, gim, off);
+      dpr += __shfl_xor_sync(0xffffffffu, dpr, off);
+      dpim += __shfl_xor_sync(0xffffffffu, dpim, off);
+      dgr += __shfl_xor_sync(0xffffffffu, dgr, off);
+      dgim += __shfl_xor_sync(0xffffffffu, dgim, off);
     }
     if (lane == 0) {
-      hq[i] = make_double2(pr, pim);
-      gq[i] = make_double2(gr, gim);
+      hq[i] = make_double2(dpr, dpim);
+      gq[i] = make_double2(dgr, dgim);
     }
   }
   if (P == 1) {
@@ -395,22 +424,35 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   __syncthreads();
   if (rank == 0)
     for (int i = tid; i <= j; i += NT) Gr[(int64_t)j * (m + 1) + i] = gp[i];
-  // w = A v_j - V h, with ||w||^2
+  // w = A v_j - V h, with ||w||^2 (coefficients in type T)
+  for (int i = tid; i <= j; i += NT) hT[i] = make_float2((float)hs[i].x, (float)hs[i].y);
+  __syncthreads();
   double n1[1] = {0.0};
-  for (int e = lo + tid; e < hi; e += NT) {
-    double ar = 0.0, ai = 0.0;
+  {
+    T nacc = 0;
+    for (int e = lo + tid; e < hi; e += NT) {
+      T ar = 0, ai = 0;
 #pragma unroll 4
-    for (int i = 0; i <= j; ++i) {
-      const double *vi_ = Vr + (int64_t)i * 2 * N;
-      const double2 h = hs[i];
-      const double vr = vi_[e], vi = vi_[N + e];
-      ar += h.x * vr - h.y * vi;
-      ai += h.x * vi + h.y * vr;
+      for (int i = 0; i <= j; ++i) {
+        const T *vi_ = Vr + (int64_t)i * 2 * N;
+        T hx, hy;
+        if constexpr (sizeof(T) == 4) {
+          hx = hT[i].x;
+          hy = hT[i].y;
+        } else {
+          hx = hs[i].x;
+          hy = hs[i].y;
+        }
+        const T vr = vi_[e], vi = vi_[N + e];
+        ar += hx * vr - hy * vi;
+        ai += hx * vi + hy * vr;
+      }
+      const T nr = aw[e] - ar, ni = aw[N + e] - ai;
+      w[e] = nr;
+      w[N + e] = ni;
+      nacc += nr * nr + ni * ni;
     }
-    const double nr = win[e] - ar, ni = win[N + e] - ai;
-    w[e] = nr;
-    w[N + e] = ni;
-    n1[0] += nr * nr + ni * ni;
+    n1[0] = (double)nacc;
   }
   cluster_sum<P, 1>(n1, red, clx);   // synchronises: w complete
   const double hn = sqrt(n1[0]);
@@ -471,9 +513,12 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
       G.matvecs[r] += 1;
       if (fin) G.state[r] = kStateResid;
       else G.jcur[r] = j + 1;
-      // algorithmic traffic of this step (vectors of 16 N bytes)
-      const unsigned long long nv = 2ull * (j + 1) + 3ull + (fin ? (unsigned long long)j + 3ull : 0ull);
-      atomicAdd(G.bytes, nv * 16ull * (unsigned long long)N);
+      // algorithmic traffic of this step: basis vectors (2 N sizeof(T) bytes)
+      // v_0..v_j read twice, v_{j+1} written and normalised, A v_j read
+      // (16 N); at a cycle end v_0..v_j read again and x read and written
+      const unsigned long long nb = 2ull * (j + 1) + 3ull + (fin ? (unsigned long long)j + 1ull : 0ull);
+      const unsigned long long nd = 1ull + (fin ? 2ull : 0ull);
+      atomicAdd(G.bytes, (nb * 2ull * sizeof(T) + nd * 16ull) * (unsigned long long)N);
     }
   }
   __syncthreads();
@@ -519,7 +564,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     __syncthreads();
   }
   if (!finish_flag) {
-    const double inv = 1.0 / hn;
+    const T inv = (T)(1.0 / hn);
     for (int e = lo + tid; e < hi; e += NT) {
       w[e] *= inv;
       w[N + e] *= inv;
@@ -527,18 +572,27 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   } else {
     const int k = j + 1;
     double *x = G.x + (int64_t)2 * r * N;
+    for (int i = tid; i < k; i += NT) hT[i] = make_float2((float)ys[i].x, (float)ys[i].y);
+    __syncthreads();
     for (int e = lo + tid; e < hi; e += NT) {
-      double ar = 0.0, ai = 0.0;
+      T ar = 0, ai = 0;
 #pragma unroll 4
       for (int i = 0; i < k; ++i) {
-        const double *vi_ = Vr + (int64_t)i * 2 * N;
-        const double2 y = ys[i];
-        const double vr = vi_[e], vi = vi_[N + e];
-        ar += y.x * vr - y.y * vi;
-        ai += y.x * vi + y.y * vr;
+        const T *vi_ = Vr + (int64_t)i * 2 * N;
+        T yx, yy;
+        if constexpr (sizeof(T) == 4) {
+          yx = hT[i].x;
+          yy = hT[i].y;
+        } else {
+          yx = ys[i].x;
+          yy = ys[i].y;
+        }
+        const T vr = vi_[e], vi = vi_[N + e];
+        ar += yx * vr - yy * vi;
+        ai += yx * vi + yy * vr;
       }
-      x[e] += ar;
-      x[N + e] += ai;
+      x[e] += (double)ar;
+      x[N + e] += (double)ai;
     }
   }
 }
@@ -619,52 +673,20 @@ __global__ void __launch_bounds__(NT) polarization_kernel(int g0, int n_prod,
   }
 }
 
-}  // namespace
-
-cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
-                               const double *Bplanar) {
-  if (n <= 0) return cudaSuccess;
-  gmres_start_kernel<<<n, NT, 0, st>>>(view(gs, sys.n_prod), Bplanar);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split, int min_b) {
-  gmres_select_kernel<<<1, 1024, 0, st>>>(gs.state, n, split, min_b, gs.act, gs.act2, gs.count);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs,
-                                const int *list, int S, double *Zc, double *slot_omega,
-                                const int *dcnt) {
-  if (S <= 0) return cudaSuccess;
-  gmres_gather_kernel<<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Zc, slot_omega, dcnt);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs,
-                              const int *list, int S, const double *Wout, const int *dcnt) {
-  if (S <= 0) return cudaSuccess;
-  if (S > 65535) return cudaErrorInvalidConfiguration;
-  const Gs G = view(gs, sys.n_prod);
-  // Long vectors: a cluster of CTAs per right-hand side, so that the FP64
-  // work of the orthogonalisation is spread over more SMs than there are
-  // live right-hand sides.
-  const int P = sys.n_prod >= 8192 ? 8 : (sys.n_prod >= 4096 ? 4 : (sys.n_prod >= 2048 ? 2 : 1));
-  // the Hessenberg columns go to shared memory for the back substitution
-  // when the restart length allows (m (m+1) complex values)
-  const int h_smem = gs.m <= kHsmemMaxM ? 1 : 0;
-  const size_t dyn = h_smem ? (size_t)gs.m * (gs.m + 1) * sizeof(double2) : 0;
+template <class T>
+cudaError_t launch_step_t(cudaStream_t st, const Gs &G, int P, int S, const int *list,
+                          const double *Wout, const int *dcnt, int h_smem, size_t dyn) {
   static bool attr_set = false;
   if (!attr_set) {
     const int mx = (int)((size_t)kHsmemMaxM * (kHsmemMaxM + 1) * sizeof(double2));
-    cudaFuncSetAttribute(gmres_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(gmres_step_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(gmres_step_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(gmres_step_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<8, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     attr_set = true;
   }
   if (P == 1) {
-    gmres_step_kernel<1><<<dim3(1, S), NT, dyn, st>>>(G, list, Wout, dcnt, h_smem);
+    gmres_step_kernel<1, T><<<dim3(1, S), NT, dyn, st>>>(G, list, Wout, dcnt, h_smem);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -679,9 +701,57 @@ cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (P == 8) return cudaLaunchKernelEx(&cfg, gmres_step_kernel<8>, G, list, Wout, dcnt, h_smem);
-  return P == 4 ? cudaLaunchKernelEx(&cfg, gmres_step_kernel<4>, G, list, Wout, dcnt, h_smem)
-                : cudaLaunchKernelEx(&cfg, gmres_step_kernel<2>, G, list, Wout, dcnt, h_smem);
+  if (P == 8) return cudaLaunchKernelEx(&cfg, gmres_step_kernel<8, T>, G, list, Wout, dcnt, h_smem);
+  return P == 4 ? cudaLaunchKernelEx(&cfg, gmres_step_kernel<4, T>, G, list, Wout, dcnt, h_smem)
+                : cudaLaunchKernelEx(&cfg, gmres_step_kernel<2, T>, G, list, Wout, dcnt, h_smem);
+}
+
+}  // namespace
+
+cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
+                               const double *Bplanar) {
+  if (n <= 0) return cudaSuccess;
+  if (!gs.V && !gs.Vf) return cudaErrorInvalidValue;
+  if (gs.Vf)
+    gmres_start_kernel<float><<<n, NT, 0, st>>>(view(gs, sys.n_prod), Bplanar);
+  else
+    gmres_start_kernel<double><<<n, NT, 0, st>>>(view(gs, sys.n_prod), Bplanar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split, int min_b) {
+  gmres_select_kernel<<<1, 1024, 0, st>>>(gs.state, n, split, min_b, gs.act, gs.act2, gs.count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs,
+                                const int *list, int S, double *Zc, double *slot_omega,
+                                const int *dcnt) {
+  if (S <= 0) return cudaSuccess;
+  if (!gs.V && !gs.Vf) return cudaErrorInvalidValue;
+  if (gs.Vf)
+    gmres_gather_kernel<float><<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Zc, slot_omega, dcnt);
+  else
+    gmres_gather_kernel<double><<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Zc, slot_omega, dcnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState &gs,
+                              const int *list, int S, const double *Wout, const int *dcnt) {
+  if (S <= 0) return cudaSuccess;
+  if (S > 65535) return cudaErrorInvalidConfiguration;
+  if (!gs.V && !gs.Vf) return cudaErrorInvalidValue;
+  const Gs G = view(gs, sys.n_prod);
+  // Long vectors: a cluster of CTAs per right-hand side, so that the FP64
+  // work of the orthogonalisation is spread over more SMs than there are
+  // live right-hand sides.
+  const int P = sys.n_prod >= 8192 ? 8 : (sys.n_prod >= 4096 ? 4 : (sys.n_prod >= 2048 ? 2 : 1));
+  // the Hessenberg columns go to shared memory for the back substitution
+  // when the restart length allows (m (m+1) complex values)
+  const int h_smem = gs.m <= kHsmemMaxM ? 1 : 0;
+  const size_t dyn = h_smem ? (size_t)gs.m * (gs.m + 1) * sizeof(double2) : 0;
+  return gs.Vf ? launch_step_t<float>(st, G, P, S, list, Wout, dcnt, h_smem, dyn)
+               : launch_step_t<double>(st, G, P, S, list, Wout, dcnt, h_smem, dyn);
 }
 
 cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0,

@@ -375,6 +375,7 @@ struct GmresState {
   double2 *sn = nullptr;    // [cap][m]
   double2 *g = nullptr;     // [cap][m+1]
   double *V = nullptr;      // [cap][m+1][2][n_prod]
+  float *Vf = nullptr;      // the same basis in float32 (refinement forms; then V is NULL)
   double *x = nullptr;      // [cap][2][n_prod]
   double *b = nullptr;      // [cap][2][n_prod]
   int *act = nullptr;       // [cap] active right-hand sides, in order

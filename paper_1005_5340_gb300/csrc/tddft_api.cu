@@ -357,7 +357,10 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   std::vector<double> dip(s->dipole, s->dipole + 3 * (size_t)np);
 
   cudaError_t e = cudaSuccess;
-#define UP(ptr, vec) if (e == cudaSuccess) e = upload(c, &(ptr), vec)
+#define UP(ptr, vec)                             \
+  do {                                           \
+    if (e == cudaSuccess) e = upload(c, &(ptr), vec); \
+  } while (0)
   UP(d.aoff, aoffv);
   UP(d.energy, energy);
   UP(d.Xo, Xo);
@@ -381,7 +384,10 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   OpWork &w = c->wk;
   w.slots = (int)S;
   w.timer = &c->timer;
-#define AL(ptr, n) if (e == cudaSuccess) e = dev_alloc(c, &(ptr), (n))
+#define AL(ptr, n)                                   \
+  do {                                               \
+    if (e == cudaSuccess) e = dev_alloc(c, &(ptr), (n)); \
+  } while (0)
   AL(w.Y, 2 * S * np);
   AL(w.W, 2 * S3 * (size_t)d.n_blocks * kBlk);
   AL(w.beta, (size_t)no * 2 * S3 * nocc);
@@ -404,7 +410,14 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   AL(g.flags, S);
   AL(g.bnorm, S); AL(g.resid, S); AL(g.omega, S);
   AL(g.H, S * (m + 1) * m); AL(g.Gm, S * (m + 1) * (m + 1)); AL(g.cs, S * m); AL(g.sn, S * m); AL(g.g, S * (m + 1));
-  AL(g.V, S * (m + 1) * 2 * np); AL(g.x, S * 2 * np); AL(g.b, S * 2 * np);
+  // the refinement forms keep their inner Krylov basis in float32: each cycle
+  // is closed by a float64 residual, so its rounding only enters the correction
+  if (refine) {
+    AL(g.Vf, S * (m + 1) * 2 * np);
+  } else {
+    AL(g.V, S * (m + 1) * 2 * np);
+  }
+  AL(g.x, S * 2 * np); AL(g.b, S * 2 * np);
   AL(g.act, S); AL(g.act2, S); AL(g.count, 2); AL(g.rho0, S); AL(g.bytes, 1);
   if (e == cudaSuccess) e = cudaMemset(g.bytes, 0, sizeof(unsigned long long));
   c->timer.dev_bytes = g.bytes;
@@ -412,9 +425,13 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   g.inner_tol = 0.0;
   c->lowprec = refine;
   c->emu = o->prec == TDDFT_PREC_FP64_EMU || o->prec == TDDFT_PREC_BF16X3_IR_EMU;
-  // the refinement form's float64 products only resolve residuals far below
-  // its tolerance: 5 slices (2^-35 of the operand scales); 6 otherwise
-  c->oz.s = o->prec == TDDFT_PREC_BF16X3_IR_EMU ? 5 : kOzDefaultSlices;
+  // the refinement form's float64 products need only resolve residuals well
+  // below its tolerance: 5 slices (2^-35 of the operand scales) down to 1e-8,
+  // 6 (2^-42) down to 1e-12, 7 below; 6 for the emulated float64 form
+  if (o->prec == TDDFT_PREC_BF16X3_IR_EMU)
+    c->oz.s = o->tol >= 1e-8 ? 5 : (o->tol >= 1e-12 ? 6 : 7);
+  else
+    c->oz.s = kOzDefaultSlices;
   if (e == cudaSuccess && c->emu) {
     e = oz_setup(c->st, d, c->oz, (int)S, c->dev_allocs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
@@ -627,6 +644,13 @@ static cudaError_t enqueue_iteration(tddft_ctx *c, cudaStream_t gs, int n, doubl
   return e;
 }
 
+// Refinement forms: the float64 residual group runs once this many right-hand
+// sides of a group of n await it (or nothing else is left), so that its fixed
+// costs are shared.
+static int residual_batch(int split, int n) {
+  return split ? std::max(1, std::min(64, n / 3)) : 1;
+}
+
 static tddft_status run_group_graph(tddft_ctx *c, int n, double eps, int split, int min_b,
                                     long max_iter) {
   constexpr int kReplays = 4;
@@ -705,7 +729,7 @@ static tddft_status polarizability_impl(tddft_ctx *c, int32_t n_omega, const dou
     // Float64 residuals that end a refinement cycle are batched: while reduced-
     // precision Arnoldi work remains, right-hand sides awaiting their residual
     // wait until enough of them have gathered to fill the float64 GEMM tiles.
-    const int min_b = split ? std::max(1, std::min(64, n / 3)) : 1;
+    const int min_b = residual_batch(split, n);
     if (c->opts.graph && !c->timer.on) {
       tddft_status gs_ = run_group_graph(c, n, eps, split, min_b, max_iter);
       if (gs_ != TDDFT_OK) return gs_;
@@ -966,7 +990,7 @@ tddft_status tddft_batch_polarizability(tddft_batch *b, int32_t n_omega, const d
       g0v.push_back(g0);
       nv.push_back(n);
       splitv.push_back(split);
-      minbv.push_back(split ? std::max(1, std::min(32, n / 4)) : 1);
+      minbv.push_back(residual_batch(split, n));
       // right-hand sides of this round, on the molecule's stream
       BCUDA(b, launch_rhs_init(c->st, c->sys, n, g0, d_omega[i], c->Zc, c->wk.omega, g.omega));
       BCUDA(b, launch_rhs_formation(c->st, c->sys, c->wk, n, g0, d_omega[i], eps, c->Z3, c->a3,
