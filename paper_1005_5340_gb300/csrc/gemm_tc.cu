@@ -6,20 +6,25 @@
 // Split-bf16 ("bf16x3"): every real operand x is stored as two bf16 planes
 // x = hi + lo (+ O(2^-17 |x|)), each row laid out [hi | lo] with Kp columns
 // per plane (Kp a multiple of 64, zero padded).  The product is accumulated
-// in float32 in tensor memory over three segments,
-//   A_hi B_hi + A_hi B_lo + A_lo B_hi ,
-// i.e. segment g reads A plane aseg[g] and B plane bseg[g].  One launch
-// computes a 128 x 128 tile of C^T per CTA:
-//   warp 0 lane 0 : TMA producer (3-stage ring of 64-deep K slices, SW128)
-//   warp 1 lane 0 : issues tcgen05.mma (M=128, N=128, K=16) into TMEM
-//   warps 0-3     : epilogue, TMEM -> registers -> global, fused per use:
-//     kStoreF32    plain float32 C^T
-//     kDscaleSplit the D(omega) scaling of eq. response-mat on (re, im)
-//                  column pairs, written back as split bf16 for the next GEMM
-// Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
-// records an error code, stops issuing work and still frees its TMEM.
+// in float32 in tensor memory as A_hi B_hi + A_hi B_lo + A_lo B_hi.  The
+// kernel is persistent (one CTA per SM over its share of the 128 x BN output
+// tiles) and warp-specialised: a TMA producer, an MMA issuer and four
+// epilogue warps that drain one TMEM accumulator while the next tile is
+// accumulated in the other.  Epilogues, fused per use:
+//     kStoreF32      plain float32 C^T
+//     kDscaleSplit   the D(omega) scaling of eq. response-mat on (re, im)
+//                    column pairs, written back as split bf16 for the next GEMM
+//     kBetaTSplit    step 2 on the stored transition vertex: beta^T, split bf16
+//     kGammaCatSplit transform 2 into the per-atom Gcat rows, split bf16
+//     kPartialF32    step 5 partial sums, float32
+// Grouped products take a tile table (per-atom operands: A rows, B K offset
+// and length per 128-row tile).  Every mbarrier wait is bounded by a
+// wall-clock limit; on expiry the CTA records an error code, stops issuing
+// work, waits (bounded) for its copies in flight and still frees its TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "internal.h"
 #include "tc_ptx.h"
@@ -28,16 +33,17 @@ namespace tddft {
 namespace {
 using namespace ptx;
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 3;
-constexpr int TC_THREADS = 128;
-constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;    // 16 KB
-// The N tile (TMEM columns, B box rows, MMA N) is a template parameter: 128
-// (2 CTAs per SM) or 64 (3 CTAs per SM), chosen per product by the autotuner.
+constexpr int TC_BM = 128, TC_BK = 64;
+constexpr int TC_THREADS = 192;
+constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;    // 16 KB per plane
+// The N tile (TMEM columns per accumulator, B box rows, MMA N) is a template
+// parameter, 128 or 64, chosen per product by the autotuner.  A stage holds
+// both planes of the A and B tiles of one 64-deep K block.
 template <int BN> struct TcShape {
   static constexpr uint32_t B_BYTES = BN * TC_BK * 2;
-  static constexpr uint32_t STAGE_BYTES = TC_A_BYTES + B_BYTES;
-  static constexpr size_t SMEM = TC_STAGES * STAGE_BYTES + 1024 + 256;
-  static constexpr int MIN_CTAS = BN == 64 ? 3 : 2;
+  static constexpr uint32_t STAGE_BYTES = 2 * TC_A_BYTES + 2 * B_BYTES;
+  static constexpr int STAGES = BN == 64 ? 4 : 3;
+  static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
@@ -52,57 +58,191 @@ __device__ __forceinline__ void store_split(__nv_bfloat16 *p, int64_t lo_off, fl
   p[lo_off] = l;
 }
 
-template <int EPI, int TC_BN>
-__global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   int M, int N, int KpA, int KpB, int nseg, int4 segs, TcEpilogue ep, int *err,
-                   const int *dcnt, int mul_n, const GTile *tiles) {
-  // graph replays: columns beyond the live count are skipped (whole CTAs)
-  if (dcnt) N = (int)min((int64_t)N, (int64_t)mul_n * (*dcnt));
-  if ((int)blockIdx.y * TC_BN >= N) return;
-  // this CTA's rows of A and K range of B (grouped products: from the tile table)
-  int m0, xoff, nkb, rows_valid, atom;
-  if (tiles) {
-    const GTile t = tiles[blockIdx.x];
-    m0 = t.row0;
-    xoff = t.xoff;
-    nkb = t.nkb;
-    rows_valid = t.rows;
-    atom = t.atom;
+// One 16-column chunk of the epilogue: row m (local row lr of the tile),
+// columns n0 + j0 .. n0 + j0 + 15, fused per use.
+template <int EPI>
+__device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, int rows_valid,
+                                           int atom, int M, int N, int n0, int j0,
+                                           const TcEpilogue &ep) {
+  if (EPI == kStoreF32) {
+    if (m < M) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = n0 + j0 + j;
+        if (n < N) ep.outF[(int64_t)n * ep.ldo + m] = v[j];
+      }
+    }
+  } else if (EPI == kPartialF32) {
+    // C layout, rows of the grouped operand
+    if (lr < rows_valid) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = n0 + j0 + j;
+        if (n < N) ep.outF[(int64_t)m * ep.ldo + n] = v[j];
+      }
+    }
+  } else if (EPI == kBetaTSplit) {
+    // row m = (atom A, E, c) of the step-2 operand; column n = 2 s + p:
+    // beta^T row (s n_occ + E) 2 + p, column ao_A + c
+    if (lr < rows_valid) {
+      const int aoA = ep.aoff[atom], nA = ep.aoff[atom + 1] - aoA;
+      const int r = m - aoA * ep.n_occ, E = r / nA, c = r - E * nA;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = n0 + j0 + j;
+        if (n < N) {
+          const int64_t row = ((int64_t)(n >> 1) * ep.n_occ + E) * 2 + (n & 1);
+          store_split(ep.outB + row * ep.ldo + aoA + c, ep.lo_off, v[j]);
+        }
+      }
+    }
+  } else if (EPI == kGammaCatSplit) {
+    // row m = orbital (atom B, b); column n = (s n_occ + E) 2 + p, j = 2 s + p:
+    // Gcat[j][xoff5_B + b n_occ + E]
+    if (m < M) {
+      const int B = ep.orb_atom[m], b = m - ep.aoff[B];
+      const int64_t xo = ep.xoff5[B] + (int64_t)b * ep.n_occ;
+      const int pair0 = (n0 + j0) >> 1;
+      if (ep.n_occ % 8 == 0 && n0 + j0 + 16 <= N) {
+        // the 16 columns are E0 .. E0+7 of one slot, both planes: four
+        // 16-byte stores (hi and lo of p = 0 and p = 1)
+        const int sl = pair0 / ep.n_occ, E0 = pair0 - sl * ep.n_occ;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) split_bf16(v[2 * e + p], h[e], l[e]);
+          __nv_bfloat16 *dst = ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E0;
+          *(uint4 *)dst = *(const uint4 *)h;
+          *(uint4 *)(dst + ep.lo_off) = *(const uint4 *)l;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + j0 + j;
+          if (n < N) {
+            const int pair = n >> 1, p = n & 1;
+            const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
+            store_split(ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E, ep.lo_off, v[j]);
+          }
+        }
+      }
+    }
   } else {
-    m0 = blockIdx.x * TC_BM;
-    xoff = 0;
-    nkb = KpA / TC_BK;
-    rows_valid = min(TC_BM, M - m0);
-    atom = -1;
+    // (re, im) pairs: columns n (even) and n+1 of the same (slot, E).
+    // omega -+ Delta, Delta = e_F - e_E, cancel near a resonance: they are
+    // formed as (omega -+ e_F) +- e_E from float (hi, lo) pairs, the
+    // first precomputed in float64 per (slot, F); the rest of D in
+    // float32 (its rounding, ~1e-7, is far below the split-bf16 error).
+    if (m < ep.rows_out) {
+      const bool live = m < M;
+      const float ef = (float)ep.eps, e2 = ef * ef, occ = (float)ep.occ_value;
+      const int pair0 = (n0 + j0) >> 1;
+      const int sl0 = pair0 / ep.n_occ, E0 = pair0 - sl0 * ep.n_occ;
+      // (omega -+ e_F) of the chunk's slot as float (hi, lo) pairs,
+      // precomputed per (slot, F) for this product
+      float4 dt = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (live) dt = ep.dterm[(int64_t)sl0 * M + m];
+      int sl = sl0, E = E0;
+#pragma unroll
+      for (int j = 0; j < 16; j += 2) {
+        const int n = n0 + j0 + j;
+        if (n >= N) continue;
+        float re = 0.f, im = 0.f;
+        if (live) {
+          if (sl != sl0) dt = ep.dterm[(int64_t)sl * M + m];   // chunk crossing a slot
+          const float2 eE = ep.eocc2[E];
+          const float xm = (dt.x + eE.x) + (dt.y + eE.y);
+          const float xp = (dt.z - eE.x) + (dt.w - eE.y);
+          const float im2 = __frcp_rn(fmaf(xm, xm, e2)), ip2 = __frcp_rn(fmaf(xp, xp, e2));
+          const float dre = occ * (xm * im2 - xp * ip2);
+          const float dim = occ * ef * (ip2 - im2);
+          re = dre * v[j] - dim * v[j + 1];
+          im = dre * v[j + 1] + dim * v[j];
+        }
+        if (++E == ep.n_occ) {
+          E = 0;
+          ++sl;
+        }
+        __nv_bfloat16 h, l;
+        split_bf16(re, h, l);
+        ep.outB[(int64_t)n * ep.ldo + m] = h;
+        ep.outB[(int64_t)n * ep.ldo + ep.lo_off + m] = l;
+        split_bf16(im, h, l);
+        ep.outB[(int64_t)(n + 1) * ep.ldo + m] = h;
+        ep.outB[(int64_t)(n + 1) * ep.ldo + ep.lo_off + m] = l;
+      }
+    }
   }
-  constexpr uint32_t TC_STAGE_BYTES = TcShape<TC_BN>::STAGE_BYTES;
+}
+
+// Persistent warp-specialised kernel: one CTA per SM walks its share of the
+// output tiles (tile t = blockIdx.x + i gridDim.x, M tiles fastest).
+//   warp 0 lane 0 : TMA producer; one ring stage holds the four planes
+//                   (A_hi, A_lo, B_hi, B_lo) of a 64-deep K block
+//   warp 1 lane 0 : tcgen05.mma issuer: A_hi B_hi + A_hi B_lo + A_lo B_hi
+//                   (M=128, N=BN, K=16) into one of two TMEM accumulators
+//   warps 2-5     : epilogue, TMEM -> registers -> global; draining tile i
+//                   while the MMA warp fills tile i+1 in the other buffer
+template <int EPI, int TC_BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   int M, int N, int KpA, int KpB, TcEpilogue ep, int *err, const int *dcnt,
+                   int mul_n, const GTile *tiles, int n_mtiles) {
+  // graph replays: columns beyond the live count are skipped (whole tiles)
+  if (dcnt) N = (int)min((int64_t)N, (int64_t)mul_n * (*dcnt));
+  const int n_ntiles = (N + TC_BN - 1) / TC_BN;
+  const int n_tiles = n_mtiles * n_ntiles;
+  if ((int)blockIdx.x >= n_tiles) return;
+  constexpr uint32_t SB = TcShape<TC_BN>::STAGE_BYTES;
+  constexpr int NS = TcShape<TC_BN>::STAGES;
+  constexpr uint32_t B_BYTES = TcShape<TC_BN>::B_BYTES;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t *full = (uint64_t *)(smem + TC_STAGES * TC_STAGE_BYTES);
-  uint64_t *empty = full + TC_STAGES;
-  uint64_t *tfull = empty + TC_STAGES;
-  uint32_t *tslot = (uint32_t *)(tfull + 1);
+  uint64_t *full = (uint64_t *)(smem + NS * SB);
+  uint64_t *empty = full + NS;
+  uint64_t *tfull = empty + NS;     // [2]
+  uint64_t *tempty = tfull + 2;     // [2]
+  uint32_t *tslot = (uint32_t *)(tempty + 2);
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.y * TC_BN;
-  const int total = nseg * nkb;
+  auto tile_of = [&](int t, int &m0, int &xoff, int &nkb, int &rows_valid, int &atom, int &n0) {
+    const int mt = t % n_mtiles, nt = t / n_mtiles;
+    n0 = nt * TC_BN;
+    if (tiles) {
+      const GTile g = tiles[mt];
+      m0 = g.row0;
+      xoff = g.xoff;
+      nkb = g.nkb;
+      rows_valid = g.rows;
+      atom = g.atom;
+    } else {
+      m0 = mt * TC_BM;
+      xoff = 0;
+      nkb = KpA / TC_BK;
+      rows_valid = min(TC_BM, M - m0);
+      atom = -1;
+    }
+  };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
     }
-    mbar_init(tfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);   // one arrival per epilogue warp
+    }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tslot)),
-                 "r"(TC_BN));
+                 "r"(2 * TC_BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -110,202 +250,123 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<TC_BN>::MIN_CTAS)
   fence_after();
   const uint32_t tmem = *tslot;
 
-  if (warp == 0 && lane == 0) {
-    // producer
-    for (int it = 0; it < total; ++it) {
-      const int s = it % TC_STAGES;
-      const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u)) {
-        atomicExch(err, 1);
-        abort_flag = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        int m0, xoff, nkb, rv, at, n0;
+        tile_of(t, m0, xoff, nkb, rv, at, n0);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % NS;
+          const uint32_t ph = (uint32_t)(g / NS) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u)) {
+            atomicExch(err, 1);
+            abort_flag = 1;
+            ok = false;
+            break;
+          }
+          if (*(volatile int *)&abort_flag) {
+            ok = false;
+            break;
+          }
+          uint8_t *st = smem + s * SB;
+          mbar_expect_tx(&full[s], SB);
+          tma_load_2d(st, &mapA, &full[s], kb * TC_BK, m0);                          // A_hi
+          tma_load_2d(st + TC_A_BYTES, &mapA, &full[s], KpA + kb * TC_BK, m0);       // A_lo
+          tma_load_2d(st + 2 * TC_A_BYTES, &mapB, &full[s], xoff + kb * TC_BK, n0);  // B_hi
+          tma_load_2d(st + 2 * TC_A_BYTES + B_BYTES, &mapB, &full[s], KpB + xoff + kb * TC_BK,
+                      n0);                                                            // B_lo
+        }
       }
-      if (*(volatile int *)&abort_flag) break;
-      const int g = it / nkb, kb = it % nkb;
-      const int ka = ((g == 0) ? segs.x : (g == 1) ? segs.y : segs.z) & 0xFF;
-      const int kbp = (((g == 0) ? segs.x : (g == 1) ? segs.y : segs.z) >> 8) & 0xFF;
-      uint8_t *sa = smem + s * TC_STAGE_BYTES;
-      uint8_t *sb = sa + TC_A_BYTES;
-      mbar_expect_tx(&full[s], TC_STAGE_BYTES);
-      tma_load_2d(sa, &mapA, &full[s], ka * KpA + kb * TC_BK, m0);
-      tma_load_2d(sb, &mapB, &full[s], kbp * KpB + xoff + kb * TC_BK, n0);
+      // copies in flight: the last NS stages issued must land before exit
+      for (int h = max(0, g - NS); h < g; ++h)
+        mbar_wait(&full[h % NS], (uint32_t)(h / NS) & 1u);
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(TC_BM, TC_BN);
-    bool ok = true;
-    for (int it = 0; it < total; ++it) {
-      const int s = it % TC_STAGES;
-      const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph)) {
-        atomicExch(err, 2);
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(TC_BM, TC_BN);
+      const uint32_t base = smem_u32(smem);
+      int g = 0, lt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++lt) {
+        int m0, xoff, nkb, rv, at, n0;
+        tile_of(t, m0, xoff, nkb, rv, at, n0);
+        const int buf = lt & 1, use = lt >> 1;
+        if (use > 0) {
+          // the epilogue has drained this buffer's previous tile
+          if (!mbar_wait(&tempty[buf], (uint32_t)(use - 1) & 1u)) {
+            atomicExch(err, 2);
+            abort_flag = 1;
+            ok = false;
+            break;
+          }
+          fence_after();
+        }
+        const uint32_t d = tmem + (uint32_t)(buf * TC_BN);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % NS;
+          if (!mbar_wait(&full[s], (uint32_t)(g / NS) & 1u)) {
+            atomicExch(err, 2);
+            abort_flag = 1;
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t ahi = base + (uint32_t)s * SB, alo = ahi + TC_A_BYTES;
+          const uint32_t bhi = ahi + 2 * TC_A_BYTES, blo = bhi + B_BYTES;
+#pragma unroll
+          for (int k = 0; k < TC_BK / 16; ++k) {
+            mma_bf16(d, desc_sw128(ahi + 32 * k), desc_sw128(bhi + 32 * k), idesc,
+                     (kb > 0 || k > 0) ? 1u : 0u);
+            mma_bf16(d, desc_sw128(ahi + 32 * k), desc_sw128(blo + 32 * k), idesc, 1u);
+            mma_bf16(d, desc_sw128(alo + 32 * k), desc_sw128(bhi + 32 * k), idesc, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&tfull[buf]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of the tile)
+    const int q = warp & 3;
+    const int lr = q * 32 + lane;
+    int lt = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+      int m0, xoff, nkb, rows_valid, atom, n0;
+      tile_of(t, m0, xoff, nkb, rows_valid, atom, n0);
+      const int buf = lt & 1, use = lt >> 1;
+      bool have = mbar_wait(&tfull[buf], (uint32_t)use & 1u);
+      // tcgen05.ld is warp-collective: one decision per warp
+      have = __all_sync(0xffffffffu, have && !*(volatile int *)&abort_flag);
+      if (!have) {
+        if (lane == 0) atomicExch(err, 3);
         abort_flag = 1;
-        ok = false;
         break;
       }
       fence_after();
-      const uint32_t sa = smem_u32(smem + s * TC_STAGE_BYTES);
-      const uint32_t sb = sa + TC_A_BYTES;
-#pragma unroll
-      for (int k = 0; k < TC_BK / 16; ++k)
-        mma_bf16(tmem, desc_sw128(sa + 32 * k), desc_sw128(sb + 32 * k), idesc,
-                 (it > 0 || k > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
-    }
-    if (ok) mma_commit(tfull);
-  }
-  __syncwarp();
-
-  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
-  bool have = mbar_wait(tfull, 0);
-  if (!have) atomicExch(err, 3);
-  fence_after();
-  // tcgen05.ld is warp-collective: take the decision once per warp
-  have = __all_sync(0xffffffffu, have && !*(volatile int *)&abort_flag);
-  const int lr = warp * 32 + lane;
-  const int m = m0 + lr;
-  if (have) {
-    for (int j0 = 0; j0 < TC_BN; j0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
-      if (EPI == kStoreF32) {
-        if (m < M) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + j0 + j;
-            if (n < N) ep.outF[(int64_t)n * ep.ldo + m] = v[j];
-          }
-        }
-      } else if (EPI == kPartialF32) {
-        // C layout, rows of the grouped operand
-        if (lr < rows_valid) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + j0 + j;
-            if (n < N) ep.outF[(int64_t)m * ep.ldo + n] = v[j];
-          }
-        }
-      } else if (EPI == kBetaTSplit) {
-        // row m = (atom A, E, c) of the step-2 operand; column n = 2 s + p:
-        // beta^T row (s n_occ + E) 2 + p, column ao_A + c
-        if (lr < rows_valid) {
-          const int aoA = ep.aoff[atom], nA = ep.aoff[atom + 1] - aoA;
-          const int r = m - aoA * ep.n_occ, E = r / nA, c = r - E * nA;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + j0 + j;
-            if (n < N) {
-              const int64_t row = ((int64_t)(n >> 1) * ep.n_occ + E) * 2 + (n & 1);
-              store_split(ep.outB + row * ep.ldo + aoA + c, ep.lo_off, v[j]);
-            }
-          }
-        }
-      } else if (EPI == kGammaCatSplit) {
-        // row m = orbital (atom B, b); column n = (s n_occ + E) 2 + p, j = 2 s + p:
-        // Gcat[j][xoff5_B + b n_occ + E]
-        if (m < M) {
-          const int B = ep.orb_atom[m], b = m - ep.aoff[B];
-          const int64_t xo = ep.xoff5[B] + (int64_t)b * ep.n_occ;
-          const int pair0 = (n0 + j0) >> 1;
-          if (ep.n_occ % 8 == 0 && n0 + j0 + 16 <= N) {
-            // the 16 columns are E0 .. E0+7 of one slot, both planes: four
-            // 16-byte stores (hi and lo of p = 0 and p = 1)
-            const int sl = pair0 / ep.n_occ, E0 = pair0 - sl * ep.n_occ;
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-              __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-              for (int e = 0; e < 8; ++e) split_bf16(v[2 * e + p], h[e], l[e]);
-              __nv_bfloat16 *dst = ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E0;
-              *(uint4 *)dst = *(const uint4 *)h;
-              *(uint4 *)(dst + ep.lo_off) = *(const uint4 *)l;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int n = n0 + j0 + j;
-              if (n < N) {
-                const int pair = n >> 1, p = n & 1;
-                const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
-                store_split(ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E, ep.lo_off, v[j]);
-              }
-            }
-          }
-        }
-      } else {
-        // (re, im) pairs: columns n (even) and n+1 of the same (slot, E).
-        // omega -+ Delta, Delta = e_F - e_E, cancel near a resonance: they are
-        // formed as (omega -+ e_F) +- e_E from float (hi, lo) pairs, the
-        // first once per slot in float64; the rest of D in float32 (its
-        // rounding, ~1e-7, is far below the split-bf16 error).
-        if (m < ep.rows_out) {
-          const bool live = m < M;
-          const float ef = (float)ep.eps, e2 = ef * ef, occ = (float)ep.occ_value;
-          const int pair0 = (n0 + j0) >> 1;
-          const int sl0 = pair0 / ep.n_occ, E0 = pair0 - sl0 * ep.n_occ;
-          // (omega -+ e_F) of the chunk's slot, once (the usual case: all 8
-          // pairs in one slot); otherwise per pair, with identical arithmetic
-          // so that no result depends on a right-hand side's slot
-          float am_hi = 0.f, am_lo = 0.f, ap_hi = 0.f, ap_lo = 0.f;
-          const bool one_slot = E0 + 8 <= ep.n_occ;
-          double eF = 0.0;
-          if (live) {
-            eF = ep.energy[ep.n_occ + m];
-            if (one_slot) {
-              const double w = ep.omega[sl0];
-              const double am = w - eF, ap = w + eF;
-              am_hi = (float)am;
-              am_lo = (float)(am - (double)am_hi);
-              ap_hi = (float)ap;
-              ap_lo = (float)(ap - (double)ap_hi);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            const int n = n0 + j0 + j;
-            if (n >= N) continue;
-            float re = 0.f, im = 0.f;
-            if (live) {
-              float xm, xp;
-              if (one_slot) {
-                const float2 eE = ep.eocc2[E0 + (j >> 1)];
-                xm = (am_hi + eE.x) + (am_lo + eE.y);
-                xp = (ap_hi - eE.x) + (ap_lo - eE.y);
-              } else {
-                // the same arithmetic with this pair's slot (chunks that cross a slot)
-                const int pair = n >> 1;
-                const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
-                const double w = ep.omega[sl];
-                const double am = w - eF, ap = w + eF;
-                const float bm_hi = (float)am, bm_lo = (float)(am - (double)bm_hi);
-                const float bp_hi = (float)ap, bp_lo = (float)(ap - (double)bp_hi);
-                const float2 eE = ep.eocc2[E];
-                xm = (bm_hi + eE.x) + (bm_lo + eE.y);
-                xp = (bp_hi - eE.x) + (bp_lo - eE.y);
-              }
-              const float im2 = __frcp_rn(fmaf(xm, xm, e2)), ip2 = __frcp_rn(fmaf(xp, xp, e2));
-              const float dre = occ * (xm * im2 - xp * ip2);
-              const float dim = occ * ef * (ip2 - im2);
-              re = dre * v[j] - dim * v[j + 1];
-              im = dre * v[j + 1] + dim * v[j];
-            }
-            __nv_bfloat16 h, l;
-            split_bf16(re, h, l);
-            ep.outB[(int64_t)n * ep.ldo + m] = h;
-            ep.outB[(int64_t)n * ep.ldo + ep.lo_off + m] = l;
-            split_bf16(im, h, l);
-            ep.outB[(int64_t)(n + 1) * ep.ldo + m] = h;
-            ep.outB[(int64_t)(n + 1) * ep.ldo + ep.lo_off + m] = l;
-          }
-        }
+      const int m = m0 + lr;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN);
+      for (int j0 = 0; j0 < TC_BN; j0 += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)j0, v);
+        epilogue16<EPI>(v, m, lr, rows_valid, atom, M, N, n0, j0, ep);
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
     }
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * TC_BN));
   }
 }
 
@@ -384,37 +445,49 @@ void tc_init_attributes() {
 }
 
 namespace {
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 1;
+  }
+  return n;
+}
+
 template <int EPI, int BN>
-cudaError_t launch_tc(cudaStream_t st, dim3 grid, const CUtensorMap &mA, const CUtensorMap &mB,
+cudaError_t launch_tc(cudaStream_t st, int grid, const CUtensorMap &mA, const CUtensorMap &mB,
                       int M, int N, int KpA, int KpB, const TcEpilogue &ep, int *err,
-                      const int *dcnt, int mul_n, const GTile *tiles) {
-  // segments: A_hi B_hi, A_hi B_lo, A_lo B_hi  (low byte: A plane, next byte: B plane)
-  const int4 segs = make_int4(0 | (0 << 8), 0 | (1 << 8), 1 | (0 << 8), 0);
+                      const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
   gemm_tc_kernel<EPI, BN><<<grid, TC_THREADS, TcShape<BN>::SMEM, st>>>(
-      mA, mB, M, N, KpA, KpB, 3, segs, ep, err, dcnt, mul_n, tiles);
+      mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n, tiles, n_mtiles);
   return cudaGetLastError();
 }
 
 template <int BN>
-cudaError_t launch_tc_epi(cudaStream_t st, int epi, dim3 grid, const CUtensorMap &mA,
-                          const CUtensorMap &mB, int M, int N, int KpA, int KpB,
-                          const TcEpilogue &ep, int *err, const int *dcnt, int mul_n,
-                          const GTile *tiles) {
+cudaError_t launch_tc_epi(cudaStream_t st, int epi, int M, int N, const CUtensorMap &mA,
+                          const CUtensorMap &mB, int KpA, int KpB, const TcEpilogue &ep, int *err,
+                          const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
+  // persistent: one CTA per SM at most, each walking its share of the tiles
+  const int64_t n_tiles = (int64_t)n_mtiles * ((N + BN - 1) / BN);
+  const int grid = (int)std::min<int64_t>(n_tiles, sm_count());
   switch (epi) {
     case kStoreF32:
-      return launch_tc<kStoreF32, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n, tiles);
+      return launch_tc<kStoreF32, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+                                      tiles, n_mtiles);
     case kDscaleSplit:
       return launch_tc<kDscaleSplit, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
-                                         tiles);
+                                         tiles, n_mtiles);
     case kBetaTSplit:
       return launch_tc<kBetaTSplit, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
-                                        tiles);
+                                        tiles, n_mtiles);
     case kGammaCatSplit:
       return launch_tc<kGammaCatSplit, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
-                                           tiles);
+                                           tiles, n_mtiles);
     case kPartialF32:
       return launch_tc<kPartialF32, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
-                                        tiles);
+                                        tiles, n_mtiles);
     default:
       return cudaErrorInvalidValue;
   }
@@ -428,13 +501,12 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
   if (A.Kp != B.Kp) return cudaErrorInvalidValue;
   tc_init_attributes();
   if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
-  dim3 grid((M + TC_BM - 1) / TC_BM, (N + bn - 1) / bn);
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  const int n_mtiles = (M + TC_BM - 1) / TC_BM;
   if (bn == 64)
-    return launch_tc_epi<64>(st, epi, grid, A.map, B.map64, M, N, A.Kp, B.Kp, ep, err, dcnt, mul_n,
-                             nullptr);
-  return launch_tc_epi<128>(st, epi, grid, A.map, B.map, M, N, A.Kp, B.Kp, ep, err, dcnt, mul_n,
-                            nullptr);
+    return launch_tc_epi<64>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+                             nullptr, n_mtiles);
+  return launch_tc_epi<128>(st, epi, M, N, A.map, B.map, A.Kp, B.Kp, ep, err, dcnt, mul_n, nullptr,
+                            n_mtiles);
 }
 
 cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const TcOperand &B,
@@ -444,13 +516,11 @@ cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const Tc
   if (n_tiles <= 0 || N <= 0) return cudaSuccess;
   tc_init_attributes();
   if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
-  dim3 grid(n_tiles, (N + bn - 1) / bn);
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   if (bn == 64)
-    return launch_tc_epi<64>(st, epi, grid, A.map, B.map64, 0, N, A.Kp, B.Kp, ep, err, dcnt, mul_n,
-                             tiles);
-  return launch_tc_epi<128>(st, epi, grid, A.map, B.map, 0, N, A.Kp, B.Kp, ep, err, dcnt, mul_n,
-                            tiles);
+    return launch_tc_epi<64>(st, epi, 0, N, A.map, B.map64, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+                             tiles, n_tiles);
+  return launch_tc_epi<128>(st, epi, 0, N, A.map, B.map, A.Kp, B.Kp, ep, err, dcnt, mul_n, tiles,
+                            n_tiles);
 }
 
 }  // namespace tddft

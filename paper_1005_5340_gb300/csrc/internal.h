@@ -165,6 +165,7 @@ struct TcEpilogue {
   int rows_out = 0;                // kDscaleSplit: rows m < rows_out written (zeros past M)
   const double *energy = nullptr;  // [n_orb]
   const float2 *eocc2 = nullptr;   // [n_occ] occupied energies as float (hi, lo)
+  const float4 *dterm = nullptr;   // [S][M] omega_s -+ e_F as float (hi, lo, hi, lo)
   const double *omega = nullptr;   // [S]
   double eps = 0.0;
   double occ_value = 0.0;
@@ -217,6 +218,7 @@ struct LpWork {
   double *omega = nullptr;         // [S]
   int *err = nullptr;              // [1] device-side error code of the GEMM waits
   float2 *eocc2 = nullptr;         // [n_occ] occupied energies as float (hi, lo)
+  float4 *dterm = nullptr;         // [S][n_virt] omega_s -+ e_F as float (hi, lo) pairs
   TcOperand opK, opXvT, opXv, opZ, opBeta, opA;
   AlphaRoute *ar = nullptr;        // steps 2 and 5 on the stored transition vertex
   int bnK = 128, bn1 = 128, bn2 = 128;   // N tiles chosen by the autotuner

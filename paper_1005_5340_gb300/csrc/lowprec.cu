@@ -64,6 +64,23 @@ __global__ void split_f32_pairs_kernel(const double *__restrict__ src, int n,
   }
 }
 
+// dterm[s][F] = (hi, lo) of omega_s - e_F and of omega_s + e_F, e_F the
+// energy of virtual state F (float64 differences, float pairs)
+__global__ void dterm_kernel(int S, int n_virt, int n_occ, const double *__restrict__ energy,
+                             const double *__restrict__ omega, float4 *__restrict__ dterm,
+                             const int *__restrict__ dcnt) {
+  if (dcnt) S = min(S, *dcnt);
+  const int64_t total = (int64_t)S * n_virt;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / n_virt), F = (int)(i - (int64_t)s * n_virt);
+    const double w = omega[s], e = energy[n_occ + F];
+    const double am = w - e, ap = w + e;
+    const float amh = (float)am, aph = (float)ap;
+    dterm[i] = make_float4(amh, (float)(am - (double)amh), aph, (float)(ap - (double)aph));
+  }
+}
+
 __global__ void to_f32_kernel(const double *__restrict__ src, int64_t n, float *__restrict__ dst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -229,6 +246,7 @@ cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
         ep.rows_out = lp.Kp2;
         ep.energy = sys.energy;
         ep.eocc2 = lp.eocc2;
+        ep.dterm = lp.dterm;
         ep.omega = lp.omega;
         ep.eps = 0.01;
         ep.occ_value = sys.occ_value;
@@ -252,6 +270,8 @@ cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
     ms = best;
     return r;
   };
+  dterm_kernel<<<grid_for((int64_t)S * sys.n_virt, 256), 256, 0, st>>>(
+      S, sys.n_virt, sys.n_occ, sys.energy, lp.omega, lp.dterm, nullptr);
   int *pick[3] = {&lp.bnK, &lp.bn1, &lp.bn2};
   for (int which = 0; which < 3 && e == cudaSuccess; ++which) {
     float t128 = 0.f, t64 = 0.f;
@@ -339,6 +359,9 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
   const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)N1;
   {
     Scope sc(lp.timer, st, kcTcT1, tflops);
+    dterm_kernel<<<grid_for((int64_t)S * sys.n_virt, 256), 256, 0, st>>>(
+        S, sys.n_virt, sys.n_occ, sys.energy, lp.omega, lp.dterm, lp.dcnt);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
     TcEpilogue e1;
     e1.outB = lp.aT;
     e1.ldo = 2 * (int64_t)lp.Kp2;
@@ -346,6 +369,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     e1.rows_out = lp.Kp2;
     e1.energy = sys.energy;
     e1.eocc2 = lp.eocc2;
+    e1.dterm = lp.dterm;
     e1.omega = lp.omega;
     e1.eps = eps;
     e1.occ_value = sys.occ_value;

@@ -467,6 +467,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     AL(L.omega, S);
     AL(L.err, 1);
     AL(L.eocc2, (size_t)nocc);
+    AL(L.dterm, S * (size_t)nv);
     if (e == cudaSuccess) e = make_operand_map(L.opK, L.Ks, np, L.KpK, 128);
     if (e == cudaSuccess) e = make_operand_map(L.opXvT, L.XvTs, nv, L.Kp1, 128);
     if (e == cudaSuccess) e = make_operand_map(L.opXv, L.Xvs, no, L.Kp2, 128);
