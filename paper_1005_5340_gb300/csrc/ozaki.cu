@@ -25,8 +25,9 @@
 //   warp 1     tcgen05.mma issuer (M=128, N=64, K=16): once slice i of a K
 //              block has landed, every pair (i, j) and (j, i) with j <= i and
 //              i + j <= s+1 goes to the TMEM accumulator of group i+j (s
-//              groups x 64 columns); the block's stages are released together
-//              after its last MMA
+//              groups x 64 columns); a slice's stage is released after the
+//              last pair that reads it, and a group of the next chunk starts
+//              as soon as the epilogue has drained it
 //   warps 2-9  epilogue (two warps per TMEM lane quadrant, 32 columns each):
 //              per chunk, TMEM -> registers -> int64 accumulators; at the end
 //              the float64 tile is stored (C or C^T)
@@ -81,12 +82,17 @@ constexpr int kOzMaxChunks = 1024;
 // group's values are live at a time (the loop is not unrolled).
 // (ns == S, passed at run time so that the loop stays rolled)
 template <int S>
-__device__ __forceinline__ void read_groups(uint32_t tcol, long long (&acc)[OZ_EPI_COLS], int ns) {
+__device__ __forceinline__ void read_groups(uint32_t tcol, long long (&acc)[OZ_EPI_COLS], int ns,
+                                            uint64_t *tempty) {
 #pragma unroll 1
   for (int grp = 0; grp < ns; ++grp) {
     const int sh = 7 * (S - 1 - grp) - oz_drop_bits(S);
     float v[32];
     tmem_ld32(tcol + (uint32_t)(grp * OZ_BN), v);
+    // this group's accumulator may be overwritten by the next chunk
+    fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&tempty[grp]);
     if (sh >= 0) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[j] += (long long)__float2int_rn(v[j]) << sh;
@@ -133,8 +139,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   uint64_t *full = (uint64_t *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
   uint64_t *empty = full + OZ_STAGES;
   uint64_t *tfull = empty + OZ_STAGES;
-  uint64_t *tempty = tfull + 1;
-  uint32_t *tslot = (uint32_t *)(tempty + 1);
+  uint64_t *tempty = tfull + 1;   // [kOzMaxSlices] one per TMEM group
+  uint32_t *tslot = (uint32_t *)(tempty + kOzMaxSlices);
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -149,7 +155,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(&empty[i], 1);
     }
     mbar_init(tfull, 1);
-    mbar_init(tempty, OZ_EPI_WARPS);   // one arrival per epilogue warp
+    for (int q = 0; q < kOzMaxSlices; ++q)
+      mbar_init(&tempty[q], OZ_EPI_WARPS);   // one arrival per epilogue warp
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -202,20 +209,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       int g = 0;
       bool ok = true;
       for (int c = 0; c < nchunks && ok; ++c) {
-        if (c > 0) {
-          // the epilogue has read the previous chunk's groups
-          if (!mbar_wait(tempty, (uint32_t)(c - 1) & 1u)) {
-            atomicExch(a.err, 22);
-            abort_flag = 1;
-            ok = false;
-            break;
-          }
-          fence_after();
-        }
-        uint32_t written = 0;
+        // groups whose previous chunk the epilogue has drained (checked
+        // before their first MMA of this chunk)
+        uint32_t written = 0, drained = (c == 0) ? 0xFFu : 0u;
         const int kb1 = min(nkb, (c + 1) * cb);
         for (int kb = c * cb; kb < kb1 && ok; ++kb) {
-          for (int i = 0; i < s; ++i) {
+          for (int i = 0; i < s && ok; ++i) {
             const int gi = g + i;
             if (!mbar_wait(&full[gi % OZ_STAGES], (uint32_t)(gi / OZ_STAGES) & 1u)) {
               atomicExch(a.err, 23);
@@ -229,6 +228,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int j = 0; j <= jmax; ++j) {
               const uint32_t sj = base + (uint32_t)((g + j) % OZ_STAGES) * OZ_STAGE_BYTES;
               const int grp = i + j;
+              if (!((drained >> grp) & 1u)) {
+                if (!mbar_wait(&tempty[grp], (uint32_t)(c - 1) & 1u)) {
+                  atomicExch(a.err, 22);
+                  abort_flag = 1;
+                  ok = false;
+                  break;
+                }
+                fence_after();
+                drained |= 1u << grp;
+              }
               const uint32_t d = tmem + (uint32_t)(grp * OZ_BN);
               uint32_t acc = (written >> grp) & 1u;
               // A slice i x B slice j
@@ -245,9 +254,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               }
               written |= 1u << grp;
             }
+            if (!ok) break;
+            // slice q is last used at step max(q, s-1-q): release what step i
+            // finished (the stage frees once these MMAs complete)
+            if (i >= s - 1 - i) mma_commit(&empty[gi % OZ_STAGES]);
+            if (s - 1 - i < i) mma_commit(&empty[(g + s - 1 - i) % OZ_STAGES]);
           }
           if (!ok) break;
-          for (int i = 0; i < s; ++i) mma_commit(&empty[(g + i) % OZ_STAGES]);
           g += s;
         }
         if (ok) mma_commit(tfull);
@@ -277,10 +290,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         break;
       }
       fence_after();
-      read_groups<S>(tcol, acc, a.ns);
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty);
+      read_groups<S>(tcol, acc, a.ns, tempty);
     }
     if (ok && lr < rows_valid && nc < N) {
       // C = acc 2^(eA + eB + u - 7(S+1)), as two exact power-of-two factors
@@ -344,72 +354,75 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Slicing
+// Slicing, in integer arithmetic on the float64 bit patterns (float64 ops run
+// at 1/64 of the float32 rate on this part).  The row exponent is e = f - 1022
+// for the largest biased exponent field f of the row (so |x| < 2^e); each x
+// becomes the fixed-point integer F = round(x 2^(7s - e)), |F| <= 2^(7s),
+// and F is written as balanced base-128 digits, most significant first:
+//   F = sum_i q_i 128^(s-i),   q_1 in [-128, 128],  q_i in [-64, 63] (i > 1),
+// so x = 2^e sum_i q_i 2^(-7i) up to the rounding of F.  Zero and subnormal
+// values (below 2^-1022, far under any row's scale) count as zero.
 // ---------------------------------------------------------------------------
-// Exponent e with |x| < 2^e for every x of a row whose largest magnitude is mx.
-__device__ __forceinline__ int row_exponent(double mx) {
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
-  return e;
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+__device__ __forceinline__ int row_exponent_of_field(int fmax) {
+  return fmax > 0 ? fmax - 1022 : 0;
+}
+__device__ __forceinline__ long long fixed_point(double x, int e, int s) {
+  const long long b = __double_as_longlong(x);
+  const int f = (int)((b >> 52) & 0x7FF);
+  if (f == 0) return 0;
+  const long long M = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);   // x = +-M 2^(f - 1075)
+  const int sh = f - 1075 + 7 * s - e;
+  long long F;
+  if (sh >= 0) F = M << sh;                       // only for s = 8 (sh <= 3)
+  else if (sh < -62) F = 0;
+  else F = (M + (1ll << (-sh - 1))) >> (-sh);     // round half up in magnitude
+  return b < 0 ? -F : F;
+}
+// bf16 bit pattern of an integer with |q| <= 128 (exact)
+__device__ __forceinline__ unsigned int bf16_bits_small(int q) {
+  if (q == 0) return 0u;
+  const unsigned int sign = q < 0 ? 0x8000u : 0u;
+  const unsigned int a = (unsigned int)(q < 0 ? -q : q);
+  const int p = 31 - __clz(a);                    // 2^p <= a < 2^(p+1), p <= 7
+  return sign | ((unsigned int)(127 + p) << 7) | ((a << (7 - p)) & 0x7Fu);
+}
+// slices of two neighbouring entries (x0, x1) of a row with exponent e,
+// stored as bf16 pairs at dst + i*Kp for slice i
+__device__ __forceinline__ void store_slices(double x0, double x1, int e, int s, int Kp,
+                                             __nv_bfloat16 *dst) {
+  long long F0 = fixed_point(x0, e, s), F1 = fixed_point(x1, e, s);
+  unsigned int w[kOzMaxSlices];
+  for (int i = s - 1; i >= 1; --i) {
+    const int d0 = (int)(((F0 + 64) & 127) - 64), d1 = (int)(((F1 + 64) & 127) - 64);
+    w[i] = bf16_bits_small(d0) | (bf16_bits_small(d1) << 16);
+    F0 = (F0 - d0) >> 7;
+    F1 = (F1 - d1) >> 7;
+  }
+  w[0] = bf16_bits_small((int)F0) | (bf16_bits_small((int)F1) << 16);
+  for (int i = 0; i < s; ++i) *(unsigned int *)(dst + (int64_t)i * Kp) = w[i];
 }
 
-// s slices of y = x 2^(7-e) (|y| < 128): q_1 = rint(y), then the remainder
-// (exact in float64) scaled by 2^7 and rounded again, and so on.
-__device__ __forceinline__ void store_slices(double y0, double y1, int s, int Kp,
-                                             __nv_bfloat16 *dst) {
-  for (int i = 0; i < s; ++i) {
-    const double q0 = rint(y0), q1 = rint(y1);
-    *(__nv_bfloat162 *)(dst + (int64_t)i * Kp) = __floats2bfloat162_rn((float)q0, (float)q1);
-    y0 = (y0 - q0) * 128.0;
-    y1 = (y1 - q1) * 128.0;
+// Block-wide max of an int (all threads receive it); red holds >= 32 ints.
+__device__ __forceinline__ int block_max_int(int v, int *red) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (threadIdx.x == 0) red[0] = t;
   }
+  __syncthreads();
+  const int r = red[0];
+  __syncthreads();
+  return r;
 }
 
 // Row r of the operand: X[r][k] for k < Kdim, or, with a column map,
 // X[r][cols[k]] (zero where cols[k] < 0).
-__global__ void oz_slice_rows_kernel(int rows, int Kdim, const double *__restrict__ X, int64_t ldx,
-                                     const int *__restrict__ cols, int s, int Kp,
-                                     __nv_bfloat16 *__restrict__ Q, int *__restrict__ E,
-                                     const int *dcnt, int mul) {
-  __shared__ double red[32];
-  int live = rows;
-  if (dcnt) live = min(rows, mul * (*dcnt));
-  auto val = [&](const double *x, int k) -> double {
-    if (k >= Kdim) return 0.0;
-    if (!cols) return x[k];
-    const int c = cols[k];
-    return c >= 0 ? x[c] : 0.0;
-  };
-  for (int r = blockIdx.x; r < live; r += gridDim.x) {
-    const double *x = X + (int64_t)r * ldx;
-    double mx = 0.0;
-    for (int k = threadIdx.x; k < Kdim; k += blockDim.x) mx = fmax(mx, fabs(val(x, k)));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (threadIdx.x == 0) red[0] = v;
-    }
-    __syncthreads();
-    const int e = row_exponent(red[0]);
-    __syncthreads();
-    if (threadIdx.x == 0) E[r] = e;
-    const double sc = ldexp(1.0, 7 - e);
-    __nv_bfloat16 *qr = Q + (int64_t)r * s * Kp;
-    for (int k = 2 * threadIdx.x; k < Kp; k += 2 * blockDim.x)
-      store_slices(val(x, k) * sc, val(x, k + 1) * sc, s, Kp, qr + k);
-  }
-}
-
-// Long rows: grid (chunks, rows).  Pass 1 raises E[r] (preset to a large
-// negative value) to the exponent of each chunk's largest magnitude; pass 2
-// slices every chunk with the row's exponent (a row of zeros keeps the preset
-// value and gives zero slices).
-constexpr int OZ_CHUNK = 4096;
-constexpr int kOzZeroRow = -1100;   // below every finite exponent
-
 __device__ __forceinline__ double gathered(const double *x, const int *cols, int k, int Kdim) {
   if (k >= Kdim) return 0.0;
   if (!cols) return x[k];
@@ -417,27 +430,47 @@ __device__ __forceinline__ double gathered(const double *x, const int *cols, int
   return c >= 0 ? x[c] : 0.0;
 }
 
+__global__ void oz_slice_rows_kernel(int rows, int Kdim, const double *__restrict__ X, int64_t ldx,
+                                     const int *__restrict__ cols, int s, int Kp,
+                                     __nv_bfloat16 *__restrict__ Q, int *__restrict__ E,
+                                     const int *dcnt, int mul) {
+  __shared__ int red[32];
+  int live = rows;
+  if (dcnt) live = min(rows, mul * (*dcnt));
+  for (int r = blockIdx.x; r < live; r += gridDim.x) {
+    const double *x = X + (int64_t)r * ldx;
+    int fm = 0;
+    for (int k = threadIdx.x; k < Kdim; k += blockDim.x) fm = max(fm, exp_field(gathered(x, cols, k, Kdim)));
+    const int e = row_exponent_of_field(block_max_int(fm, red));
+    if (threadIdx.x == 0) E[r] = e;
+    __nv_bfloat16 *qr = Q + (int64_t)r * s * Kp;
+    for (int k = 2 * threadIdx.x; k < Kp; k += 2 * blockDim.x)
+      store_slices(gathered(x, cols, k, Kdim), gathered(x, cols, k + 1, Kdim), e, s, Kp, qr + k);
+  }
+}
+
+// Long rows: grid (chunks, rows).  Pass 1 raises E[r] (preset to a large
+// negative value) to the exponent of each chunk's largest entry; pass 2
+// slices every chunk with the row's exponent (a row of zeros keeps the preset
+// value and gives zero slices).
+constexpr int OZ_CHUNK = 4096;
+
 __global__ void __launch_bounds__(256) oz_rowmax_kernel(int rows, int Kdim,
                                                         const double *__restrict__ X, int64_t ldx,
                                                         const int *__restrict__ cols,
                                                         int *__restrict__ E, const int *dcnt,
                                                         int mul) {
-  __shared__ double red[8];
+  __shared__ int red[32];
   int live = rows;
   if (dcnt) live = min(rows, mul * (*dcnt));
   const int r = blockIdx.y;
   if (r >= live) return;
   const double *x = X + (int64_t)r * ldx;
   const int k0 = blockIdx.x * OZ_CHUNK, k1 = min(Kdim, k0 + OZ_CHUNK);
-  double mx = 0.0;
-  for (int k = k0 + threadIdx.x; k < k1; k += 256) mx = fmax(mx, fabs(gathered(x, cols, k, Kdim)));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 1; i < 8; ++i) mx = fmax(mx, red[i]);
-    if (mx > 0.0) atomicMax(E + r, row_exponent(mx));
-  }
+  int fm = 0;
+  for (int k = k0 + threadIdx.x; k < k1; k += 256) fm = max(fm, exp_field(gathered(x, cols, k, Kdim)));
+  fm = block_max_int(fm, red);
+  if (threadIdx.x == 0 && fm > 0) atomicMax(E + r, row_exponent_of_field(fm));
 }
 
 __global__ void __launch_bounds__(256) oz_slice_chunks_kernel(int rows, int Kdim,
@@ -452,16 +485,14 @@ __global__ void __launch_bounds__(256) oz_slice_chunks_kernel(int rows, int Kdim
   const int r = blockIdx.y;
   if (r >= live) return;
   const double *x = X + (int64_t)r * ldx;
-  const int e = max(E[r], kOzZeroRow);   // zero row: any scale gives zero slices
-  const double sc = ldexp(1.0, 7 - (e == kOzZeroRow ? 0 : e));
+  const int e = E[r];   // a row of zeros: every entry gives F = 0 whatever e is
   __nv_bfloat16 *qr = Q + (int64_t)r * s * Kp;
   const int k0 = blockIdx.x * OZ_CHUNK, k1 = min(Kp, k0 + OZ_CHUNK);
   for (int k = k0 + 2 * threadIdx.x; k < k1; k += 512)
-    store_slices(gathered(x, cols, k, Kdim) * sc, gathered(x, cols, k + 1, Kdim) * sc, s, Kp,
-                 qr + k);
+    store_slices(gathered(x, cols, k, Kdim), gathered(x, cols, k + 1, Kdim), e, s, Kp, qr + k);
 }
 
-// 32 columns per CTA (256 threads): column maxima, then 64-row tiles staged
+// 32 columns per CTA (256 threads): column exponents, then 64-row tiles staged
 // through shared memory and written as rows of the transposed operand.
 __global__ void __launch_bounds__(256) oz_slice_cols_kernel(int Kdim, int N,
                                                             const double *__restrict__ X,
@@ -470,37 +501,37 @@ __global__ void __launch_bounds__(256) oz_slice_cols_kernel(int Kdim, int N,
                                                             int *__restrict__ E, const int *dcnt,
                                                             int mul) {
   __shared__ double tile[32][65];
-  __shared__ double red[8][32];
-  __shared__ double scl[32];
+  __shared__ int red[8][32];
+  __shared__ int ecol[32];
   int live = N;
   if (dcnt) live = (int)min((int64_t)N, (int64_t)mul * (*dcnt));
   const int n0 = blockIdx.x * 32;
   if (n0 >= live) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int n = n0 + tx;
-  double mx = 0.0;
+  int fm = 0;
   if (n < live)
-    for (int k = ty; k < Kdim; k += 8) mx = fmax(mx, fabs(X[(int64_t)k * ldx + n]));
-  red[ty][tx] = mx;
+    for (int k = ty; k < Kdim; k += 8) fm = max(fm, exp_field(X[(int64_t)k * ldx + n]));
+  red[ty][tx] = fm;
   __syncthreads();
   if (ty == 0) {
-    double v = 0.0;
-    for (int i = 0; i < 8; ++i) v = fmax(v, red[i][tx]);
-    const int e = row_exponent(v);
+    int v = 0;
+    for (int i = 0; i < 8; ++i) v = max(v, red[i][tx]);
+    const int e = row_exponent_of_field(v);
     if (n < live) E[n] = e;
-    scl[tx] = ldexp(1.0, 7 - e);
+    ecol[tx] = e;
   }
   __syncthreads();
   for (int k0 = 0; k0 < Kp; k0 += 64) {
     for (int rr = ty; rr < 64; rr += 8) {
       const int k = k0 + rr;
-      tile[tx][rr] = (k < Kdim && n < live) ? X[(int64_t)k * ldx + n] * scl[tx] : 0.0;
+      tile[tx][rr] = (k < Kdim && n < live) ? X[(int64_t)k * ldx + n] : 0.0;
     }
     __syncthreads();
     for (int cc = 0; cc < 4; ++cc) {
       const int col = ty * 4 + cc;
       if (n0 + col < live)
-        store_slices(tile[col][2 * tx], tile[col][2 * tx + 1], s, Kp,
+        store_slices(tile[col][2 * tx], tile[col][2 * tx + 1], ecol[col], s, Kp,
                      Q + (int64_t)(n0 + col) * s * Kp + k0 + 2 * tx);
     }
     __syncthreads();
