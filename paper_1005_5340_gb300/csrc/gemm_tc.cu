@@ -36,14 +36,16 @@ using namespace ptx;
 constexpr int TC_BM = 128, TC_BK = 64;
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;    // 16 KB per plane
+constexpr int TC_EOCC_MAX = 1024;   // occupied energies staged in shared memory (D(omega) epilogue)
 // The N tile (TMEM columns per accumulator, B box rows, MMA N) is a template
-// parameter, 128 or 64, chosen per product by the autotuner.  A stage holds
+// parameter, 64, 128 or 256, chosen per product by the autotuner; wider tiles
+// read fewer operand bytes per MMA from L2.  A stage holds
 // both planes of the A and B tiles of one 64-deep K block.
 template <int BN> struct TcShape {
   static constexpr uint32_t B_BYTES = BN * TC_BK * 2;
   static constexpr uint32_t STAGE_BYTES = 2 * TC_A_BYTES + 2 * B_BYTES;
-  static constexpr int STAGES = BN == 64 ? 4 : 3;
-  static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int STAGES = BN == 64 ? 4 : (BN == 128 ? 3 : 2);
+  static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256 + TC_EOCC_MAX * 8;
 };
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
@@ -60,10 +62,23 @@ __device__ __forceinline__ void store_split(__nv_bfloat16 *p, int64_t lo_off, fl
 
 // One 16-column chunk of the epilogue: row m (local row lr of the tile),
 // columns n0 + j0 .. n0 + j0 + 15, fused per use.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// kDscaleSplit: the (omega -+ e_F) terms of the chunk's first slot (loaded
+// before the chunk's TMEM read) and the occupied energies (shared memory)
+struct DscaleIn {
+  float4 dt;
+  const float2 *eocc;
+};
+
 template <int EPI>
 __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, int rows_valid,
                                            int atom, int M, int N, int n0, int j0,
-                                           const TcEpilogue &ep) {
+                                           const TcEpilogue &ep, const DscaleIn &di) {
   if (EPI == kStoreF32) {
     if (m < M) {
 #pragma unroll
@@ -141,8 +156,7 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
       const int sl0 = pair0 / ep.n_occ, E0 = pair0 - sl0 * ep.n_occ;
       // (omega -+ e_F) of the chunk's slot as float (hi, lo) pairs,
       // precomputed per (slot, F) for this product
-      float4 dt = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (live) dt = ep.dterm[(int64_t)sl0 * M + m];
+      float4 dt = di.dt;
       int sl = sl0, E = E0;
 #pragma unroll
       for (int j = 0; j < 16; j += 2) {
@@ -151,10 +165,10 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
         float re = 0.f, im = 0.f;
         if (live) {
           if (sl != sl0) dt = ep.dterm[(int64_t)sl * M + m];   // chunk crossing a slot
-          const float2 eE = ep.eocc2[E];
+          const float2 eE = di.eocc[E];
           const float xm = (dt.x + eE.x) + (dt.y + eE.y);
           const float xp = (dt.z - eE.x) + (dt.w - eE.y);
-          const float im2 = __frcp_rn(fmaf(xm, xm, e2)), ip2 = __frcp_rn(fmaf(xp, xp, e2));
+          const float im2 = rcp_approx(fmaf(xm, xm, e2)), ip2 = rcp_approx(fmaf(xp, xp, e2));
           const float dre = occ * (xm * im2 - xp * ip2);
           const float dim = occ * ef * (ip2 - im2);
           re = dre * v[j] - dim * v[j + 1];
@@ -335,6 +349,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of the tile)
     const int q = warp & 3;
     const int lr = q * 32 + lane;
+    const float2 *eocc = ep.eocc2;
+    if (EPI == kDscaleSplit && ep.n_occ <= TC_EOCC_MAX) {
+      // the occupied energies to shared memory (the four epilogue warps)
+      float2 *es = (float2 *)(tslot + 4);
+      for (int i = threadIdx.x - 64; i < ep.n_occ; i += 128) es[i] = ep.eocc2[i];
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      eocc = es;
+    }
     int lt = 0;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
       int m0, xoff, nkb, rows_valid, atom, n0;
@@ -352,9 +374,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int m = m0 + lr;
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN);
       for (int j0 = 0; j0 < TC_BN; j0 += 16) {
+        DscaleIn di;
+        di.eocc = eocc;
+        if (EPI == kDscaleSplit) {
+          const int sl0 = ((n0 + j0) >> 1) / ep.n_occ;
+          di.dt = (m < M && n0 + j0 < N) ? ep.dterm[(int64_t)sl0 * M + m]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         float v[16];
         tmem_ld16(trow + (uint32_t)j0, v);
-        epilogue16<EPI>(v, m, lr, rows_valid, atom, M, N, n0, j0, ep);
+        epilogue16<EPI>(v, m, lr, rows_valid, atom, M, N, n0, j0, ep, di);
       }
       fence_before();
       __syncwarp();
@@ -412,6 +441,7 @@ cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int 
   // box_rows for the A role (128) or the 128-wide B tile; 64 for the 64-wide B tile
   cudaError_t e = encode_bf16_map(&op.map, base, rows, 2 * (int64_t)Kp, box_rows);
   if (e == cudaSuccess) e = encode_bf16_map(&op.map64, base, rows, 2 * (int64_t)Kp, 64);
+  if (e == cudaSuccess) e = encode_bf16_map(&op.map256, base, rows, 2 * (int64_t)Kp, 256);
   if (e != cudaSuccess) return e;
   op.has64 = true;
   op.rows = rows;
@@ -441,6 +471,7 @@ void tc_init_attributes() {
   if (done) return;
   set_attr_all<128>();
   set_attr_all<64>();
+  set_attr_all<256>();
   done = true;
 }
 
@@ -505,6 +536,9 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
   if (bn == 64)
     return launch_tc_epi<64>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, ep, err, dcnt, mul_n,
                              nullptr, n_mtiles);
+  if (bn == 256)
+    return launch_tc_epi<256>(st, epi, M, N, A.map, B.map256, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+                              nullptr, n_mtiles);
   return launch_tc_epi<128>(st, epi, M, N, A.map, B.map, A.Kp, B.Kp, ep, err, dcnt, mul_n, nullptr,
                             n_mtiles);
 }
@@ -519,6 +553,9 @@ cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const Tc
   if (bn == 64)
     return launch_tc_epi<64>(st, epi, 0, N, A.map, B.map64, A.Kp, B.Kp, ep, err, dcnt, mul_n,
                              tiles, n_tiles);
+  if (bn == 256)
+    return launch_tc_epi<256>(st, epi, 0, N, A.map, B.map256, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+                              tiles, n_tiles);
   return launch_tc_epi<128>(st, epi, 0, N, A.map, B.map, A.Kp, B.Kp, ep, err, dcnt, mul_n, tiles,
                             n_tiles);
 }
@@ -598,7 +635,7 @@ extern "C" tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uin
     if (e == cudaSuccess) e = make_operand_map(*opB, Bs, N, Kp, 128);
   }
   // both N-tile widths, each checked against the float64 product
-  for (int bn : {128, 64}) {
+  for (int bn : {128, 64, 256}) {
     if (e == cudaSuccess) {
       cudaMemset(C, 0xFF, (size_t)N * M * sizeof(float));   // NaN: unwritten entries fail
       TcEpilogue ep;

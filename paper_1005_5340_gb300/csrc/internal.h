@@ -152,6 +152,7 @@ enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1, kBetaTSplit = 2, kGammaCatSplit = 
 struct TcOperand {
   CUtensorMap map;     // boxes of 64 x 128 rows
   CUtensorMap map64;   // boxes of 64 x 64 rows (the B operand of the 64-wide tile)
+  CUtensorMap map256;  // boxes of 64 x 256 rows (the B operand of the 256-wide tile)
   bool has64 = false;
   int64_t rows = 0;
   int Kp = 0;
@@ -181,7 +182,7 @@ cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int 
 cudaError_t encode_bf16_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols,
                             int box_rows);
 // dcnt (may be NULL): columns beyond mul_n * (*dcnt) are skipped.
-// bn: N tile of the kernel, 128 or 64.
+// bn: N tile of the kernel, 64, 128 or 256.
 cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
                            int epi, const TcEpilogue &ep, int *err, const int *dcnt = nullptr,
                            int mul_n = 0, int bn = 128);
@@ -227,7 +228,7 @@ struct LpWork {
 };
 
 cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &lp);
-// Time both N tiles on this context's three products (full batch) and keep the faster.
+// Time the N tiles (64, 128, 256) on this context's three products (full batch) and keep the fastest.
 cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp);
 // Out[c][mu] (float64) = Zin - chi0 K Zin (kA) or chi0 Zin (kChi0), reduced precision.
 cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWork &lp, int S,

@@ -274,10 +274,17 @@ cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
       S, sys.n_virt, sys.n_occ, sys.energy, lp.omega, lp.dterm, nullptr);
   int *pick[3] = {&lp.bnK, &lp.bn1, &lp.bn2};
   for (int which = 0; which < 3 && e == cudaSuccess; ++which) {
-    float t128 = 0.f, t64 = 0.f;
+    float t128 = 0.f, t64 = 0.f, t256 = 0.f;
     e = time_one(which, 128, t128);
     if (e == cudaSuccess) e = time_one(which, 64, t64);
-    if (e == cudaSuccess) *pick[which] = (t64 < t128) ? 64 : 128;
+    if (e == cudaSuccess) e = time_one(which, 256, t256);
+    if (e == cudaSuccess) {
+      int bn = 128;
+      float best = t128;
+      if (t64 < best) { bn = 64; best = t64; }
+      if (t256 < best) { bn = 256; best = t256; }
+      *pick[which] = bn;
+    }
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
