@@ -254,8 +254,11 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   const int N = G.n_prod;
   const int m = G.m;
   const int tid = threadIdx.x;
-  const int chunk = (N + P - 1) / P;
+  // element range of this CTA; starts on multiples of 4 (16-byte float4 access)
+  const int chunk = ((N + P - 1) / P + 3) & ~3;
   const int lo = rank * chunk, hi = min(N, lo + chunk);
+  const bool vec4 = sizeof(T) == 4 && (N & 3) == 0;
+  const int n4 = max(0, hi - lo) >> 2;
   const double *win = Wout + (int64_t)2 * s * N;
   T *Vr = basis<T>(G) + (int64_t)r * (m + 1) * 2 * N;
   const int state = G.state[r];
@@ -339,9 +342,19 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   // Gram and Hessenberg algebra stay float64), float64 otherwise.
   const T *aw;   // A v_j in type T
   if constexpr (sizeof(T) == 4) {
-    for (int e = lo + tid; e < hi; e += NT) {
-      w[e] = (T)win[e];
-      w[N + e] = (T)win[N + e];
+    if (vec4) {
+      const double2 *wr2 = (const double2 *)(win + lo), *wi2 = (const double2 *)(win + N + lo);
+      float4 *o_r = (float4 *)(w + lo), *o_i = (float4 *)(w + N + lo);
+      for (int q = tid; q < n4; q += NT) {
+        const double2 a = wr2[2 * q], b = wr2[2 * q + 1], c = wi2[2 * q], d = wi2[2 * q + 1];
+        o_r[q] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+        o_i[q] = make_float4((float)c.x, (float)c.y, (float)d.x, (float)d.y);
+      }
+    } else {
+      for (int e = lo + tid; e < hi; e += NT) {
+        w[e] = (T)win[e];
+        w[N + e] = (T)win[N + e];
+      }
     }
     __syncthreads();
     aw = w;
@@ -351,15 +364,34 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   for (int i = warp; i <= j; i += NT / 32) {
     const T *vi_ = Vr + (int64_t)i * 2 * N;
     T pr = 0, pim = 0, gr = 0, gim = 0;
+    if (vec4) {
+      // four elements per lane and load (float32 basis)
+      const float4 *v_r = (const float4 *)(vi_ + lo), *v_i = (const float4 *)(vi_ + N + lo);
+      const float4 *w_r = (const float4 *)(aw + lo), *w_i = (const float4 *)(aw + N + lo);
+      const float4 *j_r = (const float4 *)(vj + lo), *j_i = (const float4 *)(vj + N + lo);
+#pragma unroll 1
+      for (int q = lane; q < n4; q += 32) {
+        const float4 a = v_r[q], b = v_i[q], c = w_r[q], d = w_i[q], f = j_r[q], g = j_i[q];
+        pr = fmaf(a.x, c.x, fmaf(b.x, d.x, fmaf(a.y, c.y, fmaf(b.y, d.y,
+             fmaf(a.z, c.z, fmaf(b.z, d.z, fmaf(a.w, c.w, fmaf(b.w, d.w, pr))))))));
+        pim = fmaf(a.x, d.x, fmaf(-b.x, c.x, fmaf(a.y, d.y, fmaf(-b.y, c.y,
+              fmaf(a.z, d.z, fmaf(-b.z, c.z, fmaf(a.w, d.w, fmaf(-b.w, c.w, pim))))))));
+        gr = fmaf(a.x, f.x, fmaf(b.x, g.x, fmaf(a.y, f.y, fmaf(b.y, g.y,
+             fmaf(a.z, f.z, fmaf(b.z, g.z, fmaf(a.w, f.w, fmaf(b.w, g.w, gr))))))));
+        gim = fmaf(a.x, g.x, fmaf(-b.x, f.x, fmaf(a.y, g.y, fmaf(-b.y, f.y,
+              fmaf(a.z, g.z, fmaf(-b.z, f.z, fmaf(a.w, g.w, fmaf(-b.w, f.w, gim))))))));
+      }
+    } else {
 #pragma unroll 4
-    for (int e = lo + lane; e < hi; e += 32) {
-      const T wr = aw[e], wi = aw[N + e];
-      const T ar = vj[e], ai = vj[N + e];
-      const T vr = vi_[e], vi = vi_[N + e];
-      pr = fma(vr, wr, fma(vi, wi, pr));
-      pim = fma(vr, wi, fma(-vi, wr, pim));
-      gr = fma(vr, ar, fma(vi, ai, gr));
-      gim = fma(vr, ai, fma(-vi, ar, gim));
+      for (int e = lo + lane; e < hi; e += 32) {
+        const T wr = aw[e], wi = aw[N + e];
+        const T ar = vj[e], ai = vj[N + e];
+        const T vr = vi_[e], vi = vi_[N + e];
+        pr = fma(vr, wr, fma(vi, wi, pr));
+        pim = fma(vr, wi, fma(-vi, wr, pim));
+        gr = fma(vr, ar, fma(vi, ai, gr));
+        gim = fma(vr, ai, fma(-vi, ar, gim));
+      }
     }
     double dpr = pr, dpim = pim, dgr = gr, dgim = gim;
 #pragma unroll
@@ -428,7 +460,36 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   for (int i = tid; i <= j; i += NT) hT[i] = make_float2((float)hs[i].x, (float)hs[i].y);
   __syncthreads();
   double n1[1] = {0.0};
-  {
+  if (vec4) {
+    // four elements per thread and load (float32 basis); w holds A v_j here
+    float nacc = 0.f;
+    float4 *w_r = (float4 *)(w + lo), *w_i = (float4 *)(w + N + lo);
+    for (int q = tid; q < n4; q += NT) {
+      float4 ar = make_float4(0.f, 0.f, 0.f, 0.f), ai = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+      for (int i = 0; i <= j; ++i) {
+        const float *vi_ = (const float *)(Vr + (int64_t)i * 2 * N);
+        const float4 a = ((const float4 *)(vi_ + lo))[q], b = ((const float4 *)(vi_ + N + lo))[q];
+        const float hx = hT[i].x, hy = hT[i].y;
+        ar.x = fmaf(hx, a.x, fmaf(-hy, b.x, ar.x));
+        ar.y = fmaf(hx, a.y, fmaf(-hy, b.y, ar.y));
+        ar.z = fmaf(hx, a.z, fmaf(-hy, b.z, ar.z));
+        ar.w = fmaf(hx, a.w, fmaf(-hy, b.w, ar.w));
+        ai.x = fmaf(hx, b.x, fmaf(hy, a.x, ai.x));
+        ai.y = fmaf(hx, b.y, fmaf(hy, a.y, ai.y));
+        ai.z = fmaf(hx, b.z, fmaf(hy, a.z, ai.z));
+        ai.w = fmaf(hx, b.w, fmaf(hy, a.w, ai.w));
+      }
+      const float4 c = w_r[q], d = w_i[q];
+      const float4 nr = make_float4(c.x - ar.x, c.y - ar.y, c.z - ar.z, c.w - ar.w);
+      const float4 ni = make_float4(d.x - ai.x, d.y - ai.y, d.z - ai.z, d.w - ai.w);
+      w_r[q] = nr;
+      w_i[q] = ni;
+      nacc += nr.x * nr.x + nr.y * nr.y + nr.z * nr.z + nr.w * nr.w + ni.x * ni.x +
+              ni.y * ni.y + ni.z * ni.z + ni.w * ni.w;
+    }
+    n1[0] = (double)nacc;
+  } else {
     T nacc = 0;
     for (int e = lo + tid; e < hi; e += NT) {
       T ar = 0, ai = 0;
@@ -565,15 +626,51 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   }
   if (!finish_flag) {
     const T inv = (T)(1.0 / hn);
-    for (int e = lo + tid; e < hi; e += NT) {
-      w[e] *= inv;
-      w[N + e] *= inv;
+    if (vec4) {
+      float4 *w_r = (float4 *)(w + lo), *w_i = (float4 *)(w + N + lo);
+      const float fi = (float)inv;
+      for (int q = tid; q < n4; q += NT) {
+        float4 a = w_r[q], b = w_i[q];
+        a.x *= fi; a.y *= fi; a.z *= fi; a.w *= fi;
+        b.x *= fi; b.y *= fi; b.z *= fi; b.w *= fi;
+        w_r[q] = a;
+        w_i[q] = b;
+      }
+    } else {
+      for (int e = lo + tid; e < hi; e += NT) {
+        w[e] *= inv;
+        w[N + e] *= inv;
+      }
     }
   } else {
     const int k = j + 1;
     double *x = G.x + (int64_t)2 * r * N;
     for (int i = tid; i < k; i += NT) hT[i] = make_float2((float)ys[i].x, (float)ys[i].y);
     __syncthreads();
+    if (vec4) {
+      double2 *x_r = (double2 *)(x + lo), *x_i = (double2 *)(x + N + lo);
+      for (int q = tid; q < n4; q += NT) {
+        float4 ar = make_float4(0.f, 0.f, 0.f, 0.f), ai = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+        for (int i = 0; i < k; ++i) {
+          const float *vi_ = (const float *)(Vr + (int64_t)i * 2 * N);
+          const float4 a = ((const float4 *)(vi_ + lo))[q], b = ((const float4 *)(vi_ + N + lo))[q];
+          const float yx = hT[i].x, yy = hT[i].y;
+          ar.x = fmaf(yx, a.x, fmaf(-yy, b.x, ar.x));
+          ar.y = fmaf(yx, a.y, fmaf(-yy, b.y, ar.y));
+          ar.z = fmaf(yx, a.z, fmaf(-yy, b.z, ar.z));
+          ar.w = fmaf(yx, a.w, fmaf(-yy, b.w, ar.w));
+          ai.x = fmaf(yx, b.x, fmaf(yy, a.x, ai.x));
+          ai.y = fmaf(yx, b.y, fmaf(yy, a.y, ai.y));
+          ai.z = fmaf(yx, b.z, fmaf(yy, a.z, ai.z));
+          ai.w = fmaf(yx, b.w, fmaf(yy, a.w, ai.w));
+        }
+        double2 p0 = x_r[2 * q], p1 = x_r[2 * q + 1], q0 = x_i[2 * q], q1 = x_i[2 * q + 1];
+        p0.x += (double)ar.x; p0.y += (double)ar.y; p1.x += (double)ar.z; p1.y += (double)ar.w;
+        q0.x += (double)ai.x; q0.y += (double)ai.y; q1.x += (double)ai.z; q1.y += (double)ai.w;
+        x_r[2 * q] = p0; x_r[2 * q + 1] = p1; x_i[2 * q] = q0; x_i[2 * q + 1] = q1;
+      }
+    } else
     for (int e = lo + tid; e < hi; e += NT) {
       T ar = 0, ai = 0;
 #pragma unroll 4
