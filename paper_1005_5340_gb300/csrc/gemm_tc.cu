@@ -81,10 +81,19 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
                                            const TcEpilogue &ep, const DscaleIn &di) {
   if (EPI == kStoreF32) {
     if (m < M) {
+      if (ep.ksplit > 1) {
+        // two K halves add into the zeroed output (0 + a + b: either order)
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int n = n0 + j0 + j;
-        if (n < N) ep.outF[(int64_t)n * ep.ldo + m] = v[j];
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + j0 + j;
+          if (n < N) atomicAdd(ep.outF + (int64_t)n * ep.ldo + m, v[j]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + j0 + j;
+          if (n < N) ep.outF[(int64_t)n * ep.ldo + m] = v[j];
+        }
       }
     }
   } else if (EPI == kPartialF32) {
@@ -206,7 +215,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // graph replays: columns beyond the live count are skipped (whole tiles)
   if (dcnt) N = (int)min((int64_t)N, (int64_t)mul_n * (*dcnt));
   const int n_ntiles = (N + TC_BN - 1) / TC_BN;
-  const int n_tiles = n_mtiles * n_ntiles;
+  const int ksplit = ep.ksplit;
+  const int n_tiles = n_mtiles * n_ntiles * ksplit;
   if ((int)blockIdx.x >= n_tiles) return;
   constexpr uint32_t SB = TcShape<TC_BN>::STAGE_BYTES;
   constexpr int NS = TcShape<TC_BN>::STAGES;
@@ -222,20 +232,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto tile_of = [&](int t, int &m0, int &xoff, int &nkb, int &rows_valid, int &atom, int &n0) {
-    const int mt = t % n_mtiles, nt = t / n_mtiles;
+  // tile t: M tile fastest, then the K slice (split K), then the N tile;
+  // xa / xb: K offsets (elements) of the A and B tiles within a plane
+  auto tile_of = [&](int t, int &m0, int &xa, int &xb, int &nkb, int &rows_valid, int &atom,
+                     int &n0) {
+    const int mt = t % n_mtiles, rest = t / n_mtiles;
+    const int ks = rest % ksplit, nt = rest / ksplit;
     n0 = nt * TC_BN;
     if (tiles) {
       const GTile g = tiles[mt];
       m0 = g.row0;
-      xoff = g.xoff;
+      xa = 0;
+      xb = g.xoff;
       nkb = g.nkb;
       rows_valid = g.rows;
       atom = g.atom;
     } else {
+      const int nkb_all = KpA / TC_BK;
+      const int kb0 = ks * nkb_all / ksplit, kb1 = (ks + 1) * nkb_all / ksplit;
       m0 = mt * TC_BM;
-      xoff = 0;
-      nkb = KpA / TC_BK;
+      xa = kb0 * TC_BK;
+      xb = kb0 * TC_BK;
+      nkb = kb1 - kb0;
       rows_valid = min(TC_BM, M - m0);
       atom = -1;
     }
@@ -270,8 +288,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        int m0, xoff, nkb, rv, at, n0;
-        tile_of(t, m0, xoff, nkb, rv, at, n0);
+        int m0, xa, xoff, nkb, rv, at, n0;
+        tile_of(t, m0, xa, xoff, nkb, rv, at, n0);
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % NS;
           const uint32_t ph = (uint32_t)(g / NS) & 1u;
@@ -287,8 +305,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           uint8_t *st = smem + s * SB;
           mbar_expect_tx(&full[s], SB);
-          tma_load_2d(st, &mapA, &full[s], kb * TC_BK, m0);                          // A_hi
-          tma_load_2d(st + TC_A_BYTES, &mapA, &full[s], KpA + kb * TC_BK, m0);       // A_lo
+          tma_load_2d(st, &mapA, &full[s], xa + kb * TC_BK, m0);                     // A_hi
+          tma_load_2d(st + TC_A_BYTES, &mapA, &full[s], KpA + xa + kb * TC_BK, m0);  // A_lo
           tma_load_2d(st + 2 * TC_A_BYTES, &mapB, &full[s], xoff + kb * TC_BK, n0);  // B_hi
           tma_load_2d(st + 2 * TC_A_BYTES + B_BYTES, &mapB, &full[s], KpB + xoff + kb * TC_BK,
                       n0);                                                            // B_lo
@@ -307,8 +325,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int g = 0, lt = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++lt) {
-        int m0, xoff, nkb, rv, at, n0;
-        tile_of(t, m0, xoff, nkb, rv, at, n0);
+        int m0, xa, xoff, nkb, rv, at, n0;
+        tile_of(t, m0, xa, xoff, nkb, rv, at, n0);
         const int buf = lt & 1, use = lt >> 1;
         if (use > 0) {
           // the epilogue has drained this buffer's previous tile
@@ -359,8 +377,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     int lt = 0;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
-      int m0, xoff, nkb, rows_valid, atom, n0;
-      tile_of(t, m0, xoff, nkb, rows_valid, atom, n0);
+      int m0, xa, xoff, nkb, rows_valid, atom, n0;
+      tile_of(t, m0, xa, xoff, nkb, rows_valid, atom, n0);
       const int buf = lt & 1, use = lt >> 1;
       bool have = mbar_wait(&tfull[buf], (uint32_t)use & 1u);
       // tcgen05.ld is warp-collective: one decision per warp
@@ -501,7 +519,7 @@ cudaError_t launch_tc_epi(cudaStream_t st, int epi, int M, int N, const CUtensor
                           const CUtensorMap &mB, int KpA, int KpB, const TcEpilogue &ep, int *err,
                           const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
   // persistent: one CTA per SM at most, each walking its share of the tiles
-  const int64_t n_tiles = (int64_t)n_mtiles * ((N + BN - 1) / BN);
+  const int64_t n_tiles = (int64_t)n_mtiles * ((N + BN - 1) / BN) * ep.ksplit;
   const int grid = (int)std::min<int64_t>(n_tiles, sm_count());
   switch (epi) {
     case kStoreF32:
@@ -533,13 +551,22 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
   tc_init_attributes();
   if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
   const int n_mtiles = (M + TC_BM - 1) / TC_BM;
+  TcEpilogue e = ep;
+  e.ksplit = 1;
+  if (epi == kStoreF32 && ep.split_ok && A.Kp / TC_BK >= 32 &&
+      (int64_t)n_mtiles * ((N + bn - 1) / bn) < 2 * (int64_t)sm_count()) {
+    // too few tiles for the SMs: two K halves, added into the zeroed output
+    e.ksplit = 2;
+    cudaError_t r = cudaMemsetAsync(ep.outF, 0, (size_t)N * ep.ldo * sizeof(float), st);
+    if (r != cudaSuccess) return r;
+  }
   if (bn == 64)
-    return launch_tc_epi<64>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+    return launch_tc_epi<64>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, e, err, dcnt, mul_n,
                              nullptr, n_mtiles);
   if (bn == 256)
-    return launch_tc_epi<256>(st, epi, M, N, A.map, B.map256, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+    return launch_tc_epi<256>(st, epi, M, N, A.map, B.map256, A.Kp, B.Kp, e, err, dcnt, mul_n,
                               nullptr, n_mtiles);
-  return launch_tc_epi<128>(st, epi, M, N, A.map, B.map, A.Kp, B.Kp, ep, err, dcnt, mul_n, nullptr,
+  return launch_tc_epi<128>(st, epi, M, N, A.map, B.map, A.Kp, B.Kp, e, err, dcnt, mul_n, nullptr,
                             n_mtiles);
 }
 
@@ -550,13 +577,15 @@ cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const Tc
   if (n_tiles <= 0 || N <= 0) return cudaSuccess;
   tc_init_attributes();
   if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
+  TcEpilogue e = ep;
+  e.ksplit = 1;
   if (bn == 64)
-    return launch_tc_epi<64>(st, epi, 0, N, A.map, B.map64, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+    return launch_tc_epi<64>(st, epi, 0, N, A.map, B.map64, A.Kp, B.Kp, e, err, dcnt, mul_n,
                              tiles, n_tiles);
   if (bn == 256)
-    return launch_tc_epi<256>(st, epi, 0, N, A.map, B.map256, A.Kp, B.Kp, ep, err, dcnt, mul_n,
+    return launch_tc_epi<256>(st, epi, 0, N, A.map, B.map256, A.Kp, B.Kp, e, err, dcnt, mul_n,
                               tiles, n_tiles);
-  return launch_tc_epi<128>(st, epi, 0, N, A.map, B.map, A.Kp, B.Kp, ep, err, dcnt, mul_n, tiles,
+  return launch_tc_epi<128>(st, epi, 0, N, A.map, B.map, A.Kp, B.Kp, e, err, dcnt, mul_n, tiles,
                             n_tiles);
 }
 

@@ -171,6 +171,8 @@ struct TcEpilogue {
   double eps = 0.0;
   double occ_value = 0.0;
   int n_occ = 0;
+  int split_ok = 0;                // kStoreF32: the launch may split K in two (adds into outF)
+  int ksplit = 1;                  // set by the launcher
   const int *aoff = nullptr;       // kBetaTSplit, kGammaCatSplit
   const int *orb_atom = nullptr;   // kGammaCatSplit
   const int *xoff5 = nullptr;      // kGammaCatSplit

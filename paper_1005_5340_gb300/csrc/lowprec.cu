@@ -316,6 +316,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
       Scope sc(lp.timer, st, kcTcK, 2.0 * ncols * (double)np * np);
       ep.outF = lp.Yt;
       ep.ldo = np;
+      ep.split_ok = 1;
       err = launch_gemm_tc(st, lp.opK, lp.opZ, np, ncols, kStoreF32, ep, lp.err, lp.dcnt, 2,
                            lp.bnK);
       if (err != cudaSuccess) return err;
