@@ -367,15 +367,17 @@ def run_ours(args):
     value = total_points / (ms_max / 1e3)
 
     # end to end through the public API with host buffers
-    e2e_steps = max(1, args.e2e_steps)
-    host_groups = [omega[g] for g in groups]
+    # the same groups as the timed steps, from pinned host memory through the
+    # public call (omega in, P out), host wall clock
+    e2e_steps = args.e2e_steps or args.steps
+    host_groups = [torch.tensor(omega[g], dtype=torch.float64).pin_memory() for g in groups]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_points = 0
     for i in range(e2e_steps):
-        g = host_groups[i % len(host_groups)]
+        g = host_groups[(args.warmup + i) % len(host_groups)]
         P, info = ctx.polarizability(g, w["eps"])
-        e2e_points += g.size
+        e2e_points += g.numel()
     dt = time.perf_counter() - t0
     e2e = {"value": world * e2e_points / dt, "unit": "omega-points/s",
            "h2d_bytes_per_step": int(8 * per_step),

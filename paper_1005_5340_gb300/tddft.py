@@ -301,6 +301,16 @@ class Context:
             st = self._lib.tddft_polarizability(self.h, n, om.data_ptr(), float(eps),
                                                 torch.view_as_real(P).data_ptr(), stats,
                                                 DEVICE_PTRS)
+        elif _is_torch(omega):
+            # host tensors (pinned ones are copied without staging); P in pinned memory
+            import torch
+            om = omega.to(torch.float64).contiguous()
+            n = om.numel()
+            P = torch.empty((n, 3, 3), dtype=torch.complex128,
+                            pin_memory=torch.cuda.is_available())
+            stats = (SolveStats * (3 * n))()
+            st = self._lib.tddft_polarizability(self.h, n, om.data_ptr(), float(eps),
+                                                torch.view_as_real(P).data_ptr(), stats, 0)
         else:
             om = np.ascontiguousarray(np.atleast_1d(omega), dtype=np.float64)
             n = om.size
