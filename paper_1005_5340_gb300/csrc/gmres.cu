@@ -393,17 +393,18 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
         gim = fma(vr, ai, fma(-vi, ar, gim));
       }
     }
-    double dpr = pr, dpim = pim, dgr = gr, dgim = gim;
+    // across the warp in type T (the float32 basis: float64 shuffles would load
+    // the FP64 pipe with every vector), then float64 per warp
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      dpr += __shfl_xor_sync(0xffffffffu, dpr, off);
-      dpim += __shfl_xor_sync(0xffffffffu, dpim, off);
-      dgr += __shfl_xor_sync(0xffffffffu, dgr, off);
-      dgim += __shfl_xor_sync(0xffffffffu, dgim, off);
+      pr += __shfl_xor_sync(0xffffffffu, pr, off);
+      pim += __shfl_xor_sync(0xffffffffu, pim, off);
+      gr += __shfl_xor_sync(0xffffffffu, gr, off);
+      gim += __shfl_xor_sync(0xffffffffu, gim, off);
     }
     if (lane == 0) {
-      hq[i] = make_double2(dpr, dpim);
-      gq[i] = make_double2(dgr, dgim);
+      hq[i] = make_double2((double)pr, (double)pim);
+      gq[i] = make_double2((double)gr, (double)gim);
     }
   }
   if (P == 1) {
@@ -488,7 +489,8 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
       nacc += nr.x * nr.x + nr.y * nr.y + nr.z * nr.z + nr.w * nr.w + ni.x * ni.x +
               ni.y * ni.y + ni.z * ni.z + ni.w * ni.w;
     }
-    n1[0] = (double)nacc;
+    for (int off = 16; off > 0; off >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, off);
+    n1[0] = lane == 0 ? (double)nacc : 0.0;   // the block sum adds the warps' totals
   } else {
     T nacc = 0;
     for (int e = lo + tid; e < hi; e += NT) {
