@@ -398,8 +398,7 @@ def run_ours(args):
     if args.graph:
         gpu_launches = int(round(gpu_launches * args.steps))
     chi_cls = ["f64_vertex", "f64_beta", "f64_gemm_T1", "f64_dscale", "f64_gemm_T2",
-               "f64_block_dot", "lp_vertex", "lp_beta", "tc_gemm_T1_dscale", "tc_gemm_T2",
-               "lp_block_dot", "emu_gemm_T1", "emu_gemm_T2", "alpha_gather", "tc_alpha_beta",
+               "f64_block_dot", "tc_gemm_T1_dscale", "tc_gemm_T2", "emu_gemm_T1", "emu_gemm_T2", "alpha_gather", "tc_alpha_beta",
                "tc_alpha_dot", "emu_alpha_beta", "emu_alpha_dot"]
     chi_ms = sum(timing[c]["ms"] for c in chi_cls)
     n_virt = s.n_orb - s.n_occ

@@ -6,9 +6,7 @@
 // One CTA handles one block and 16 columns; each thread owns a 4 x 4 (a, b)
 // tile of one column, so every shared-memory operand feeds two FMAs per
 // load, and each vertex block is read once for 16 columns in the dot phase.
-// Templated on the arithmetic type (float64 path, float32 path) and on the
-// layout of gamma: [n_orb][ncols][n_occ] (float64 path) or
-// [(s n_occ + E) 2 + p][n_orb] (float32 path, c = 2 s + p).
+// float64 throughout; gamma is laid out [n_orb][ncols][n_occ].
 #include "internal.h"
 
 namespace tddft {
@@ -16,15 +14,15 @@ namespace {
 
 constexpr int BD_COLS = 16;
 
-template <class T, bool GAMMA_T>
 __global__ void __launch_bounds__(256, 2) block_dot_kernel(
     int ncols, int n_occ, int n_prod, int n_orb, const int *__restrict__ aoff,
     const int2 *__restrict__ blk_atoms, const int *__restrict__ blk_ptr,
-    const int *__restrict__ blk_prod, const T *__restrict__ Vpad, const T *__restrict__ Xo,
-    const T *__restrict__ gamma, const double *__restrict__ Zin, int subtract,
+    const int *__restrict__ blk_prod, const double *__restrict__ Vpad,
+    const double *__restrict__ Xo, const double *__restrict__ gamma, const double *__restrict__ Zin, int subtract,
     double *__restrict__ Out, const int *__restrict__ dcnt) {
-  // E-slices of 16 (float) or 8 (double) keep the static shared memory < 48 KB
-  constexpr int BD_E = sizeof(T) == 8 ? 8 : 16;
+  using T = double;
+  // E-slices of 8 keep the static shared memory < 48 KB
+  constexpr int BD_E = 8;
   __shared__ T XA[BD_E][kMaxOrb + 1], XB[BD_E][kMaxOrb + 1];
   // gamma slices of the A and B rows, [2][BD_COLS][BD_E][kMaxOrb + 1], reused for G
   __shared__ T gbuf[2 * BD_COLS * BD_E * (kMaxOrb + 1)];
@@ -63,29 +61,15 @@ __global__ void __launch_bounds__(256, 2) block_dot_kernel(
       XB[e][r] = (r < nB && E < n_occ) ? Xo[(int64_t)(aoB + r) * n_occ + E] : T(0);
     }
     for (int i = t; i < BD_COLS * BD_E * kMaxOrb; i += 256) {
-      int c, e, r;
-      if (GAMMA_T) {   // r fastest: contiguous in gamma^T
-        c = i / (BD_E * kMaxOrb);
-        const int rem = i % (BD_E * kMaxOrb);
-        e = rem / kMaxOrb;
-        r = rem % kMaxOrb;
-      } else {         // e fastest: contiguous in gamma
-        c = i / (BD_E * kMaxOrb);
-        const int rem = i % (BD_E * kMaxOrb);
-        r = rem / BD_E;
-        e = rem % BD_E;
-      }
+      // e fastest: contiguous in gamma
+      const int c = i / (BD_E * kMaxOrb);
+      const int rem = i % (BD_E * kMaxOrb);
+      const int r = rem / BD_E, e = rem % BD_E;
       const int E = E0 + e, cc = c0 + c;
       T va = T(0), vb = T(0);
       if (cc < nact && E < n_occ) {
-        if (GAMMA_T) {
-          const int64_t row = ((int64_t)(cc >> 1) * n_occ + E) * 2 + (cc & 1);
-          if (r < nA) va = gamma[row * n_orb + aoA + r];
-          if (r < nB) vb = gamma[row * n_orb + aoB + r];
-        } else {
-          if (r < nA) va = gamma[((int64_t)(aoA + r) * ncols + cc) * n_occ + E];
-          if (r < nB) vb = gamma[((int64_t)(aoB + r) * ncols + cc) * n_occ + E];
-        }
+        if (r < nA) va = gamma[((int64_t)(aoA + r) * ncols + cc) * n_occ + E];
+        if (r < nB) vb = gamma[((int64_t)(aoB + r) * ncols + cc) * n_occ + E];
       }
       gA(c, e, r) = va;
       gB(c, e, r) = vb;
@@ -145,26 +129,21 @@ __global__ void __launch_bounds__(256, 2) block_dot_kernel(
       if (lane == c) mine = part[c];
     if (lane < BD_COLS && c0 + lane < nact) {
       const int64_t o = (int64_t)(c0 + lane) * n_prod + mu;
-      Out[o] = subtract ? Zin[o] - (double)mine : (double)mine;
+      Out[o] = subtract ? Zin[o] - mine : mine;
     }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_block_dot(cudaStream_t st, bool f64, int ncols, const DevSystem &sys,
-                             const void *Vpad, const void *Xo, const void *gamma,
+cudaError_t launch_block_dot(cudaStream_t st, int ncols, const DevSystem &sys,
+                             const double *Vpad, const double *Xo, const double *gamma,
                              const double *Zin, int subtract, double *Out, const int *dcnt) {
   dim3 grid(sys.n_blocks, (ncols + BD_COLS - 1) / BD_COLS);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  if (f64)
-    block_dot_kernel<double, false><<<grid, 256, 0, st>>>(
-        ncols, sys.n_occ, sys.n_prod, sys.n_orb, sys.aoff, sys.blk_atoms, sys.blk_ptr, sys.blk_prod,
-        (const double *)Vpad, (const double *)Xo, (const double *)gamma, Zin, subtract, Out, dcnt);
-  else
-    block_dot_kernel<float, true><<<grid, 256, 0, st>>>(
-        ncols, sys.n_occ, sys.n_prod, sys.n_orb, sys.aoff, sys.blk_atoms, sys.blk_ptr, sys.blk_prod,
-        (const float *)Vpad, (const float *)Xo, (const float *)gamma, Zin, subtract, Out, dcnt);
+  block_dot_kernel<<<grid, 256, 0, st>>>(ncols, sys.n_occ, sys.n_prod, sys.n_orb, sys.aoff,
+                                         sys.blk_atoms, sys.blk_ptr, sys.blk_prod, Vpad, Xo,
+                                         gamma, Zin, subtract, Out, dcnt);
   return cudaGetLastError();
 }
 

@@ -52,8 +52,8 @@ struct DevSystem {
 enum KernelClass {
   // float64 operator
   kcGemmK = 0, kcVertex, kcBeta, kcGemmT1, kcDscale, kcGemmT2, kcSddmm,
-  // reduced-precision operator (tensor-core GEMMs, float32 sparse kernels)
-  kcTcK, kcLpVertex, kcLpBeta, kcTcT1, kcTcT2, kcLpSddmm, kcLpSplit,
+  // reduced-precision operator (split-bf16 tensor-core GEMMs)
+  kcTcK, kcTcT1, kcTcT2, kcLpSplit,
   // solver
   kcGmresStep, kcGmresGather, kcGmresSelect, kcRhs, kcMisc,
   // float64 products emulated on the tensor cores (integer slices)
@@ -126,10 +126,9 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
 cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &wk, int S, int g0,
                                  const double *omega_all, double eps, double *Z3, double *a3,
                                  double *Out);
-// Step 5 (block dots) for ncols real columns: float64 (gamma [n_orb][ncols][n_occ],
-// Vpad/Xo double) or float32 (gamma^T [(s n_occ+E) 2+p][n_orb], Vpad/Xo float).
-cudaError_t launch_block_dot(cudaStream_t st, bool f64, int ncols, const DevSystem &sys,
-                             const void *Vpad, const void *Xo, const void *gamma,
+// Step 5 (block dots) for ncols real columns in float64, gamma [n_orb][ncols][n_occ].
+cudaError_t launch_block_dot(cudaStream_t st, int ncols, const DevSystem &sys,
+                             const double *Vpad, const double *Xo, const double *gamma,
                              const double *Zin, int subtract, double *Out, const int *dcnt);
 cudaError_t launch_interleaved_to_planar(cudaStream_t st, int n_rhs, int n, const double *in,
                                          double *out);
@@ -210,14 +209,10 @@ struct LpWork {
   __nv_bfloat16 *Ks = nullptr;     // [n_prod][2 KpK]   K split
   __nv_bfloat16 *XvTs = nullptr;   // [n_virt][2 Kp1]   X_virt^T split
   __nv_bfloat16 *Xvs = nullptr;    // [n_orb][2 Kp2]    X_virt split
-  float *Xo32 = nullptr;           // [n_orb][n_occ]
-  float *Vpad32 = nullptr;         // [n_prod][kBlk]
   __nv_bfloat16 *Zb = nullptr;     // [2S][2 KpK]       operator input, split
   float *Yt = nullptr;             // [2S][n_prod]      K z
-  float *W = nullptr;              // [2S][n_blocks][kBlk]
   __nv_bfloat16 *betaT = nullptr;  // [2 S n_occ][2 Kp1], row (s*n_occ+E)*2+p
   __nv_bfloat16 *aT = nullptr;     // [2 S n_occ][2 Kp2]
-  float *gammaT = nullptr;         // [2 S n_occ][n_orb]
   double *omega = nullptr;         // [S]
   int *err = nullptr;              // [1] device-side error code of the GEMM waits
   float2 *eocc2 = nullptr;         // [n_occ] occupied energies as float (hi, lo)

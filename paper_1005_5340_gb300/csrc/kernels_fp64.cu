@@ -575,7 +575,7 @@ cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &
                           ncolE, wk.gamma, ncolE);
   }
   if (err != cudaSuccess) return err;
-  return launch_block_dot(st, true, 2 * S, sys, sys.Vpad, sys.Xo, wk.gamma, nullptr, 0, Out,
+  return launch_block_dot(st, 2 * S, sys, sys.Vpad, sys.Xo, wk.gamma, nullptr, 0, Out,
                           nullptr);
 }
 
@@ -660,7 +660,7 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
   }
   {
     Scope sc(wk.timer, st, kcSddmm, ncols * sys.sf.dot);
-    err = launch_block_dot(st, true, ncols, sys, sys.Vpad, sys.Xo, wk.gamma, Zin,
+    err = launch_block_dot(st, ncols, sys, sys.Vpad, sys.Xo, wk.gamma, Zin,
                            mode == kA ? 1 : 0, Out, wk.dcnt);
     if (err != cudaSuccess) return err;
   }

@@ -1,16 +1,15 @@
 // Reduced-precision application of A(omega) z = z - chi0(omega) (K z)
-// (Sec. 4.1, with chi0 . y by the re-associated steps of Sec. 4.2) used for
-// the inner GMRES iterations of the refinement forms.  The three dense
-// products (K z, X_virt^T beta, X_virt a) run on the tensor cores in split
-// bf16 with float32 accumulation (gemm_tc.cu); the block-sparse vertex
-// contractions run in float32 on the CUDA cores.  Layouts (n = right-hand-side
-// column, complex planes interleaved per occupied state):
+// (Sec. 4.1, chi0 . y by steps 1-5 of Table t:flops on the stored transition
+// vertex) used for the inner GMRES iterations of the refinement forms.  Every
+// product runs on the tensor cores in split bf16 with float32 accumulation
+// (gemm_tc.cu): K z, step 2 (per atom, alpha.cu), X_virt^T beta with the
+// D(omega) epilogue, X_virt a into the per-atom Gcat rows, step 5 (per atom).
+// Layouts (n = right-hand-side column, complex planes interleaved per
+// occupied state):
 //   Zb     [2S][2 KpK]          z split, row c = 2 s + p
 //   Yt     [2S][n_prod]         K z
-//   W      [2S][nb][16x16]      sum_nu y^nu V_nu per block
 //   betaT  [2 S n_occ][2 Kp1]   beta^T split, row (s n_occ + E) 2 + p
 //   aT     [2 S n_occ][2 Kp2]   (D . X_virt^T beta)^T split
-//   gammaT [2 S n_occ][n_orb]   (X_virt a)^T
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -81,126 +80,6 @@ __global__ void dterm_kernel(int S, int n_virt, int n_occ, const double *__restr
   }
 }
 
-__global__ void to_f32_kernel(const double *__restrict__ src, int64_t n, float *__restrict__ dst) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (float)src[i];
-}
-
-template <class TIn>
-__global__ void __launch_bounds__(256) lp_vertex(int nb, int ncols, int n_prod,
-                                                 const int *__restrict__ blk_ptr,
-                                                 const int *__restrict__ blk_prod,
-                                                 const float *__restrict__ Vpad,
-                                                 const TIn *__restrict__ Y, float *__restrict__ W,
-                                                 const int *__restrict__ dcnt) {
-  constexpr int COLS = 8;
-  __shared__ float ys[32][COLS];
-  const int k = blockIdx.x;
-  const int c0 = blockIdx.y * COLS;
-  if (dcnt) ncols = min(ncols, 2 * *dcnt);
-  if (c0 >= ncols) return;
-  const int t = threadIdx.x;
-  const int p0 = blk_ptr[k], p1 = blk_ptr[k + 1];
-  float acc[COLS];
-#pragma unroll
-  for (int c = 0; c < COLS; ++c) acc[c] = 0.f;
-  for (int q0 = p0; q0 < p1; q0 += 32) {
-    __syncthreads();
-    {
-      const int pp = t / COLS, c = t % COLS;
-      const int q = q0 + pp;
-      ys[pp][c] = (q < p1 && c0 + c < ncols) ? (float)Y[(int64_t)(c0 + c) * n_prod + blk_prod[q]] : 0.f;
-    }
-    __syncthreads();
-    const int qn = min(32, p1 - q0);
-    for (int pp = 0; pp < qn; ++pp) {
-      const float v = Vpad[(int64_t)(q0 + pp) * kBlk + t];
-#pragma unroll
-      for (int c = 0; c < COLS; ++c) acc[c] = fmaf(ys[pp][c], v, acc[c]);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < COLS; ++c)
-    if (c0 + c < ncols) W[((int64_t)(c0 + c) * nb + k) * kBlk + t] = acc[c];
-}
-
-// beta^T (split bf16) for atom A and 4 columns (2 slots); thread = occupied state E.
-__global__ void __launch_bounds__(128) lp_beta(int ncols, int nb, int n_occ, int Kp1,
-                                               const int *__restrict__ aoff,
-                                               const int *__restrict__ adj_ptr,
-                                               const int4 *__restrict__ adj,
-                                               const float *__restrict__ W,
-                                               const float *__restrict__ Xo,
-                                               __nv_bfloat16 *__restrict__ betaT,
-                                               const int *__restrict__ dcnt) {
-  constexpr int COLS = 4;
-  __shared__ float Ws[COLS][kMaxOrb][kMaxOrb + 1];
-  __shared__ float Xs[kMaxOrb][128];
-  const int A = blockIdx.x;
-  const int c0 = blockIdx.y * COLS;
-  if (dcnt) ncols = min(ncols, 2 * *dcnt);
-  if (c0 >= ncols) return;
-  const int aoA = aoff[A], nA = aoff[A + 1] - aoA;
-  const int e0 = adj_ptr[A], e1 = adj_ptr[A + 1];
-  for (int E0 = 0; E0 < n_occ; E0 += 128) {
-    const int E = E0 + threadIdx.x;
-    float acc[COLS][kMaxOrb];
-#pragma unroll
-    for (int c = 0; c < COLS; ++c)
-#pragma unroll
-      for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = 0.f;
-    for (int e = e0; e < e1; ++e) {
-      const int4 ent = adj[e];
-      const int k = ent.x, B = ent.y, tr = ent.z;
-      const int bo = aoff[B], nB = aoff[B + 1] - bo;
-      // this entry's X_occ column: all loads issued together, parked in shared memory
-      {
-        float xr[kMaxOrb];
-#pragma unroll
-        for (int b = 0; b < kMaxOrb; ++b)
-          xr[b] = (b < nB && E < n_occ) ? Xo[(int64_t)(bo + b) * n_occ + E] : 0.f;
-        __syncthreads();
-#pragma unroll
-        for (int b = 0; b < kMaxOrb; ++b) Xs[b][threadIdx.x] = xr[b];
-      }
-      for (int i = threadIdx.x; i < COLS * kBlk; i += 128) {
-        const int c = i / kBlk, ab = i % kBlk, a = ab / kMaxOrb, b = ab % kMaxOrb;
-        float v = 0.f;
-        if (c0 + c < ncols)
-          v = tr ? W[((int64_t)(c0 + c) * nb + k) * kBlk + b * kMaxOrb + a]
-                 : W[((int64_t)(c0 + c) * nb + k) * kBlk + a * kMaxOrb + b];
-        Ws[c][a][b] = v;
-      }
-      __syncthreads();
-      for (int b = 0; b < nB; ++b) {
-        const float xv = Xs[b][threadIdx.x];
-#pragma unroll
-        for (int c = 0; c < COLS; ++c)
-#pragma unroll
-          for (int a = 0; a < kMaxOrb; ++a) acc[c][a] = fmaf(Ws[c][a][b], xv, acc[c][a]);
-      }
-    }
-    if (E < n_occ) {
-#pragma unroll
-      for (int c = 0; c < COLS; ++c) {
-        const int cc = c0 + c;
-        if (cc >= ncols) continue;
-        const int64_t row = ((int64_t)(cc >> 1) * n_occ + E) * 2 + (cc & 1);
-        __nv_bfloat16 *dst = betaT + row * 2 * Kp1 + aoA;
-#pragma unroll
-        for (int a = 0; a < kMaxOrb; ++a) {
-          if (a < nA) {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(acc[c][a]);
-            dst[a] = hi;
-            dst[Kp1 + a] = __float2bfloat16_rn(acc[c][a] - __bfloat162float(hi));
-          }
-        }
-      }
-    }
-  }
-}
-
 }  // namespace
 
 cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
@@ -208,9 +87,7 @@ cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &
   split_rows_kernel<<<g, 256, 0, st>>>(sys.K, sys.n_prod, 1, sys.n_prod, sys.n_prod, lp.KpK, lp.Ks);
   split_rows_kernel<<<g, 256, 0, st>>>(sys.XvT, sys.n_orb, 1, sys.n_virt, sys.n_orb, lp.Kp1, lp.XvTs);
   split_rows_kernel<<<g, 256, 0, st>>>(sys.Xv, sys.n_virt, 1, sys.n_orb, sys.n_virt, lp.Kp2, lp.Xvs);
-  to_f32_kernel<<<g, 256, 0, st>>>(sys.Xo, (int64_t)sys.n_orb * sys.n_occ, lp.Xo32);
   split_f32_pairs_kernel<<<4, 256, 0, st>>>(sys.energy, sys.n_occ, lp.eocc2);
-  to_f32_kernel<<<g, 256, 0, st>>>(sys.Vpad, (int64_t)sys.n_prod * kBlk, lp.Vpad32);
   const size_t rows = (size_t)2 * lp.slots * sys.n_occ;
   cudaMemsetAsync(lp.Zb, 0, (size_t)2 * lp.slots * 2 * lp.KpK * sizeof(__nv_bfloat16), st);
   cudaMemsetAsync(lp.betaT, 0, rows * 2 * lp.Kp1 * sizeof(__nv_bfloat16), st);
@@ -255,10 +132,16 @@ cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
           r = launch_gemm_tc(st, lp.opXvT, lp.opBeta, sys.n_virt, (int)N1, kDscaleSplit, ep, lp.err,
                              nullptr, 0, bn);
       } else {
-        ep.outF = lp.gammaT;
-        ep.ldo = sys.n_orb;
+        const AlphaRoute &ar = *lp.ar;
+        ep.outB = ar.gcat_q;
+        ep.ldo = 2 * (int64_t)ar.kcat5;
+        ep.lo_off = ar.kcat5;
+        ep.n_occ = sys.n_occ;
+        ep.aoff = sys.aoff;
+        ep.orb_atom = ar.orb_atom;
+        ep.xoff5 = ar.xoff5;
         if (r == cudaSuccess)
-          r = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kStoreF32, ep, lp.err,
+          r = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kGammaCatSplit, ep, lp.err,
                              nullptr, 0, bn);
       }
       if (r == cudaSuccess) r = cudaEventRecord(b, st);
@@ -322,47 +205,27 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
       if (err != cudaSuccess) return err;
     }
   }
-  if (lp.ar) {
-    // steps 1-2 on the stored transition vertex: gather v^nu per atom, then
-    // beta^T = (alpha_A Ycat_A)^T per atom on the tensor cores
-    const AlphaRoute &ar = *lp.ar;
-    {
-      Scope sc(lp.timer, st, kcAlphaGather, 0.0);
-      err = launch_alpha_gather_lp(st, ar, ncols, mode == kA ? (const void *)lp.Yt : Zin,
-                                   mode != kA, np, lp.dcnt);
-      if (err != cudaSuccess) return err;
-    }
-    {
-      Scope sc(lp.timer, st, kcTcStep2, ncols * ar.flops2);
-      TcEpilogue eb;
-      eb.outB = lp.betaT;
-      eb.ldo = 2 * (int64_t)lp.Kp1;
-      eb.lo_off = lp.Kp1;
-      eb.n_occ = sys.n_occ;
-      eb.aoff = sys.aoff;
-      err = launch_gemm_tc_grouped(st, ar.a2, ar.ycat, ar.tiles2, ar.n_tiles2, ncols, kBetaTSplit,
-                                   eb, lp.err, lp.dcnt, 2);
-      if (err != cudaSuccess) return err;
-    }
-  } else {
-    {
-      Scope sc(lp.timer, st, kcLpVertex, 2.0 * ncols * (double)kBlk * np);
-      dim3 grid(sys.n_blocks, (ncols + 7) / 8);
-      if (mode == kA)
-        lp_vertex<float><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
-                                               lp.Vpad32, lp.Yt, lp.W, lp.dcnt);
-      else
-        lp_vertex<double><<<grid, 256, 0, st>>>(sys.n_blocks, ncols, np, sys.blk_ptr, sys.blk_prod,
-                                                lp.Vpad32, Zin, lp.W, lp.dcnt);
-      if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    }
-    {
-      Scope sc(lp.timer, st, kcLpBeta, ncols * sys.sf.beta);
-      dim3 grid(sys.n_atoms, (ncols + 3) / 4);
-      lp_beta<<<grid, 128, 0, st>>>(ncols, sys.n_blocks, sys.n_occ, lp.Kp1, sys.aoff, sys.adj_ptr,
-                                    sys.adj, lp.W, lp.Xo32, lp.betaT, lp.dcnt);
-      if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    }
+  if (!lp.ar) return cudaErrorInvalidValue;
+  const AlphaRoute &ar = *lp.ar;
+  // steps 1-2 on the stored transition vertex: gather v^nu per atom, then
+  // beta^T = (alpha_A Ycat_A)^T per atom on the tensor cores
+  {
+    Scope sc(lp.timer, st, kcAlphaGather, 0.0);
+    err = launch_alpha_gather_lp(st, ar, ncols, mode == kA ? (const void *)lp.Yt : Zin,
+                                 mode != kA, np, lp.dcnt);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(lp.timer, st, kcTcStep2, ncols * ar.flops2);
+    TcEpilogue eb;
+    eb.outB = lp.betaT;
+    eb.ldo = 2 * (int64_t)lp.Kp1;
+    eb.lo_off = lp.Kp1;
+    eb.n_occ = sys.n_occ;
+    eb.aoff = sys.aoff;
+    err = launch_gemm_tc_grouped(st, ar.a2, ar.ycat, ar.tiles2, ar.n_tiles2, ncols, kBetaTSplit,
+                                 eb, lp.err, lp.dcnt, 2);
+    if (err != cudaSuccess) return err;
   }
   const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)N1;
   {
@@ -386,50 +249,31 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
                          lp.dcnt, 2 * sys.n_occ, lp.bn1);
     if (err != cudaSuccess) return err;
   }
-  if (lp.ar) {
-    // gamma into the per-atom Gcat rows, then step 5 per atom and the sum
-    // of each product's (one or two) partials
-    const AlphaRoute &ar = *lp.ar;
-    {
-      Scope sc(lp.timer, st, kcTcT2, tflops);
-      TcEpilogue e2;
-      e2.outB = ar.gcat_q;
-      e2.ldo = 2 * (int64_t)ar.kcat5;
-      e2.lo_off = ar.kcat5;
-      e2.n_occ = sys.n_occ;
-      e2.aoff = sys.aoff;
-      e2.orb_atom = ar.orb_atom;
-      e2.xoff5 = ar.xoff5;
-      err = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kGammaCatSplit, e2, lp.err,
-                           lp.dcnt, 2 * sys.n_occ, lp.bn2);
-      if (err != cudaSuccess) return err;
-    }
-    {
-      Scope sc(lp.timer, st, kcTcStep5, ncols * ar.flops5);
-      TcEpilogue e5;
-      e5.outF = ar.P2f;
-      e5.ldo = ar.ldp;
-      err = launch_gemm_tc_grouped(st, ar.a5, ar.gcat, ar.tiles5, ar.n_tiles5, ncols, kPartialF32,
-                                   e5, lp.err, lp.dcnt, 2);
-      if (err == cudaSuccess)
-        err = launch_alpha_combine(st, ar, ncols, np, false, Zin, mode == kA ? 1 : 0, Out, lp.dcnt);
-      if (err != cudaSuccess) return err;
-    }
-    return cudaSuccess;
-  }
+  // gamma into the per-atom Gcat rows, then step 5 per atom and the sum
+  // of each product's (one or two) partials
   {
     Scope sc(lp.timer, st, kcTcT2, tflops);
     TcEpilogue e2;
-    e2.outF = lp.gammaT;
-    e2.ldo = sys.n_orb;
-    err = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kStoreF32, e2, lp.err, lp.dcnt,
-                         2 * sys.n_occ, lp.bn2);
+    e2.outB = ar.gcat_q;
+    e2.ldo = 2 * (int64_t)ar.kcat5;
+    e2.lo_off = ar.kcat5;
+    e2.n_occ = sys.n_occ;
+    e2.aoff = sys.aoff;
+    e2.orb_atom = ar.orb_atom;
+    e2.xoff5 = ar.xoff5;
+    err = launch_gemm_tc(st, lp.opXv, lp.opA, sys.n_orb, (int)N1, kGammaCatSplit, e2, lp.err,
+                         lp.dcnt, 2 * sys.n_occ, lp.bn2);
     if (err != cudaSuccess) return err;
   }
   {
-    Scope sc(lp.timer, st, kcLpSddmm, ncols * sys.sf.dot);
-    err = launch_block_dot(st, false, ncols, sys, lp.Vpad32, lp.Xo32, lp.gammaT, Zin,
-                           mode == kA ? 1 : 0, Out, lp.dcnt);
+    Scope sc(lp.timer, st, kcTcStep5, ncols * ar.flops5);
+    TcEpilogue e5;
+    e5.outF = ar.P2f;
+    e5.ldo = ar.ldp;
+    err = launch_gemm_tc_grouped(st, ar.a5, ar.gcat, ar.tiles5, ar.n_tiles5, ncols, kPartialF32,
+                                 e5, lp.err, lp.dcnt, 2);
+    if (err == cudaSuccess)
+      err = launch_alpha_combine(st, ar, ncols, np, false, Zin, mode == kA ? 1 : 0, Out, lp.dcnt);
     if (err != cudaSuccess) return err;
   }
   return cudaSuccess;

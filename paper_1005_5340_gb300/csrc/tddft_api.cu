@@ -96,8 +96,8 @@ namespace tddft {
 const char *kernel_class_name(int k) {
   static const char *names[kcCount] = {
       "f64_gemm_K",  "f64_vertex",   "f64_beta",      "f64_gemm_T1",  "f64_dscale",
-      "f64_gemm_T2", "f64_block_dot", "tc_gemm_K",    "lp_vertex",    "lp_beta",
-      "tc_gemm_T1_dscale", "tc_gemm_T2", "lp_block_dot", "lp_split_z", "gmres_step",
+      "f64_gemm_T2", "f64_block_dot", "tc_gemm_K",    "tc_gemm_T1_dscale", "tc_gemm_T2",
+      "lp_split_z", "gmres_step",
       "gmres_gather", "gmres_select", "rhs_formation", "misc", "emu_slice", "emu_gemm_K",
       "emu_gemm_T1", "emu_gemm_T2", "alpha_gather", "tc_alpha_beta", "tc_alpha_dot",
       "emu_alpha_beta", "emu_alpha_dot"};
@@ -456,14 +456,10 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     AL(L.Ks, (size_t)np * 2 * L.KpK);
     AL(L.XvTs, (size_t)nv * 2 * L.Kp1);
     AL(L.Xvs, (size_t)no * 2 * L.Kp2);
-    AL(L.Xo32, (size_t)no * nocc);
-    AL(L.Vpad32, (size_t)np * kBlk);
     AL(L.Zb, 2 * S * 2 * (size_t)L.KpK);
     AL(L.Yt, 2 * S * (size_t)np);
-    AL(L.W, 2 * S * (size_t)d.n_blocks * kBlk);
     AL(L.betaT, rows1 * 2 * L.Kp1);
     AL(L.aT, rows1 * 2 * L.Kp2);
-    AL(L.gammaT, rows1 * no);
     AL(L.omega, S);
     AL(L.err, 1);
     AL(L.eocc2, (size_t)nocc);
