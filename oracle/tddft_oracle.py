@@ -36,9 +36,13 @@ Conventions (readings of the paper):
   which is the paper's "E.F < 0 after the Fermi shift" condition.
 * P is the paper's P_ik = d_i . X_k (eq. eqpolarizability); the physical
   polarizability is alpha = -P, whose imaginary part is >= 0 for omega > 0.
-* GMRES stops when the true residual ||b - A x|| / ||b|| <= tol (recomputed
-  at each restart and at exit); the paper's eps_P / eps_X criterion is not
-  used.
+* GMRES stops by default when the true residual ||b - A x|| / ||b|| <= tol
+  (recomputed at each restart and at exit).  ``stop="eps_p"`` and
+  ``stop="eps_px"`` take the paper's criterion of Sec. 4.1 instead: the
+  error estimates eps_P = |A^-1| |<d|r>| / |<d|X>| and eps_X = |A^-1| |r| / |X|
+  with |A^-1| the Frobenius norm of the inverse of the square Krylov
+  representation of A (``error_estimates``); "eps_p" stops on eps_P <= tol,
+  "eps_px" on eps_P <= tol and eps_X <= tol (the paper's combined rule).
 """
 from __future__ import annotations
 
@@ -257,23 +261,85 @@ def _givens(a: complex, b: float):
     return c, s
 
 
-def gmres(matvec, b, restart: int, tol: float, max_restarts: int = 200, x0=None):
+STOP_RULES = ("residual", "eps_p", "eps_px")
+
+
+def _ratio(F: float, num: float, den: float) -> float:
+    """F num / den, read as 0 when num = 0 and as infinity when only den = 0."""
+    if num == 0.0:
+        return 0.0
+    if den == 0.0:
+        return math.inf
+    return F * num / den
+
+
+def error_estimates(Finv: float, r, x, d):
+    """The paper's error estimates of Sec. 4.1 for the iterate x with residual
+    r = b - A x: Delta X = A^-1 r and Delta P = <d|A^-1|r> are estimated with
+    a matrix norm of A^-1, |A^-1| ~ Finv, so that
+        eps_P = Finv |<d|r>| / |<d|x>|,   eps_X = Finv ||r|| / ||x||.
+    d is real, so <d|r> = d . r.  Returns (eps_P, eps_X)."""
+    r = np.asarray(r, dtype=complex)
+    x = np.asarray(x, dtype=complex)
+    return (_ratio(Finv, abs(d @ r), abs(d @ x)),
+            _ratio(Finv, np.linalg.norm(r), np.linalg.norm(x)))
+
+
+def krylov_inverse_norm(Hsq) -> float:
+    """|A^-1| ~ sqrt(sum_ij |<i|A^-1|j>|^2) (Sec. 4.1): the Frobenius norm of
+    the inverse of the square Krylov representation H_ij = <i|A|j> of A on
+    the current basis (infinity when it is singular)."""
+    try:
+        return float(np.linalg.norm(np.linalg.inv(Hsq), "fro"))
+    except np.linalg.LinAlgError:
+        return math.inf
+
+
+def _stop_met(stop: str, ep: float, ex: float, tol: float) -> bool:
+    if stop == "eps_p":
+        return ep <= tol
+    return ep <= tol and ex <= tol
+
+
+def gmres(matvec, b, restart: int, tol: float, max_restarts: int = 200, x0=None,
+          stop: str = "residual", d=None, trace: bool = False):
     """Restarted GMRES(m): Arnoldi with modified Gram-Schmidt, Givens QR of the
     Hessenberg matrix, minimal residual in each Krylov space.  The first
     basis vector is the (normalised) residual, which for a zero initial guess
-    is b itself.  Stops when ||b - A x|| / ||b|| <= tol, that residual being
-    recomputed from scratch after every cycle.
+    is b itself.
 
-    Returns (x, info) with info = dict(converged, matvecs, cycles, resid)."""
+    stop = "residual": a cycle ends once the Givens residual estimate
+    |g_{j+1}| / ||b|| <= tol, and the solve ends when ||b - A x|| / ||b|| <= tol,
+    that residual being recomputed from scratch after every cycle.
+    stop = "eps_p" / "eps_px" (the paper's criterion, needs the real vector d
+    of P = <d|X>): after every Arnoldi step j the iterate x_j = x + V y_j
+    (y_j the least-squares solution on the unrotated Hessenberg matrix), its
+    residual r_j = r_0 - sum_i y_i A v_i and |A^-1| ~ ||H_j^-1||_F of the
+    square (j+1) x (j+1) Hessenberg block give eps_P and eps_X
+    (``error_estimates``); the cycle ends once the rule holds, and the solve
+    ends when it holds for the recomputed residual with the |A^-1| of the
+    cycle's last step (before any cycle, |A^-1| is unknown: infinity).
+
+    Returns (x, info) with info = dict(converged, matvecs, cycles, resid,
+    eps_p, eps_x) and, with trace, info["trace"] = [(cycle, j, Finv, eps_p,
+    eps_x), ...] of every step."""
+    if stop not in STOP_RULES:
+        raise ValueError(f"stop must be one of {STOP_RULES}")
     b = np.asarray(b, dtype=complex)
     bnorm = np.linalg.norm(b)
     n = b.shape[0]
     x = np.zeros(n, dtype=complex) if x0 is None else np.array(x0, dtype=complex)
-    info = dict(converged=False, matvecs=0, cycles=0, resid=1.0)
+    info = dict(converged=False, matvecs=0, cycles=0, resid=1.0, eps_p=math.nan,
+                eps_x=math.nan)
+    if trace:
+        info["trace"] = []
+    if stop != "residual":
+        d = np.asarray(d, dtype=float)
     if bnorm == 0.0:
         info.update(converged=True, resid=0.0)
         return x, info
     m = restart
+    Flast = math.inf
     for cycle in range(max_restarts + 1):
         if cycle == 0 and x0 is None:
             r = b.copy()
@@ -282,14 +348,22 @@ def gmres(matvec, b, restart: int, tol: float, max_restarts: int = 200, x0=None)
             info["matvecs"] += 1
         beta = np.linalg.norm(r)
         info["resid"] = beta / bnorm
-        if beta / bnorm <= tol:
+        if stop == "residual":
+            done = beta / bnorm <= tol
+        else:
+            ep, ex = error_estimates(Flast, r, x, d)
+            info.update(eps_p=ep, eps_x=ex)
+            done = beta == 0.0 or _stop_met(stop, ep, ex, tol)
+        if done:
             info["converged"] = True
             return x, info
         if cycle == max_restarts:
             break
         info["cycles"] += 1
         V = np.zeros((m + 1, n), dtype=complex)
+        AV = np.zeros((m, n), dtype=complex)
         H = np.zeros((m + 1, m), dtype=complex)
+        Hraw = np.zeros((m + 1, m), dtype=complex)
         cs = np.zeros(m)
         sn = np.zeros(m, dtype=complex)
         g = np.zeros(m + 1, dtype=complex)
@@ -298,12 +372,14 @@ def gmres(matvec, b, restart: int, tol: float, max_restarts: int = 200, x0=None)
         k = 0
         for j in range(m):
             w = matvec(V[j])
+            AV[j] = w
             info["matvecs"] += 1
             for i in range(j + 1):
                 H[i, j] = np.vdot(V[i], w)
                 w = w - H[i, j] * V[i]
             hnext = np.linalg.norm(w)
             H[j + 1, j] = hnext
+            Hraw[:, j] = H[:, j]
             for i in range(j):
                 t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
                 H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + cs[i] * H[i + 1, j]
@@ -315,7 +391,18 @@ def gmres(matvec, b, restart: int, tol: float, max_restarts: int = 200, x0=None)
             g[j + 1] = -np.conj(s) * g[j]
             g[j] = c * g[j]
             k = j + 1
-            if hnext == 0.0 or abs(g[j + 1]) / bnorm <= tol:
+            if stop == "residual":
+                hit = abs(g[j + 1]) / bnorm <= tol
+            else:
+                Flast = krylov_inverse_norm(Hraw[:k, :k])
+                rhs = np.zeros(k + 1, dtype=complex)
+                rhs[0] = beta
+                yj = np.linalg.lstsq(Hraw[:k + 1, :k], rhs, rcond=None)[0]
+                ep, ex = error_estimates(Flast, r - yj @ AV[:k], x + yj @ V[:k], d)
+                if trace:
+                    info["trace"].append((cycle, j, Flast, ep, ex))
+                hit = _stop_met(stop, ep, ex, tol)
+            if hnext == 0.0 or hit:
                 break
             V[j + 1] = w / hnext
         y = np.zeros(k, dtype=complex)
@@ -326,9 +413,11 @@ def gmres(matvec, b, restart: int, tol: float, max_restarts: int = 200, x0=None)
 
 
 def polarizability_gmres(sysm, omegas, eps: float, restart: int, tol: float,
-                         max_restarts: int = 200, dirs=(0, 1, 2), op=None):
+                         max_restarts: int = 200, dirs=(0, 1, 2), op=None,
+                         stop: str = "residual"):
     """Matrix-free P(omega) for each omega: b_k = chi0 d_k, GMRES on
-    (1 - chi0 K) X_k = b_k, P_ik = d_i . X_k.
+    (1 - chi0 K) X_k = b_k, P_ik = d_i . X_k.  ``stop`` is the GMRES stopping
+    rule (``gmres``), with d = d_k for the right-hand side of direction k.
 
     Returns (P [n_omega, 3, len(dirs)] complex, infos list)."""
     op = op or StepOperator(sysm)
@@ -339,7 +428,7 @@ def polarizability_gmres(sysm, omegas, eps: float, restart: int, tol: float,
         for jk, k in enumerate(dirs):
             b = op.apply(sysm.dipole[k].astype(complex), w, eps)
             x, info = gmres(lambda z: apply_A(sysm, op, z, w, eps), b, restart, tol,
-                            max_restarts)
+                            max_restarts, stop=stop, d=sysm.dipole[k])
             info.update(omega=float(w), dir=int(k))
             infos.append(info)
             P[iw, :, jk] = sysm.dipole @ x
