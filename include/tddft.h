@@ -106,6 +106,17 @@ typedef struct {
   const double *dipole;
 } tddft_system;
 
+/* GMRES stopping rules (Sec. 4.1).  The error estimates use |A^-1| ~ the
+ * Frobenius norm of the inverse of the square Krylov representation of A at
+ * the cycle's latest step, and d = the dipole of the right-hand side's field
+ * direction (P = <d|X>):
+ *   eps_P = |A^-1| |<d|r>| / |<d|X>|,   eps_X = |A^-1| ||r|| / ||X||. */
+typedef enum {
+  TDDFT_STOP_RESIDUAL = 0, /* ||b - A x||_2 / ||b||_2 <= tol */
+  TDDFT_STOP_EPS_P = 1,    /* eps_P <= tol (the paper's quick rule) */
+  TDDFT_STOP_EPS_PX = 2    /* eps_P <= tol and eps_X <= tol (the paper's combined rule) */
+} tddft_stop_rule;
+
 /*
  * Solver and resource options.
  *  prec: a tddft_precision.  With BF16X3_IR(_EMU), tddft_chi0_apply and
@@ -114,8 +125,9 @@ typedef struct {
  *  restart: GMRES restart length m (1..256).
  *  max_restarts: cycles before an (omega, direction) is declared not
  *      converged (>= 1).
- *  tol: stop when ||b - A x||_2 / ||b||_2 <= tol, the residual recomputed in
- *      float64 at the end of each cycle (> 0).
+ *  tol: the tolerance of the stopping rule (> 0).  With TDDFT_STOP_RESIDUAL
+ *      the solve stops when ||b - A x||_2 / ||b||_2 <= tol, the residual
+ *      recomputed in float64 at the end of each cycle.
  *  batch: maximum number of right-hand sides solved together (>= 1); sizes
  *      every device workspace allocated by tddft_create.
  *  stream: cudaStream_t for all work (NULL = legacy default stream).
@@ -129,6 +141,11 @@ typedef struct {
  *      device; the host checks for completion every few replays.  0 = one
  *      launch sequence per iteration sized on the host.  Per-kernel timing
  *      (tddft_timing_*) forces 0.
+ *  stop: a tddft_stop_rule.  With the error estimates a cycle ends at the
+ *      first Arnoldi step whose estimates (from the Givens/Hessenberg data
+ *      and the cycle's <d|v_i>, <x0|v_i>, <d|A v_i>) meet the rule, and the
+ *      solve ends when the rule holds for the float64 residual recomputed at
+ *      the end of the cycle, with |A^-1| of the cycle's last step.
  */
 typedef struct {
   int32_t prec;
@@ -139,6 +156,7 @@ typedef struct {
   void *stream;
   double inner_tol;
   int32_t graph;
+  int32_t stop;
 } tddft_options;
 
 /* Per-(omega, direction) solver report. */
@@ -146,8 +164,10 @@ typedef struct {
   int32_t matvecs;   /* applications of A, residual checks included */
   int32_t cycles;    /* GMRES cycles started */
   double resid;      /* final ||b - A x|| / ||b|| (float64) */
-  int32_t converged; /* 1 if resid <= tol */
+  int32_t converged; /* 1 if the stopping rule was met */
   int32_t flags;     /* bit 0: a supplied initial guess was worse than zero and dropped */
+  double eps_p;      /* final eps_P and eps_X (TDDFT_STOP_EPS_*; NaN with the residual rule) */
+  double eps_x;
 } tddft_solve_stats;
 
 /*

@@ -11,6 +11,17 @@
 //                    done, not converged (cycle limit) and a restart.
 // Right-hand sides that are done drop out of the active list, so the batched
 // operator only works on live ones.
+// Stopping rules: the relative residual ||b - A x|| / ||b|| <= tol, or the
+// error estimates of Sec. 4.1, eps_P = |A^-1| |<d|r>| / |<d|x>| (alone, or
+// together with eps_X = |A^-1| ||r|| / ||x||) <= tol, where |A^-1| is the
+// Frobenius norm of the inverse of the square Krylov representation H_j of A
+// and d the dipole of the right-hand side's direction.  For those each step
+// keeps, per right-hand side, delta_i = <d|v_i>, xi_i = <x0|v_i> and
+// phi_i = <d|A v_i> of the cycle, and solves R_j [y, c] = [g, e_j] with the
+// rotated Hessenberg triangle: y gives <d|x_j>, ||x_j|| and <d|r_j> =
+// <d|r_0> - sum_i phi_i y_i, and c (the last column of R_j^-1) extends
+// ||R_j^-1||_F^2; ||H_j^-1||_F follows because H_j and R_j differ by a unitary
+// factor except in the last diagonal entry (before the last rotation in H_j).
 #include <cooperative_groups.h>
 
 #include "internal.h"
@@ -66,8 +77,19 @@ __device__ void block_sum(double (&v)[NV], double *red /* [NV][NT/32] */) {
   }
 }
 
+// Per-right-hand-side scalars of the error estimates (crit[r][kCrit]).
+constexpr int kCrit = 10;
+constexpr int kCrFsum = 0;   // ||R_j^-1||_F^2 of the current cycle's rotated triangle
+constexpr int kCrFsq = 1;    // ||H_j^-1||_F^2 of the latest step (infinity before any)
+constexpr int kCrPd0 = 2;    // <d|x0> (complex) of the current cycle
+constexpr int kCrXn0 = 4;    // ||x0||^2
+constexpr int kCrDr0 = 5;    // <d|r0> (complex)
+constexpr int kCrEpsP = 7;   // eps_P and eps_X at the latest residual check
+constexpr int kCrEpsX = 8;
+
 struct Gs {
   int m, max_restarts, n_prod;
+  int stop;   // 0: relative residual, 1: eps_P, 2: eps_P and eps_X
   double tol, inner_tol;
   double *rho0;
   int *state, *jcur, *cycles, *matvecs, *conv, *flags;
@@ -78,9 +100,14 @@ struct Gs {
   const int *act;
   unsigned long long *bytes;
   double2 *Gm;
+  const double *dip;   // [3][n_prod] dipoles
+  const int *dir;      // [cap] direction of each right-hand side
+  double *crit;        // [cap][kCrit]
+  double2 *cvec;       // [cap][3 m + 2]: delta_0..m, xi_0..m, phi_0..m-1
 };
 
-Gs view(const GmresState &s, int n_prod) {
+Gs view(const GmresState &s, const DevSystem &sys) {
+  const int n_prod = sys.n_prod;
   Gs v;
   v.m = s.m; v.max_restarts = s.max_restarts; v.n_prod = n_prod; v.tol = s.tol;
   v.inner_tol = s.inner_tol; v.rho0 = s.rho0;
@@ -91,6 +118,11 @@ Gs view(const GmresState &s, int n_prod) {
   v.Vf = s.Vf;
   v.bytes = s.bytes;
   v.Gm = s.Gm;
+  v.stop = s.stop;
+  v.dip = sys.dip;
+  v.dir = s.dir;
+  v.crit = s.crit;
+  v.cvec = s.cvec;
   return v;
 }
 
@@ -98,24 +130,41 @@ template <class T> __device__ __forceinline__ T *basis(const Gs &G);
 template <> __device__ __forceinline__ double *basis<double>(const Gs &G) { return G.V; }
 template <> __device__ __forceinline__ float *basis<float>(const Gs &G) { return G.Vf; }
 
+// F num / den, read as 0 when num = 0 and as infinity when only den = 0.
+__device__ inline double est_ratio(double F, double num, double den) {
+  if (num == 0.0) return 0.0;
+  if (den == 0.0) return __longlong_as_double(0x7ff0000000000000LL);
+  return F * num / den;
+}
+__device__ inline bool stop_met(int stop, double ep, double ex, double tol) {
+  return stop == 1 ? ep <= tol : (ep <= tol && ex <= tol);
+}
+
 // Start: store b, x = 0, v_0 = b / ||b||.
 template <class T>
 __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__restrict__ Bp) {
-  __shared__ double red[NT / 32];
+  __shared__ double red[3 * (NT / 32)];
   const int r = blockIdx.x;
   const int N = G.n_prod;
   const double *bin = Bp + (int64_t)2 * r * N;
   double *b = G.b + (int64_t)2 * r * N;
   double *x = G.x + (int64_t)2 * r * N;
   T *v0 = basis<T>(G) + (int64_t)r * (G.m + 1) * 2 * N;
-  double s[1] = {0.0};
+  double s[3] = {0.0, 0.0, 0.0};
   for (int e = threadIdx.x; e < 2 * N; e += NT) {
     double t = bin[e];
     b[e] = t;
     x[e] = 0.0;
     s[0] += t * t;
   }
-  block_sum<1>(s, red);
+  if (G.stop) {
+    const double *d = G.dip + (int64_t)G.dir[r] * N;
+    for (int e = threadIdx.x; e < N; e += NT) {
+      s[1] = fma(d[e], bin[e], s[1]);
+      s[2] = fma(d[e], bin[N + e], s[2]);
+    }
+  }
+  block_sum<3>(s, red);
   const double nrm = sqrt(s[0]);
   if (nrm > 0.0) {
     const double inv = 1.0 / nrm;
@@ -126,6 +175,23 @@ __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__r
     G.matvecs[r] = 0;
     G.jcur[r] = 0;
     G.flags[r] = 0;
+    if (G.stop) {
+      // x0 = 0, r0 = b: <d|x0> = 0, ||x0|| = 0, <d|r0> = <d|b>; |A^-1| unknown
+      double *cr = G.crit + (int64_t)r * kCrit;
+      const double nan = __longlong_as_double(0x7ff8000000000000LL);
+      cr[kCrFsum] = 0.0;
+      cr[kCrFsq] = __longlong_as_double(0x7ff0000000000000LL);
+      cr[kCrPd0] = 0.0;
+      cr[kCrPd0 + 1] = 0.0;
+      cr[kCrXn0] = 0.0;
+      cr[kCrDr0] = s[1];
+      cr[kCrDr0 + 1] = s[2];
+      cr[kCrEpsP] = nan;
+      cr[kCrEpsX] = nan;
+      double2 *cv = G.cvec + (int64_t)r * (3 * G.m + 2);
+      cv[0] = nrm > 0.0 ? make_double2(s[1] / nrm, s[2] / nrm) : make_double2(0.0, 0.0);
+      cv[G.m + 1] = make_double2(0.0, 0.0);
+    }
     if (nrm > 0.0) {
       G.state[r] = kStateArnoldi;
       G.cycles[r] = 1;
@@ -246,6 +312,11 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   __shared__ float2 hT[257];   // coefficients in float32 for the float32 basis
   __shared__ int finish_flag;
   __shared__ double2 s_gj;
+  // error estimates: this step's <d|A v_j>, <d|w>, <x0|w>, |a|^2 and |rho|^2
+  // of the last diagonal before and after its rotation, |g_{j+1}|, the
+  // cycle's scalars read at entry, and the updated Frobenius sums
+  __shared__ double2 s_phi, s_dw, s_xw;
+  __shared__ double s_a2, s_rho2, s_est, s_cr[6], s_F[2];
   extern __shared__ double2 hdyn[];   // the Hessenberg columns when h_smem
   const int s = blockIdx.y;
   if (dcnt && s >= *dcnt) return;          // the same for the whole cluster
@@ -267,20 +338,42 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   if (state == kStateResid) {
     // r = b - A x ; decide done / not converged / restart
     const double *b = G.b + (int64_t)2 * r * N;
-    double s2[1] = {0.0};
+    double *x = G.x + (int64_t)2 * r * N;
+    // [0] ||r||^2; with the error estimates also <d|r>, <d|b>, <d|x>, <x|r>
+    // (complex) and ||x||^2
+    double s2[10] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int e = lo + tid; e < hi; e += NT) {
       const double tr = b[e] - win[e], ti = b[N + e] - win[N + e];
       Vr[e] = (T)tr;
       Vr[N + e] = (T)ti;
       s2[0] += tr * tr + ti * ti;
     }
-    cluster_sum<P, 1>(s2, red, clx);
+    if (G.stop) {
+      const double *d = G.dip + (int64_t)G.dir[r] * N;
+      for (int e = lo + tid; e < hi; e += NT) {
+        const double tr = b[e] - win[e], ti = b[N + e] - win[N + e];
+        const double de = d[e], xr = x[e], xi = x[N + e];
+        s2[1] = fma(de, tr, s2[1]);
+        s2[2] = fma(de, ti, s2[2]);
+        s2[3] = fma(de, b[e], s2[3]);
+        s2[4] = fma(de, b[N + e], s2[4]);
+        s2[5] = fma(de, xr, s2[5]);
+        s2[6] = fma(de, xi, s2[6]);
+        s2[7] = fma(xr, tr, fma(xi, ti, s2[7]));
+        s2[8] = fma(xr, ti, fma(-xi, tr, s2[8]));
+        s2[9] = fma(xr, xr, fma(xi, xi, s2[9]));
+      }
+      cluster_sum<P, 10>(s2, red, clx);
+    } else {
+      double t1[1] = {s2[0]};
+      cluster_sum<P, 1>(t1, red, clx);
+      s2[0] = t1[0];
+    }
     double rho = sqrt(s2[0]);
     bool rejected = false;
     if (cyc == 0 && rho > G.bnorm[r]) {
       // the residual of a supplied initial guess: zero is the fallback and the
       // judge, so a guess worse than zero is dropped
-      double *x = G.x + (int64_t)2 * r * N;
       for (int e = lo + tid; e < hi; e += NT) {
         Vr[e] = (T)b[e];
         Vr[N + e] = (T)b[N + e];
@@ -289,10 +382,25 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
       }
       rho = G.bnorm[r];
       rejected = true;
+      // r = b and x = 0
+      s2[1] = s2[3];
+      s2[2] = s2[4];
+      for (int q = 5; q < 10; ++q) s2[q] = 0.0;
     }
     const double rel = rho / G.bnorm[r];
+    double ep = 0.0, ex = 0.0;
+    bool met;
+    if (G.stop) {
+      // eps_P and eps_X of x with the |A^-1| of the last step of the last cycle
+      const double Fn = sqrt(G.crit[(int64_t)r * kCrit + kCrFsq]);
+      ep = est_ratio(Fn, hypot(s2[1], s2[2]), hypot(s2[5], s2[6]));
+      ex = est_ratio(Fn, rho, sqrt(s2[9]));
+      met = rho == 0.0 || stop_met(G.stop, ep, ex, G.tol);
+    } else {
+      met = rel <= G.tol;
+    }
     int next;
-    if (rel <= G.tol) next = 0;
+    if (met) next = 0;
     else if (cyc >= G.max_restarts) next = 1;
     else next = 2;
     if (next == 2) {
@@ -308,6 +416,23 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
       G.matvecs[r] += 1;
       G.resid[r] = rel;
       if (rejected) G.flags[r] |= 1;
+      if (G.stop) {
+        double *cr = G.crit + (int64_t)r * kCrit;
+        cr[kCrEpsP] = ep;
+        cr[kCrEpsX] = ex;
+        if (next == 2) {
+          // the next cycle starts from x0 = x, r0 = r, v_0 = r / rho
+          cr[kCrFsum] = 0.0;
+          cr[kCrPd0] = s2[5];
+          cr[kCrPd0 + 1] = s2[6];
+          cr[kCrXn0] = s2[9];
+          cr[kCrDr0] = s2[1];
+          cr[kCrDr0 + 1] = s2[2];
+          double2 *cv = G.cvec + (int64_t)r * (3 * m + 2);
+          cv[0] = make_double2(s2[1] / rho, s2[2] / rho);
+          cv[m + 1] = make_double2(s2[7] / rho, s2[8] / rho);
+        }
+      }
       if (next == 0) { G.state[r] = kStateDone; G.conv[r] = 1; }
       else if (next == 1) { G.state[r] = kStateDone; G.conv[r] = 0; }
       else {
@@ -325,6 +450,16 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   const int j = G.jcur[r];
   const double2 gj0 = G.g[(int64_t)r * (m + 1) + j];
   const double rho0 = G.rho0[r];
+  if (G.stop && tid == 0) {
+    // read before the first cluster synchronisation: rank 0 rewrites them
+    const double *cr = G.crit + (int64_t)r * kCrit;
+    s_cr[0] = cr[kCrFsum];
+    s_cr[1] = cr[kCrPd0];
+    s_cr[2] = cr[kCrPd0 + 1];
+    s_cr[3] = cr[kCrXn0];
+    s_cr[4] = cr[kCrDr0];
+    s_cr[5] = cr[kCrDr0 + 1];
+  }
   T *w = Vr + (int64_t)(j + 1) * 2 * N;
   const T *vj = Vr + (int64_t)j * 2 * N;
   const int warp = tid >> 5, lane = tid & 31;
@@ -517,7 +652,34 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     }
     n1[0] = (double)nacc;
   }
-  cluster_sum<P, 1>(n1, red, clx);   // synchronises: w complete
+  if (G.stop) {
+    // <d|A v_j>, <d|w> and <x0|w> over this CTA's elements (A v_j from the
+    // operator output; w as just written, by other threads of this CTA)
+    __syncthreads();
+    const double *d = G.dip + (int64_t)G.dir[r] * N;
+    const double *x0 = G.x + (int64_t)2 * r * N;
+    double q7[7] = {n1[0], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int e = lo + tid; e < hi; e += NT) {
+      const double de = d[e], ar = win[e], ai = win[N + e];
+      const double nr = (double)w[e], ni = (double)w[N + e];
+      const double xr = x0[e], xi = x0[N + e];
+      q7[1] = fma(de, ar, q7[1]);
+      q7[2] = fma(de, ai, q7[2]);
+      q7[3] = fma(de, nr, q7[3]);
+      q7[4] = fma(de, ni, q7[4]);
+      q7[5] = fma(xr, nr, fma(xi, ni, q7[5]));
+      q7[6] = fma(xr, ni, fma(-xi, nr, q7[6]));
+    }
+    cluster_sum<P, 7>(q7, red, clx);   // synchronises: w complete
+    n1[0] = q7[0];
+    if (tid == 0) {
+      s_phi = make_double2(q7[1], q7[2]);
+      s_dw = make_double2(q7[3], q7[4]);
+      s_xw = make_double2(q7[5], q7[6]);
+    }
+  } else {
+    cluster_sum<P, 1>(n1, red, clx);   // synchronises: w complete
+  }
   const double hn = sqrt(n1[0]);
 
   // the earlier rotations to shared memory (all threads), then thread 0
@@ -560,33 +722,141 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     const double2 gnext = make_double2(-t.x, -t.y);
     const double2 gj = make_double2(c * gj0.x, c * gj0.y);
     const double est = cabs2(gnext);
-    // a cycle ends at the tolerance, at the restart length, on breakdown, or
+    // a cycle ends at the tolerance (of the residual rule; the error
+    // estimates decide below), at the restart length, on breakdown, or
     // (refinement forms) once it has reduced its own residual by inner_tol
-    const bool fin = (est <= G.tol * G.bnorm[r]) || (j + 1 == m) || !(hn > 0.0) ||
+    const bool fin = (!G.stop && est <= G.tol * G.bnorm[r]) || (j + 1 == m) || !(hn > 0.0) ||
                      (est <= G.inner_tol * rho0);
     finish_flag = fin ? 1 : 0;
     s_gj = gj;
-    if (rank == 0) {
-      double2 *Hc = G.H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);
-      for (int i = 0; i <= j; ++i) Hc[i] = hs[i];
-      G.cs[(int64_t)r * m + j] = c;
-      G.sn[(int64_t)r * m + j] = sv;
-      G.g[(int64_t)r * (m + 1) + j] = gj;
-      G.g[(int64_t)r * (m + 1) + j + 1] = gnext;
-      G.matvecs[r] += 1;
-      if (fin) G.state[r] = kStateResid;
-      else G.jcur[r] = j + 1;
-      // algorithmic traffic of this step: basis vectors (2 N sizeof(T) bytes)
-      // v_0..v_j read twice, v_{j+1} written and normalised, A v_j read
-      // (16 N); at a cycle end v_0..v_j read again and x read and written
-      const unsigned long long nb = 2ull * (j + 1) + 3ull + (fin ? (unsigned long long)j + 1ull : 0ull);
-      const unsigned long long nd = 1ull + (fin ? 2ull : 0ull);
-      atomicAdd(G.bytes, (nb * 2ull * sizeof(T) + nd * 16ull) * (unsigned long long)N);
+    s_a2 = aa * aa;
+    s_rho2 = aa * aa + hn * hn;
+    s_est = est;
+    gq[0] = make_double2(c, 0.0);   // the new rotation, kept for the writes below
+    hq[0] = sv;
+    hq[1] = gnext;
+  }
+  __syncthreads();
+  const double c_new = gq[0].x;
+  const double2 sv_new = hq[0], gnext_new = hq[1];
+  if (G.stop) {
+    // R_j [y, c] = [g, e_j] (R_j: earlier rotated columns, shared memory when
+    // they fit, and column j from this step), then the estimates of x_j
+    const int k = j + 1;
+    const double2 *Hr = G.H + (int64_t)r * (m + 1) * m;
+    const double2 *gg = G.g + (int64_t)r * (m + 1);
+    if (h_smem) {
+      for (int idx = tid; idx < j * (m + 1); idx += NT) {
+        const int l = idx / (m + 1), i = idx - l * (m + 1);
+        if (i <= l) hdyn[idx] = Hr[idx];
+      }
+    }
+    for (int i = tid; i < j; i += NT) hp[i] = gg[i];
+    __syncthreads();
+    const double2 *Hs = h_smem ? hdyn : Hr;
+    if (warp == 0) {
+      for (int i = k - 1; i >= 0; --i) {
+        double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
+        for (int l = i + 1 + lane; l < k; l += 32) {
+          const double2 hil = (l == j) ? hs[i] : Hs[(int64_t)l * (m + 1) + i];
+          const double2 p = cmul(hil, ys[l]), q = cmul(hil, gq[l]);
+          sr += p.x;
+          si += p.y;
+          cr += q.x;
+          ci += q.y;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, off);
+          si += __shfl_xor_sync(0xffffffffu, si, off);
+          cr += __shfl_xor_sync(0xffffffffu, cr, off);
+          ci += __shfl_xor_sync(0xffffffffu, ci, off);
+        }
+        if (lane == 0) {
+          const double2 gi = (i == j) ? s_gj : hp[i];
+          const double2 hii = (i == j) ? hs[j] : Hs[(int64_t)i * (m + 1) + i];
+          ys[i] = cdiv(make_double2(gi.x - sr, gi.y - si), hii);
+          gq[i] = cdiv(make_double2((i == j ? 1.0 : 0.0) - cr, -ci), hii);
+        }
+        __syncwarp();
+      }
+      // <d|x_j> = <d|x0> + sum delta_i y_i, <d|r_j> = <d|r0> - sum phi_i y_i,
+      // ||x_j||^2 = ||x0||^2 + 2 Re sum xi_i y_i + sum |y_i|^2, and the
+      // squared norm of the last column of R_j^-1
+      const double2 *cv = G.cvec + (int64_t)r * (3 * m + 2);
+      double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int i = lane; i < k; i += 32) {
+        const double2 yi = ys[i], ci = gq[i];
+        const double2 dl = cv[i], xi = cv[m + 1 + i];
+        const double2 ph = (i == j) ? s_phi : cv[2 * m + 2 + i];
+        const double2 a = cmul(dl, yi), bq = cmul(ph, yi), cq = cmul(xi, yi);
+        acc[0] += a.x;
+        acc[1] += a.y;
+        acc[2] += bq.x;
+        acc[3] += bq.y;
+        acc[4] += cq.x;
+        acc[5] += yi.x * yi.x + yi.y * yi.y;
+        acc[6] += ci.x * ci.x + ci.y * ci.y;
+      }
+#pragma unroll
+      for (int q = 0; q < 7; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+      if (lane == 0) {
+        const double Pr = s_cr[1] + acc[0], Pi = s_cr[2] + acc[1];
+        const double dr = s_cr[4] - acc[2], di = s_cr[5] - acc[3];
+        const double xx = fmax(0.0, s_cr[3] + 2.0 * acc[4] + acc[5]);
+        const double Fsum = s_cr[0] + acc[6];
+        // H_j differs from R_j only in the last diagonal entry: a instead of rho
+        const double Fsq = s_a2 > 0.0 ? s_cr[0] + acc[6] * (s_rho2 / s_a2)
+                                      : __longlong_as_double(0x7ff0000000000000LL);
+        const double Fn = sqrt(Fsq);
+        const double ep = est_ratio(Fn, hypot(dr, di), hypot(Pr, Pi));
+        const double ex = est_ratio(Fn, s_est, sqrt(xx));
+        if (stop_met(G.stop, ep, ex, G.tol)) finish_flag = 1;
+        s_F[0] = Fsum;
+        s_F[1] = Fsq;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && rank == 0) {
+    const bool fin = finish_flag != 0;
+    double2 *Hc = G.H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) Hc[i] = hs[i];
+    G.cs[(int64_t)r * m + j] = c_new;
+    G.sn[(int64_t)r * m + j] = sv_new;
+    G.g[(int64_t)r * (m + 1) + j] = s_gj;
+    G.g[(int64_t)r * (m + 1) + j + 1] = gnext_new;
+    G.matvecs[r] += 1;
+    if (fin) G.state[r] = kStateResid;
+    else G.jcur[r] = j + 1;
+    // algorithmic traffic of this step: basis vectors (2 N sizeof(T) bytes)
+    // v_0..v_j read twice, v_{j+1} written and normalised, A v_j read
+    // (16 N); at a cycle end v_0..v_j read again and x read and written;
+    // the error estimates read d (8 N), A v_j and x0 (16 N each) and w
+    const unsigned long long nb = 2ull * (j + 1) + 3ull + (fin ? (unsigned long long)j + 1ull : 0ull) +
+                                  (G.stop ? 1ull : 0ull);
+    const unsigned long long nd = 1ull + (fin ? 2ull : 0ull);
+    const unsigned long long ne = G.stop ? 40ull : 0ull;
+    atomicAdd(G.bytes, (nb * 2ull * sizeof(T) + nd * 16ull + ne) * (unsigned long long)N);
+    if (G.stop) {
+      double *cr = G.crit + (int64_t)r * kCrit;
+      cr[kCrFsum] = s_F[0];
+      cr[kCrFsq] = s_F[1];
+      double2 *cv = G.cvec + (int64_t)r * (3 * m + 2);
+      cv[2 * m + 2 + j] = s_phi;
+      if (hn > 0.0) {
+        // v_{j+1} = w / hn
+        const double inv = 1.0 / hn;
+        cv[j + 1] = make_double2(s_dw.x * inv, s_dw.y * inv);
+        cv[m + 1 + j + 1] = make_double2(s_xw.x * inv, s_xw.y * inv);
+      }
     }
   }
   __syncthreads();
-  if (finish_flag) {
-    // back substitution R y = g with the rotated (upper triangular)
+  if (finish_flag && !G.stop) {
+    // back substitution R y = g (with the error estimates, ys holds y already) with the rotated (upper triangular)
     // Hessenberg matrix: its earlier columns (shared memory when they fit)
     // and g_0..g_{j-1} staged by all threads, column j and g_j from this
     // step; warp 0 solves, lanes over the columns l > i
@@ -730,7 +1000,8 @@ __global__ void __launch_bounds__(NT) gmres_export_kernel(Gs G, int g0, double *
 // Right-hand sides g0 .. g0+n-1 of a spectrum: index g -> (omega g/3, direction g%3).
 __global__ void rhs_init_kernel(int n, int g0, int n_prod, const double *__restrict__ omega_all,
                                 const double *__restrict__ dip, double *__restrict__ Zc,
-                                double *__restrict__ slot_omega, double *__restrict__ gs_omega) {
+                                double *__restrict__ slot_omega, double *__restrict__ gs_omega,
+                                int *__restrict__ gs_dir) {
   const int r = blockIdx.x;
   const int g = g0 + r;
   const int k = g % 3;
@@ -743,6 +1014,7 @@ __global__ void rhs_init_kernel(int n, int g0, int n_prod, const double *__restr
   if (threadIdx.x == 0) {
     slot_omega[r] = omega_all[g / 3];
     gs_omega[r] = omega_all[g / 3];
+    if (gs_dir) gs_dir[r] = k;
   }
 }
 
@@ -812,9 +1084,9 @@ cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState
   if (n <= 0) return cudaSuccess;
   if (!gs.V && !gs.Vf) return cudaErrorInvalidValue;
   if (gs.Vf)
-    gmres_start_kernel<float><<<n, NT, 0, st>>>(view(gs, sys.n_prod), Bplanar);
+    gmres_start_kernel<float><<<n, NT, 0, st>>>(view(gs, sys), Bplanar);
   else
-    gmres_start_kernel<double><<<n, NT, 0, st>>>(view(gs, sys.n_prod), Bplanar);
+    gmres_start_kernel<double><<<n, NT, 0, st>>>(view(gs, sys), Bplanar);
   return cudaGetLastError();
 }
 
@@ -829,9 +1101,9 @@ cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresStat
   if (S <= 0) return cudaSuccess;
   if (!gs.V && !gs.Vf) return cudaErrorInvalidValue;
   if (gs.Vf)
-    gmres_gather_kernel<float><<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Zc, slot_omega, dcnt);
+    gmres_gather_kernel<float><<<S, NT, 0, st>>>(view(gs, sys), list, Zc, slot_omega, dcnt);
   else
-    gmres_gather_kernel<double><<<S, NT, 0, st>>>(view(gs, sys.n_prod), list, Zc, slot_omega, dcnt);
+    gmres_gather_kernel<double><<<S, NT, 0, st>>>(view(gs, sys), list, Zc, slot_omega, dcnt);
   return cudaGetLastError();
 }
 
@@ -840,7 +1112,7 @@ cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState 
   if (S <= 0) return cudaSuccess;
   if (S > 65535) return cudaErrorInvalidConfiguration;
   if (!gs.V && !gs.Vf) return cudaErrorInvalidValue;
-  const Gs G = view(gs, sys.n_prod);
+  const Gs G = view(gs, sys);
   // Long vectors: a cluster of CTAs per right-hand side, so that the FP64
   // work of the orthogonalisation is spread over more SMs than there are
   // live right-hand sides.
@@ -855,23 +1127,24 @@ cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState 
 
 cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0,
                             const double *omega_all, double *Zc, double *slot_omega,
-                            double *gs_omega) {
+                            double *gs_omega, int *gs_dir) {
   if (n <= 0) return cudaSuccess;
-  rhs_init_kernel<<<n, 256, 0, st>>>(n, g0, sys.n_prod, omega_all, sys.dip, Zc, slot_omega, gs_omega);
+  rhs_init_kernel<<<n, 256, 0, st>>>(n, g0, sys.n_prod, omega_all, sys.dip, Zc, slot_omega,
+                                     gs_omega, gs_dir);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gmres_guess(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n, int g0,
                                const double *x0) {
   if (n <= 0) return cudaSuccess;
-  gmres_guess_kernel<<<n, NT, 0, st>>>(view(gs, sys.n_prod), g0, x0);
+  gmres_guess_kernel<<<n, NT, 0, st>>>(view(gs, sys), g0, x0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gmres_export(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n, int g0,
                                 double *X) {
   if (n <= 0) return cudaSuccess;
-  gmres_export_kernel<<<n, NT, 0, st>>>(view(gs, sys.n_prod), g0, X);
+  gmres_export_kernel<<<n, NT, 0, st>>>(view(gs, sys), g0, X);
   return cudaGetLastError();
 }
 

@@ -382,6 +382,12 @@ struct GmresState {
   int *act2 = nullptr;      // [cap] second list (right-hand sides awaiting A x) when split
   int *count = nullptr;     // [2]
   unsigned long long *bytes = nullptr;   // [1] algorithmic bytes of the GMRES steps
+  // stopping rule: 0 relative residual, 1 eps_P <= tol, 2 eps_P and eps_X <= tol
+  // (Sec. 4.1 error estimates; the buffers below exist only for 1 and 2)
+  int stop = 0;
+  int *dir = nullptr;       // [cap] field direction of each right-hand side
+  double *crit = nullptr;   // [cap][10] scalars of the estimates (gmres.cu)
+  double2 *cvec = nullptr;  // [cap][3 m + 2] <d|v_i>, <x0|v_i>, <d|A v_i> of the cycle
 };
 
 cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
@@ -401,7 +407,7 @@ cudaError_t launch_gmres_step(cudaStream_t st, const DevSystem &sys, GmresState 
 // Zc rows 2r, 2r+1 = (d_{g%3}, 0), slot and solver frequencies set.
 cudaError_t launch_rhs_init(cudaStream_t st, const DevSystem &sys, int n, int g0,
                             const double *omega_all, double *Zc, double *slot_omega,
-                            double *gs_omega);
+                            double *gs_omega, int *gs_dir);
 // x of right-hand sides g0..g0+n-1 = rows of x0 (interleaved); their first
 // product is then the residual of the guess.
 cudaError_t launch_gmres_guess(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n, int g0,

@@ -261,6 +261,8 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   if (o->restart < 1 || o->restart > 256 || o->max_restarts < 1 || !(o->tol > 0.0) ||
       !std::isfinite(o->tol) || o->batch < 1)
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "bad options (restart 1..256, max_restarts >= 1, tol > 0, batch >= 1)");
+  if (o->stop < TDDFT_STOP_RESIDUAL || o->stop > TDDFT_STOP_EPS_PX)
+    return fail(nullptr, TDDFT_ERR_INVALID_ARG, "unknown stopping rule");
   std::string msg;
   tddft_status code;
   int n_occ = 0;
@@ -419,6 +421,10 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   }
   AL(g.x, S * 2 * np); AL(g.b, S * 2 * np);
   AL(g.act, S); AL(g.act2, S); AL(g.count, 2); AL(g.rho0, S); AL(g.bytes, 1);
+  g.stop = o->stop;
+  if (g.stop) {
+    AL(g.dir, S); AL(g.crit, S * 10); AL(g.cvec, S * (3 * m + 2));
+  }
   if (e == cudaSuccess) e = cudaMemset(g.bytes, 0, sizeof(unsigned long long));
   c->timer.dev_bytes = g.bytes;
   c->timer.dev_bytes_cls = kcGmresStep;
@@ -712,11 +718,11 @@ static tddft_status polarizability_impl(tddft_ctx *c, int32_t n_omega, const dou
 
   bool all_conv = true;
   std::vector<int> h_mv(S), h_cy(S), h_cv(S), h_fl(S);
-  std::vector<double> h_res(S);
+  std::vector<double> h_res(S), h_crit(g.stop ? (size_t)S * 10 : 0);
   const long max_iter = (long)(g.max_restarts + 1) * (g.m + 1) + 4;
   for (int g0 = 0; g0 < total; g0 += S) {
     const int n = std::min(S, total - g0);
-    CUDA_TRY(c, launch_rhs_init(st, c->sys, n, g0, d_omega, c->Zc, c->wk.omega, g.omega));
+    CUDA_TRY(c, launch_rhs_init(st, c->sys, n, g0, d_omega, c->Zc, c->wk.omega, g.omega, g.dir));
     CUDA_TRY(c, launch_rhs_formation(st, c->sys, c->wk, n, g0, d_omega, eps, c->Z3, c->a3,
                                      c->Wout));
     CUDA_TRY(c, launch_gmres_start(st, c->sys, g, n, c->Wout));
@@ -783,6 +789,9 @@ static tddft_status polarizability_impl(tddft_ctx *c, int32_t n_omega, const dou
     CUDA_TRY(c, cudaMemcpyAsync(h_cv.data(), g.conv, n * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaMemcpyAsync(h_res.data(), g.resid, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaMemcpyAsync(h_fl.data(), g.flags, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (g.stop)
+      CUDA_TRY(c, cudaMemcpyAsync(h_crit.data(), g.crit, (size_t)n * 10 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
     c->timer.resolve();
     for (int r = 0; r < n; ++r) {
@@ -794,6 +803,8 @@ static tddft_status polarizability_impl(tddft_ctx *c, int32_t n_omega, const dou
         t.resid = h_res[r];
         t.converged = h_cv[r];
         t.flags = h_fl[r];
+        t.eps_p = g.stop ? h_crit[(size_t)r * 10 + 7] : NAN;
+        t.eps_x = g.stop ? h_crit[(size_t)r * 10 + 8] : NAN;
       }
     }
   }
@@ -989,7 +1000,8 @@ tddft_status tddft_batch_polarizability(tddft_batch *b, int32_t n_omega, const d
       splitv.push_back(split);
       minbv.push_back(residual_batch(split, n));
       // right-hand sides of this round, on the molecule's stream
-      BCUDA(b, launch_rhs_init(c->st, c->sys, n, g0, d_omega[i], c->Zc, c->wk.omega, g.omega));
+      BCUDA(b, launch_rhs_init(c->st, c->sys, n, g0, d_omega[i], c->Zc, c->wk.omega, g.omega,
+                               g.dir));
       BCUDA(b, launch_rhs_formation(c->st, c->sys, c->wk, n, g0, d_omega[i], eps, c->Z3, c->a3,
                                     c->Wout));
       BCUDA(b, launch_gmres_start(c->st, c->sys, g, n, c->Wout));
@@ -1037,12 +1049,15 @@ tddft_status tddft_batch_polarizability(tddft_batch *b, int32_t n_omega, const d
       const int n = nv[a], g0 = g0v[a];
       BCUDA(b, launch_polarization(c->st, c->sys, g, n, g0, d_P[i]));
       std::vector<int> mv(n), cy(n), cv(n), fl(n);
-      std::vector<double> rs(n);
+      std::vector<double> rs(n), cr(g.stop ? (size_t)n * 10 : 0);
       BCUDA(b, cudaMemcpyAsync(mv.data(), g.matvecs, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
       BCUDA(b, cudaMemcpyAsync(cy.data(), g.cycles, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
       BCUDA(b, cudaMemcpyAsync(cv.data(), g.conv, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
       BCUDA(b, cudaMemcpyAsync(fl.data(), g.flags, n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
       BCUDA(b, cudaMemcpyAsync(rs.data(), g.resid, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      if (g.stop)
+        BCUDA(b, cudaMemcpyAsync(cr.data(), g.crit, (size_t)n * 10 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->st));
       BCUDA(b, cudaStreamSynchronize(c->st));
       if (check_device_error(c) != TDDFT_OK)
         return bfail(b, TDDFT_ERR_TIMEOUT, "molecule " + std::to_string(i) + ": " + c->err);
@@ -1055,6 +1070,8 @@ tddft_status tddft_batch_polarizability(tddft_batch *b, int32_t n_omega, const d
           t.resid = rs[q];
           t.converged = cv[q];
           t.flags = fl[q];
+          t.eps_p = g.stop ? cr[(size_t)q * 10 + 7] : NAN;
+          t.eps_x = g.stop ? cr[(size_t)q * 10 + 8] : NAN;
         }
       }
     }

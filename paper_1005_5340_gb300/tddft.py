@@ -21,6 +21,8 @@ STATUS_NAMES = ["OK", "INVALID_ARG", "SHAPE", "NOMEM", "CUDA", "NOT_CONVERGED", 
                 "UNSUPPORTED"]
 DEVICE_PTRS = 1
 PREC = {"fp64": 0, "fp64emu": 1, "bf16x3": 2, "bf16x3emu": 3}
+# GMRES stopping rules (Sec. 4.1): relative residual, eps_P, eps_P and eps_X
+STOP = {"residual": 0, "eps_p": 1, "eps_px": 2}
 
 
 class TddftError(RuntimeError):
@@ -42,13 +44,15 @@ class _Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_restarts", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("batch", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("inner_tol", ctypes.c_double), ("graph", ctypes.c_int32)]
+                ("inner_tol", ctypes.c_double), ("graph", ctypes.c_int32),
+                ("stop", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("matvecs", ctypes.c_int32), ("cycles", ctypes.c_int32),
                 ("resid", ctypes.c_double), ("converged", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("eps_p", ctypes.c_double),
+                ("eps_x", ctypes.c_double)]
 
 
 # Every exported symbol with its ctypes signature (checked by the tests
@@ -152,7 +156,7 @@ class Context:
 
     def __init__(self, system, *, restart: int = 40, max_restarts: int = 200, tol: float = 1e-6,
                  batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4, stream=None,
-                 graph: bool = False):
+                 graph: bool = False, stop: str = "residual"):
         lib = load_library()
         self._lib = lib
         s, keep = _marshal(system)
@@ -160,7 +164,7 @@ class Context:
             stream = _current_stream()
         self.stream_handle = stream
         o = _Options(PREC[prec], restart, max_restarts, tol, batch, stream or 0, inner_tol,
-                     1 if graph else 0)
+                     1 if graph else 0, STOP[stop])
         self.prec = prec
         h = ctypes.c_void_p()
         st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
@@ -352,12 +356,13 @@ class Batch:
     """Several molecules solved together (tddft_batch_*)."""
 
     def __init__(self, systems, *, restart: int = 40, max_restarts: int = 200, tol: float = 1e-6,
-                 batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4):
+                 batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4,
+                 stop: str = "residual"):
         lib = load_library()
         self._lib = lib
         marsh = [_marshal(s) for s in systems]
         arr = (_System * len(systems))(*[m[0] for m in marsh])
-        o = _Options(PREC[prec], restart, max_restarts, tol, batch, None, inner_tol, 0)
+        o = _Options(PREC[prec], restart, max_restarts, tol, batch, None, inner_tol, 0, STOP[stop])
         h = ctypes.c_void_p()
         st = lib.tddft_batch_create(len(systems), arr, ctypes.byref(o), ctypes.byref(h))
         if st != OK:
@@ -402,7 +407,9 @@ def _stats_dict(stats, n):
         cycles=np.array([s.cycles for s in stats]).reshape(n, 3),
         resid=np.array([s.resid for s in stats]).reshape(n, 3),
         converged=np.array([s.converged for s in stats], dtype=bool).reshape(n, 3),
-        guess_rejected=np.array([s.flags & 1 for s in stats], dtype=bool).reshape(n, 3))
+        guess_rejected=np.array([s.flags & 1 for s in stats], dtype=bool).reshape(n, 3),
+        eps_p=np.array([s.eps_p for s in stats]).reshape(n, 3),
+        eps_x=np.array([s.eps_x for s in stats]).reshape(n, 3))
 
 
 class Mlp:

@@ -24,6 +24,36 @@ def test_every_declared_function_is_exported_and_bound(lib):
     assert set(tddft.SIGNATURES) <= set(names)
 
 
+def test_struct_layouts_match_the_header(tmp_path):
+    """Sizes and field offsets of the structs the binding passes by pointer,
+    as a C compiler lays them out from include/tddft.h."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"tddft_system": tddft._System, "tddft_options": tddft._Options,
+               "tddft_solve_stats": tddft.SolveStats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "tddft.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(out[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(out[f"{cname}.{f}"]) == getattr(py, f).offset, f"{cname}.{f}"
+
+
 def _create(sysm, **opt):
     lib = tddft.load_library()
     keep = dict(
@@ -42,7 +72,7 @@ def _create(sysm, **opt):
                       keep["K"].ctypes.data, keep["d"].ctypes.data)
     o = tddft._Options(opt.get("prec", 0), opt.get("restart", 10), opt.get("max_restarts", 5),
                        opt.get("tol", 1e-8), opt.get("batch", 4), None, opt.get("inner_tol", 1e-4),
-                       opt.get("graph", 0))
+                       opt.get("graph", 0), opt.get("stop", 0))
     h = ctypes.c_void_p()
     st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
     return st, lib.tddft_last_error(None).decode(), h
@@ -97,6 +127,8 @@ def test_validation_rejects_bad_input_before_device_work(lib):
     assert _bad(lambda s: None, prec=2, inner_tol=1.5)[0] == tddft.ERR_INVALID_ARG
     assert _bad(lambda s: None, prec=3, inner_tol=0.0)[0] == tddft.ERR_INVALID_ARG
     assert _bad(lambda s: None, prec=-1)[0] == tddft.ERR_UNSUPPORTED
+    assert _bad(lambda s: None, stop=3)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, stop=-1)[0] == tddft.ERR_INVALID_ARG
 
 
 def test_emulated_gemm_rejects_bad_arguments_on_the_host(lib):
