@@ -146,6 +146,10 @@ typedef enum {
  *      and the cycle's <d|v_i>, <x0|v_i>, <d|A v_i>) meet the rule, and the
  *      solve ends when the rule holds for the float64 residual recomputed at
  *      the end of the cycle, with |A^-1| of the cycle's last step.
+ *  emu_slices: slices of the emulated float64 products (TDDFT_PREC_FP64_EMU,
+ *      TDDFT_PREC_BF16X3_IR_EMU): 0 chooses them (6 for FP64_EMU; from tol
+ *      for BF16X3_IR_EMU), else 3..8.  Fewer slices are faster and coarser:
+ *      s slices keep about 7 s + 1 bits of each row or column.
  */
 typedef struct {
   int32_t prec;
@@ -157,6 +161,7 @@ typedef struct {
   double inner_tol;
   int32_t graph;
   int32_t stop;
+  int32_t emu_slices;
 } tddft_options;
 
 /* Per-(omega, direction) solver report. */

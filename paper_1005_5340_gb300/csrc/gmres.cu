@@ -104,6 +104,8 @@ struct Gs {
   const int *dir;      // [cap] direction of each right-hand side
   double *crit;        // [cap][kCrit]
   double2 *cvec;       // [cap][3 m + 2]: delta_0..m, xi_0..m, phi_0..m-1
+  const float *dipf;   // the dipoles in float32 (float32 basis with estimates), else NULL
+  float *xf;           // x in float32 (float32 basis with the eps_X estimate), else NULL
 };
 
 Gs view(const GmresState &s, const DevSystem &sys) {
@@ -123,12 +125,21 @@ Gs view(const GmresState &s, const DevSystem &sys) {
   v.dir = s.dir;
   v.crit = s.crit;
   v.cvec = s.cvec;
+  v.dipf = s.dipf;
+  v.xf = s.xf;
   return v;
 }
 
 template <class T> __device__ __forceinline__ T *basis(const Gs &G);
 template <> __device__ __forceinline__ double *basis<double>(const Gs &G) { return G.V; }
 template <> __device__ __forceinline__ float *basis<float>(const Gs &G) { return G.Vf; }
+// the dipoles and x in the basis type, for the error-estimate dot products
+template <class T> __device__ __forceinline__ const T *dip_t(const Gs &G);
+template <> __device__ __forceinline__ const double *dip_t<double>(const Gs &G) { return G.dip; }
+template <> __device__ __forceinline__ const float *dip_t<float>(const Gs &G) { return G.dipf; }
+template <class T> __device__ __forceinline__ T *x_t(const Gs &G);
+template <> __device__ __forceinline__ double *x_t<double>(const Gs &G) { return G.x; }
+template <> __device__ __forceinline__ float *x_t<float>(const Gs &G) { return G.xf; }
 
 // F num / den, read as 0 when num = 0 and as infinity when only den = 0.
 __device__ inline double est_ratio(double F, double num, double den) {
@@ -157,6 +168,8 @@ __global__ void __launch_bounds__(NT) gmres_start_kernel(Gs G, const double *__r
     x[e] = 0.0;
     s[0] += t * t;
   }
+  if (G.xf)
+    for (int e = threadIdx.x; e < 2 * N; e += NT) G.xf[(int64_t)2 * r * N + e] = 0.0f;
   if (G.stop) {
     const double *d = G.dip + (int64_t)G.dir[r] * N;
     for (int e = threadIdx.x; e < N; e += NT) {
@@ -301,7 +314,9 @@ __device__ void cluster_sum(double (&v)[NV], double *red, double *clx) {
 // are reduced across the cluster through distributed shared memory.  Every
 // CTA takes the same decisions from the same totals; rank 0 writes the
 // per-right-hand-side scalars.
-template <int P, class T>
+// EST: 0 the residual rule; 1 and 2 the error estimates (eps_P; eps_P and
+// eps_X), the latter also needing <x0|v_i>.
+template <int P, class T, int EST>
 __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__restrict__ list,
                                                         const double *__restrict__ Wout,
                                                         const int *__restrict__ dcnt,
@@ -342,16 +357,13 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     // [0] ||r||^2; with the error estimates also <d|r>, <d|b>, <d|x>, <x|r>
     // (complex) and ||x||^2
     double s2[10] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const double *d = EST ? G.dip + (int64_t)G.dir[r] * N : nullptr;
     for (int e = lo + tid; e < hi; e += NT) {
       const double tr = b[e] - win[e], ti = b[N + e] - win[N + e];
       Vr[e] = (T)tr;
       Vr[N + e] = (T)ti;
       s2[0] += tr * tr + ti * ti;
-    }
-    if (G.stop) {
-      const double *d = G.dip + (int64_t)G.dir[r] * N;
-      for (int e = lo + tid; e < hi; e += NT) {
-        const double tr = b[e] - win[e], ti = b[N + e] - win[N + e];
+      if constexpr (EST > 0) {
         const double de = d[e], xr = x[e], xi = x[N + e];
         s2[1] = fma(de, tr, s2[1]);
         s2[2] = fma(de, ti, s2[2]);
@@ -363,6 +375,8 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
         s2[8] = fma(xr, ti, fma(-xi, tr, s2[8]));
         s2[9] = fma(xr, xr, fma(xi, xi, s2[9]));
       }
+    }
+    if constexpr (EST > 0) {
       cluster_sum<P, 10>(s2, red, clx);
     } else {
       double t1[1] = {s2[0]};
@@ -380,6 +394,13 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
         x[e] = 0.0;
         x[N + e] = 0.0;
       }
+      if constexpr (EST == 2 && sizeof(T) == 4) {
+        float *xf = G.xf + (int64_t)2 * r * N;
+        for (int e = lo + tid; e < hi; e += NT) {
+          xf[e] = 0.0f;
+          xf[N + e] = 0.0f;
+        }
+      }
       rho = G.bnorm[r];
       rejected = true;
       // r = b and x = 0
@@ -390,12 +411,12 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     const double rel = rho / G.bnorm[r];
     double ep = 0.0, ex = 0.0;
     bool met;
-    if (G.stop) {
+    if constexpr (EST > 0) {
       // eps_P and eps_X of x with the |A^-1| of the last step of the last cycle
       const double Fn = sqrt(G.crit[(int64_t)r * kCrit + kCrFsq]);
       ep = est_ratio(Fn, hypot(s2[1], s2[2]), hypot(s2[5], s2[6]));
       ex = est_ratio(Fn, rho, sqrt(s2[9]));
-      met = rho == 0.0 || stop_met(G.stop, ep, ex, G.tol);
+      met = rho == 0.0 || stop_met(EST, ep, ex, G.tol);
     } else {
       met = rel <= G.tol;
     }
@@ -416,7 +437,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
       G.matvecs[r] += 1;
       G.resid[r] = rel;
       if (rejected) G.flags[r] |= 1;
-      if (G.stop) {
+      if constexpr (EST > 0) {
         double *cr = G.crit + (int64_t)r * kCrit;
         cr[kCrEpsP] = ep;
         cr[kCrEpsX] = ex;
@@ -450,7 +471,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   const int j = G.jcur[r];
   const double2 gj0 = G.g[(int64_t)r * (m + 1) + j];
   const double rho0 = G.rho0[r];
-  if (G.stop && tid == 0) {
+  if (EST > 0 && tid == 0) {
     // read before the first cluster synchronisation: rank 0 rewrites them
     const double *cr = G.crit + (int64_t)r * kCrit;
     s_cr[0] = cr[kCrFsum];
@@ -595,10 +616,17 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   // w = A v_j - V h, with ||w||^2 (coefficients in type T)
   for (int i = tid; i <= j; i += NT) hT[i] = make_float2((float)hs[i].x, (float)hs[i].y);
   __syncthreads();
-  double n1[1] = {0.0};
+  // ||w||^2, and with the error estimates <d|A v_j>, <d|w> (and <x0|w>) from
+  // the values in registers (d and x0 in the basis type)
+  double q7[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const T *dT = nullptr, *x0T = nullptr;
+  if constexpr (EST > 0) {
+    dT = dip_t<T>(G) + (int64_t)G.dir[r] * N;
+    if constexpr (EST == 2) x0T = x_t<T>(G) + (int64_t)2 * r * N;
+  }
   if (vec4) {
     // four elements per thread and load (float32 basis); w holds A v_j here
-    float nacc = 0.f;
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float4 *w_r = (float4 *)(w + lo), *w_i = (float4 *)(w + N + lo);
     for (int q = tid; q < n4; q += NT) {
       float4 ar = make_float4(0.f, 0.f, 0.f, 0.f), ai = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -621,13 +649,33 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
       const float4 ni = make_float4(d.x - ai.x, d.y - ai.y, d.z - ai.z, d.w - ai.w);
       w_r[q] = nr;
       w_i[q] = ni;
-      nacc += nr.x * nr.x + nr.y * nr.y + nr.z * nr.z + nr.w * nr.w + ni.x * ni.x +
-              ni.y * ni.y + ni.z * ni.z + ni.w * ni.w;
+      acc[0] += nr.x * nr.x + nr.y * nr.y + nr.z * nr.z + nr.w * nr.w + ni.x * ni.x +
+                ni.y * ni.y + ni.z * ni.z + ni.w * ni.w;
+      if constexpr (EST > 0) {
+        const float4 dp = ((const float4 *)((const float *)dT + lo))[q];
+        acc[1] += dp.x * c.x + dp.y * c.y + dp.z * c.z + dp.w * c.w;
+        acc[2] += dp.x * d.x + dp.y * d.y + dp.z * d.z + dp.w * d.w;
+        acc[3] += dp.x * nr.x + dp.y * nr.y + dp.z * nr.z + dp.w * nr.w;
+        acc[4] += dp.x * ni.x + dp.y * ni.y + dp.z * ni.z + dp.w * ni.w;
+        if constexpr (EST == 2) {
+          const float4 xr = ((const float4 *)((const float *)x0T + lo))[q];
+          const float4 xi = ((const float4 *)((const float *)x0T + N + lo))[q];
+          acc[5] += xr.x * nr.x + xi.x * ni.x + xr.y * nr.y + xi.y * ni.y + xr.z * nr.z +
+                    xi.z * ni.z + xr.w * nr.w + xi.w * ni.w;
+          acc[6] += xr.x * ni.x - xi.x * nr.x + xr.y * ni.y - xi.y * nr.y + xr.z * ni.z -
+                    xi.z * nr.z + xr.w * ni.w - xi.w * nr.w;
+        }
+      }
     }
-    for (int off = 16; off > 0; off >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, off);
-    n1[0] = lane == 0 ? (double)nacc : 0.0;   // the block sum adds the warps' totals
+    constexpr int NQ = EST == 0 ? 1 : (EST == 1 ? 5 : 7);
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      float v = acc[k];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      q7[k] = lane == 0 ? (double)v : 0.0;   // the block sum adds the warps' totals
+    }
   } else {
-    T nacc = 0;
+    T acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int e = lo + tid; e < hi; e += NT) {
       T ar = 0, ai = 0;
 #pragma unroll 4
@@ -645,42 +693,40 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
         ar += hx * vr - hy * vi;
         ai += hx * vi + hy * vr;
       }
-      const T nr = aw[e] - ar, ni = aw[N + e] - ai;
+      const T avr = aw[e], avi = aw[N + e];
+      const T nr = avr - ar, ni = avi - ai;
       w[e] = nr;
       w[N + e] = ni;
-      nacc += nr * nr + ni * ni;
+      acc[0] += nr * nr + ni * ni;
+      if constexpr (EST > 0) {
+        const T de = dT[e];
+        acc[1] += de * avr;
+        acc[2] += de * avi;
+        acc[3] += de * nr;
+        acc[4] += de * ni;
+        if constexpr (EST == 2) {
+          const T xr = x0T[e], xi = x0T[N + e];
+          acc[5] += xr * nr + xi * ni;
+          acc[6] += xr * ni - xi * nr;
+        }
+      }
     }
-    n1[0] = (double)nacc;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) q7[k] = (double)acc[k];
   }
-  if (G.stop) {
-    // <d|A v_j>, <d|w> and <x0|w> over this CTA's elements (A v_j from the
-    // operator output; w as just written, by other threads of this CTA)
-    __syncthreads();
-    const double *d = G.dip + (int64_t)G.dir[r] * N;
-    const double *x0 = G.x + (int64_t)2 * r * N;
-    double q7[7] = {n1[0], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int e = lo + tid; e < hi; e += NT) {
-      const double de = d[e], ar = win[e], ai = win[N + e];
-      const double nr = (double)w[e], ni = (double)w[N + e];
-      const double xr = x0[e], xi = x0[N + e];
-      q7[1] = fma(de, ar, q7[1]);
-      q7[2] = fma(de, ai, q7[2]);
-      q7[3] = fma(de, nr, q7[3]);
-      q7[4] = fma(de, ni, q7[4]);
-      q7[5] = fma(xr, nr, fma(xi, ni, q7[5]));
-      q7[6] = fma(xr, ni, fma(-xi, nr, q7[6]));
-    }
+  if constexpr (EST > 0) {
     cluster_sum<P, 7>(q7, red, clx);   // synchronises: w complete
-    n1[0] = q7[0];
     if (tid == 0) {
       s_phi = make_double2(q7[1], q7[2]);
       s_dw = make_double2(q7[3], q7[4]);
       s_xw = make_double2(q7[5], q7[6]);
     }
   } else {
+    double n1[1] = {q7[0]};
     cluster_sum<P, 1>(n1, red, clx);   // synchronises: w complete
+    q7[0] = n1[0];
   }
-  const double hn = sqrt(n1[0]);
+  const double hn = sqrt(q7[0]);
 
   // the earlier rotations to shared memory (all threads), then thread 0
   // applies them to the new column in order
@@ -725,7 +771,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     // a cycle ends at the tolerance (of the residual rule; the error
     // estimates decide below), at the restart length, on breakdown, or
     // (refinement forms) once it has reduced its own residual by inner_tol
-    const bool fin = (!G.stop && est <= G.tol * G.bnorm[r]) || (j + 1 == m) || !(hn > 0.0) ||
+    const bool fin = (!EST && est <= G.tol * G.bnorm[r]) || (j + 1 == m) || !(hn > 0.0) ||
                      (est <= G.inner_tol * rho0);
     finish_flag = fin ? 1 : 0;
     s_gj = gj;
@@ -739,7 +785,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
   __syncthreads();
   const double c_new = gq[0].x;
   const double2 sv_new = hq[0], gnext_new = hq[1];
-  if (G.stop) {
+  if constexpr (EST > 0) {
     // R_j [y, c] = [g, e_j] (R_j: earlier rotated columns, shared memory when
     // they fit, and column j from this step), then the estimates of x_j
     const int k = j + 1;
@@ -813,7 +859,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
         const double Fn = sqrt(Fsq);
         const double ep = est_ratio(Fn, hypot(dr, di), hypot(Pr, Pi));
         const double ex = est_ratio(Fn, s_est, sqrt(xx));
-        if (stop_met(G.stop, ep, ex, G.tol)) finish_flag = 1;
+        if (stop_met(EST, ep, ex, G.tol)) finish_flag = 1;
         s_F[0] = Fsum;
         s_F[1] = Fsq;
       }
@@ -833,14 +879,16 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     else G.jcur[r] = j + 1;
     // algorithmic traffic of this step: basis vectors (2 N sizeof(T) bytes)
     // v_0..v_j read twice, v_{j+1} written and normalised, A v_j read
-    // (16 N); at a cycle end v_0..v_j read again and x read and written;
-    // the error estimates read d (8 N), A v_j and x0 (16 N each) and w
-    const unsigned long long nb = 2ull * (j + 1) + 3ull + (fin ? (unsigned long long)j + 1ull : 0ull) +
-                                  (G.stop ? 1ull : 0ull);
+    // (16 N); at a cycle end v_0..v_j read again and x read and written
+    const unsigned long long nb = 2ull * (j + 1) + 3ull + (fin ? (unsigned long long)j + 1ull : 0ull);
     const unsigned long long nd = 1ull + (fin ? 2ull : 0ull);
-    const unsigned long long ne = G.stop ? 40ull : 0ull;
+    // the error estimates read d (and x0) in the basis type; x0's float32
+    // copy is rewritten with x at a cycle end
+    const unsigned long long ne =
+        (EST == 0 ? 0ull : (EST == 1 ? 1ull : 3ull)) * sizeof(T) +
+        (EST == 2 && sizeof(T) == 4 && fin ? 8ull : 0ull);
     atomicAdd(G.bytes, (nb * 2ull * sizeof(T) + nd * 16ull + ne) * (unsigned long long)N);
-    if (G.stop) {
+    if constexpr (EST > 0) {
       double *cr = G.crit + (int64_t)r * kCrit;
       cr[kCrFsum] = s_F[0];
       cr[kCrFsq] = s_F[1];
@@ -855,7 +903,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     }
   }
   __syncthreads();
-  if (finish_flag && !G.stop) {
+  if (finish_flag && !EST) {
     // back substitution R y = g (with the error estimates, ys holds y already) with the rotated (upper triangular)
     // Hessenberg matrix: its earlier columns (shared memory when they fit)
     // and g_0..g_{j-1} staged by all threads, column j and g_j from this
@@ -941,6 +989,12 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
         p0.x += (double)ar.x; p0.y += (double)ar.y; p1.x += (double)ar.z; p1.y += (double)ar.w;
         q0.x += (double)ai.x; q0.y += (double)ai.y; q1.x += (double)ai.z; q1.y += (double)ai.w;
         x_r[2 * q] = p0; x_r[2 * q + 1] = p1; x_i[2 * q] = q0; x_i[2 * q + 1] = q1;
+        if constexpr (EST == 2) {
+          // the float32 copy of x for the next cycle's <x0|w>
+          float *xf = G.xf + (int64_t)2 * r * N;
+          ((float4 *)(xf + lo))[q] = make_float4((float)p0.x, (float)p0.y, (float)p1.x, (float)p1.y);
+          ((float4 *)(xf + N + lo))[q] = make_float4((float)q0.x, (float)q0.y, (float)q1.x, (float)q1.y);
+        }
       }
     } else
     for (int e = lo + tid; e < hi; e += NT) {
@@ -962,6 +1016,11 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
       }
       x[e] += (double)ar;
       x[N + e] += (double)ai;
+      if constexpr (EST == 2 && sizeof(T) == 4) {
+        float *xf = G.xf + (int64_t)2 * r * N;
+        xf[e] = (float)x[e];
+        xf[N + e] = (float)x[N + e];
+      }
     }
   }
 }
@@ -978,6 +1037,13 @@ __global__ void __launch_bounds__(NT) gmres_guess_kernel(Gs G, int g0,
   for (int e = threadIdx.x; e < N; e += NT) {
     x[e] = src[2 * e];
     x[N + e] = src[2 * e + 1];
+  }
+  if (G.xf) {
+    float *xf = G.xf + (int64_t)2 * r * N;
+    for (int e = threadIdx.x; e < N; e += NT) {
+      xf[e] = (float)src[2 * e];
+      xf[N + e] = (float)src[2 * e + 1];
+    }
   }
   if (threadIdx.x == 0) {
     G.state[r] = kStateResid;
@@ -1044,20 +1110,20 @@ __global__ void __launch_bounds__(NT) polarization_kernel(int g0, int n_prod,
   }
 }
 
-template <class T>
-cudaError_t launch_step_t(cudaStream_t st, const Gs &G, int P, int S, const int *list,
+template <class T, int EST>
+cudaError_t launch_step_e(cudaStream_t st, const Gs &G, int P, int S, const int *list,
                           const double *Wout, const int *dcnt, int h_smem, size_t dyn) {
   static bool attr_set = false;
   if (!attr_set) {
     const int mx = (int)((size_t)kHsmemMaxM * (kHsmemMaxM + 1) * sizeof(double2));
-    cudaFuncSetAttribute(gmres_step_kernel<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(gmres_step_kernel<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(gmres_step_kernel<4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(gmres_step_kernel<8, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<1, T, EST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<2, T, EST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<4, T, EST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(gmres_step_kernel<8, T, EST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     attr_set = true;
   }
   if (P == 1) {
-    gmres_step_kernel<1, T><<<dim3(1, S), NT, dyn, st>>>(G, list, Wout, dcnt, h_smem);
+    gmres_step_kernel<1, T, EST><<<dim3(1, S), NT, dyn, st>>>(G, list, Wout, dcnt, h_smem);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -1072,9 +1138,25 @@ cudaError_t launch_step_t(cudaStream_t st, const Gs &G, int P, int S, const int 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (P == 8) return cudaLaunchKernelEx(&cfg, gmres_step_kernel<8, T>, G, list, Wout, dcnt, h_smem);
-  return P == 4 ? cudaLaunchKernelEx(&cfg, gmres_step_kernel<4, T>, G, list, Wout, dcnt, h_smem)
-                : cudaLaunchKernelEx(&cfg, gmres_step_kernel<2, T>, G, list, Wout, dcnt, h_smem);
+  if (P == 8) return cudaLaunchKernelEx(&cfg, gmres_step_kernel<8, T, EST>, G, list, Wout, dcnt, h_smem);
+  return P == 4 ? cudaLaunchKernelEx(&cfg, gmres_step_kernel<4, T, EST>, G, list, Wout, dcnt, h_smem)
+                : cudaLaunchKernelEx(&cfg, gmres_step_kernel<2, T, EST>, G, list, Wout, dcnt, h_smem);
+}
+
+template <class T>
+cudaError_t launch_step_t(cudaStream_t st, const Gs &G, int P, int S, const int *list,
+                          const double *Wout, const int *dcnt, int h_smem, size_t dyn) {
+  switch (G.stop) {
+    case 0: return launch_step_e<T, 0>(st, G, P, S, list, Wout, dcnt, h_smem, dyn);
+    case 1: return launch_step_e<T, 1>(st, G, P, S, list, Wout, dcnt, h_smem, dyn);
+    default: return launch_step_e<T, 2>(st, G, P, S, list, Wout, dcnt, h_smem, dyn);
+  }
+}
+
+// Float32 copies of the dipoles for the float32-basis estimates.
+__global__ void dip_to_f32_kernel(int n, const double *__restrict__ src, float *__restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
 }
 
 }  // namespace
@@ -1088,6 +1170,14 @@ cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState
   else
     gmres_start_kernel<double><<<n, NT, 0, st>>>(view(gs, sys), Bplanar);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gmres_prepare(cudaStream_t st, const DevSystem &sys, GmresState &gs) {
+  if (gs.dipf) {
+    dip_to_f32_kernel<<<64, 256, 0, st>>>(3 * sys.n_prod, sys.dip, gs.dipf);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split, int min_b) {

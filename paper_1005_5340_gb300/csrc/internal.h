@@ -388,6 +388,8 @@ struct GmresState {
   int *dir = nullptr;       // [cap] field direction of each right-hand side
   double *crit = nullptr;   // [cap][10] scalars of the estimates (gmres.cu)
   double2 *cvec = nullptr;  // [cap][3 m + 2] <d|v_i>, <x0|v_i>, <d|A v_i> of the cycle
+  float *dipf = nullptr;    // [3][n_prod] dipoles in float32 (float32 basis with estimates)
+  float *xf = nullptr;      // [cap][2][n_prod] x in float32 (float32 basis, rule 2)
 };
 
 cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState &gs, int n,
@@ -396,6 +398,8 @@ cudaError_t launch_gmres_start(cudaStream_t st, const DevSystem &sys, GmresState
 // an Arnoldi step in act (count[0]), those awaiting A x in act2 (count[1]).
 // min_b: with split, the float64 group runs only once min_b right-hand sides
 // await it or no Arnoldi work is left (otherwise count[1] is reported as 0).
+// Create-time constants of the GMRES state (the float32 dipoles).
+cudaError_t launch_gmres_prepare(cudaStream_t st, const DevSystem &sys, GmresState &gs);
 cudaError_t launch_gmres_select(cudaStream_t st, GmresState &gs, int n, int split, int min_b = 1);
 cudaError_t launch_gmres_gather(cudaStream_t st, const DevSystem &sys, GmresState &gs,
                                 const int *list, int S, double *Zc, double *slot_omega,

@@ -263,6 +263,8 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "bad options (restart 1..256, max_restarts >= 1, tol > 0, batch >= 1)");
   if (o->stop < TDDFT_STOP_RESIDUAL || o->stop > TDDFT_STOP_EPS_PX)
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "unknown stopping rule");
+  if (o->emu_slices != 0 && (o->emu_slices < kOzMinSlices || o->emu_slices > kOzMaxSlices))
+    return fail(nullptr, TDDFT_ERR_INVALID_ARG, "emu_slices must be 0 or 3..8");
   std::string msg;
   tddft_status code;
   int n_occ = 0;
@@ -424,7 +426,10 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   g.stop = o->stop;
   if (g.stop) {
     AL(g.dir, S); AL(g.crit, S * 10); AL(g.cvec, S * (3 * m + 2));
+    if (refine) AL(g.dipf, 3 * (size_t)np);
+    if (refine && g.stop == TDDFT_STOP_EPS_PX) AL(g.xf, S * 2 * np);
   }
+  if (e == cudaSuccess) e = launch_gmres_prepare(c->st, d, g);
   if (e == cudaSuccess) e = cudaMemset(g.bytes, 0, sizeof(unsigned long long));
   c->timer.dev_bytes = g.bytes;
   c->timer.dev_bytes_cls = kcGmresStep;
@@ -438,6 +443,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     c->oz.s = o->tol >= 1e-8 ? 5 : (o->tol >= 1e-12 ? 6 : 7);
   else
     c->oz.s = kOzDefaultSlices;
+  if (o->emu_slices) c->oz.s = o->emu_slices;
   if (e == cudaSuccess && c->emu) {
     e = oz_setup(c->st, d, c->oz, (int)S, c->dev_allocs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);

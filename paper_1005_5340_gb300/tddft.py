@@ -45,7 +45,7 @@ class _Options(ctypes.Structure):
                 ("max_restarts", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("batch", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("inner_tol", ctypes.c_double), ("graph", ctypes.c_int32),
-                ("stop", ctypes.c_int32)]
+                ("stop", ctypes.c_int32), ("emu_slices", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):
@@ -156,7 +156,7 @@ class Context:
 
     def __init__(self, system, *, restart: int = 40, max_restarts: int = 200, tol: float = 1e-6,
                  batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4, stream=None,
-                 graph: bool = False, stop: str = "residual"):
+                 graph: bool = False, stop: str = "residual", emu_slices: int = 0):
         lib = load_library()
         self._lib = lib
         s, keep = _marshal(system)
@@ -164,7 +164,7 @@ class Context:
             stream = _current_stream()
         self.stream_handle = stream
         o = _Options(PREC[prec], restart, max_restarts, tol, batch, stream or 0, inner_tol,
-                     1 if graph else 0, STOP[stop])
+                     1 if graph else 0, STOP[stop], emu_slices)
         self.prec = prec
         h = ctypes.c_void_p()
         st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
@@ -357,12 +357,13 @@ class Batch:
 
     def __init__(self, systems, *, restart: int = 40, max_restarts: int = 200, tol: float = 1e-6,
                  batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4,
-                 stop: str = "residual"):
+                 stop: str = "residual", emu_slices: int = 0):
         lib = load_library()
         self._lib = lib
         marsh = [_marshal(s) for s in systems]
         arr = (_System * len(systems))(*[m[0] for m in marsh])
-        o = _Options(PREC[prec], restart, max_restarts, tol, batch, None, inner_tol, 0, STOP[stop])
+        o = _Options(PREC[prec], restart, max_restarts, tol, batch, None, inner_tol, 0, STOP[stop],
+                     emu_slices)
         h = ctypes.c_void_p()
         st = lib.tddft_batch_create(len(systems), arr, ctypes.byref(o), ctypes.byref(h))
         if st != OK:

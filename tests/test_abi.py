@@ -72,7 +72,7 @@ def _create(sysm, **opt):
                       keep["K"].ctypes.data, keep["d"].ctypes.data)
     o = tddft._Options(opt.get("prec", 0), opt.get("restart", 10), opt.get("max_restarts", 5),
                        opt.get("tol", 1e-8), opt.get("batch", 4), None, opt.get("inner_tol", 1e-4),
-                       opt.get("graph", 0), opt.get("stop", 0))
+                       opt.get("graph", 0), opt.get("stop", 0), opt.get("emu_slices", 0))
     h = ctypes.c_void_p()
     st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
     return st, lib.tddft_last_error(None).decode(), h
@@ -129,6 +129,8 @@ def test_validation_rejects_bad_input_before_device_work(lib):
     assert _bad(lambda s: None, prec=-1)[0] == tddft.ERR_UNSUPPORTED
     assert _bad(lambda s: None, stop=3)[0] == tddft.ERR_INVALID_ARG
     assert _bad(lambda s: None, stop=-1)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, prec=1, emu_slices=2)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, prec=1, emu_slices=9)[0] == tddft.ERR_INVALID_ARG
 
 
 def test_emulated_gemm_rejects_bad_arguments_on_the_host(lib):
