@@ -241,6 +241,60 @@ tddft_status tddft_polarizability(tddft_ctx *ctx, int32_t n_omega, const double 
                                   int32_t flags);
 
 /*
+ * Adaptive frequency grid and pole extraction: the step the paper names as
+ * its next one (Sec. 8, conclusions), for a spectrum resolved only where it
+ * has structure.  The absorption is S(omega) = Im alpha_tr(omega) with
+ * alpha_tr = -(P_xx + P_yy + P_zz) / 3 (alpha = -P, eq. eqpolarizability).
+ *
+ * Grid: n_initial uniform points on [w_lo, w_hi] (both included), then
+ * rounds.  The first round takes every interval.  A round solves the
+ * midpoints of its intervals longer than 2 min_step, in ascending order and
+ * as many as the grid has room for, with one tddft_polarizability call
+ * (batched on the GPU).  Both halves of an interval go to the next round when
+ * |S(mid) - (S(left) + S(right)) / 2| > rel_tol * max |S| over the grid so
+ * far.  It stops when no interval is left or the grid holds max_points.
+ *
+ * Poles: each local maximum i of S on the final grid (S_i > S_{i-1},
+ * S_i >= S_{i+1}, S_i > peak_floor * max S) is fitted on its five nearest
+ * grid points (a window of five indices clamped to the grid) with one pole
+ * and a constant background,
+ *     alpha_tr(z) = g / (Omega^2 - z^2) + b,   z = omega + i eps,
+ * by linear least squares in (p = Omega^2, b, q = g + b p):
+ * alpha p + z^2 b - q = alpha z^2.  For an isolated transition this is the
+ * exact form of the response of this model (its poles are the eigenvalues
+ * Omega_n^2 of Delta^2 + W^1/2 M^T K M W^1/2, W = 2 (n_o - n_u) Delta).
+ */
+typedef struct {
+  int32_t n_initial;   /* >= 2 */
+  int32_t max_points;  /* >= n_initial; capacity of omega and P */
+  double rel_tol;      /* > 0 */
+  double min_step;     /* >= 0 (Hartree) */
+  double peak_floor;   /* in [0, 1) */
+} tddft_adaptive_options;
+
+typedef struct {
+  double omega;        /* Omega = sqrt(max(Re p, 0)) (Hartree) */
+  double g_re, g_im;   /* the fitted residue g */
+  double peak;         /* S at the grid maximum */
+  double omega_peak;   /* the grid frequency of that maximum */
+} tddft_pole;
+
+/*
+ * Run the adaptive grid on ctx (its precision, tol, stopping rule and batch)
+ * and extract the poles.  Host buffers: omega [max_points] (ascending on
+ * return), P [max_points][3][3] complex interleaved, poles [max_poles].
+ * *n_points receives the grid size; *n_poles the number of peaks found (the
+ * first max_poles of them, in ascending frequency, are written).
+ * Errors: INVALID_ARG (null pointers, w_hi <= w_lo, eps <= 0, bad options),
+ * and whatever tddft_polarizability returns (NOT_CONVERGED included), in
+ * which case the outputs hold the grid solved so far.
+ */
+tddft_status tddft_spectrum_adaptive(tddft_ctx *ctx, double w_lo, double w_hi, double eps,
+                                     const tddft_adaptive_options *opts, double *omega,
+                                     double *P, int32_t *n_points, tddft_pole *poles,
+                                     int32_t max_poles, int32_t *n_poles);
+
+/*
  * tddft_polarizability with warm starts and the solutions returned.
  *  x0 (may be NULL): n_omega x 3 x n_prod complex interleaved, row w*3+k the
  *      initial guess of (omega[w], direction k).  Each guess first costs one

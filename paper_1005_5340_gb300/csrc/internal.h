@@ -62,6 +62,8 @@ enum KernelClass {
   kcAlphaGather, kcTcStep2, kcTcStep5, kcOzStep2, kcOzStep5, kcCount
 };
 const char *kernel_class_name(int k);
+// Record msg as the context's last error (tddft_last_error) and return s.
+tddft_status set_ctx_error(tddft_ctx *c, tddft_status s, const std::string &msg);
 
 struct Timer {
   bool on = false;

@@ -93,6 +93,10 @@ tddft_status check_omega(tddft_ctx *c, int n, const double *omega, bool device) 
 }  // namespace
 
 namespace tddft {
+tddft_status set_ctx_error(tddft_ctx *c, tddft_status s, const std::string &msg) {
+  return fail(c, s, msg);
+}
+
 const char *kernel_class_name(int k) {
   static const char *names[kcCount] = {
       "f64_gemm_K",  "f64_vertex",   "f64_beta",      "f64_gemm_T1",  "f64_dscale",

@@ -55,6 +55,17 @@ class SolveStats(ctypes.Structure):
                 ("eps_x", ctypes.c_double)]
 
 
+class AdaptiveOptions(ctypes.Structure):
+    _fields_ = [("n_initial", ctypes.c_int32), ("max_points", ctypes.c_int32),
+                ("rel_tol", ctypes.c_double), ("min_step", ctypes.c_double),
+                ("peak_floor", ctypes.c_double)]
+
+
+class Pole(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("g_re", ctypes.c_double), ("g_im", ctypes.c_double),
+                ("peak", ctypes.c_double), ("omega_peak", ctypes.c_double)]
+
+
 # Every exported symbol with its ctypes signature (checked by the tests
 # against include/tddft.h).
 _P = ctypes.c_void_p
@@ -73,6 +84,9 @@ SIGNATURES = {
     "tddft_polarizability_guess": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P,
                                                   _P, _P, _P, ctypes.c_int32]),
     "tddft_sizes": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "tddft_spectrum_adaptive": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, _P, _P, _P, _P, _P,
+                                               ctypes.c_int32, _P]),
     "tddft_tuning": (ctypes.c_int, [_P, _P]),
     "tddft_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "tddft_batch_polarizability": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P]),
@@ -293,6 +307,27 @@ class Context:
             float(h_over_eps), torch.view_as_real(X.contiguous()).data_ptr(), F.data_ptr(),
             torch.view_as_real(lin).data_ptr(), scale.data_ptr()))
         return F, lin, scale
+
+    def spectrum_adaptive(self, w_lo, w_hi, eps, *, n_initial: int = 33, max_points: int = 512,
+                          rel_tol: float = 0.02, min_step: float | None = None,
+                          peak_floor: float = 0.02, max_poles: int = 256):
+        """tddft_spectrum_adaptive: (omega [n], P [n, 3, 3] complex, poles) with
+        poles a list of dicts (omega, g, peak, omega_peak)."""
+        o = AdaptiveOptions(n_initial, max_points, rel_tol,
+                            eps / 8.0 if min_step is None else min_step, peak_floor)
+        om = np.empty(max_points, dtype=np.float64)
+        P = np.empty((max_points, 3, 3), dtype=np.complex128)
+        poles = (Pole * max(1, max_poles))()
+        n_pts, n_pol = ctypes.c_int32(), ctypes.c_int32()
+        st = self._lib.tddft_spectrum_adaptive(self.h, float(w_lo), float(w_hi), float(eps),
+                                               ctypes.byref(o), om.ctypes.data, P.ctypes.data,
+                                               ctypes.byref(n_pts), poles, max_poles,
+                                               ctypes.byref(n_pol))
+        self._check(st)
+        n = n_pts.value
+        out = [dict(omega=p.omega, g=complex(p.g_re, p.g_im), peak=p.peak,
+                    omega_peak=p.omega_peak) for p in poles[:min(n_pol.value, max_poles)]]
+        return om[:n].copy(), P[:n].copy(), out
 
     def polarizability(self, omega, eps, *, raise_on_nonconvergence: bool = True):
         """P[w, i, k] (complex, n_omega x 3 x 3) and per-(w, k) stats."""

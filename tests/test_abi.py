@@ -34,7 +34,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"tddft_system": tddft._System, "tddft_options": tddft._Options,
-               "tddft_solve_stats": tddft.SolveStats}
+               "tddft_solve_stats": tddft.SolveStats,
+               "tddft_adaptive_options": tddft.AdaptiveOptions, "tddft_pole": tddft.Pole}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "tddft.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
@@ -155,6 +156,8 @@ def test_more_than_16_orbitals_per_atom_is_unsupported(lib):
 def test_calls_on_a_null_context_fail_cleanly(lib):
     assert lib.tddft_chi0_apply(None, 1, None, 0.1, None, None, 0) == tddft.ERR_INVALID_ARG
     assert lib.tddft_polarizability(None, 1, None, 0.1, None, None, 0) == tddft.ERR_INVALID_ARG
+    assert lib.tddft_spectrum_adaptive(None, 0.0, 1.0, 0.01, None, None, None, None, None, 0,
+                                       None) == tddft.ERR_INVALID_ARG
     lib.tddft_destroy(None)
     assert isinstance(lib.tddft_last_error(None), bytes)
 
