@@ -215,6 +215,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // graph replays: columns beyond the live count are skipped (whole tiles)
   if (dcnt) N = (int)min((int64_t)N, (int64_t)mul_n * (*dcnt));
   const int n_ntiles = (N + TC_BN - 1) / TC_BN;
+  // the N tiles share the columns evenly (multiples of 16, at most TC_BN):
+  // tiles of one M row block then run at the same pace, so the second one
+  // finds the A tile (the large operand of the K product) still in L2
+  const int tn = min(TC_BN, ((N + n_ntiles - 1) / n_ntiles + 15) & ~15);
   const int ksplit = ep.ksplit;
   const int n_tiles = n_mtiles * n_ntiles * ksplit;
   if ((int)blockIdx.x >= n_tiles) return;
@@ -232,13 +236,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // tile t: M tile fastest, then the K slice (split K), then the N tile;
+  // tile t: M tile fastest, then the K slice (split K), then the N tile of
+  // tn columns;
   // xa / xb: K offsets (elements) of the A and B tiles within a plane
   auto tile_of = [&](int t, int &m0, int &xa, int &xb, int &nkb, int &rows_valid, int &atom,
                      int &n0) {
     const int mt = t % n_mtiles, rest = t / n_mtiles;
     const int ks = rest % ksplit, nt = rest / ksplit;
-    n0 = nt * TC_BN;
+    n0 = nt * tn;
     if (tiles) {
       const GTile g = tiles[mt];
       m0 = g.row0;
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
-      constexpr uint32_t idesc = idesc_bf16(TC_BM, TC_BN);
+      const uint32_t idesc = idesc_bf16(TC_BM, tn);
       const uint32_t base = smem_u32(smem);
       int g = 0, lt = 0;
       bool ok = true;
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       fence_after();
       const int m = m0 + lr;
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN);
-      for (int j0 = 0; j0 < TC_BN; j0 += 16) {
+      for (int j0 = 0; j0 < tn; j0 += 16) {
         DscaleIn di;
         di.eocc = eocc;
         if (EPI == kDscaleSplit) {
