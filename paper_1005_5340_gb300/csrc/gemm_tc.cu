@@ -237,12 +237,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // tile t: M tile fastest, then the K slice (split K), then the N tile of
-  // tn columns;
+  // tn columns; in a cluster launch (ep.ncl > 1) the N tile is fastest, so
+  // the CTAs of a cluster (one GPC, one L2 partition) read the same A tile;
   // xa / xb: K offsets (elements) of the A and B tiles within a plane
   auto tile_of = [&](int t, int &m0, int &xa, int &xb, int &nkb, int &rows_valid, int &atom,
                      int &n0) {
-    const int mt = t % n_mtiles, rest = t / n_mtiles;
-    const int ks = rest % ksplit, nt = rest / ksplit;
+    int mt, ks, nt;
+    if (ep.ncl > 1) {
+      nt = t % n_ntiles;
+      const int rest = t / n_ntiles;
+      mt = rest % n_mtiles;
+      ks = rest / n_mtiles;
+    } else {
+      mt = t % n_mtiles;
+      const int rest = t / n_mtiles;
+      ks = rest % ksplit;
+      nt = rest / ksplit;
+    }
     n0 = nt * tn;
     if (tiles) {
       const GTile g = tiles[mt];
@@ -514,9 +525,36 @@ template <int EPI, int BN>
 cudaError_t launch_tc(cudaStream_t st, int grid, const CUtensorMap &mA, const CUtensorMap &mB,
                       int M, int N, int KpA, int KpB, const TcEpilogue &ep, int *err,
                       const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
-  gemm_tc_kernel<EPI, BN><<<grid, TC_THREADS, TcShape<BN>::SMEM, st>>>(
-      mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n, tiles, n_mtiles);
-  return cudaGetLastError();
+  if (ep.ncl <= 1) {
+    gemm_tc_kernel<EPI, BN><<<grid, TC_THREADS, TcShape<BN>::SMEM, st>>>(
+        mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n, tiles, n_mtiles);
+    return cudaGetLastError();
+  }
+  // clusters of ncl CTAs; the grid is at most the clusters that fit at once
+  // (a persistent CTA that waited for a slot would run its tiles last)
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = TcShape<BN>::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ep.ncl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  static int fit[5] = {0, 0, 0, 0, 0};   // co-resident clusters per cluster size
+  if (ep.ncl > 4) return cudaErrorInvalidValue;
+  if (fit[ep.ncl] == 0) {
+    cfg.gridDim = dim3(ep.ncl * sm_count());
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, gemm_tc_kernel<EPI, BN>, &cfg) != cudaSuccess || n < 1)
+      return cudaErrorInvalidConfiguration;
+    fit[ep.ncl] = n;
+  }
+  cfg.gridDim = dim3(std::min(grid / ep.ncl, fit[ep.ncl]) * ep.ncl);
+  return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<EPI, BN>, mA, mB, M, N, KpA, KpB, ep, err, dcnt,
+                            mul_n, tiles, n_mtiles);
 }
 
 template <int BN>
@@ -564,6 +602,11 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
     e.ksplit = 2;
     cudaError_t r = cudaMemsetAsync(ep.outF, 0, (size_t)N * ep.ldo * sizeof(float), st);
     if (r != cudaSuccess) return r;
+  } else if (epi == kStoreF32 && ep.split_ok && A.Kp / TC_BK >= 32) {
+    // a long shared A (the kernel matrix) and a few N tiles: one cluster per
+    // M row block, so that A comes from DRAM once
+    const int nnt = (N + bn - 1) / bn;
+    if (nnt >= 2 && nnt <= 4) e.ncl = nnt;
   }
   if (bn == 64)
     return launch_tc_epi<64>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, e, err, dcnt, mul_n,

@@ -174,6 +174,7 @@ struct TcEpilogue {
   int n_occ = 0;
   int split_ok = 0;                // kStoreF32: the launch may split K in two (adds into outF)
   int ksplit = 1;                  // set by the launcher
+  int ncl = 1;                     // set by the launcher: > 1, clusters of ncl CTAs, one per N tile
   const int *aoff = nullptr;       // kBetaTSplit, kGammaCatSplit
   const int *orb_atom = nullptr;   // kGammaCatSplit
   const int *xoff5 = nullptr;      // kGammaCatSplit
