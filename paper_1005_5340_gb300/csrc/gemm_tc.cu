@@ -602,9 +602,10 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
     e.ksplit = 2;
     cudaError_t r = cudaMemsetAsync(ep.outF, 0, (size_t)N * ep.ldo * sizeof(float), st);
     if (r != cudaSuccess) return r;
-  } else if (epi == kStoreF32 && ep.split_ok && A.Kp / TC_BK >= 32) {
+  }
+  if (epi == kStoreF32 && ep.split_ok && A.Kp / TC_BK >= 32) {
     // a long shared A (the kernel matrix) and a few N tiles: one cluster per
-    // M row block, so that A comes from DRAM once
+    // M row block (and K half), so that A comes from DRAM once
     const int nnt = (N + bn - 1) / bn;
     if (nnt >= 2 && nnt <= 4) e.ncl = nnt;
   }

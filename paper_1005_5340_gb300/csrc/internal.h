@@ -228,7 +228,8 @@ struct LpWork {
 };
 
 cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &lp);
-// Time the N tiles (64, 128, 256) on this context's three products (full batch) and keep the fastest.
+// Time the N tiles (64, 128, 256) on this context's three products (the full batch; the
+// K product also at half of it) and keep the fastest, best of four runs each.
 cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp);
 // Out[c][mu] (float64) = Zin - chi0 K Zin (kA) or chi0 Zin (kChi0), reduced precision.
 cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWork &lp, int S,

@@ -108,14 +108,19 @@ cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
     TcEpilogue ep;
     cudaError_t r = cudaSuccess;
     float best = 1e30f;
-    for (int rep = 0; rep < 3 && r == cudaSuccess; ++rep) {
+    for (int rep = 0; rep < 5 && r == cudaSuccess; ++rep) {
       r = cudaEventRecord(a, st);
       if (which == 0) {
         ep.outF = lp.Yt;
         ep.ldo = sys.n_prod;
+        // the live count shrinks as right-hand sides converge: the full and
+        // the half batch, back to back
         if (r == cudaSuccess)
           r = launch_gemm_tc(st, lp.opK, lp.opZ, sys.n_prod, ncols, kStoreF32, ep, lp.err, nullptr,
                              0, bn);
+        if (r == cudaSuccess)
+          r = launch_gemm_tc(st, lp.opK, lp.opZ, sys.n_prod, (ncols / 2 + 1) & ~1, kStoreF32, ep,
+                             lp.err, nullptr, 0, bn);
       } else if (which == 1) {
         ep.outB = lp.aT;
         ep.ldo = 2 * (int64_t)lp.Kp2;
