@@ -113,6 +113,7 @@ cudaError_t lp_autotune(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
       if (which == 0) {
         ep.outF = lp.Yt;
         ep.ldo = sys.n_prod;
+        ep.split_ok = 1;   // as in the operator: split K and clusters where they apply
         // the live count shrinks as right-hand sides converge: the full and
         // the half batch, back to back
         if (r == cudaSuccess)
