@@ -45,6 +45,24 @@ KERNELS_PER_SCOPE_EMU = dict(KERNELS_PER_SCOPE, rhs_formation=11)
 # slice pairs of one emulated float64 product (s slices: pairs with i + j <= s + 1)
 EMU_PAIRS = {"fp64emu": 21, "bf16x3emu": 15}
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the tensor-core products, from one-pass ncu captures of the default bench
+# command (64-atom molecule, full batch of 192 right-hand sides):
+#   T1 + D(omega) (gemm_tc_kernel<1, 256>): 168.1 + 89.9 MB for the algorithmic
+#     2 n_virt n_orb N1 = 57.58 GFLOP (N1 = 49152); the B operand and the
+#     output scale with N1, so the traffic is taken proportional to the flops;
+#   K z (gemm_tc_kernel<0, 128>, clusters of 3 with split K): 381.5 + 15.5 MB,
+#     the split kernel matrix read about once whatever the batch: per launch.
+TRAFFIC = {"tc_gemm_T1_dscale": ("per_flop", (168.1e6 + 89.9e6) / 57.58e9),
+           "tc_gemm_K": ("per_launch", 381.5e6 + 15.5e6)}
+
+
+def traffic_of(name: str, flops_per_launch: float):
+    if name not in TRAFFIC:
+        return None
+    kind, v = TRAFFIC[name]
+    return v * flops_per_launch if kind == "per_flop" else v
+
 
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -262,7 +280,9 @@ def roofline_of(timing: dict, step_ms: float, prec: str = "bf16x3emu") -> dict:
         note = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": None, "peak_source": note, "share_of_step": d["ms"] / step_ms,
+            "traffic": traffic_of(name, d["flops"] / launches),
+            "traffic_unit": "bytes per launch (ncu, scaled to this class's mean launch)",
+            "peak_source": note, "share_of_step": d["ms"] / step_ms,
             "launches": d["launches"], "ms_per_launch": d["ms"] / launches}
 
 
