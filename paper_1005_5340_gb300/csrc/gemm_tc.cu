@@ -34,7 +34,8 @@ namespace {
 using namespace ptx;
 
 constexpr int TC_BM = 128, TC_BK = 64;
-constexpr int TC_THREADS = 192;
+constexpr int TC_EPI_WARPS = 8;                     // two per TMEM lane quadrant
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;   // producer, MMA issuer, epilogue
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;    // 16 KB per plane
 constexpr int TC_EOCC_MAX = 1024;   // occupied energies staged in shared memory (D(omega) epilogue)
 // The N tile (TMEM columns per accumulator, B box rows, MMA N) is a template
@@ -200,13 +201,14 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
 }
 
 // Persistent warp-specialised kernel: one CTA per SM walks its share of the
-// output tiles (tile t = blockIdx.x + i gridDim.x, M tiles fastest).
+// output tiles (tile t = blockIdx.x + i gridDim.x).
 //   warp 0 lane 0 : TMA producer; one ring stage holds the four planes
 //                   (A_hi, A_lo, B_hi, B_lo) of a 64-deep K block
 //   warp 1 lane 0 : tcgen05.mma issuer: A_hi B_hi + A_hi B_lo + A_lo B_hi
 //                   (M=128, N=BN, K=16) into one of two TMEM accumulators
-//   warps 2-5     : epilogue, TMEM -> registers -> global; draining tile i
-//                   while the MMA warp fills tile i+1 in the other buffer
+//   warps 2-9     : epilogue, TMEM -> registers -> global, two warps per
+//                   TMEM lane quadrant (half of the columns each); draining
+//                   tile i while the MMA warp fills tile i+1 in the other buffer
 template <int EPI, int TC_BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);   // one arrival per epilogue warp
+      mbar_init(&tempty[b], TC_EPI_WARPS);   // one arrival per epilogue warp
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -387,8 +389,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (EPI == kDscaleSplit && ep.n_occ <= TC_EOCC_MAX) {
       // the occupied energies to shared memory (the four epilogue warps)
       float2 *es = (float2 *)(tslot + 4);
-      for (int i = threadIdx.x - 64; i < ep.n_occ; i += 128) es[i] = ep.eocc2[i];
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      for (int i = threadIdx.x - 64; i < ep.n_occ; i += 32 * TC_EPI_WARPS) es[i] = ep.eocc2[i];
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_EPI_WARPS) : "memory");
       eocc = es;
     }
     int lt = 0;
@@ -407,7 +409,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       fence_after();
       const int m = m0 + lr;
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN);
-      for (int j0 = 0; j0 < tn; j0 += 16) {
+      // the two warps of a lane quadrant take the two halves of the columns
+      const int half = ((tn >> 4) + 1) / 2 * 16;
+      const int j_lo = (warp >= 6) ? half : 0, j_hi = (warp >= 6) ? tn : half;
+      for (int j0 = j_lo; j0 < j_hi; j0 += 16) {
         DscaleIn di;
         di.eocc = eocc;
         if (EPI == kDscaleSplit) {
