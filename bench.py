@@ -48,13 +48,13 @@ EMU_PAIRS = {"fp64emu": 21, "bf16x3emu": 15}
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the tensor-core products, from one-pass ncu captures of the default bench
 # command (64-atom molecule, full batch of 192 right-hand sides):
-#   T1 + D(omega) (gemm_tc_kernel<1, 256>): 168.1 + 89.9 MB for the algorithmic
+#   T1 + D(omega) (gemm_tc_kernel<1, 256>): 168.1 + 91.4 MB for the algorithmic
 #     2 n_virt n_orb N1 = 57.58 GFLOP (N1 = 49152); the B operand and the
 #     output scale with N1, so the traffic is taken proportional to the flops;
-#   K z (gemm_tc_kernel<0, 128>, clusters of 3 with split K): 381.5 + 15.5 MB,
+#   K z (gemm_tc_kernel<0, 128>, clusters of 3 with split K): 388.2 + 17.9 MB,
 #     the split kernel matrix read about once whatever the batch: per launch.
-TRAFFIC = {"tc_gemm_T1_dscale": ("per_flop", (168.1e6 + 89.9e6) / 57.58e9),
-           "tc_gemm_K": ("per_launch", 381.5e6 + 15.5e6)}
+TRAFFIC = {"tc_gemm_T1_dscale": ("per_flop", (168.1e6 + 91.4e6) / 57.58e9),
+           "tc_gemm_K": ("per_launch", 388.2e6 + 17.9e6)}
 
 
 def traffic_of(name: str, flops_per_launch: float):
