@@ -233,13 +233,14 @@ FORM_NOTE = {
     "fp64": "plain float64 GMRES, device resident",
     "fp64emu": "float64 GMRES whose dense products are float64 emulated on the bf16 tensor "
                "cores (6 integer slices per operand, exact sums)",
-    "bf16x3": "GMRES cycles with split-bf16 tensor-core products and float32 sparse kernels, "
-              "each cycle closed by a float64 residual (iterative refinement); RHS, basis, "
-              "Givens in float64",
+    "bf16x3": "GMRES cycles with split-bf16 tensor-core products (steps 2 and 5 on the "
+              "stored transition vertex), each cycle closed by a float64 residual (iterative "
+              "refinement); RHS in float64; float32 basis, float64 Arnoldi scalars and Givens",
     "bf16x3emu": "GMRES cycles with split-bf16 tensor-core products (steps 2 and 5 on the "
                  "stored transition vertex), each cycle closed by a float64 residual whose "
                  "products are float64 emulated on the tensor cores (5 integer slices, exact "
-                 "sums); RHS formation likewise; basis, Arnoldi and Givens in float64",
+                 "sums); RHS formation likewise; float32 basis, float64 Arnoldi scalars and "
+                 "Givens",
 }
 DTYPE = {"fp64": "f64", "fp64emu": "f64 (emulated on bf16 tensor cores)",
          "bf16x3": "bf16x3+f64", "bf16x3emu": "bf16x3+f64 (emulated on bf16 tensor cores)"}

@@ -56,11 +56,13 @@ typedef enum {
                                (tddft_gemm_f64_emulated with 6 slices: error about
                                2^-42 |A|_row |B|_col K); vertex contractions, block dots,
                                Arnoldi and Givens stay native float64 */
-  TDDFT_PREC_BF16X3_IR = 2, /* inner GMRES products in split bf16 on the tensor cores
-                               (hi*hi + hi*lo + lo*hi, float32 accumulation) and float32
-                               vertex contractions; right-hand sides, residuals that end
-                               each cycle, Arnoldi, Givens and the basis in float64
-                               (iterative refinement) */
+  TDDFT_PREC_BF16X3_IR = 2, /* inner GMRES cycles whose products all run in split bf16
+                               on the tensor cores (hi*hi + hi*lo + lo*hi, float32
+                               accumulation): K z, steps 2 and 5 on the stored transition
+                               vertex, both transforms; their Krylov basis in float32
+                               with the Arnoldi coefficients, Givens rotations and
+                               reductions in float64; right-hand sides and the residual
+                               that ends each cycle in float64 (iterative refinement) */
   TDDFT_PREC_BF16X3_IR_EMU = 3  /* TDDFT_PREC_BF16X3_IR whose float64 right-hand sides and
                                    cycle-end residuals use emulated float64 products as in
                                    TDDFT_PREC_FP64_EMU, with the slice count chosen from tol
