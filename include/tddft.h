@@ -415,6 +415,13 @@ int64_t tddft_mlp_num_params(const tddft_mlp *mlp);
 /* Copy the packed parameters to (set = 0) or from (set = 1) a host buffer of
  * n = tddft_mlp_num_params floats; setting also resets the Adam state. */
 tddft_status tddft_mlp_params(tddft_mlp *mlp, float *host, int64_t n, int32_t set);
+/* Write the packed parameters to a file, or read them back into a network of
+ * the same shape (this also resets the Adam state).  Format (little endian):
+ * the 8 bytes "TDDFTMLP", int32 version 1, int32 n_in, width, n_out, int64
+ * n_params, then n_params float32.  Errors: INVALID_ARG (null, unopenable or
+ * truncated file, bad magic or version), SHAPE (another network's shape). */
+tddft_status tddft_mlp_save(tddft_mlp *mlp, const char *path);
+tddft_status tddft_mlp_load(tddft_mlp *mlp, const char *path);
 /* Y [rows][n_out] = network(F [rows][n_in]); bf16 != 0 uses bf16 weights. */
 tddft_status tddft_mlp_forward(tddft_mlp *mlp, int64_t rows, const float *F, float *Y,
                                int32_t bf16);

@@ -12,6 +12,8 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -367,6 +369,17 @@ const float *ctx_product_features(const tddft_ctx *c);
 
 using namespace tddft;
 
+// File layout of tddft_mlp_save / tddft_mlp_load.
+namespace {
+constexpr char kMlpMagic[8] = {'T', 'D', 'D', 'F', 'T', 'M', 'L', 'P'};
+struct MlpFileHeader {
+  char magic[8];
+  int32_t version, n_in, width, n_out;
+  int64_t n_params;
+};
+static_assert(sizeof(MlpFileHeader) == 32, "file header layout");
+}  // namespace
+
 extern "C" {
 
 tddft_status tddft_mlp_create(int32_t n_in, int32_t width, int32_t n_out, int64_t max_rows,
@@ -450,6 +463,52 @@ tddft_status tddft_mlp_params(tddft_mlp *p, float *host, int64_t n, int32_t set)
   if (e != cudaSuccess) return mfail(p, TDDFT_ERR_CUDA, cudaGetErrorString(e));
   if (set) p->step = 0;
   return TDDFT_OK;
+}
+
+tddft_status tddft_mlp_save(tddft_mlp *p, const char *path) {
+  if (!p || !path) return mfail(p, TDDFT_ERR_INVALID_ARG, "null network or path");
+  std::vector<float> h((size_t)p->n_params);
+  const tddft_status st = tddft_mlp_params(p, h.data(), p->n_params, 0);
+  if (st != TDDFT_OK) return st;
+  MlpFileHeader hd;
+  std::memcpy(hd.magic, kMlpMagic, 8);
+  hd.version = 1;
+  hd.n_in = p->n_in;
+  hd.width = p->width;
+  hd.n_out = p->n_out;
+  hd.n_params = p->n_params;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return mfail(p, TDDFT_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+            std::fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? TDDFT_OK : mfail(p, TDDFT_ERR_INVALID_ARG, std::string("cannot write ") + path);
+}
+
+tddft_status tddft_mlp_load(tddft_mlp *p, const char *path) {
+  if (!p || !path) return mfail(p, TDDFT_ERR_INVALID_ARG, "null network or path");
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return mfail(p, TDDFT_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  MlpFileHeader hd;
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kMlpMagic, 8) != 0 ||
+      hd.version != 1) {
+    std::fclose(f);
+    return mfail(p, TDDFT_ERR_INVALID_ARG, "not a network file of version 1");
+  }
+  if (hd.n_in != p->n_in || hd.width != p->width || hd.n_out != p->n_out ||
+      hd.n_params != p->n_params) {
+    std::fclose(f);
+    return mfail(p, TDDFT_ERR_SHAPE,
+                 "the file holds a " + std::to_string(hd.n_in) + "-" + std::to_string(hd.width) +
+                     "-" + std::to_string(hd.n_out) + " network, this one is " +
+                     std::to_string(p->n_in) + "-" + std::to_string(p->width) + "-" +
+                     std::to_string(p->n_out));
+  }
+  std::vector<float> h((size_t)p->n_params);
+  const bool ok = std::fread(h.data(), sizeof(float), h.size(), f) == h.size();
+  std::fclose(f);
+  if (!ok) return mfail(p, TDDFT_ERR_INVALID_ARG, "truncated network file");
+  return tddft_mlp_params(p, h.data(), p->n_params, 1);
 }
 
 tddft_status tddft_mlp_forward(tddft_mlp *p, int64_t rows, const float *F, float *Y, int32_t bf16) {

@@ -100,6 +100,8 @@ SIGNATURES = {
     "tddft_mlp_last_error": (ctypes.c_char_p, [_P]),
     "tddft_mlp_num_params": (ctypes.c_int64, [_P]),
     "tddft_mlp_params": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32]),
+    "tddft_mlp_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "tddft_mlp_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "tddft_mlp_forward": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int32]),
     "tddft_mlp_backward": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
     "tddft_mlp_train_step": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
@@ -487,6 +489,14 @@ class Mlp:
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
         self._check(self._lib.tddft_mlp_params(self.h, p.ctypes.data, self.n_params, 1))
+
+    def save(self, path):
+        """tddft_mlp_save: the parameters to a file."""
+        self._check(self._lib.tddft_mlp_save(self.h, os.fsencode(path)))
+
+    def load(self, path):
+        """tddft_mlp_load: parameters of a network of this shape from a file."""
+        self._check(self._lib.tddft_mlp_load(self.h, os.fsencode(path)))
 
     def forward(self, F, bf16: bool = False):
         import torch

@@ -158,6 +158,8 @@ def test_calls_on_a_null_context_fail_cleanly(lib):
     assert lib.tddft_polarizability(None, 1, None, 0.1, None, None, 0) == tddft.ERR_INVALID_ARG
     assert lib.tddft_spectrum_adaptive(None, 0.0, 1.0, 0.01, None, None, None, None, None, 0,
                                        None) == tddft.ERR_INVALID_ARG
+    assert lib.tddft_mlp_save(None, b"x") == tddft.ERR_INVALID_ARG
+    assert lib.tddft_mlp_load(None, b"x") == tddft.ERR_INVALID_ARG
     lib.tddft_destroy(None)
     assert isinstance(lib.tddft_last_error(None), bytes)
 

@@ -54,6 +54,32 @@ def test_network_kernels_match_oracle(width, rows):
     net.close()
 
 
+def test_parameters_survive_a_file_round_trip(tmp_path):
+    """tddft_mlp_save / tddft_mlp_load: the same parameters and the same
+    forward pass after a round trip; a network of another shape is refused."""
+    import torch
+    net = T().Mlp(10, 64, 2, max_rows=256, seed=7)
+    rng = np.random.default_rng(4)
+    p = (rng.standard_normal(net.n_params) * 0.2).astype(np.float32)
+    net.set_params(p)
+    path = tmp_path / "guess.net"
+    net.save(path)
+    other = T().Mlp(10, 64, 2, max_rows=256, seed=8)
+    other.load(path)
+    assert np.array_equal(other.get_params(), p)
+    F = torch.from_numpy(rng.standard_normal((100, 10)).astype(np.float32)).cuda()
+    assert np.array_equal(other.forward(F).cpu().numpy(), net.forward(F).cpu().numpy())
+    wrong = T().Mlp(10, 32, 2, max_rows=16, seed=9)
+    with pytest.raises(T().TddftError) as e:
+        wrong.load(path)
+    assert e.value.status == T().ERR_SHAPE
+    with pytest.raises(T().TddftError) as e:
+        other.load(tmp_path / "missing.net")
+    assert e.value.status == T().ERR_INVALID_ARG
+    for net_ in (net, other, wrong):
+        net_.close()
+
+
 def test_untrained_network_starts_at_zero_output():
     import torch
     net = T().Mlp(10, 256, 2, max_rows=64, seed=1)
