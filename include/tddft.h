@@ -314,8 +314,9 @@ tddft_status tddft_polarizability_guess(tddft_ctx *ctx, int32_t n_omega, const d
 /*
  * Tile shapes chosen by the autotuner of a refinement-form context: at
  * create, each tensor-core product (K z, X_virt^T beta, X_virt a) is timed
- * with 128- and 64-wide N tiles on the context's full batch and the faster
- * is kept.  n_tiles[0..2] receive the widths (0 for a float64 context).
+ * with 64-, 128- and 256-wide N tiles on the context's full batch (K z also
+ * at half of it), best of four runs, and the fastest is kept.  n_tiles[0..2]
+ * receive the widths (0 for a float64 context).
  */
 tddft_status tddft_tuning(const tddft_ctx *ctx, int32_t *n_tiles);
 
