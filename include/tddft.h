@@ -302,7 +302,7 @@ tddft_status tddft_spectrum_adaptive(tddft_ctx *ctx, double w_lo, double w_hi, d
  *      initial guess of (omega[w], direction k).  Each guess first costs one
  *      float64 product A x0; if ||b - A x0|| > ||b||, zero is used instead
  *      (stats flags bit 0), so plain zero-guess GMRES is both the fallback
- *      and the judge of a guess.
+ *      and the arbiter of a guess.
  *  X (may be NULL): receives the solutions X_k(omega) in the same layout.
  *  x0 and X are device pointers: flags must include TDDFT_DEVICE_PTRS when
  *  either is given.  Everything else as tddft_polarizability.
@@ -396,7 +396,7 @@ tddft_status tddft_gemm_f64_emulated(int32_t M, int32_t N, int32_t K, const doub
  * neighbours.  Features (10 per product): Re/Im X(omega-)/s, Re/Im
  * X(omega+)/s, t, omega, (omega+ - omega-)/eps, bilocal flag, d_k^mu / rms(d_k),
  * ||V_mu|| / mean ||V||.  The guess enters tddft_polarizability_guess, where
- * zero-guess GMRES remains the fallback and the judge.
+ * zero-guess GMRES remains the fallback and the arbiter.
  *
  * Network: n_in -> width -> width -> n_out, tanh on the hidden layers,
  * float32 parameters packed [W1 (width x n_in, row-major), b1, W2, b2,

@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(NT, 4) gmres_step_kernel(Gs G, const int *__re
     bool rejected = false;
     if (cyc == 0 && rho > G.bnorm[r]) {
       // the residual of a supplied initial guess: zero is the fallback and the
-      // judge, so a guess worse than zero is dropped
+      // arbiter, so a guess worse than zero is dropped
       for (int e = lo + tid; e < hi; e += NT) {
         Vr[e] = (T)b[e];
         Vr[N + e] = (T)b[N + e];
