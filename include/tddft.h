@@ -250,8 +250,9 @@ tddft_status tddft_polarizability(tddft_ctx *ctx, int32_t n_omega, const double 
  *
  * Grid: n_initial uniform points on [w_lo, w_hi] (both included), then
  * rounds.  The first round takes every interval.  A round solves the
- * midpoints of its intervals longer than 2 min_step, in ascending order and
- * as many as the grid has room for, with one tddft_polarizability call
+ * midpoints of its intervals longer than 2 min_step (whose midpoint is not
+ * already a grid point), in ascending order and as many as the grid has room
+ * for, with one tddft_polarizability call
  * (batched on the GPU).  Both halves of an interval go to the next round when
  * |S(mid) - (S(left) + S(right)) / 2| > rel_tol * max |S| over the grid so
  * far.  It stops when no interval is left or the grid holds max_points.

@@ -91,6 +91,8 @@ def adaptive_grid(solve, w_lo, w_hi, n_initial, max_points, rel_tol, min_step):
     flagged = list(zip(om[:-1], om[1:]))
     while flagged and len(S) < max_points:
         flagged = [iv for iv in flagged if iv[1] - iv[0] > 2.0 * min_step]
+        # an interval whose midpoint rounds onto a grid point cannot be split
+        flagged = [iv for iv in flagged if 0.5 * (iv[0] + iv[1]) not in S]
         flagged = flagged[:max_points - len(S)]
         if not flagged:
             break

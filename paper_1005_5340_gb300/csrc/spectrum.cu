@@ -130,6 +130,13 @@ extern "C" tddft_status tddft_spectrum_adaptive(tddft_ctx *ctx, double w_lo, dou
     std::vector<std::pair<double, double>> live;
     for (const auto &iv : flagged)
       if (iv.second - iv.first > 2.0 * o->min_step) live.push_back(iv);
+    // an interval whose midpoint rounds onto a grid point cannot be split
+    {
+      std::vector<std::pair<double, double>> keep;
+      for (const auto &iv : live)
+        if (!grid.count(0.5 * (iv.first + iv.second))) keep.push_back(iv);
+      live.swap(keep);
+    }
     const size_t room = (size_t)(o->max_points - (int32_t)grid.size());
     if (live.size() > room) live.resize(room);
     if (live.empty()) break;

@@ -105,3 +105,13 @@ def test_grid_respects_its_point_budget():
     solve = lambda w: -SO.alpha_from_poles(Om, G, w, 0.01)
     om, _ = SO.adaptive_grid(solve, 0.0, 1.2, 25, 60, 1e-4, 1e-4)
     assert len(om) == 60 and np.all(np.diff(om) > 0)
+
+
+def test_refinement_stops_at_the_floating_point_resolution():
+    """With no tolerance to stop it, the rule still ends: an interval whose
+    midpoint rounds onto one of its ends is not split again."""
+    Om = np.array([0.31])
+    G = np.array([0.2])[:, None, None] * np.eye(3)[None]
+    solve = lambda w: -SO.alpha_from_poles(Om, G, w, 0.01)
+    om, _ = SO.adaptive_grid(solve, 0.30, 0.30 + 4e-15, 3, 10 ** 6, 1e-300, 0.0)
+    assert len(om) < 100 and np.all(np.diff(om) > 0)
