@@ -6,8 +6,12 @@ with tanh hidden layers and the packed parameter layout
 [W1 (width x n_in), b1, W2 (width x width), b2, W3 (n_out x width), b3];
 the guess x0 = lin + s * y; the loss mean_r |x0_r - x*_r|^2 / |x*_r|^2 and
 its gradient; and the per-product features built from two solved
-neighbouring frequencies.  Pinned by finite differences and by the exact
-reduction of an untrained network to linear interpolation.
+neighbouring frequencies.  Pinned by a hand-built 2 -> 3 -> 3 -> 2 network
+whose outputs are worked out by hand from literal weights (activation,
+packing order and orientation of every block), by a hand-built three-product
+feature case with every column written out from its definition, by finite
+differences and by the exact reduction of an untrained network to linear
+interpolation.
 """
 from __future__ import annotations
 
