@@ -5,10 +5,10 @@ solving its own share of the frequencies).
 One step = one group of frequencies x 3 field directions solved to the
 workload's tolerance through the whole hot path (RHS formation chi0 . d,
 then GMRES with A z = z - chi0 (K z) until every right-hand side meets
-||b - A x|| / ||b|| <= tol, then P = d . X).  The metric is omega-points/s
-(an omega-point counts once all three directions converged).
+||b - A x|| / ||b|| <= tol, then P = d . X).  The metric is omega-points/s:
+an omega-point counts once all three of its directions converged.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload medium64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large256]
     python bench.py --impl reference     # the CPU oracle on the host cores
 
 Prints one JSON line (rank 0).
@@ -36,32 +36,38 @@ METRIC = "omega-points/s at 1e-6 rel. residual"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (DFMA) nominal rate; no tensor path for FP64
 # FP32 CUDA-core peak from unit counts: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
 FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# kernel launches behind one timed scope (the others launch one kernel each)
-KERNELS_PER_SCOPE = {"rhs_formation": 7, "emu_gemm_K": 2, "emu_gemm_T1": 2, "emu_gemm_T2": 2,
-                     "emu_alpha_beta": 2, "emu_alpha_dot": 3, "tc_alpha_dot": 2}
+# nominal dense tensor rates relative to bf16 (TF32 is half the bf16 rate)
+TF32_PER_BF16 = 0.5
+
+# Kernel launches behind one timed scope (every other scope launches one
+# kernel).  The slicing scope launches one kernel, or two (plus a memset)
+# for rows of more than 8192 entries: counted as one, a lower bound.
+KERNELS_PER_SCOPE = {"rhs_formation": 7}
 # emulated right-hand-side formation: dipole rows, slice + step 2, slice + T1,
 # expand, slice + T2, slice + step 5, combine
 KERNELS_PER_SCOPE_EMU = dict(KERNELS_PER_SCOPE, rhs_formation=11)
 # slice pairs of one emulated float64 product (s slices: pairs with i + j <= s + 1)
-EMU_PAIRS = {"fp64emu": 21, "bf16x3emu": 15}
+EMU_PAIRS = {"fp64emu": 21, "bf16x3emu": 15, "tf32emu": 15}
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the tensor-core products, from one-pass ncu captures of the default bench
-# command (64-atom molecule, full batch of 192 right-hand sides):
-#   T1 + D(omega) (gemm_tc_kernel<1, 256>): 168.1 + 91.4 MB for the algorithmic
-#     2 n_virt n_orb N1 = 57.58 GFLOP (N1 = 49152); the B operand and the
-#     output scale with N1, so the traffic is taken proportional to the flops;
-#   K z (gemm_tc_kernel<0, 128>, clusters of 3 with split K): 388.2 + 17.9 MB,
-#     the split kernel matrix read about once whatever the batch: per launch.
-TRAFFIC = {"tc_gemm_T1_dscale": ("per_flop", (168.1e6 + 91.4e6) / 57.58e9),
-           "tc_gemm_K": ("per_launch", 388.2e6 + 17.9e6)}
+# Timing classes of the library (tddft_timing_*) that launch the same
+# kernel function: the roofline entry is per kernel, over all its classes.
+KERNEL_OF_CLASS = {
+    "tc_gemm_K": "gemm_tc_kernel", "tc_gemm_T1_dscale": "gemm_tc_kernel",
+    "tc_gemm_T2": "gemm_tc_kernel", "tc_alpha_beta": "gemm_tc_kernel",
+    "tc_alpha_dot": "gemm_tc_kernel",
+    "emu_gemm_K": "ozaki_gemm_kernel", "emu_gemm_T1": "ozaki_gemm_kernel",
+    "emu_gemm_T2": "ozaki_gemm_kernel", "emu_alpha_beta": "ozaki_gemm_kernel",
+    "emu_alpha_dot": "ozaki_gemm_kernel",
+    "f64_gemm_K": "gemm_f64_kernel", "f64_gemm_T1": "gemm_f64_kernel",
+    "f64_gemm_T2": "gemm_f64_kernel",
+    "gmres_step": "gmres_step_kernel",
+}
 
-
-def traffic_of(name: str, flops_per_launch: float):
-    if name not in TRAFFIC:
-        return None
-    kind, v = TRAFFIC[name]
-    return v * flops_per_launch if kind == "per_flop" else v
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
+# flop of a kernel, from ncu captures (one kernel, a few launches) whose
+# summaries are under profiles/; None where no capture of the current
+# kernel exists.
+TRAFFIC_PER_FLOP = {}
 
 
 def measured_peaks():
@@ -77,22 +83,29 @@ def measured_peaks():
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=4)
+    p.add_argument("--steps", type=int, default=8)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="medium64")
+    p.add_argument("--workload", default="large256")
     p.add_argument("--omega-per-step", type=int, default=64)
-    p.add_argument("--e2e-steps", type=int, default=1)
-    p.add_argument("--cpu-sample", type=int, default=0,
-                   help="omega-points in the CPU-oracle sample (0: one per 3 host cores)")
+    p.add_argument("--timing-steps", type=int, default=0,
+                   help="steps of the instrumented pass for the kernel split (0: one pass "
+                        "over this rank's frequency groups, at most --steps)")
+    p.add_argument("--cpu-products", type=int, default=3,
+                   help="oracle A z products timed in the CPU-oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--prec", choices=["fp64", "fp64emu", "bf16x3", "bf16x3emu"],
+    p.add_argument("--prec", choices=["fp64", "fp64emu", "bf16x3", "bf16x3emu", "tf32", "tf32emu"],
                    default="bf16x3emu")
     p.add_argument("--no-fp64-compare", action="store_true",
-                   help="skip timing the plain float64 form on one step for the speedup")
+                   help="skip timing the plain float64 form on the frequency subset")
+    p.add_argument("--fp64-stride", type=int, default=32,
+                   help="the plain float64 form runs on every k-th frequency of the grid")
+    p.add_argument("--fp64-steps", type=int, default=4,
+                   help="timed steps the float64 subset is cut into")
     p.add_argument("--inner-tol", type=float, default=1e-4)
-    p.add_argument("--graph", action="store_true",
-                   help="replay each GMRES iteration as a captured CUDA graph")
+    p.add_argument("--graph", type=int, default=0, choices=[0, 1, 2],
+                   help="GMRES driver: 0 host loop, 1 replays of a captured iteration, 2 the "
+                        "whole loop on the device (one conditional-graph launch per group)")
     return p.parse_args()
 
 
@@ -100,12 +113,14 @@ def parse():
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of the GPU this process runs on, selected by UUID
+    (nvidia-smi's own indices ignore CUDA_VISIBLE_DEVICES)."""
+    Q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
         self.proc = None
         self.lines = []   # (host time, csv line)
         self.t0 = None
@@ -114,8 +129,10 @@ class ClockSampler:
         """Start sampling every 50 ms and wait (at most 5 s) for the first
         sample, so that the timed region that follows is covered."""
         try:
+            if not self.uuid:
+                raise RuntimeError("no GPU UUID")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                ["nvidia-smi", "-i", self.uuid, f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
@@ -134,7 +151,8 @@ class ClockSampler:
     def stop(self):
         t1 = time.perf_counter()
         if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "uuid": self.uuid}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -158,7 +176,16 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "uuid": self.uuid}
+
+
+def gpu_uuid(local: int) -> str | None:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        return None
+    return u if u.startswith("GPU-") else "GPU-" + u
 
 
 # ---------------------------------------------------------------------------
@@ -189,17 +216,83 @@ def omega_schedule(n_omega: int, rank: int, world: int, per_step: int):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
-def cpu_oracle_run(workload: str, n_points: int, cores: int, pool_state: dict | None = None):
+_CPU = {}
+
+
+def _cpu_init(workload):
     import oracle.tddft_oracle as O
-    w = synth.WORKLOADS[workload]
-    om = synth.omega_grid(w["n_omega"], w["w_hi"])
-    pick = om[np.linspace(0, om.size - 1, n_points).round().astype(int)]
+    s, w = synth.workload(workload)
+    _CPU.update(O=O, s=s, w=w, op=O.StepOperator(s))
+
+
+def _cpu_products(args):
+    """Time n oracle products A z = z - chi0 (K z) (the matrix-free operator
+    the oracle's GMRES applies) at frequency omega, after one untimed one."""
+    n, omega, seed = args
+    O, s, w, op = _CPU["O"], _CPU["s"], _CPU["w"], _CPU["op"]
+    z = synth.random_complex_vectors(1, s.n_prod, seed)[0]
+    O.apply_A(s, op, z, omega, w["eps"])
     t0 = time.perf_counter()
-    P, infos = O.polarizability_gmres_parallel((synth.workload_system, (workload,)), pick,
-                                               w["eps"], w["restart"], w["tol"], workers=cores)
-    dt = time.perf_counter() - t0
-    conv = all(i["converged"] for i in infos)
-    return n_points / dt, dt, conv, pick
+    for _ in range(n):
+        z = O.apply_A(s, op, z, omega, w["eps"])
+        z /= np.linalg.norm(z)
+    return (time.perf_counter() - t0) / n
+
+
+class CpuOracle:
+    """The oracle's matrix-free float64 operator on the host cores: P = 3
+    spawned processes (one per field direction, as the paper's tasks are one
+    (omega, direction) each), each with cores / P BLAS threads; 3 rather
+    than one per core so that the workload's matrices (about 15 GB per
+    process at 256 atoms) fit in host memory.  A right-hand side of GMRES(m)
+    costs one product for b = chi0 d_k (timed as an A product) and about one
+    full cycle of m products, so an omega-point (3 directions) is counted as
+    3 (m + 1) products at the measured aggregate product rate."""
+
+    P = 3
+
+    def __init__(self, workload: str, cores: int):
+        import multiprocessing as mp
+        self.workload = workload
+        self.cores = cores
+        self.procs = max(1, min(self.P, cores))
+        self.threads = max(1, cores // self.procs)
+        self.w = synth.WORKLOADS[workload]
+        env = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                              "MKL_NUM_THREADS")}
+        for v in env:
+            os.environ[v] = str(self.threads)
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_cpu_init,
+                                                     initargs=(workload,))
+        finally:
+            for v, val in env.items():
+                if val is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = val
+
+    def per_product_s(self, n: int, step: int) -> float:
+        """Wall time per product of the processes together (each runs n)."""
+        omega = 0.5 * self.w["w_hi"]
+        t = self.pool.map(_cpu_products, [(n, omega, 101 + step * self.procs + i)
+                                          for i in range(self.procs)], chunksize=1)
+        return max(t) / self.procs
+
+    def points_per_s(self, t_product: float) -> float:
+        return 1.0 / (3 * (self.w["restart"] + 1) * t_product)
+
+    def sample_text(self, n: int) -> str:
+        m = self.w["restart"]
+        return (f"{n} oracle A z products (K z, then the five chi0 steps of Table t:flops) in "
+                f"each of {self.procs} concurrent processes with {self.threads} BLAS threads "
+                f"(one vector each, omega = {0.5 * self.w['w_hi']} Ha, after one untimed "
+                f"product); an omega-point counted as 3 directions x (1 + m) products, m = {m} "
+                f"(one full GMRES({m}) cycle plus b = chi0 d_k)")
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def host_cores() -> int:
@@ -214,26 +307,24 @@ def run_reference(args):
     if rank != 0:
         return
     cores = host_cores()
-    w = synth.WORKLOADS[args.workload]
-    per_step = max(1, math.ceil(cores / 3))
-    for _ in range(args.warmup):
-        cpu_oracle_run(args.workload, per_step, cores)
-    times = []
-    for _ in range(args.steps):
-        _, dt, conv, pick = cpu_oracle_run(args.workload, per_step, cores)
-        times.append(dt)
-    total = sum(times)
-    value = per_step * args.steps / total
-    sample = (f"{per_step} omega-points x 3 directions per step (evenly spread over the "
-              f"{w['n_omega']}-point grid), oracle GMRES(m={w['restart']}) to tol {w['tol']}")
+    cpu = CpuOracle(args.workload, cores)
+    try:
+        for i in range(args.warmup):
+            cpu.per_product_s(1, i)
+        times = [cpu.per_product_s(1, args.warmup + i) for i in range(args.steps)]
+    finally:
+        cpu.close()
+    t_prod = sum(times) / len(times)
+    value = cpu.points_per_s(t_prod)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "omega-points/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * t_prod, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(args.workload, "oracle on host cores"),
+        "config": config_of(args.workload, "the float64 oracle on the host cores; a step is one "
+                                           "oracle A z product"),
         "cpu_baseline": {"value": value, "unit": "omega-points/s", "cores": cores,
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle", "sample": cpu.sample_text(1) + " (per step)"},
         "e2e": {"value": value, "unit": "omega-points/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -251,50 +342,83 @@ FORM_NOTE = {
                  "products are float64 emulated on the tensor cores (5 integer slices, exact "
                  "sums); RHS formation likewise; float32 basis, float64 Arnoldi scalars and "
                  "Givens",
+    "tf32": "GMRES cycles with TF32 tensor-core products (one TF32 product each), each cycle "
+            "closed by a native float64 residual; float32 basis, float64 Arnoldi scalars",
+    "tf32emu": "GMRES cycles with TF32 tensor-core products (one TF32 product each), each "
+               "cycle closed by a float64 residual whose products are float64 emulated on "
+               "the tensor cores (5 integer slices); float32 basis, float64 Arnoldi scalars",
 }
 DTYPE = {"fp64": "f64", "fp64emu": "f64 (emulated on bf16 tensor cores)",
-         "bf16x3": "bf16x3+f64", "bf16x3emu": "bf16x3+f64 (emulated on bf16 tensor cores)"}
+         "bf16x3": "bf16x3+f64", "bf16x3emu": "bf16x3+f64 (emulated on bf16 tensor cores)",
+         "tf32": "tf32+f64", "tf32emu": "tf32+f64 (emulated on bf16 tensor cores)"}
 
 
-def roofline_of(timing: dict, step_ms: float, prec: str = "bf16x3emu") -> dict:
-    """Roofline entry of the kernel class with the largest device time."""
+def per_kernel(timing: dict) -> dict:
+    """Timing classes summed per kernel function (classes not in
+    KERNEL_OF_CLASS are kernels of their own)."""
+    out = {}
+    for name, d in timing.items():
+        if not d["launches"]:
+            continue
+        k = KERNEL_OF_CLASS.get(name, name)
+        e = out.setdefault(k, {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0,
+                               "classes": []})
+        e["ms"] += d["ms"]
+        e["launches"] += d["launches"]
+        e["flops"] += d["flops"]
+        e["bytes"] += d.get("bytes", 0.0)
+        e["classes"].append(name)
+    return out
+
+
+def roofline_of(timing: dict, step_ms: float, prec: str) -> dict:
+    """Roofline entry of the kernel with the largest device time."""
     peaks, src = measured_peaks()
-    name, d = max(timing.items(), key=lambda kv: kv[1]["ms"])
+    kern = per_kernel(timing)
+    name, d = max(kern.items(), key=lambda kv: kv[1]["ms"])
     launches = max(1, d["launches"])
     per_launch_s = d["ms"] / launches / 1e3
-    achieved = (d["flops"] / launches) / per_launch_s / 1e12 if d["flops"] else None
-    if not d["flops"] and d.get("bytes"):
-        # memory-bound class with device-counted algorithmic bytes
+    base = {"kernel": name, "classes": d["classes"], "share_of_step": d["ms"] / step_ms,
+            "launches": d["launches"], "ms_per_launch": d["ms"] / launches}
+    if not d["flops"] and d["bytes"]:
+        # memory-bound kernel with device-counted algorithmic bytes
         achieved = (d["bytes"] / launches) / per_launch_s / 1e9
         peak = peaks["hbm_gbs"]
-        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{src} HBM copy bandwidth",
-                "algorithmic_bytes_per_launch": d["bytes"] / launches,
-                "share_of_step": d["ms"] / step_ms, "launches": d["launches"],
-                "ms_per_launch": d["ms"] / launches}
-    if name.startswith("tc_"):
-        peak = peaks["bf16_tflops_sustained"] / 3.0
+        return dict(base, bound="hbm", achieved=achieved, peak=peak, unit="GB/s",
+                    frac=achieved / peak, traffic=None,
+                    peak_source=f"{src} HBM copy bandwidth",
+                    algorithmic_bytes_per_launch=d["bytes"] / launches)
+    achieved = (d["flops"] / launches) / per_launch_s / 1e12 if d["flops"] else None
+    sus = peaks["bf16_tflops_sustained"]
+    tc_tf32 = prec.startswith("tf32") and name == "gemm_tc_tf32_kernel"
+    if name == "gemm_tc_kernel":
+        peak = sus / 3.0
         bound, note = "tensor", (f"split bf16: 3 bf16 products per algorithmic product; peak = "
-                                 f"{src} sustained bf16 {peaks['bf16_tflops_sustained']} / 3")
-    elif name.startswith("emu_gemm") or name.startswith("emu_alpha"):
+                                 f"{src} sustained bf16 {sus} / 3")
+    elif name == "gemm_tc_tf32_kernel" or tc_tf32:
+        peak = sus * TF32_PER_BF16
+        bound, note = "tensor", (f"TF32: one TF32 product per algorithmic product; peak = {src} "
+                                 f"sustained bf16 {sus} x {TF32_PER_BF16} (nominal TF32/bf16 "
+                                 f"ratio)")
+    elif name == "ozaki_gemm_kernel":
         pairs = EMU_PAIRS.get(prec, 21)
-        peak = peaks["bf16_tflops_sustained"] / pairs
+        peak = sus / pairs
         bound, note = "tensor", (f"float64 emulated with {pairs} bf16 slice products per "
-                                 f"algorithmic product; peak = {src} sustained bf16 "
-                                 f"{peaks['bf16_tflops_sustained']} / {pairs}")
-    elif name.startswith("f64_"):
+                                 f"algorithmic product; peak = {src} sustained bf16 {sus} / "
+                                 f"{pairs}")
+    elif name == "gemm_f64_kernel":
         peak, bound = FP64_NOMINAL_TFLOPS, "alu"
         note = "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry among the measured peaks)"
     else:
         peak, bound = FP32_UNIT_TFLOPS, "alu"
         note = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
-    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic_of(name, d["flops"] / launches),
-            "traffic_unit": "bytes per launch (ncu, scaled to this class's mean launch)",
-            "peak_source": note, "share_of_step": d["ms"] / step_ms,
-            "launches": d["launches"], "ms_per_launch": d["ms"] / launches}
+    tpf = TRAFFIC_PER_FLOP.get(name)
+    traffic = tpf * d["flops"] / launches if (tpf and d["flops"]) else None
+    return dict(base, bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s",
+                frac=(achieved / peak) if achieved else None, traffic=traffic,
+                traffic_unit="DRAM bytes per mean launch (ncu bytes per flop x the mean "
+                             "launch's algorithmic flops)",
+                peak_source=note)
 
 
 def config_of(workload: str, extra: str):
@@ -302,13 +426,19 @@ def config_of(workload: str, extra: str):
     return {"workload": f"{workload}: {w['n_atoms']} atoms, 13 orbitals/atom, "
                         f"{w['n_omega']} omegas in [0,{w['w_hi']}] Ha x 3 directions, "
                         f"eps {w['eps']} Ha, GMRES({w['restart']}) tol {w['tol']}",
-            "l2": "operator inputs (K alone) larger than L2",
+            "l2": "operator inputs (K alone) larger than L2: no flush between steps",
             "note": extra}
 
 
 # ---------------------------------------------------------------------------
 # the GPU path
 # ---------------------------------------------------------------------------
+def converged_points(info) -> tuple[int, int]:
+    """(omega-points with all three directions converged, the others)."""
+    ok = np.asarray(info["converged"]).all(axis=1)
+    return int(ok.sum()), int((~ok).sum())
+
+
 def run_ours(args):
     import torch
     from paper_1005_5340_gb300 import tddft
@@ -330,39 +460,42 @@ def run_ours(args):
     omega = w["omega"]
     groups = omega_schedule(omega.size, rank, world, args.omega_per_step)
     per_step = len(groups[0])
+    t_create = time.perf_counter()
     ctx = tddft.Context(s, batch=3 * per_step, restart=w["restart"], tol=w["tol"],
                         max_restarts=200, stream=stream.cuda_stream, prec=args.prec,
                         inner_tol=args.inner_tol, graph=args.graph)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t_create
     dev_groups = [torch.tensor(omega[g], dtype=torch.float64, device=dev) for g in groups]
 
     def step(i):
         g = dev_groups[i % len(dev_groups)]
-        P, info = ctx.polarizability(g, w["eps"])
-        return int(np.sum(info["matvecs"])), int(g.numel()), int(np.sum(info["cycles"]))
+        P, info = ctx.polarizability(g, w["eps"], raise_on_nonconvergence=False)
+        ok, bad = converged_points(info)
+        return int(np.sum(info["matvecs"])), ok, bad, int(np.sum(info["cycles"]))
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
             step(i)
     torch.cuda.synchronize()
 
-    # timed region: device-resident inputs, device events on the library stream
-    # the timed steps run uninstrumented; the per-kernel split comes from the
-    # same steps run again with CUDA events around every kernel class
-    clk = ClockSampler(local)
+    # timed region: device-resident inputs, device events on the library stream;
+    # the timed steps run uninstrumented (the per-kernel split comes from an
+    # instrumented pass afterwards)
+    clk = ClockSampler(gpu_uuid(local))
     ctx.timing_enable(False)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    points = 0
-    matvecs = 0
-    cycles = 0
+    points = unconverged = matvecs = cycles = 0
     with torch.cuda.stream(stream):
         e0.record(stream)
         for i in range(args.steps):
-            mv, n, cy = step(args.warmup + i)
-            points += n
+            mv, ok, bad, cy = step(args.warmup + i)
+            points += ok
+            unconverged += bad
             matvecs += mv
             cycles += cy
         e1.record(stream)
@@ -371,98 +504,128 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    # the same steps again, instrumented (non-graph), for the kernel split
+    t = torch.tensor([ms, float(points), float(unconverged)], dtype=torch.float64, device=dev)
+    if dist:
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tp = t[1:].clone()
+        dist.all_reduce(tp, op=dist.ReduceOp.SUM)
+        ms_max, total_points, total_bad = float(tm.item()), float(tp[0].item()), float(tp[1].item())
+    else:
+        ms_max, total_points, total_bad = ms, float(points), float(unconverged)
+    value = total_points / (ms_max / 1e3)
+
+    # end to end through the public call with host buffers: the same steps
+    # (same groups, same count), omega from pinned host memory in, P to
+    # pinned host memory out, host wall clock
+    host_groups = [torch.tensor(omega[g], dtype=torch.float64).pin_memory() for g in groups]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_points = 0
+    for i in range(args.steps):
+        g = host_groups[(args.warmup + i) % len(host_groups)]
+        P, info = ctx.polarizability(g, w["eps"], raise_on_nonconvergence=False)
+        e2e_points += converged_points(info)[0]
+    dt = time.perf_counter() - t0
+    te = torch.tensor([dt, float(e2e_points)], dtype=torch.float64, device=dev)
+    if dist:
+        tm = te[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tp = te[1:].clone()
+        dist.all_reduce(tp, op=dist.ReduceOp.SUM)
+        dt, e2e_points = float(tm.item()), float(tp.item())
+    e2e = {"value": e2e_points / dt, "unit": "omega-points/s",
+           "h2d_bytes_per_step": int(8 * per_step),
+           "d2h_bytes_per_step": int(16 * 9 * per_step),
+           "steps": args.steps,
+           "note": "the timed steps again through tddft_polarizability with host pointers "
+                   "(pinned omega in, pinned P out; the call returns once P is on the host)"}
+
+    # the per-kernel split: one instrumented pass (CUDA events around every
+    # kernel launch on the library stream)
+    n_timing = args.timing_steps or min(args.steps, len(dev_groups))
     ctx.timing_enable(True)
     torch.cuda.synchronize()
     i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         i0.record(stream)
-        for i in range(args.steps):
+        for i in range(n_timing):
             step(args.warmup + i)
         i1.record(stream)
     torch.cuda.synchronize()
     timing_ms = i0.elapsed_time(i1)
     timing = ctx.timing()
     ctx.timing_enable(False)
-    t = torch.tensor([ms, float(points)], dtype=torch.float64, device=dev)
-    if dist:
-        tm = t[:1].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        tp = t[1:].clone()
-        dist.all_reduce(tp, op=dist.ReduceOp.SUM)
-        ms_max, total_points = float(tm.item()), float(tp.item())
-    else:
-        ms_max, total_points = ms, float(points)
-    value = total_points / (ms_max / 1e3)
-
-    # end to end through the public API with host buffers
-    # the same groups as the timed steps, from pinned host memory through the
-    # public call (omega in, P out), host wall clock
-    e2e_steps = args.e2e_steps or args.steps
-    host_groups = [torch.tensor(omega[g], dtype=torch.float64).pin_memory() for g in groups]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_points = 0
-    for i in range(e2e_steps):
-        g = host_groups[(args.warmup + i) % len(host_groups)]
-        P, info = ctx.polarizability(g, w["eps"])
-        e2e_points += g.numel()
-    dt = time.perf_counter() - t0
-    e2e = {"value": world * e2e_points / dt, "unit": "omega-points/s",
-           "h2d_bytes_per_step": int(8 * per_step),
-           "d2h_bytes_per_step": int(16 * 9 * per_step + 24 * 3 * per_step)}
+    tuning = list(ctx.tuning())
+    ctx.close()
 
     if rank != 0:
-        ctx.close()
         if dist:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel class
     roofline = roofline_of(timing, timing_ms, args.prec)
-    roofline["timing"] = ("per-launch CUDA-event durations from the same steps run again, "
-                          "instrumented, after the (uninstrumented) timed region")
+    roofline["timing"] = (f"per-launch CUDA-event durations from an instrumented pass over "
+                          f"{n_timing} of the timed steps, after the (uninstrumented) timed region")
     per_scope = KERNELS_PER_SCOPE_EMU if args.prec.endswith("emu") else KERNELS_PER_SCOPE
-    gpu_launches = int(sum(v["launches"] * per_scope.get(k, 1) for k, v in timing.items()))
+    launches_timing = sum(v["launches"] * per_scope.get(k, 1) for k, v in timing.items())
+    gpu_launches = int(round(launches_timing * args.steps / max(1, n_timing)))
     chi_cls = ["f64_vertex", "f64_beta", "f64_gemm_T1", "f64_dscale", "f64_gemm_T2",
-               "f64_block_dot", "tc_gemm_T1_dscale", "tc_gemm_T2", "emu_gemm_T1", "emu_gemm_T2", "alpha_gather", "tc_alpha_beta",
-               "tc_alpha_dot", "emu_alpha_beta", "emu_alpha_dot"]
-    chi_ms = sum(timing[c]["ms"] for c in chi_cls)
+               "f64_block_dot", "tc_gemm_T1_dscale", "tc_gemm_T2", "emu_gemm_T1", "emu_gemm_T2",
+               "alpha_gather", "tc_alpha_beta", "tc_alpha_dot", "emu_alpha_beta", "emu_alpha_dot",
+               "lp_dterm", "alpha_combine"]
+    chi_ms = sum(timing[c]["ms"] for c in chi_cls if c in timing)
     n_virt = s.n_orb - s.n_occ
-    t1_flops = (timing["f64_gemm_T1"]["flops"] + timing["tc_gemm_T1_dscale"]["flops"]
-                + timing["emu_gemm_T1"]["flops"])
+    t1_flops = sum(timing[c]["flops"] for c in ("f64_gemm_T1", "tc_gemm_T1_dscale", "emu_gemm_T1")
+                   if c in timing)
     chi_applies = t1_flops / (4.0 * n_virt * s.n_orb * s.n_occ)
     chi0_tflops = chi_applies * chi0_flops_per_rhs(s) / (chi_ms / 1e3) / 1e12 if chi_ms else None
 
     plain = None
     if args.prec != "fp64" and not args.no_fp64_compare:
-        # the plain float64 form on the same frequency groups (one warm-up, one timed step)
-        ctx64 = tddft.Context(s, batch=3 * per_step, restart=w["restart"], tol=w["tol"],
+        # the plain float64 form on a fixed subset of the grid (every k-th
+        # frequency), cut into several timed steps after one warm-up frequency
+        sub = omega[::args.fp64_stride]
+        nst = max(1, min(args.fp64_steps, sub.size))
+        parts = [p for p in np.array_split(sub, nst) if p.size]
+        per = max(p.size for p in parts)
+        ctx64 = tddft.Context(s, batch=3 * per, restart=w["restart"], tol=w["tol"],
                               max_restarts=200, stream=stream.cuda_stream, prec="fp64")
+        dparts = [torch.tensor(p, dtype=torch.float64, device=dev) for p in parts]
         with torch.cuda.stream(stream):
-            ctx64.polarizability(dev_groups[0], w["eps"])
+            ctx64.polarizability(dparts[0][:1], w["eps"], raise_on_nonconvergence=False)
             torch.cuda.synchronize()
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             f0.record(stream)
-            P64, info64 = ctx64.polarizability(dev_groups[1 % len(dev_groups)], w["eps"])
+            pts64 = mv64 = 0
+            for dp in dparts:
+                P64, info64 = ctx64.polarizability(dp, w["eps"], raise_on_nonconvergence=False)
+                pts64 += converged_points(info64)[0]
+                mv64 += int(np.sum(info64["matvecs"]))
             f1.record(stream)
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1)
-        pts64 = int(dev_groups[1 % len(dev_groups)].numel())
         ctx64.close()
         rate64 = pts64 / (ms64 / 1e3)
-        plain = {"value": rate64, "unit": "omega-points/s", "steps": 1,
-                 "matvecs_per_rhs": float(np.mean(info64["matvecs"])),
-                 "speedup_of_chosen_form": value / rate64}
+        plain = {"value": rate64, "unit": "omega-points/s", "steps": len(parts),
+                 "subset": f"every {args.fp64_stride}th frequency of the grid: {sub.size} omega "
+                           f"x 3 directions in {len(parts)} timed steps of <= {per} omega",
+                 "matvecs_per_rhs": mv64 / max(1, 3 * sub.size),
+                 "speedup_of_chosen_form": value / rate64 if rate64 else None}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        npts = args.cpu_sample or max(1, math.ceil(cores / 3))
-        v, dt_cpu, conv, pick = cpu_oracle_run(args.workload, npts, cores)
-        cpu = {"value": v, "unit": "omega-points/s", "cores": cores, "kind": "oracle",
-               "sample": f"{npts} omega-points x 3 directions spread over the grid "
-                         f"({dt_cpu:.1f} s wall, converged={conv})"}
+        oracle_cpu = CpuOracle(args.workload, cores)
+        try:
+            tp = oracle_cpu.per_product_s(args.cpu_products, 0)
+        finally:
+            oracle_cpu.close()
+        cpu = {"value": oracle_cpu.points_per_s(tp), "unit": "omega-points/s", "cores": cores,
+               "kind": "oracle", "sample": oracle_cpu.sample_text(args.cpu_products)
+               + f" ({tp:.2f} s per product)"}
 
     out = {
         "metric": METRIC, "value": value, "unit": "omega-points/s", "n_gpus": world,
@@ -473,18 +636,24 @@ def run_ours(args):
         "config": dict(config_of(args.workload, FORM_NOTE[args.prec]),
                        precision=args.prec, inner_tol=args.inner_tol,
                        omega_per_step=per_step, parallelism=f"frequency shards x{world}"),
+        "unconverged_points": int(total_bad),
+        "create_s": t_create,
         "chi0_tflops": chi0_tflops,
-        "matvecs_per_rhs": matvecs / max(1, 3 * points),
-        "cycles_per_rhs": cycles / max(1, 3 * points),
+        "matvecs_per_rhs": matvecs / max(1, 3 * (points + unconverged)),
+        "cycles_per_rhs": cycles / max(1, 3 * (points + unconverged)),
         "plain_fp64": plain,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": gpu_launches,
+        "gpu_launches_note": "launches of the library's kernels in the timed steps, counted "
+                             "per timed scope in the instrumented pass and scaled to the "
+                             "timed step count (a lower bound)",
+        "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
+                    for k, v in per_kernel(timing).items()},
         "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},
         "kernel_launches": {k: v["launches"] for k, v in timing.items() if v["launches"]},
-        "tc_n_tiles": list(ctx.tuning()),
+        "tc_n_tiles": tuning,
     }
     print(json.dumps(out), flush=True)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
 
@@ -507,13 +676,15 @@ def run_batch(args):
     for i in range(args.warmup):
         b.polarizability(groups[i % len(groups)], eps)
     torch.cuda.synchronize()
-    clk = ClockSampler(0)
+    clk = ClockSampler(gpu_uuid(0))
     clk.start()
     t0 = time.perf_counter()
     mv = 0
+    ok_pts = 0
     for i in range(args.steps):
-        P, st = b.polarizability(groups[i], eps)
+        P, st = b.polarizability(groups[i], eps, raise_on_nonconvergence=False)
         mv += int(st["matvecs"].sum())
+        ok_pts += int(st["converged"].all(axis=2).sum())
     dt = time.perf_counter() - t0
     clocks = clk.stop()
     b.close()
@@ -530,7 +701,7 @@ def run_batch(args):
             seq_time += time.perf_counter() - a
     seq_rate = len(mols) * per / seq_time
     print(json.dumps({
-        "metric": METRIC, "value": points / dt, "unit": "omega-points/s", "n_gpus": 1,
+        "metric": METRIC, "value": ok_pts / dt, "unit": "omega-points/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[args.prec], "data": "synthetic",
@@ -539,9 +710,10 @@ def run_batch(args):
                                f"{per} omega x 3 directions each per step, eps {eps}, "
                                f"GMRES({restart}) tol {tol}",
                    "precision": args.prec, "parallelism": "one graph per round, a branch per molecule"},
+        "unconverged_points": points - ok_pts,
         "matvecs_per_rhs": mv / (3 * points), "clocks": clocks,
         "one_molecule_at_a_time": {"value": seq_rate, "unit": "omega-points/s",
-                                   "speedup_of_batch": (points / dt) / seq_rate},
+                                   "speedup_of_batch": (ok_pts / dt) / seq_rate},
         "roofline": None, "e2e": None, "cpu_baseline": None,
     }), flush=True)
 

@@ -63,13 +63,31 @@ typedef enum {
                                with the Arnoldi coefficients, Givens rotations and
                                reductions in float64; right-hand sides and the residual
                                that ends each cycle in float64 (iterative refinement) */
-  TDDFT_PREC_BF16X3_IR_EMU = 3  /* TDDFT_PREC_BF16X3_IR whose float64 right-hand sides and
+  TDDFT_PREC_BF16X3_IR_EMU = 3, /* TDDFT_PREC_BF16X3_IR whose float64 right-hand sides and
                                    cycle-end residuals use emulated float64 products as in
                                    TDDFT_PREC_FP64_EMU, with the slice count chosen from tol
                                    so that their error stays well below it: 5 slices (about
                                    2^-35 |A|_row |B|_col K) for tol >= 1e-8, 6 for tol >=
                                    1e-12, 7 below */
+  TDDFT_PREC_TF32_IR = 4,     /* as TDDFT_PREC_BF16X3_IR, but every product of the inner
+                                 cycles is one TF32 product on the tensor cores
+                                 (tcgen05 kind::tf32: operands rounded to 10 mantissa bits,
+                                 float32 accumulation; relative error ~1e-3) */
+  TDDFT_PREC_TF32_IR_EMU = 5  /* TDDFT_PREC_TF32_IR with the float64 right-hand sides and
+                                 residuals of TDDFT_PREC_BF16X3_IR_EMU */
 } tddft_precision;
+
+/* Initial guesses of tddft_polarizability (Sec. 4.1 starts from zero; the
+ * other two are warm starts from neighbouring solved frequencies). */
+typedef enum {
+  TDDFT_GUESS_ZERO = 0,    /* every right-hand side from x0 = 0 */
+  TDDFT_GUESS_INTERP = 1,  /* frequency sweep in three passes (every 4th frequency and the
+                              last from zero; then index 2 mod 4 from the solved neighbours
+                              at distance 2; then the rest from distance 1), each guess the
+                              linear interpolation of the two neighbours' solutions */
+  TDDFT_GUESS_LEARNED = 2  /* the same sweep, each guess interpolation + the learned
+                              correction of the network loaded by tddft_guess_load */
+} tddft_guess;
 
 /*
  * One molecule (inputs of Sec. 2-3: eqs. lcao, vertex-ansatz,
@@ -137,21 +155,39 @@ typedef enum {
  *      reduced precision) also ends once its residual estimate has dropped
  *      by this factor; the float64 residual then starts the next cycle.
  *      In (0, 1); ignored for TDDFT_PREC_FP64 and TDDFT_PREC_FP64_EMU.
- *  graph: 1 = tddft_polarizability captures one GMRES iteration of a group
- *      (selection, gathers, operators, Arnoldi/Givens/residual updates) in a
- *      CUDA graph and replays it, every kernel reading the live count on the
- *      device; the host checks for completion every few replays.  0 = one
- *      launch sequence per iteration sized on the host.  Per-kernel timing
- *      (tddft_timing_*) forces 0.
+ *  graph: how tddft_polarizability drives the GMRES iterations of a group.
+ *      0 = one launch sequence per iteration, sized on the host from the
+ *      live count (an 8-byte read-back per iteration).
+ *      1 = one iteration (selection, gathers, operators, Arnoldi/Givens/
+ *      residual updates) captured in a CUDA graph and replayed, every kernel
+ *      reading the live count on the device; the host checks for completion
+ *      every few replays.
+ *      2 = the whole loop on the device: one graph launch per group, whose
+ *      conditional WHILE node repeats the captured iteration until no
+ *      right-hand side of the group is live; the host waits once per group.
+ *      The loop is bounded by (max_restarts + 1)(restart + 1) + 4
+ *      iterations (beyond it: TDDFT_ERR_TIMEOUT).
+ *      Per-kernel timing (tddft_timing_*) forces 0.
  *  stop: a tddft_stop_rule.  With the error estimates a cycle ends at the
  *      first Arnoldi step whose estimates (from the Givens/Hessenberg data
  *      and the cycle's <d|v_i>, <x0|v_i>, <d|A v_i>) meet the rule, and the
  *      solve ends when the rule holds for the float64 residual recomputed at
  *      the end of the cycle, with |A^-1| of the cycle's last step.
  *  emu_slices: slices of the emulated float64 products (TDDFT_PREC_FP64_EMU,
- *      TDDFT_PREC_BF16X3_IR_EMU): 0 chooses them (6 for FP64_EMU; from tol
- *      for BF16X3_IR_EMU), else 3..8.  Fewer slices are faster and coarser:
- *      s slices keep about 7 s + 1 bits of each row or column.
+ *      TDDFT_PREC_BF16X3_IR_EMU, TDDFT_PREC_TF32_IR_EMU): 0 chooses them (6
+ *      for FP64_EMU; from tol for the refinement forms), else 3..8.  Fewer
+ *      slices are faster and coarser: s slices keep about 7 s + 1 bits of
+ *      each row or column.
+ *  n_tile: tensor-core forms: 0 lets the autotuner pick the N tile of each
+ *      product at create; 64, 128 or 256 uses that tile for all of them.
+ *  guess: a tddft_guess for tddft_polarizability (TDDFT_GUESS_LEARNED needs
+ *      tddft_guess_load before the first solve).
+ *  wait_timeout_ns: the limit of every wait inside the tensor-core kernels
+ *      (mbarrier waits on copies, MMAs and the epilogue); 0 means 2 s.  On
+ *      expiry the kernel records the failure, stops issuing work, lets its
+ *      own copies and MMAs in flight finish (bounded by 2 s), frees its
+ *      tensor memory and returns; the call then returns TDDFT_ERR_TIMEOUT
+ *      and the context stays usable.  tddft_set_wait_timeout changes it.
  */
 typedef struct {
   int32_t prec;
@@ -164,7 +200,15 @@ typedef struct {
   int32_t graph;
   int32_t stop;
   int32_t emu_slices;
+  int32_t n_tile;
+  int32_t guess;
+  int64_t wait_timeout_ns;
 } tddft_options;
+
+/* Change the wait limit of a context's tensor-core kernels (see
+ * tddft_options.wait_timeout_ns; 0 = 2 s) for its later calls.
+ * Synchronises the context's stream. */
+tddft_status tddft_set_wait_timeout(tddft_ctx *ctx, int64_t wait_timeout_ns);
 
 /* Per-(omega, direction) solver report. */
 typedef struct {
@@ -321,6 +365,16 @@ tddft_status tddft_polarizability_guess(tddft_ctx *ctx, int32_t n_omega, const d
  */
 tddft_status tddft_tuning(const tddft_ctx *ctx, int32_t *n_tiles);
 
+/*
+ * Launch plan of the split-bf16 K product (tensor-core forms) for n_rhs
+ * right-hand sides (2 n_rhs real columns) with the context's N tile: *ncl
+ * receives the cluster size (1: no clusters; 2..4: one CTA per N tile of an
+ * M row block, in one cluster), *ksplit the number of K slices (1 or 2, the
+ * slices added into a zeroed output).  Host-side query, no device work.
+ */
+tddft_status tddft_kproduct_plan(const tddft_ctx *ctx, int32_t n_rhs, int32_t *ncl,
+                                 int32_t *ksplit);
+
 /* Sizes of a context (any pointer may be NULL). */
 tddft_status tddft_sizes(const tddft_ctx *ctx, int32_t *n_orb, int32_t *n_occ, int32_t *n_prod,
                          int32_t *n_blocks);
@@ -363,6 +417,15 @@ tddft_status tddft_timing_bytes(tddft_ctx *ctx, int32_t i, double *bytes);
  */
 tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uint64_t seed,
                                  double *max_rel_err);
+
+/*
+ * The same self-test for the TF32 GEMM of TDDFT_PREC_TF32_IR (tcgen05
+ * kind::tf32, Sec. 4.2 transforms in tf32): both operands rounded to tf32
+ * (10 explicit mantissa bits), float32 accumulation; expected error
+ * about 2^-11 relative per entry.  Same arguments, allocation and errors.
+ */
+tddft_status tddft_selftest_gemm_tf32(int32_t M, int32_t N, int32_t K, uint64_t seed,
+                                      double *max_rel_err);
 
 /*
  * Float64 matrix product emulated on the bf16 tensor cores (the dense
@@ -454,15 +517,43 @@ tddft_status tddft_guess_combine(int64_t n_target, int32_t n_prod, const float *
                                  void *stream);
 
 /*
+ * Warm-started frequency sweep inside tddft_polarizability (and inside
+ * tddft_polarizability_guess when x0 is NULL) for a context whose guess
+ * mode (tddft_options.guess, tddft_set_guess) is not TDDFT_GUESS_ZERO.  The
+ * paper solves each frequency from zero (Sec. 4.1) and names warm starts
+ * from neighbouring frequencies as future work (Sec. 8).  The frequencies
+ * must increase.  Passes (tddft_sweep_plan): every 4th frequency and the
+ * last from zero; then the rest of index 2 mod 4; then the others, each
+ * guessed from its two nearest solved neighbours omega- < omega < omega+ as
+ * the interpolation (1 - t) X(omega-) + t X(omega+), plus s y with the
+ * network's correction y for TDDFT_GUESS_LEARNED (features: the spacing
+ * term is the pass's mean (omega+ - omega-) over eps).  Each guess is
+ * arbitrated as in tddft_polarizability_guess, so every frequency meets the
+ * same float64 tolerance whatever the mode.  Allocates its device buffers
+ * per call (the solutions of all frequencies and one chunk's guesses).
+ */
+/* pass[i] (0, 1, 2) and the neighbours left[i], right[i] (-1 in pass 0) of
+ * frequency i of an n_omega-point sweep.  Host only. */
+tddft_status tddft_sweep_plan(int32_t n_omega, int32_t *pass, int32_t *left, int32_t *right);
+/* Set the context's guess mode (a tddft_guess) for its later solves. */
+tddft_status tddft_set_guess(tddft_ctx *ctx, int32_t guess);
+/* Load the learned guess's network (a tddft_mlp_save file of a 10 -> width
+ * -> width -> 2 network) into the context, replacing any earlier one; its
+ * inference scratch is sized for the context's batch.  Errors: INVALID_ARG
+ * (unreadable file), SHAPE (not 10 inputs and 2 outputs), NOMEM. */
+tddft_status tddft_guess_load(tddft_ctx *ctx, const char *weights_path);
+
+/*
  * Several molecules of uneven size solved together (every (molecule, omega,
  * direction) is an independent right-hand side).  tddft_batch_create makes
  * one context per molecule, each on a private stream, with the same options
  * (options.stream and options.graph are ignored).  tddft_batch_polarizability
  * solves the same omega grid (host pointer) for every molecule: in each
  * round, every molecule forms its next group of at most options.batch
- * right-hand sides, then one CUDA graph whose parallel branches hold one
- * device-driven GMRES iteration of every molecule is replayed until all
- * groups are done.  P (host): n_mol x n_omega x 3 x 3 complex interleaved;
+ * right-hand sides, then one CUDA graph is launched once: it holds, for
+ * every molecule, a conditional WHILE node (independent of the others, so
+ * they run side by side) that repeats that molecule's device-driven GMRES
+ * iteration until its group is done (the bound of options.graph = 2).  P (host): n_mol x n_omega x 3 x 3 complex interleaved;
  * stats (host, may be NULL): n_mol x n_omega x 3.  Returns NOT_CONVERGED if
  * any entry missed tol (P still filled).
  */

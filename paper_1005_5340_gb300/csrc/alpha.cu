@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tc_ptx.h"
 
 namespace tddft {
 namespace {
@@ -62,25 +63,31 @@ __global__ void alpha_build_kernel(int n_prod, int n_occ, int K2max, int K5max,
 }
 
 // dst[r][k] = hi(src[r][k]), dst[r][Kp + k] = lo(src[r][k])   (rows of length Kp)
+// With tf32: float dst[r][k] = src[r][k] rounded to tf32.
 __global__ void split_dense_kernel(const double *__restrict__ src, int64_t rows, int Kp,
-                                   __nv_bfloat16 *__restrict__ dst) {
+                                   void *__restrict__ dstv, bool tf32) {
   const int64_t total = rows * Kp;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / Kp;
     const int k = (int)(i - r * Kp);
     const double x = src[i];
+    if (tf32) {
+      ((float *)dstv)[i] = ptx::tf32_round((float)x);
+      continue;
+    }
+    __nv_bfloat16 *dst = (__nv_bfloat16 *)dstv;
     const __nv_bfloat16 hi = __double2bfloat16(x);
     dst[r * 2 * Kp + k] = hi;
     dst[r * 2 * Kp + Kp + k] = __double2bfloat16(x - (double)__bfloat162float(hi));
   }
 }
 
-// Ycat[c][k] = Y[c][lcat[k]] (0 where lcat[k] < 0), split bf16
+// Ycat[c][k] = Y[c][lcat[k]] (0 where lcat[k] < 0), split bf16 (or tf32)
 template <class T>
 __global__ void gather_split_kernel(int ncols, int kcat, const int *__restrict__ lcat,
                                     const T *__restrict__ Y, int64_t ld,
-                                    __nv_bfloat16 *__restrict__ dst, const int *dcnt) {
+                                    void *__restrict__ dstv, bool tf32, const int *dcnt) {
   if (dcnt) ncols = min(ncols, 2 * *dcnt);
   const int64_t total = (int64_t)ncols * kcat;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -89,6 +96,11 @@ __global__ void gather_split_kernel(int ncols, int kcat, const int *__restrict__
     const int k = (int)(i - c * kcat);
     const int mu = lcat[k];
     const float x = mu >= 0 ? (float)Y[c * ld + mu] : 0.f;
+    if (tf32) {
+      ((float *)dstv)[i] = ptx::tf32_round(x);
+      continue;
+    }
+    __nv_bfloat16 *dst = (__nv_bfloat16 *)dstv;
     const __nv_bfloat16 hi = __float2bfloat16_rn(x);
     dst[c * 2 * kcat + k] = hi;
     dst[c * 2 * kcat + kcat + k] = __float2bfloat16_rn(x - __bfloat162float(hi));
@@ -239,17 +251,17 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
     al((void **)&qg, (size_t)ncap * 2 * ar.kcat5 * sizeof(__nv_bfloat16));
     al((void **)&ar.P2f, (size_t)rows5 * ar.ldp * sizeof(float));
     if (e == cudaSuccess) {
-      split_dense_kernel<<<152 * 8, 256, 0, st>>>(a2, ar.rows2, ar.K2max, q2);
-      split_dense_kernel<<<152 * 8, 256, 0, st>>>(a5, rows5, ar.K5max, q5);
+      split_dense_kernel<<<152 * 8, 256, 0, st>>>(a2, ar.rows2, ar.K2max, q2, ar.tf32);
+      split_dense_kernel<<<152 * 8, 256, 0, st>>>(a5, rows5, ar.K5max, q5, ar.tf32);
       e = cudaGetLastError();
     }
     // Gcat pads (never written) must read as zero
     if (e == cudaSuccess)
       e = cudaMemsetAsync(qg, 0, (size_t)ncap * 2 * ar.kcat5 * sizeof(__nv_bfloat16), st);
-    if (e == cudaSuccess) e = make_operand_map(ar.a2, q2, ar.rows2, ar.K2max, 128);
-    if (e == cudaSuccess) e = make_operand_map(ar.a5, q5, rows5, ar.K5max, 128);
-    if (e == cudaSuccess) e = make_operand_map(ar.ycat, qy, ncap, ar.kcat2, 128);
-    if (e == cudaSuccess) e = make_operand_map(ar.gcat, qg, ncap, ar.kcat5, 128);
+    if (e == cudaSuccess) e = make_operand_map(ar.a2, q2, ar.rows2, ar.K2max, 128, ar.tf32);
+    if (e == cudaSuccess) e = make_operand_map(ar.a5, q5, rows5, ar.K5max, 128, ar.tf32);
+    if (e == cudaSuccess) e = make_operand_map(ar.ycat, qy, ncap, ar.kcat2, 128, ar.tf32);
+    if (e == cudaSuccess) e = make_operand_map(ar.gcat, qg, ncap, ar.kcat5, 128, ar.tf32);
     ar.ycat_q = qy;
     ar.gcat_q = qg;
   }
@@ -288,10 +300,10 @@ cudaError_t launch_alpha_gather_lp(cudaStream_t st, const AlphaRoute &ar, int nc
   __nv_bfloat16 *dst = ar.ycat_q;
   if (y_f64)
     gather_split_kernel<double><<<g, 256, 0, st>>>(ncols, ar.kcat2, ar.lcat, (const double *)Y, ld,
-                                                   dst, dcnt);
+                                                   dst, ar.tf32, dcnt);
   else
     gather_split_kernel<float><<<g, 256, 0, st>>>(ncols, ar.kcat2, ar.lcat, (const float *)Y, ld,
-                                                  dst, dcnt);
+                                                  dst, ar.tf32, dcnt);
   return cudaGetLastError();
 }
 

@@ -6,11 +6,17 @@
 // Split-bf16 ("bf16x3"): every real operand x is stored as two bf16 planes
 // x = hi + lo (+ O(2^-17 |x|)), each row laid out [hi | lo] with Kp columns
 // per plane (Kp a multiple of 64, zero padded).  The product is accumulated
-// in float32 in tensor memory as A_hi B_hi + A_hi B_lo + A_lo B_hi.  The
+// in float32 in tensor memory as A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// TF32 (template flag TF): every operand row is Kp floats rounded to tf32,
+// the same 4 bytes per K entry; a 64-deep K block is two 32-wide boxes of
+// 128-byte rows, where split bf16 has the hi and lo boxes, and the product
+// is one tcgen05 kind::tf32 MMA chain (8 MMAs of K = 8 per block, against 12
+// of K = 16 for split bf16; the tf32 rate is half the bf16 rate).  The
 // kernel is persistent (one CTA per SM over its share of the 128 x BN output
-// tiles) and warp-specialised: a TMA producer, an MMA issuer and four
+// tiles) and warp-specialised: a TMA producer, an MMA issuer and eight
 // epilogue warps that drain one TMEM accumulator while the next tile is
-// accumulated in the other.  Epilogues, fused per use:
+// accumulated in the other.  Epilogues, fused per use (the split-bf16 next
+// operands are written as tf32 floats in the TF32 form):
 //     kStoreF32      plain float32 C^T
 //     kDscaleSplit   the D(omega) scaling of eq. response-mat on (re, im)
 //                    column pairs, written back as split bf16 for the next GEMM
@@ -61,6 +67,16 @@ __device__ __forceinline__ void store_split(__nv_bfloat16 *p, int64_t lo_off, fl
   p[lo_off] = l;
 }
 
+// element idx of a next-GEMM operand: split bf16 (hi at idx, lo at idx +
+// lo_off) or, in the TF32 form, one tf32-rounded float at idx
+template <bool TF>
+__device__ __forceinline__ void put_operand(void *base, int64_t idx, int64_t lo_off, float x) {
+  if (TF)
+    ((float *)base)[idx] = tf32_round(x);
+  else
+    store_split((__nv_bfloat16 *)base + idx, lo_off, x);
+}
+
 // One 16-column chunk of the epilogue: row m (local row lr of the tile),
 // columns n0 + j0 .. n0 + j0 + 15, fused per use.
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -76,7 +92,7 @@ struct DscaleIn {
   const float2 *eocc;
 };
 
-template <int EPI>
+template <int EPI, bool TF>
 __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, int rows_valid,
                                            int atom, int M, int N, int n0, int j0,
                                            const TcEpilogue &ep, const DscaleIn &di) {
@@ -117,7 +133,7 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
         const int n = n0 + j0 + j;
         if (n < N) {
           const int64_t row = ((int64_t)(n >> 1) * ep.n_occ + E) * 2 + (n & 1);
-          store_split(ep.outB + row * ep.ldo + aoA + c, ep.lo_off, v[j]);
+          put_operand<TF>(ep.outB, row * ep.ldo + aoA + c, ep.lo_off, v[j]);
         }
       }
     }
@@ -134,12 +150,22 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
         const int sl = pair0 / ep.n_occ, E0 = pair0 - sl * ep.n_occ;
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-          __align__(16) __nv_bfloat16 h[8], l[8];
+          const int64_t at = (int64_t)(2 * sl + p) * ep.ldo + xo + E0;
+          if (TF) {
+            // eight floats: two 16-byte stores
+            float *dst = (float *)ep.outB + at;
+            *(float4 *)dst = make_float4(tf32_round(v[p]), tf32_round(v[2 + p]),
+                                         tf32_round(v[4 + p]), tf32_round(v[6 + p]));
+            *(float4 *)(dst + 4) = make_float4(tf32_round(v[8 + p]), tf32_round(v[10 + p]),
+                                               tf32_round(v[12 + p]), tf32_round(v[14 + p]));
+          } else {
+            __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) split_bf16(v[2 * e + p], h[e], l[e]);
-          __nv_bfloat16 *dst = ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E0;
-          *(uint4 *)dst = *(const uint4 *)h;
-          *(uint4 *)(dst + ep.lo_off) = *(const uint4 *)l;
+            for (int e = 0; e < 8; ++e) split_bf16(v[2 * e + p], h[e], l[e]);
+            __nv_bfloat16 *dst = (__nv_bfloat16 *)ep.outB + at;
+            *(uint4 *)dst = *(const uint4 *)h;
+            *(uint4 *)(dst + ep.lo_off) = *(const uint4 *)l;
+          }
         }
       } else {
 #pragma unroll
@@ -148,7 +174,7 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
           if (n < N) {
             const int pair = n >> 1, p = n & 1;
             const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
-            store_split(ep.outB + (int64_t)(2 * sl + p) * ep.ldo + xo + E, ep.lo_off, v[j]);
+            put_operand<TF>(ep.outB, (int64_t)(2 * sl + p) * ep.ldo + xo + E, ep.lo_off, v[j]);
           }
         }
       }
@@ -188,13 +214,8 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
           E = 0;
           ++sl;
         }
-        __nv_bfloat16 h, l;
-        split_bf16(re, h, l);
-        ep.outB[(int64_t)n * ep.ldo + m] = h;
-        ep.outB[(int64_t)n * ep.ldo + ep.lo_off + m] = l;
-        split_bf16(im, h, l);
-        ep.outB[(int64_t)(n + 1) * ep.ldo + m] = h;
-        ep.outB[(int64_t)(n + 1) * ep.ldo + ep.lo_off + m] = l;
+        put_operand<TF>(ep.outB, (int64_t)n * ep.ldo + m, ep.lo_off, re);
+        put_operand<TF>(ep.outB, (int64_t)(n + 1) * ep.ldo + m, ep.lo_off, im);
       }
     }
   }
@@ -209,7 +230,7 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
 //   warps 2-9     : epilogue, TMEM -> registers -> global, two warps per
 //                   TMEM lane quadrant (half of the columns each); draining
 //                   tile i while the MMA warp fills tile i+1 in the other buffer
-template <int EPI, int TC_BN>
+template <int EPI, int TC_BN, bool TF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int M, int N, int KpA, int KpB, TcEpilogue ep, int *err, const int *dcnt,
@@ -234,8 +255,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t *empty = full + NS;
   uint64_t *tfull = empty + NS;     // [2]
   uint64_t *tempty = tfull + 2;     // [2]
-  uint32_t *tslot = (uint32_t *)(tempty + 2);
+  uint64_t *drain = tempty + 2;     // completion of every MMA this CTA issued
+  uint32_t *tslot = (uint32_t *)(drain + 1);
   __shared__ int abort_flag;
+  const uint64_t lim = wait_limit(err);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // tile t: M tile fastest, then the K slice (split K), then the N tile of
@@ -286,6 +309,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], TC_EPI_WARPS);   // one arrival per epilogue warp
     }
+    mbar_init(drain, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -311,7 +335,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % NS;
           const uint32_t ph = (uint32_t)(g / NS) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u)) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, lim)) {
             atomicExch(err, 1);
             abort_flag = 1;
             ok = false;
@@ -322,12 +346,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             break;
           }
           uint8_t *st = smem + s * SB;
+          // second box of each operand: the lo plane (split bf16) or the
+          // upper 32 entries of the K block (TF32)
+          const int secA = TF ? 32 : KpA, secB = TF ? 32 : KpB;
           mbar_expect_tx(&full[s], SB);
-          tma_load_2d(st, &mapA, &full[s], xa + kb * TC_BK, m0);                     // A_hi
-          tma_load_2d(st + TC_A_BYTES, &mapA, &full[s], KpA + xa + kb * TC_BK, m0);  // A_lo
-          tma_load_2d(st + 2 * TC_A_BYTES, &mapB, &full[s], xoff + kb * TC_BK, n0);  // B_hi
-          tma_load_2d(st + 2 * TC_A_BYTES + B_BYTES, &mapB, &full[s], KpB + xoff + kb * TC_BK,
-                      n0);                                                            // B_lo
+          tma_load_2d(st, &mapA, &full[s], xa + kb * TC_BK, m0);                      // A_hi / A_0
+          tma_load_2d(st + TC_A_BYTES, &mapA, &full[s], secA + xa + kb * TC_BK, m0);  // A_lo / A_1
+          tma_load_2d(st + 2 * TC_A_BYTES, &mapB, &full[s], xoff + kb * TC_BK, n0);   // B_hi / B_0
+          tma_load_2d(st + 2 * TC_A_BYTES + B_BYTES, &mapB, &full[s], secB + xoff + kb * TC_BK,
+                      n0);                                                             // B_lo / B_1
         }
       }
       // copies in flight: the last NS stages issued must land before exit
@@ -338,7 +365,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
-      const uint32_t idesc = idesc_bf16(TC_BM, tn);
+      const uint32_t idesc = TF ? idesc_tf32(TC_BM, tn) : idesc_bf16(TC_BM, tn);
       const uint32_t base = smem_u32(smem);
       int g = 0, lt = 0;
       bool ok = true;
@@ -348,7 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int buf = lt & 1, use = lt >> 1;
         if (use > 0) {
           // the epilogue has drained this buffer's previous tile
-          if (!mbar_wait(&tempty[buf], (uint32_t)(use - 1) & 1u)) {
+          if (!mbar_wait(&tempty[buf], (uint32_t)(use - 1) & 1u, lim)) {
             atomicExch(err, 2);
             abort_flag = 1;
             ok = false;
@@ -359,7 +386,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t d = tmem + (uint32_t)(buf * TC_BN);
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % NS;
-          if (!mbar_wait(&full[s], (uint32_t)(g / NS) & 1u)) {
+          if (!mbar_wait(&full[s], (uint32_t)(g / NS) & 1u, lim)) {
             atomicExch(err, 2);
             abort_flag = 1;
             ok = false;
@@ -368,17 +395,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           fence_after();
           const uint32_t ahi = base + (uint32_t)s * SB, alo = ahi + TC_A_BYTES;
           const uint32_t bhi = ahi + 2 * TC_A_BYTES, blo = bhi + B_BYTES;
+          if (TF) {
 #pragma unroll
-          for (int k = 0; k < TC_BK / 16; ++k) {
-            mma_bf16(d, desc_sw128(ahi + 32 * k), desc_sw128(bhi + 32 * k), idesc,
-                     (kb > 0 || k > 0) ? 1u : 0u);
-            mma_bf16(d, desc_sw128(ahi + 32 * k), desc_sw128(blo + 32 * k), idesc, 1u);
-            mma_bf16(d, desc_sw128(alo + 32 * k), desc_sw128(bhi + 32 * k), idesc, 1u);
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t a0 = h ? alo : ahi, b0 = h ? blo : bhi;
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                mma_tf32(d, desc_sw128(a0 + 32 * k), desc_sw128(b0 + 32 * k), idesc,
+                         (kb > 0 || h > 0 || k > 0) ? 1u : 0u);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < TC_BK / 16; ++k) {
+              mma_bf16(d, desc_sw128(ahi + 32 * k), desc_sw128(bhi + 32 * k), idesc,
+                       (kb > 0 || k > 0) ? 1u : 0u);
+              mma_bf16(d, desc_sw128(ahi + 32 * k), desc_sw128(blo + 32 * k), idesc, 1u);
+              mma_bf16(d, desc_sw128(alo + 32 * k), desc_sw128(bhi + 32 * k), idesc, 1u);
+            }
           }
           mma_commit(&empty[s]);
         }
         if (ok) mma_commit(&tfull[buf]);
       }
+      // every MMA issued here (also after an abort) completes before the
+      // tensor memory is freed
+      mma_commit(drain);
+      mbar_wait(drain, 0u);
     }
     __syncwarp();
   } else {
@@ -398,7 +440,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int m0, xa, xoff, nkb, rows_valid, atom, n0;
       tile_of(t, m0, xa, xoff, nkb, rows_valid, atom, n0);
       const int buf = lt & 1, use = lt >> 1;
-      bool have = mbar_wait(&tfull[buf], (uint32_t)use & 1u);
+      bool have = mbar_wait(&tfull[buf], (uint32_t)use & 1u, lim);
       // tcgen05.ld is warp-collective: one decision per warp
       have = __all_sync(0xffffffffu, have && !*(volatile int *)&abort_flag);
       if (!have) {
@@ -422,7 +464,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         float v[16];
         tmem_ld16(trow + (uint32_t)j0, v);
-        epilogue16<EPI>(v, m, lr, rows_valid, atom, M, N, n0, j0, ep, di);
+        epilogue16<EPI, TF>(v, m, lr, rows_valid, atom, M, N, n0, j0, ep, di);
       }
       fence_before();
       __syncwarp();
@@ -474,24 +516,51 @@ cudaError_t encode_bf16_map(CUtensorMap *map, const void *base, int64_t rows, in
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// A 2-D bf16 operand [rows][2*Kp] ([hi | lo] planes), boxes of 64 x box_rows.
-cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows) {
+// Row-major float32 matrix [rows][cols] (cols a multiple of 64) with
+// 128-byte swizzled boxes of 32 columns x box_rows rows (tf32 operands).
+cudaError_t encode_f32_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols,
+                           int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if (cols % TC_BK != 0 || ((uintptr_t)base & 15) != 0) return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+  cuuint32_t estr[2] = {1, 1};
+  cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// A 2-D operand of Kp entries per row (Kp a multiple of 64): split bf16
+// [rows][2*Kp] ([hi | lo] planes, boxes of 64 x box_rows) or, with tf32,
+// float32 [rows][Kp] (boxes of 32 x box_rows); the same bytes per row.
+cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows,
+                             bool tf32) {
   if (Kp % TC_BK != 0) return cudaErrorInvalidValue;
-  // box_rows for the A role (128) or the 128-wide B tile; 64 for the 64-wide B tile
-  cudaError_t e = encode_bf16_map(&op.map, base, rows, 2 * (int64_t)Kp, box_rows);
-  if (e == cudaSuccess) e = encode_bf16_map(&op.map64, base, rows, 2 * (int64_t)Kp, 64);
-  if (e == cudaSuccess) e = encode_bf16_map(&op.map256, base, rows, 2 * (int64_t)Kp, 256);
+  auto enc = [&](CUtensorMap *m, int br) {
+    return tf32 ? encode_f32_map(m, base, rows, (int64_t)Kp, br)
+                : encode_bf16_map(m, base, rows, 2 * (int64_t)Kp, br);
+  };
+  // box_rows for the A role (128) or the 128-wide B tile; 64 and 256 for the other B tiles
+  cudaError_t e = enc(&op.map, box_rows);
+  if (e == cudaSuccess) e = enc(&op.map64, 64);
+  if (e == cudaSuccess) e = enc(&op.map256, 256);
   if (e != cudaSuccess) return e;
   op.has64 = true;
   op.rows = rows;
   op.Kp = Kp;
+  op.tf32 = tf32;
   return cudaSuccess;
 }
 
 namespace {
 template <int EPI, int BN>
 void set_attr() {
-  cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TcShape<BN>::SMEM);
+  cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)TcShape<BN>::SMEM);
 }
 
@@ -526,12 +595,12 @@ int sm_count() {
   return n;
 }
 
-template <int EPI, int BN>
+template <int EPI, int BN, bool TF>
 cudaError_t launch_tc(cudaStream_t st, int grid, const CUtensorMap &mA, const CUtensorMap &mB,
                       int M, int N, int KpA, int KpB, const TcEpilogue &ep, int *err,
                       const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
   if (ep.ncl <= 1) {
-    gemm_tc_kernel<EPI, BN><<<grid, TC_THREADS, TcShape<BN>::SMEM, st>>>(
+    gemm_tc_kernel<EPI, BN, TF><<<grid, TC_THREADS, TcShape<BN>::SMEM, st>>>(
         mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n, tiles, n_mtiles);
     return cudaGetLastError();
   }
@@ -553,16 +622,17 @@ cudaError_t launch_tc(cudaStream_t st, int grid, const CUtensorMap &mA, const CU
   if (fit[ep.ncl] == 0) {
     cfg.gridDim = dim3(ep.ncl * sm_count());
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, gemm_tc_kernel<EPI, BN>, &cfg) != cudaSuccess || n < 1)
+    if (cudaOccupancyMaxActiveClusters(&n, gemm_tc_kernel<EPI, BN, TF>, &cfg) != cudaSuccess ||
+        n < 1)
       return cudaErrorInvalidConfiguration;
     fit[ep.ncl] = n;
   }
   cfg.gridDim = dim3(std::min(grid / ep.ncl, fit[ep.ncl]) * ep.ncl);
-  return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<EPI, BN>, mA, mB, M, N, KpA, KpB, ep, err, dcnt,
-                            mul_n, tiles, n_mtiles);
+  return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<EPI, BN, TF>, mA, mB, M, N, KpA, KpB, ep, err,
+                            dcnt, mul_n, tiles, n_mtiles);
 }
 
-template <int BN>
+template <int BN, bool TF>
 cudaError_t launch_tc_epi(cudaStream_t st, int epi, int M, int N, const CUtensorMap &mA,
                           const CUtensorMap &mB, int KpA, int KpB, const TcEpilogue &ep, int *err,
                           const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
@@ -571,57 +641,80 @@ cudaError_t launch_tc_epi(cudaStream_t st, int epi, int M, int N, const CUtensor
   const int grid = (int)std::min<int64_t>(n_tiles, sm_count());
   switch (epi) {
     case kStoreF32:
-      return launch_tc<kStoreF32, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+      return launch_tc<kStoreF32, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
                                       tiles, n_mtiles);
     case kDscaleSplit:
-      return launch_tc<kDscaleSplit, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+      return launch_tc<kDscaleSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
                                          tiles, n_mtiles);
     case kBetaTSplit:
-      return launch_tc<kBetaTSplit, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+      return launch_tc<kBetaTSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
                                         tiles, n_mtiles);
     case kGammaCatSplit:
-      return launch_tc<kGammaCatSplit, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+      return launch_tc<kGammaCatSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
                                            tiles, n_mtiles);
     case kPartialF32:
-      return launch_tc<kPartialF32, BN>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
+      return launch_tc<kPartialF32, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
                                         tiles, n_mtiles);
     default:
       return cudaErrorInvalidValue;
   }
 }
+// the N tile's B map and the operand format select the kernel
+cudaError_t dispatch_bn(cudaStream_t st, int epi, int M, int N, const TcOperand &A,
+                        const TcOperand &B, const TcEpilogue &e, int *err, const int *dcnt,
+                        int mul_n, const GTile *tiles, int n_mtiles, int bn) {
+  if (A.tf32) {
+    if (bn == 64)
+      return launch_tc_epi<64, true>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, e, err, dcnt,
+                                     mul_n, tiles, n_mtiles);
+    if (bn == 256)
+      return launch_tc_epi<256, true>(st, epi, M, N, A.map, B.map256, A.Kp, B.Kp, e, err, dcnt,
+                                      mul_n, tiles, n_mtiles);
+    return launch_tc_epi<128, true>(st, epi, M, N, A.map, B.map, A.Kp, B.Kp, e, err, dcnt, mul_n,
+                                    tiles, n_mtiles);
+  }
+  if (bn == 64)
+    return launch_tc_epi<64, false>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, e, err, dcnt,
+                                    mul_n, tiles, n_mtiles);
+  if (bn == 256)
+    return launch_tc_epi<256, false>(st, epi, M, N, A.map, B.map256, A.Kp, B.Kp, e, err, dcnt,
+                                     mul_n, tiles, n_mtiles);
+  return launch_tc_epi<128, false>(st, epi, M, N, A.map, B.map, A.Kp, B.Kp, e, err, dcnt, mul_n,
+                                   tiles, n_mtiles);
+}
 }  // namespace
+
+void tc_split_plan(int Kp, int M, int N, int bn, int *ksplit, int *ncl) {
+  const int n_mtiles = (M + TC_BM - 1) / TC_BM;
+  *ksplit = 1;
+  *ncl = 1;
+  if (Kp / TC_BK < 32) return;
+  const int nnt = (N + bn - 1) / bn;
+  // too few tiles for the SMs: two K halves, added into the zeroed output
+  if ((int64_t)n_mtiles * nnt < 2 * (int64_t)sm_count()) *ksplit = 2;
+  // a long shared A (the kernel matrix) and a few N tiles: one cluster per
+  // M row block (and K half), so that A comes from DRAM once
+  if (nnt >= 2 && nnt <= 4) *ncl = nnt;
+}
 
 cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
                            int epi, const TcEpilogue &ep, int *err, const int *dcnt, int mul_n,
                            int bn) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (A.Kp != B.Kp) return cudaErrorInvalidValue;
+  if (A.Kp != B.Kp || A.tf32 != B.tf32) return cudaErrorInvalidValue;
   tc_init_attributes();
   if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
   const int n_mtiles = (M + TC_BM - 1) / TC_BM;
   TcEpilogue e = ep;
   e.ksplit = 1;
-  if (epi == kStoreF32 && ep.split_ok && A.Kp / TC_BK >= 32 &&
-      (int64_t)n_mtiles * ((N + bn - 1) / bn) < 2 * (int64_t)sm_count()) {
-    // too few tiles for the SMs: two K halves, added into the zeroed output
-    e.ksplit = 2;
-    cudaError_t r = cudaMemsetAsync(ep.outF, 0, (size_t)N * ep.ldo * sizeof(float), st);
-    if (r != cudaSuccess) return r;
+  if (epi == kStoreF32 && ep.split_ok) {
+    tc_split_plan(A.Kp, M, N, bn, &e.ksplit, &e.ncl);
+    if (e.ksplit > 1) {
+      cudaError_t r = cudaMemsetAsync(ep.outF, 0, (size_t)N * ep.ldo * sizeof(float), st);
+      if (r != cudaSuccess) return r;
+    }
   }
-  if (epi == kStoreF32 && ep.split_ok && A.Kp / TC_BK >= 32) {
-    // a long shared A (the kernel matrix) and a few N tiles: one cluster per
-    // M row block (and K half), so that A comes from DRAM once
-    const int nnt = (N + bn - 1) / bn;
-    if (nnt >= 2 && nnt <= 4) e.ncl = nnt;
-  }
-  if (bn == 64)
-    return launch_tc_epi<64>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, e, err, dcnt, mul_n,
-                             nullptr, n_mtiles);
-  if (bn == 256)
-    return launch_tc_epi<256>(st, epi, M, N, A.map, B.map256, A.Kp, B.Kp, e, err, dcnt, mul_n,
-                              nullptr, n_mtiles);
-  return launch_tc_epi<128>(st, epi, M, N, A.map, B.map, A.Kp, B.Kp, e, err, dcnt, mul_n, nullptr,
-                            n_mtiles);
+  return dispatch_bn(st, epi, M, N, A, B, e, err, dcnt, mul_n, nullptr, n_mtiles, bn);
 }
 
 cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const TcOperand &B,
@@ -631,16 +724,10 @@ cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const Tc
   if (n_tiles <= 0 || N <= 0) return cudaSuccess;
   tc_init_attributes();
   if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
+  if (A.tf32 != B.tf32) return cudaErrorInvalidValue;
   TcEpilogue e = ep;
   e.ksplit = 1;
-  if (bn == 64)
-    return launch_tc_epi<64>(st, epi, 0, N, A.map, B.map64, A.Kp, B.Kp, e, err, dcnt, mul_n,
-                             tiles, n_tiles);
-  if (bn == 256)
-    return launch_tc_epi<256>(st, epi, 0, N, A.map, B.map256, A.Kp, B.Kp, e, err, dcnt, mul_n,
-                              tiles, n_tiles);
-  return launch_tc_epi<128>(st, epi, 0, N, A.map, B.map, A.Kp, B.Kp, e, err, dcnt, mul_n, tiles,
-                            n_tiles);
+  return dispatch_bn(st, epi, 0, N, A, B, e, err, dcnt, mul_n, tiles, n_tiles, bn);
 }
 
 }  // namespace tddft
@@ -660,7 +747,7 @@ __device__ __forceinline__ double hash_uniform(uint64_t i, uint64_t seed) {
   return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 __global__ void st_fill_split(int rows, int K, int Kp, uint64_t seed, double *full,
-                              __nv_bfloat16 *split) {
+                              __nv_bfloat16 *split, bool tf32) {
   const int64_t total = (int64_t)rows * Kp;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -668,6 +755,10 @@ __global__ void st_fill_split(int rows, int K, int Kp, uint64_t seed, double *fu
     const int k = (int)(i % Kp);
     const double x = (k < K) ? hash_uniform((uint64_t)(r * K + k), seed) : 0.0;
     if (k < K) full[r * K + k] = x;
+    if (tf32) {
+      ((float *)split)[i] = ptx::tf32_round((float)x);
+      continue;
+    }
     const __nv_bfloat16 hi = __double2bfloat16(x);
     split[r * 2 * Kp + k] = hi;
     split[r * 2 * Kp + Kp + k] = __double2bfloat16(x - (double)__bfloat162float(hi));
@@ -691,8 +782,9 @@ __global__ void st_ref(int M, int N, int K, const double *A, const double *B, co
 }  // namespace
 }  // namespace tddft
 
-extern "C" tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uint64_t seed,
-                                            double *max_rel_err) {
+namespace {
+tddft_status selftest_gemm(int32_t M, int32_t N, int32_t K, uint64_t seed, double *max_rel_err,
+                           bool tf32) {
   using namespace tddft;
   if (M < 1 || N < 1 || K < 1 || !max_rel_err) return TDDFT_ERR_INVALID_ARG;
   const int Kp = round_up(K, 64);
@@ -707,15 +799,15 @@ extern "C" tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uin
   if (e == cudaSuccess) e = cudaMalloc(&Bs, (size_t)N * 2 * Kp * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&C, (size_t)N * M * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&e2, 2 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&err, ptx::kErrInts * sizeof(int));
   TcOperand *opA = new TcOperand(), *opB = new TcOperand();
   if (e == cudaSuccess) {
     cudaMemset(e2, 0, 2 * sizeof(double));
-    cudaMemset(err, 0, sizeof(int));
-    st_fill_split<<<304, 256>>>(M, K, Kp, seed, A, As);
-    st_fill_split<<<304, 256>>>(N, K, Kp, seed + 1, B, Bs);
-    e = make_operand_map(*opA, As, M, Kp, 128);
-    if (e == cudaSuccess) e = make_operand_map(*opB, Bs, N, Kp, 128);
+    cudaMemset(err, 0, ptx::kErrInts * sizeof(int));
+    st_fill_split<<<304, 256>>>(M, K, Kp, seed, A, As, tf32);
+    st_fill_split<<<304, 256>>>(N, K, Kp, seed + 1, B, Bs, tf32);
+    e = make_operand_map(*opA, As, M, Kp, 128, tf32);
+    if (e == cudaSuccess) e = make_operand_map(*opB, Bs, N, Kp, 128, tf32);
   }
   // both N-tile widths, each checked against the float64 product
   for (int bn : {128, 64, 256}) {
@@ -745,4 +837,15 @@ extern "C" tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uin
   delete opB;
   cudaFree(A); cudaFree(B); cudaFree(As); cudaFree(Bs); cudaFree(C); cudaFree(e2); cudaFree(err);
   return status;
+}
+}  // namespace
+
+extern "C" tddft_status tddft_selftest_gemm(int32_t M, int32_t N, int32_t K, uint64_t seed,
+                                            double *max_rel_err) {
+  return selftest_gemm(M, N, K, seed, max_rel_err, false);
+}
+
+extern "C" tddft_status tddft_selftest_gemm_tf32(int32_t M, int32_t N, int32_t K, uint64_t seed,
+                                                 double *max_rel_err) {
+  return selftest_gemm(M, N, K, seed, max_rel_err, true);
 }

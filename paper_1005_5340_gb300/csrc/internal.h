@@ -59,7 +59,9 @@ enum KernelClass {
   // float64 products emulated on the tensor cores (integer slices)
   kcOzSlice, kcOzK, kcOzT1, kcOzT2,
   // steps 2 and 5 on the stored transition vertex
-  kcAlphaGather, kcTcStep2, kcTcStep5, kcOzStep2, kcOzStep5, kcCount
+  kcAlphaGather, kcTcStep2, kcTcStep5, kcOzStep2, kcOzStep5,
+  // small kernels of the tensor-core forms: D(omega) terms, sum of the step-5 partials
+  kcDterm, kcCombine, kcCount
 };
 const char *kernel_class_name(int k);
 // Record msg as the context's last error (tddft_last_error) and return s.
@@ -155,13 +157,15 @@ struct TcOperand {
   CUtensorMap map64;   // boxes of 64 x 64 rows (the B operand of the 64-wide tile)
   CUtensorMap map256;  // boxes of 64 x 256 rows (the B operand of the 256-wide tile)
   bool has64 = false;
+  bool tf32 = false;   // float32 rows of Kp tf32 values instead of split bf16
   int64_t rows = 0;
   int Kp = 0;
 };
 
 struct TcEpilogue {
   float *outF = nullptr;           // kStoreF32: C^T[n][m] at n*ldo + m
-  __nv_bfloat16 *outB = nullptr;   // kDscaleSplit: hi at n*ldo + m, lo at n*ldo + lo_off + m
+  void *outB = nullptr;            // kDscaleSplit: hi at n*ldo + m, lo at n*ldo + lo_off + m
+                                   // (bf16; a tf32 float at n*ldo + m for tf32 operands)
   int64_t ldo = 0;
   int64_t lo_off = 0;
   int rows_out = 0;                // kDscaleSplit: rows m < rows_out written (zeros past M)
@@ -180,7 +184,8 @@ struct TcEpilogue {
   const int *xoff5 = nullptr;      // kGammaCatSplit
 };
 
-cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows);
+cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows,
+                             bool tf32 = false);
 // Row-major bf16 [rows][cols] (cols a multiple of 64) with 128-byte swizzled
 // boxes of 64 columns x box_rows rows.
 cudaError_t encode_bf16_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols,
@@ -203,11 +208,28 @@ cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const Tc
                                    const TcEpilogue &ep, int *err, const int *dcnt = nullptr,
                                    int mul_n = 0, int bn = 128);
 void tc_init_attributes();
+// Split K (ksplit 1 or 2) and cluster size (ncl 1..4) of a kStoreF32 product
+// with split_ok (the K product): A of M rows and padded K Kp, N columns, N tile bn.
+void tc_split_plan(int Kp, int M, int N, int bn, int *ksplit, int *ncl);
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Warm-started sweep (sweep.cu): frequencies solved per chunk, one solver
+// group at most, and the learned network's rows (3 x frequencies x n_prod)
+// at most kSweepMaxRows (its float32 activations: 2 x rows x width).
+constexpr int64_t kSweepMaxRows = (int64_t)1 << 22;
+inline int sweep_chunk_freqs(int slots, int n_prod) {
+  const int64_t cw = slots / 3 > 1 ? slots / 3 : 1;
+  const int64_t cap = kSweepMaxRows / (3 * (int64_t)n_prod);
+  return (int)(cw < cap ? cw : (cap > 1 ? cap : 1));
+}
+tddft_status sweep_polarizability(tddft_ctx *c, int32_t n_omega, const double *omega, double eps,
+                                  double *Xout, double *P, tddft_solve_stats *stats,
+                                  int32_t flags);
+
 struct LpWork {
   int slots = 0;
+  bool tf32 = false;               // operands are float32 rows of tf32 values (same bytes)
   int KpK = 0, Kp1 = 0, Kp2 = 0;   // padded K of the K product, transform 1, transform 2
   __nv_bfloat16 *Ks = nullptr;     // [n_prod][2 KpK]   K split
   __nv_bfloat16 *XvTs = nullptr;   // [n_virt][2 Kp1]   X_virt^T split
@@ -332,8 +354,9 @@ struct AlphaRoute {
   int *xoff5 = nullptr;       // [n_atoms] Gcat segment of each atom
   int *orb_atom = nullptr;    // [n_orb]
   int ldp = 0;                // P2 row stride (2 S)
-  // split bf16 (reduced-precision operator)
+  // split bf16 (reduced-precision operator), or tf32 rows of the same bytes
   bool lp = false;
+  bool tf32 = false;
   TcOperand a2, a5, ycat, gcat;
   __nv_bfloat16 *ycat_q = nullptr, *gcat_q = nullptr;   // [2S][2 kcat2], [2S][2 kcat5]
   float *P2f = nullptr;
@@ -385,6 +408,7 @@ struct GmresState {
   int *act = nullptr;       // [cap] active right-hand sides, in order
   int *act2 = nullptr;      // [cap] second list (right-hand sides awaiting A x) when split
   int *count = nullptr;     // [2]
+  int *loopctl = nullptr;   // [2] device-driven loop: iterations run, 1 if the bound was hit
   unsigned long long *bytes = nullptr;   // [1] algorithmic bytes of the GMRES steps
   // stopping rule: 0 relative residual, 1 eps_P <= tol, 2 eps_P and eps_X <= tol
   // (Sec. 4.1 error estimates; the buffers below exist only for 1 and 2)

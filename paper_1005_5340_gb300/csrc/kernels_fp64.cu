@@ -426,10 +426,13 @@ namespace {
 cudaError_t alpha_beta_emulated(cudaStream_t st, const DevSystem &sys, OpWork &wk, int n_rows,
                                 const double *Ysrc, const int *dcnt) {
   AlphaRoute &ar = *wk.ar;
+  cudaError_t err;
+  {
+    Scope sc(wk.timer, st, kcOzSlice, 0.0);
+    err = launch_oz_slice_rows(st, Ysrc, sys.n_prod, n_rows, ar.kcat2, ar.oycat, dcnt, 2, ar.lcat);
+    if (err != cudaSuccess) return err;
+  }
   Scope sc(wk.timer, st, kcOzStep2, n_rows * ar.flops2);
-  cudaError_t err = launch_oz_slice_rows(st, Ysrc, sys.n_prod, n_rows, ar.kcat2, ar.oycat, dcnt, 2,
-                                         ar.lcat);
-  if (err != cudaSuccess) return err;
   OzEpilogue eb;
   eb.mode = kOzBetaT;
   eb.C = wk.beta;
@@ -450,10 +453,14 @@ cudaError_t alpha_dot_emulated(cudaStream_t st, const DevSystem &sys, OpWork &wk
   const int64_t ncolE = (int64_t)ncols * sys.n_occ;
   cudaError_t err;
   {
-    Scope sc(wk.timer, st, timer_class,
-             timer_class == kcOzT2 ? 2.0 * sys.n_virt * (double)sys.n_orb * ncolE : 0.0);
+    Scope sc(wk.timer, st, kcOzSlice, 0.0);
     err = launch_oz_slice_cols(st, wk.abuf, ncolE, sys.n_virt, (int)ncolE, oz.Bt2, dcnt,
                                2 * sys.n_occ);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(wk.timer, st, timer_class,
+             timer_class == kcOzT2 ? 2.0 * sys.n_virt * (double)sys.n_orb * ncolE : 0.0);
     OzEpilogue eg;
     eg.mode = kOzGammaCat;
     eg.C = ar.gcat64;
@@ -462,23 +469,27 @@ cudaError_t alpha_dot_emulated(cudaStream_t st, const DevSystem &sys, OpWork &wk
     eg.orb_atom = ar.orb_atom;
     eg.xoff5 = ar.xoff5;
     eg.n_occ = sys.n_occ;
-    if (err == cudaSuccess)
-      err = launch_gemm_oz_ex(st, oz.Xv, oz.Bt2, sys.n_orb, (int)ncolE, eg, nullptr, 0, 0, oz.err,
-                              dcnt, 2 * sys.n_occ);
+    err = launch_gemm_oz_ex(st, oz.Xv, oz.Bt2, sys.n_orb, (int)ncolE, eg, nullptr, 0, 0, oz.err,
+                            dcnt, 2 * sys.n_occ);
     if (err != cudaSuccess) return err;
   }
-  Scope sc(wk.timer, st, kcOzStep5, ncols * ar.flops5);
-  err = launch_oz_slice_rows(st, ar.gcat64, ar.kcat5, ncols, ar.kcat5, ar.ogcat, dcnt, 2);
-  OzEpilogue ep;
-  ep.mode = kOzC;
-  ep.C = ar.P2d;
-  ep.ldc = ar.ldp;
-  if (err == cudaSuccess)
+  {
+    Scope sc(wk.timer, st, kcOzSlice, 0.0);
+    err = launch_oz_slice_rows(st, ar.gcat64, ar.kcat5, ncols, ar.kcat5, ar.ogcat, dcnt, 2);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(wk.timer, st, kcOzStep5, ncols * ar.flops5);
+    OzEpilogue ep;
+    ep.mode = kOzC;
+    ep.C = ar.P2d;
+    ep.ldc = ar.ldp;
     err = launch_gemm_oz_ex(st, ar.oa5, ar.ogcat, 0, ncols, ep, ar.tiles5, ar.n_tiles5,
                             ar.max_nkb5, oz.err, dcnt, 2);
-  if (err == cudaSuccess)
-    err = launch_alpha_combine(st, ar, ncols, sys.n_prod, true, Zin, subtract, Out, dcnt);
-  return err;
+    if (err != cudaSuccess) return err;
+  }
+  Scope sc(wk.timer, st, kcCombine, 0.0);
+  return launch_alpha_combine(st, ar, ncols, sys.n_prod, true, Zin, subtract, Out, dcnt);
 }
 
 // chi0 (or A) with every dense product emulated in float64 and steps 2 and
@@ -492,12 +503,15 @@ cudaError_t apply_alpha_emulated(cudaStream_t st, const DevSystem &sys, OpWork &
   cudaError_t err = alpha_beta_emulated(st, sys, wk, ncols, Y, wk.dcnt);
   if (err != cudaSuccess) return err;
   {
-    Scope sc(wk.timer, st, kcOzT1, 2.0 * sys.n_virt * (double)sys.n_orb * ncolE);
+    Scope sc(wk.timer, st, kcOzSlice, 0.0);
     err = launch_oz_slice_rows(st, wk.beta, sys.n_orb, (int)ncolE, sys.n_orb, oz.Bt1, wk.dcnt,
                                2 * sys.n_occ);
-    if (err == cudaSuccess)
-      err = launch_gemm_oz(st, oz.XvT, oz.Bt1, sys.n_virt, (int)ncolE, wk.abuf, ncolE, 0, oz.err,
-                           wk.dcnt, 2 * sys.n_occ);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(wk.timer, st, kcOzT1, 2.0 * sys.n_virt * (double)sys.n_orb * ncolE);
+    err = launch_gemm_oz(st, oz.XvT, oz.Bt1, sys.n_virt, (int)ncolE, wk.abuf, ncolE, 0, oz.err,
+                         wk.dcnt, 2 * sys.n_occ);
     if (err != cudaSuccess) return err;
   }
   {
@@ -592,8 +606,11 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
     double *Yout = (mode == kKernel) ? Out : wk.Y;
     if (wk.oz) {
       // emulated: (K z_c)_mu = sum_nu K[mu][nu] z_c[nu], stored transposed
+      {
+        Scope sc(wk.timer, st, kcOzSlice, 0.0);
+        err = launch_oz_slice_rows(st, Zin, np, ncols, np, wk.oz->Z, wk.dcnt, 2);
+      }
       Scope sc(wk.timer, st, kcOzK, 2.0 * ncols * (double)np * np);
-      err = launch_oz_slice_rows(st, Zin, np, ncols, np, wk.oz->Z, wk.dcnt, 2);
       if (err == cudaSuccess)
         err = launch_gemm_oz(st, wk.oz->K, wk.oz->Z, np, ncols, Yout, np, 1, wk.oz->err, wk.dcnt,
                              2);
@@ -625,9 +642,12 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
   const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)ncolE;
   if (wk.oz) {
     // emulated: slices of the columns of beta (rows of beta^T), then X_virt^T beta
+    {
+      Scope sc(wk.timer, st, kcOzSlice, 0.0);
+      err = launch_oz_slice_cols(st, wk.beta, ncolE, sys.n_orb, (int)ncolE, wk.oz->Bt1, wk.dcnt,
+                                 2 * sys.n_occ);
+    }
     Scope sc(wk.timer, st, kcOzT1, tflops);
-    err = launch_oz_slice_cols(st, wk.beta, ncolE, sys.n_orb, (int)ncolE, wk.oz->Bt1, wk.dcnt,
-                               2 * sys.n_occ);
     if (err == cudaSuccess)
       err = launch_gemm_oz(st, wk.oz->XvT, wk.oz->Bt1, sys.n_virt, (int)ncolE, wk.abuf, ncolE, 0,
                            wk.oz->err, wk.dcnt, 2 * sys.n_occ);
@@ -645,9 +665,12 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   if (wk.oz) {
+    {
+      Scope sc(wk.timer, st, kcOzSlice, 0.0);
+      err = launch_oz_slice_cols(st, wk.abuf, ncolE, sys.n_virt, (int)ncolE, wk.oz->Bt2, wk.dcnt,
+                                 2 * sys.n_occ);
+    }
     Scope sc(wk.timer, st, kcOzT2, tflops);
-    err = launch_oz_slice_cols(st, wk.abuf, ncolE, sys.n_virt, (int)ncolE, wk.oz->Bt2, wk.dcnt,
-                               2 * sys.n_occ);
     if (err == cudaSuccess)
       err = launch_gemm_oz(st, wk.oz->Xv, wk.oz->Bt2, sys.n_orb, (int)ncolE, wk.gamma, ncolE, 0,
                            wk.oz->err, wk.dcnt, 2 * sys.n_occ);

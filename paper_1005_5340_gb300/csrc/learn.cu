@@ -364,6 +364,8 @@ const DevSystem *ctx_system(const tddft_ctx *c);
 cudaStream_t ctx_stream(const tddft_ctx *c);
 void ctx_set_error(tddft_ctx *c, const char *msg);
 const float *ctx_product_features(const tddft_ctx *c);
+int ctx_slots(const tddft_ctx *c);
+void ctx_set_guess_net(tddft_ctx *c, tddft_mlp *net);
 
 }  // namespace tddft
 
@@ -589,6 +591,40 @@ tddft_status tddft_guess_features(tddft_ctx *ctx, int32_t n_target, const int32_
     ctx_set_error(ctx, cudaGetErrorString(e));
     return TDDFT_ERR_CUDA;
   }
+  return TDDFT_OK;
+}
+
+tddft_status tddft_guess_load(tddft_ctx *ctx, const char *path) {
+  if (!ctx) return TDDFT_ERR_INVALID_ARG;
+  ctx_set_error(ctx, "");
+  if (!path) {
+    ctx_set_error(ctx, "path is NULL");
+    return TDDFT_ERR_INVALID_ARG;
+  }
+  FILE *f = std::fopen(path, "rb");
+  MlpFileHeader hd;
+  const bool ok = f && std::fread(&hd, sizeof(hd), 1, f) == 1 &&
+                  std::memcmp(hd.magic, kMlpMagic, 8) == 0 && hd.version == 1;
+  if (f) std::fclose(f);
+  if (!ok) {
+    ctx_set_error(ctx, (std::string("not a readable network file of version 1: ") + path).c_str());
+    return TDDFT_ERR_INVALID_ARG;
+  }
+  if (hd.n_in != 10 || hd.n_out != 2) {
+    ctx_set_error(ctx, "the guess network maps 10 features to 2 outputs");
+    return TDDFT_ERR_SHAPE;
+  }
+  const DevSystem &s = *ctx_system(ctx);
+  const int64_t rows = 3 * (int64_t)sweep_chunk_freqs(ctx_slots(ctx), s.n_prod) * s.n_prod;
+  tddft_mlp *net = nullptr;
+  tddft_status st = tddft_mlp_create(hd.n_in, hd.width, hd.n_out, rows, 0, ctx_stream(ctx), &net);
+  if (st == TDDFT_OK) st = tddft_mlp_load(net, path);
+  if (st != TDDFT_OK) {
+    ctx_set_error(ctx, net ? net->err.c_str() : g_mlp_error.c_str());
+    if (net) tddft_mlp_destroy(net);
+    return st;
+  }
+  ctx_set_guess_net(ctx, net);
   return TDDFT_OK;
 }
 

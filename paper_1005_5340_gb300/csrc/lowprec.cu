@@ -1,9 +1,11 @@
 // Reduced-precision application of A(omega) z = z - chi0(omega) (K z)
 // (Sec. 4.1, chi0 . y by steps 1-5 of Table t:flops on the stored transition
 // vertex) used for the inner GMRES iterations of the refinement forms.  Every
-// product runs on the tensor cores in split bf16 with float32 accumulation
-// (gemm_tc.cu): K z, step 2 (per atom, alpha.cu), X_virt^T beta with the
-// D(omega) epilogue, X_virt a into the per-atom Gcat rows, step 5 (per atom).
+// product runs on the tensor cores in split bf16 (or, in the TF32 forms, in
+// tf32; the same buffers hold Kp floats per row instead of the [hi | lo]
+// planes) with float32 accumulation (gemm_tc.cu): K z, step 2 (per atom,
+// alpha.cu), X_virt^T beta with the D(omega) epilogue, X_virt a into the
+// per-atom Gcat rows, step 5 (per atom).
 // Layouts (n = right-hand-side column, complex planes interleaved per
 // occupied state):
 //   Zb     [2S][2 KpK]          z split, row c = 2 s + p
@@ -13,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include "internal.h"
+#include "tc_ptx.h"
 
 namespace tddft {
 namespace {
@@ -38,8 +41,9 @@ struct Scope {
 };
 
 // dst[r][k] = hi(src[r, k]), dst[r][Kp + k] = lo(src[r, k]); zero for k >= cols.
+// With tf32: dst is float [r][Kp], the value rounded to tf32 (same bytes per row).
 __global__ void split_rows_kernel(const double *__restrict__ src, int64_t rs, int64_t cs, int rows,
-                                  int cols, int Kp, __nv_bfloat16 *__restrict__ dst,
+                                  int cols, int Kp, void *__restrict__ dstv, bool tf32,
                                   const int *__restrict__ dcnt = nullptr, int mul_r = 0) {
   if (dcnt) rows = min(rows, mul_r * *dcnt);
   const int64_t total = (int64_t)rows * Kp;
@@ -48,6 +52,11 @@ __global__ void split_rows_kernel(const double *__restrict__ src, int64_t rs, in
     const int64_t r = i / Kp;
     const int k = (int)(i % Kp);
     double x = (k < cols) ? src[r * rs + (int64_t)k * cs] : 0.0;
+    if (tf32) {
+      ((float *)dstv)[i] = ptx::tf32_round((float)x);
+      continue;
+    }
+    __nv_bfloat16 *dst = (__nv_bfloat16 *)dstv;
     const __nv_bfloat16 hi = __double2bfloat16(x);
     const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
     dst[r * 2 * Kp + k] = hi;
@@ -84,9 +93,12 @@ __global__ void dterm_kernel(int S, int n_virt, int n_occ, const double *__restr
 
 cudaError_t lp_prepare_constants(cudaStream_t st, const DevSystem &sys, LpWork &lp) {
   const int g = 152 * 8;
-  split_rows_kernel<<<g, 256, 0, st>>>(sys.K, sys.n_prod, 1, sys.n_prod, sys.n_prod, lp.KpK, lp.Ks);
-  split_rows_kernel<<<g, 256, 0, st>>>(sys.XvT, sys.n_orb, 1, sys.n_virt, sys.n_orb, lp.Kp1, lp.XvTs);
-  split_rows_kernel<<<g, 256, 0, st>>>(sys.Xv, sys.n_virt, 1, sys.n_orb, sys.n_virt, lp.Kp2, lp.Xvs);
+  split_rows_kernel<<<g, 256, 0, st>>>(sys.K, sys.n_prod, 1, sys.n_prod, sys.n_prod, lp.KpK, lp.Ks,
+                                       lp.tf32);
+  split_rows_kernel<<<g, 256, 0, st>>>(sys.XvT, sys.n_orb, 1, sys.n_virt, sys.n_orb, lp.Kp1, lp.XvTs,
+                                       lp.tf32);
+  split_rows_kernel<<<g, 256, 0, st>>>(sys.Xv, sys.n_virt, 1, sys.n_orb, sys.n_virt, lp.Kp2, lp.Xvs,
+                                       lp.tf32);
   split_f32_pairs_kernel<<<4, 256, 0, st>>>(sys.energy, sys.n_occ, lp.eocc2);
   const size_t rows = (size_t)2 * lp.slots * sys.n_occ;
   cudaMemsetAsync(lp.Zb, 0, (size_t)2 * lp.slots * 2 * lp.KpK * sizeof(__nv_bfloat16), st);
@@ -198,7 +210,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     {
       Scope sc(lp.timer, st, kcLpSplit, 0.0);
       split_rows_kernel<<<grid_for((int64_t)ncols * lp.KpK, 256), 256, 0, st>>>(
-          Zin, np, 1, ncols, np, lp.KpK, lp.Zb, lp.dcnt, 2);
+          Zin, np, 1, ncols, np, lp.KpK, lp.Zb, lp.tf32, lp.dcnt, 2);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     {
@@ -235,10 +247,13 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
   }
   const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)N1;
   {
-    Scope sc(lp.timer, st, kcTcT1, tflops);
+    Scope sc(lp.timer, st, kcDterm, 0.0);
     dterm_kernel<<<grid_for((int64_t)S * sys.n_virt, 256), 256, 0, st>>>(
         S, sys.n_virt, sys.n_occ, sys.energy, lp.omega, lp.dterm, lp.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  {
+    Scope sc(lp.timer, st, kcTcT1, tflops);
     TcEpilogue e1;
     e1.outB = lp.aT;
     e1.ldo = 2 * (int64_t)lp.Kp2;
@@ -278,8 +293,11 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     e5.ldo = ar.ldp;
     err = launch_gemm_tc_grouped(st, ar.a5, ar.gcat, ar.tiles5, ar.n_tiles5, ncols, kPartialF32,
                                  e5, lp.err, lp.dcnt, 2);
-    if (err == cudaSuccess)
-      err = launch_alpha_combine(st, ar, ncols, np, false, Zin, mode == kA ? 1 : 0, Out, lp.dcnt);
+    if (err != cudaSuccess) return err;
+  }
+  {
+    Scope sc(lp.timer, st, kcCombine, 0.0);
+    err = launch_alpha_combine(st, ar, ncols, np, false, Zin, mode == kA ? 1 : 0, Out, lp.dcnt);
     if (err != cudaSuccess) return err;
   }
   return cudaSuccess;

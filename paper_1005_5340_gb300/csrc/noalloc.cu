@@ -33,6 +33,7 @@ extern "C" tddft_status tddft_chi0_apply_noalloc(tddft_ctx *ctx, int32_t n_rhs,
                                                  const double *z, double *out, int32_t flags) {
   using namespace tddft;
   if (!ctx) return TDDFT_ERR_INVALID_ARG;
+  ctx_set_error(ctx, "");   // no stale message from an earlier failed call
   if (!(flags & TDDFT_DEVICE_PTRS) || !omega || !z || !out) {
     ctx_set_error(ctx, "tddft_chi0_apply_noalloc takes device pointers only (flags bit 0)");
     return TDDFT_ERR_INVALID_ARG;

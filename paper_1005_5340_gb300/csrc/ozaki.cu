@@ -140,8 +140,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   uint64_t *empty = full + OZ_STAGES;
   uint64_t *tfull = empty + OZ_STAGES;
   uint64_t *tempty = tfull + 1;   // [kOzMaxSlices] one per TMEM group
-  uint32_t *tslot = (uint32_t *)(tempty + kOzMaxSlices);
+  uint64_t *drain = tempty + kOzMaxSlices;   // completion of every MMA this CTA issued
+  uint32_t *tslot = (uint32_t *)(drain + 1);
   __shared__ int abort_flag;
+  const uint64_t lim = wait_limit(a.err);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int s = S;
@@ -157,6 +159,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     mbar_init(tfull, 1);
     for (int q = 0; q < kOzMaxSlices; ++q)
       mbar_init(&tempty[q], OZ_EPI_WARPS);   // one arrival per epilogue warp
+    mbar_init(drain, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int i = 0; i < s; ++i, ++g) {
           const int slot = g % OZ_STAGES;
           const uint32_t ph = (uint32_t)(g / OZ_STAGES) & 1u;
-          if (!mbar_wait(&empty[slot], ph ^ 1u)) {
+          if (!mbar_wait(&empty[slot], ph ^ 1u, lim)) {
             atomicExch(a.err, 21);
             abort_flag = 1;
             ok = false;
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int kb = c * cb; kb < kb1 && ok; ++kb) {
           for (int i = 0; i < s && ok; ++i) {
             const int gi = g + i;
-            if (!mbar_wait(&full[gi % OZ_STAGES], (uint32_t)(gi / OZ_STAGES) & 1u)) {
+            if (!mbar_wait(&full[gi % OZ_STAGES], (uint32_t)(gi / OZ_STAGES) & 1u, lim)) {
               atomicExch(a.err, 23);
               abort_flag = 1;
               ok = false;
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               const uint32_t sj = base + (uint32_t)((g + j) % OZ_STAGES) * OZ_STAGE_BYTES;
               const int grp = i + j;
               if (!((drained >> grp) & 1u)) {
-                if (!mbar_wait(&tempty[grp], (uint32_t)(c - 1) & 1u)) {
+                if (!mbar_wait(&tempty[grp], (uint32_t)(c - 1) & 1u, lim)) {
                   atomicExch(a.err, 22);
                   abort_flag = 1;
                   ok = false;
@@ -265,6 +268,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
         if (ok) mma_commit(tfull);
       }
+      // every MMA issued here (also after an abort) completes before the
+      // tensor memory is freed
+      mma_commit(drain);
+      mbar_wait(drain, 0u);
     }
     __syncwarp();
   } else {
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     for (int j = 0; j < OZ_EPI_COLS; ++j) acc[j] = 0;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
-      bool have = mbar_wait(tfull, (uint32_t)c & 1u);
+      bool have = mbar_wait(tfull, (uint32_t)c & 1u, lim);
       // tcgen05.ld is warp-collective: one decision per warp
       have = __all_sync(0xffffffffu, have && !*(volatile int *)&abort_flag);
       if (!have) {
@@ -680,7 +687,7 @@ cudaError_t oz_setup(cudaStream_t st, const DevSystem &sys, OzWork &oz, int slot
   if (r == cudaSuccess) r = alloc((size_t)rowsT * s * std::max(Kp1, Kp2) * bf, &qT);
   const int64_t ne = (int64_t)np + nv + no + rowsZ + 2 * rowsT;
   if (r == cudaSuccess) r = alloc((size_t)ne * sizeof(int), &e);
-  if (r == cudaSuccess) r = alloc(sizeof(int), (void **)&oz.err);
+  if (r == cudaSuccess) r = alloc(ptx::kErrInts * sizeof(int), (void **)&oz.err);
   if (r != cudaSuccess) return r;
   int *ep = (int *)e;
   auto bq = [](void *p) { return (__nv_bfloat16 *)p; };
@@ -696,7 +703,7 @@ cudaError_t oz_setup(cudaStream_t st, const DevSystem &sys, OzWork &oz, int slot
   ep += rowsT;
   if (r == cudaSuccess) r = oz_operand(oz.Bt2, bq(qT), ep, rowsT, nv, s, OZ_BN);
   if (r == cudaSuccess) r = oz_init_attributes();
-  if (r == cudaSuccess) r = cudaMemsetAsync(oz.err, 0, sizeof(int), st);
+  if (r == cudaSuccess) r = cudaMemsetAsync(oz.err, 0, ptx::kErrInts * sizeof(int), st);
   if (r == cudaSuccess) r = launch_oz_slice_rows(st, sys.K, np, np, np, oz.K);
   if (r == cudaSuccess) r = launch_oz_slice_rows(st, sys.XvT, no, nv, no, oz.XvT);
   if (r == cudaSuccess) r = launch_oz_slice_rows(st, sys.Xv, nv, no, nv, oz.Xv);
@@ -729,11 +736,11 @@ extern "C" tddft_status tddft_gemm_f64_emulated(int32_t M, int32_t N, int32_t K,
   if (e == cudaSuccess) e = alloc((size_t)N * slices * Kp * sizeof(__nv_bfloat16), &qb);
   if (e == cudaSuccess) e = alloc((size_t)M * sizeof(int), &ea);
   if (e == cudaSuccess) e = alloc((size_t)N * sizeof(int), &eb);
-  if (e == cudaSuccess) e = alloc(sizeof(int), &err);
+  if (e == cudaSuccess) e = alloc(ptx::kErrInts * sizeof(int), &err);
   OzOperand oa, ob;
   if (e == cudaSuccess) e = oz_operand(oa, (__nv_bfloat16 *)qa, (int *)ea, M, K, slices, OZ_BM);
   if (e == cudaSuccess) e = oz_operand(ob, (__nv_bfloat16 *)qb, (int *)eb, N, K, slices, OZ_BN);
-  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, ptx::kErrInts * sizeof(int), st);
   if (e == cudaSuccess) e = launch_oz_slice_rows(st, A, lda, M, K, oa);
   if (e == cudaSuccess) e = launch_oz_slice_cols(st, B, ldb, K, N, ob);
   if (e == cudaSuccess) e = launch_gemm_oz(st, oa, ob, M, N, C, ldc, 0, (int *)err);

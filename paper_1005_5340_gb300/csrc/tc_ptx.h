@@ -11,6 +11,12 @@ namespace ptx {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;      // 2 s
 
+// Device error buffer of the tensor-core kernels: int[4] = {error code,
+// reserved, wait limit in ns (64-bit, low word first)}; a zero limit means
+// kWaitLimitNs.  The limit bounds the waits of the pipeline roles; the
+// drains after an abort (copies and MMAs in flight) always use kWaitLimitNs.
+constexpr int kErrInts = 4;
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -38,14 +44,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false once kWaitLimitNs has passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait: false once limit_ns has passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return true;
+}
+__device__ __forceinline__ uint64_t wait_limit(const int *err) {
+  const unsigned long long v = *(const volatile unsigned long long *)(err + 2);
+  return v ? (uint64_t)v : kWaitLimitNs;
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
                                             int c1) {
@@ -69,6 +80,28 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+// kind::tf32 instruction descriptor: D f32, A and B tf32 (format code 2),
+// both K-major.  A 128-byte swizzle row holds 32 tf32 values; an MMA takes
+// K = 8 (32 bytes), so the shared-memory descriptors advance as for bf16.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+// x rounded to tf32 (10 explicit mantissa bits, to nearest, ties away), as a
+// float whose 13 low mantissa bits are zero
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return __uint_as_float(y);
 }
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
                                          uint32_t accum) {

@@ -31,6 +31,7 @@ struct tddft_ctx {
   double *Z3 = nullptr;     // [6][n_prod] the three dipole vectors (planar)
   double *a3 = nullptr;     // [n_virt][6][n_occ] X_virt^T beta(d_k)
   int *h_count = nullptr;   // pinned
+  tddft_mlp *guess_net = nullptr;   // network of the learned guess (tddft_guess_load)
   std::vector<void *> dev_allocs;
   std::string err;
 };
@@ -75,6 +76,8 @@ bool all_finite(const double *p, size_t n) {
 }
 
 void release(tddft_ctx *c) {
+  if (c->guess_net) tddft_mlp_destroy(c->guess_net);
+  c->guess_net = nullptr;
   c->timer.destroy();
   if (c->gst) cudaStreamDestroy(c->gst);
   c->gst = nullptr;
@@ -104,7 +107,7 @@ const char *kernel_class_name(int k) {
       "lp_split_z", "gmres_step",
       "gmres_gather", "gmres_select", "rhs_formation", "misc", "emu_slice", "emu_gemm_K",
       "emu_gemm_T1", "emu_gemm_T2", "alpha_gather", "tc_alpha_beta", "tc_alpha_dot",
-      "emu_alpha_beta", "emu_alpha_dot"};
+      "emu_alpha_beta", "emu_alpha_dot", "lp_dterm", "alpha_combine"};
   return (k >= 0 && k < kcCount) ? names[k] : "?";
 }
 
@@ -248,6 +251,20 @@ tddft_status validate_system(const tddft_system *s, std::string &msg, tddft_stat
   code = TDDFT_OK;
   return TDDFT_OK;
 }
+int ptx_err_ints() { return 4; }   // the tensor-core kernels' error buffer (tc_ptx.h)
+
+// The wait limit of the context's tensor-core kernels, in their error
+// buffers (int[4]: code, reserved, 64-bit limit in ns; 0 = 2 s).
+cudaError_t set_wait_limit(tddft_ctx *c, int64_t ns) {
+  const unsigned long long v = (unsigned long long)ns;
+  cudaError_t e = cudaSuccess;
+  for (int *flag : {c->lowprec ? c->lp.err : nullptr, c->emu ? c->oz.err : nullptr}) {
+    if (!flag || e != cudaSuccess) continue;
+    e = cudaMemcpyAsync(flag + 2, &v, sizeof(v), cudaMemcpyHostToDevice, c->st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  return e;
+}
 }  // namespace
 
 extern "C" {
@@ -257,14 +274,23 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   if (!out) return fail(nullptr, TDDFT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!o) return fail(nullptr, TDDFT_ERR_INVALID_ARG, "options are NULL");
-  if (o->prec < TDDFT_PREC_FP64 || o->prec > TDDFT_PREC_BF16X3_IR_EMU)
+  if (o->prec < TDDFT_PREC_FP64 || o->prec > TDDFT_PREC_TF32_IR_EMU)
     return fail(nullptr, TDDFT_ERR_UNSUPPORTED, "unknown precision");
-  const bool refine = o->prec == TDDFT_PREC_BF16X3_IR || o->prec == TDDFT_PREC_BF16X3_IR_EMU;
+  if (o->n_tile != 0 && o->n_tile != 64 && o->n_tile != 128 && o->n_tile != 256)
+    return fail(nullptr, TDDFT_ERR_INVALID_ARG, "n_tile must be 0, 64, 128 or 256");
+  if (o->guess < TDDFT_GUESS_ZERO || o->guess > TDDFT_GUESS_LEARNED)
+    return fail(nullptr, TDDFT_ERR_INVALID_ARG, "unknown initial guess");
+  if (o->wait_timeout_ns < 0)
+    return fail(nullptr, TDDFT_ERR_INVALID_ARG, "wait_timeout_ns must be >= 0");
+  const bool tf32 = o->prec == TDDFT_PREC_TF32_IR || o->prec == TDDFT_PREC_TF32_IR_EMU;
+  const bool refine = o->prec == TDDFT_PREC_BF16X3_IR || o->prec == TDDFT_PREC_BF16X3_IR_EMU || tf32;
   if (refine && !(o->inner_tol > 0.0 && o->inner_tol < 1.0))
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
   if (o->restart < 1 || o->restart > 256 || o->max_restarts < 1 || !(o->tol > 0.0) ||
       !std::isfinite(o->tol) || o->batch < 1)
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "bad options (restart 1..256, max_restarts >= 1, tol > 0, batch >= 1)");
+  if (o->graph < 0 || o->graph > 2)
+    return fail(nullptr, TDDFT_ERR_INVALID_ARG, "graph must be 0, 1 or 2");
   if (o->stop < TDDFT_STOP_RESIDUAL || o->stop > TDDFT_STOP_EPS_PX)
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "unknown stopping rule");
   if (o->emu_slices != 0 && (o->emu_slices < kOzMinSlices || o->emu_slices > kOzMaxSlices))
@@ -426,7 +452,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     AL(g.V, S * (m + 1) * 2 * np);
   }
   AL(g.x, S * 2 * np); AL(g.b, S * 2 * np);
-  AL(g.act, S); AL(g.act2, S); AL(g.count, 2); AL(g.rho0, S); AL(g.bytes, 1);
+  AL(g.act, S); AL(g.act2, S); AL(g.count, 2); AL(g.rho0, S); AL(g.bytes, 1); AL(g.loopctl, 2);
   g.stop = o->stop;
   if (g.stop) {
     AL(g.dir, S); AL(g.crit, S * 10); AL(g.cvec, S * (3 * m + 2));
@@ -439,11 +465,12 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
   c->timer.dev_bytes_cls = kcGmresStep;
   g.inner_tol = 0.0;
   c->lowprec = refine;
-  c->emu = o->prec == TDDFT_PREC_FP64_EMU || o->prec == TDDFT_PREC_BF16X3_IR_EMU;
+  c->emu = o->prec == TDDFT_PREC_FP64_EMU || o->prec == TDDFT_PREC_BF16X3_IR_EMU ||
+           o->prec == TDDFT_PREC_TF32_IR_EMU;
   // the refinement form's float64 products need only resolve residuals well
   // below its tolerance: 5 slices (2^-35 of the operand scales) down to 1e-8,
   // 6 (2^-42) down to 1e-12, 7 below; 6 for the emulated float64 form
-  if (o->prec == TDDFT_PREC_BF16X3_IR_EMU)
+  if (o->prec == TDDFT_PREC_BF16X3_IR_EMU || o->prec == TDDFT_PREC_TF32_IR_EMU)
     c->oz.s = o->tol >= 1e-8 ? 5 : (o->tol >= 1e-12 ? 6 : 7);
   else
     c->oz.s = kOzDefaultSlices;
@@ -457,12 +484,14 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     if (e == cudaSuccess)
       e = cudaMemset(w.beta, 0, (size_t)no * 2 * S3 * nocc * sizeof(double));
   }
+  c->ar.tf32 = tf32;
   if (e == cudaSuccess && (c->emu || refine))
     e = alpha_setup(c->st, s, d, c->ar, (int)S, refine, c->emu, c->oz.s, c->dev_allocs);
   if (c->lowprec) {
     g.inner_tol = o->inner_tol;
     LpWork &L = c->lp;
     L.slots = (int)S;
+    L.tf32 = tf32;
     L.KpK = round_up(np, 64);
     L.Kp1 = round_up(no, 64);
     L.Kp2 = round_up(nv, 64);
@@ -477,21 +506,28 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     AL(L.betaT, rows1 * 2 * L.Kp1);
     AL(L.aT, rows1 * 2 * L.Kp2);
     AL(L.omega, S);
-    AL(L.err, 1);
+    AL(L.err, ptx_err_ints());
     AL(L.eocc2, (size_t)nocc);
     AL(L.dterm, S * (size_t)nv);
-    if (e == cudaSuccess) e = make_operand_map(L.opK, L.Ks, np, L.KpK, 128);
-    if (e == cudaSuccess) e = make_operand_map(L.opXvT, L.XvTs, nv, L.Kp1, 128);
-    if (e == cudaSuccess) e = make_operand_map(L.opXv, L.Xvs, no, L.Kp2, 128);
-    if (e == cudaSuccess) e = make_operand_map(L.opZ, L.Zb, 2 * (int64_t)S, L.KpK, 128);
-    if (e == cudaSuccess) e = make_operand_map(L.opBeta, L.betaT, (int64_t)rows1, L.Kp1, 128);
-    if (e == cudaSuccess) e = make_operand_map(L.opA, L.aT, (int64_t)rows1, L.Kp2, 128);
+    if (e == cudaSuccess) e = make_operand_map(L.opK, L.Ks, np, L.KpK, 128, tf32);
+    if (e == cudaSuccess) e = make_operand_map(L.opXvT, L.XvTs, nv, L.Kp1, 128, tf32);
+    if (e == cudaSuccess) e = make_operand_map(L.opXv, L.Xvs, no, L.Kp2, 128, tf32);
+    if (e == cudaSuccess) e = make_operand_map(L.opZ, L.Zb, 2 * (int64_t)S, L.KpK, 128, tf32);
+    if (e == cudaSuccess) e = make_operand_map(L.opBeta, L.betaT, (int64_t)rows1, L.Kp1, 128, tf32);
+    if (e == cudaSuccess) e = make_operand_map(L.opA, L.aT, (int64_t)rows1, L.Kp2, 128, tf32);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(L.err, 0, ptx_err_ints() * sizeof(int), c->st);
     if (e == cudaSuccess) e = lp_prepare_constants(c->st, d, L);
     if (e == cudaSuccess) tc_init_attributes();
-    if (e == cudaSuccess) e = lp_autotune(c->st, d, L);
+    if (o->n_tile) {
+      L.bnK = L.bn1 = L.bn2 = o->n_tile;
+    } else if (e == cudaSuccess) {
+      e = lp_autotune(c->st, d, L);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   }
 #undef AL
+  if (e == cudaSuccess) e = set_wait_limit(c, o->wait_timeout_ns);
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_count, 2 * sizeof(int));
   if (e == cudaSuccess && o->graph) e = cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking);
   if (e == cudaSuccess) tc_init_attributes();
@@ -514,6 +550,28 @@ void tddft_destroy(tddft_ctx *c) {
 
 const char *tddft_last_error(const tddft_ctx *c) {
   return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+tddft_status tddft_set_wait_timeout(tddft_ctx *c, int64_t ns) {
+  if (!c) return TDDFT_ERR_INVALID_ARG;
+  c->err.clear();
+  if (ns < 0) return fail(c, TDDFT_ERR_INVALID_ARG, "wait_timeout_ns must be >= 0");
+  CUDA_TRY(c, set_wait_limit(c, ns));
+  c->opts.wait_timeout_ns = ns;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_kproduct_plan(const tddft_ctx *c, int32_t n_rhs, int32_t *ncl,
+                                 int32_t *ksplit) {
+  if (!c || !ncl || !ksplit || n_rhs < 1) return TDDFT_ERR_INVALID_ARG;
+  *ncl = 1;
+  *ksplit = 1;
+  if (!c->lowprec) return TDDFT_OK;
+  int ks = 1, nc = 1;
+  tc_split_plan(c->lp.KpK, c->sys.n_prod, 2 * n_rhs, c->lp.bnK, &ks, &nc);
+  *ncl = nc;
+  *ksplit = ks;
+  return TDDFT_OK;
 }
 
 tddft_status tddft_tuning(const tddft_ctx *c, int32_t *n_tiles) {
@@ -611,9 +669,27 @@ static tddft_status polarizability_impl(tddft_ctx *c, int32_t n_omega, const dou
                                         double eps, const double *x0, double *Xout, double *P,
                                         tddft_solve_stats *stats, int32_t flags);
 
+// Without explicit guesses, a context whose guess mode is not zero runs the
+// warm-started frequency sweep (sweep.cu), which calls polarizability_impl
+// per chunk with the guesses it forms.
+static tddft_status polarizability_entry(tddft_ctx *c, int32_t n_omega, const double *omega,
+                                         double eps, const double *x0, double *X, double *P,
+                                         tddft_solve_stats *stats, int32_t flags) {
+  if (!c) return TDDFT_ERR_INVALID_ARG;
+  c->err.clear();
+  if (n_omega < 1) return fail(c, TDDFT_ERR_SHAPE, "n_omega must be >= 1");
+  if (!P) return fail(c, TDDFT_ERR_INVALID_ARG, "P is NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, TDDFT_ERR_INVALID_ARG, "eps must be > 0");
+  tddft_status s0 = check_omega(c, n_omega, omega, (flags & TDDFT_DEVICE_PTRS) != 0);
+  if (s0 != TDDFT_OK) return s0;
+  if (!x0 && c->opts.guess != TDDFT_GUESS_ZERO)
+    return sweep_polarizability(c, n_omega, omega, eps, X, P, stats, flags);
+  return polarizability_impl(c, n_omega, omega, eps, x0, X, P, stats, flags);
+}
+
 tddft_status tddft_polarizability(tddft_ctx *c, int32_t n_omega, const double *omega, double eps,
                                   double *P, tddft_solve_stats *stats, int32_t flags) {
-  return polarizability_impl(c, n_omega, omega, eps, nullptr, nullptr, P, stats, flags);
+  return polarizability_entry(c, n_omega, omega, eps, nullptr, nullptr, P, stats, flags);
 }
 
 tddft_status tddft_polarizability_guess(tddft_ctx *c, int32_t n_omega, const double *omega,
@@ -621,7 +697,16 @@ tddft_status tddft_polarizability_guess(tddft_ctx *c, int32_t n_omega, const dou
                                         tddft_solve_stats *stats, int32_t flags) {
   if (c && !(flags & TDDFT_DEVICE_PTRS) && (x0 || X))
     return fail(c, TDDFT_ERR_INVALID_ARG, "x0 and X must be device pointers (flags bit 0)");
-  return polarizability_impl(c, n_omega, omega, eps, x0, X, P, stats, flags);
+  return polarizability_entry(c, n_omega, omega, eps, x0, X, P, stats, flags);
+}
+
+tddft_status tddft_set_guess(tddft_ctx *c, int32_t guess) {
+  if (!c) return TDDFT_ERR_INVALID_ARG;
+  c->err.clear();
+  if (guess < TDDFT_GUESS_ZERO || guess > TDDFT_GUESS_LEARNED)
+    return fail(c, TDDFT_ERR_INVALID_ARG, "unknown initial guess");
+  c->opts.guess = guess;
+  return TDDFT_OK;
 }
 
 // One GMRES iteration of a group of n right-hand sides, captured once in a
@@ -629,10 +714,30 @@ tddft_status tddft_polarizability_guess(tddft_ctx *c, int32_t n_omega, const dou
 // n live right-hand sides and every kernel reads the live counts on the
 // device, so no host decision is needed between iterations.  The host reads
 // the counts back every kReplays launches.
+// Loop control of the device-driven GMRES loop (one WHILE node per group):
+// right after the selection of each iteration, keep the node repeating while
+// some right-hand side is live and the iteration bound holds; ctl[0] counts
+// the iterations, ctl[1] = 1 records that the bound stopped the loop.
+__global__ void loop_control_kernel(cudaGraphConditionalHandle h, const int *__restrict__ count,
+                                    int *__restrict__ ctl, int max_iter) {
+  const bool live = count[0] > 0 || count[1] > 0;
+  const int it = ++ctl[0];
+  bool go = live;
+  if (live && it > max_iter) {
+    ctl[1] = 1;
+    go = false;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // Enqueue one device-driven GMRES iteration of context c's current group of
 // n right-hand sides on stream gs (no host decision, no synchronisation).
+// With loop: the body of a WHILE node, whose condition the control kernel
+// sets after the selection (the rest of the iteration then finds no live
+// right-hand side and does no work).
 static cudaError_t enqueue_iteration(tddft_ctx *c, cudaStream_t gs, int n, double eps, int split,
-                                     int min_b) {
+                                     int min_b, const cudaGraphConditionalHandle *loop = nullptr,
+                                     int max_iter = 0) {
   GmresState &g = c->gs;
   OpWork wk = c->wk;
   LpWork lp = c->lp;
@@ -641,6 +746,10 @@ static cudaError_t enqueue_iteration(tddft_ctx *c, cudaStream_t gs, int n, doubl
   wk.dcnt = g.count + (split ? 1 : 0);
   lp.dcnt = g.count;
   cudaError_t e = launch_gmres_select(gs, g, n, split, min_b);
+  if (e == cudaSuccess && loop) {
+    loop_control_kernel<<<1, 1, 0, gs>>>(*loop, g.count, g.loopctl, max_iter);
+    e = cudaGetLastError();
+  }
   if (split) {
     if (e == cudaSuccess) e = launch_gmres_gather(gs, c->sys, g, g.act, n, c->Zc, lp.omega, g.count);
     if (e == cudaSuccess) e = launch_apply_operator_lp(gs, c->sys, lp, n, kA, eps, c->Zc, c->Wout);
@@ -662,6 +771,58 @@ static cudaError_t enqueue_iteration(tddft_ctx *c, cudaStream_t gs, int n, doubl
 // costs are shared.
 static int residual_batch(int split, int n) {
   return split ? std::max(1, std::min(64, n / 3)) : 1;
+}
+
+// Add to graph `parent` a WHILE node (no dependencies) whose body, captured
+// on stream cs, is one device-driven GMRES iteration of context c's group.
+static cudaError_t add_device_loop(tddft_ctx *c, cudaGraph_t parent, cudaStream_t cs, int n,
+                                   double eps, int split, int min_b, int max_iter) {
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, parent, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, parent, nullptr, nullptr, 0, &p);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t e1 = enqueue_iteration(c, cs, n, eps, split, min_b, &h, max_iter);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+  return e1 != cudaSuccess ? e1 : e2;
+}
+
+// The whole GMRES loop of a group as one graph launch: a WHILE node repeats
+// the iteration on the device until no right-hand side is live (or the
+// iteration bound is hit: TIMEOUT); the host waits once, at the end.
+static tddft_status run_group_device_loop(tddft_ctx *c, int n, double eps, int split, int min_b,
+                                          long max_iter) {
+  GmresState &g = c->gs;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct Cleanup {
+    cudaGraph_t &g; cudaGraphExec_t &e;
+    ~Cleanup() { if (e) cudaGraphExecDestroy(e); if (g) cudaGraphDestroy(g); }
+  } cleanup{graph, exec};
+  CUDA_TRY(c, cudaGraphCreate(&graph, 0));
+  cudaError_t e = add_device_loop(c, graph, c->gst, n, eps, split, min_b, (int)max_iter);
+  if (e != cudaSuccess)
+    return fail(c, TDDFT_ERR_CUDA, std::string("device loop capture failed: ") +
+                                       cudaGetErrorString(e));
+  CUDA_TRY(c, cudaGraphInstantiate(&exec, graph, 0));
+  CUDA_TRY(c, cudaMemsetAsync(g.loopctl, 0, 2 * sizeof(int), c->st));
+  CUDA_TRY(c, cudaGraphLaunch(exec, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_count, g.loopctl, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                              c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  if (c->h_count[1]) return fail(c, TDDFT_ERR_TIMEOUT, "GMRES driver exceeded its iteration bound");
+  return TDDFT_OK;
 }
 
 static tddft_status run_group_graph(tddft_ctx *c, int n, double eps, int split, int min_b,
@@ -743,7 +904,10 @@ static tddft_status polarizability_impl(tddft_ctx *c, int32_t n_omega, const dou
     // precision Arnoldi work remains, right-hand sides awaiting their residual
     // wait until enough of them have gathered to fill the float64 GEMM tiles.
     const int min_b = residual_batch(split, n);
-    if (c->opts.graph && !c->timer.on) {
+    if (c->opts.graph == 2 && !c->timer.on) {
+      tddft_status gs_ = run_group_device_loop(c, n, eps, split, min_b, max_iter);
+      if (gs_ != TDDFT_OK) return gs_;
+    } else if (c->opts.graph == 1 && !c->timer.on) {
       tddft_status gs_ = run_group_graph(c, n, eps, split, min_b, max_iter);
       if (gs_ != TDDFT_OK) return gs_;
     } else {
@@ -862,6 +1026,18 @@ namespace tddft {
 const DevSystem *ctx_system(const tddft_ctx *c) { return &c->sys; }
 cudaStream_t ctx_stream(const tddft_ctx *c) { return c->st; }
 void ctx_set_error(tddft_ctx *c, const char *msg) { c->err = msg; }
+int ctx_slots(const tddft_ctx *c) { return c->wk.slots; }
+int ctx_guess_mode(const tddft_ctx *c) { return c->opts.guess; }
+tddft_mlp *ctx_guess_net(const tddft_ctx *c) { return c->guess_net; }
+void ctx_set_guess_net(tddft_ctx *c, tddft_mlp *net) {
+  if (c->guess_net) tddft_mlp_destroy(c->guess_net);
+  c->guess_net = net;
+}
+tddft_status ctx_polarizability_groups(tddft_ctx *c, int32_t n_omega, const double *omega,
+                                       double eps, const double *x0, double *X, double *P,
+                                       tddft_solve_stats *stats, int32_t flags) {
+  return polarizability_impl(c, n_omega, omega, eps, x0, X, P, stats, flags);
+}
 const float *ctx_product_features(const tddft_ctx *c) { return c->sys.pfeat; }
 }  // namespace tddft
 
@@ -971,7 +1147,6 @@ tddft_status tddft_batch_polarizability(tddft_batch *b, int32_t n_omega, const d
     return bfail(b, TDDFT_ERR_INVALID_ARG, "omega holds NaN or Inf");
   const int nm = (int)b->ctx.size();
   const int total = 3 * n_omega;
-  constexpr int kReplays = 4;
   std::vector<double *> d_omega(nm, nullptr);
   std::vector<double2 *> d_P(nm, nullptr);
   struct Free {
@@ -1018,39 +1193,39 @@ tddft_status tddft_batch_polarizability(tddft_batch *b, int32_t n_omega, const d
       BCUDA(b, cudaEventRecord(ev[i], c->st));
       BCUDA(b, cudaStreamWaitEvent(b->main, ev[i], 0));
     }
-    // one graph per round: a branch per molecule, each one GMRES iteration
+    // one graph launch per round: a WHILE node per molecule (independent
+    // nodes, so the molecules' iterations run side by side), each repeating
+    // that molecule's GMRES iteration on the device until its group is done
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     struct GFree {
       cudaGraph_t &g; cudaGraphExec_t &e;
       ~GFree() { if (e) cudaGraphExecDestroy(e); if (g) cudaGraphDestroy(g); }
     } gfr{graph, exec};
-    BCUDA(b, cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaEventRecord(ev[nm], b->main);
-    for (size_t a = 0; a < act.size() && ce == cudaSuccess; ++a) {
+    BCUDA(b, cudaStreamSynchronize(b->main));
+    BCUDA(b, cudaGraphCreate(&graph, 0));
+    for (size_t a = 0; a < act.size(); ++a) {
       tddft_ctx *c = b->ctx[act[a]];
-      ce = cudaStreamWaitEvent(c->st, ev[nm], 0);
-      if (ce == cudaSuccess) ce = enqueue_iteration(c, c->st, nv[a], eps, splitv[a], minbv[a]);
-      if (ce == cudaSuccess) ce = cudaEventRecord(ev[act[a]], c->st);
-      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->main, ev[act[a]], 0);
+      const GmresState &g = c->gs;
+      const long bound = (long)(g.max_restarts + 1) * (g.m + 1) + 4;
+      const cudaError_t ce = add_device_loop(c, graph, b->main, nv[a], eps, splitv[a], minbv[a],
+                                             (int)std::min(bound, max_iter));
+      if (ce != cudaSuccess)
+        return bfail(b, TDDFT_ERR_CUDA, std::string("graph capture failed: ") +
+                                            cudaGetErrorString(ce));
     }
-    cudaError_t ce2 = cudaStreamEndCapture(b->main, &graph);
-    if (ce != cudaSuccess || ce2 != cudaSuccess)
-      return bfail(b, TDDFT_ERR_CUDA, std::string("graph capture failed: ") +
-                                          cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
     BCUDA(b, cudaGraphInstantiate(&exec, graph, 0));
-    for (long it = 0;; it += kReplays) {
-      if (it > max_iter) return bfail(b, TDDFT_ERR_TIMEOUT, "batch driver exceeded its bound");
-      for (int k = 0; k < kReplays; ++k) BCUDA(b, cudaGraphLaunch(exec, b->main));
-      for (size_t a = 0; a < act.size(); ++a)
-        BCUDA(b, cudaMemcpyAsync(b->h_counts + 2 * a, b->ctx[act[a]]->gs.count, 2 * sizeof(int),
-                                 cudaMemcpyDeviceToHost, b->main));
-      BCUDA(b, cudaStreamSynchronize(b->main));
-      bool live = false;
-      for (size_t a = 0; a < act.size(); ++a)
-        live = live || b->h_counts[2 * a] > 0 || b->h_counts[2 * a + 1] > 0;
-      if (!live) break;
-    }
+    for (size_t a = 0; a < act.size(); ++a)
+      BCUDA(b, cudaMemsetAsync(b->ctx[act[a]]->gs.loopctl, 0, 2 * sizeof(int), b->main));
+    BCUDA(b, cudaGraphLaunch(exec, b->main));
+    for (size_t a = 0; a < act.size(); ++a)
+      BCUDA(b, cudaMemcpyAsync(b->h_counts + 2 * a, b->ctx[act[a]]->gs.loopctl, 2 * sizeof(int),
+                               cudaMemcpyDeviceToHost, b->main));
+    BCUDA(b, cudaStreamSynchronize(b->main));
+    for (size_t a = 0; a < act.size(); ++a)
+      if (b->h_counts[2 * a + 1])
+        return bfail(b, TDDFT_ERR_TIMEOUT, "molecule " + std::to_string(act[a]) +
+                                               ": GMRES driver exceeded its iteration bound");
     // results of the round
     for (size_t a = 0; a < act.size(); ++a) {
       const int i = act[a];

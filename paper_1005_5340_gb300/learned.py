@@ -1,21 +1,17 @@
-"""Frequency sweep with a learned initial guess (host-side driver).
+"""Learned initial guess: training of the guess network (host-side driver).
 
-The spectrum is solved in three passes over the uniform grid:
-  pass 0: every 4th frequency and the last one, from a zero guess;
-  pass 1: the remaining frequencies with index = 2 mod 4, each from its two
-          solved neighbours at distance 2;
-  pass 2: the rest (odd indices), from their neighbours at distance 1.
-In passes 1 and 2 the guess is the linear interpolation of the neighbours'
-solutions (mode "interp") or that interpolation corrected per product by the
-network of tddft_mlp_* (mode "learned"); mode "zero" solves every pass from
-zero.  Each guess first costs one float64 product and is dropped in favour
-of zero when it is worse (tddft_polarizability_guess), so converged results
-meet the same float64 residual tolerance in every mode.
-
-Everything runs in the library's kernels; this module only orders the
-frequencies, gathers the neighbour indices and drives training.
+The warm-started frequency sweep itself (three passes over the grid, guesses
+from the two nearest solved neighbours, interpolated or corrected by the
+network, each arbitrated against the zero guess) runs inside the library:
+tddft_polarizability with a context whose guess mode is "interp" or
+"learned" (tddft_set_guess, tddft_guess_load).  This module gathers training
+targets from solved spectra (the sweep's pass plan comes from
+tddft_sweep_plan) and drives the library's training kernels.
 """
 from __future__ import annotations
+
+import os
+import tempfile
 
 import numpy as np
 
@@ -23,18 +19,15 @@ from . import synth
 
 
 def sweep_passes(n_omega: int):
-    """(indices, left neighbour, right neighbour) per pass; pass 0 has none."""
-    p0 = sorted(set(range(0, n_omega, 4)) | {n_omega - 1})
-    solved = set(p0)
-    passes = [(np.array(p0), None, None)]
-    for cond in (lambda i: i % 4 == 2, lambda i: True):
-        idx = [i for i in range(n_omega) if i not in solved and cond(i)]
-        srt = sorted(solved)
-        left = [max(j for j in srt if j < i) for i in idx]
-        right = [min(j for j in srt if j > i) for i in idx]
-        passes.append((np.array(idx, dtype=int), np.array(left), np.array(right)))
-        solved |= set(idx)
-    return passes
+    """(indices, left neighbour, right neighbour) per pass of the library's
+    sweep (tddft_sweep_plan); pass 0 has no neighbours."""
+    from .tddft import sweep_plan
+    pas, left, right = sweep_plan(n_omega)
+    out = []
+    for p in range(3):
+        idx = np.flatnonzero(pas == p)
+        out.append((idx, None, None) if p == 0 else (idx, left[idx], right[idx]))
+    return out
 
 
 def _targets(omega, idx, left, right):
@@ -48,38 +41,24 @@ def _targets(omega, idx, left, right):
     return nb, t, omega[ii], k.astype(np.int32), omega[rr] - omega[ll]
 
 
-def solve_sweep(ctx, omega, eps, mode="zero", mlp=None, bf16=True):
-    """Solve the spectrum pass by pass.  Returns (P [n,3,3] complex numpy,
-    stats dict with per-(omega, dir) matvecs/cycles/resid/converged/
-    guess_rejected, X [3n, n_prod] complex CUDA tensor)."""
-    import torch
-    omega = np.asarray(omega, dtype=float)
-    n = omega.size
-    dev = torch.device("cuda", torch.cuda.current_device())
-    X = torch.zeros((3 * n, ctx.n_prod), dtype=torch.complex128, device=dev)
-    P = np.zeros((n, 3, 3), dtype=complex)
-    stats = {k: np.zeros((n, 3), dtype=dt) for k, dt in
-             (("matvecs", int), ("cycles", int), ("resid", float), ("converged", bool),
-              ("guess_rejected", bool))}
-    for pi, (idx, left, right) in enumerate(sweep_passes(n)):
-        if idx.size == 0:
-            continue
-        x0 = None
-        if pi > 0 and mode != "zero":
-            nb, t, om_t, k, h = _targets(omega, idx, left, right)
-            F, lin, scale = ctx.guess_features(nb, t, om_t, k, float(np.mean(h)) / eps, X)
-            if mode == "learned":
-                Y = mlp.forward(F, bf16=bf16)
-                x0 = mlp.combine(Y, lin, scale)
-            else:
-                x0 = lin
-        Pp, Xp, st = ctx.polarizability_guess(omega[idx], eps, x0)
-        rows = (np.repeat(idx, 3) * 3 + np.tile(np.arange(3), idx.size))
-        X[torch.as_tensor(rows, device=dev)] = Xp
-        P[idx] = Pp.cpu().numpy()
-        for key in stats:
-            stats[key][idx] = st[key]
-    return P, stats, X
+def solve_sweep(ctx, omega, eps, mode="zero", mlp=None):
+    """The library's sweep on ctx in the given mode ("zero", "interp" or
+    "learned"; mlp is loaded into the context for "learned").  Returns
+    (P [n,3,3] complex numpy, stats dict, X [3n, n_prod] complex CUDA tensor)."""
+    if mode == "learned":
+        fd, path = tempfile.mkstemp(suffix=".net")
+        os.close(fd)
+        try:
+            mlp.save(path)
+            ctx.guess_load(path)
+        finally:
+            os.remove(path)
+    ctx.set_guess(mode)
+    try:
+        P, X, st = ctx.polarizability_guess(np.asarray(omega, dtype=float), eps)
+    finally:
+        ctx.set_guess("zero")
+    return P.cpu().numpy(), st, X
 
 
 def training_targets(ctx, omega, eps, X):

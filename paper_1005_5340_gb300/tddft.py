@@ -20,7 +20,9 @@ OK, ERR_INVALID_ARG, ERR_SHAPE, ERR_NOMEM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIME
 STATUS_NAMES = ["OK", "INVALID_ARG", "SHAPE", "NOMEM", "CUDA", "NOT_CONVERGED", "TIMEOUT",
                 "UNSUPPORTED"]
 DEVICE_PTRS = 1
-PREC = {"fp64": 0, "fp64emu": 1, "bf16x3": 2, "bf16x3emu": 3}
+PREC = {"fp64": 0, "fp64emu": 1, "bf16x3": 2, "bf16x3emu": 3, "tf32": 4, "tf32emu": 5}
+# initial guesses of tddft_polarizability
+GUESS = {"zero": 0, "interp": 1, "learned": 2}
 # GMRES stopping rules (Sec. 4.1): relative residual, eps_P, eps_P and eps_X
 STOP = {"residual": 0, "eps_p": 1, "eps_px": 2}
 
@@ -45,7 +47,9 @@ class _Options(ctypes.Structure):
                 ("max_restarts", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("batch", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("inner_tol", ctypes.c_double), ("graph", ctypes.c_int32),
-                ("stop", ctypes.c_int32), ("emu_slices", ctypes.c_int32)]
+                ("stop", ctypes.c_int32), ("emu_slices", ctypes.c_int32),
+                ("n_tile", ctypes.c_int32), ("guess", ctypes.c_int32),
+                ("wait_timeout_ns", ctypes.c_int64)]
 
 
 class SolveStats(ctypes.Structure):
@@ -88,6 +92,8 @@ SIGNATURES = {
                                                ctypes.c_double, _P, _P, _P, _P, _P,
                                                ctypes.c_int32, _P]),
     "tddft_tuning": (ctypes.c_int, [_P, _P]),
+    "tddft_set_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "tddft_kproduct_plan": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "tddft_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "tddft_batch_polarizability": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P]),
     "tddft_batch_context": (ctypes.c_void_p, [_P, ctypes.c_int32]),
@@ -109,6 +115,9 @@ SIGNATURES = {
     "tddft_guess_features": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
                                             _P, _P, _P, _P]),
     "tddft_guess_combine": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P, _P]),
+    "tddft_sweep_plan": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P]),
+    "tddft_set_guess": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "tddft_guess_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "tddft_timing_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "tddft_timing_count": (ctypes.c_int32, [_P]),
     "tddft_timing_get": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
@@ -116,6 +125,8 @@ SIGNATURES = {
     "tddft_timing_bytes": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "tddft_selftest_gemm": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "tddft_selftest_gemm_tf32": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "tddft_gemm_f64_emulated": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                _P, ctypes.c_int64, _P, ctypes.c_int64, _P,
                                                ctypes.c_int64, ctypes.c_int32, _P]),
@@ -172,7 +183,8 @@ class Context:
 
     def __init__(self, system, *, restart: int = 40, max_restarts: int = 200, tol: float = 1e-6,
                  batch: int = 64, prec: str = "fp64", inner_tol: float = 1e-4, stream=None,
-                 graph: bool = False, stop: str = "residual", emu_slices: int = 0):
+                 graph: int = 0, stop: str = "residual", emu_slices: int = 0,
+                 n_tile: int = 0, guess: str = "zero", wait_timeout_ns: int = 0):
         lib = load_library()
         self._lib = lib
         s, keep = _marshal(system)
@@ -180,7 +192,8 @@ class Context:
             stream = _current_stream()
         self.stream_handle = stream
         o = _Options(PREC[prec], restart, max_restarts, tol, batch, stream or 0, inner_tol,
-                     1 if graph else 0, STOP[stop], emu_slices)
+                     int(graph), STOP[stop], emu_slices, n_tile, GUESS[guess],
+                     wait_timeout_ns)
         self.prec = prec
         h = ctypes.c_void_p()
         st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
@@ -363,6 +376,25 @@ class Context:
             self._check(st)
         return P, _stats_dict(stats, n)
 
+    def set_guess(self, mode: str):
+        """tddft_set_guess: 'zero', 'interp' or 'learned' for the later solves."""
+        self._check(self._lib.tddft_set_guess(self.h, GUESS[mode]))
+
+    def guess_load(self, path):
+        """tddft_guess_load: the learned guess's network from a tddft_mlp_save file."""
+        self._check(self._lib.tddft_guess_load(self.h, os.fsencode(path)))
+
+    def set_wait_timeout(self, ns: int):
+        """tddft_set_wait_timeout: the limit of the tensor-core kernels' waits (0 = 2 s)."""
+        self._check(self._lib.tddft_set_wait_timeout(self.h, int(ns)))
+
+    def kproduct_plan(self, n_rhs: int):
+        """(cluster size, K slices) of the split-bf16 K product for n_rhs vectors."""
+        ncl, ks = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.tddft_kproduct_plan(self.h, n_rhs, ctypes.byref(ncl),
+                                                  ctypes.byref(ks)))
+        return ncl.value, ks.value
+
     def tuning(self):
         """N-tile widths the autotuner chose for (K z, transform 1, transform 2)."""
         t = (ctypes.c_int32 * 3)()
@@ -400,7 +432,7 @@ class Batch:
         marsh = [_marshal(s) for s in systems]
         arr = (_System * len(systems))(*[m[0] for m in marsh])
         o = _Options(PREC[prec], restart, max_restarts, tol, batch, None, inner_tol, 0, STOP[stop],
-                     emu_slices)
+                     emu_slices, 0, 0, 0)
         h = ctypes.c_void_p()
         st = lib.tddft_batch_create(len(systems), arr, ctypes.byref(o), ctypes.byref(h))
         if st != OK:
@@ -536,11 +568,22 @@ class Mlp:
         return x0
 
 
-def selftest_gemm(M: int, N: int, K: int, seed: int = 1) -> float:
-    """Max relative error of the split-bf16 tensor-core GEMM against float64."""
+def sweep_plan(n_omega: int):
+    """tddft_sweep_plan: (pass, left, right) int arrays of an n-point sweep."""
+    lib = load_library()
+    out = [np.empty(n_omega, dtype=np.int32) for _ in range(3)]
+    st = lib.tddft_sweep_plan(n_omega, *(a.ctypes.data for a in out))
+    if st != OK:
+        raise TddftError(st, "tddft_sweep_plan failed")
+    return tuple(out)
+
+
+def selftest_gemm(M: int, N: int, K: int, seed: int = 1, tf32: bool = False) -> float:
+    """Max relative error of the split-bf16 (or TF32) tensor-core GEMM against float64."""
     lib = load_library()
     err = ctypes.c_double()
-    st = lib.tddft_selftest_gemm(M, N, K, seed, ctypes.byref(err))
+    fn = lib.tddft_selftest_gemm_tf32 if tf32 else lib.tddft_selftest_gemm
+    st = fn(M, N, K, seed, ctypes.byref(err))
     if st != OK:
         raise TddftError(st, "tensor-core GEMM self-test failed")
     return err.value

@@ -73,7 +73,8 @@ def _create(sysm, **opt):
                       keep["K"].ctypes.data, keep["d"].ctypes.data)
     o = tddft._Options(opt.get("prec", 0), opt.get("restart", 10), opt.get("max_restarts", 5),
                        opt.get("tol", 1e-8), opt.get("batch", 4), None, opt.get("inner_tol", 1e-4),
-                       opt.get("graph", 0), opt.get("stop", 0), opt.get("emu_slices", 0))
+                       opt.get("graph", 0), opt.get("stop", 0), opt.get("emu_slices", 0),
+                       opt.get("n_tile", 0), opt.get("guess", 0), opt.get("wait_timeout_ns", 0))
     h = ctypes.c_void_p()
     st = lib.tddft_create(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
     return st, lib.tddft_last_error(None).decode(), h
@@ -132,6 +133,10 @@ def test_validation_rejects_bad_input_before_device_work(lib):
     assert _bad(lambda s: None, stop=-1)[0] == tddft.ERR_INVALID_ARG
     assert _bad(lambda s: None, prec=1, emu_slices=2)[0] == tddft.ERR_INVALID_ARG
     assert _bad(lambda s: None, prec=1, emu_slices=9)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, prec=2, n_tile=96)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, prec=2, n_tile=-64)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, wait_timeout_ns=-1)[0] == tddft.ERR_INVALID_ARG
+    assert _bad(lambda s: None, guess=3)[0] != tddft.OK
 
 
 def test_emulated_gemm_rejects_bad_arguments_on_the_host(lib):
@@ -170,3 +175,21 @@ def test_create_without_a_gpu_reports_a_cuda_error(lib):
         pytest.skip("a GPU is present")
     st, msg, h = _create(synth.tiny_system(3))
     assert st in (tddft.ERR_CUDA, tddft.ERR_NOMEM) and msg and not h.value
+
+
+def test_sweep_plan_follows_its_definition(lib):
+    """tddft_sweep_plan (host only): pass 0 = every 4th frequency and the last;
+    pass 1 = the other indices 2 mod 4; pass 2 = the rest; every guessed
+    frequency's neighbours are the nearest frequencies solved in earlier
+    passes, one on each side."""
+    for n in list(range(1, 14)) + [64, 257, 512]:
+        pas, left, right = tddft.sweep_plan(n)
+        for i in range(n):
+            if i % 4 == 0 or i == n - 1:
+                assert pas[i] == 0 and left[i] == -1 and right[i] == -1
+            else:
+                assert pas[i] == (1 if i % 4 == 2 else 2)
+                before = [j for j in range(n) if pas[j] < pas[i]]
+                assert left[i] == max(j for j in before if j < i)
+                assert right[i] == min(j for j in before if j > i)
+    assert lib.tddft_sweep_plan(0, None, None, None) == tddft.ERR_INVALID_ARG

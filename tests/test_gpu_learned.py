@@ -169,3 +169,43 @@ def test_trained_network_gains_over_interpolation():
     assert e_mlp < e_lin
     assert mv["learned"] <= mv["zero"]
     net.close()
+
+
+def test_learned_sweep_through_the_c_boundary(tmp_path):
+    """tddft_options.guess and tddft_guess_load: a learned-guess spectrum from
+    tddft_polarizability alone (host pointers, no Python arithmetic), every
+    frequency at the float64 tolerance and equal to the zero-guess spectrum
+    within it; the interpolating mode likewise; the errors of a missing or
+    misshapen network."""
+    s, w = synth.workload("tiny4")
+    om = np.linspace(0.40, 0.47, 33)
+    net = T().Mlp(10, 64, 2, max_rows=1024, seed=11)
+    rng = np.random.default_rng(2)
+    p = net.get_params()
+    p[-(2 * 64 + 2):] = rng.normal(size=2 * 64 + 2).astype(np.float32) * 1e-3
+    net.set_params(p)
+    path = tmp_path / "g.net"
+    net.save(path)
+    res = {}
+    for mode in ("zero", "interp", "learned"):
+        with T().Context(s, batch=48, restart=w["restart"], tol=1e-10, guess=mode) as ctx:
+            if mode == "learned":
+                ctx.guess_load(path)
+            P, st = ctx.polarizability(om, w["eps"])
+        assert st["converged"].all() and np.all(st["resid"] <= 1e-10)
+        res[mode] = (P, int(st["matvecs"].sum()))
+    for mode in ("interp", "learned"):
+        assert np.max(np.abs(res[mode][0] - res["zero"][0])) <= 1e-8 * np.max(np.abs(res["zero"][0]))
+    print("products:", {k: v[1] for k, v in res.items()})
+    with T().Context(s, batch=48, restart=w["restart"], tol=1e-10, guess="learned") as ctx:
+        with pytest.raises(T().TddftError) as e:
+            ctx.polarizability(om, w["eps"])
+        assert e.value.status == T().ERR_INVALID_ARG
+        wrong = T().Mlp(12, 16, 2, max_rows=16, seed=1)
+        wpath = tmp_path / "w.net"
+        wrong.save(wpath)
+        with pytest.raises(T().TddftError) as e:
+            ctx.guess_load(wpath)
+        assert e.value.status == T().ERR_SHAPE
+        wrong.close()
+    net.close()
