@@ -34,6 +34,13 @@ from paper_1005_5340_gb300 import synth  # noqa: E402
 
 METRIC = "omega-points/s at 1e-6 rel. residual"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (DFMA) nominal rate; no tensor path for FP64
+# cuBLAS float64 GEMM on the GB300s, `python bench.py --probe-peaks`
+# (profiles/peaks_fp64_tf32.md); None until measured
+FP64_MEASURED_TFLOPS = None
+FP64_TFLOPS = FP64_MEASURED_TFLOPS or FP64_NOMINAL_TFLOPS
+FP64_NOTE = ("measured cuBLAS DGEMM 8192^3 on this GB300 (bench.py --probe-peaks)"
+             if FP64_MEASURED_TFLOPS else
+             "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry among the measured peaks)")
 # FP32 CUDA-core peak from unit counts: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
 FP32_UNIT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # nominal dense tensor rates relative to bf16 (TF32 is half the bf16 rate)
@@ -103,6 +110,13 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=4,
                    help="timed steps the float64 subset is cut into")
     p.add_argument("--inner-tol", type=float, default=1e-4)
+    p.add_argument("--profile-case", choices=["oz", "step2"],
+                   help="run one small case for an ncu capture and exit: 'oz' the emulated "
+                        "float64 GEMM on a transform-1 shape (2816 x 16384 x 3328, 5 slices), "
+                        "'step2' two reduced-precision products A z of the 64-atom molecule at "
+                        "batch 192 with the N tile forced to 128")
+    p.add_argument("--probe-peaks", action="store_true",
+                   help="print the measured cuBLAS float64 and TF32 GEMM rates and exit")
     p.add_argument("--graph", type=int, default=0, choices=[0, 1, 2],
                    help="GMRES driver: 0 host loop, 1 replays of a captured iteration, 2 the "
                         "whole loop on the device (one conditional-graph launch per group)")
@@ -371,6 +385,27 @@ def per_kernel(timing: dict) -> dict:
     return out
 
 
+def kernel_peak(name: str, prec: str):
+    """(bound, peak TFLOP/s FP64-equivalent, note) of a compute kernel."""
+    peaks, src = measured_peaks()
+    sus = peaks["bf16_tflops_sustained"]
+    if name == "gemm_tc_kernel" and prec.startswith("tf32"):
+        return "tensor", sus * TF32_PER_BF16, (f"TF32: one TF32 product per algorithmic product; "
+                                                f"peak = {src} sustained bf16 {sus} x "
+                                                f"{TF32_PER_BF16} (nominal TF32/bf16 ratio)")
+    if name == "gemm_tc_kernel":
+        return "tensor", sus / 3.0, (f"split bf16: 3 bf16 products per algorithmic product; "
+                                     f"peak = {src} sustained bf16 {sus} / 3")
+    if name == "ozaki_gemm_kernel":
+        pairs = EMU_PAIRS.get(prec, 21)
+        return "tensor", sus / pairs, (f"float64 emulated with {pairs} bf16 slice products per "
+                                       f"algorithmic product; peak = {src} sustained bf16 {sus} "
+                                       f"/ {pairs}")
+    if name == "gemm_f64_kernel":
+        return "alu", FP64_TFLOPS, FP64_NOTE
+    return "alu", FP32_UNIT_TFLOPS, "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
+
+
 def roofline_of(timing: dict, step_ms: float, prec: str) -> dict:
     """Roofline entry of the kernel with the largest device time."""
     peaks, src = measured_peaks()
@@ -389,29 +424,7 @@ def roofline_of(timing: dict, step_ms: float, prec: str) -> dict:
                     peak_source=f"{src} HBM copy bandwidth",
                     algorithmic_bytes_per_launch=d["bytes"] / launches)
     achieved = (d["flops"] / launches) / per_launch_s / 1e12 if d["flops"] else None
-    sus = peaks["bf16_tflops_sustained"]
-    tc_tf32 = prec.startswith("tf32") and name == "gemm_tc_tf32_kernel"
-    if name == "gemm_tc_kernel":
-        peak = sus / 3.0
-        bound, note = "tensor", (f"split bf16: 3 bf16 products per algorithmic product; peak = "
-                                 f"{src} sustained bf16 {sus} / 3")
-    elif name == "gemm_tc_tf32_kernel" or tc_tf32:
-        peak = sus * TF32_PER_BF16
-        bound, note = "tensor", (f"TF32: one TF32 product per algorithmic product; peak = {src} "
-                                 f"sustained bf16 {sus} x {TF32_PER_BF16} (nominal TF32/bf16 "
-                                 f"ratio)")
-    elif name == "ozaki_gemm_kernel":
-        pairs = EMU_PAIRS.get(prec, 21)
-        peak = sus / pairs
-        bound, note = "tensor", (f"float64 emulated with {pairs} bf16 slice products per "
-                                 f"algorithmic product; peak = {src} sustained bf16 {sus} / "
-                                 f"{pairs}")
-    elif name == "gemm_f64_kernel":
-        peak, bound = FP64_NOMINAL_TFLOPS, "alu"
-        note = "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry among the measured peaks)"
-    else:
-        peak, bound = FP32_UNIT_TFLOPS, "alu"
-        note = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
+    bound, peak, note = kernel_peak(name, prec)
     tpf = TRAFFIC_PER_FLOP.get(name)
     traffic = tpf * d["flops"] / launches if (tpf and d["flops"]) else None
     return dict(base, bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s",
@@ -419,6 +432,20 @@ def roofline_of(timing: dict, step_ms: float, prec: str) -> dict:
                 traffic_unit="DRAM bytes per mean launch (ncu bytes per flop x the mean "
                              "launch's algorithmic flops)",
                 peak_source=note)
+
+
+def kernel_table(timing: dict, prec: str) -> dict:
+    """Per kernel: device time, launches and, for the GEMMs, the achieved
+    FP64-equivalent rate against its peak."""
+    out = {}
+    for k, v in per_kernel(timing).items():
+        e = {"ms": round(v["ms"], 3), "launches": v["launches"]}
+        if v["flops"] and v["ms"]:
+            bound, peak, _ = kernel_peak(k, prec)
+            rate = v["flops"] / (v["ms"] / 1e3) / 1e12
+            e.update(tflops=round(rate, 2), frac=round(rate / peak, 4))
+        out[k] = e
+    return out
 
 
 def config_of(workload: str, extra: str):
@@ -647,8 +674,7 @@ def run_ours(args):
         "gpu_launches_note": "launches of the library's kernels in the timed steps, counted "
                              "per timed scope in the instrumented pass and scaled to the "
                              "timed step count (a lower bound)",
-        "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
-                    for k, v in per_kernel(timing).items()},
+        "kernels": kernel_table(timing, args.prec),
         "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items() if v["launches"]},
         "kernel_launches": {k: v["launches"] for k, v in timing.items() if v["launches"]},
         "tc_n_tiles": tuning,
@@ -718,9 +744,67 @@ def run_batch(args):
     }), flush=True)
 
 
+def probe_peaks(args):
+    """Library GEMM rates on this GPU that MEASURED_PEAKS.json does not hold:
+    cuBLAS float64 (DGEMM) and TF32 (float32 GEMM with TF32 tensor cores),
+    8192^3, best of 10 after a warm-up (CUDA events), 2 N^3 flops each."""
+    import torch
+    torch.cuda.set_device(0)
+    n = 8192
+    out = {}
+    for name, dt, tf32 in (("fp64_tflops", torch.float64, False), ("tf32_tflops", torch.float32, True)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["how"] = "torch.matmul 8192^3, best of 10 (CUDA events), 2 N^3 flops"
+    out["gpu"] = torch.cuda.get_device_name(0)
+    print(json.dumps(out), flush=True)
+
+
+def profile_case(args):
+    """Small cases for ncu captures (one kernel, a few launches, a few GB)."""
+    import torch
+    from paper_1005_5340_gb300 import tddft
+    torch.cuda.set_device(0)
+    if args.profile_case == "oz":
+        M, K, N = 2816, 3328, 16384
+        g = torch.Generator(device="cuda").manual_seed(1)
+        A = torch.randn(M, K, dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn(K, N, dtype=torch.float64, device="cuda", generator=g)
+        for _ in range(2):
+            C = tddft.gemm_f64_emulated(A, B, 5)
+        torch.cuda.synchronize()
+        print("oz case done", float(C[0, 0]))
+    else:
+        s, w = synth.workload("medium64")
+        z = synth.random_complex_vectors(192, s.n_prod, 3)
+        om = np.linspace(0.1, 1.4, 192)
+        with tddft.Context(s, batch=192, prec="bf16x3", n_tile=128) as ctx:
+            for _ in range(2):
+                out = ctx.apply_A(z, om, w["eps"])
+        print("step2 case done", abs(out[0, 0]))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args)
+    elif args.probe_peaks:
+        probe_peaks(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch32":
         run_batch(args)

@@ -67,8 +67,17 @@ __device__ __forceinline__ void store_split(__nv_bfloat16 *p, int64_t lo_off, fl
   p[lo_off] = l;
 }
 
+// Row stride, in elements, of a next-GEMM operand written by an epilogue:
+// ep.ldo counts bf16 elements of a split row ([hi | lo], 2 Kp); a TF32 row
+// holds the same bytes as Kp floats, so its stride in floats is ep.ldo / 2.
+template <bool TF>
+__device__ __forceinline__ int64_t operand_ld(const TcEpilogue &ep) {
+  return TF ? ep.ldo / 2 : ep.ldo;
+}
+
 // element idx of a next-GEMM operand: split bf16 (hi at idx, lo at idx +
-// lo_off) or, in the TF32 form, one tf32-rounded float at idx
+// lo_off) or, in the TF32 form, one tf32-rounded float at idx (idx computed
+// with operand_ld)
 template <bool TF>
 __device__ __forceinline__ void put_operand(void *base, int64_t idx, int64_t lo_off, float x) {
   if (TF)
@@ -133,7 +142,7 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
         const int n = n0 + j0 + j;
         if (n < N) {
           const int64_t row = ((int64_t)(n >> 1) * ep.n_occ + E) * 2 + (n & 1);
-          put_operand<TF>(ep.outB, row * ep.ldo + aoA + c, ep.lo_off, v[j]);
+          put_operand<TF>(ep.outB, row * operand_ld<TF>(ep) + aoA + c, ep.lo_off, v[j]);
         }
       }
     }
@@ -150,7 +159,7 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
         const int sl = pair0 / ep.n_occ, E0 = pair0 - sl * ep.n_occ;
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-          const int64_t at = (int64_t)(2 * sl + p) * ep.ldo + xo + E0;
+          const int64_t at = (int64_t)(2 * sl + p) * operand_ld<TF>(ep) + xo + E0;
           if (TF) {
             // eight floats: two 16-byte stores
             float *dst = (float *)ep.outB + at;
@@ -174,7 +183,8 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
           if (n < N) {
             const int pair = n >> 1, p = n & 1;
             const int sl = pair / ep.n_occ, E = pair - sl * ep.n_occ;
-            put_operand<TF>(ep.outB, (int64_t)(2 * sl + p) * ep.ldo + xo + E, ep.lo_off, v[j]);
+            put_operand<TF>(ep.outB, (int64_t)(2 * sl + p) * operand_ld<TF>(ep) + xo + E, ep.lo_off,
+                            v[j]);
           }
         }
       }
@@ -214,8 +224,8 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
           E = 0;
           ++sl;
         }
-        put_operand<TF>(ep.outB, (int64_t)n * ep.ldo + m, ep.lo_off, re);
-        put_operand<TF>(ep.outB, (int64_t)(n + 1) * ep.ldo + m, ep.lo_off, im);
+        put_operand<TF>(ep.outB, (int64_t)n * operand_ld<TF>(ep) + m, ep.lo_off, re);
+        put_operand<TF>(ep.outB, (int64_t)(n + 1) * operand_ld<TF>(ep) + m, ep.lo_off, im);
       }
     }
   }
