@@ -36,7 +36,7 @@ METRIC = "omega-points/s at 1e-6 rel. residual"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (DFMA) nominal rate; no tensor path for FP64
 # cuBLAS float64 GEMM on the GB300s, `python bench.py --probe-peaks`
 # (profiles/peaks_fp64_tf32.md); None until measured
-FP64_MEASURED_TFLOPS = None
+FP64_MEASURED_TFLOPS = 1.099
 FP64_TFLOPS = FP64_MEASURED_TFLOPS or FP64_NOMINAL_TFLOPS
 FP64_NOTE = ("measured cuBLAS DGEMM 8192^3 on this GB300 (bench.py --probe-peaks)"
              if FP64_MEASURED_TFLOPS else
@@ -784,10 +784,14 @@ def profile_case(args):
         g = torch.Generator(device="cuda").manual_seed(1)
         A = torch.randn(M, K, dtype=torch.float64, device="cuda", generator=g)
         B = torch.randn(K, N, dtype=torch.float64, device="cuda", generator=g)
-        for _ in range(2):
-            C = tddft.gemm_f64_emulated(A, B, 5)
+        C = tddft.gemm_f64_emulated(A, B, 5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        C = tddft.gemm_f64_emulated(A, B, 5)
+        e1.record()
         torch.cuda.synchronize()
-        print("oz case done", float(C[0, 0]))
+        print(f"oz case: {e0.elapsed_time(e1):.3f} ms for the second call (slicing included)",
+              float(C[0, 0]))
     else:
         s, w = synth.workload("medium64")
         z = synth.random_complex_vectors(192, s.n_prod, 3)

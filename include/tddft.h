@@ -85,8 +85,16 @@ typedef enum {
                               last from zero; then index 2 mod 4 from the solved neighbours
                               at distance 2; then the rest from distance 1), each guess the
                               linear interpolation of the two neighbours' solutions */
-  TDDFT_GUESS_LEARNED = 2  /* the same sweep, each guess interpolation + the learned
+  TDDFT_GUESS_LEARNED = 2, /* the same sweep, each guess interpolation + the learned
                               correction of the network loaded by tddft_guess_load */
+  TDDFT_GUESS_INTERP_SUBSPACE = 3,  /* the sweep with an augmentation subspace per frequency:
+                                       the six neighbour solutions X_k(omega-), X_k(omega+)
+                                       (k = 0, 1, 2) and the three interpolated guesses; each
+                                       direction starts from the minimum-residual point of
+                                       that span, ||chi0 d_k - A x|| minimised with A applied
+                                       in the context's precision (9 products per frequency,
+                                       3 per right-hand side) */
+  TDDFT_GUESS_LEARNED_SUBSPACE = 4  /* the same with the learned guesses in the subspace */
 } tddft_guess;
 
 /*
@@ -268,6 +276,30 @@ tddft_status tddft_chi0_apply_noalloc(tddft_ctx *ctx, int32_t n_rhs, const doubl
 /* out_r = K . z_r (the precomputed kernel of Sec. 4.1); same layout rules. */
 tddft_status tddft_kernel_apply(tddft_ctx *ctx, int32_t n_rhs, const double *z, double *out,
                                 int32_t flags);
+
+/*
+ * Matrix-free K z from the product centres: a labelled variant of the
+ * matrix-free Hartree product the paper names as future work (Sec. 8), in
+ * the multipole form of Sec. 5 restricted to its monopole term, for kernels
+ *     K_{mu nu} = g(|C_{c(mu)} - C_{c(nu)}|) + diag delta_{mu nu},
+ *     g(r) = 1 / sqrt(r^2 + softening^2),
+ * i.e. every product a point charge at its centre (the synthetic inputs'
+ * kernel; extended product functions would add l > 0 moments, not built).
+ * Products sharing a centre act through the centre's total charge, so
+ *     (K z)_mu = diag z_mu + sum_c g(|C_{c(mu)} - C_c|) sum_{nu at c} z_nu
+ * is exact up to rounding with n_centres^2 kernel evaluations per vector and
+ * no stored K.  Float64, deterministic.
+ *  centres [n_centres][3] (bohr) and prod_centre [n_prod] (centre index of
+ *  each product, 0 <= c < n_centres): HOST pointers.  z, out: DEVICE
+ *  pointers, n_rhs x n_prod complex interleaved.  stream: cudaStream_t
+ *  (NULL = legacy default), synchronised before returning.  Allocates and
+ *  frees its scratch (about 32 n_rhs n_centres bytes).
+ * Errors: INVALID_ARG (NULL, sizes < 1, softening < 0 or NaN), SHAPE (a
+ * centre index out of range), NOMEM, CUDA.
+ */
+tddft_status tddft_kernel_apply_centres(int32_t n_prod, int32_t n_centres, const double *centres,
+                                        const int32_t *prod_centre, double softening, double diag,
+                                        int32_t n_rhs, const double *z, double *out, void *stream);
 
 /* out_r = A(omega_r) z_r = z_r - chi0(omega_r) (K z_r)  (Sec. 4.1). */
 tddft_status tddft_apply_A(tddft_ctx *ctx, int32_t n_rhs, const double *omega, double eps,

@@ -165,7 +165,7 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   while ((int)lcat.size() < ar.kcat2) lcat.push_back(-1);
   ar.kcat5 = kcat5;
   ar.ldp = 2 * std::max(slots, 3);
-  // tiles (128 rows of the per-atom operands)
+  // tiles (128 rows of the per-atom operands), atom by atom
   std::vector<GTile> t2, t5;
   ar.flops2 = ar.flops5 = 0.0;
   for (int A = 0; A < na; ++A) {

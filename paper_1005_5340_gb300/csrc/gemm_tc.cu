@@ -272,13 +272,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // tile t: M tile fastest, then the K slice (split K), then the N tile of
-  // tn columns; in a cluster launch (ep.ncl > 1) the N tile is fastest, so
-  // the CTAs of a cluster (one GPC, one L2 partition) read the same A tile;
+  // tn columns (the small A of the transforms stays in L2 while each B tile
+  // is read once); in a cluster launch (ep.ncl > 1) and in a grouped product
+  // (per-atom A operands, the large operand of steps 2 and 5) the N tile is
+  // fastest, so consecutive CTAs (in a cluster: one GPC, one L2 partition)
+  // read the same A tile, which DRAM then supplies once;
   // xa / xb: K offsets (elements) of the A and B tiles within a plane
   auto tile_of = [&](int t, int &m0, int &xa, int &xb, int &nkb, int &rows_valid, int &atom,
                      int &n0) {
     int mt, ks, nt;
-    if (ep.ncl > 1) {
+    if (ep.ncl > 1 || tiles) {
       nt = t % n_ntiles;
       const int rest = t / n_ntiles;
       mt = rest % n_mtiles;

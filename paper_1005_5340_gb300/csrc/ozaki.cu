@@ -65,6 +65,7 @@ struct OzArgs {
   OzEpilogue ep;
   int vec;      // kOzC with 16-byte aligned rows: double2 stores
   const GTile *tiles;   // grouped product: one entry per M tile (NULL: plain row tiles)
+  int mgroup;           // plain tiles: M tiles per group of the L2-aware tile order
   int *err;
   const int *dcnt;
   int mul_n;
@@ -116,19 +117,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                       const __grid_constant__ CUtensorMap mapB, OzArgs a) {
   int N = a.N;
   if (a.dcnt) N = (int)min((int64_t)N, (int64_t)a.mul_n * (*a.dcnt));
-  const int n0 = blockIdx.y * OZ_BN;
+  // tile (mt, nt) of this CTA, in an L2-aware order: the M tiles (rows of
+  // A, or entries of the tile table) in groups of a.mgroup (A panels that fit
+  // in L2 together), every N tile of a group before the next group, the M
+  // tile fastest within it, so that each A panel is read from DRAM about once
+  int mt, nt;
+  {
+    const int Mt = gridDim.x, Nt = gridDim.y, G = a.mgroup;
+    const int lin = blockIdx.x + Mt * blockIdx.y;
+    const int g = lin / (G * Nt), r = lin - g * (G * Nt);
+    const int Gg = min(G, Mt - g * G);
+    mt = g * G + r % Gg;
+    nt = r / Gg;
+  }
+  const int n0 = nt * OZ_BN;
   if (n0 >= N) return;
   // this CTA's rows of A and K range of B
   int m0, xoff, nkb, rows_valid, atom;
   if (a.tiles) {
-    const GTile t = a.tiles[blockIdx.x];
+    const GTile t = a.tiles[mt];
     m0 = t.row0;
     xoff = t.xoff;
     nkb = t.nkb;
     rows_valid = t.rows;
     atom = t.atom;
   } else {
-    m0 = blockIdx.x * OZ_BM;
+    m0 = mt * OZ_BM;
     xoff = 0;
     nkb = a.KpA / OZ_BK;
     rows_valid = min(OZ_BM, a.M - m0);
@@ -212,12 +226,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       int g = 0;
       bool ok = true;
       for (int c = 0; c < nchunks && ok; ++c) {
-        // groups whose previous chunk the epilogue has drained (checked
-        // before their first MMA of this chunk)
-        uint32_t written = 0, drained = (c == 0) ? 0xFFu : 0u;
+        // every group of the previous chunk drained by the epilogue before
+        // the first MMA of this chunk (one wait per group, here, so that the
+        // issue loop below is straight-line code)
+        if (c > 0) {
+          for (int grp = 0; grp < S && ok; ++grp) {
+            if (!mbar_wait(&tempty[grp], (uint32_t)(c - 1) & 1u, lim)) {
+              atomicExch(a.err, 22);
+              abort_flag = 1;
+              ok = false;
+            }
+          }
+          if (!ok) break;
+          fence_after();
+        }
         const int kb1 = min(nkb, (c + 1) * cb);
         for (int kb = c * cb; kb < kb1 && ok; ++kb) {
-          for (int i = 0; i < s && ok; ++i) {
+          const bool first_kb = kb == c * cb;
+          // slice pairs (i, j), i >= j, i + j <= S - 1, in the order i, then j;
+          // the unrolled schedule is fixed by S.  (i, j) is the first pair of
+          // its group (i + j) in that order exactly when i - j <= 1.
+#pragma unroll
+          for (int i = 0; i < S; ++i) {
             const int gi = g + i;
             if (!mbar_wait(&full[gi % OZ_STAGES], (uint32_t)(gi / OZ_STAGES) & 1u, lim)) {
               atomicExch(a.err, 23);
@@ -227,27 +257,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             }
             fence_after();
             const uint32_t si = base + (uint32_t)(gi % OZ_STAGES) * OZ_STAGE_BYTES;
-            const int jmax = min(i, s - 1 - i);
-            for (int j = 0; j <= jmax; ++j) {
+#pragma unroll
+            for (int j = 0; j <= (i < S - 1 - i ? i : S - 1 - i); ++j) {
               const uint32_t sj = base + (uint32_t)((g + j) % OZ_STAGES) * OZ_STAGE_BYTES;
-              const int grp = i + j;
-              if (!((drained >> grp) & 1u)) {
-                if (!mbar_wait(&tempty[grp], (uint32_t)(c - 1) & 1u, lim)) {
-                  atomicExch(a.err, 22);
-                  abort_flag = 1;
-                  ok = false;
-                  break;
-                }
-                fence_after();
-                drained |= 1u << grp;
-              }
-              const uint32_t d = tmem + (uint32_t)(grp * OZ_BN);
-              uint32_t acc = (written >> grp) & 1u;
+              const uint32_t d = tmem + (uint32_t)((i + j) * OZ_BN);
+              const bool overwrite = first_kb && (i - j <= 1);
               // A slice i x B slice j
 #pragma unroll
               for (int k = 0; k < OZ_BK / 16; ++k)
                 mma_bf16(d, desc_sw128(si + 32 * k), desc_sw128(sj + OZ_A_BYTES + 32 * k), idesc,
-                         (acc | (uint32_t)k) ? 1u : 0u);
+                         (overwrite && k == 0) ? 0u : 1u);
               if (j < i) {
                 // A slice j x B slice i
 #pragma unroll
@@ -255,16 +274,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                   mma_bf16(d, desc_sw128(sj + 32 * k), desc_sw128(si + OZ_A_BYTES + 32 * k),
                            idesc, 1u);
               }
-              written |= 1u << grp;
             }
-            if (!ok) break;
-            // slice q is last used at step max(q, s-1-q): release what step i
+            // slice q is last used at step max(q, S-1-q): release what step i
             // finished (the stage frees once these MMAs complete)
-            if (i >= s - 1 - i) mma_commit(&empty[gi % OZ_STAGES]);
-            if (s - 1 - i < i) mma_commit(&empty[(g + s - 1 - i) % OZ_STAGES]);
+            if (i >= S - 1 - i) mma_commit(&empty[gi % OZ_STAGES]);
+            if (S - 1 - i < i) mma_commit(&empty[(g + S - 1 - i) % OZ_STAGES]);
           }
           if (!ok) break;
-          g += s;
+          g += S;
         }
         if (ok) mma_commit(tfull);
       }
@@ -638,6 +655,13 @@ cudaError_t launch_gemm_oz_ex(cudaStream_t st, const OzOperand &A, const OzOpera
   a.ep = ep;
   a.vec = (ep.mode == kOzC && (ep.ldc % 2) == 0 && ((uintptr_t)ep.C & 15) == 0) ? 1 : 0;
   a.tiles = tiles;
+  {
+    // M tiles whose A panels (s slices of the whole K) fill about 40 MB of L2
+    // (grid.x = Mt, the tiles or 128-row blocks)
+    const double panel = (double)OZ_BM * A.s * A.Kp * sizeof(__nv_bfloat16);
+    const int Mt = tiles ? n_tiles : (M + OZ_BM - 1) / OZ_BM;
+    a.mgroup = std::max(1, std::min(Mt, (int)(40.0e6 / panel)));
+  }
   a.err = err;
   a.dcnt = dcnt;
   a.mul_n = mul_n;

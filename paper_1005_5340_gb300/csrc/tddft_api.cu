@@ -278,7 +278,7 @@ tddft_status tddft_create(const tddft_system *s, const tddft_options *o, tddft_c
     return fail(nullptr, TDDFT_ERR_UNSUPPORTED, "unknown precision");
   if (o->n_tile != 0 && o->n_tile != 64 && o->n_tile != 128 && o->n_tile != 256)
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "n_tile must be 0, 64, 128 or 256");
-  if (o->guess < TDDFT_GUESS_ZERO || o->guess > TDDFT_GUESS_LEARNED)
+  if (o->guess < TDDFT_GUESS_ZERO || o->guess > TDDFT_GUESS_LEARNED_SUBSPACE)
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "unknown initial guess");
   if (o->wait_timeout_ns < 0)
     return fail(nullptr, TDDFT_ERR_INVALID_ARG, "wait_timeout_ns must be >= 0");
@@ -703,7 +703,7 @@ tddft_status tddft_polarizability_guess(tddft_ctx *c, int32_t n_omega, const dou
 tddft_status tddft_set_guess(tddft_ctx *c, int32_t guess) {
   if (!c) return TDDFT_ERR_INVALID_ARG;
   c->err.clear();
-  if (guess < TDDFT_GUESS_ZERO || guess > TDDFT_GUESS_LEARNED)
+  if (guess < TDDFT_GUESS_ZERO || guess > TDDFT_GUESS_LEARNED_SUBSPACE)
     return fail(c, TDDFT_ERR_INVALID_ARG, "unknown initial guess");
   c->opts.guess = guess;
   return TDDFT_OK;

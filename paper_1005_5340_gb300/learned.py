@@ -42,10 +42,11 @@ def _targets(omega, idx, left, right):
 
 
 def solve_sweep(ctx, omega, eps, mode="zero", mlp=None):
-    """The library's sweep on ctx in the given mode ("zero", "interp" or
-    "learned"; mlp is loaded into the context for "learned").  Returns
+    """The library's sweep on ctx in the given mode ("zero", "interp",
+    "learned", "interp_subspace" or "learned_subspace"; mlp is loaded into
+    the context for the learned modes).  Returns
     (P [n,3,3] complex numpy, stats dict, X [3n, n_prod] complex CUDA tensor)."""
-    if mode == "learned":
+    if mode.startswith("learned"):
         fd, path = tempfile.mkstemp(suffix=".net")
         os.close(fd)
         try:

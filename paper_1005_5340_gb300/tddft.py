@@ -22,7 +22,7 @@ STATUS_NAMES = ["OK", "INVALID_ARG", "SHAPE", "NOMEM", "CUDA", "NOT_CONVERGED", 
 DEVICE_PTRS = 1
 PREC = {"fp64": 0, "fp64emu": 1, "bf16x3": 2, "bf16x3emu": 3, "tf32": 4, "tf32emu": 5}
 # initial guesses of tddft_polarizability
-GUESS = {"zero": 0, "interp": 1, "learned": 2}
+GUESS = {"zero": 0, "interp": 1, "learned": 2, "interp_subspace": 3, "learned_subspace": 4}
 # GMRES stopping rules (Sec. 4.1): relative residual, eps_P, eps_P and eps_X
 STOP = {"residual": 0, "eps_p": 1, "eps_px": 2}
 
@@ -81,6 +81,9 @@ SIGNATURES = {
     "tddft_chi0_apply_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
                                                 ctypes.c_int32]),
     "tddft_kernel_apply": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
+    "tddft_kernel_apply_centres": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                                  _P, _P, _P]),
     "tddft_apply_A": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
                                      ctypes.c_int32]),
     "tddft_polarizability": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
@@ -566,6 +569,24 @@ class Mlp:
         if st != OK:
             raise TddftError(st, "tddft_guess_combine failed")
         return x0
+
+
+def kernel_apply_centres(centres, prod_centre, z, softening: float = 1.0, diag: float = 0.05):
+    """tddft_kernel_apply_centres: K z for a CUDA tensor z (n_rhs x n_prod complex)
+    from the distinct product centres (n_c x 3) and each product's centre index."""
+    import torch
+    c = np.ascontiguousarray(centres, dtype=np.float64)
+    pc = np.ascontiguousarray(prod_centre, dtype=np.int32)
+    z = z.to(torch.complex128).contiguous()
+    out = torch.empty_like(z)
+    lib = load_library()
+    st = lib.tddft_kernel_apply_centres(pc.size, c.shape[0], c.ctypes.data, pc.ctypes.data,
+                                        float(softening), float(diag), z.shape[0],
+                                        torch.view_as_real(z).data_ptr(),
+                                        torch.view_as_real(out).data_ptr(), _current_stream())
+    if st != OK:
+        raise TddftError(st, "tddft_kernel_apply_centres failed")
+    return out
 
 
 def sweep_plan(n_omega: int):

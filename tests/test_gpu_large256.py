@@ -84,3 +84,35 @@ def test_large256_bench_step_residuals_checked_by_the_oracle(large):
         r = np.linalg.norm(b - O.apply_A(s, op, X[g], x, w["eps"])) / np.linalg.norm(b)
         print(f"large256 RHS {g}: oracle residual {r:.3e}")
         assert r <= 1.01 * w["tol"]
+
+
+def test_large256_centre_form_of_the_kernel_product(large):
+    """The matrix-free K z from the 1494 distinct product centres against the
+    dense kernel on sampled vectors, and its time against the dense float64
+    product of a context (192 vectors)."""
+    import torch
+    s, w = large
+    uc, inv = np.unique(s.centres, axis=0, return_inverse=True)
+    pc = inv.astype(np.int32).ravel()
+    z = synth.random_complex_vectors(192, s.n_prod, 41)
+    zd = torch.from_numpy(z).cuda()
+    T().kernel_apply_centres(uc, pc, zd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = T().kernel_apply_centres(uc, pc, zd)
+    torch.cuda.synchronize()
+    t_c = time.perf_counter() - t0
+    with T().Context(s, batch=192) as ctx:
+        ctx.kernel_apply(zd)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dense = ctx.kernel_apply(zd)
+        torch.cuda.synchronize()
+        t_d = time.perf_counter() - t0
+    out, dense = out.cpu().numpy(), dense.cpu().numpy()
+    for r in (0, 191):
+        ref = s.K @ z[r]
+        assert np.max(np.abs(out[r] - ref)) / np.max(np.abs(ref)) < 1e-12
+    assert np.max(np.abs(out - dense)) / np.max(np.abs(dense)) < 1e-12
+    print(f"large256 K z, 192 vectors: centre form {uc.shape[0]} centres {1e3 * t_c:.2f} ms, "
+          f"dense float64 {1e3 * t_d:.2f} ms")
