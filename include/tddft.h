@@ -319,6 +319,26 @@ tddft_status tddft_polarizability(tddft_ctx *ctx, int32_t n_omega, const double 
                                   int32_t flags);
 
 /*
+ * tddft_polarizability with checkpoint and resume.  Every (omega, direction)
+ * is independent (Sec. 6.2.3), so a spectrum can be computed in pieces: the
+ * frequencies of omega[] without a record in the file at `path` (created if
+ * missing) are solved, in groups of the context's batch / 3 frequencies, and
+ * each group's records are appended and synced to the file before the next
+ * group starts; P and stats are then filled for every requested frequency,
+ * solved now or read back.  A record holds omega, eps, P and the three
+ * directions' statistics; frequencies are matched by the exact bits of omega
+ * and eps.  The file's header fingerprints the problem (n_prod, n_orb, n_occ,
+ * precision, stopping rule, restart, tol): a file of another problem is
+ * refused (INVALID_ARG).  A record cut short by an interruption is dropped
+ * and its frequency solved again.  Host pointers.  *n_solved (may be NULL)
+ * receives the number of frequencies solved by this call.  Errors: as
+ * tddft_polarizability, and INVALID_ARG for an unreadable or unwritable file.
+ */
+tddft_status tddft_polarizability_resume(tddft_ctx *ctx, int32_t n_omega, const double *omega,
+                                         double eps, double *P, tddft_solve_stats *stats,
+                                         const char *path, int32_t *n_solved);
+
+/*
  * Adaptive frequency grid and pole extraction: the step the paper names as
  * its next one (Sec. 8, conclusions), for a spectrum resolved only where it
  * has structure.  The absorption is S(omega) = Im alpha_tr(omega) with

@@ -264,7 +264,9 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
 //   x[r][k] = 2^e[r] * sum_i q_i[r][k] 2^(-7 i),   |q_1| <= 128, |q_i| <= 64,
 // stored as exact bf16 integers [rows][s*Kp] (slice i at column i*Kp).
 struct OzOperand {
-  CUtensorMap map;
+  CUtensorMap map;     // boxes of 64 columns x box_rows rows
+  CUtensorMap map96;   // B role only: boxes of 96 rows (has96)
+  bool has96 = false;
   __nv_bfloat16 *q = nullptr;
   int *e = nullptr;
   int64_t rows = 0;

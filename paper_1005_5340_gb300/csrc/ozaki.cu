@@ -47,14 +47,21 @@ namespace tddft {
 namespace {
 using namespace ptx;
 
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64, OZ_STAGES = 9;
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64;
 constexpr int OZ_EPI_WARPS = 8;                        // 2 per TMEM lane quadrant
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;      // producer, MMA, epilogue
-constexpr int OZ_EPI_COLS = OZ_BN / 2;                  // columns per epilogue thread
 constexpr uint32_t OZ_A_BYTES = OZ_BM * OZ_BK * 2;   // 16 KB
-constexpr uint32_t OZ_B_BYTES = OZ_BN * OZ_BK * 2;   //  8 KB
-constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
-constexpr size_t OZ_SMEM = (size_t)OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+// The N tile: 96 columns where the s groups fit in tensor memory (s x 96 <=
+// 512, s <= 5), else 64; each MMA then does 1.5x the work for the same A
+// tile read from shared memory.  9 stages of 24 KB, or 8 of 28 KB.
+template <int BN> struct OzShape {
+  static constexpr int EPI_COLS = BN / 2;                      // columns per epilogue thread
+  static constexpr uint32_t B_BYTES = BN * OZ_BK * 2;
+  static constexpr uint32_t STAGE_BYTES = OZ_A_BYTES + B_BYTES;
+  static constexpr int STAGES = BN == 64 ? 9 : 8;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+};
+__host__ __device__ constexpr int oz_bn(int S) { return S * 96 <= 512 ? 96 : 64; }
 
 struct OzArgs {
   int M, N;
@@ -82,25 +89,52 @@ constexpr int kOzMaxChunks = 1024;
 // weight is a rounded right shift of the (exact, < 2^25) group sum.  One
 // group's values are live at a time (the loop is not unrolled).
 // (ns == S, passed at run time so that the loop stays rolled)
-template <int S>
-__device__ __forceinline__ void read_groups(uint32_t tcol, long long (&acc)[OZ_EPI_COLS], int ns,
+// Columns j0 .. j0 + n - 1 of acc from v (n = 16 or 32).
+template <int N, int EC>
+__device__ __forceinline__ void add_group(long long (&acc)[EC], const float *v, int j0, int sh) {
+  if (sh >= 0) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j0 + j] += (long long)__float2int_rn(v[j]) << sh;
+  } else {
+    const int r = -sh, half = 1 << (r - 1);
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j0 + j] += (long long)((__float2int_rn(v[j]) + half) >> r);
+  }
+}
+
+// tcol: this thread's lane and its first column (h EPI_COLS) in group 0.
+// With 96-wide groups, half h = 0 reads 32 + 16 columns, h = 1 reads 16 +
+// 32, so that every 32-column load starts on a multiple of 32 columns.
+template <int S, int BN>
+__device__ __forceinline__ void read_groups(uint32_t tcol, int h,
+                                            long long (&acc)[OzShape<BN>::EPI_COLS], int ns,
                                             uint64_t *tempty) {
 #pragma unroll 1
   for (int grp = 0; grp < ns; ++grp) {
     const int sh = 7 * (S - 1 - grp) - oz_drop_bits(S);
-    float v[32];
-    tmem_ld32(tcol + (uint32_t)(grp * OZ_BN), v);
+    const uint32_t g0 = tcol + (uint32_t)(grp * BN);
+    float v[32], u[16];
+    if (BN == 64) {
+      tmem_ld32(g0, v);
+    } else if (h == 0) {
+      tmem_ld32(g0, v);
+      tmem_ld16(g0 + 32, u);
+    } else {
+      tmem_ld16(g0, u);
+      tmem_ld32(g0 + 16, v);
+    }
     // this group's accumulator may be overwritten by the next chunk
     fence_before();
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&tempty[grp]);
-    if (sh >= 0) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] += (long long)__float2int_rn(v[j]) << sh;
+    if (BN == 64) {
+      add_group<32>(acc, v, 0, sh);
+    } else if (h == 0) {
+      add_group<32>(acc, v, 0, sh);
+      add_group<16>(acc, u, 32, sh);
     } else {
-      const int r = -sh, half = 1 << (r - 1);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] += (long long)((__float2int_rn(v[j]) + half) >> r);
+      add_group<16>(acc, u, 0, sh);
+      add_group<32>(acc, v, 16, sh);
     }
   }
 }
@@ -111,7 +145,7 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-template <int S>
+template <int S, int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                       const __grid_constant__ CUtensorMap mapB, OzArgs a) {
@@ -130,7 +164,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     mt = g * G + r % Gg;
     nt = r / Gg;
   }
-  const int n0 = nt * OZ_BN;
+  constexpr int OZ_STAGES = OzShape<BN>::STAGES;
+  constexpr uint32_t OZ_STAGE_BYTES = OzShape<BN>::STAGE_BYTES;
+  constexpr int OZ_EPI_COLS = OzShape<BN>::EPI_COLS;
+  const int n0 = nt * BN;
   if (n0 >= N) return;
   // this CTA's rows of A and K range of B
   int m0, xoff, nkb, rows_valid, atom;
@@ -163,7 +200,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   constexpr int s = S;
   const int cb = a.cb;
   const int nchunks = (nkb + cb - 1) / cb;
-  constexpr uint32_t tcols = S <= 4 ? 256u : 512u;
+  constexpr uint32_t tcols = S * BN <= 256 ? 256u : 512u;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < OZ_STAGES; ++i) {
@@ -221,7 +258,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(OZ_BM, OZ_BN);
+      constexpr uint32_t idesc = idesc_bf16(OZ_BM, BN);
       const uint32_t base = smem_u32(smem);
       int g = 0;
       bool ok = true;
@@ -260,7 +297,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
             for (int j = 0; j <= (i < S - 1 - i ? i : S - 1 - i); ++j) {
               const uint32_t sj = base + (uint32_t)((g + j) % OZ_STAGES) * OZ_STAGE_BYTES;
-              const uint32_t d = tmem + (uint32_t)((i + j) * OZ_BN);
+              const uint32_t d = tmem + (uint32_t)((i + j) * BN);
               const bool overwrite = first_kb && (i - j <= 1);
               // A slice i x B slice j
 #pragma unroll
@@ -314,7 +351,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         break;
       }
       fence_after();
-      read_groups<S>(tcol, acc, a.ns, tempty);
+      read_groups<S, BN>(tcol, h, acc, a.ns, tempty);
     }
     if (ok && lr < rows_valid && nc < N) {
       // C = acc 2^(eA + eB + u - 7(S+1)), as two exact power-of-two factors
@@ -566,15 +603,19 @@ int chunk_blocks(int s) { return std::max(1, 4096 / (s + 2) / OZ_BK); }
 
 template <int S>
 cudaError_t launch_oz_kernel(cudaStream_t st, dim3 grid, const CUtensorMap &mA,
-                             const CUtensorMap &mB, const OzArgs &a) {
-  ozaki_gemm_kernel<S><<<grid, OZ_THREADS, OZ_SMEM, st>>>(mA, mB, a);
+                             const OzOperand &B, const OzArgs &a) {
+  constexpr int BN = oz_bn(S);
+  ozaki_gemm_kernel<S, BN><<<grid, OZ_THREADS, OzShape<BN>::SMEM, st>>>(
+      mA, BN == 64 ? B.map : B.map96, a);
   return cudaGetLastError();
 }
 
 template <int S>
 cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(ozaki_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)OZ_SMEM);
+  constexpr int BN = oz_bn(S);
+  return cudaFuncSetAttribute(ozaki_gemm_kernel<S, BN>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)OzShape<BN>::SMEM);
 }
 }  // namespace
 
@@ -601,7 +642,14 @@ cudaError_t oz_operand(OzOperand &op, __nv_bfloat16 *q, int *e, int64_t rows, in
   op.rows = rows;
   op.Kp = round_up(Kdim, OZ_BK);
   op.s = s;
-  return encode_bf16_map(&op.map, q, rows, (int64_t)s * op.Kp, box_rows);
+  cudaError_t r = encode_bf16_map(&op.map, q, rows, (int64_t)s * op.Kp, box_rows);
+  // the B role also gets 96-row boxes (the N tile of 3 to 5 slices)
+  op.has96 = false;
+  if (r == cudaSuccess && box_rows == OZ_BN) {
+    r = encode_bf16_map(&op.map96, q, rows, (int64_t)s * op.Kp, 96);
+    op.has96 = r == cudaSuccess;
+  }
+  return r;
 }
 
 cudaError_t launch_oz_slice_rows(cudaStream_t st, const double *X, int64_t ldx, int rows, int Kdim,
@@ -665,15 +713,17 @@ cudaError_t launch_gemm_oz_ex(cudaStream_t st, const OzOperand &A, const OzOpera
   a.err = err;
   a.dcnt = dcnt;
   a.mul_n = mul_n;
-  dim3 grid(tiles ? n_tiles : (M + OZ_BM - 1) / OZ_BM, (N + OZ_BN - 1) / OZ_BN);
+  const int bn = oz_bn(A.s);
+  if (bn == 96 && !B.has96) return cudaErrorInvalidValue;
+  dim3 grid(tiles ? n_tiles : (M + OZ_BM - 1) / OZ_BM, (N + bn - 1) / bn);
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   switch (A.s) {
-    case 3: return launch_oz_kernel<3>(st, grid, A.map, B.map, a);
-    case 4: return launch_oz_kernel<4>(st, grid, A.map, B.map, a);
-    case 5: return launch_oz_kernel<5>(st, grid, A.map, B.map, a);
-    case 6: return launch_oz_kernel<6>(st, grid, A.map, B.map, a);
-    case 7: return launch_oz_kernel<7>(st, grid, A.map, B.map, a);
-    case 8: return launch_oz_kernel<8>(st, grid, A.map, B.map, a);
+    case 3: return launch_oz_kernel<3>(st, grid, A.map, B, a);
+    case 4: return launch_oz_kernel<4>(st, grid, A.map, B, a);
+    case 5: return launch_oz_kernel<5>(st, grid, A.map, B, a);
+    case 6: return launch_oz_kernel<6>(st, grid, A.map, B, a);
+    case 7: return launch_oz_kernel<7>(st, grid, A.map, B, a);
+    case 8: return launch_oz_kernel<8>(st, grid, A.map, B, a);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1027,6 +1027,7 @@ const DevSystem *ctx_system(const tddft_ctx *c) { return &c->sys; }
 cudaStream_t ctx_stream(const tddft_ctx *c) { return c->st; }
 void ctx_set_error(tddft_ctx *c, const char *msg) { c->err = msg; }
 int ctx_slots(const tddft_ctx *c) { return c->wk.slots; }
+const tddft_options *ctx_options(const tddft_ctx *c) { return &c->opts; }
 int ctx_guess_mode(const tddft_ctx *c) { return c->opts.guess; }
 tddft_mlp *ctx_guess_net(const tddft_ctx *c) { return c->guess_net; }
 void ctx_set_guess_net(tddft_ctx *c, tddft_mlp *net) {

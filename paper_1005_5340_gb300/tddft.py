@@ -90,6 +90,8 @@ SIGNATURES = {
                                             ctypes.c_int32]),
     "tddft_polarizability_guess": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P,
                                                   _P, _P, _P, ctypes.c_int32]),
+    "tddft_polarizability_resume": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, _P,
+                                                   ctypes.c_char_p, _P]),
     "tddft_sizes": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "tddft_spectrum_adaptive": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, _P, _P, _P, _P, _P,
@@ -397,6 +399,21 @@ class Context:
         self._check(self._lib.tddft_kproduct_plan(self.h, n_rhs, ctypes.byref(ncl),
                                                   ctypes.byref(ks)))
         return ncl.value, ks.value
+
+    def polarizability_resume(self, omega, eps, path, *, raise_on_nonconvergence: bool = True):
+        """tddft_polarizability_resume: (P [n,3,3], stats, frequencies solved by this call),
+        finished frequencies appended to and read back from the checkpoint at path."""
+        om = np.ascontiguousarray(np.atleast_1d(omega), dtype=np.float64)
+        n = om.size
+        P = np.empty((n, 3, 3), dtype=np.complex128)
+        stats = (SolveStats * (3 * n))()
+        solved = ctypes.c_int32()
+        st = self._lib.tddft_polarizability_resume(self.h, n, om.ctypes.data, float(eps),
+                                                   P.ctypes.data, stats, os.fsencode(path),
+                                                   ctypes.byref(solved))
+        if st != OK and not (st == ERR_NOT_CONVERGED and not raise_on_nonconvergence):
+            self._check(st)
+        return P, _stats_dict(stats, n), solved.value
 
     def tuning(self):
         """N-tile widths the autotuner chose for (K z, transform 1, transform 2)."""
