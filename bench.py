@@ -745,7 +745,15 @@ def run_batch(args):
         "matvecs_per_rhs": mv / (3 * points), "clocks": clocks,
         "one_molecule_at_a_time": {"value": seq_rate, "unit": "omega-points/s",
                                    "speedup_of_batch": (ok_pts / dt) / seq_rate},
-        "roofline": None, "e2e": None, "cpu_baseline": None,
+        "e2e": {"value": ok_pts / dt, "unit": "omega-points/s",
+                "h2d_bytes_per_step": 8 * per, "d2h_bytes_per_step": 16 * 9 * per * len(mols),
+                "note": "the timed calls themselves: tddft_batch_polarizability takes host omega "
+                        "and returns host P, so the value is end to end"},
+        "roofline": None,
+        "roofline_note": "the batch runs every group as device-driven graph loops, which the "
+                         "per-kernel CUDA events of the instrumented pass do not enter; the "
+                         "kernels are those of the single-molecule line",
+        "cpu_baseline": None,
     }), flush=True)
 
 
