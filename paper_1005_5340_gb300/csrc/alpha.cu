@@ -9,6 +9,18 @@
 // bilocal product mu on (A, B) the vertex block V_mu^{ab} (a in A, b in B)
 // gives alpha_mu^{aE} = sum_b V^{ab} X_b^E and alpha_mu^{bE} = sum_a V^{ab} X_a^E;
 // a local product (A, A) has alpha_mu^{aE} = sum_{a'} V^{aa'} X_a'^E.
+//
+// The reduced-precision step 2 runs over 16-orbital chunks of the orbital
+// axis instead of atoms: chunk k holds orbitals 16k .. 16k+15 (of one or
+// more atoms), its product list L(k) is the union of their lists L_A, and
+// its operand row (k, E, c16) holds alpha^{cE} of orbital c = 16k + c16 on
+// L(k), zero on the products outside L_{A(c)}.  The product runs with the
+// right-hand-side columns as the M axis, so that each thread of its
+// epilogue holds the 16 orbitals of one (k, E): one whole 32-byte sector of
+// a beta^T row per plane, written with 16-byte stores.  (A per-atom segment
+// of 13 orbitals is 26 bytes and fills no sector; its 2-byte stores made
+// step 2 store bound.)  The union roughly doubles the step's MMA work,
+// which stays below the store time it saves.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -80,6 +92,43 @@ __global__ void split_dense_kernel(const double *__restrict__ src, int64_t rows,
     const __nv_bfloat16 hi = __double2bfloat16(x);
     dst[r * 2 * Kp + k] = hi;
     dst[r * 2 * Kp + Kp + k] = __double2bfloat16(x - (double)__bfloat162float(hi));
+  }
+}
+
+// The chunk operand of the reduced-precision step 2: row r = (k n_occ + E)
+// 16 + c16, column q < K2c holds alpha of orbital o = 16k + c16 on the
+// product at position q of L(k) (posmap[k][c16][q]: its position in
+// L_{A(o)}, or -1 where it is not in that list; zero rows past n_orb), split
+// bf16 [rows][2 K2c] or tf32 [rows][K2c].
+__global__ void alpha_chunk_kernel(int64_t rows, int K2c, int n_occ, int n_orb, int K2max,
+                                   const int *__restrict__ aoff, const int *__restrict__ orb_atom,
+                                   const int *__restrict__ posmap, const double *__restrict__ a2,
+                                   void *__restrict__ dstv, bool tf32) {
+  const int64_t total = rows * K2c;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / K2c;
+    const int q = (int)(i - r * K2c);
+    const int c16 = (int)(r & 15);
+    const int64_t kE = r >> 4;
+    const int k = (int)(kE / n_occ), E = (int)(kE - (int64_t)k * n_occ);
+    const int o = 16 * k + c16;
+    double x = 0.0;
+    if (o < n_orb) {
+      const int p = posmap[((int64_t)k * 16 + c16) * K2c + q];
+      if (p >= 0) {
+        const int A = orb_atom[o], aoA = aoff[A], nA = aoff[A + 1] - aoA;
+        x = a2[((int64_t)aoA * n_occ + (int64_t)E * nA + (o - aoA)) * K2max + p];
+      }
+    }
+    if (tf32) {
+      ((float *)dstv)[i] = ptx::tf32_round((float)x);
+      continue;
+    }
+    __nv_bfloat16 *dst = (__nv_bfloat16 *)dstv;
+    const __nv_bfloat16 hi = __double2bfloat16(x);
+    dst[r * 2 * K2c + q] = hi;
+    dst[r * 2 * K2c + K2c + q] = __double2bfloat16(x - (double)__bfloat162float(hi));
   }
 }
 
@@ -194,6 +243,62 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   std::vector<int> orb_atom(no);
   for (int A = 0; A < na; ++A)
     for (int a = ao[A]; a < ao[A + 1]; ++a) orb_atom[a] = A;
+  // the 16-orbital chunks of the reduced-precision step 2: lists L(k), their
+  // Ycat segments, the position map into the atoms' lists, and the tiles
+  // (128 chunk rows, i.e. 8 occupied states, each)
+  const int nch = (no + 15) / 16;
+  std::vector<int> lcatc, posmap, xoffc(nch, 0);
+  std::vector<GTile> t2c;
+  if (lp) {
+    std::vector<std::vector<int>> Lc(nch);
+    int kc = 0;
+    for (int k = 0; k < nch; ++k) {
+      std::vector<int> &u = Lc[k];
+      for (int o = 16 * k, last = -1; o < std::min(no, 16 * k + 16); ++o) {
+        if (orb_atom[o] == last) continue;
+        last = orb_atom[o];
+        u.insert(u.end(), L[last].begin(), L[last].end());
+      }
+      std::sort(u.begin(), u.end());
+      u.erase(std::unique(u.begin(), u.end()), u.end());
+      kc = std::max(kc, (int)u.size());
+    }
+    ar.K2c = round_up(std::max(kc, 1), 64);
+    ar.rows2c = (int64_t)nch * nocc * 16;
+    posmap.assign((size_t)nch * 16 * ar.K2c, -1);
+    for (int k = 0; k < nch; ++k) {
+      const int xo = (int)lcatc.size();
+      for (int mu : Lc[k]) lcatc.push_back(mu);
+      while (lcatc.size() % 64) lcatc.push_back(-1);
+      for (int c16 = 0; c16 < 16 && 16 * k + c16 < no; ++c16) {
+        const std::vector<int> &LA = L[orb_atom[16 * k + c16]];   // increasing product order
+        for (int q = 0; q < (int)Lc[k].size(); ++q) {
+          auto it = std::lower_bound(LA.begin(), LA.end(), Lc[k][q]);
+          if (it != LA.end() && *it == Lc[k][q])
+            posmap[((size_t)k * 16 + c16) * ar.K2c + q] = (int)(it - LA.begin());
+        }
+      }
+      xoffc[k] = xo;
+    }
+    // tile order: bands of kBand consecutive chunks; within a band the
+    // 128-row blocks (8 occupied states) run block by block across the
+    // band's chunks, so that the 32-byte runs the band writes into one beta^T
+    // row (16 kBand orbitals) are written close together in time and leave
+    // L2 as whole lines; the band's Ycat segments stay in L2 meanwhile
+    constexpr int kBand = 16;
+    const int rows = nocc * 16;
+    for (int b0 = 0; b0 < nch; b0 += kBand)
+      for (int m = 0; m < rows; m += 128)
+        for (int k = b0; k < std::min(nch, b0 + kBand); ++k) {
+          if (Lc[k].empty()) continue;   // no product on the chunk's atoms: beta stays zero
+          t2c.push_back(GTile{k * rows + m, xoffc[k], ((int)Lc[k].size() + 63) / 64,
+                              std::min(128, rows - m), k, 0, 0, 0});
+        }
+    ar.kcat2c = std::max((int)lcatc.size(), 64);
+    while ((int)lcatc.size() < ar.kcat2c) lcatc.push_back(-1);
+    ar.n_tiles2c = (int)t2c.size();
+    if (t2c.empty()) t2c.push_back(GTile{0, 0, 0, 0, 0, 0, 0, 0});
+  }
 
   cudaError_t e = cudaSuccess;
   auto up = [&](void **p, const void *src, size_t bytes) {
@@ -219,6 +324,14 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   up((void **)&ar.pos5, pos5.data(), pos5.size() * sizeof(int2));
   up((void **)&ar.xoff5, xoff5.data(), xoff5.size() * sizeof(int));
   up((void **)&ar.orb_atom, orb_atom.data(), orb_atom.size() * sizeof(int));
+  int *posmap_d = nullptr;   // set-up only (freed below)
+  if (lp) {
+    up((void **)&ar.tiles2c, t2c.data(), t2c.size() * sizeof(GTile));
+    up((void **)&ar.lcatc, lcatc.data(), lcatc.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&posmap_d, posmap.size() * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(posmap_d, posmap.data(), posmap.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
   // product info in Vpad (block) order: blk_prod[q] = mu
   int *rowoff5_d = nullptr;
   int4 *pinfo_d = nullptr;
@@ -245,22 +358,23 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   if (lp) {
     ar.lp = true;
     __nv_bfloat16 *q2 = nullptr, *q5 = nullptr, *qy = nullptr, *qg = nullptr;
-    al((void **)&q2, n2 * 2 * sizeof(__nv_bfloat16));
+    al((void **)&q2, (size_t)ar.rows2c * 2 * ar.K2c * sizeof(__nv_bfloat16));
     al((void **)&q5, n5 * 2 * sizeof(__nv_bfloat16));
-    al((void **)&qy, (size_t)ncap * 2 * ar.kcat2 * sizeof(__nv_bfloat16));
+    al((void **)&qy, (size_t)ncap * 2 * ar.kcat2c * sizeof(__nv_bfloat16));
     al((void **)&qg, (size_t)ncap * 2 * ar.kcat5 * sizeof(__nv_bfloat16));
     al((void **)&ar.P2f, (size_t)rows5 * ar.ldp * sizeof(float));
     if (e == cudaSuccess) {
-      split_dense_kernel<<<152 * 8, 256, 0, st>>>(a2, ar.rows2, ar.K2max, q2, ar.tf32);
+      alpha_chunk_kernel<<<152 * 8, 256, 0, st>>>(ar.rows2c, ar.K2c, nocc, no, ar.K2max, sys.aoff,
+                                                  ar.orb_atom, posmap_d, a2, q2, ar.tf32);
       split_dense_kernel<<<152 * 8, 256, 0, st>>>(a5, rows5, ar.K5max, q5, ar.tf32);
       e = cudaGetLastError();
     }
     // Gcat pads (never written) must read as zero
     if (e == cudaSuccess)
       e = cudaMemsetAsync(qg, 0, (size_t)ncap * 2 * ar.kcat5 * sizeof(__nv_bfloat16), st);
-    if (e == cudaSuccess) e = make_operand_map(ar.a2, q2, ar.rows2, ar.K2max, 128, ar.tf32);
+    if (e == cudaSuccess) e = make_operand_map(ar.a2, q2, ar.rows2c, ar.K2c, 128, ar.tf32);
     if (e == cudaSuccess) e = make_operand_map(ar.a5, q5, rows5, ar.K5max, 128, ar.tf32);
-    if (e == cudaSuccess) e = make_operand_map(ar.ycat, qy, ncap, ar.kcat2, 128, ar.tf32);
+    if (e == cudaSuccess) e = make_operand_map(ar.ycat, qy, ncap, ar.kcat2c, 128, ar.tf32);
     if (e == cudaSuccess) e = make_operand_map(ar.gcat, qg, ncap, ar.kcat5, 128, ar.tf32);
     ar.ycat_q = qy;
     ar.gcat_q = qg;
@@ -291,18 +405,19 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(a2);
   cudaFree(a5);
+  cudaFree(posmap_d);
   return e;
 }
 
 cudaError_t launch_alpha_gather_lp(cudaStream_t st, const AlphaRoute &ar, int ncols, const void *Y,
                                    bool y_f64, int64_t ld, const int *dcnt) {
-  const int g = grid_for((int64_t)ncols * ar.kcat2, 256);
+  const int g = grid_for((int64_t)ncols * ar.kcat2c, 256);
   __nv_bfloat16 *dst = ar.ycat_q;
   if (y_f64)
-    gather_split_kernel<double><<<g, 256, 0, st>>>(ncols, ar.kcat2, ar.lcat, (const double *)Y, ld,
-                                                   dst, ar.tf32, dcnt);
+    gather_split_kernel<double><<<g, 256, 0, st>>>(ncols, ar.kcat2c, ar.lcatc, (const double *)Y,
+                                                   ld, dst, ar.tf32, dcnt);
   else
-    gather_split_kernel<float><<<g, 256, 0, st>>>(ncols, ar.kcat2, ar.lcat, (const float *)Y, ld,
+    gather_split_kernel<float><<<g, 256, 0, st>>>(ncols, ar.kcat2c, ar.lcatc, (const float *)Y, ld,
                                                   dst, ar.tf32, dcnt);
   return cudaGetLastError();
 }

@@ -20,11 +20,14 @@
 //     kStoreF32      plain float32 C^T
 //     kDscaleSplit   the D(omega) scaling of eq. response-mat on (re, im)
 //                    column pairs, written back as split bf16 for the next GEMM
-//     kBetaTSplit    step 2 on the stored transition vertex: beta^T, split bf16
+//                    (E-major input columns, slot-major output rows)
+//     kBetaChunkSplit step 2 on the stored transition vertex (16-orbital
+//                    chunks, right-hand-side columns as M): beta^T, split
+//                    bf16, one 32-byte run per thread and plane
 //     kGammaCatSplit transform 2 into the per-atom Gcat rows, split bf16
 //     kPartialF32    step 5 partial sums, float32
 // Grouped products take a tile table (per-atom operands: A rows, B K offset
-// and length per 128-row tile).  Every mbarrier wait is bounded by a
+// and length per 128-row tile; for step 2, B rows and the A K offset).  Every mbarrier wait is bounded by a
 // wall-clock limit; on expiry the CTA records an error code, stops issuing
 // work, waits (bounded) for its copies in flight and still frees its TMEM.
 #include <cuda.h>
@@ -131,19 +134,32 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
         if (n < N) ep.outF[(int64_t)m * ep.ldo + n] = v[j];
       }
     }
-  } else if (EPI == kBetaTSplit) {
-    // row m = (atom A, E, c) of the step-2 operand; column n = 2 s + p:
-    // beta^T row (s n_occ + E) 2 + p, column ao_A + c
-    if (lr < rows_valid) {
-      const int aoA = ep.aoff[atom], nA = ep.aoff[atom + 1] - aoA;
-      const int r = m - aoA * ep.n_occ, E = r / nA, c = r - E * nA;
+  } else if (EPI == kBetaChunkSplit) {
+    // row m = column 2 s + p of the right-hand sides; columns n0 + j0 ..
+    // n0 + j0 + 15 = the orbitals 16 k .. 16 k + 15 (k = atom, the chunk) of
+    // one occupied state E: one 32-byte run of the beta^T row E M + m per
+    // plane (N: the end of the tile's valid columns; M: the live columns).
+    // The rows are E-major so that the rows one tile writes lie together
+    // (slot-major rows put each of its 64 slots in another memory page)
+    if (m < M && n0 + j0 < N) {
+      const int E = ((n0 + j0) >> 4) - atom * ep.n_occ;
+      const int64_t row = (int64_t)E * M + m;
+      const int64_t at = row * operand_ld<TF>(ep) + 16 * (int64_t)atom;
+      if (TF) {
+        float4 *dst = (float4 *)((float *)ep.outB + at);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int n = n0 + j0 + j;
-        if (n < N) {
-          const int64_t row = ((int64_t)(n >> 1) * ep.n_occ + E) * 2 + (n & 1);
-          put_operand<TF>(ep.outB, row * operand_ld<TF>(ep) + aoA + c, ep.lo_off, v[j]);
-        }
+        for (int q = 0; q < 4; ++q)
+          dst[q] = make_float4(tf32_round(v[4 * q]), tf32_round(v[4 * q + 1]),
+                               tf32_round(v[4 * q + 2]), tf32_round(v[4 * q + 3]));
+      } else {
+        __align__(16) __nv_bfloat16 h[16], l[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) split_bf16(v[j], h[j], l[j]);
+        __nv_bfloat16 *dst = (__nv_bfloat16 *)ep.outB + at;
+        *(uint4 *)dst = *(const uint4 *)h;
+        *(uint4 *)(dst + 8) = *(const uint4 *)(h + 8);
+        *(uint4 *)(dst + ep.lo_off) = *(const uint4 *)l;
+        *(uint4 *)(dst + ep.lo_off + 8) = *(const uint4 *)(l + 8);
       }
     }
   } else if (EPI == kGammaCatSplit) {
@@ -195,22 +211,31 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
     // formed as (omega -+ e_F) +- e_E from float (hi, lo) pairs, the
     // first precomputed in float64 per (slot, F); the rest of D in
     // float32 (its rounding, ~1e-7, is far below the split-bf16 error).
+    // The B operand (beta^T) rows, the columns n here, are E-major:
+    // n = (E hs + s) 2 + p for hs = N / (2 n_occ) live slots; the output
+    // rows are slot-major, (s n_occ + E) 2 + p, the order transform 2 and
+    // its Gcat epilogue take.
     if (m < ep.rows_out) {
       const bool live = m < M;
       const float ef = (float)ep.eps, e2 = ef * ef, occ = (float)ep.occ_value;
+      const int hs = max(1, N / (2 * ep.n_occ));
       const int pair0 = (n0 + j0) >> 1;
-      const int sl0 = pair0 / ep.n_occ, E0 = pair0 - sl0 * ep.n_occ;
-      // (omega -+ e_F) of the chunk's slot as float (hi, lo) pairs,
-      // precomputed per (slot, F) for this product
+      int E = pair0 / hs, sl = pair0 - E * hs;
+      // (omega -+ e_F) of each pair's slot as float (hi, lo) pairs,
+      // precomputed per (slot, F) for this product; the first is loaded
+      // before the chunk's TMEM read
       float4 dt = di.dt;
-      int sl = sl0, E = E0;
+      int dsl = sl;
 #pragma unroll
       for (int j = 0; j < 16; j += 2) {
         const int n = n0 + j0 + j;
         if (n >= N) continue;
         float re = 0.f, im = 0.f;
         if (live) {
-          if (sl != sl0) dt = ep.dterm[(int64_t)sl * M + m];   // chunk crossing a slot
+          if (sl != dsl) {
+            dt = ep.dterm[(int64_t)sl * M + m];
+            dsl = sl;
+          }
           const float2 eE = di.eocc[E];
           const float xm = (dt.x + eE.x) + (dt.y + eE.y);
           const float xp = (dt.z - eE.x) + (dt.w - eE.y);
@@ -220,12 +245,13 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
           re = dre * v[j] - dim * v[j + 1];
           im = dre * v[j + 1] + dim * v[j];
         }
-        if (++E == ep.n_occ) {
-          E = 0;
-          ++sl;
+        const int64_t nout = ((int64_t)sl * ep.n_occ + E) * 2;
+        put_operand<TF>(ep.outB, nout * operand_ld<TF>(ep) + m, ep.lo_off, re);
+        put_operand<TF>(ep.outB, (nout + 1) * operand_ld<TF>(ep) + m, ep.lo_off, im);
+        if (++sl == hs) {
+          sl = 0;
+          ++E;
         }
-        put_operand<TF>(ep.outB, (int64_t)n * operand_ld<TF>(ep) + m, ep.lo_off, re);
-        put_operand<TF>(ep.outB, (int64_t)(n + 1) * operand_ld<TF>(ep) + m, ep.lo_off, im);
       }
     }
   }
@@ -245,13 +271,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int M, int N, int KpA, int KpB, TcEpilogue ep, int *err, const int *dcnt,
                    int mul_n, const GTile *tiles, int n_mtiles) {
-  // graph replays: columns beyond the live count are skipped (whole tiles)
-  if (dcnt) N = (int)min((int64_t)N, (int64_t)mul_n * (*dcnt));
-  const int n_ntiles = (N + TC_BN - 1) / TC_BN;
+  // graph replays: right-hand-side columns beyond the live count are
+  // skipped (whole tiles); they are the M axis of step 2, else the N axis
+  constexpr bool kChunk = EPI == kBetaChunkSplit;
+  if (dcnt) {
+    const int live = (int)min((int64_t)(kChunk ? M : N), (int64_t)mul_n * (*dcnt));
+    if (kChunk)
+      M = live;
+    else
+      N = live;
+  }
+  // step 2: n_ntiles counts the M tiles of the columns, run fastest
+  const int n_ntiles = kChunk ? (M + TC_BM - 1) / TC_BM : (N + TC_BN - 1) / TC_BN;
   // the N tiles share the columns evenly (multiples of 16, at most TC_BN):
   // tiles of one M row block then run at the same pace, so the second one
   // finds the A tile (the large operand of the K product) still in L2
-  const int tn = min(TC_BN, ((N + n_ntiles - 1) / n_ntiles + 15) & ~15);
+  const int tn = kChunk ? TC_BN : min(TC_BN, ((N + n_ntiles - 1) / n_ntiles + 15) & ~15);
   const int ksplit = ep.ksplit;
   const int n_tiles = n_mtiles * n_ntiles * ksplit;
   if ((int)blockIdx.x >= n_tiles) return;
@@ -278,8 +313,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // fastest, so consecutive CTAs (in a cluster: one GPC, one L2 partition)
   // read the same A tile, which DRAM then supplies once;
   // xa / xb: K offsets (elements) of the A and B tiles within a plane
+  // step 2 (kChunk): the table runs over the B rows (chunk rows), the M
+  // tiles of the columns fastest, so that DRAM supplies each B tile once;
+  // rows_valid is then the tile's valid B rows (columns of the output)
   auto tile_of = [&](int t, int &m0, int &xa, int &xb, int &nkb, int &rows_valid, int &atom,
                      int &n0) {
+    if (kChunk) {
+      const GTile g = tiles[t / n_ntiles];
+      m0 = (t % n_ntiles) * TC_BM;
+      xa = g.xoff;
+      xb = 0;
+      nkb = g.nkb;
+      rows_valid = g.rows;
+      atom = g.atom;
+      n0 = g.row0;
+      return;
+    }
     int mt, ks, nt;
     if (ep.ncl > 1 || tiles) {
       nt = t % n_ntiles;
@@ -471,13 +520,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         DscaleIn di;
         di.eocc = eocc;
         if (EPI == kDscaleSplit) {
-          const int sl0 = ((n0 + j0) >> 1) / ep.n_occ;
+          const int hs = max(1, N / (2 * ep.n_occ));   // live slots (E-major columns)
+          const int sl0 = ((n0 + j0) >> 1) % hs;
           di.dt = (m < M && n0 + j0 < N) ? ep.dterm[(int64_t)sl0 * M + m]
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float v[16];
         tmem_ld16(trow + (uint32_t)j0, v);
-        epilogue16<EPI, TF>(v, m, lr, rows_valid, atom, M, N, n0, j0, ep, di);
+        epilogue16<EPI, TF>(v, m, lr, rows_valid, atom, M, kChunk ? n0 + rows_valid : N, n0, j0,
+                            ep, di);
       }
       fence_before();
       __syncwarp();
@@ -581,7 +632,7 @@ template <int BN>
 void set_attr_all() {
   set_attr<kStoreF32, BN>();
   set_attr<kDscaleSplit, BN>();
-  set_attr<kBetaTSplit, BN>();
+  set_attr<kBetaChunkSplit, BN>();
   set_attr<kGammaCatSplit, BN>();
   set_attr<kPartialF32, BN>();
 }
@@ -650,7 +701,9 @@ cudaError_t launch_tc_epi(cudaStream_t st, int epi, int M, int N, const CUtensor
                           const CUtensorMap &mB, int KpA, int KpB, const TcEpilogue &ep, int *err,
                           const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
   // persistent: one CTA per SM at most, each walking its share of the tiles
-  const int64_t n_tiles = (int64_t)n_mtiles * ((N + BN - 1) / BN) * ep.ksplit;
+  const int64_t n_tiles = epi == kBetaChunkSplit
+                              ? (int64_t)n_mtiles * ((M + TC_BM - 1) / TC_BM)
+                              : (int64_t)n_mtiles * ((N + BN - 1) / BN) * ep.ksplit;
   const int grid = (int)std::min<int64_t>(n_tiles, sm_count());
   switch (epi) {
     case kStoreF32:
@@ -659,9 +712,9 @@ cudaError_t launch_tc_epi(cudaStream_t st, int epi, int M, int N, const CUtensor
     case kDscaleSplit:
       return launch_tc<kDscaleSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
                                          tiles, n_mtiles);
-    case kBetaTSplit:
-      return launch_tc<kBetaTSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
-                                        tiles, n_mtiles);
+    case kBetaChunkSplit:
+      return launch_tc<kBetaChunkSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt,
+                                                mul_n, tiles, n_mtiles);
     case kGammaCatSplit:
       return launch_tc<kGammaCatSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
                                            tiles, n_mtiles);
@@ -740,7 +793,9 @@ cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const Tc
   if (A.tf32 != B.tf32) return cudaErrorInvalidValue;
   TcEpilogue e = ep;
   e.ksplit = 1;
-  return dispatch_bn(st, epi, 0, N, A, B, e, err, dcnt, mul_n, tiles, n_tiles, bn);
+  // step 2: the N columns of the launch are the M axis (rows of A = Ycat)
+  return dispatch_bn(st, epi, epi == kBetaChunkSplit ? N : 0, N, A, B, e, err, dcnt, mul_n, tiles,
+                     n_tiles, bn);
 }
 
 }  // namespace tddft

@@ -149,7 +149,7 @@ struct GTile {
   int row0, xoff, nkb, rows, atom, pad0, pad1, pad2;
 };
 
-enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1, kBetaTSplit = 2, kGammaCatSplit = 3, kPartialF32 = 4 };
+enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1, kBetaChunkSplit = 2, kGammaCatSplit = 3, kPartialF32 = 4 };
 
 // A bf16 operand [rows][2*Kp] ([hi | lo] planes) with its TMA descriptor.
 struct TcOperand {
@@ -179,7 +179,7 @@ struct TcEpilogue {
   int split_ok = 0;                // kStoreF32: the launch may split K in two (adds into outF)
   int ksplit = 1;                  // set by the launcher
   int ncl = 1;                     // set by the launcher: > 1, clusters of ncl CTAs, one per N tile
-  const int *aoff = nullptr;       // kBetaTSplit, kGammaCatSplit
+  const int *aoff = nullptr;       // kGammaCatSplit
   const int *orb_atom = nullptr;   // kGammaCatSplit
   const int *xoff5 = nullptr;      // kGammaCatSplit
 };
@@ -195,11 +195,17 @@ cudaError_t encode_bf16_map(CUtensorMap *map, const void *base, int64_t rows, in
 cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand &B, int M, int N,
                            int epi, const TcEpilogue &ep, int *err, const int *dcnt = nullptr,
                            int mul_n = 0, int bn = 128);
-// Grouped product over a tile table (one CTA row per tile, see GTile):
-//   kBetaTSplit     A row m = (atom A, E, c) of the step-2 operand, column n =
-//                   2 s + p: beta^T split at row (s n_occ + E) 2 + p, column
-//                   ao_A + c (hi at outB[row*ldo + col], lo at + lo_off)
-//   kPartialF32     outF[m*ldo + n] for the valid rows of each tile
+// Grouped product over a tile table (see GTile):
+//   kBetaChunkSplit the table runs over the B operand (chunk rows of the
+//                   step-2 operand, atom = chunk k, rows = valid rows, xoff =
+//                   the K offset of the chunk's Ycat segment in A); A = Ycat,
+//                   its rows (the M axis, N columns of the launch, 128-row
+//                   tiles fastest) are the columns m = 2 s + p.  Column
+//                   n = (k n_occ + E) 16 + c16 of the tile: beta^T split at
+//                   row (s n_occ + E) 2 + p, columns 16 k .. 16 k + 15 (hi at
+//                   outB[row*ldo + col], lo at + lo_off), 16-byte stores
+//   kPartialF32     one tile row block per table entry (A rows, B K offset
+//                   and length); outF[m*ldo + n] for the valid rows
 // (the plain launch_gemm_tc also takes kGammaCatSplit: row m = orbital (B, b),
 // column n = (s n_occ + E) 2 + p -> Gcat split at row 2 s + p, column
 // xoff5_B + b n_occ + E.)
@@ -236,7 +242,7 @@ struct LpWork {
   __nv_bfloat16 *Xvs = nullptr;    // [n_orb][2 Kp2]    X_virt split
   __nv_bfloat16 *Zb = nullptr;     // [2S][2 KpK]       operator input, split
   float *Yt = nullptr;             // [2S][n_prod]      K z
-  __nv_bfloat16 *betaT = nullptr;  // [2 S n_occ][2 Kp1], row (s*n_occ+E)*2+p
+  __nv_bfloat16 *betaT = nullptr;  // [2 S n_occ][2 Kp1], row E*nc + 2s+p (nc live columns)
   __nv_bfloat16 *aT = nullptr;     // [2 S n_occ][2 Kp2]
   double *omega = nullptr;         // [S]
   int *err = nullptr;              // [1] device-side error code of the GEMM waits
@@ -356,11 +362,17 @@ struct AlphaRoute {
   int *xoff5 = nullptr;       // [n_atoms] Gcat segment of each atom
   int *orb_atom = nullptr;    // [n_orb]
   int ldp = 0;                // P2 row stride (2 S)
-  // split bf16 (reduced-precision operator), or tf32 rows of the same bytes
+  // split bf16 (reduced-precision operator), or tf32 rows of the same bytes;
+  // its step 2 runs over 16-orbital chunks: a2 [rows2c][K2c] with row
+  // (k n_occ + E) 16 + c16, Ycat [2S][kcat2c] in chunk segments (lcatc)
   bool lp = false;
   bool tf32 = false;
+  int K2c = 0, kcat2c = 0, n_tiles2c = 0;
+  int64_t rows2c = 0;          // 16 n_occ ceil(n_orb / 16)
+  GTile *tiles2c = nullptr;    // 128 chunk rows each; atom = chunk index
+  int *lcatc = nullptr;        // [kcat2c]
   TcOperand a2, a5, ycat, gcat;
-  __nv_bfloat16 *ycat_q = nullptr, *gcat_q = nullptr;   // [2S][2 kcat2], [2S][2 kcat5]
+  __nv_bfloat16 *ycat_q = nullptr, *gcat_q = nullptr;   // [2S][2 kcat2c], [2S][2 kcat5]
   float *P2f = nullptr;
   // emulated float64
   bool emu = false;
