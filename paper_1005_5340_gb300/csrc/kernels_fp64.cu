@@ -9,6 +9,8 @@
 //   n_mu    = sum_ab V_mu^{ab} (X_occ gamma^T)^{ab}      (step 5, blockdot.cu)
 // Complex vectors are kept as two real planes; X, V and K are real, so only
 // the D(omega) scaling mixes the planes.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace tddft {
@@ -244,29 +246,49 @@ __global__ void __launch_bounds__(BT_THREADS) beta_kernel(
 // D = n_E [1/(omega - Delta + i eps) - 1/(omega + Delta + i eps)],
 // Delta = e_F - e_E  (eq. response-mat, both orderings of the pair merged).
 // ---------------------------------------------------------------------------
+// 1 / x for x > 0 of normal range (here x is a product of two sums of
+// squares, between ~1e-10 and ~1e4): a float32 seed refined by two
+// Newton-Raphson steps y <- y + y (1 - x y), each squaring the relative
+// error (2^-23 -> 2^-46 -> below the float64 rounding).
+__device__ __forceinline__ double recip_nr(double x) {
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)x));
+  double y = (double)yf;
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+// D(omega) of one (occupied E, virtual F) pair, Delta = e_F - e_E:
+// occ [1/(omega - Delta + i eps) - 1/(omega + Delta + i eps)] from
+// xm = omega - Delta and xp = omega + Delta; the two denominators share one
+// reciprocal: 1/Am = Ap / (Am Ap), 1/Ap = Am / (Am Ap).
+__device__ __forceinline__ double2 d_factor(double xm, double xp, double eps, double occ) {
+  const double e2 = eps * eps;
+  const double Am = fma(xm, xm, e2), Ap = fma(xp, xp, e2);
+  const double q = occ * recip_nr(Am * Ap);
+  const double im2 = Ap * q, ip2 = Am * q;   // occ / Am, occ / Ap
+  return make_double2(xm * im2 - xp * ip2, eps * (ip2 - im2));
+}
+
+// a[F][(2s, 2s+1)][E] *= D_EF(omega_s): one block per (F, s) row pair, the
+// threads over E
 __global__ void dscale_kernel(int n_virt, int S, int n_occ, double occ_value,
                               const double *__restrict__ energy, const double *__restrict__ omega,
                               double eps, double *__restrict__ a, const int *__restrict__ dcnt) {
-  const int64_t total = (int64_t)n_virt * S * n_occ;
+  const int64_t row = blockIdx.x;   // F * S + s
+  const int F = (int)(row / S), s = (int)(row - (int64_t)F * S);
   const int S_act = dcnt ? min(S, *dcnt) : S;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int E = (int)(idx % n_occ);
-    const int64_t rest = idx / n_occ;
-    const int s = (int)(rest % S);
-    const int F = (int)(rest / S);
-    if (s >= S_act) continue;
-    const double delta = energy[n_occ + F] - energy[E];
-    const double w = omega[s];
-    // 1/(x + i eps) = (x - i eps) / (x^2 + eps^2)
-    const double xm = w - delta, xp = w + delta;
-    const double im2 = 1.0 / (xm * xm + eps * eps), ip2 = 1.0 / (xp * xp + eps * eps);
-    const double d_re = occ_value * (xm * im2 - xp * ip2);
-    const double d_im = occ_value * (-eps * im2 + eps * ip2);
-    const int64_t base = ((int64_t)F * 2 * S + 2 * s) * n_occ + E;
-    const double re = a[base], im = a[base + n_occ];
-    a[base] = d_re * re - d_im * im;
-    a[base + n_occ] = d_re * im + d_im * re;
+  if (F >= n_virt || s >= S_act) return;
+  const double eF = energy[n_occ + F], w = omega[s];
+  double *re_row = a + ((int64_t)F * 2 * S + 2 * s) * n_occ, *im_row = re_row + n_occ;
+  for (int E = threadIdx.x; E < n_occ; E += blockDim.x) {
+    const double delta = eF - energy[E];
+    const double2 d = d_factor(w - delta, w + delta, eps, occ_value);
+    const double re = re_row[E], im = im_row[E];
+    re_row[E] = d.x * re - d.y * im;
+    im_row[E] = d.x * im + d.y * re;
   }
 }
 
@@ -290,30 +312,25 @@ __global__ void p2i_kernel(int n_rhs, int n, const double *__restrict__ in, doub
   }
 }
 
-// a[F][(2s, 2s+1)][E] = D_EF(omega_{(g0+s)/3}) * a3[F][(2k, 2k+1)][E], k = (g0+s) % 3
+// a[F][(2s, 2s+1)][E] = D_EF(omega_{(g0+s)/3}) * a3[F][(2k, 2k+1)][E], k = (g0+s) % 3:
+// one block per (F, s) row pair, the threads over E
 __global__ void rhs_expand_kernel(int n_virt, int S, int n_occ, int g0, double occ_value,
                                   const double *__restrict__ energy,
                                   const double *__restrict__ omega_all, double eps,
                                   const double *__restrict__ a3, double *__restrict__ a) {
-  const int64_t total = (int64_t)n_virt * S * n_occ;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int E = (int)(idx % n_occ);
-    const int64_t rest = idx / n_occ;
-    const int s = (int)(rest % S);
-    const int F = (int)(rest / S);
-    const int g = g0 + s, k = g % 3;
-    const double delta = energy[n_occ + F] - energy[E];
-    const double w = omega_all[g / 3];
-    const double xm = w - delta, xp = w + delta;
-    const double im2 = 1.0 / (xm * xm + eps * eps), ip2 = 1.0 / (xp * xp + eps * eps);
-    const double d_re = occ_value * (xm * im2 - xp * ip2);
-    const double d_im = occ_value * (-eps * im2 + eps * ip2);
-    const int64_t src = ((int64_t)F * 6 + 2 * k) * n_occ + E;
-    const double re = a3[src], im = a3[src + n_occ];
-    const int64_t dst = ((int64_t)F * 2 * S + 2 * s) * n_occ + E;
-    a[dst] = d_re * re - d_im * im;
-    a[dst + n_occ] = d_re * im + d_im * re;
+  const int64_t row = blockIdx.x;   // F * S + s
+  const int F = (int)(row / S), s = (int)(row - (int64_t)F * S);
+  if (F >= n_virt) return;
+  const int g = g0 + s, k = g % 3;
+  const double eF = energy[n_occ + F], w = omega_all[g / 3];
+  const double *src = a3 + ((int64_t)F * 6 + 2 * k) * n_occ;
+  double *dst = a + ((int64_t)F * 2 * S + 2 * s) * n_occ;
+  for (int E = threadIdx.x; E < n_occ; E += blockDim.x) {
+    const double delta = eF - energy[E];
+    const double2 d = d_factor(w - delta, w + delta, eps, occ_value);
+    const double re = src[E], im = src[E + n_occ];
+    dst[E] = d.x * re - d.y * im;
+    dst[E + n_occ] = d.x * im + d.y * re;
   }
 }
 
@@ -516,7 +533,7 @@ cudaError_t apply_alpha_emulated(cudaStream_t st, const DevSystem &sys, OpWork &
   }
   {
     Scope sc(wk.timer, st, kcDscale, 0.0);
-    dscale_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
+    dscale_kernel<<<(unsigned)std::max<int64_t>(1, (int64_t)sys.n_virt * S), 128, 0, st>>>(
         sys.n_virt, S, sys.n_occ, sys.occ_value, sys.energy, wk.omega, eps, wk.abuf, wk.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
@@ -545,7 +562,7 @@ cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &
     if (err == cudaSuccess)
       err = launch_gemm_oz(st, wk.oz->XvT, wk.oz->Bt1, sys.n_virt, n6, a3, n6, 0, wk.oz->err);
     if (err == cudaSuccess) {
-      rhs_expand_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
+      rhs_expand_kernel<<<(unsigned)std::max<int64_t>(1, (int64_t)sys.n_virt * S), 128, 0, st>>>(
           sys.n_virt, S, sys.n_occ, g0, sys.occ_value, sys.energy, omega_all, eps, a3, wk.abuf);
       err = cudaGetLastError();
     }
@@ -576,7 +593,7 @@ cudaError_t launch_rhs_formation(cudaStream_t st, const DevSystem &sys, OpWork &
   if (err != cudaSuccess) return err;
   // per right-hand side: D(omega) a_k, X_virt a, block dot
   const int64_t ncolE = (int64_t)2 * S * sys.n_occ;
-  rhs_expand_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
+  rhs_expand_kernel<<<(unsigned)std::max<int64_t>(1, (int64_t)sys.n_virt * S), 128, 0, st>>>(
       sys.n_virt, S, sys.n_occ, g0, sys.occ_value, sys.energy, omega_all, eps, a3, wk.abuf);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (wk.oz) {
@@ -660,7 +677,7 @@ cudaError_t launch_apply_operator(cudaStream_t st, const DevSystem &sys, OpWork 
   }
   {
     Scope sc(wk.timer, st, kcDscale, 0.0);
-    dscale_kernel<<<grid_for((int64_t)sys.n_virt * S * sys.n_occ, 256), 256, 0, st>>>(
+    dscale_kernel<<<(unsigned)std::max<int64_t>(1, (int64_t)sys.n_virt * S), 128, 0, st>>>(
         sys.n_virt, S, sys.n_occ, sys.occ_value, sys.energy, wk.omega, eps, wk.abuf, wk.dcnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
