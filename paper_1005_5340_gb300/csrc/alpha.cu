@@ -215,7 +215,7 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   ar.kcat5 = kcat5;
   ar.ldp = 2 * std::max(slots, 3);
   // tiles (128 rows of the per-atom operands), atom by atom
-  std::vector<GTile> t2, t5;
+  std::vector<GTile> t2, t5, t5lp;   // t5lp: 256-row entries (two M blocks per tile)
   ar.flops2 = ar.flops5 = 0.0;
   for (int A = 0; A < na; ++A) {
     const int nA = ao[A + 1] - ao[A], K = (int)L[A].size();
@@ -227,11 +227,15 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
     for (int m = 0; m < K; m += 128)
       t5.push_back(GTile{rowoff5[A] + m, xoff5[A], (rows + 63) / 64, std::min(128, K - m), A, 0,
                          0, 0});
+    for (int m = 0; m < K; m += 256)
+      t5lp.push_back(GTile{rowoff5[A] + m, xoff5[A], (rows + 63) / 64, std::min(256, K - m), A, 0,
+                           0, 0});
     ar.flops2 += 2.0 * rows * K;
     ar.flops5 += 2.0 * rows * K;
   }
   ar.n_tiles2 = (int)t2.size();
   ar.n_tiles5 = (int)t5.size();
+  ar.n_tiles5lp = (int)t5lp.size();
   ar.max_nkb2 = ar.K2max / 64;
   ar.max_nkb5 = ar.K5max / 64;
   std::vector<int2> pos5(np);
@@ -317,9 +321,11 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
     // no products at all: keep one empty tile list
     t2.push_back(GTile{0, 0, 0, 0, 0, 0, 0, 0});
     t5.push_back(GTile{0, 0, 0, 0, 0, 0, 0, 0});
+    t5lp.push_back(GTile{0, 0, 0, 0, 0, 0, 0, 0});
   }
   up((void **)&ar.tiles2, t2.data(), t2.size() * sizeof(GTile));
   up((void **)&ar.tiles5, t5.data(), t5.size() * sizeof(GTile));
+  if (lp) up((void **)&ar.tiles5lp, t5lp.data(), t5lp.size() * sizeof(GTile));
   up((void **)&ar.lcat, lcat.data(), lcat.size() * sizeof(int));
   up((void **)&ar.pos5, pos5.data(), pos5.size() * sizeof(int2));
   up((void **)&ar.xoff5, xoff5.data(), xoff5.size() * sizeof(int));

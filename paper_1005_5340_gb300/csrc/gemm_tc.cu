@@ -57,6 +57,19 @@ template <int BN> struct TcShape {
   static constexpr int STAGES = BN == 64 ? 4 : (BN == 128 ? 3 : 2);
   static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256 + TC_EOCC_MAX * 8;
 };
+// Per epilogue: step 5 (kPartialF32) runs two M blocks per tile (M2): the
+// tile's B (the atom's Gcat rows) is loaded once for 256 vertex rows, whose
+// two A tiles share the stage; two accumulators per TMEM buffer (4 BN
+// columns, so BN <= 128) and two stages.
+template <int EPI, int BN> struct TcCfg {
+  static constexpr bool M2 = EPI == kPartialF32;
+  static constexpr uint32_t B_BYTES = TcShape<BN>::B_BYTES;
+  static constexpr uint32_t STAGE_BYTES = (M2 ? 4 : 2) * TC_A_BYTES + 2 * B_BYTES;
+  static constexpr int STAGES = M2 ? 2 : TcShape<BN>::STAGES;
+  static constexpr int ACC = M2 ? 2 * BN : BN;                  // TMEM columns per buffer
+  static constexpr int TCOLS = 2 * ACC > 512 ? 512 : 2 * ACC;   // allocated (M2 needs BN <= 128)
+  static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256 + TC_EOCC_MAX * 8;
+};
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
   hi = __float2bfloat16_rn(x);
@@ -290,9 +303,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int ksplit = ep.ksplit;
   const int n_tiles = n_mtiles * n_ntiles * ksplit;
   if ((int)blockIdx.x >= n_tiles) return;
-  constexpr uint32_t SB = TcShape<TC_BN>::STAGE_BYTES;
-  constexpr int NS = TcShape<TC_BN>::STAGES;
-  constexpr uint32_t B_BYTES = TcShape<TC_BN>::B_BYTES;
+  constexpr bool kM2 = TcCfg<EPI, TC_BN>::M2;
+  constexpr uint32_t SB = TcCfg<EPI, TC_BN>::STAGE_BYTES;
+  constexpr int NS = TcCfg<EPI, TC_BN>::STAGES;
+  constexpr uint32_t B_BYTES = TcCfg<EPI, TC_BN>::B_BYTES;
+  constexpr int ACC = TcCfg<EPI, TC_BN>::ACC;
+  constexpr int TCOLS = TcCfg<EPI, TC_BN>::TCOLS;
+  // B tile offset in a stage (after the one or two A tiles, both planes)
+  constexpr uint32_t B_OFF = (kM2 ? 4 : 2) * TC_A_BYTES;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned stage ring (required by the 128-byte swizzle atoms)
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -378,7 +396,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tslot)),
-                 "r"(2 * TC_BN));
+                 "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -414,9 +432,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           mbar_expect_tx(&full[s], SB);
           tma_load_2d(st, &mapA, &full[s], xa + kb * TC_BK, m0);                      // A_hi / A_0
           tma_load_2d(st + TC_A_BYTES, &mapA, &full[s], secA + xa + kb * TC_BK, m0);  // A_lo / A_1
-          tma_load_2d(st + 2 * TC_A_BYTES, &mapB, &full[s], xoff + kb * TC_BK, n0);   // B_hi / B_0
-          tma_load_2d(st + 2 * TC_A_BYTES + B_BYTES, &mapB, &full[s], secB + xoff + kb * TC_BK,
-                      n0);                                                             // B_lo / B_1
+          if (kM2) {   // the second M block's A tile
+            tma_load_2d(st + 2 * TC_A_BYTES, &mapA, &full[s], xa + kb * TC_BK, m0 + TC_BM);
+            tma_load_2d(st + 3 * TC_A_BYTES, &mapA, &full[s], secA + xa + kb * TC_BK,
+                        m0 + TC_BM);
+          }
+          tma_load_2d(st + B_OFF, &mapB, &full[s], xoff + kb * TC_BK, n0);           // B_hi / B_0
+          tma_load_2d(st + B_OFF + B_BYTES, &mapB, &full[s], secB + xoff + kb * TC_BK,
+                      n0);                                                         // B_lo / B_1
         }
       }
       // copies in flight: the last NS stages issued must land before exit
@@ -445,7 +468,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           fence_after();
         }
-        const uint32_t d = tmem + (uint32_t)(buf * TC_BN);
+        const uint32_t d = tmem + (uint32_t)(buf * ACC);
+        // M2: the second M block (accumulator d + TC_BN) only where the
+        // table entry has rows there
+        const int nblk = (kM2 && rv > TC_BM) ? 2 : 1;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % NS;
           if (!mbar_wait(&full[s], (uint32_t)(g / NS) & 1u, lim)) {
@@ -455,24 +481,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             break;
           }
           fence_after();
-          const uint32_t ahi = base + (uint32_t)s * SB, alo = ahi + TC_A_BYTES;
-          const uint32_t bhi = ahi + 2 * TC_A_BYTES, blo = bhi + B_BYTES;
-          if (TF) {
+          const uint32_t bhi = base + (uint32_t)s * SB + B_OFF, blo = bhi + B_BYTES;
+          for (int blk = 0; blk < nblk; ++blk) {
+            const uint32_t ahi = base + (uint32_t)s * SB + (uint32_t)blk * 2 * TC_A_BYTES,
+                           alo = ahi + TC_A_BYTES;
+            const uint32_t db = d + (uint32_t)(blk * TC_BN);
+            if (TF) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const uint32_t a0 = h ? alo : ahi, b0 = h ? blo : bhi;
+              for (int h = 0; h < 2; ++h) {
+                const uint32_t a0 = h ? alo : ahi, b0 = h ? blo : bhi;
 #pragma unroll
-              for (int k = 0; k < 4; ++k)
-                mma_tf32(d, desc_sw128(a0 + 32 * k), desc_sw128(b0 + 32 * k), idesc,
-                         (kb > 0 || h > 0 || k > 0) ? 1u : 0u);
-            }
-          } else {
+                for (int k = 0; k < 4; ++k)
+                  mma_tf32(db, desc_sw128(a0 + 32 * k), desc_sw128(b0 + 32 * k), idesc,
+                           (kb > 0 || h > 0 || k > 0) ? 1u : 0u);
+              }
+            } else {
 #pragma unroll
-            for (int k = 0; k < TC_BK / 16; ++k) {
-              mma_bf16(d, desc_sw128(ahi + 32 * k), desc_sw128(bhi + 32 * k), idesc,
-                       (kb > 0 || k > 0) ? 1u : 0u);
-              mma_bf16(d, desc_sw128(ahi + 32 * k), desc_sw128(blo + 32 * k), idesc, 1u);
-              mma_bf16(d, desc_sw128(alo + 32 * k), desc_sw128(bhi + 32 * k), idesc, 1u);
+              for (int k = 0; k < TC_BK / 16; ++k) {
+                mma_bf16(db, desc_sw128(ahi + 32 * k), desc_sw128(bhi + 32 * k), idesc,
+                         (kb > 0 || k > 0) ? 1u : 0u);
+                mma_bf16(db, desc_sw128(ahi + 32 * k), desc_sw128(blo + 32 * k), idesc, 1u);
+                mma_bf16(db, desc_sw128(alo + 32 * k), desc_sw128(bhi + 32 * k), idesc, 1u);
+              }
             }
           }
           mma_commit(&empty[s]);
@@ -511,11 +541,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       fence_after();
-      const int m = m0 + lr;
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN);
       // the two warps of a lane quadrant take the two halves of the columns
+      // (M2: the two M blocks, all columns each)
+      const int blk = (kM2 && warp >= 6) ? 1 : 0;
+      const int m = m0 + blk * TC_BM + lr;
+      const int rv_blk = kM2 ? min(TC_BM, rows_valid - blk * TC_BM) : rows_valid;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC + blk * TC_BN);
       const int half = ((tn >> 4) + 1) / 2 * 16;
-      const int j_lo = (warp >= 6) ? half : 0, j_hi = (warp >= 6) ? tn : half;
+      const int j_lo = kM2 ? 0 : ((warp >= 6) ? half : 0);
+      const int j_hi = kM2 ? tn : ((warp >= 6) ? tn : half);
       for (int j0 = j_lo; j0 < j_hi; j0 += 16) {
         DscaleIn di;
         di.eocc = eocc;
@@ -527,8 +561,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         float v[16];
         tmem_ld16(trow + (uint32_t)j0, v);
-        epilogue16<EPI, TF>(v, m, lr, rows_valid, atom, M, kChunk ? n0 + rows_valid : N, n0, j0,
-                            ep, di);
+        epilogue16<EPI, TF>(v, m, lr, rv_blk, atom, M, kChunk ? n0 + rows_valid : N, n0, j0, ep,
+                            di);
       }
       fence_before();
       __syncwarp();
@@ -540,7 +574,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(2 * TC_BN));
+                 "r"(TCOLS));
   }
 }
 
@@ -622,10 +656,13 @@ cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int 
 namespace {
 template <int EPI, int BN>
 void set_attr() {
+  // (two M blocks need BN <= 128; the other instances are never launched,
+  // and a refused attribute would leave an error for the next check)
+  if constexpr (TcCfg<EPI, BN>::M2 && BN > 128) return;
   cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TcShape<BN>::SMEM);
+                       (int)TcCfg<EPI, BN>::SMEM);
   cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TcShape<BN>::SMEM);
+                       (int)TcCfg<EPI, BN>::SMEM);
 }
 
 template <int BN>
@@ -664,7 +701,7 @@ cudaError_t launch_tc(cudaStream_t st, int grid, const CUtensorMap &mA, const CU
                       int M, int N, int KpA, int KpB, const TcEpilogue &ep, int *err,
                       const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
   if (ep.ncl <= 1) {
-    gemm_tc_kernel<EPI, BN, TF><<<grid, TC_THREADS, TcShape<BN>::SMEM, st>>>(
+    gemm_tc_kernel<EPI, BN, TF><<<grid, TC_THREADS, TcCfg<EPI, BN>::SMEM, st>>>(
         mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n, tiles, n_mtiles);
     return cudaGetLastError();
   }
@@ -672,7 +709,7 @@ cudaError_t launch_tc(cudaStream_t st, int grid, const CUtensorMap &mA, const CU
   // (a persistent CTA that waited for a slot would run its tiles last)
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(TC_THREADS);
-  cfg.dynamicSmemBytes = TcShape<BN>::SMEM;
+  cfg.dynamicSmemBytes = TcCfg<EPI, BN>::SMEM;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -791,6 +828,7 @@ cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const Tc
   tc_init_attributes();
   if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
   if (A.tf32 != B.tf32) return cudaErrorInvalidValue;
+  if (epi == kPartialF32 && bn > 128) return cudaErrorInvalidValue;   // two M blocks: 4 bn TMEM columns
   TcEpilogue e = ep;
   e.ksplit = 1;
   // step 2: the N columns of the launch are the M axis (rows of A = Ycat)

@@ -204,8 +204,9 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
 //                   n = (k n_occ + E) 16 + c16 of the tile: beta^T split at
 //                   row (s n_occ + E) 2 + p, columns 16 k .. 16 k + 15 (hi at
 //                   outB[row*ldo + col], lo at + lo_off), 16-byte stores
-//   kPartialF32     one tile row block per table entry (A rows, B K offset
-//                   and length); outF[m*ldo + n] for the valid rows
+//   kPartialF32     one table entry per tile (A rows, up to 256: two M
+//                   blocks sharing the B tile; B K offset and length);
+//                   outF[m*ldo + n] for the valid rows
 // (the plain launch_gemm_tc also takes kGammaCatSplit: row m = orbital (B, b),
 // column n = (s n_occ + E) 2 + p -> Gcat split at row 2 s + p, column
 // xoff5_B + b n_occ + E.)
@@ -371,6 +372,8 @@ struct AlphaRoute {
   int64_t rows2c = 0;          // 16 n_occ ceil(n_orb / 16)
   GTile *tiles2c = nullptr;    // 128 chunk rows each; atom = chunk index
   int *lcatc = nullptr;        // [kcat2c]
+  GTile *tiles5lp = nullptr;   // step 5 of the reduced-precision operator: 256-row entries
+  int n_tiles5lp = 0;
   TcOperand a2, a5, ycat, gcat;
   __nv_bfloat16 *ycat_q = nullptr, *gcat_q = nullptr;   // [2S][2 kcat2c], [2S][2 kcat5]
   float *P2f = nullptr;

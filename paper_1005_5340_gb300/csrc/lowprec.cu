@@ -291,7 +291,7 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     TcEpilogue e5;
     e5.outF = ar.P2f;
     e5.ldo = ar.ldp;
-    err = launch_gemm_tc_grouped(st, ar.a5, ar.gcat, ar.tiles5, ar.n_tiles5, ncols, kPartialF32,
+    err = launch_gemm_tc_grouped(st, ar.a5, ar.gcat, ar.tiles5lp, ar.n_tiles5lp, ncols, kPartialF32,
                                  e5, lp.err, lp.dcnt, 2);
     if (err != cudaSuccess) return err;
   }
