@@ -10,17 +10,18 @@
 // gives alpha_mu^{aE} = sum_b V^{ab} X_b^E and alpha_mu^{bE} = sum_a V^{ab} X_a^E;
 // a local product (A, A) has alpha_mu^{aE} = sum_{a'} V^{aa'} X_a'^E.
 //
-// The reduced-precision step 2 runs over 16-orbital chunks of the orbital
-// axis instead of atoms: chunk k holds orbitals 16k .. 16k+15 (of one or
-// more atoms), its product list L(k) is the union of their lists L_A, and
-// its operand row (k, E, c16) holds alpha^{cE} of orbital c = 16k + c16 on
-// L(k), zero on the products outside L_{A(c)}.  The product runs with the
-// right-hand-side columns as the M axis, so that each thread of its
-// epilogue holds the 16 orbitals of one (k, E): one whole 32-byte sector of
-// a beta^T row per plane, written with 16-byte stores.  (A per-atom segment
-// of 13 orbitals is 26 bytes and fills no sector; its 2-byte stores made
-// step 2 store bound.)  The union roughly doubles the step's MMA work,
-// which stays below the store time it saves.
+// The reduced-precision step 2 runs over W-orbital chunks of the orbital
+// axis instead of atoms (W = kStep2Chunk, a multiple of 16): chunk k holds
+// orbitals Wk .. Wk+W-1 (of one or more atoms), its product list L(k) is
+// the union of their lists L_A, and its operand row (k, E, cw) holds
+// alpha^{cE} of orbital c = Wk + cw on L(k), zero on the products outside
+// L_{A(c)}.  The product runs with the right-hand-side columns as the M
+// axis, so that each thread of its epilogue holds 16 consecutive orbitals
+// of one (k, E): one whole 32-byte sector of a beta^T row per plane,
+// written with 16-byte stores.  (A per-atom segment of 13 orbitals is 26
+// bytes and fills no sector; its 2-byte stores made step 2 store bound.)
+// The union adds MMA work (2x for W = 16) and vertex bytes, both below the
+// store time it saves.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -96,8 +97,8 @@ __global__ void split_dense_kernel(const double *__restrict__ src, int64_t rows,
 }
 
 // The chunk operand of the reduced-precision step 2: row r = (k n_occ + E)
-// 16 + c16, column q < K2c holds alpha of orbital o = 16k + c16 on the
-// product at position q of L(k) (posmap[k][c16][q]: its position in
+// W + cw, column q < K2c holds alpha of orbital o = Wk + cw on the
+// product at position q of L(k) (posmap[k][cw][q]: its position in
 // L_{A(o)}, or -1 where it is not in that list; zero rows past n_orb), split
 // bf16 [rows][2 K2c] or tf32 [rows][K2c].
 __global__ void alpha_chunk_kernel(int64_t rows, int K2c, int n_occ, int n_orb, int K2max,
@@ -109,13 +110,14 @@ __global__ void alpha_chunk_kernel(int64_t rows, int K2c, int n_occ, int n_orb, 
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / K2c;
     const int q = (int)(i - r * K2c);
-    const int c16 = (int)(r & 15);
-    const int64_t kE = r >> 4;
+    constexpr int W = kStep2Chunk;
+    const int cw = (int)(r % W);
+    const int64_t kE = r / W;
     const int k = (int)(kE / n_occ), E = (int)(kE - (int64_t)k * n_occ);
-    const int o = 16 * k + c16;
+    const int o = W * k + cw;
     double x = 0.0;
     if (o < n_orb) {
-      const int p = posmap[((int64_t)k * 16 + c16) * K2c + q];
+      const int p = posmap[((int64_t)k * W + cw) * K2c + q];
       if (p >= 0) {
         const int A = orb_atom[o], aoA = aoff[A], nA = aoff[A + 1] - aoA;
         x = a2[((int64_t)aoA * n_occ + (int64_t)E * nA + (o - aoA)) * K2max + p];
@@ -247,10 +249,11 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   std::vector<int> orb_atom(no);
   for (int A = 0; A < na; ++A)
     for (int a = ao[A]; a < ao[A + 1]; ++a) orb_atom[a] = A;
-  // the 16-orbital chunks of the reduced-precision step 2: lists L(k), their
+  // the W-orbital chunks of the reduced-precision step 2: lists L(k), their
   // Ycat segments, the position map into the atoms' lists, and the tiles
-  // (128 chunk rows, i.e. 8 occupied states, each)
-  const int nch = (no + 15) / 16;
+  // (128 chunk rows, i.e. 128 / W occupied states, each)
+  constexpr int W = kStep2Chunk;
+  const int nch = (no + W - 1) / W;
   std::vector<int> lcatc, posmap, xoffc(nch, 0);
   std::vector<GTile> t2c;
   if (lp) {
@@ -258,7 +261,7 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
     int kc = 0;
     for (int k = 0; k < nch; ++k) {
       std::vector<int> &u = Lc[k];
-      for (int o = 16 * k, last = -1; o < std::min(no, 16 * k + 16); ++o) {
+      for (int o = W * k, last = -1; o < std::min(no, W * k + W); ++o) {
         if (orb_atom[o] == last) continue;
         last = orb_atom[o];
         u.insert(u.end(), L[last].begin(), L[last].end());
@@ -268,29 +271,29 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
       kc = std::max(kc, (int)u.size());
     }
     ar.K2c = round_up(std::max(kc, 1), 64);
-    ar.rows2c = (int64_t)nch * nocc * 16;
-    posmap.assign((size_t)nch * 16 * ar.K2c, -1);
+    ar.rows2c = (int64_t)nch * nocc * W;
+    posmap.assign((size_t)nch * W * ar.K2c, -1);
     for (int k = 0; k < nch; ++k) {
       const int xo = (int)lcatc.size();
       for (int mu : Lc[k]) lcatc.push_back(mu);
       while (lcatc.size() % 64) lcatc.push_back(-1);
-      for (int c16 = 0; c16 < 16 && 16 * k + c16 < no; ++c16) {
-        const std::vector<int> &LA = L[orb_atom[16 * k + c16]];   // increasing product order
+      for (int cw = 0; cw < W && W * k + cw < no; ++cw) {
+        const std::vector<int> &LA = L[orb_atom[W * k + cw]];   // increasing product order
         for (int q = 0; q < (int)Lc[k].size(); ++q) {
           auto it = std::lower_bound(LA.begin(), LA.end(), Lc[k][q]);
           if (it != LA.end() && *it == Lc[k][q])
-            posmap[((size_t)k * 16 + c16) * ar.K2c + q] = (int)(it - LA.begin());
+            posmap[((size_t)k * W + cw) * ar.K2c + q] = (int)(it - LA.begin());
         }
       }
       xoffc[k] = xo;
     }
     // tile order: bands of kBand consecutive chunks; within a band the
-    // 128-row blocks (8 occupied states) run block by block across the
+    // 128-row blocks (128 / W occupied states) run block by block across the
     // band's chunks, so that the 32-byte runs the band writes into one beta^T
-    // row (16 kBand orbitals) are written close together in time and leave
+    // row (W kBand orbitals) are written close together in time and leave
     // L2 as whole lines; the band's Ycat segments stay in L2 meanwhile
     constexpr int kBand = 16;
-    const int rows = nocc * 16;
+    const int rows = nocc * W;
     for (int b0 = 0; b0 < nch; b0 += kBand)
       for (int m = 0; m < rows; m += 128)
         for (int k = b0; k < std::min(nch, b0 + kBand); ++k) {

@@ -149,15 +149,17 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
     }
   } else if (EPI == kBetaChunkSplit) {
     // row m = column 2 s + p of the right-hand sides; columns n0 + j0 ..
-    // n0 + j0 + 15 = the orbitals 16 k .. 16 k + 15 (k = atom, the chunk) of
-    // one occupied state E: one 32-byte run of the beta^T row E M + m per
-    // plane (N: the end of the tile's valid columns; M: the live columns).
+    // n0 + j0 + 15 = 16 orbitals W k + cw .. of chunk k (= atom; W =
+    // kStep2Chunk) and one occupied state E: one 32-byte run of the beta^T
+    // row E M + m per plane (N: the end of the tile's valid columns; M: the
+    // live columns).
     // The rows are E-major so that the rows one tile writes lie together
     // (slot-major rows put each of its 64 slots in another memory page)
     if (m < M && n0 + j0 < N) {
-      const int E = ((n0 + j0) >> 4) - atom * ep.n_occ;
+      const int E = (n0 + j0) / kStep2Chunk - atom * ep.n_occ;
+      const int cw = (n0 + j0) % kStep2Chunk;
       const int64_t row = (int64_t)E * M + m;
-      const int64_t at = row * operand_ld<TF>(ep) + 16 * (int64_t)atom;
+      const int64_t at = row * operand_ld<TF>(ep) + (int64_t)kStep2Chunk * atom + cw;
       if (TF) {
         float4 *dst = (float4 *)((float *)ep.outB + at);
 #pragma unroll

@@ -149,6 +149,12 @@ struct GTile {
   int row0, xoff, nkb, rows, atom, pad0, pad1, pad2;
 };
 
+// Orbitals per chunk of the reduced-precision step 2 (a multiple of 16:
+// each epilogue thread writes 16 of a chunk's orbitals as one 32-byte run).
+// 16 measured fastest: 32 halves the union lists' extra MMA work but reads
+// more vertex bytes per launch, and took 2.9 against 2.0 ms per product.
+constexpr int kStep2Chunk = 16;
+
 enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1, kBetaChunkSplit = 2, kGammaCatSplit = 3, kPartialF32 = 4 };
 
 // A bf16 operand [rows][2*Kp] ([hi | lo] planes) with its TMA descriptor.

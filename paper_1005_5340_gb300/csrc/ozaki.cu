@@ -263,20 +263,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       int g = 0;
       bool ok = true;
       for (int c = 0; c < nchunks && ok; ++c) {
-        // every group of the previous chunk drained by the epilogue before
-        // the first MMA of this chunk (one wait per group, here, so that the
-        // issue loop below is straight-line code)
-        if (c > 0) {
-          for (int grp = 0; grp < S && ok; ++grp) {
-            if (!mbar_wait(&tempty[grp], (uint32_t)(c - 1) & 1u, lim)) {
-              atomicExch(a.err, 22);
-              abort_flag = 1;
-              ok = false;
-            }
-          }
-          if (!ok) break;
-          fence_after();
-        }
         const int kb1 = min(nkb, (c + 1) * cb);
         for (int kb = c * cb; kb < kb1 && ok; ++kb) {
           const bool first_kb = kb == c * cb;
@@ -291,6 +277,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               abort_flag = 1;
               ok = false;
               break;
+            }
+            // each group of the previous chunk drained by the epilogue (which
+            // drains them in order) before its first MMA of this chunk: the
+            // groups first used at step i are 2i - 1 and 2i, so the MMAs of
+            // the first groups overlap the drain of the later ones
+            if (first_kb && c > 0) {
+#pragma unroll
+              for (int grp = (i == 0 ? 0 : 2 * i - 1); grp <= 2 * i && grp < S; ++grp)
+                if (ok && !mbar_wait(&tempty[grp], (uint32_t)(c - 1) & 1u, lim)) {
+                  atomicExch(a.err, 22);
+                  abort_flag = 1;
+                  ok = false;
+                }
+              if (!ok) break;
             }
             fence_after();
             const uint32_t si = base + (uint32_t)(gi % OZ_STAGES) * OZ_STAGE_BYTES;
