@@ -38,6 +38,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <vector>
 
 #include "internal.h"
@@ -72,7 +73,8 @@ struct OzArgs {
   OzEpilogue ep;
   int vec;      // kOzC with 16-byte aligned rows: double2 stores
   const GTile *tiles;   // grouped product: one entry per M tile (NULL: plain row tiles)
-  int mgroup;           // plain tiles: M tiles per group of the L2-aware tile order
+  int mgroup;           // M tiles per group of the L2-aware tile order
+  int Mt, Nt;           // M tiles (rows / 128, or table entries) and N tiles
   int *err;
   const int *dcnt;
   int mul_n;
@@ -151,40 +153,42 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                       const __grid_constant__ CUtensorMap mapB, OzArgs a) {
   int N = a.N;
   if (a.dcnt) N = (int)min((int64_t)N, (int64_t)a.mul_n * (*a.dcnt));
-  // tile (mt, nt) of this CTA, in an L2-aware order: the M tiles (rows of
-  // A, or entries of the tile table) in groups of a.mgroup (A panels that fit
-  // in L2 together), every N tile of a group before the next group, the M
-  // tile fastest within it, so that each A panel is read from DRAM about once
-  int mt, nt;
-  {
-    const int Mt = gridDim.x, Nt = gridDim.y, G = a.mgroup;
-    const int lin = blockIdx.x + Mt * blockIdx.y;
-    const int g = lin / (G * Nt), r = lin - g * (G * Nt);
-    const int Gg = min(G, Mt - g * G);
-    mt = g * G + r % Gg;
-    nt = r / Gg;
-  }
   constexpr int OZ_STAGES = OzShape<BN>::STAGES;
   constexpr uint32_t OZ_STAGE_BYTES = OzShape<BN>::STAGE_BYTES;
   constexpr int OZ_EPI_COLS = OzShape<BN>::EPI_COLS;
-  const int n0 = nt * BN;
-  if (n0 >= N) return;
-  // this CTA's rows of A and K range of B
-  int m0, xoff, nkb, rows_valid, atom;
-  if (a.tiles) {
-    const GTile t = a.tiles[mt];
-    m0 = t.row0;
-    xoff = t.xoff;
-    nkb = t.nkb;
-    rows_valid = t.rows;
-    atom = t.atom;
-  } else {
-    m0 = mt * OZ_BM;
-    xoff = 0;
-    nkb = a.KpA / OZ_BK;
-    rows_valid = min(OZ_BM, a.M - m0);
-    atom = -1;
-  }
+  // Persistent: CTA b walks tiles t = b, b + gridDim.x, ...  Tile t -> (mt,
+  // nt) in an L2-aware order: the M tiles (rows of A, or entries of the tile
+  // table) in groups of a.mgroup (A panels that fit in L2 together), every N
+  // tile of a group before the next group, the M tile fastest within it, so
+  // that each A panel is read from DRAM about once.  Tiles past the live
+  // columns are skipped by every role alike.
+  const int Mt = a.Mt, Nt = a.Nt, n_tiles = Mt * Nt;
+  struct Tile {
+    int m0, xoff, nkb, rows_valid, atom, n0;
+  };
+  auto tile_of = [&](int t, Tile &T) -> bool {
+    const int G = a.mgroup;
+    const int g = t / (G * Nt), r = t - g * (G * Nt);
+    const int Gg = min(G, Mt - g * G);
+    const int mt = g * G + r % Gg, nt = r / Gg;
+    T.n0 = nt * BN;
+    if (T.n0 >= N) return false;
+    if (a.tiles) {
+      const GTile gt = a.tiles[mt];
+      T.m0 = gt.row0;
+      T.xoff = gt.xoff;
+      T.nkb = gt.nkb;
+      T.rows_valid = gt.rows;
+      T.atom = gt.atom;
+    } else {
+      T.m0 = mt * OZ_BM;
+      T.xoff = 0;
+      T.nkb = a.KpA / OZ_BK;
+      T.rows_valid = min(OZ_BM, a.M - T.m0);
+      T.atom = -1;
+    }
+    return true;
+  };
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
@@ -199,7 +203,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int s = S;
   const int cb = a.cb;
-  const int nchunks = (nkb + cb - 1) / cb;
   constexpr uint32_t tcols = S * BN <= 256 ? 256u : 512u;
 
   if (threadIdx.x == 0) {
@@ -227,27 +230,33 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: stage g = kb * s + i holds slice i of K block kb
+      // producer: stage g = (kb * s + i) counted over this CTA's tiles holds
+      // slice i of K block kb
       int g = 0;
       bool ok = true;
-      for (int kb = 0; kb < nkb && ok; ++kb) {
-        for (int i = 0; i < s; ++i, ++g) {
-          const int slot = g % OZ_STAGES;
-          const uint32_t ph = (uint32_t)(g / OZ_STAGES) & 1u;
-          if (!mbar_wait(&empty[slot], ph ^ 1u, lim)) {
-            atomicExch(a.err, 21);
-            abort_flag = 1;
-            ok = false;
-            break;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        Tile T;
+        if (!tile_of(t, T)) continue;
+        for (int kb = 0; kb < T.nkb && ok; ++kb) {
+          for (int i = 0; i < s; ++i, ++g) {
+            const int slot = g % OZ_STAGES;
+            const uint32_t ph = (uint32_t)(g / OZ_STAGES) & 1u;
+            if (!mbar_wait(&empty[slot], ph ^ 1u, lim)) {
+              atomicExch(a.err, 21);
+              abort_flag = 1;
+              ok = false;
+              break;
+            }
+            if (*(volatile int *)&abort_flag) {
+              ok = false;
+              break;
+            }
+            uint8_t *sa = smem + slot * OZ_STAGE_BYTES;
+            mbar_expect_tx(&full[slot], OZ_STAGE_BYTES);
+            tma_load_2d(sa, &mapA, &full[slot], i * a.KpA + kb * OZ_BK, T.m0);
+            tma_load_2d(sa + OZ_A_BYTES, &mapB, &full[slot], i * a.KpB + T.xoff + kb * OZ_BK,
+                        T.n0);
           }
-          if (*(volatile int *)&abort_flag) {
-            ok = false;
-            break;
-          }
-          uint8_t *sa = smem + slot * OZ_STAGE_BYTES;
-          mbar_expect_tx(&full[slot], OZ_STAGE_BYTES);
-          tma_load_2d(sa, &mapA, &full[slot], i * a.KpA + kb * OZ_BK, m0);
-          tma_load_2d(sa + OZ_A_BYTES, &mapB, &full[slot], i * a.KpB + xoff + kb * OZ_BK, n0);
         }
       }
       // copies in flight: the last OZ_STAGES stages issued (each the latest
@@ -261,66 +270,73 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       constexpr uint32_t idesc = idesc_bf16(OZ_BM, BN);
       const uint32_t base = smem_u32(smem);
       int g = 0;
+      int gc = 0;   // chunks issued by this CTA (over its tiles)
       bool ok = true;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        const int kb1 = min(nkb, (c + 1) * cb);
-        for (int kb = c * cb; kb < kb1 && ok; ++kb) {
-          const bool first_kb = kb == c * cb;
-          // slice pairs (i, j), i >= j, i + j <= S - 1, in the order i, then j;
-          // the unrolled schedule is fixed by S.  (i, j) is the first pair of
-          // its group (i + j) in that order exactly when i - j <= 1.
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        Tile T;
+        if (!tile_of(t, T)) continue;
+        const int nchunks = (T.nkb + cb - 1) / cb;
+        for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+          const int kb1 = min(T.nkb, (c + 1) * cb);
+          for (int kb = c * cb; kb < kb1 && ok; ++kb) {
+            const bool first_kb = kb == c * cb;
+            // slice pairs (i, j), i >= j, i + j <= S - 1, in the order i, then
+            // j; the unrolled schedule is fixed by S.  (i, j) is the first
+            // pair of its group (i + j) in that order exactly when i - j <= 1.
 #pragma unroll
-          for (int i = 0; i < S; ++i) {
-            const int gi = g + i;
-            if (!mbar_wait(&full[gi % OZ_STAGES], (uint32_t)(gi / OZ_STAGES) & 1u, lim)) {
-              atomicExch(a.err, 23);
-              abort_flag = 1;
-              ok = false;
-              break;
-            }
-            // each group of the previous chunk drained by the epilogue (which
-            // drains them in order) before its first MMA of this chunk: the
-            // groups first used at step i are 2i - 1 and 2i, so the MMAs of
-            // the first groups overlap the drain of the later ones
-            if (first_kb && c > 0) {
+            for (int i = 0; i < S; ++i) {
+              const int gi = g + i;
+              if (!mbar_wait(&full[gi % OZ_STAGES], (uint32_t)(gi / OZ_STAGES) & 1u, lim)) {
+                atomicExch(a.err, 23);
+                abort_flag = 1;
+                ok = false;
+                break;
+              }
+              // each group of the previous chunk (of this tile or the one
+              // before) drained by the epilogue, which drains them in order,
+              // before its first MMA of this chunk: the groups first used at
+              // step i are 2i - 1 and 2i, so the MMAs of the first groups
+              // overlap the drain of the later ones
+              if (first_kb && gc > 0) {
 #pragma unroll
-              for (int grp = (i == 0 ? 0 : 2 * i - 1); grp <= 2 * i && grp < S; ++grp)
-                if (ok && !mbar_wait(&tempty[grp], (uint32_t)(c - 1) & 1u, lim)) {
-                  atomicExch(a.err, 22);
-                  abort_flag = 1;
-                  ok = false;
-                }
-              if (!ok) break;
-            }
-            fence_after();
-            const uint32_t si = base + (uint32_t)(gi % OZ_STAGES) * OZ_STAGE_BYTES;
+                for (int grp = (i == 0 ? 0 : 2 * i - 1); grp <= 2 * i && grp < S; ++grp)
+                  if (ok && !mbar_wait(&tempty[grp], (uint32_t)(gc - 1) & 1u, lim)) {
+                    atomicExch(a.err, 22);
+                    abort_flag = 1;
+                    ok = false;
+                  }
+                if (!ok) break;
+              }
+              fence_after();
+              const uint32_t si = base + (uint32_t)(gi % OZ_STAGES) * OZ_STAGE_BYTES;
 #pragma unroll
-            for (int j = 0; j <= (i < S - 1 - i ? i : S - 1 - i); ++j) {
-              const uint32_t sj = base + (uint32_t)((g + j) % OZ_STAGES) * OZ_STAGE_BYTES;
-              const uint32_t d = tmem + (uint32_t)((i + j) * BN);
-              const bool overwrite = first_kb && (i - j <= 1);
-              // A slice i x B slice j
-#pragma unroll
-              for (int k = 0; k < OZ_BK / 16; ++k)
-                mma_bf16(d, desc_sw128(si + 32 * k), desc_sw128(sj + OZ_A_BYTES + 32 * k), idesc,
-                         (overwrite && k == 0) ? 0u : 1u);
-              if (j < i) {
-                // A slice j x B slice i
+              for (int j = 0; j <= (i < S - 1 - i ? i : S - 1 - i); ++j) {
+                const uint32_t sj = base + (uint32_t)((g + j) % OZ_STAGES) * OZ_STAGE_BYTES;
+                const uint32_t d = tmem + (uint32_t)((i + j) * BN);
+                const bool overwrite = first_kb && (i - j <= 1);
+                // A slice i x B slice j
 #pragma unroll
                 for (int k = 0; k < OZ_BK / 16; ++k)
-                  mma_bf16(d, desc_sw128(sj + 32 * k), desc_sw128(si + OZ_A_BYTES + 32 * k),
-                           idesc, 1u);
+                  mma_bf16(d, desc_sw128(si + 32 * k), desc_sw128(sj + OZ_A_BYTES + 32 * k),
+                           idesc, (overwrite && k == 0) ? 0u : 1u);
+                if (j < i) {
+                  // A slice j x B slice i
+#pragma unroll
+                  for (int k = 0; k < OZ_BK / 16; ++k)
+                    mma_bf16(d, desc_sw128(sj + 32 * k), desc_sw128(si + OZ_A_BYTES + 32 * k),
+                             idesc, 1u);
+                }
               }
+              // slice q is last used at step max(q, S-1-q): release what step i
+              // finished (the stage frees once these MMAs complete)
+              if (i >= S - 1 - i) mma_commit(&empty[gi % OZ_STAGES]);
+              if (S - 1 - i < i) mma_commit(&empty[(g + S - 1 - i) % OZ_STAGES]);
             }
-            // slice q is last used at step max(q, S-1-q): release what step i
-            // finished (the stage frees once these MMAs complete)
-            if (i >= S - 1 - i) mma_commit(&empty[gi % OZ_STAGES]);
-            if (S - 1 - i < i) mma_commit(&empty[(g + S - 1 - i) % OZ_STAGES]);
+            if (!ok) break;
+            g += S;
           }
-          if (!ok) break;
-          g += S;
+          if (ok) mma_commit(tfull);
         }
-        if (ok) mma_commit(tfull);
       }
       // every MMA issued here (also after an abort) completes before the
       // tensor memory is freed
@@ -333,74 +349,82 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // and columns 32 h .. 32 h + 31 of every group, h = (w - 2) / 4
     const int q = warp & 3, h = (warp - 2) >> 2;
     const int lr = q * 32 + lane;
-    const int m = m0 + lr;
-    const int nc = n0 + h * OZ_EPI_COLS;
     const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * OZ_EPI_COLS);
-    long long acc[OZ_EPI_COLS];
+    int gc = 0;   // chunks drained (over this CTA's tiles)
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      Tile T;
+      if (!tile_of(t, T)) continue;
+      const int m = T.m0 + lr;
+      const int nc = T.n0 + h * OZ_EPI_COLS;
+      const int nchunks = (T.nkb + cb - 1) / cb;
+      long long acc[OZ_EPI_COLS];
 #pragma unroll
-    for (int j = 0; j < OZ_EPI_COLS; ++j) acc[j] = 0;
-    bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      bool have = mbar_wait(tfull, (uint32_t)c & 1u, lim);
-      // tcgen05.ld is warp-collective: one decision per warp
-      have = __all_sync(0xffffffffu, have && !*(volatile int *)&abort_flag);
-      if (!have) {
-        if (lane == 0) atomicExch(a.err, 24);
-        abort_flag = 1;
-        ok = false;
-        break;
+      for (int j = 0; j < OZ_EPI_COLS; ++j) acc[j] = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c, ++gc) {
+        bool have = mbar_wait(tfull, (uint32_t)gc & 1u, lim);
+        // tcgen05.ld is warp-collective: one decision per warp
+        have = __all_sync(0xffffffffu, have && !*(volatile int *)&abort_flag);
+        if (!have) {
+          if (lane == 0) atomicExch(a.err, 24);
+          abort_flag = 1;
+          ok = false;
+          break;
+        }
+        fence_after();
+        read_groups<S, BN>(tcol, h, acc, a.ns, tempty);
       }
-      fence_after();
-      read_groups<S, BN>(tcol, h, acc, a.ns, tempty);
-    }
-    if (ok && lr < rows_valid && nc < N) {
-      // C = acc 2^(eA + eB + u - 7(S+1)), as two exact power-of-two factors
-      const double fa = pow2(a.eA[m] + oz_drop_bits(S) - 7 * (S + 1));
-      const OzEpilogue &ep = a.ep;
-      if (ep.mode == kOzC) {
-        double *crow = ep.C + (int64_t)m * ep.ldc + nc;
-        if (a.vec && nc + OZ_EPI_COLS <= N) {
+      if (!ok) break;
+      if (lr < T.rows_valid && nc < N) {
+        // C = acc 2^(eA + eB + u - 7(S+1)), as two exact power-of-two factors
+        const double fa = pow2(a.eA[m] + oz_drop_bits(S) - 7 * (S + 1));
+        const OzEpilogue &ep = a.ep;
+        if (ep.mode == kOzC) {
+          double *crow = ep.C + (int64_t)m * ep.ldc + nc;
+          if (a.vec && nc + OZ_EPI_COLS <= N) {
 #pragma unroll
-          for (int j = 0; j < OZ_EPI_COLS; j += 2) {
-            double2 w;
-            w.x = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
-            w.y = (double)acc[j + 1] * fa * pow2(__ldg(a.eB + nc + j + 1));
-            *(double2 *)(crow + j) = w;
+            for (int j = 0; j < OZ_EPI_COLS; j += 2) {
+              double2 w;
+              w.x = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+              w.y = (double)acc[j + 1] * fa * pow2(__ldg(a.eB + nc + j + 1));
+              *(double2 *)(crow + j) = w;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < OZ_EPI_COLS; ++j)
+              if (nc + j < N) crow[j] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
           }
-        } else {
+        } else if (ep.mode == kOzCT) {
 #pragma unroll
           for (int j = 0; j < OZ_EPI_COLS; ++j)
-            if (nc + j < N) crow[j] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
-        }
-      } else if (ep.mode == kOzCT) {
+            if (nc + j < N)
+              ep.C[(int64_t)(nc + j) * ep.ldc + m] =
+                  (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+        } else if (ep.mode == kOzBetaT) {
+          // row m = (atom A, E, c): beta^T[(j n_occ + E)][ao_A + c] for column j
+          const int aoA = ep.aoff[T.atom], nA = ep.aoff[T.atom + 1] - aoA;
+          const int r = m - aoA * ep.n_occ, E = r / nA, c = r - E * nA;
+          double *dst = ep.C + (int64_t)E * ep.ldc + aoA + c;
+          const int64_t step = (int64_t)ep.n_occ * ep.ldc;
 #pragma unroll
-        for (int j = 0; j < OZ_EPI_COLS; ++j)
-          if (nc + j < N)
-            ep.C[(int64_t)(nc + j) * ep.ldc + m] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
-      } else if (ep.mode == kOzBetaT) {
-        // row m = (atom A, E, c): beta^T[(j n_occ + E)][ao_A + c] for column j
-        const int aoA = ep.aoff[atom], nA = ep.aoff[atom + 1] - aoA;
-        const int r = m - aoA * ep.n_occ, E = r / nA, c = r - E * nA;
-        double *dst = ep.C + (int64_t)E * ep.ldc + aoA + c;
-        const int64_t step = (int64_t)ep.n_occ * ep.ldc;
+          for (int j = 0; j < OZ_EPI_COLS; ++j)
+            if (nc + j < N)
+              dst[(int64_t)(nc + j) * step] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+        } else {
+          // kOzGammaCat: row m = orbital (atom B, b), column n = j n_occ + E ->
+          // Gcat[j][xoff_B + b n_occ + E]
+          const int B = ep.orb_atom[m], b = m - ep.aoff[B];
+          const int64_t xo = ep.xoff5[B] + (int64_t)b * ep.n_occ;
+          int jj = nc / ep.n_occ, E = nc - jj * ep.n_occ;
 #pragma unroll
-        for (int j = 0; j < OZ_EPI_COLS; ++j)
-          if (nc + j < N)
-            dst[(int64_t)(nc + j) * step] = (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
-      } else {
-        // kOzGammaCat: row m = orbital (atom B, b), column n = j n_occ + E ->
-        // Gcat[j][xoff_B + b n_occ + E]
-        const int B = ep.orb_atom[m], b = m - ep.aoff[B];
-        const int64_t xo = ep.xoff5[B] + (int64_t)b * ep.n_occ;
-        int jj = nc / ep.n_occ, E = nc - jj * ep.n_occ;
-#pragma unroll
-        for (int j = 0; j < OZ_EPI_COLS; ++j) {
-          if (nc + j < N)
-            ep.C[(int64_t)jj * ep.ldc + xo + E] =
-                (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
-          if (++E == ep.n_occ) {
-            E = 0;
-            ++jj;
+          for (int j = 0; j < OZ_EPI_COLS; ++j) {
+            if (nc + j < N)
+              ep.C[(int64_t)jj * ep.ldc + xo + E] =
+                  (double)acc[j] * fa * pow2(__ldg(a.eB + nc + j));
+            if (++E == ep.n_occ) {
+              E = 0;
+              ++jj;
+            }
           }
         }
       }
@@ -715,8 +739,19 @@ cudaError_t launch_gemm_oz_ex(cudaStream_t st, const OzOperand &A, const OzOpera
   a.mul_n = mul_n;
   const int bn = oz_bn(A.s);
   if (bn == 96 && !B.has96) return cudaErrorInvalidValue;
-  dim3 grid(tiles ? n_tiles : (M + OZ_BM - 1) / OZ_BM, (N + bn - 1) / bn);
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  // persistent grid: one CTA per SM at most, each walking its share of the tiles
+  a.Mt = tiles ? n_tiles : (M + OZ_BM - 1) / OZ_BM;
+  a.Nt = (N + bn - 1) / bn;
+  if ((int64_t)a.Mt * a.Nt > INT32_MAX) return cudaErrorInvalidConfiguration;
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n_sm < 1)
+      n_sm = 1;
+  }
+  dim3 grid((unsigned)std::min<int64_t>((int64_t)a.Mt * a.Nt, n_sm));
   switch (A.s) {
     case 3: return launch_oz_kernel<3>(st, grid, A.map, B, a);
     case 4: return launch_oz_kernel<4>(st, grid, A.map, B, a);
