@@ -10,18 +10,21 @@
 // gives alpha_mu^{aE} = sum_b V^{ab} X_b^E and alpha_mu^{bE} = sum_a V^{ab} X_a^E;
 // a local product (A, A) has alpha_mu^{aE} = sum_{a'} V^{aa'} X_a'^E.
 //
-// The reduced-precision step 2 runs over W-orbital chunks of the orbital
-// axis instead of atoms (W = kStep2Chunk, a multiple of 16): chunk k holds
-// orbitals Wk .. Wk+W-1 (of one or more atoms), its product list L(k) is
-// the union of their lists L_A, and its operand row (k, E, cw) holds
-// alpha^{cE} of orbital c = Wk + cw on L(k), zero on the products outside
-// L_{A(c)}.  The product runs with the right-hand-side columns as the M
-// axis, so that each thread of its epilogue holds 16 consecutive orbitals
-// of one (k, E): one whole 32-byte sector of a beta^T row per plane,
-// written with 16-byte stores.  (A per-atom segment of 13 orbitals is 26
-// bytes and fills no sector; its 2-byte stores made step 2 store bound.)
-// The union adds MMA work (2x for W = 16) and vertex bytes, both below the
-// store time it saves.
+// The reduced-precision step 2 runs over 16-orbital chunks of the orbital
+// axis: chunk k holds orbitals 16k .. 16k+15, split into parts, the runs of
+// its orbitals on one atom (one to three parts for atoms of 13 orbitals).
+// Its operand rows, per block of 16 occupied states, are ordered (c16, e):
+// row ((k nEB + b) 16 + c16) 16 + e holds alpha^{cE} of orbital 16k + c16
+// and occupied state E = 16b + e over the per-atom list L_A of that
+// orbital's atom (zero past n_orb or n_occ).  The product of a tile (the
+// right-hand-side columns as M, one chunk and one E block as the 256 N
+// columns, c16-major in tensor memory) runs part by part: each part's MMAs
+// cover its own columns with N = 16 x its orbitals and its own atom's K
+// range, so no MMA work is spent on products outside an orbital's list.  The
+// epilogue gathers, for each thread's E, the 16 orbitals of the chunk (16
+// 4-column tensor-memory loads) and writes them as one whole 32-byte sector
+// of a beta^T row per plane.  (A per-atom output segment of 13 orbitals is
+// 26 bytes and fills no sector; its 2-byte stores made step 2 store bound.)
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -96,32 +99,27 @@ __global__ void split_dense_kernel(const double *__restrict__ src, int64_t rows,
   }
 }
 
-// The chunk operand of the reduced-precision step 2: row r = (k n_occ + E)
-// W + cw, column q < K2c holds alpha of orbital o = Wk + cw on the
-// product at position q of L(k) (posmap[k][cw][q]: its position in
-// L_{A(o)}, or -1 where it is not in that list; zero rows past n_orb), split
-// bf16 [rows][2 K2c] or tf32 [rows][K2c].
-__global__ void alpha_chunk_kernel(int64_t rows, int K2c, int n_occ, int n_orb, int K2max,
-                                   const int *__restrict__ aoff, const int *__restrict__ orb_atom,
-                                   const int *__restrict__ posmap, const double *__restrict__ a2,
-                                   void *__restrict__ dstv, bool tf32) {
-  const int64_t total = rows * K2c;
+// The part operand of the reduced-precision step 2: row r = ((k nEB + b) 16
+// + c16) 16 + e holds the per-atom row of orbital o = 16k + c16 and occupied
+// state E = 16b + e (the K2max columns of alpha over L_{A(o)}), zero past
+// n_orb or n_occ; split bf16 [rows][2 K2max] or tf32 [rows][K2max].
+__global__ void alpha_part_kernel(int64_t rows, int K2max, int n_occ, int n_orb, int nEB,
+                                  const int *__restrict__ aoff, const int *__restrict__ orb_atom,
+                                  const double *__restrict__ a2, void *__restrict__ dstv,
+                                  bool tf32) {
+  const int64_t total = rows * K2max;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / K2c;
-    const int q = (int)(i - r * K2c);
-    constexpr int W = kStep2Chunk;
-    const int cw = (int)(r % W);
-    const int64_t kE = r / W;
-    const int k = (int)(kE / n_occ), E = (int)(kE - (int64_t)k * n_occ);
-    const int o = W * k + cw;
+    const int64_t r = i / K2max;
+    const int q = (int)(i - r * K2max);
+    const int e = (int)(r & 15), c16 = (int)((r >> 4) & 15);
+    const int64_t kb = r >> 8;   // k nEB + b
+    const int k = (int)(kb / nEB), b = (int)(kb - (int64_t)k * nEB);
+    const int o = 16 * k + c16, E = 16 * b + e;
     double x = 0.0;
-    if (o < n_orb) {
-      const int p = posmap[((int64_t)k * W + cw) * K2c + q];
-      if (p >= 0) {
-        const int A = orb_atom[o], aoA = aoff[A], nA = aoff[A + 1] - aoA;
-        x = a2[((int64_t)aoA * n_occ + (int64_t)E * nA + (o - aoA)) * K2max + p];
-      }
+    if (o < n_orb && E < n_occ) {
+      const int A = orb_atom[o], aoA = aoff[A], nA = aoff[A + 1] - aoA;
+      x = a2[((int64_t)aoA * n_occ + (int64_t)E * nA + (o - aoA)) * K2max + q];
     }
     if (tf32) {
       ((float *)dstv)[i] = ptx::tf32_round((float)x);
@@ -129,8 +127,8 @@ __global__ void alpha_chunk_kernel(int64_t rows, int K2c, int n_occ, int n_orb, 
     }
     __nv_bfloat16 *dst = (__nv_bfloat16 *)dstv;
     const __nv_bfloat16 hi = __double2bfloat16(x);
-    dst[r * 2 * K2c + q] = hi;
-    dst[r * 2 * K2c + K2c + q] = __double2bfloat16(x - (double)__bfloat162float(hi));
+    dst[r * 2 * K2max + q] = hi;
+    dst[r * 2 * K2max + K2max + q] = __double2bfloat16(x - (double)__bfloat162float(hi));
   }
 }
 
@@ -249,62 +247,37 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   std::vector<int> orb_atom(no);
   for (int A = 0; A < na; ++A)
     for (int a = ao[A]; a < ao[A + 1]; ++a) orb_atom[a] = A;
-  // the W-orbital chunks of the reduced-precision step 2: lists L(k), their
-  // Ycat segments, the position map into the atoms' lists, and the tiles
-  // (128 chunk rows, i.e. 128 / W occupied states, each)
-  constexpr int W = kStep2Chunk;
-  const int nch = (no + W - 1) / W;
-  std::vector<int> lcatc, posmap, xoffc(nch, 0);
-  std::vector<GTile> t2c;
+  // the parts of the 16-orbital chunks of the reduced-precision step 2
+  // (runs of a chunk's orbitals on one atom; past n_orb, one zero part) and
+  // its tiles, one per (chunk, block of 16 occupied states): bands of 16
+  // chunks, the E blocks of a band run block by block across its chunks
+  const int nch = (no + 15) / 16, nEB = (nocc + 15) / 16;
+  std::vector<int4> parts;   // {c16 start | n << 8, atom, Ycat K offset, K blocks}
+  std::vector<int> pptr(nch + 1, 0);
+  std::vector<GTile> t2p;
   if (lp) {
-    std::vector<std::vector<int>> Lc(nch);
-    int kc = 0;
     for (int k = 0; k < nch; ++k) {
-      std::vector<int> &u = Lc[k];
-      for (int o = W * k, last = -1; o < std::min(no, W * k + W); ++o) {
-        if (orb_atom[o] == last) continue;
-        last = orb_atom[o];
-        u.insert(u.end(), L[last].begin(), L[last].end());
+      for (int c = 0; c < 16;) {
+        const int o = 16 * k + c;
+        const int A = o < no ? orb_atom[o] : -1;
+        int n = 1;
+        while (c + n < 16 && (16 * k + c + n < no ? orb_atom[16 * k + c + n] : -1) == A) ++n;
+        // an atom without products, or the zero tail: one K block of zero
+        // vertex rows, so that its columns are written (as zeros) too
+        const int nkb = A >= 0 ? std::max(1, ((int)L[A].size() + 63) / 64) : 1;
+        parts.push_back(make_int4(c | (n << 8), A, A >= 0 ? xoff2[A] : 0, nkb));
+        c += n;
       }
-      std::sort(u.begin(), u.end());
-      u.erase(std::unique(u.begin(), u.end()), u.end());
-      kc = std::max(kc, (int)u.size());
+      pptr[k + 1] = (int)parts.size();
     }
-    ar.K2c = round_up(std::max(kc, 1), 64);
-    ar.rows2c = (int64_t)nch * nocc * W;
-    posmap.assign((size_t)nch * W * ar.K2c, -1);
-    for (int k = 0; k < nch; ++k) {
-      const int xo = (int)lcatc.size();
-      for (int mu : Lc[k]) lcatc.push_back(mu);
-      while (lcatc.size() % 64) lcatc.push_back(-1);
-      for (int cw = 0; cw < W && W * k + cw < no; ++cw) {
-        const std::vector<int> &LA = L[orb_atom[W * k + cw]];   // increasing product order
-        for (int q = 0; q < (int)Lc[k].size(); ++q) {
-          auto it = std::lower_bound(LA.begin(), LA.end(), Lc[k][q]);
-          if (it != LA.end() && *it == Lc[k][q])
-            posmap[((size_t)k * W + cw) * ar.K2c + q] = (int)(it - LA.begin());
-        }
-      }
-      xoffc[k] = xo;
-    }
-    // tile order: bands of kBand consecutive chunks; within a band the
-    // 128-row blocks (128 / W occupied states) run block by block across the
-    // band's chunks, so that the 32-byte runs the band writes into one beta^T
-    // row (W kBand orbitals) are written close together in time and leave
-    // L2 as whole lines; the band's Ycat segments stay in L2 meanwhile
+    ar.rows2p = (int64_t)nch * nEB * 256;
     constexpr int kBand = 16;
-    const int rows = nocc * W;
     for (int b0 = 0; b0 < nch; b0 += kBand)
-      for (int m = 0; m < rows; m += 128)
-        for (int k = b0; k < std::min(nch, b0 + kBand); ++k) {
-          if (Lc[k].empty()) continue;   // no product on the chunk's atoms: beta stays zero
-          t2c.push_back(GTile{k * rows + m, xoffc[k], ((int)Lc[k].size() + 63) / 64,
-                              std::min(128, rows - m), k, 0, 0, 0});
-        }
-    ar.kcat2c = std::max((int)lcatc.size(), 64);
-    while ((int)lcatc.size() < ar.kcat2c) lcatc.push_back(-1);
-    ar.n_tiles2c = (int)t2c.size();
-    if (t2c.empty()) t2c.push_back(GTile{0, 0, 0, 0, 0, 0, 0, 0});
+      for (int b = 0; b < nEB; ++b)
+        for (int k = b0; k < std::min(nch, b0 + kBand); ++k)
+          t2p.push_back(GTile{(k * nEB + b) * 256, pptr[k], pptr[k + 1] - pptr[k],
+                              std::min(16, nocc - 16 * b), k, 0, 0, 0});
+    ar.n_tiles2p = (int)t2p.size();
   }
 
   cudaError_t e = cudaSuccess;
@@ -333,13 +306,9 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   up((void **)&ar.pos5, pos5.data(), pos5.size() * sizeof(int2));
   up((void **)&ar.xoff5, xoff5.data(), xoff5.size() * sizeof(int));
   up((void **)&ar.orb_atom, orb_atom.data(), orb_atom.size() * sizeof(int));
-  int *posmap_d = nullptr;   // set-up only (freed below)
   if (lp) {
-    up((void **)&ar.tiles2c, t2c.data(), t2c.size() * sizeof(GTile));
-    up((void **)&ar.lcatc, lcatc.data(), lcatc.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&posmap_d, posmap.size() * sizeof(int));
-    if (e == cudaSuccess)
-      e = cudaMemcpy(posmap_d, posmap.data(), posmap.size() * sizeof(int), cudaMemcpyHostToDevice);
+    up((void **)&ar.tiles2p, t2p.data(), t2p.size() * sizeof(GTile));
+    up((void **)&ar.parts, parts.data(), parts.size() * sizeof(int4));
   }
   // product info in Vpad (block) order: blk_prod[q] = mu
   int *rowoff5_d = nullptr;
@@ -367,23 +336,23 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   if (lp) {
     ar.lp = true;
     __nv_bfloat16 *q2 = nullptr, *q5 = nullptr, *qy = nullptr, *qg = nullptr;
-    al((void **)&q2, (size_t)ar.rows2c * 2 * ar.K2c * sizeof(__nv_bfloat16));
+    al((void **)&q2, (size_t)ar.rows2p * 2 * ar.K2max * sizeof(__nv_bfloat16));
     al((void **)&q5, n5 * 2 * sizeof(__nv_bfloat16));
-    al((void **)&qy, (size_t)ncap * 2 * ar.kcat2c * sizeof(__nv_bfloat16));
+    al((void **)&qy, (size_t)ncap * 2 * ar.kcat2 * sizeof(__nv_bfloat16));
     al((void **)&qg, (size_t)ncap * 2 * ar.kcat5 * sizeof(__nv_bfloat16));
     al((void **)&ar.P2f, (size_t)rows5 * ar.ldp * sizeof(float));
     if (e == cudaSuccess) {
-      alpha_chunk_kernel<<<152 * 8, 256, 0, st>>>(ar.rows2c, ar.K2c, nocc, no, ar.K2max, sys.aoff,
-                                                  ar.orb_atom, posmap_d, a2, q2, ar.tf32);
+      alpha_part_kernel<<<152 * 8, 256, 0, st>>>(ar.rows2p, ar.K2max, nocc, no, nEB, sys.aoff,
+                                                 ar.orb_atom, a2, q2, ar.tf32);
       split_dense_kernel<<<152 * 8, 256, 0, st>>>(a5, rows5, ar.K5max, q5, ar.tf32);
       e = cudaGetLastError();
     }
     // Gcat pads (never written) must read as zero
     if (e == cudaSuccess)
       e = cudaMemsetAsync(qg, 0, (size_t)ncap * 2 * ar.kcat5 * sizeof(__nv_bfloat16), st);
-    if (e == cudaSuccess) e = make_operand_map(ar.a2, q2, ar.rows2c, ar.K2c, 128, ar.tf32);
+    if (e == cudaSuccess) e = make_operand_map(ar.a2, q2, ar.rows2p, ar.K2max, 128, ar.tf32);
     if (e == cudaSuccess) e = make_operand_map(ar.a5, q5, rows5, ar.K5max, 128, ar.tf32);
-    if (e == cudaSuccess) e = make_operand_map(ar.ycat, qy, ncap, ar.kcat2c, 128, ar.tf32);
+    if (e == cudaSuccess) e = make_operand_map(ar.ycat, qy, ncap, ar.kcat2, 128, ar.tf32);
     if (e == cudaSuccess) e = make_operand_map(ar.gcat, qg, ncap, ar.kcat5, 128, ar.tf32);
     ar.ycat_q = qy;
     ar.gcat_q = qg;
@@ -414,19 +383,18 @@ cudaError_t alpha_setup(cudaStream_t st, const tddft_system *h, const DevSystem 
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(a2);
   cudaFree(a5);
-  cudaFree(posmap_d);
   return e;
 }
 
 cudaError_t launch_alpha_gather_lp(cudaStream_t st, const AlphaRoute &ar, int ncols, const void *Y,
                                    bool y_f64, int64_t ld, const int *dcnt) {
-  const int g = grid_for((int64_t)ncols * ar.kcat2c, 256);
+  const int g = grid_for((int64_t)ncols * ar.kcat2, 256);
   __nv_bfloat16 *dst = ar.ycat_q;
   if (y_f64)
-    gather_split_kernel<double><<<g, 256, 0, st>>>(ncols, ar.kcat2c, ar.lcatc, (const double *)Y,
-                                                   ld, dst, ar.tf32, dcnt);
+    gather_split_kernel<double><<<g, 256, 0, st>>>(ncols, ar.kcat2, ar.lcat, (const double *)Y, ld,
+                                                   dst, ar.tf32, dcnt);
   else
-    gather_split_kernel<float><<<g, 256, 0, st>>>(ncols, ar.kcat2c, ar.lcatc, (const float *)Y, ld,
+    gather_split_kernel<float><<<g, 256, 0, st>>>(ncols, ar.kcat2, ar.lcat, (const float *)Y, ld,
                                                   dst, ar.tf32, dcnt);
   return cudaGetLastError();
 }

@@ -21,15 +21,16 @@
 //     kDscaleSplit   the D(omega) scaling of eq. response-mat on (re, im)
 //                    column pairs, written back as split bf16 for the next GEMM
 //                    (E-major input columns, slot-major output rows)
-//     kBetaChunkSplit step 2 on the stored transition vertex (16-orbital
-//                    chunks, right-hand-side columns as M): beta^T, split
-//                    bf16, one 32-byte run per thread and plane
+//     kBetaPartSplit step 2 on the stored transition vertex (16-orbital
+//                    chunks in per-atom parts, right-hand-side columns as M):
+//                    beta^T, split bf16, one 32-byte run per thread and plane
 //     kGammaCatSplit transform 2 into the per-atom Gcat rows, split bf16
 //     kPartialF32    step 5 partial sums, float32
 // Grouped products take a tile table (per-atom operands: A rows, B K offset
-// and length per 128-row tile; for step 2, B rows and the A K offset).  Every mbarrier wait is bounded by a
-// wall-clock limit; on expiry the CTA records an error code, stops issuing
-// work, waits (bounded) for its copies in flight and still frees its TMEM.
+// and length per 128-row tile; for step 2, per (chunk, E block) entries and
+// the chunks' parts).  Every mbarrier wait is bounded by a wall-clock
+// limit; on expiry the CTA records an error code, stops issuing work, waits
+// (bounded) for its copies in flight and still frees its TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -147,36 +148,8 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
         if (n < N) ep.outF[(int64_t)m * ep.ldo + n] = v[j];
       }
     }
-  } else if (EPI == kBetaChunkSplit) {
-    // row m = column 2 s + p of the right-hand sides; columns n0 + j0 ..
-    // n0 + j0 + 15 = 16 orbitals W k + cw .. of chunk k (= atom; W =
-    // kStep2Chunk) and one occupied state E: one 32-byte run of the beta^T
-    // row E M + m per plane (N: the end of the tile's valid columns; M: the
-    // live columns).
-    // The rows are E-major so that the rows one tile writes lie together
-    // (slot-major rows put each of its 64 slots in another memory page)
-    if (m < M && n0 + j0 < N) {
-      const int E = (n0 + j0) / kStep2Chunk - atom * ep.n_occ;
-      const int cw = (n0 + j0) % kStep2Chunk;
-      const int64_t row = (int64_t)E * M + m;
-      const int64_t at = row * operand_ld<TF>(ep) + (int64_t)kStep2Chunk * atom + cw;
-      if (TF) {
-        float4 *dst = (float4 *)((float *)ep.outB + at);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          dst[q] = make_float4(tf32_round(v[4 * q]), tf32_round(v[4 * q + 1]),
-                               tf32_round(v[4 * q + 2]), tf32_round(v[4 * q + 3]));
-      } else {
-        __align__(16) __nv_bfloat16 h[16], l[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) split_bf16(v[j], h[j], l[j]);
-        __nv_bfloat16 *dst = (__nv_bfloat16 *)ep.outB + at;
-        *(uint4 *)dst = *(const uint4 *)h;
-        *(uint4 *)(dst + 8) = *(const uint4 *)(h + 8);
-        *(uint4 *)(dst + ep.lo_off) = *(const uint4 *)l;
-        *(uint4 *)(dst + ep.lo_off + 8) = *(const uint4 *)(l + 8);
-      }
-    }
+  } else if (EPI == kBetaPartSplit) {
+    // (written by the kernel's own epilogue loop)
   } else if (EPI == kGammaCatSplit) {
     // row m = orbital (atom B, b); column n = (s n_occ + E) 2 + p, j = 2 s + p:
     // Gcat[j][xoff5_B + b n_occ + E]
@@ -284,11 +257,15 @@ __device__ __forceinline__ void epilogue16(const float (&v)[16], int m, int lr, 
 template <int EPI, int TC_BN, bool TF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   int M, int N, int KpA, int KpB, TcEpilogue ep, int *err, const int *dcnt,
-                   int mul_n, const GTile *tiles, int n_mtiles) {
+                   const __grid_constant__ CUtensorMap mapB64,
+                   const __grid_constant__ CUtensorMap mapB128, int M, int N, int KpA, int KpB,
+                   TcEpilogue ep, int *err, const int *dcnt, int mul_n, const GTile *tiles,
+                   int n_mtiles) {
   // graph replays: right-hand-side columns beyond the live count are
   // skipped (whole tiles); they are the M axis of step 2, else the N axis
-  constexpr bool kChunk = EPI == kBetaChunkSplit;
+  constexpr bool kChunk = EPI == kBetaPartSplit;
+  // the part-based step 2 is built for the 256-wide tile (16 c16 x 16 e)
+  if (kChunk && TC_BN != 256) return;
   if (dcnt) {
     const int live = (int)min((int64_t)(kChunk ? M : N), (int64_t)mul_n * (*dcnt));
     if (kChunk)
@@ -333,9 +310,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // fastest, so consecutive CTAs (in a cluster: one GPC, one L2 partition)
   // read the same A tile, which DRAM then supplies once;
   // xa / xb: K offsets (elements) of the A and B tiles within a plane
-  // step 2 (kChunk): the table runs over the B rows (chunk rows), the M
-  // tiles of the columns fastest, so that DRAM supplies each B tile once;
-  // rows_valid is then the tile's valid B rows (columns of the output)
+  // step 2 (kChunk): the table runs over (chunk, E block) entries, the M
+  // tiles of the columns fastest, so that DRAM supplies each B block once;
+  // xa = the first part, nkb = the part count, rows_valid = the valid E,
+  // n0 = the B row base of the entry
   auto tile_of = [&](int t, int &m0, int &xa, int &xb, int &nkb, int &rows_valid, int &atom,
                      int &n0) {
     if (kChunk) {
@@ -414,7 +392,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         int m0, xa, xoff, nkb, rv, at, n0;
         tile_of(t, m0, xa, xoff, nkb, rv, at, n0);
-        for (int kb = 0; kb < nkb; ++kb, ++g) {
+        // step 2: one K loop per part (its atom's Ycat segment, its B rows)
+        const int nparts = kChunk ? nkb : 1;
+        for (int p = 0; p < nparts && ok; ++p) {
+        int pxa = xa, pxb = xoff, prow = n0, pnkb = nkb, pncol = TC_BN;
+        if (kChunk) {
+          const int4 pi = ep.parts[xa + p];
+          pxa = pi.z;
+          pxb = 0;
+          prow = n0 + (pi.x & 255) * 16;
+          pnkb = pi.w;
+          pncol = (pi.x >> 8) * 16;
+        }
+        for (int kb = 0; kb < pnkb; ++kb, ++g) {
           const int s = g % NS;
           const uint32_t ph = (uint32_t)(g / NS) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, lim)) {
@@ -431,17 +421,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           // second box of each operand: the lo plane (split bf16) or the
           // upper 32 entries of the K block (TF32)
           const int secA = TF ? 32 : KpA, secB = TF ? 32 : KpB;
-          mbar_expect_tx(&full[s], SB);
-          tma_load_2d(st, &mapA, &full[s], xa + kb * TC_BK, m0);                      // A_hi / A_0
-          tma_load_2d(st + TC_A_BYTES, &mapA, &full[s], secA + xa + kb * TC_BK, m0);  // A_lo / A_1
+          // step 2: the smallest B box that holds the part's rows (64, 128 or
+          // 256), whose bytes the stage then expects
+          const CUtensorMap *mb = &mapB;
+          uint32_t bbytes = B_BYTES;
+          if (kChunk && pncol <= 64) {
+            mb = &mapB64;
+            bbytes = 64 * TC_BK * 2;
+          } else if (kChunk && pncol <= 128) {
+            mb = &mapB128;
+            bbytes = 128 * TC_BK * 2;
+          }
+          mbar_expect_tx(&full[s], SB - 2 * (B_BYTES - bbytes));
+          tma_load_2d(st, &mapA, &full[s], pxa + kb * TC_BK, m0);                      // A_hi / A_0
+          tma_load_2d(st + TC_A_BYTES, &mapA, &full[s], secA + pxa + kb * TC_BK, m0);  // A_lo / A_1
           if (kM2) {   // the second M block's A tile
-            tma_load_2d(st + 2 * TC_A_BYTES, &mapA, &full[s], xa + kb * TC_BK, m0 + TC_BM);
-            tma_load_2d(st + 3 * TC_A_BYTES, &mapA, &full[s], secA + xa + kb * TC_BK,
+            tma_load_2d(st + 2 * TC_A_BYTES, &mapA, &full[s], pxa + kb * TC_BK, m0 + TC_BM);
+            tma_load_2d(st + 3 * TC_A_BYTES, &mapA, &full[s], secA + pxa + kb * TC_BK,
                         m0 + TC_BM);
           }
-          tma_load_2d(st + B_OFF, &mapB, &full[s], xoff + kb * TC_BK, n0);           // B_hi / B_0
-          tma_load_2d(st + B_OFF + B_BYTES, &mapB, &full[s], secB + xoff + kb * TC_BK,
-                      n0);                                                         // B_lo / B_1
+          tma_load_2d(st + B_OFF, mb, &full[s], pxb + kb * TC_BK, prow);           // B_hi / B_0
+          tma_load_2d(st + B_OFF + B_BYTES, mb, &full[s], secB + pxb + kb * TC_BK,
+                      prow);                                                     // B_lo / B_1
+        }
         }
       }
       // copies in flight: the last NS stages issued must land before exit
@@ -470,11 +472,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           fence_after();
         }
-        const uint32_t d = tmem + (uint32_t)(buf * ACC);
+        const uint32_t d0 = tmem + (uint32_t)(buf * ACC);
         // M2: the second M block (accumulator d + TC_BN) only where the
         // table entry has rows there
         const int nblk = (kM2 && rv > TC_BM) ? 2 : 1;
-        for (int kb = 0; kb < nkb; ++kb, ++g) {
+        // step 2: one K loop per part, into the part's own columns
+        // (c16 start x 16, N = 16 x its orbitals) with its own descriptor
+        const int nparts = kChunk ? nkb : 1;
+        for (int p = 0; p < nparts && ok; ++p) {
+        int pnkb = nkb;
+        uint32_t pidesc = idesc, d = d0;
+        if (kChunk) {
+          const int4 pi = ep.parts[xa + p];
+          const int ncol = (pi.x >> 8) * 16;
+          pnkb = pi.w;
+          d = d0 + (uint32_t)((pi.x & 255) * 16);
+          pidesc = TF ? idesc_tf32(TC_BM, ncol) : idesc_bf16(TC_BM, ncol);
+        }
+        for (int kb = 0; kb < pnkb; ++kb, ++g) {
           const int s = g % NS;
           if (!mbar_wait(&full[s], (uint32_t)(g / NS) & 1u, lim)) {
             atomicExch(err, 2);
@@ -494,20 +509,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t a0 = h ? alo : ahi, b0 = h ? blo : bhi;
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                  mma_tf32(db, desc_sw128(a0 + 32 * k), desc_sw128(b0 + 32 * k), idesc,
+                  mma_tf32(db, desc_sw128(a0 + 32 * k), desc_sw128(b0 + 32 * k), pidesc,
                            (kb > 0 || h > 0 || k > 0) ? 1u : 0u);
               }
             } else {
 #pragma unroll
               for (int k = 0; k < TC_BK / 16; ++k) {
-                mma_bf16(db, desc_sw128(ahi + 32 * k), desc_sw128(bhi + 32 * k), idesc,
+                mma_bf16(db, desc_sw128(ahi + 32 * k), desc_sw128(bhi + 32 * k), pidesc,
                          (kb > 0 || k > 0) ? 1u : 0u);
-                mma_bf16(db, desc_sw128(ahi + 32 * k), desc_sw128(blo + 32 * k), idesc, 1u);
-                mma_bf16(db, desc_sw128(alo + 32 * k), desc_sw128(bhi + 32 * k), idesc, 1u);
+                mma_bf16(db, desc_sw128(ahi + 32 * k), desc_sw128(blo + 32 * k), pidesc, 1u);
+                mma_bf16(db, desc_sw128(alo + 32 * k), desc_sw128(bhi + 32 * k), pidesc, 1u);
               }
             }
           }
           mma_commit(&empty[s]);
+        }
         }
         if (ok) mma_commit(&tfull[buf]);
       }
@@ -552,7 +568,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int half = ((tn >> 4) + 1) / 2 * 16;
       const int j_lo = kM2 ? 0 : ((warp >= 6) ? half : 0);
       const int j_hi = kM2 ? tn : ((warp >= 6) ? tn : half);
-      for (int j0 = j_lo; j0 < j_hi; j0 += 16) {
+      if (kChunk) {
+        // step 2: tensor-memory column c16 16 + e holds orbital 16 k + c16
+        // (k = atom, the chunk) and occupied state E = 16 eb + e of column
+        // m = m0 + lr; each warp of a lane quadrant takes 8 of the 16 e, four
+        // at a time, and writes each E's 16 orbitals as one 32-byte run of
+        // the beta^T row E M + m per plane (M: the live columns)
+        const int eb = n0 / 256 - atom * ((ep.n_occ + 15) / 16);
+        const int mm = m0 + lr;
+#pragma unroll 1
+        for (int r = 0; r < 2; ++r) {
+          const int e0 = ((warp >= 6) ? 8 : 0) + 4 * r;
+          float v[16][4];
+          tmem_ld4x16(trow + (uint32_t)e0, v);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (mm >= M || e0 + e >= rows_valid) continue;
+            const int64_t row = (int64_t)(16 * eb + e0 + e) * M + mm;
+            const int64_t at = row * operand_ld<TF>(ep) + 16 * (int64_t)atom;
+            if (TF) {
+              float4 *dst = (float4 *)((float *)ep.outB + at);
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                dst[c] = make_float4(tf32_round(v[4 * c][e]), tf32_round(v[4 * c + 1][e]),
+                                     tf32_round(v[4 * c + 2][e]), tf32_round(v[4 * c + 3][e]));
+            } else {
+              __align__(16) __nv_bfloat16 hh[16], ll[16];
+#pragma unroll
+              for (int c = 0; c < 16; ++c) split_bf16(v[c][e], hh[c], ll[c]);
+              __nv_bfloat16 *dst = (__nv_bfloat16 *)ep.outB + at;
+              *(uint4 *)dst = *(const uint4 *)hh;
+              *(uint4 *)(dst + 8) = *(const uint4 *)(hh + 8);
+              *(uint4 *)(dst + ep.lo_off) = *(const uint4 *)ll;
+              *(uint4 *)(dst + ep.lo_off + 8) = *(const uint4 *)(ll + 8);
+            }
+          }
+        }
+      }
+      for (int j0 = j_lo; j0 < j_hi && !kChunk; j0 += 16) {
         DscaleIn di;
         di.eocc = eocc;
         if (EPI == kDscaleSplit) {
@@ -563,8 +616,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         float v[16];
         tmem_ld16(trow + (uint32_t)j0, v);
-        epilogue16<EPI, TF>(v, m, lr, rv_blk, atom, M, kChunk ? n0 + rows_valid : N, n0, j0, ep,
-                            di);
+        epilogue16<EPI, TF>(v, m, lr, rv_blk, atom, M, N, n0, j0, ep, di);
       }
       fence_before();
       __syncwarp();
@@ -671,7 +723,7 @@ template <int BN>
 void set_attr_all() {
   set_attr<kStoreF32, BN>();
   set_attr<kDscaleSplit, BN>();
-  set_attr<kBetaChunkSplit, BN>();
+  set_attr<kBetaPartSplit, BN>();
   set_attr<kGammaCatSplit, BN>();
   set_attr<kPartialF32, BN>();
 }
@@ -700,11 +752,12 @@ int sm_count() {
 
 template <int EPI, int BN, bool TF>
 cudaError_t launch_tc(cudaStream_t st, int grid, const CUtensorMap &mA, const CUtensorMap &mB,
-                      int M, int N, int KpA, int KpB, const TcEpilogue &ep, int *err,
-                      const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
+                      const CUtensorMap &mB64, const CUtensorMap &mB128, int M, int N, int KpA,
+                      int KpB, const TcEpilogue &ep, int *err, const int *dcnt, int mul_n,
+                      const GTile *tiles, int n_mtiles) {
   if (ep.ncl <= 1) {
     gemm_tc_kernel<EPI, BN, TF><<<grid, TC_THREADS, TcCfg<EPI, BN>::SMEM, st>>>(
-        mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n, tiles, n_mtiles);
+        mA, mB, mB64, mB128, M, N, KpA, KpB, ep, err, dcnt, mul_n, tiles, n_mtiles);
     return cudaGetLastError();
   }
   // clusters of ncl CTAs; the grid is at most the clusters that fit at once
@@ -731,35 +784,36 @@ cudaError_t launch_tc(cudaStream_t st, int grid, const CUtensorMap &mA, const CU
     fit[ep.ncl] = n;
   }
   cfg.gridDim = dim3(std::min(grid / ep.ncl, fit[ep.ncl]) * ep.ncl);
-  return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<EPI, BN, TF>, mA, mB, M, N, KpA, KpB, ep, err,
-                            dcnt, mul_n, tiles, n_mtiles);
+  return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<EPI, BN, TF>, mA, mB, mB64, mB128, M, N, KpA, KpB,
+                            ep, err, dcnt, mul_n, tiles, n_mtiles);
 }
 
 template <int BN, bool TF>
 cudaError_t launch_tc_epi(cudaStream_t st, int epi, int M, int N, const CUtensorMap &mA,
-                          const CUtensorMap &mB, int KpA, int KpB, const TcEpilogue &ep, int *err,
+                          const CUtensorMap &mB, const CUtensorMap &mB64, const CUtensorMap &mB128,
+                          int KpA, int KpB, const TcEpilogue &ep, int *err,
                           const int *dcnt, int mul_n, const GTile *tiles, int n_mtiles) {
   // persistent: one CTA per SM at most, each walking its share of the tiles
-  const int64_t n_tiles = epi == kBetaChunkSplit
+  const int64_t n_tiles = epi == kBetaPartSplit
                               ? (int64_t)n_mtiles * ((M + TC_BM - 1) / TC_BM)
                               : (int64_t)n_mtiles * ((N + BN - 1) / BN) * ep.ksplit;
   const int grid = (int)std::min<int64_t>(n_tiles, sm_count());
   switch (epi) {
     case kStoreF32:
-      return launch_tc<kStoreF32, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
-                                      tiles, n_mtiles);
+      return launch_tc<kStoreF32, BN, TF>(st, grid, mA, mB, mB64, mB128, M, N, KpA, KpB, ep, err,
+                                    dcnt, mul_n, tiles, n_mtiles);
     case kDscaleSplit:
-      return launch_tc<kDscaleSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
-                                         tiles, n_mtiles);
-    case kBetaChunkSplit:
-      return launch_tc<kBetaChunkSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt,
-                                                mul_n, tiles, n_mtiles);
+      return launch_tc<kDscaleSplit, BN, TF>(st, grid, mA, mB, mB64, mB128, M, N, KpA, KpB, ep, err,
+                                    dcnt, mul_n, tiles, n_mtiles);
+    case kBetaPartSplit:
+      return launch_tc<kBetaPartSplit, BN, TF>(st, grid, mA, mB, mB64, mB128, M, N, KpA, KpB, ep,
+                                               err, dcnt, mul_n, tiles, n_mtiles);
     case kGammaCatSplit:
-      return launch_tc<kGammaCatSplit, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
-                                           tiles, n_mtiles);
+      return launch_tc<kGammaCatSplit, BN, TF>(st, grid, mA, mB, mB64, mB128, M, N, KpA, KpB, ep,
+                                               err, dcnt, mul_n, tiles, n_mtiles);
     case kPartialF32:
-      return launch_tc<kPartialF32, BN, TF>(st, grid, mA, mB, M, N, KpA, KpB, ep, err, dcnt, mul_n,
-                                        tiles, n_mtiles);
+      return launch_tc<kPartialF32, BN, TF>(st, grid, mA, mB, mB64, mB128, M, N, KpA, KpB, ep, err,
+                                    dcnt, mul_n, tiles, n_mtiles);
     default:
       return cudaErrorInvalidValue;
   }
@@ -768,24 +822,25 @@ cudaError_t launch_tc_epi(cudaStream_t st, int epi, int M, int N, const CUtensor
 cudaError_t dispatch_bn(cudaStream_t st, int epi, int M, int N, const TcOperand &A,
                         const TcOperand &B, const TcEpilogue &e, int *err, const int *dcnt,
                         int mul_n, const GTile *tiles, int n_mtiles, int bn) {
+  // (the 64- and 128-row B maps go along for step 2's per-part boxes)
   if (A.tf32) {
     if (bn == 64)
-      return launch_tc_epi<64, true>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, e, err, dcnt,
-                                     mul_n, tiles, n_mtiles);
+      return launch_tc_epi<64, true>(st, epi, M, N, A.map, B.map64, B.map64, B.map, A.Kp, B.Kp, e,
+                                     err, dcnt, mul_n, tiles, n_mtiles);
     if (bn == 256)
-      return launch_tc_epi<256, true>(st, epi, M, N, A.map, B.map256, A.Kp, B.Kp, e, err, dcnt,
-                                      mul_n, tiles, n_mtiles);
-    return launch_tc_epi<128, true>(st, epi, M, N, A.map, B.map, A.Kp, B.Kp, e, err, dcnt, mul_n,
-                                    tiles, n_mtiles);
+      return launch_tc_epi<256, true>(st, epi, M, N, A.map, B.map256, B.map64, B.map, A.Kp, B.Kp,
+                                      e, err, dcnt, mul_n, tiles, n_mtiles);
+    return launch_tc_epi<128, true>(st, epi, M, N, A.map, B.map, B.map64, B.map, A.Kp, B.Kp, e,
+                                    err, dcnt, mul_n, tiles, n_mtiles);
   }
   if (bn == 64)
-    return launch_tc_epi<64, false>(st, epi, M, N, A.map, B.map64, A.Kp, B.Kp, e, err, dcnt,
-                                    mul_n, tiles, n_mtiles);
+    return launch_tc_epi<64, false>(st, epi, M, N, A.map, B.map64, B.map64, B.map, A.Kp, B.Kp, e,
+                                    err, dcnt, mul_n, tiles, n_mtiles);
   if (bn == 256)
-    return launch_tc_epi<256, false>(st, epi, M, N, A.map, B.map256, A.Kp, B.Kp, e, err, dcnt,
-                                     mul_n, tiles, n_mtiles);
-  return launch_tc_epi<128, false>(st, epi, M, N, A.map, B.map, A.Kp, B.Kp, e, err, dcnt, mul_n,
-                                   tiles, n_mtiles);
+    return launch_tc_epi<256, false>(st, epi, M, N, A.map, B.map256, B.map64, B.map, A.Kp, B.Kp, e,
+                                     err, dcnt, mul_n, tiles, n_mtiles);
+  return launch_tc_epi<128, false>(st, epi, M, N, A.map, B.map, B.map64, B.map, A.Kp, B.Kp, e, err,
+                                   dcnt, mul_n, tiles, n_mtiles);
 }
 }  // namespace
 
@@ -830,11 +885,13 @@ cudaError_t launch_gemm_tc_grouped(cudaStream_t st, const TcOperand &A, const Tc
   tc_init_attributes();
   if (bn == 64 && !B.has64) return cudaErrorInvalidValue;
   if (A.tf32 != B.tf32) return cudaErrorInvalidValue;
-  if (epi == kPartialF32 && bn > 128) return cudaErrorInvalidValue;   // two M blocks: 4 bn TMEM columns
+  // two M blocks need 4 bn TMEM columns; the part-based step 2 needs 16 x 16
+  if (epi == kPartialF32 && bn > 128) return cudaErrorInvalidValue;
+  if (epi == kBetaPartSplit && bn != 256) return cudaErrorInvalidValue;
   TcEpilogue e = ep;
   e.ksplit = 1;
   // step 2: the N columns of the launch are the M axis (rows of A = Ycat)
-  return dispatch_bn(st, epi, epi == kBetaChunkSplit ? N : 0, N, A, B, e, err, dcnt, mul_n, tiles,
+  return dispatch_bn(st, epi, epi == kBetaPartSplit ? N : 0, N, A, B, e, err, dcnt, mul_n, tiles,
                      n_tiles, bn);
 }
 

@@ -149,13 +149,7 @@ struct GTile {
   int row0, xoff, nkb, rows, atom, pad0, pad1, pad2;
 };
 
-// Orbitals per chunk of the reduced-precision step 2 (a multiple of 16:
-// each epilogue thread writes 16 of a chunk's orbitals as one 32-byte run).
-// 16 measured fastest: 32 halves the union lists' extra MMA work but reads
-// more vertex bytes per launch, and took 2.9 against 2.0 ms per product.
-constexpr int kStep2Chunk = 16;
-
-enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1, kBetaChunkSplit = 2, kGammaCatSplit = 3, kPartialF32 = 4 };
+enum TcEpi { kStoreF32 = 0, kDscaleSplit = 1, kBetaPartSplit = 2, kGammaCatSplit = 3, kPartialF32 = 4 };
 
 // A bf16 operand [rows][2*Kp] ([hi | lo] planes) with its TMA descriptor.
 struct TcOperand {
@@ -188,6 +182,7 @@ struct TcEpilogue {
   const int *aoff = nullptr;       // kGammaCatSplit
   const int *orb_atom = nullptr;   // kGammaCatSplit
   const int *xoff5 = nullptr;      // kGammaCatSplit
+  const int4 *parts = nullptr;     // kBetaPartSplit: the chunks' parts
 };
 
 cudaError_t make_operand_map(TcOperand &op, const void *base, int64_t rows, int Kp, int box_rows,
@@ -202,13 +197,14 @@ cudaError_t launch_gemm_tc(cudaStream_t st, const TcOperand &A, const TcOperand 
                            int epi, const TcEpilogue &ep, int *err, const int *dcnt = nullptr,
                            int mul_n = 0, int bn = 128);
 // Grouped product over a tile table (see GTile):
-//   kBetaChunkSplit the table runs over the B operand (chunk rows of the
-//                   step-2 operand, atom = chunk k, rows = valid rows, xoff =
-//                   the K offset of the chunk's Ycat segment in A); A = Ycat,
-//                   its rows (the M axis, N columns of the launch, 128-row
-//                   tiles fastest) are the columns m = 2 s + p.  Column
-//                   n = (k n_occ + E) 16 + c16 of the tile: beta^T split at
-//                   row (s n_occ + E) 2 + p, columns 16 k .. 16 k + 15 (hi at
+//   kBetaPartSplit  (N tile 256) the table runs over (chunk k, E block b)
+//                   entries (atom = k, row0 = B row base, xoff / nkb = the
+//                   first part and the part count, rows = valid E); A =
+//                   Ycat, its rows (the M axis, N columns of the launch,
+//                   128-row tiles fastest) are the columns m = 2 s + p.  Each
+//                   part (an atom's run of the chunk's orbitals) is a K loop
+//                   of its own into its own columns c16 16 + e; the tile
+//                   writes beta^T row E M + m, columns 16 k .. 16 k + 15 (hi at
 //                   outB[row*ldo + col], lo at + lo_off), 16-byte stores
 //   kPartialF32     one table entry per tile (A rows, up to 256: two M
 //                   blocks sharing the B tile; B K offset and length);
@@ -370,14 +366,15 @@ struct AlphaRoute {
   int *orb_atom = nullptr;    // [n_orb]
   int ldp = 0;                // P2 row stride (2 S)
   // split bf16 (reduced-precision operator), or tf32 rows of the same bytes;
-  // its step 2 runs over 16-orbital chunks: a2 [rows2c][K2c] with row
-  // (k n_occ + E) 16 + c16, Ycat [2S][kcat2c] in chunk segments (lcatc)
+  // its step 2 runs over the parts of 16-orbital chunks: a2 [rows2p][K2max]
+  // with row ((k nEB + b) 16 + c16) 16 + e, Ycat [2S][kcat2] per atom
   bool lp = false;
   bool tf32 = false;
-  int K2c = 0, kcat2c = 0, n_tiles2c = 0;
-  int64_t rows2c = 0;          // 16 n_occ ceil(n_orb / 16)
-  GTile *tiles2c = nullptr;    // 128 chunk rows each; atom = chunk index
-  int *lcatc = nullptr;        // [kcat2c]
+  int n_tiles2p = 0;
+  int64_t rows2p = 0;          // 256 ceil(n_orb / 16) ceil(n_occ / 16)
+  GTile *tiles2p = nullptr;    // per (chunk, E block): row0, parts index (xoff) and
+                               // count (nkb), valid E (rows), chunk (atom)
+  int4 *parts = nullptr;       // {c16 start | n << 8, atom, Ycat K offset, K blocks}
   GTile *tiles5lp = nullptr;   // step 5 of the reduced-precision operator: 256-row entries
   int n_tiles5lp = 0;
   TcOperand a2, a5, ycat, gcat;

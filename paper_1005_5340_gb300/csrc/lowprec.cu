@@ -4,7 +4,7 @@
 // product runs on the tensor cores in split bf16 (or, in the TF32 forms, in
 // tf32; the same buffers hold Kp floats per row instead of the [hi | lo]
 // planes) with float32 accumulation (gemm_tc.cu): K z, step 2 (per
-// 16-orbital chunk, alpha.cu), X_virt^T beta with the D(omega) epilogue,
+// 16-orbital chunk in per-atom parts, alpha.cu), X_virt^T beta with the D(omega) epilogue,
 // X_virt a into the per-atom Gcat rows, step 5 (per atom).
 // Layouts (n = right-hand-side column, complex planes interleaved per
 // occupied state):
@@ -226,8 +226,8 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
   }
   if (!lp.ar) return cudaErrorInvalidValue;
   const AlphaRoute &ar = *lp.ar;
-  // steps 1-2 on the stored transition vertex: gather v^nu per 16-orbital
-  // chunk, then beta^T = Ycat_k alpha_k^T per chunk on the tensor cores
+  // steps 1-2 on the stored transition vertex: gather v^nu per atom, then
+  // beta^T per 16-orbital chunk, part by part, on the tensor cores
   {
     Scope sc(lp.timer, st, kcAlphaGather, 0.0);
     err = launch_alpha_gather_lp(st, ar, ncols, mode == kA ? (const void *)lp.Yt : Zin,
@@ -241,8 +241,9 @@ cudaError_t launch_apply_operator_lp(cudaStream_t st, const DevSystem &sys, LpWo
     eb.ldo = 2 * (int64_t)lp.Kp1;
     eb.lo_off = lp.Kp1;
     eb.n_occ = sys.n_occ;
-    err = launch_gemm_tc_grouped(st, ar.ycat, ar.a2, ar.tiles2c, ar.n_tiles2c, ncols,
-                                 kBetaChunkSplit, eb, lp.err, lp.dcnt, 2);
+    eb.parts = ar.parts;
+    err = launch_gemm_tc_grouped(st, ar.ycat, ar.a2, ar.tiles2p, ar.n_tiles2p, ncols,
+                                 kBetaPartSplit, eb, lp.err, lp.dcnt, 2, 256);
     if (err != cudaSuccess) return err;
   }
   const double tflops = 2.0 * sys.n_virt * (double)sys.n_orb * (double)N1;

@@ -117,6 +117,36 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
           smem_u32(bar))
       : "memory");
 }
+// Sixteen 4-column loads at columns taddr + 16 c (c = 0..15), then the wait:
+// v[c][j] = column 16 c + j of this thread's lane.
+__device__ __forceinline__ void tmem_ld4x16(uint32_t taddr, float (&v)[16][4]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%64];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%65];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%66];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%67];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16, %17, %18, %19}, [%68];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20, %21, %22, %23}, [%69];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24, %25, %26, %27}, [%70];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%28, %29, %30, %31}, [%71];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%32, %33, %34, %35}, [%72];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%36, %37, %38, %39}, [%73];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%40, %41, %42, %43}, [%74];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%44, %45, %46, %47}, [%75];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%48, %49, %50, %51}, [%76];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%52, %53, %54, %55}, [%77];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%56, %57, %58, %59}, [%78];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%60, %61, %62, %63}, [%79];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u), "r"(taddr + 64u), "r"(taddr + 80u), "r"(taddr + 96u), "r"(taddr + 112u), "r"(taddr + 128u), "r"(taddr + 144u), "r"(taddr + 160u), "r"(taddr + 176u), "r"(taddr + 192u), "r"(taddr + 208u), "r"(taddr + 224u), "r"(taddr + 240u)
+      : "memory");
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[c][j] = __uint_as_float(r[4 * c + j]);
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
