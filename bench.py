@@ -74,7 +74,7 @@ KERNEL_OF_CLASS = {
 # flop of a kernel, from ncu captures (one kernel, a few launches) whose
 # summaries are under profiles/; None where no capture of the current
 # kernel exists.
-TRAFFIC_PER_FLOP = {"gemm_tc_kernel": 32.15e9 / 8.938e12}   # profiles/gemm_tc_dram_large256.md
+TRAFFIC_PER_FLOP = {"gemm_tc_kernel": 31.06e9 / 8.938e12}   # profiles/gemm_tc_dram_large256.md
 
 
 def measured_peaks():
