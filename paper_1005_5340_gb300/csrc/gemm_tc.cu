@@ -263,22 +263,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                    int n_mtiles) {
   // graph replays: right-hand-side columns beyond the live count are
   // skipped (whole tiles); they are the M axis of step 2, else the N axis
-  constexpr bool kChunk = EPI == kBetaPartSplit;
+  constexpr bool kPart = EPI == kBetaPartSplit;
   // the part-based step 2 is built for the 256-wide tile (16 c16 x 16 e)
-  if (kChunk && TC_BN != 256) return;
+  if (kPart && TC_BN != 256) return;
   if (dcnt) {
-    const int live = (int)min((int64_t)(kChunk ? M : N), (int64_t)mul_n * (*dcnt));
-    if (kChunk)
+    const int live = (int)min((int64_t)(kPart ? M : N), (int64_t)mul_n * (*dcnt));
+    if (kPart)
       M = live;
     else
       N = live;
   }
   // step 2: n_ntiles counts the M tiles of the columns, run fastest
-  const int n_ntiles = kChunk ? (M + TC_BM - 1) / TC_BM : (N + TC_BN - 1) / TC_BN;
+  const int n_ntiles = kPart ? (M + TC_BM - 1) / TC_BM : (N + TC_BN - 1) / TC_BN;
   // the N tiles share the columns evenly (multiples of 16, at most TC_BN):
   // tiles of one M row block then run at the same pace, so the second one
   // finds the A tile (the large operand of the K product) still in L2
-  const int tn = kChunk ? TC_BN : min(TC_BN, ((N + n_ntiles - 1) / n_ntiles + 15) & ~15);
+  const int tn = kPart ? TC_BN : min(TC_BN, ((N + n_ntiles - 1) / n_ntiles + 15) & ~15);
   const int ksplit = ep.ksplit;
   const int n_tiles = n_mtiles * n_ntiles * ksplit;
   if ((int)blockIdx.x >= n_tiles) return;
@@ -310,13 +310,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // fastest, so consecutive CTAs (in a cluster: one GPC, one L2 partition)
   // read the same A tile, which DRAM then supplies once;
   // xa / xb: K offsets (elements) of the A and B tiles within a plane
-  // step 2 (kChunk): the table runs over (chunk, E block) entries, the M
+  // step 2 (kPart): the table runs over (chunk, E block) entries, the M
   // tiles of the columns fastest, so that DRAM supplies each B block once;
   // xa = the first part, nkb = the part count, rows_valid = the valid E,
   // n0 = the B row base of the entry
   auto tile_of = [&](int t, int &m0, int &xa, int &xb, int &nkb, int &rows_valid, int &atom,
                      int &n0) {
-    if (kChunk) {
+    if (kPart) {
       const GTile g = tiles[t / n_ntiles];
       m0 = (t % n_ntiles) * TC_BM;
       xa = g.xoff;
@@ -393,10 +393,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int m0, xa, xoff, nkb, rv, at, n0;
         tile_of(t, m0, xa, xoff, nkb, rv, at, n0);
         // step 2: one K loop per part (its atom's Ycat segment, its B rows)
-        const int nparts = kChunk ? nkb : 1;
+        const int nparts = kPart ? nkb : 1;
         for (int p = 0; p < nparts && ok; ++p) {
         int pxa = xa, pxb = xoff, prow = n0, pnkb = nkb, pncol = TC_BN;
-        if (kChunk) {
+        if (kPart) {
           const int4 pi = ep.parts[xa + p];
           pxa = pi.z;
           pxb = 0;
@@ -425,10 +425,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           // 256), whose bytes the stage then expects
           const CUtensorMap *mb = &mapB;
           uint32_t bbytes = B_BYTES;
-          if (kChunk && pncol <= 64) {
+          if (kPart && pncol <= 64) {
             mb = &mapB64;
             bbytes = 64 * TC_BK * 2;
-          } else if (kChunk && pncol <= 128) {
+          } else if (kPart && pncol <= 128) {
             mb = &mapB128;
             bbytes = 128 * TC_BK * 2;
           }
@@ -478,11 +478,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int nblk = (kM2 && rv > TC_BM) ? 2 : 1;
         // step 2: one K loop per part, into the part's own columns
         // (c16 start x 16, N = 16 x its orbitals) with its own descriptor
-        const int nparts = kChunk ? nkb : 1;
+        const int nparts = kPart ? nkb : 1;
         for (int p = 0; p < nparts && ok; ++p) {
         int pnkb = nkb;
         uint32_t pidesc = idesc, d = d0;
-        if (kChunk) {
+        if (kPart) {
           const int4 pi = ep.parts[xa + p];
           const int ncol = (pi.x >> 8) * 16;
           pnkb = pi.w;
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int half = ((tn >> 4) + 1) / 2 * 16;
       const int j_lo = kM2 ? 0 : ((warp >= 6) ? half : 0);
       const int j_hi = kM2 ? tn : ((warp >= 6) ? tn : half);
-      if (kChunk) {
+      if (kPart) {
         // step 2: tensor-memory column c16 16 + e holds orbital 16 k + c16
         // (k = atom, the chunk) and occupied state E = 16 eb + e of column
         // m = m0 + lr; each warp of a lane quadrant takes 8 of the 16 e, four
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
-      for (int j0 = j_lo; j0 < j_hi && !kChunk; j0 += 16) {
+      for (int j0 = j_lo; j0 < j_hi && !kPart; j0 += 16) {
         DscaleIn di;
         di.eocc = eocc;
         if (EPI == kDscaleSplit) {
